@@ -1,0 +1,315 @@
+/*
+ * safhire.h -- C ABI of the GB300 (sm_103a) implementation of the server side
+ * of one Safhire round (arXiv 2509.01253): a network's linear layer evaluated
+ * as plaintext-weight x RLWE-ciphertext products on RNS ciphertexts, followed
+ * by the secret output shuffle and fast packing, with no bootstrapping.
+ *
+ * Conventions (every entry point):
+ *  - Returns sf_status (SF_OK = 0).  On failure a human-readable message is
+ *    kept per thread; read it with sf_last_error().  No exception crosses the ABI.
+ *  - Handles (sf_params, sf_ctx, sf_secret_key, sf_rotkeys, sf_layer) are
+ *    owned by the library; free them with the matching *_destroy.
+ *  - Buffers named d_* are CALLER-owned device pointers, h_* are caller-owned
+ *    host pointers.  The library never frees them and keeps no reference
+ *    after the call returns (device work it enqueued may still read them until
+ *    the stream reaches that point).
+ *  - Residues are uint64 words in [0, q) for every modulus (30- and 50-bit
+ *    primes alike).  A ciphertext is uint64[2][L][N]: part 0 is the mask a,
+ *    part 1 is b = a*s + m + e (Sec. 2.1 sign convention), limb-major, natural
+ *    coefficient order.  Arrays of ciphertexts are uint64[count][2][L][N].
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is enqueued on it and may still be running when a
+ *    call returns, unless the call writes a host buffer (then it synchronises
+ *    the stream before returning).  Errors detected on the device are latched
+ *    in a device status word that sf_sync() reports.
+ *  - Nothing here falls back to the CPU: without a usable CUDA device every
+ *    device entry point fails with SF_ECUDA.
+ *
+ * Parameters: t = 2 instance of the paper's prime-power cyclotomic ring
+ * (M = 2N, N = phi(M) a power of two, Sec. 2.1), RNS modulus Q = prod q_i of
+ * L data primes plus P = prod p_k of K special primes for hybrid key
+ * switching; all primes are 1 mod 2N.  Key-switch digits are consecutive
+ * groups of K data limbs, dnum = ceil(L / K).
+ */
+#ifndef SAFHIRE_H
+#define SAFHIRE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* status                                                                    */
+/* ------------------------------------------------------------------------ */
+
+typedef int32_t sf_status;
+
+#define SF_OK 0
+#define SF_EINVAL 1   /* invalid argument: null pointer, size or index out of range, unknown key */
+#define SF_ENOMEM 2   /* host or device allocation failed, or a memory budget was exceeded */
+#define SF_ECUDA 3    /* a CUDA runtime call failed, or no usable device */
+#define SF_ETIMEOUT 4 /* a bounded device-side wait ran out (status word set by a kernel) */
+#define SF_ESTALE 5   /* serving: message for a stale or mismatched (session, round) */
+#define SF_ERANGE 6   /* a value does not fit the requested representation */
+#define SF_EBUSY 7    /* serving: admission refused (no slot or memory free) */
+#define SF_ENOTSUP 8  /* valid request that this build does not implement */
+
+/* Copies the calling thread's last error message into buf (always
+ * NUL-terminated when len > 0) and returns the status that set it. */
+sf_status sf_last_error(char *buf, size_t len);
+
+/* Library version string (static storage). */
+const char *sf_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* parameters (host only)                                                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct sf_params sf_params;
+
+/* Sec. 2.1, Table 2 (parameter roles).  Ring degree N = 2^log_n with
+ * 10 <= log_n <= 16.  n_data (1..8) data primes of data_bits bits and
+ * n_special (1..4) special primes of special_bits bits, 20 <= bits <= 50.
+ * Primes: the largest primes below 2^bits that are 1 mod 2N, in descending
+ * order; when data_bits == special_bits the first n_special found are the
+ * special primes and the next n_data the data primes.  sigma: standard
+ * deviation of the rounded Gaussian noise.  Errors: SF_EINVAL for values
+ * out of range, SF_ENOMEM. */
+sf_status sf_params_create(int32_t log_n, int32_t n_data, int32_t data_bits, int32_t n_special,
+                           int32_t special_bits, double sigma, sf_params **out);
+void sf_params_destroy(sf_params *p);
+
+#define SF_MAX_MODULI 12
+typedef struct {
+    int32_t log_n;
+    int32_t n;          /* N */
+    int32_t n_data;     /* L */
+    int32_t n_special;  /* K */
+    int32_t dnum;       /* key-switch digits, ceil(L / K) */
+    double sigma;
+    uint64_t moduli[SF_MAX_MODULI]; /* q_0..q_{L-1}, then p_0..p_{K-1} */
+} sf_params_info;
+
+sf_status sf_params_get_info(const sf_params *p, sf_params_info *out);
+
+/* ------------------------------------------------------------------------ */
+/* context: one per (params, device)                                         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct sf_ctx sf_ctx;
+
+/* Uploads the NTT, base-conversion and automorphism tables to `device` and
+ * makes that device current for every later call on this context.  The
+ * params handle must outlive the context.  Errors: SF_EINVAL, SF_ECUDA,
+ * SF_ENOMEM. */
+sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **out);
+void sf_ctx_destroy(sf_ctx *ctx);
+
+/* Tuning and instrumentation knobs (name, value):
+ *   "ks_batch"      merges per key-switch batch (1..4096; default chosen per N)
+ *   "leaf_chunk"    linear-layer outputs per leaf batch (power of two)
+ *   "use_graph"     1 = capture a layer's launch sequence in a CUDA graph and
+ *                   replay it (default 1), 0 = launch directly
+ *   "kernel_timing" 1 = bracket every launch with CUDA events on its stream
+ *                   and accumulate per-kernel times (read with sf_kernel_stats)
+ * Errors: SF_EINVAL for an unknown name or value. */
+sf_status sf_ctx_set_option(sf_ctx *ctx, const char *name, int64_t value);
+
+/* Waits for `stream`, then reports (and clears) the context's device status
+ * word: SF_OK, or the first error a kernel latched (SF_ETIMEOUT, SF_EINVAL). */
+sf_status sf_sync(sf_ctx *ctx, void *stream);
+
+/* Per-kernel counters since the last reset: for each kernel family, the
+ * number of launches and (when kernel_timing is on) the summed device time.
+ * names/launches/ms are arrays of `cap` entries; *count receives the number
+ * of families (at most cap are written).  Names are static strings. */
+sf_status sf_kernel_stats(sf_ctx *ctx, const char **names, int64_t *launches, double *ms,
+                          int32_t cap, int32_t *count);
+sf_status sf_kernel_stats_reset(sf_ctx *ctx);
+
+/* ------------------------------------------------------------------------ */
+/* keys, encryption, decryption (client side; used by tests and the bench)  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct sf_secret_key sf_secret_key;
+typedef struct sf_rotkeys sf_rotkeys;
+
+/* Sec. 2.1 / Sec. 4.2: secret key s(X) with N coefficients uniform in
+ * {-1, 0, 1}, drawn from SplitMix64(seed) with Lemire's bounded draw.  The
+ * key stays resident on the context's device.  Errors: SF_ECUDA, SF_ENOMEM. */
+sf_status sf_keygen(sf_ctx *ctx, uint64_t seed, sf_secret_key **out);
+void sf_secret_key_destroy(sf_secret_key *sk);
+/* Copies s(X) to h_s (int64[N]). */
+sf_status sf_secret_key_export(const sf_secret_key *sk, int64_t *h_s);
+
+/* Sec. 4.2: key-switching keys for the automorphisms X -> X^d, one per entry
+ * of d[0..nd-1] (odd, 1 < d < 2N); d = NULL / nd = 0 selects the set the
+ * packing needs, {2^k + 1 : 1 <= k <= log2 N}.  Key for d, digit j:
+ * (alpha_j, alpha_j*s + e_j - P*g_j*s(X^d)) mod PQ, g_j the CRT gadget of
+ * digit j.  Randomness: SplitMix64 stream seeded with seed XOR d*0x9E3779B97F4A7C15;
+ * per digit alpha over the L+K moduli then e.  Keys stay resident on the
+ * device until destroyed.  Errors: SF_EINVAL (bad d), SF_ECUDA, SF_ENOMEM. */
+sf_status sf_gen_rotation_keys(sf_ctx *ctx, const sf_secret_key *sk, const int32_t *d, int32_t nd,
+                               uint64_t seed, sf_rotkeys **out);
+void sf_rotkeys_destroy(sf_rotkeys *rk);
+/* Copies the key for d to h_key, uint64[dnum][2][L+K][N], coefficient
+ * domain (tests compare it with an independent implementation). */
+sf_status sf_rotkeys_export(sf_ctx *ctx, const sf_rotkeys *rk, int32_t d, uint64_t *h_key);
+
+/* Fixed-point encoding of inputs: out[i] = round(scale * x[i]), half away
+ * from zero.  Errors: SF_ERANGE if a result does not fit int64. */
+sf_status sf_encode_input(const double *x, int64_t count, double scale, int64_t *out);
+
+/* Sec. 4.3 "Flatten and chunk" + Sec. 2.1: encrypts h_msg[0..count) (int64,
+ * count <= n_cts * N, zero-padded) into n_cts ciphertexts at d_cts
+ * (uint64[n_cts][2][L][N]).  Randomness: one SplitMix64(seed) stream, per
+ * ciphertext the mask a limb by limb (Lemire draw mod q_i) then the error
+ * (rounded Box-Muller Gaussian, sigma).  Errors: SF_EINVAL, SF_ECUDA. */
+sf_status sf_encrypt(sf_ctx *ctx, const sf_secret_key *sk, const int64_t *h_msg, int64_t count,
+                     uint64_t seed, uint64_t *d_cts, int32_t n_cts, void *stream);
+
+/* Sec. 2.1 decryption without the final projection: h_residues receives
+ * b - a*s mod q_i, uint64[n_cts][L][N].  Synchronises `stream`. */
+sf_status sf_decrypt(sf_ctx *ctx, const sf_secret_key *sk, const uint64_t *d_cts, int32_t n_cts,
+                     uint64_t *h_residues, void *stream);
+
+/* Sec. 4.5 client read-out: CRT of the residues (uint64[n_cts][L][N]) to the
+ * centred integer in (-Q/2, Q/2], divided by scale.  Value v is read from
+ * ciphertext v / (N/stride) at coefficient (v mod (N/stride)) * stride, for
+ * v < count.  Errors: SF_EINVAL if count exceeds n_cts * N / stride. */
+sf_status sf_decode(const sf_params *p, const uint64_t *h_residues, int32_t n_cts, int32_t stride,
+                    int32_t count, double scale, double *out);
+
+/* ------------------------------------------------------------------------ */
+/* linear layers                                                             */
+/* ------------------------------------------------------------------------ */
+
+/* One linear term of a layer (Sec. 4.4 "Convolution"; Sec. 5 f(x) = Ax + b):
+ * a convolution over the input segment of H x W x C_in values (row-major,
+ * channels last, Sec. 4.3) that starts at flat index in_offset of the layer
+ * input.  Output H' x W' x C_out with H' = (H + 2 pad - kh) / stride + 1.
+ * A fully connected layer is H = W = kh = kw = 1; global-average-pooled FC is
+ * a kernel as large as its input; a residual shortcut is a second term over
+ * its own input segment (all terms must agree on H', W', C_out). */
+typedef struct {
+    int32_t in_offset;
+    int32_t H, W, C_in;
+    int32_t C_out;
+    int32_t kh, kw;
+    int32_t stride, pad;
+} sf_conv_term;
+
+typedef struct sf_layer sf_layer;
+
+/* Quantises and uploads the weights: Wq = round(weight_scale * W) for every
+ * term (W: float64, per term [C_out][kh][kw][C_in], terms concatenated), and
+ * the optional bias (float64[C_out], NULL = none) as round(bias_scale * b).
+ * The quantised integers stay resident on the device.  Errors: SF_EINVAL
+ * (geometry), SF_ERANGE (|Wq| >= 2^62), SF_ENOMEM, SF_ECUDA. */
+sf_status sf_encode_weights(sf_ctx *ctx, const sf_conv_term *terms, int32_t n_terms, const double *W,
+                            const double *bias, double weight_scale, double bias_scale,
+                            sf_layer **out);
+void sf_layer_destroy(sf_layer *layer);
+
+typedef struct {
+    int32_t E_in;        /* flattened input values */
+    int32_t E_out;       /* outputs E' */
+    int32_t k_in;        /* input ciphertexts ceil(E_in / N) */
+    int32_t group_size;  /* n = min(N/2, next power of two >= E') values per packed ciphertext */
+    int32_t n_groups;    /* packed output ciphertexts ceil(E' / n) */
+    int64_t ks_count;    /* key switches of the paper's algorithm: groups * ((n-1) + log2(N/n)) */
+} sf_layer_info;
+
+sf_status sf_layer_get_info(const sf_ctx *ctx, const sf_layer *layer, sf_layer_info *out);
+
+/* The server round for one linear layer (Sec. 4.4, steps 6-10, gamma = 0):
+ *   6 extraction: the row of stream position p = jN + k is N^-1 X^-k ct_j;
+ *   7 unshuffle: input index i sits at position sigma_prev^-1(i)
+ *     (h_sigma_prev: uint32[E_in], position -> index; NULL = identity, the
+ *     first round);
+ *   8 linear layer: y_o = sum_i Wq[o,i] * row(i), evaluated exactly as
+ *     sum_j w_{o,j}(X) * ct_j with the weight polynomial w_{o,j};
+ *   9 shuffle: leaf l of group g is y_{sigma_out(g n + l)} (h_sigma_out:
+ *     uint32[E_out]; NULL = no shuffle, the last layer, Sec. 5);
+ *  10 fast packing: PackLWEs tree over the n leaves of each group (padding
+ *     leaves are zero), then the field trace; packed value l sits at
+ *     coefficient l*N/n of output ciphertext g, times Wq*x scale; the bias
+ *     (if any) is added there.
+ * d_in: uint64[k_in][2][L][N]; d_out: uint64[out_capacity][2][L][N].
+ * *n_out receives the number of packed ciphertexts written.  The result is
+ * bit-identical to the paper's algorithm evaluated literally.
+ * Errors: SF_EINVAL (k_in mismatch, capacity too small, missing key, bad
+ * permutation), SF_ENOMEM, SF_ECUDA. */
+sf_status sf_eval_linear_layer(sf_ctx *ctx, const sf_layer *layer, const sf_rotkeys *rk,
+                               const uint64_t *d_in, int32_t k_in, const uint32_t *h_sigma_prev,
+                               const uint32_t *h_sigma_out, uint64_t *d_out, int32_t out_capacity,
+                               int32_t *n_out, void *stream);
+
+/* Same round with HOST buffers: copies h_in to the device, evaluates, and
+ * copies the packed ciphertexts back to h_out (uint64[out_capacity][2][L][N]).
+ * Synchronises `stream`.  Pinned host memory gives the fastest copies. */
+sf_status sf_eval_linear_layer_host(sf_ctx *ctx, const sf_layer *layer, const sf_rotkeys *rk,
+                                    const uint64_t *h_in, int32_t k_in, const uint32_t *h_sigma_prev,
+                                    const uint32_t *h_sigma_out, uint64_t *h_out, int32_t out_capacity,
+                                    int32_t *n_out, void *stream);
+
+/* Steps 6-8 only, for selected outputs: d_out[t] = y_{outputs[t]} (the RLWE
+ * row of that output before shuffling and packing), coefficient domain,
+ * uint64[n_outputs][2][L][N].  Errors: SF_EINVAL for an output index out of
+ * range. */
+sf_status sf_linear_outputs(sf_ctx *ctx, const sf_layer *layer, const uint64_t *d_in, int32_t k_in,
+                            const uint32_t *h_sigma_prev, const int32_t *h_outputs, int32_t n_outputs,
+                            uint64_t *d_out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* building blocks                                                           */
+/* ------------------------------------------------------------------------ */
+
+/* Sec. 2.2: for each of `count` ciphertexts, apply X -> X^d to a and b
+ * (RLWE under s(X^d)) and key-switch back to s(X) with the hybrid gadget:
+ * out = (ModDown(sum_j c_j alpha_j), tau_d(b) + ModDown(sum_j c_j b_j)),
+ * c_j = ModUp of digit j of tau_d(a).  d_ct, d_out: uint64[count][2][L][N]
+ * (may not overlap).  Errors: SF_EINVAL if rk holds no key for d. */
+sf_status sf_rotate(sf_ctx *ctx, const sf_rotkeys *rk, int32_t d, const uint64_t *d_ct, uint64_t *d_out,
+                    int32_t count, void *stream);
+
+/* Sec. 2.4 / Sec. 4.4 "Fast Packing" at t = 2: packs n_leaves ciphertexts
+ * (zero-padded to n, a power of two with n_leaves <= n <= N/2) into one
+ * ciphertext whose coefficient l*N/n is N times coefficient 0 of leaf l; all
+ * other coefficients are cleared by the field trace.  Uses (n - 1) + log2(N/n)
+ * key switches.  d_leaves: uint64[n_leaves][2][L][N]; d_out: uint64[2][L][N]. */
+sf_status sf_pack(sf_ctx *ctx, const sf_rotkeys *rk, const uint64_t *d_leaves, int32_t n_leaves, int32_t n,
+                  uint64_t *d_out, void *stream);
+
+/* Sec. 4.4 "Partial trace extraction" (Lemma 1) at gamma = 0 and t = 2: the
+ * RLWE row for coefficient i is N^-1 X^-i ct (its trace is an encryption of
+ * coefficient i).  gamma > 0 (client-supplied powers, d_powers) returns
+ * SF_ENOTSUP.  d_ct, d_out: uint64[2][L][N]. */
+sf_status sf_extract(sf_ctx *ctx, const uint64_t *d_ct, int32_t i, int32_t gamma, const uint64_t *d_powers,
+                     uint64_t *d_out, void *stream);
+
+/* Sec. 4.4 "Shuffle": sigma_r drawn uniformly from a seed derived from the
+ * session id and the round: Fisher-Yates from the top driven by
+ * SplitMix64(session_seed XOR round*0x9E3779B97F4A7C15) with Lemire draws;
+ * perm[k] = sigma(k) (position k holds row sigma(k)).  Host only. */
+sf_status sf_permutation(uint64_t session_seed, uint32_t round, uint32_t n, uint32_t *perm);
+
+/* Gathers whole ciphertexts: d_out[k] = d_in[h_perm[k]] for k < count
+ * (h_perm must be a permutation of [0, count)).  Errors: SF_EINVAL. */
+sf_status sf_shuffle_cts(sf_ctx *ctx, const uint32_t *h_perm, const uint64_t *d_in, uint64_t *d_out,
+                         int32_t count, void *stream);
+
+/* Negacyclic product per limb (via the NTT): d_out[t] = d_a[t] * d_b[t] in
+ * Z_{q_i}[X]/(X^N+1), arrays uint64[n_polys][L][N].  A test hook for the
+ * transform kernels. */
+sf_status sf_poly_mul(sf_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b, uint64_t *d_out, int32_t n_polys,
+                      void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAFHIRE_H */
