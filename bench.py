@@ -1,0 +1,395 @@
+"""Benchmark: encrypted linear layers per second on one GB300 (or N replicas).
+
+One step = one full server round of the benchmark layer through the C ABI
+(sf_eval_linear_layer): a ResNet-20 stage-1 convolution, 3x3, 16 -> 16
+channels on a 16x32x32 input, ring N = 2^14 with 3 x 50-bit data primes and
+one 50-bit special prime, fixed-point scale 2^40, with the input unshuffle and
+the output shuffle; 16384 leaf products, 16382 pack-tree merges and 2 trace
+steps (16384 automorphism + hybrid key switches), 2 packed output ciphertexts.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the CPU oracle (the plain schoolbook implementation
+under oracle/) on the host cores, on a bounded sample of the same workload
+extrapolated to whole layers.  Under torchrun each rank runs an independent
+replica (the round has no cross-GPU exchange); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encrypted linear layers/s"
+UNIT = "layers/s"
+WORKLOAD = ("conv16: ResNet-20 conv 3x3 16->16 on 16x32x32 (E = E' = 16384), N = 2^14, 3 x 50-bit + 1 "
+            "special prime, scale 2^40, input unshuffle + output shuffle, 2 packed outputs of 8192, "
+            "16384 key switches per layer")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ workload ----
+
+class Workload:
+    """Keys, weights and the encrypted input of the benchmark layer, resident on the device."""
+
+    def __init__(self, device: int):
+        import torch
+        import paper_2509_01253_gb300 as sf
+        from paper_2509_01253_gb300 import workloads as wl
+        self.sf, self.torch = sf, torch
+        self.ps = ps = wl.PARAMS["conv16"]
+        self.case = case = wl.conv16_case()
+        self.params = sf.sf_params_create(ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits, ps.sigma)
+        self.ctx = sf.sf_ctx_create(self.params, device)
+        self.sk = sf.sf_keygen(self.ctx, 203)
+        self.rk = sf.sf_gen_rotation_keys(self.ctx, self.sk, None, 205)
+        W = np.concatenate([w.ravel() for w in case.weights])
+        self.layer = sf.sf_encode_weights(self.ctx, case.terms, W, None, ps.delta, ps.delta ** 2)
+        self.info = sf.sf_layer_get_info(self.ctx, self.layer)
+        self.n, self.L = 1 << ps.log_n, ps.n_data
+        xs = case.x[case.sigma_prev.astype(np.int64)]
+        self.msg = sf.sf_encode_input(xs, ps.delta)
+        self.k_in, self.G = self.info["k_in"], self.info["n_groups"]
+        dev = f"cuda:{device}"
+        self.d_in = torch.zeros((self.k_in, 2, self.L, self.n), dtype=torch.int64, device=dev)
+        sf.sf_encrypt(self.ctx, self.sk, self.msg, 204, self.d_in, self.k_in)
+        self.d_out = torch.zeros((self.G, 2, self.L, self.n), dtype=torch.int64, device=dev)
+        self.stream = torch.cuda.current_stream(device)
+        self.ct_bytes = 2 * self.L * self.n * 8
+
+    def step(self):
+        self.sf.sf_eval_linear_layer(self.ctx, self.layer, self.rk, self.d_in, self.k_in, self.case.sigma_prev,
+                                     self.case.sigma_out, self.d_out, self.G, self.stream)
+
+    def check(self) -> float:
+        """Max |decoded - float64| over all outputs (not timed)."""
+        from paper_2509_01253_gb300 import workloads as wl
+        sf = self.sf
+        sf.sf_sync(self.ctx, self.stream)
+        res = np.zeros((self.G, self.L, self.n), dtype=np.uint64)
+        sf.sf_decrypt(self.ctx, self.sk, self.d_out, self.G, res, self.stream)
+        vals = sf.sf_decode(self.params, res, self.G, self.n // self.info["group_size"], self.info["E_out"],
+                            self.ps.delta ** 2)
+        ref = wl.float_reference(self.case)[self.case.sigma_out.astype(np.int64)]
+        return float(np.abs(vals - ref).max())
+
+
+def flush_l2(buf):
+    buf.add_(1)
+
+
+def launches(sf, ctx) -> dict:
+    return {name: (cnt, ms) for name, cnt, ms in sf.sf_kernel_stats(ctx)}
+
+
+# ------------------------------------------------------------ roofline ----
+
+def algorithmic_bytes(kernel: str, info: dict, n: int, L: int, K: int, dnum: int, launches_per_layer: int) -> float:
+    """Algorithmic HBM bytes per launch for the key-switch kernels: every
+    merge must read its pair of ciphertexts (2 x [2][L][N] words), write one
+    ciphertext, and read the rotation key once per launch batch; per the
+    5-kernel pipeline, each kernel's share is its own unavoidable operands."""
+    w = 8
+    ct = 2 * L * n * w
+    nm = L + K
+    merges = info["ks_count"]
+    per_merge = {
+        # gather u.a (E, O: L limbs each) -> write partial iNTT (L limbs)
+        "ks1_gather_inv_row": (2 * L + L) * n * w,
+        # read partial (L limbs), write digit extensions dnum*(nm - K) limbs
+        "ks2_modup_col": (L + dnum * (nm - 1)) * n * w,
+        # read extensions + own limbs, key 2*dnum*nm limbs, write 2*nm accumulators
+        "ks3_inner_row": (dnum * nm + 2 * dnum * nm + 2 * nm) * n * w,
+        # read 2K P-limbs, write 2L converted limbs
+        "ks4_moddown_col": (2 * K + 2 * L) * n * w,
+        # read 2L converted + 2L accumulators + E, O, write the merged ciphertext
+        "ks5_finish_row": (4 * L) * n * w + 3 * ct,
+    }
+    if kernel not in per_merge:
+        return 0.0
+    return per_merge[kernel] * merges / launches_per_layer
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs"), "measured"
+    except (OSError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------- CPU baseline ----
+
+def oracle_sample(max_seconds: float = 20.0):
+    """Times the oracle on a bounded sample of the benchmark layer: key
+    switches (rotate at N = 2^14) and leaf outputs, extrapolated to one layer
+    (16384 of each).  Returns (layers/s, cores, sample description)."""
+    import oracle as O
+    from paper_2509_01253_gb300 import workloads as wl
+    ps = wl.PARAMS["conv16"]
+    case = wl.conv16_case()
+    prm = O.make_params(ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits)
+    s_o = O.keygen(prm, 203)
+    keys = O.rotation_keys(prm, s_o, 205, [3])
+    xs = case.x[case.sigma_prev.astype(np.int64)]
+    cts = O.encrypt(prm, s_o, O.quantize(xs, ps.delta), 204, 1)
+    terms = [O.ConvTerm(t.in_offset, t.H, t.W, t.C_in, t.C_out, t.kh, t.kw, t.stride, t.pad) for t in case.terms]
+    lay = O.make_layer(terms, case.weights, None, ps.delta, ps.delta ** 2)
+    t0 = time.perf_counter()
+    n_leaf = 0
+    while True:
+        O.linear_output(prm, lay, cts, int(case.sigma_out[n_leaf % 16384]), case.sigma_prev)
+        n_leaf += 1
+        if n_leaf >= 8 or time.perf_counter() - t0 > max_seconds / 4:
+            break
+    t_leaf = (time.perf_counter() - t0) / n_leaf
+    t0 = time.perf_counter()
+    n_ks = 0
+    while True:
+        O.rotate(prm, keys, 3, cts[0])
+        n_ks += 1
+        if n_ks >= 2 or time.perf_counter() - t0 > max_seconds / 2:
+            break
+    t_ks = (time.perf_counter() - t0) / n_ks
+    t_layer = 16384 * t_leaf + 16384 * t_ks
+    cores = os.cpu_count()
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        pass
+    omp = os.environ.get("OMP_NUM_THREADS")
+    if omp:
+        cores = min(cores, int(omp))
+    desc = (f"{n_leaf} leaf outputs ({t_leaf:.3f} s each) + {n_ks} key switches ({t_ks:.2f} s each) of the "
+            f"conv16 layer at full size, extrapolated x16384 each (packing additions not counted)")
+    return 1.0 / t_layer, cores, desc
+
+
+# ----------------------------------------------------------------- main ----
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        return dist, ws, rank, local
+    return None, 1, 0, 0
+
+
+def run_reference(args, dist, ws, rank):
+    if rank != 0:
+        return 0
+    times = []
+    cores = desc = None
+    for i in range(args.warmup + args.steps):
+        v, cores, desc = oracle_sample(max_seconds=8.0)
+        if i >= args.warmup:
+            times.append(1.0 / v)
+    sec = sum(times) / len(times)
+    value = 1.0 / sec
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    dist, ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, dist, ws, rank)
+    import torch
+    import paper_2509_01253_gb300 as sf
+    torch.cuda.set_device(local)
+    wl_ = Workload(local)
+    stream = wl_.stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
+    for _ in range(max(3, args.warmup)):
+        wl_.step()
+    torch.cuda.synchronize()
+    err = wl_.check()
+    # ---- timed region: device-resident inputs
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    sf.sf_kernel_stats_reset(wl_.ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush_l2(flush)
+        ev[i][0].record(stream)
+        wl_.step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    stats = launches(sf, wl_.ctx)
+    n_launch = sum(c for c, _ in stats.values())
+    if dist:
+        t = torch.tensor([total_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t[0])
+    value = ws * args.steps / total_s
+    # ---- end to end: host buffers through the C ABI, copies inside the timed region
+    pin_in = torch.empty((wl_.k_in, 2, wl_.L, wl_.n), dtype=torch.int64, pin_memory=True)
+    pin_in.copy_(wl_.d_in.cpu())
+    pin_out = torch.empty((wl_.G, 2, wl_.L, wl_.n), dtype=torch.int64, pin_memory=True)
+    h_in = pin_in.numpy().view(np.uint64)
+    h_out = pin_out.numpy().view(np.uint64)
+    for _ in range(2):
+        sf.sf_eval_linear_layer_host(wl_.ctx, wl_.layer, wl_.rk, h_in, wl_.k_in, wl_.case.sigma_prev,
+                                     wl_.case.sigma_out, h_out, wl_.G, stream)
+    if dist:
+        dist.barrier()
+    e2e_s = 0.0
+    for i in range(args.steps):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sf.sf_eval_linear_layer_host(wl_.ctx, wl_.layer, wl_.rk, h_in, wl_.k_in, wl_.case.sigma_prev,
+                                     wl_.case.sigma_out, h_out, wl_.G, stream)
+        e2e_s += time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t[0])
+    e2e_value = ws * args.steps / e2e_s
+    h2d = wl_.k_in * wl_.ct_bytes + 4 * (wl_.info["E_in"] + wl_.info["E_out"])
+    d2h = wl_.G * wl_.ct_bytes
+    # ---- per-kernel device time (instrumented pass: events around every launch)
+    sf.sf_kernel_stats_reset(wl_.ctx)
+    sf.sf_ctx_set_option(wl_.ctx, "kernel_timing", 1)
+    k_steps = max(2, min(args.steps, 5))
+    for _ in range(k_steps):
+        flush_l2(flush)
+        wl_.step()
+    torch.cuda.synchronize()
+    kstats = launches(sf, wl_.ctx)
+    sf.sf_ctx_set_option(wl_.ctx, "kernel_timing", 0)
+    total_kernel_ms = sum(ms for _, ms in kstats.values())
+    top = max(kstats, key=lambda k: kstats[k][1])
+    cnt, ms = kstats[top]
+    per_layer = cnt // k_steps
+    p_info = sf.sf_params_get_info(wl_.params)
+    alg = algorithmic_bytes(top, wl_.info, wl_.n, wl_.L, p_info["n_special"], p_info["dnum"], per_layer)
+    avg_s = ms / cnt / 1e3
+    peak, peak_kind = load_peaks()
+    achieved = alg / avg_s / 1e9 if alg else None
+    roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "peak_source": peak_kind, "avg_launch_us": avg_s * 1e6, "launches_per_layer": per_layer,
+                "share_of_device_time": ms / total_kernel_ms if total_kernel_ms else None}
+    kernel_table = {k: {"launches_per_layer": c // k_steps, "ms_per_layer": m / k_steps} for k, (c, m) in kstats.items() if c}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "ks_batch": None, "max_abs_err": err},
+            "clocks": clk, "gpu_launches": n_launch // 1,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": roofline, "kernels": kernel_table}
+    if rank == 0 and not args.no_cpu_baseline:
+        v, cores, desc = oracle_sample()
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

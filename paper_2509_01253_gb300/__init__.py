@@ -1,0 +1,354 @@
+"""Thin Python binding of the C ABI in include/safhire.h.
+
+Every function has the name of the C entry point it calls and only marshals
+arguments: device buffers are passed as raw pointers (ints) or objects with a
+``data_ptr()`` (torch tensors), host arrays as numpy arrays, streams as
+``torch.cuda.Stream`` / raw handles / None.  A non-zero status raises
+:class:`SafhireError` with the library's message.  All computation happens in
+the CUDA library ``_safhire.so``; there is no CPU fallback: if the library
+cannot be built or loaded, or no GPU is present, the calls fail.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SF_OK, SF_EINVAL, SF_ENOMEM, SF_ECUDA, SF_ETIMEOUT, SF_ESTALE, SF_ERANGE, SF_EBUSY, SF_ENOTSUP = range(9)
+SF_MAX_MODULI = 12
+
+
+class SafhireError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"[status {status}] {message}")
+        self.status = status
+        self.message = message
+
+
+class sf_params_info(ctypes.Structure):
+    _fields_ = [("log_n", ctypes.c_int32), ("n", ctypes.c_int32), ("n_data", ctypes.c_int32),
+                ("n_special", ctypes.c_int32), ("dnum", ctypes.c_int32), ("sigma", ctypes.c_double),
+                ("moduli", ctypes.c_uint64 * SF_MAX_MODULI)]
+
+
+class sf_conv_term(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int32) for f in ("in_offset", "H", "W", "C_in", "C_out", "kh", "kw", "stride", "pad")]
+
+
+class sf_layer_info(ctypes.Structure):
+    _fields_ = [("E_in", ctypes.c_int32), ("E_out", ctypes.c_int32), ("k_in", ctypes.c_int32),
+                ("group_size", ctypes.c_int32), ("n_groups", ctypes.c_int32), ("ks_count", ctypes.c_int64)]
+
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_u32 = ctypes.c_uint32
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+_dbl = ctypes.c_double
+_pp = ctypes.POINTER(ctypes.c_void_p)
+
+_SIGS = {
+    "sf_last_error": (_i32, [ctypes.c_char_p, ctypes.c_size_t]),
+    "sf_version": (ctypes.c_char_p, []),
+    "sf_params_create": (_i32, [_i32, _i32, _i32, _i32, _i32, _dbl, _pp]),
+    "sf_params_destroy": (None, [_vp]),
+    "sf_params_get_info": (_i32, [_vp, ctypes.POINTER(sf_params_info)]),
+    "sf_ctx_create": (_i32, [_vp, _i32, _pp]),
+    "sf_ctx_destroy": (None, [_vp]),
+    "sf_ctx_set_option": (_i32, [_vp, ctypes.c_char_p, _i64]),
+    "sf_sync": (_i32, [_vp, _vp]),
+    "sf_kernel_stats": (_i32, [_vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_i64),
+                               ctypes.POINTER(_dbl), _i32, ctypes.POINTER(_i32)]),
+    "sf_kernel_stats_reset": (_i32, [_vp]),
+    "sf_keygen": (_i32, [_vp, _u64, _pp]),
+    "sf_secret_key_destroy": (None, [_vp]),
+    "sf_secret_key_export": (_i32, [_vp, _vp]),
+    "sf_gen_rotation_keys": (_i32, [_vp, _vp, _vp, _i32, _u64, _pp]),
+    "sf_rotkeys_destroy": (None, [_vp]),
+    "sf_rotkeys_export": (_i32, [_vp, _vp, _i32, _vp]),
+    "sf_encode_input": (_i32, [_vp, _i64, _dbl, _vp]),
+    "sf_encrypt": (_i32, [_vp, _vp, _vp, _i64, _u64, _vp, _i32, _vp]),
+    "sf_decrypt": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp]),
+    "sf_decode": (_i32, [_vp, _vp, _i32, _i32, _i32, _dbl, _vp]),
+    "sf_encode_weights": (_i32, [_vp, ctypes.POINTER(sf_conv_term), _i32, _vp, _vp, _dbl, _dbl, _pp]),
+    "sf_layer_destroy": (None, [_vp]),
+    "sf_layer_get_info": (_i32, [_vp, _vp, ctypes.POINTER(sf_layer_info)]),
+    "sf_eval_linear_layer": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _i32, ctypes.POINTER(_i32), _vp]),
+    "sf_eval_linear_layer_host": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _i32, ctypes.POINTER(_i32), _vp]),
+    "sf_linear_outputs": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp]),
+    "sf_rotate": (_i32, [_vp, _vp, _i32, _vp, _vp, _i32, _vp]),
+    "sf_pack": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp]),
+    "sf_extract": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp]),
+    "sf_permutation": (_i32, [_u64, _u32, _u32, _vp]),
+    "sf_shuffle_cts": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
+    "sf_poly_mul": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.OUT
+
+
+def lib() -> ctypes.CDLL:
+    """Loads _safhire.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != SF_OK:
+        buf = ctypes.create_string_buffer(512)
+        lib().sf_last_error(buf, 512)
+        raise SafhireError(st, buf.value.decode(errors="replace"))
+
+
+def _ptr(x):
+    """Device or host buffer -> integer address (None stays None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a buffer")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    raise TypeError(f"cannot pass {type(s)} as a stream")
+
+
+def _out_handle(fn, *args):
+    h = ctypes.c_void_p()
+    _check(fn(*args, ctypes.byref(h)))
+    return h.value
+
+
+# ------------------------------------------------------------------ params --
+
+def sf_version() -> str:
+    return lib().sf_version().decode()
+
+
+def sf_params_create(log_n, n_data, data_bits, n_special, special_bits, sigma=3.2):
+    return _out_handle(lib().sf_params_create, log_n, n_data, data_bits, n_special, special_bits, sigma)
+
+
+def sf_params_destroy(p):
+    lib().sf_params_destroy(p)
+
+
+def sf_params_get_info(p) -> dict:
+    info = sf_params_info()
+    _check(lib().sf_params_get_info(p, ctypes.byref(info)))
+    nm = info.n_data + info.n_special
+    return {"log_n": info.log_n, "n": info.n, "n_data": info.n_data, "n_special": info.n_special,
+            "dnum": info.dnum, "sigma": info.sigma, "moduli": [int(info.moduli[i]) for i in range(nm)]}
+
+
+# ----------------------------------------------------------------- context --
+
+def sf_ctx_create(params, device=0):
+    return _out_handle(lib().sf_ctx_create, params, device)
+
+
+def sf_ctx_destroy(ctx):
+    lib().sf_ctx_destroy(ctx)
+
+
+def sf_ctx_set_option(ctx, name: str, value: int):
+    _check(lib().sf_ctx_set_option(ctx, name.encode(), int(value)))
+
+
+def sf_sync(ctx, stream=None):
+    _check(lib().sf_sync(ctx, _stream(stream)))
+
+
+def sf_kernel_stats(ctx) -> list:
+    cap = 64
+    names = (ctypes.c_char_p * cap)()
+    launches = (ctypes.c_int64 * cap)()
+    ms = (ctypes.c_double * cap)()
+    cnt = ctypes.c_int32()
+    _check(lib().sf_kernel_stats(ctx, names, launches, ms, cap, ctypes.byref(cnt)))
+    return [(names[i].decode(), int(launches[i]), float(ms[i])) for i in range(min(cnt.value, cap))]
+
+
+def sf_kernel_stats_reset(ctx):
+    _check(lib().sf_kernel_stats_reset(ctx))
+
+
+# -------------------------------------------------------------------- keys --
+
+def sf_keygen(ctx, seed: int):
+    return _out_handle(lib().sf_keygen, ctx, seed)
+
+
+def sf_secret_key_destroy(sk):
+    lib().sf_secret_key_destroy(sk)
+
+
+def sf_secret_key_export(sk, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.int64)
+    _check(lib().sf_secret_key_export(sk, _ptr(out)))
+    return out
+
+
+def sf_gen_rotation_keys(ctx, sk, d=None, seed=0):
+    if d is None:
+        return _out_handle(lib().sf_gen_rotation_keys, ctx, sk, None, 0, seed)
+    arr = np.ascontiguousarray(d, dtype=np.int32)
+    return _out_handle(lib().sf_gen_rotation_keys, ctx, sk, _ptr(arr), arr.size, seed)
+
+
+def sf_rotkeys_destroy(rk):
+    lib().sf_rotkeys_destroy(rk)
+
+
+def sf_rotkeys_export(ctx, rk, d: int, out: np.ndarray) -> np.ndarray:
+    _check(lib().sf_rotkeys_export(ctx, rk, d, _ptr(out)))
+    return out
+
+
+# ------------------------------------------------------ encrypt / decrypt --
+
+def sf_encode_input(x, scale: float) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    out = np.zeros(x.size, dtype=np.int64)
+    _check(lib().sf_encode_input(_ptr(x), x.size, scale, _ptr(out)))
+    return out
+
+
+def sf_encrypt(ctx, sk, msg, seed: int, d_cts, n_cts: int, stream=None):
+    msg = np.ascontiguousarray(msg, dtype=np.int64).ravel()
+    _check(lib().sf_encrypt(ctx, sk, _ptr(msg) if msg.size else None, msg.size, seed, _ptr(d_cts), n_cts,
+                            _stream(stream)))
+
+
+def sf_decrypt(ctx, sk, d_cts, n_cts: int, out: np.ndarray, stream=None) -> np.ndarray:
+    if out.dtype != np.uint64:
+        raise TypeError("residues are uint64")
+    _check(lib().sf_decrypt(ctx, sk, _ptr(d_cts), n_cts, _ptr(out), _stream(stream)))
+    return out
+
+
+def sf_decode(params, residues: np.ndarray, n_cts: int, stride: int, count: int, scale: float) -> np.ndarray:
+    residues = np.ascontiguousarray(residues, dtype=np.uint64)
+    out = np.zeros(count, dtype=np.float64)
+    _check(lib().sf_decode(params, _ptr(residues), n_cts, stride, count, scale, _ptr(out)))
+    return out
+
+
+# ------------------------------------------------------------------ layers --
+
+def _terms(terms):
+    arr = (sf_conv_term * len(terms))()
+    for i, t in enumerate(terms):
+        if isinstance(t, dict):
+            vals = [t.get(f, 0 if f in ("in_offset", "pad") else 1) for f, _ in sf_conv_term._fields_]
+        else:
+            vals = [getattr(t, f, 0 if f in ("in_offset", "pad") else 1) for f, _ in sf_conv_term._fields_]
+        for (f, _), v in zip(sf_conv_term._fields_, vals):
+            setattr(arr[i], f, int(v))
+    return arr
+
+
+def sf_encode_weights(ctx, terms, W, bias, weight_scale: float, bias_scale: float = 0.0):
+    arr = _terms(terms)
+    w = np.ascontiguousarray(W, dtype=np.float64).ravel()
+    b = None if bias is None else np.ascontiguousarray(bias, dtype=np.float64).ravel()
+    return _out_handle(lib().sf_encode_weights, ctx, arr, len(terms), _ptr(w), _ptr(b), weight_scale, bias_scale)
+
+
+def sf_layer_destroy(layer):
+    lib().sf_layer_destroy(layer)
+
+
+def sf_layer_get_info(ctx, layer) -> dict:
+    info = sf_layer_info()
+    _check(lib().sf_layer_get_info(ctx, layer, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in sf_layer_info._fields_}
+
+
+def _perm(p):
+    return None if p is None else np.ascontiguousarray(p, dtype=np.uint32)
+
+
+def sf_eval_linear_layer(ctx, layer, rk, d_in, k_in: int, sigma_prev, sigma_out, d_out, out_capacity: int,
+                         stream=None) -> int:
+    sp, so = _perm(sigma_prev), _perm(sigma_out)
+    n_out = ctypes.c_int32()
+    _check(lib().sf_eval_linear_layer(ctx, layer, rk, _ptr(d_in), k_in, _ptr(sp), _ptr(so), _ptr(d_out),
+                                      out_capacity, ctypes.byref(n_out), _stream(stream)))
+    return n_out.value
+
+
+def sf_eval_linear_layer_host(ctx, layer, rk, h_in: np.ndarray, k_in: int, sigma_prev, sigma_out, h_out: np.ndarray,
+                              out_capacity: int, stream=None) -> int:
+    sp, so = _perm(sigma_prev), _perm(sigma_out)
+    n_out = ctypes.c_int32()
+    _check(lib().sf_eval_linear_layer_host(ctx, layer, rk, _ptr(h_in), k_in, _ptr(sp), _ptr(so), _ptr(h_out),
+                                           out_capacity, ctypes.byref(n_out), _stream(stream)))
+    return n_out.value
+
+
+def sf_linear_outputs(ctx, layer, d_in, k_in: int, sigma_prev, outputs, d_out, stream=None):
+    sp = _perm(sigma_prev)
+    outs = np.ascontiguousarray(outputs, dtype=np.int32)
+    _check(lib().sf_linear_outputs(ctx, layer, _ptr(d_in), k_in, _ptr(sp), _ptr(outs), outs.size, _ptr(d_out),
+                                   _stream(stream)))
+
+
+# --------------------------------------------------------- building blocks --
+
+def sf_rotate(ctx, rk, d: int, d_ct, d_out, count: int, stream=None):
+    _check(lib().sf_rotate(ctx, rk, d, _ptr(d_ct), _ptr(d_out), count, _stream(stream)))
+
+
+def sf_pack(ctx, rk, d_leaves, n_leaves: int, n: int, d_out, stream=None):
+    _check(lib().sf_pack(ctx, rk, _ptr(d_leaves), n_leaves, n, _ptr(d_out), _stream(stream)))
+
+
+def sf_extract(ctx, d_ct, i: int, gamma: int, d_powers, d_out, stream=None):
+    _check(lib().sf_extract(ctx, _ptr(d_ct), i, gamma, _ptr(d_powers), _ptr(d_out), _stream(stream)))
+
+
+def sf_permutation(session_seed: int, rnd: int, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.uint32)
+    _check(lib().sf_permutation(session_seed, rnd, n, _ptr(out) if n else None))
+    return out
+
+
+def sf_shuffle_cts(ctx, perm, d_in, d_out, count: int, stream=None):
+    p = _perm(perm)
+    _check(lib().sf_shuffle_cts(ctx, _ptr(p), _ptr(d_in), _ptr(d_out), count, _stream(stream)))
+
+
+def sf_poly_mul(ctx, d_a, d_b, d_out, n_polys: int, stream=None):
+    _check(lib().sf_poly_mul(ctx, _ptr(d_a), _ptr(d_b), _ptr(d_out), n_polys, _stream(stream)))
+
+
+EXPORTED = sorted(_SIGS)

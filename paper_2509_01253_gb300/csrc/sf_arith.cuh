@@ -1,0 +1,109 @@
+// sf_arith.cuh -- 64-bit modular arithmetic for moduli q < 2^51.
+//
+// Residues live in uint64 words.  Three published reductions are used:
+//  * Shoup (1996) / Harvey (2014) multiplication by a fixed operand w with the
+//    precomputed companion w' = floor(w * 2^64 / q): for any x < 2^64,
+//    x*w - floor(x*w'/2^64)*q lies in [0, 2q).
+//  * Montgomery (1985) REDC with R = 2^64 for products of two variable
+//    residues: for T < q*2^64, (T + m q)/2^64 with m = T * (-q^-1) mod 2^64
+//    lies in [0, 2q) and equals T * 2^-64 mod q.
+//  * Harvey's lazy butterflies keep NTT values in [0, 4q) (forward) and
+//    [0, 2q) (inverse); 4q < 2^53 leaves ample headroom in 64 bits.
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define SF_HD __host__ __device__ __forceinline__
+#else
+#define SF_HD inline
+#endif
+
+typedef uint64_t u64;
+
+SF_HD u64 sf_mulhi(u64 a, u64 b)
+{
+#if defined(__CUDA_ARCH__)
+    return __umul64hi(a, b);
+#else
+    return (u64)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// x*w mod q in [0, 2q) for any x < 2^64; w < q, wp = floor(w 2^64 / q).
+SF_HD u64 sf_mul_shoup_lazy(u64 x, u64 w, u64 wp, u64 q)
+{
+    u64 qhat = sf_mulhi(x, wp);
+    return x * w - qhat * q;
+}
+
+SF_HD u64 sf_mul_shoup(u64 x, u64 w, u64 wp, u64 q)
+{
+    u64 r = sf_mul_shoup_lazy(x, w, wp, q);
+    return r >= q ? r - q : r;
+}
+
+SF_HD u64 sf_csub(u64 x, u64 q) { return x >= q ? x - q : x; }
+
+SF_HD u64 sf_add(u64 a, u64 b, u64 q) { return sf_csub(a + b, q); }
+
+SF_HD u64 sf_sub(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+
+// 128-bit accumulator for sums of products (hi, lo).
+struct sf_u128 {
+    u64 lo, hi;
+};
+
+SF_HD void sf_mac128(sf_u128 &acc, u64 a, u64 b)
+{
+    u64 lo = a * b;
+    u64 hi = sf_mulhi(a, b);
+    u64 nlo = acc.lo + lo;
+    acc.hi += hi + (nlo < lo ? 1 : 0);
+    acc.lo = nlo;
+}
+
+// Montgomery REDC: returns T * 2^-64 mod q in [0, 2q) for T = hi*2^64 + lo < q*2^64.
+// qinv_neg = -q^-1 mod 2^64.
+SF_HD u64 sf_redc_lazy(u64 hi, u64 lo, u64 q, u64 qinv_neg)
+{
+    u64 m = lo * qinv_neg;
+    u64 mq_hi = sf_mulhi(m, q);
+    // lo + (m*q mod 2^64) == 0 mod 2^64, with a carry out exactly when lo != 0
+    return hi + mq_hi + (lo != 0 ? 1 : 0);
+}
+
+SF_HD u64 sf_redc(u64 hi, u64 lo, u64 q, u64 qinv_neg)
+{
+    return sf_csub(sf_redc_lazy(hi, lo, q, qinv_neg), q);
+}
+
+// a * b_mont * 2^-64 mod q: with b_mont = b * 2^64 mod q this is a*b mod q.
+SF_HD u64 sf_mul_mont(u64 a, u64 b_mont, u64 q, u64 qinv_neg)
+{
+    return sf_redc(sf_mulhi(a, b_mont), a * b_mont, q, qinv_neg);
+}
+
+// Forward (Cooley-Tukey) lazy butterfly: X, Y in [0, 4q) -> X', Y' in [0, 4q).
+SF_HD void sf_bfly_ct(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 two_q)
+{
+    u64 x = X >= two_q ? X - two_q : X;
+    u64 t = sf_mul_shoup_lazy(Y, w, wp, q);
+    X = x + t;
+    Y = x - t + two_q;
+}
+
+// Inverse (Gentleman-Sande) lazy butterfly: X, Y in [0, 2q) -> X', Y' in [0, 2q).
+SF_HD void sf_bfly_gs(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 two_q)
+{
+    u64 x = X + Y;
+    u64 t = X - Y + two_q;
+    X = x >= two_q ? x - two_q : x;
+    Y = sf_mul_shoup_lazy(t, w, wp, q);
+}
+
+// Reduce a lazy value in [0, 4q) to [0, q).
+SF_HD u64 sf_reduce4(u64 x, u64 q, u64 two_q)
+{
+    x = x >= two_q ? x - two_q : x;
+    return x >= q ? x - q : x;
+}

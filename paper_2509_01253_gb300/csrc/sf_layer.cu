@@ -1,0 +1,351 @@
+// sf_layer.cu -- the linear-layer round (Sec. 4.4, steps 6-10) on the GPU.
+//
+// Steps 6-8 (extraction at gamma = 0, unshuffle, linear layer): the row
+// extracted for stream position p = jN + k is N^-1 X^-k ct_j, so output o is
+//     y_o = sum_j w_{o,j}(X) * ct_j,   w_{o,j} = N^-1 sum_{taps i in ct j} Wq[o,i] X^-k(i)
+// with k(i) the in-ciphertext position of input i after unshuffling
+// (p = sigma_prev^-1(i)).  Two kernels per batch of outputs:
+//   leaf_col : builds the sparse w_{o,j} column tile straight in shared memory
+//              (no global read) and runs the forward column pass,
+//   leaf_row : forward row pass, then the product with every input ciphertext
+//              (NTT domain, Montgomery form) accumulated in 128 bits -> leaf.
+// Step 9 (shuffle) is the slot -> output map sigma_out; step 10 (packing) is
+// the PackLWEs tree plus field trace driven by sf_pack_tree below.
+#include "sf_internal.h"
+#include "sf_kernels.cuh"
+#include "sf_ks.h"
+#include "sf_layer.h"
+
+__device__ __forceinline__ int leaf_output(const SfLeafParams &P, int slot)
+{
+    if (slot >= P.n_slots_valid) return -1;
+    return P.sig_out ? P.sig_out[slot] : slot;
+}
+
+// leaf_col: grid (C/16 column tiles, k_in * L, slots)
+__global__ void __launch_bounds__(SF_THREADS) k_leaf_col(SfRing R, SfLeafParams P)
+{
+    extern __shared__ u64 sm[];
+    const SfGeo g = ring_geo(R);
+    const int c0 = blockIdx.x * SF_TC;
+    const int j = blockIdx.y / R.L, i = blockIdx.y % R.L;
+    const int slot = P.s0 + blockIdx.z;
+    const int o = leaf_output(P, slot);
+    if (o < 0) return;
+    const int ne = col_tile_elems(g);
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) sm[e] = 0;
+    __syncthreads();
+    const SfMod &M = R.m[i];
+    const int co = o % P.C_out, hw = o / P.C_out;
+    const int ho = hw / P.W_out, wo = hw % P.W_out;
+    for (int ti = 0; ti < P.n_terms; ++ti) {
+        const SfTermDev &T = P.t[ti];
+        const int ntap = T.kh * T.kw * T.C_in;
+        for (int tt = threadIdx.x; tt < ntap; tt += blockDim.x) {
+            int dh = tt / (T.kw * T.C_in), rem = tt % (T.kw * T.C_in);
+            int dw = rem / T.C_in, ci = rem % T.C_in;
+            int h = ho * T.stride - T.pad + dh, w = wo * T.stride - T.pad + dw;
+            if (h < 0 || h >= T.H || w < 0 || w >= T.W) continue;
+            int idx = T.in_offset + (h * T.W + w) * T.C_in + ci;
+            int p = P.pos_of ? P.pos_of[idx] : idx;
+            if ((p >> R.log_n) != j) continue;
+            int k = p & (R.n - 1);
+            int cidx = k ? R.n - k : 0;
+            int col = cidx & (g.c - 1);
+            if (col < c0 || col >= c0 + SF_TC) continue;
+            int64_t wq = P.wq[T.w_off + ((size_t)(co * T.kh + dh) * T.kw + dw) * T.C_in + ci];
+            int64_t r = wq % (int64_t)M.q;
+            u64 v = (u64)(r < 0 ? r + (int64_t)M.q : r);
+            v = sf_mul_shoup(v, M.ninv, M.ninv_p, M.q);
+            if (k && v) v = M.q - v;   // X^-k = -X^(N-k)
+            sm[(cidx >> g.log_c) * SF_TC + (col - c0)] = v;
+        }
+    }
+    __syncthreads();
+    tile_forward(sm, col_tile_desc(g), R.psi + ((size_t)i << R.log_n), R.psi_p + ((size_t)i << R.log_n), M.q);
+    u64 *dst = P.w1 + (((size_t)blockIdx.z * P.k_in + j) * R.L + i) * R.n;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) dst[col_tile_gidx(g, c0, e)] = sm[e];
+}
+
+// leaf_row: grid (R/16 row tiles, L, slots)
+template <int EPT>
+__global__ void __launch_bounds__(SF_THREADS) k_leaf_row(SfRing R, SfLeafParams P)
+{
+    extern __shared__ u64 sm[];
+    const SfGeo g = ring_geo(R);
+    const int r0 = blockIdx.x * SF_TR, i = blockIdx.y;
+    const int slot = P.s0 + blockIdx.z;
+    const int o = leaf_output(P, slot);
+    const size_t tile_off = (size_t)r0 * g.c;
+    u64 *leaf = P.leaves + P.leaf_stride * blockIdx.z;
+    u64 *da = leaf + ((size_t)i << R.log_n) + tile_off;
+    u64 *db = leaf + ((size_t)(R.L + i) << R.log_n) + tile_off;
+    if (o < 0) {
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+            int e = threadIdx.x + k * SF_THREADS;
+            da[e] = 0;
+            db[e] = 0;
+        }
+        return;
+    }
+    const SfMod M = R.m[i];
+    const TileDesc td = row_tile_desc(g, r0);
+    sf_u128 acc_a[EPT], acc_b[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) acc_a[k] = acc_b[k] = {0, 0};
+    for (int j = 0; j < P.k_in; ++j) {
+        const u64 *src = P.w1 + (((size_t)blockIdx.z * P.k_in + j) * R.L + i) * R.n + tile_off;
+        for (int e = threadIdx.x; e < SF_TR * g.c; e += blockDim.x) sm[e] = src[e];
+        __syncthreads();
+        tile_forward(sm, td, R.psi + ((size_t)i << R.log_n), R.psi_p + ((size_t)i << R.log_n), M.q);
+        const u64 *ca = P.ct_mont + (((size_t)j * 2 + 0) * R.L + i) * R.n + tile_off;
+        const u64 *cb = P.ct_mont + (((size_t)j * 2 + 1) * R.L + i) * R.n + tile_off;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+            int e = threadIdx.x + k * SF_THREADS;
+            u64 w = sm[e];
+            sf_mac128(acc_a[k], w, __ldg(ca + e));
+            sf_mac128(acc_b[k], w, __ldg(cb + e));
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+        int e = threadIdx.x + k * SF_THREADS;
+        da[e] = sf_redc(acc_a[k].hi, acc_a[k].lo, M.q, M.qinv_neg);
+        db[e] = sf_redc(acc_b[k].hi, acc_b[k].lo, M.q, M.qinv_neg);
+    }
+}
+
+sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStream_t st)
+{
+    const SfRing &R = ctx->ring;
+    if (cnt <= 0) return SF_OK;
+    const size_t col_tile = sizeof(u64) * R.r * SF_TC, row_tile = sizeof(u64) * R.c * SF_TR;
+    cudaEvent_t ev;
+    for (int off = 0; off < cnt; off += 65535) {
+        SfLeafParams p = P;
+        int c = std::min(65535, cnt - off);
+        p.s0 = P.s0 + off;
+        p.w1 = P.w1;    // w1 holds `cnt` slots; reuse from its start for each sub-launch
+        p.leaves = P.leaves + P.leaf_stride * off;
+        sf_launch_begin(ctx, SFK_LEAF_COL, st, &ev);
+        k_leaf_col<<<dim3(R.c / SF_TC, P.k_in * R.L, c), SF_THREADS, col_tile, st>>>(R, p);
+        sf_launch_end(ctx, SFK_LEAF_COL, st, ev);
+        sf_launch_begin(ctx, SFK_LEAF_ROW, st, &ev);
+        dim3 gr(R.r / SF_TR, R.L, c);
+        switch ((R.c * SF_TR) / SF_THREADS) {
+        case 2: k_leaf_row<2><<<gr, SF_THREADS, row_tile, st>>>(R, p); break;
+        case 4: k_leaf_row<4><<<gr, SF_THREADS, row_tile, st>>>(R, p); break;
+        case 8: k_leaf_row<8><<<gr, SF_THREADS, row_tile, st>>>(R, p); break;
+        case 16: k_leaf_row<16><<<gr, SF_THREADS, row_tile, st>>>(R, p); break;
+        default: return sf_set_error(SF_EINVAL, "unsupported ring split");
+        }
+        sf_launch_end(ctx, SFK_LEAF_ROW, st, ev);
+    }
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+// ------------------------------------------------------------ pack tree --
+
+// G groups of n leaves in A ([G][n] ciphertexts, NTT domain); group g has
+// valid[g] non-zero leaves (the rest are zero).  B has room for [G][n/2].
+// Node i of a level is zero iff i >= valid[g]; a merge whose O-node is zero
+// runs without O (identical result, X^s * 0 = 0), and merges producing zero
+// nodes are skipped.  Result: G packed ciphertexts (NTT domain) at *res with
+// group stride *res_stride.
+sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int32_t> &key_d, size_t key_words,
+                       u64 *A, u64 *B, int G, int n, const std::vector<int> &valid, u64 *ks_scratch, int batch,
+                       u64 **res, size_t *res_stride, cudaStream_t st)
+{
+    const SfRing &R = ctx->ring;
+    const size_t ct = (size_t)2 * R.L * R.n;
+    auto key_for = [&](int d, const u64 **k) -> sf_status {
+        for (size_t t = 0; t < key_d.size(); ++t)
+            if (key_d[t] == d) {
+                *k = keys_base + key_words * t;
+                return SF_OK;
+            }
+        return sf_set_error(SF_EINVAL, "no rotation key for d = %d", d);
+    };
+    u64 *cur = A, *nxt = B;
+    size_t cur_gs = (size_t)n * ct, nxt_gs = (size_t)(n / 2 > 0 ? n / 2 : 1) * ct;
+    int log_n_grp = 0;
+    while ((1 << log_n_grp) < n) ++log_n_grp;
+    int full = 0;
+    while (full < G && valid[full] >= n) ++full;   // leading full groups
+    for (int lvl = 1; lvl <= log_n_grp; ++lvl) {
+        const int half = n >> lvl;
+        const int d = (1 << lvl) + 1;
+        const u64 *key;
+        SF_TRY(key_for(d, &key));
+        SfKsBatch kb;
+        memset(&kb, 0, sizeof(kb));
+        kb.E_stride = ct;
+        kb.O_stride = ct;
+        kb.out_stride = ct;
+        kb.E_outer = cur_gs;
+        kb.O_outer = cur_gs;
+        kb.out_outer = nxt_gs;
+        kb.d = d;
+        kb.s = (unsigned)(R.n >> lvl);
+        kb.add_v = 1;
+        kb.key = key;
+        if (full > 0) {
+            SfKsBatch b = kb;
+            b.E = cur;
+            b.O = cur + (size_t)half * ct;
+            b.out = nxt;
+            b.inner = half;
+            b.count = full * half;
+            SF_TRY(sf_ks_run(ctx, b, ks_scratch, batch, st));
+        }
+        for (int gi = full; gi < G; ++gi) {
+            const int V = valid[gi];
+            const int active = std::min(V, half);
+            const int with_o = std::max(0, std::min(active, V - half));
+            SfKsBatch b = kb;
+            b.E = cur + gi * cur_gs;
+            b.out = nxt + gi * nxt_gs;
+            b.inner = 1 << 30;
+            if (with_o > 0) {
+                SfKsBatch b1 = b;
+                b1.O = b.E + (size_t)half * ct;
+                b1.count = with_o;
+                SF_TRY(sf_ks_run(ctx, b1, ks_scratch, batch, st));
+            }
+            if (active > with_o) {
+                SfKsBatch b2 = b;
+                b2.O = nullptr;
+                b2.first = with_o;
+                b2.count = active - with_o;
+                SF_TRY(sf_ks_run(ctx, b2, ks_scratch, batch, st));
+            }
+        }
+        std::swap(cur, nxt);
+        std::swap(cur_gs, nxt_gs);
+    }
+    // field trace: for k = log2(n)+1 .. log2(N): ct <- ct + tau_{2^k+1}(ct)
+    for (int k = log_n_grp + 1; k <= R.log_n; ++k) {
+        const int d = (1 << k) + 1;
+        const u64 *key;
+        SF_TRY(key_for(d, &key));
+        SfKsBatch b;
+        memset(&b, 0, sizeof(b));
+        b.E = cur;
+        b.E_stride = cur_gs;
+        b.out = nxt;
+        b.out_stride = nxt_gs;
+        b.inner = 1 << 30;
+        b.count = G;
+        b.d = d;
+        b.add_v = 1;
+        b.key = key;
+        SF_TRY(sf_ks_run(ctx, b, ks_scratch, batch, st));
+        std::swap(cur, nxt);
+        std::swap(cur_gs, nxt_gs);
+    }
+    *res = cur;
+    *res_stride = cur_gs;
+    return SF_OK;
+}
+
+// ------------------------------------------------------------- small ops --
+
+// Bias (the affine part b of f(x) = Ax + b): b-part coefficient l*N/n of
+// group g gets bq[channel(sigma_out(g n + l))].
+__global__ void k_add_bias(SfRing R, u64 *out, int G, int n, int E_out, const int *sig_out, const int64_t *bq,
+                           int C_out)
+{
+    const size_t ct = (size_t)2 * R.L * R.n;
+    const int stride = R.n / n;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < G * n; x += gridDim.x * blockDim.x) {
+        if (x >= E_out) continue;
+        int g = x / n, l = x % n;
+        int o = sig_out ? sig_out[x] : x;
+        int64_t v = bq[o % C_out];
+        for (int i = 0; i < R.L; ++i) {
+            int64_t q = (int64_t)R.m[i].q;
+            int64_t r = v % q;
+            if (r < 0) r += q;
+            u64 *p = out + g * ct + ((size_t)(R.L + i) << R.log_n) + (size_t)l * stride;
+            *p = sf_add(*p, (u64)r, (u64)q);
+        }
+    }
+}
+
+sf_status sf_add_bias(sf_ctx *ctx, u64 *out, int G, int n, int E_out, const int *d_sig_out, const int64_t *d_bq,
+                      int C_out, cudaStream_t st)
+{
+    cudaEvent_t ev;
+    sf_launch_begin(ctx, SFK_ELEMWISE, st, &ev);
+    int total = G * n;
+    k_add_bias<<<std::max(1, std::min((total + 255) / 256, 1024)), 256, 0, st>>>(ctx->ring, out, G, n, E_out, d_sig_out,
+                                                                                 d_bq, C_out);
+    sf_launch_end(ctx, SFK_ELEMWISE, st, ev);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+// Whole-ciphertext gather: out[k] = in[perm[k]].
+__global__ void k_shuffle_cts(const u64 *in, u64 *out, const int *perm, int count, size_t ct_words)
+{
+    size_t total = (size_t)count * ct_words;
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
+        size_t k = x / ct_words, w = x % ct_words;
+        out[x] = in[(size_t)perm[k] * ct_words + w];
+    }
+}
+
+sf_status sf_shuffle_launch(sf_ctx *ctx, const u64 *in, u64 *out, const int *d_perm, int count, cudaStream_t st)
+{
+    const size_t ct = (size_t)2 * ctx->ring.L * ctx->ring.n;
+    cudaEvent_t ev;
+    sf_launch_begin(ctx, SFK_SHUFFLE, st, &ev);
+    size_t total = (size_t)count * ct;
+    k_shuffle_cts<<<(int)std::min<size_t>((total + 255) / 256, 152 * 32), 256, 0, st>>>(in, out, d_perm, count, ct);
+    sf_launch_end(ctx, SFK_SHUFFLE, st, ev);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+// Extraction at gamma = 0 (Lemma 1 with t = 2): out = N^-1 X^-i ct, coefficient domain.
+__global__ void k_extract(SfRing R, const u64 *ct, u64 *out, int i)
+{
+    const size_t total = (size_t)2 * R.L * R.n;
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
+        int limb = (int)((x >> R.log_n) % R.L);
+        int k = (int)(x & (R.n - 1));
+        size_t base = x - k;
+        const SfMod &M = R.m[limb];
+        // coefficient k of X^-i a = coefficient k + i of a, negated when k + i >= N
+        int src = k + i;
+        u64 v = ct[base + (src & (R.n - 1))];
+        if (src >= R.n && v) v = M.q - v;
+        out[x] = sf_mul_shoup(v, M.ninv, M.ninv_p, M.q);
+    }
+}
+
+sf_status sf_extract_launch(sf_ctx *ctx, const u64 *ct, u64 *out, int i, cudaStream_t st)
+{
+    cudaEvent_t ev;
+    sf_launch_begin(ctx, SFK_ELEMWISE, st, &ev);
+    size_t total = (size_t)2 * ctx->ring.L * ctx->ring.n;
+    k_extract<<<(int)((total + 255) / 256), 256, 0, st>>>(ctx->ring, ct, out, i);
+    sf_launch_end(ctx, SFK_ELEMWISE, st, ev);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+sf_status sf_layer_init_attributes()
+{
+    const int mx = 227 * 1024;
+    SF_CUDA_TRY(cudaFuncSetAttribute(k_leaf_col, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    SF_CUDA_TRY(cudaFuncSetAttribute(k_leaf_row<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    SF_CUDA_TRY(cudaFuncSetAttribute(k_leaf_row<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    SF_CUDA_TRY(cudaFuncSetAttribute(k_leaf_row<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    SF_CUDA_TRY(cudaFuncSetAttribute(k_leaf_row<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    return SF_OK;
+}

@@ -1,0 +1,35 @@
+// sf_layer.h -- linear-layer leaves, pack tree and small ciphertext ops.
+#pragma once
+#include "sf_internal.h"
+
+struct SfTermDev {
+    int in_offset, H, W, C_in, C_out, kh, kw, stride, pad;
+    int w_off;  // offset of this term's weights in the concatenated array
+};
+
+// Slot s (s0 <= s < s0 + count) of a leaf launch computes output sig_out[s]
+// (or s when sig_out is null); slots >= n_slots_valid are zero padding leaves.
+struct SfLeafParams {
+    SfTermDev t[2];
+    int n_terms;
+    int C_out, W_out;
+    int k_in;
+    int s0;
+    int n_slots_valid;
+    const int64_t *wq;      // quantised weights (device)
+    const int *pos_of;      // input index -> stream position (null = identity)
+    const int *sig_out;     // slot -> output index (null = identity)
+    const u64 *ct_mont;     // [k_in][2][L][N] NTT domain, Montgomery form
+    u64 *w1;                // [slots][k_in][L][N] column-pass scratch
+    u64 *leaves;            // leaf of slot s0 + z at leaves + z * leaf_stride
+    size_t leaf_stride;
+};
+
+sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStream_t st);
+sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int32_t> &key_d, size_t key_words,
+                       u64 *A, u64 *B, int G, int n, const std::vector<int> &valid, u64 *ks_scratch, int batch,
+                       u64 **res, size_t *res_stride, cudaStream_t st);
+sf_status sf_add_bias(sf_ctx *ctx, u64 *out, int G, int n, int E_out, const int *d_sig_out, const int64_t *d_bq,
+                      int C_out, cudaStream_t st);
+sf_status sf_shuffle_launch(sf_ctx *ctx, const u64 *in, u64 *out, const int *d_perm, int count, cudaStream_t st);
+sf_status sf_extract_launch(sf_ctx *ctx, const u64 *ct, u64 *out, int i, cudaStream_t st);

@@ -1,0 +1,372 @@
+"""GPU path against the CPU oracle, through the C ABI.
+
+Bit-exact on every residue for integer work (NTT products, keys, encryption,
+rotations, packing, whole layer rounds) on sizes the oracle finishes in
+seconds, spanning several tiles and ragged groups; at the full benchmark size
+(conv16: N = 2^14, 16384 outputs) on sampled outputs the oracle computes one
+by one, plus decrypted error <= 1e-3 against float64 on every output.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2509_01253_gb300 as sf
+from paper_2509_01253_gb300 import workloads as wl
+
+from _gpu import Session, dev_zeros, from_dev, gpu_layer, oracle_layer, oracle_params, stream_input, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    sf.lib()
+
+
+def _rand_residues(rng, mods, count, n):
+    return np.stack([np.stack([rng.integers(0, q, n, dtype=np.uint64) for q in mods]) for _ in range(count)])
+
+
+# ------------------------------------------------------------------ NTT ----
+
+@pytest.mark.parametrize("log_n,L,bits,K", [(10, 3, 50, 1), (11, 4, 50, 2), (12, 2, 30, 1), (13, 5, 50, 2)])
+def test_poly_mul_matches_schoolbook(oracle, log_n, L, bits, K):
+    """NTT -> pointwise -> inverse NTT equals the schoolbook negacyclic product."""
+    s = Session(log_n, L, bits, K, rot=False)
+    try:
+        rng = np.random.default_rng(log_n)
+        q = s.info["moduli"][:L]
+        a = _rand_residues(rng, q, 2, s.n)
+        b = _rand_residues(rng, q, 2, s.n)
+        out = dev_zeros(2, L, s.n)
+        sf.sf_poly_mul(s.ctx, to_dev(a), to_dev(b), out, 2 * L)
+        got = from_dev(out)
+        for t in range(2):
+            for i in range(L):
+                assert (got[t, i] == oracle.polymul(a[t, i], b[t, i], q[i])).all(), (t, i)
+    finally:
+        s.close()
+
+
+def test_poly_mul_full_size_sampled(oracle):
+    """One limb of a full N = 2^14 product (the benchmark ring)."""
+    ps = wl.PARAMS["conv16"]
+    s = Session.from_set(ps, rot=False)
+    try:
+        rng = np.random.default_rng(7)
+        q = s.info["moduli"][:s.L]
+        a = _rand_residues(rng, q, 1, s.n)
+        b = _rand_residues(rng, q, 1, s.n)
+        out = dev_zeros(1, s.L, s.n)
+        sf.sf_poly_mul(s.ctx, to_dev(a), to_dev(b), out, s.L)
+        got = from_dev(out)
+        assert (got[0, 1] == oracle.polymul(a[0, 1], b[0, 1], q[1])).all()
+    finally:
+        s.close()
+
+
+# ------------------------------------------------------- keys / encryption --
+
+@pytest.mark.parametrize("pset", ["fc64", "conv16"])
+def test_keygen_encrypt_decrypt_bit_exact(oracle, pset):
+    ps = wl.PARAMS[pset]
+    s = Session.from_set(ps, sk_seed=103, rot=False)
+    try:
+        prm = oracle_params(oracle, ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits)
+        assert s.info["moduli"] == prm.q + prm.p
+        s_o = oracle.keygen(prm, 103)
+        assert (sf.sf_secret_key_export(s.sk, s.n) == s_o).all()
+        rng = np.random.default_rng(5)
+        msg = rng.integers(-2 ** 40, 2 ** 40, s.n + 77)
+        d = s.encrypt(msg, 104, 2)
+        want = oracle.encrypt(prm, s_o, msg, 104, 2)
+        assert (from_dev(d) == want.reshape(2, 2, s.L, s.n)).all()
+        assert (s.decrypt(d, 2) == oracle.decrypt(prm, s_o, want)).all()
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("pset,ds", [("fc64", None), ("conv16", [3, 16385])])
+def test_rotation_keys_bit_exact(oracle, pset, ds):
+    ps = wl.PARAMS[pset]
+    s = Session.from_set(ps, sk_seed=11, rk_seed=12, rot_d=ds)
+    try:
+        prm = oracle_params(oracle, ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits)
+        s_o = oracle.keygen(prm, 11)
+        for d in (ds or oracle.default_rotation_indices(prm)):
+            got = np.zeros((prm.dnum, 2, prm.L + prm.K, prm.n), dtype=np.uint64)
+            sf.sf_rotkeys_export(s.ctx, s.rk, d, got)
+            assert (got == oracle.rotkey(prm, s_o, 12, d)).all(), d
+    finally:
+        s.close()
+
+
+# --------------------------------------------------------------- rotate -----
+
+@pytest.mark.parametrize("log_n,L,bits,K", [(10, 3, 50, 1), (10, 4, 50, 2), (10, 5, 50, 2), (11, 2, 30, 1)])
+def test_rotate_bit_exact_all_keys(oracle, log_n, L, bits, K):
+    s = Session(log_n, L, bits, K, sk_seed=21, rk_seed=22)
+    try:
+        prm = oracle_params(oracle, log_n, L, bits, K)
+        s_o = oracle.keygen(prm, 21)
+        keys = oracle.rotation_keys(prm, s_o, 22)
+        msg = np.random.default_rng(3).integers(-2 ** 20, 2 ** 20, 3 * s.n)
+        d_ct = s.encrypt(msg, 23, 3)
+        cts = from_dev(d_ct).reshape(3, 2, L, s.n)
+        out = dev_zeros(3, 2, L, s.n)
+        for d in oracle.default_rotation_indices(prm):
+            sf.sf_rotate(s.ctx, s.rk, d, d_ct, out, 3)
+            got = from_dev(out)
+            for j in range(3):
+                assert (got[j] == oracle.rotate(prm, keys, d, cts[j])).all(), (d, j)
+    finally:
+        s.close()
+
+
+def test_rotate_full_size(oracle):
+    """Benchmark ring N = 2^14, 3 x 50-bit + 1 special, the first-level and
+    the last trace automorphisms."""
+    ps = wl.PARAMS["conv16"]
+    ds = [3, 16385]
+    s = Session.from_set(ps, sk_seed=31, rk_seed=32, rot_d=ds)
+    try:
+        prm = oracle_params(oracle, ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits)
+        s_o = oracle.keygen(prm, 31)
+        keys = oracle.rotation_keys(prm, s_o, 32, ds)
+        msg = np.random.default_rng(4).integers(-2 ** 40, 2 ** 40, s.n)
+        d_ct = s.encrypt(msg, 33, 1)
+        ct = from_dev(d_ct).reshape(2, s.L, s.n)
+        out = dev_zeros(1, 2, s.L, s.n)
+        for d in ds:
+            sf.sf_rotate(s.ctx, s.rk, d, d_ct, out, 1)
+            assert (from_dev(out)[0] == oracle.rotate(prm, keys, d, ct)).all(), d
+    finally:
+        s.close()
+
+
+# ----------------------------------------------------------------- pack -----
+
+@pytest.mark.parametrize("n_leaves,n", [(1, 1), (2, 2), (5, 8), (8, 8), (64, 64), (100, 128), (3, 512)])
+def test_pack_bit_exact(oracle, n_leaves, n):
+    log_n, L, K = 10, 3, 1
+    s = Session(log_n, L, 50, K, sk_seed=41, rk_seed=42)
+    try:
+        prm = oracle_params(oracle, log_n, L, 50, K)
+        s_o = oracle.keygen(prm, 41)
+        keys = oracle.rotation_keys(prm, s_o, 42)
+        msg = np.random.default_rng(n_leaves).integers(-2 ** 30, 2 ** 30, n_leaves * s.n)
+        d_ct = s.encrypt(msg, 43, n_leaves)
+        leaves = list(from_dev(d_ct).reshape(n_leaves, 2, L, s.n))
+        out = dev_zeros(2, L, s.n)
+        sf.sf_pack(s.ctx, s.rk, d_ct, n_leaves, n, out)
+        assert (from_dev(out) == oracle.pack(prm, keys, leaves, n=n)).all()
+    finally:
+        s.close()
+
+
+# ---------------------------------------------------------- linear layer -----
+
+def _run_layer(sess, case, delta, out_scale, weight_scale, n_capacity=64, integer_input=False):
+    lay = gpu_layer(sess, case, weight_scale, out_scale)
+    info = sf.sf_layer_get_info(sess.ctx, lay)
+    xs = stream_input(case)
+    msg = (xs * delta).astype(np.int64) if integer_input else sf.sf_encode_input(xs, delta)
+    d_in = sess.encrypt(msg, 77, info["k_in"])
+    d_out = dev_zeros(max(n_capacity, info["n_groups"]), 2, sess.L, sess.n)
+    n_out = sf.sf_eval_linear_layer(sess.ctx, lay, sess.rk, d_in, info["k_in"], case.sigma_prev, case.sigma_out,
+                                    d_out, d_out.shape[0])
+    sf.sf_sync(sess.ctx)
+    assert n_out == info["n_groups"]
+    return lay, info, msg, d_in, from_dev(d_out)[:n_out]
+
+
+def _oracle_layer_run(oracle, prm, case, msg, weight_scale, out_scale, s_seed, rk_seed, k_in):
+    s_o = oracle.keygen(prm, s_seed)
+    keys = oracle.rotation_keys(prm, s_o, rk_seed)
+    cts = oracle.encrypt(prm, s_o, msg, 77, k_in)
+    lay = oracle_layer(oracle, case, weight_scale, out_scale)
+    c = oracle.Counter()
+    out = oracle.eval_linear_layer(prm, lay, keys, cts, case.sigma_prev, case.sigma_out, c)
+    return out, s_o, c.ks
+
+
+def test_fc64_layer_bit_exact(oracle):
+    """The 64x64 FC layer at N = 2^12 (2 x 30-bit + 1 special), with input and
+    output shuffles: every residue of the packed output equals the oracle's."""
+    ps = wl.PARAMS["fc64"]
+    case = wl.fc64_case()
+    s = Session.from_set(ps, sk_seed=103, rk_seed=105)
+    try:
+        lay, info, msg, _, got = _run_layer(s, case, ps.delta, ps.delta ** 2, ps.delta)
+        assert info["ks_count"] == 69
+        prm = oracle_params(oracle, ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits)
+        assert (msg == oracle.quantize(stream_input(case), ps.delta)).all()
+        want, s_o, ks = _oracle_layer_run(oracle, prm, case, msg, ps.delta, ps.delta ** 2, 103, 105, info["k_in"])
+        assert ks == 69
+        assert (got == want).all()
+        # decrypted error against float64
+        vals = sf.sf_decode(s.params, s.decrypt(to_dev(got), 1), 1, s.n // info["group_size"], 64, ps.delta ** 2)
+        ref = wl.float_reference(case)[case.sigma_out.astype(np.int64)]
+        assert np.abs(vals - ref).max() <= 1e-3
+        sf.sf_layer_destroy(lay)
+    finally:
+        s.close()
+
+
+SCALED = {
+    # name: (log_n, L, bits, K, case factory, weight_scale, delta)
+    "conv_one_group": (10, 3, 50, 1, lambda: wl.small_conv_case(1, 8, 8, 8, 8), 2.0 ** 20, 2.0 ** 20),
+    "conv_ragged_two_groups": (10, 3, 50, 1, lambda: wl.small_conv_case(2, 10, 10, 6, 7), 2.0 ** 20, 2.0 ** 20),
+    "shortcut_bias_k_in_3": (11, 4, 50, 2, lambda: wl.small_conv_case(3, 14, 14, 8, 6, stride=2, shortcut=True,
+                                                                        bias=True), 2.0 ** 20, 2.0 ** 20),
+    "fc_bias_dnum3": (10, 5, 50, 2, lambda: wl.fc_case(4, 300, 37, bias=True), 2.0 ** 20, 2.0 ** 20),
+    "fc_30bit_no_shuffle": (10, 2, 30, 1, lambda: wl.fc_case(5, 200, 50, shuffle=False), 2.0 ** 12, 2.0 ** 12),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SCALED))
+def test_scaled_layer_bit_exact(oracle, name):
+    """Whole rounds on scaled rings: several tiles, ragged last group, k_in > 1,
+    residual shortcut term, bias, every digit layout (dnum = 1 limb, 2 limbs,
+    uneven last digit)."""
+    log_n, L, bits, K, make, wsc, delta = SCALED[name]
+    case = make()
+    s = Session(log_n, L, bits, K, sk_seed=51, rk_seed=52)
+    try:
+        lay, info, msg, _, got = _run_layer(s, case, delta, delta * wsc, wsc)
+        prm = oracle_params(oracle, log_n, L, bits, K)
+        assert (msg == oracle.quantize(stream_input(case), delta)).all()
+        want, s_o, ks = _oracle_layer_run(oracle, prm, case, msg, wsc, delta * wsc, 51, 52, info["k_in"])
+        assert ks == info["ks_count"]
+        assert (got == want).all()
+        sf.sf_layer_destroy(lay)
+    finally:
+        s.close()
+
+
+def test_ks_batch_size_does_not_change_results(oracle):
+    """Identical inputs under different launch batchings give identical
+    residues (a race between merges would show up here)."""
+    log_n, L, bits, K, make, wsc, delta = SCALED["conv_ragged_two_groups"]
+    case = make()
+    s = Session(log_n, L, bits, K, sk_seed=61, rk_seed=62)
+    try:
+        outs = []
+        for b in (1, 3, 64):
+            sf.sf_ctx_set_option(s.ctx, "ks_batch", b)
+            lay, info, msg, _, got = _run_layer(s, case, delta, delta * wsc, wsc)
+            outs.append(got)
+            sf.sf_layer_destroy(lay)
+        assert all((o == outs[0]).all() for o in outs[1:])
+    finally:
+        s.close()
+
+
+# ----------------------------------------------- full benchmark size -------
+
+def test_conv16_full_size(oracle):
+    """The benchmark layer (ResNet-20 conv 16->16 on 16x32x32, N = 2^14):
+    sampled leaves bit-exact against the oracle, decrypted outputs within
+    1e-3 of float64 on all 16384 outputs."""
+    ps = wl.PARAMS["conv16"]
+    case = wl.conv16_case()
+    s = Session.from_set(ps, sk_seed=203, rk_seed=205)
+    try:
+        lay, info, msg, d_in, got = _run_layer(s, case, ps.delta, ps.delta ** 2, ps.delta)
+        assert info["n_groups"] == 2 and info["group_size"] == 8192 and info["ks_count"] == 16384
+        res = s.decrypt(to_dev(got), 2)
+        vals = sf.sf_decode(s.params, res, 2, 2, 16384, ps.delta ** 2)
+        ref = wl.float_reference(case)[case.sigma_out.astype(np.int64)]
+        err = np.abs(vals - ref).max()
+        assert err <= 1e-3, err
+        # sampled leaves (steps 6-8) against the oracle's direct product
+        prm = oracle_params(oracle, ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits)
+        olay = oracle_layer(oracle, case, ps.delta, ps.delta ** 2)
+        cts = from_dev(d_in).reshape(1, 2, s.L, s.n)
+        sample = np.random.default_rng(9).choice(16384, 12, replace=False).astype(np.int32)
+        sample[:3] = [0, 16383, 32 * 16 + 5]          # corners and an interior output
+        d_leaf = dev_zeros(len(sample), 2, s.L, s.n)
+        sf.sf_linear_outputs(s.ctx, lay, d_in, 1, case.sigma_prev, sample, d_leaf)
+        leaves = from_dev(d_leaf)
+        for t, o in enumerate(sample):
+            assert (leaves[t] == oracle.linear_output(prm, olay, cts, int(o), case.sigma_prev)).all(), o
+        sf.sf_layer_destroy(lay)
+    finally:
+        s.close()
+
+
+def test_conv16_integer_mode_exact(oracle):
+    """Integer weights (scale 1) and integer inputs at scale 2^40: decrypting
+    and rounding reproduces the quantised cleartext result exactly."""
+    ps = wl.PARAMS["conv16"]
+    case = wl.small_conv_case(7, 32, 32, 16, 16, integer=True)
+    s = Session.from_set(ps, sk_seed=301, rk_seed=302)
+    try:
+        lay, info, msg, _, got = _run_layer(s, case, ps.delta, ps.delta, 1.0, integer_input=True)
+        res = s.decrypt(to_dev(got), info["n_groups"])
+        vals = sf.sf_decode(s.params, res, info["n_groups"], s.n // info["group_size"], case.E_out, ps.delta)
+        ref = wl.float_reference(case)[case.sigma_out.astype(np.int64)]
+        assert (np.rint(vals) == ref).all()
+        # pack-tree noise (about N * n * key-switch noise) stays far below scale / 2
+        assert np.abs(vals - ref).max() < 1e-3
+        sf.sf_layer_destroy(lay)
+    finally:
+        s.close()
+
+
+# ---------------------------------------------------------- small ops -------
+
+def test_extract_and_shuffle(oracle):
+    log_n, L = 10, 3
+    s = Session(log_n, L, 50, 1, rot=False)
+    try:
+        prm = oracle_params(oracle, log_n, L, 50, 1)
+        msg = np.random.default_rng(8).integers(-1000, 1000, 4 * s.n)
+        d_ct = s.encrypt(msg, 9, 4)
+        cts = from_dev(d_ct).reshape(4, 2, L, s.n)
+        out = dev_zeros(2, L, s.n)
+        for i in (0, 1, 517, s.n - 1):
+            sf.sf_extract(s.ctx, d_ct, i, 0, None, out)
+            got = from_dev(out)
+            for part in range(2):
+                for li, q in enumerate(prm.q):
+                    ninv = pow(s.n, -1, q)
+                    want = oracle.monomial_mul(cts[0, part, li], -i, q)
+                    want = np.array([oracle.lib().or_mulmod(int(v), ninv, q) for v in want], dtype=np.uint64)
+                    assert (got[part, li] == want).all()
+        with pytest.raises(sf.SafhireError) as e:
+            sf.sf_extract(s.ctx, d_ct, 0, 1, None, out)
+        assert e.value.status == sf.SF_ENOTSUP
+        perm = np.array([2, 0, 3, 1], dtype=np.uint32)
+        sh = dev_zeros(4, 2, L, s.n)
+        sf.sf_shuffle_cts(s.ctx, perm, d_ct, sh, 4)
+        assert (from_dev(sh) == cts[perm.astype(np.int64)]).all()
+    finally:
+        s.close()
+
+
+def test_errors_are_reported():
+    s = Session(10, 3, 50, 1, rot_d=[3, 5])
+    try:
+        d_ct = s.encrypt(np.arange(10), 1, 1)
+        out = dev_zeros(1, 2, 3, s.n)
+        with pytest.raises(sf.SafhireError) as e:
+            sf.sf_rotate(s.ctx, s.rk, 9, d_ct, out, 1)
+        assert e.value.status == sf.SF_EINVAL
+        case = wl.small_conv_case(1, 8, 8, 8, 8)
+        lay = gpu_layer(s, case, 2.0 ** 20, 2.0 ** 40)
+        with pytest.raises(sf.SafhireError) as e:      # needs keys 9, 17, ... that are missing
+            sf.sf_eval_linear_layer(s.ctx, lay, s.rk, d_ct, 1, None, None, out, 1)
+        assert e.value.status == sf.SF_EINVAL
+        with pytest.raises(sf.SafhireError) as e:      # wrong number of input ciphertexts
+            sf.sf_eval_linear_layer(s.ctx, lay, s.rk, d_ct, 2, None, None, out, 1)
+        assert e.value.status == sf.SF_EINVAL
+        bad = np.zeros(case.E_in, dtype=np.uint32)     # not a permutation
+        with pytest.raises(sf.SafhireError) as e:
+            sf.sf_eval_linear_layer(s.ctx, lay, s.rk, d_ct, 1, bad, None, out, 1)
+        assert e.value.status == sf.SF_EINVAL
+        sf.sf_layer_destroy(lay)
+        sf.sf_sync(s.ctx)
+    finally:
+        s.close()
