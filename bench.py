@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true",
+                    help="profiling case: the same conv kernel shapes on 8x16x16 (2048 outputs, ~2 GB on device)")
     return ap.parse_args()
 
 
@@ -110,13 +112,13 @@ class ClockSampler:
 class Workload:
     """Keys, weights and the encrypted input of the benchmark layer, resident on the device."""
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, small: bool = False):
         import torch
         import paper_2509_01253_gb300 as sf
         from paper_2509_01253_gb300 import workloads as wl
         self.sf, self.torch = sf, torch
         self.ps = ps = wl.PARAMS["conv16"]
-        self.case = case = wl.conv16_case()
+        self.case = case = wl.small_conv_case(201, 8, 16, 16, 16) if small else wl.conv16_case()
         self.params = sf.sf_params_create(ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits, ps.sigma)
         self.ctx = sf.sf_ctx_create(self.params, device)
         self.sk = sf.sf_keygen(self.ctx, 203)
@@ -272,7 +274,8 @@ def run_reference(args, dist, ws, rank):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "parallelism": "host cores (OpenMP)"},
+            "config": {"workload": WORKLOAD if not args.small else "conv16-small (profiling case): " + WORKLOAD.replace(
+                "16x32x32 (E = E' = 16384)", "8x16x16 (E = E' = 2048)"), "parallelism": "host cores (OpenMP)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -287,7 +290,7 @@ def main():
     import torch
     import paper_2509_01253_gb300 as sf
     torch.cuda.set_device(local)
-    wl_ = Workload(local)
+    wl_ = Workload(local, small=args.small)
     stream = wl_.stream
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
     for _ in range(max(3, args.warmup)):
@@ -303,12 +306,14 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
     for i in range(args.steps):
         flush_l2(flush)
         ev[i][0].record(stream)
         wl_.step()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     if dist:
         dist.barrier()
     clk = clocks.stop()
@@ -374,7 +379,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+            "config": {"workload": WORKLOAD if not args.small else "conv16-small (profiling case): " + WORKLOAD.replace(
+                "16x32x32 (E = E' = 16384)", "8x16x16 (E = E' = 2048)"), "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "ks_batch": None, "max_abs_err": err},
             "clocks": clk, "gpu_launches": n_launch // 1,

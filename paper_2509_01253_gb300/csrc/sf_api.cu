@@ -112,6 +112,7 @@ extern "C" sf_status sf_gen_rotation_keys(sf_ctx *ctx, const sf_secret_key *sk, 
         if (x <= 1 || x >= 2 * R.n || !(x & 1)) return sf_set_error(SF_EINVAL, "automorphism index %d invalid", x);
     sf_rotkeys *rk = new sf_rotkeys();
     rk->ctx = ctx;
+    rk->gen = sf_next_generation();
     rk->d = ds;
     rk->key_words = (size_t)R.dnum * 2 * R.nm * R.n;
     sf_status st = device_buffer((void **)&rk->d_keys, sizeof(u64) * rk->key_words * ds.size());
@@ -331,6 +332,7 @@ extern "C" sf_status sf_encode_weights(sf_ctx *ctx, const sf_conv_term *terms, i
     if ((int64_t)Ho * Wo * Co > (1 << 30)) return sf_set_error(SF_EINVAL, "output too large");
     sf_layer *L = new sf_layer();
     L->ctx = ctx;
+    L->gen = sf_next_generation();
     L->terms.assign(terms, terms + n_terms);
     L->E_in = E_in;
     L->H_out = Ho;
@@ -501,35 +503,82 @@ extern "C" sf_status sf_eval_linear_layer(sf_ctx *ctx, const sf_layer *L, const 
         h_sig.assign(h_sigma_out, h_sigma_out + L->E_out);
         SF_CUDA_TRY(cudaMemcpyAsync(d_sig, h_sig.data(), sizeof(int) * L->E_out, cudaMemcpyHostToDevice, st));
     }
-    SF_TRY(prepare_inputs(ctx, d_in, k_in, d_ct, st));
-    // steps 6-9: leaves in slot order (slot = g n + l), only the E' real ones
-    SfLeafParams P = leaf_params(L);
-    P.k_in = k_in;
-    P.pos_of = h_sigma_prev ? d_pos : nullptr;
-    P.sig_out = h_sigma_out ? d_sig : nullptr;
-    P.ct_mont = d_ct;
-    P.w1 = d_w1;
-    P.n_slots_valid = L->E_out;
-    P.leaf_stride = ct;
-    for (int s0 = 0; s0 < L->E_out; s0 += LB) {
-        int cnt = std::min(LB, L->E_out - s0);
-        SfLeafParams p = P;
-        p.s0 = s0;
-        p.leaves = A + (size_t)s0 * ct;
-        SF_TRY(sf_leaves_launch(ctx, p, cnt, st));
+    // The launch sequence below depends only on pointers and shapes, so it is
+    // captured once into a CUDA graph per (layer, keys, buffers, workspace)
+    // and replayed; with kernel timing on it is launched directly.
+    auto launch_all = [&](cudaStream_t s) -> sf_status {
+        SF_TRY(prepare_inputs(ctx, d_in, k_in, d_ct, s));
+        // steps 6-9: leaves in slot order (slot = g n + l), only the E' real ones
+        SfLeafParams P = leaf_params(L);
+        P.k_in = k_in;
+        P.pos_of = h_sigma_prev ? d_pos : nullptr;
+        P.sig_out = h_sigma_out ? d_sig : nullptr;
+        P.ct_mont = d_ct;
+        P.w1 = d_w1;
+        P.n_slots_valid = L->E_out;
+        P.leaf_stride = ct;
+        for (int s0 = 0; s0 < L->E_out; s0 += LB) {
+            int cnt = std::min(LB, L->E_out - s0);
+            SfLeafParams p = P;
+            p.s0 = s0;
+            p.leaves = A + (size_t)s0 * ct;
+            SF_TRY(sf_leaves_launch(ctx, p, cnt, s));
+        }
+        // step 10: pack every group
+        std::vector<int> valid(G);
+        for (int g = 0; g < G; ++g) valid[g] = std::min(n, L->E_out - g * n);
+        u64 *res = nullptr;
+        size_t res_stride = 0;
+        SF_TRY(sf_pack_tree(ctx, rk->d_keys, rk->d, rk->key_words, A, B, G, n, valid, d_ks, batch, &res, &res_stride,
+                            s));
+        std::vector<SfPolyJob> jobs;
+        for (int g = 0; g < G; ++g)
+            for (int x = 0; x < 2 * R.L; ++x)
+                jobs.push_back({res + res_stride * g + (size_t)x * R.n, d_out + ct * g + (size_t)x * R.n, x % R.L});
+        SF_TRY(sf_ntt_jobs(ctx, jobs.data(), (int)jobs.size(), true, s));
+        if (L->d_bq) SF_TRY(sf_add_bias(ctx, d_out, G, n, L->E_out, h_sigma_out ? d_sig : nullptr, L->d_bq, L->C_out, s));
+        return SF_OK;
+    };
+    if (!ctx->use_graph || ctx->kernel_timing) {
+        SF_TRY(launch_all(st));
+    } else {
+        uint64_t key[12] = {L->gen, rk->gen, (uint64_t)(uintptr_t)d_in, (uint64_t)(uintptr_t)d_out, (uint64_t)k_in,
+                            (uint64_t)(h_sigma_prev != nullptr), (uint64_t)(h_sigma_out != nullptr),
+                            (uint64_t)(uintptr_t)ws, (uint64_t)batch, (uint64_t)LB, 1, 0};
+        SfGraphEntry *hit = nullptr;
+        for (auto &e : ctx->graphs)
+            if (!memcmp(e.key, key, sizeof(key))) hit = &e;
+        if (!hit) {
+            std::vector<int64_t> before(SFK_COUNT);
+            for (int k = 0; k < SFK_COUNT; ++k) before[k] = ctx->stats[k].launches;
+            cudaStream_t cap;
+            SF_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            sf_status lst = ce == cudaSuccess ? launch_all(cap) : sf_set_error(SF_ECUDA, "stream capture failed");
+            cudaError_t ee = cudaStreamEndCapture(cap, &graph);
+            cudaStreamDestroy(cap);
+            if (lst != SF_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return lst;
+            }
+            if (ee != cudaSuccess || !graph) return sf_set_error(SF_ECUDA, "graph capture failed: %s", cudaGetErrorString(ee));
+            SfGraphEntry e;
+            memcpy(e.key, key, sizeof(key));
+            cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) return sf_set_error(SF_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ie));
+            e.launches.resize(SFK_COUNT);
+            for (int k = 0; k < SFK_COUNT; ++k) {
+                e.launches[k] = ctx->stats[k].launches - before[k];
+                ctx->stats[k].launches = before[k];
+            }
+            ctx->graphs.push_back(e);
+            hit = &ctx->graphs.back();
+        }
+        SF_CUDA_TRY(cudaGraphLaunch(hit->exec, st));
+        for (int k = 0; k < SFK_COUNT; ++k) ctx->stats[k].launches += hit->launches[k];
     }
-    // step 10: pack every group
-    std::vector<int> valid(G);
-    for (int g = 0; g < G; ++g) valid[g] = std::min(n, L->E_out - g * n);
-    u64 *res = nullptr;
-    size_t res_stride = 0;
-    SF_TRY(sf_pack_tree(ctx, rk->d_keys, rk->d, rk->key_words, A, B, G, n, valid, d_ks, batch, &res, &res_stride, st));
-    std::vector<SfPolyJob> jobs;
-    for (int g = 0; g < G; ++g)
-        for (int x = 0; x < 2 * R.L; ++x)
-            jobs.push_back({res + res_stride * g + (size_t)x * R.n, d_out + ct * g + (size_t)x * R.n, x % R.L});
-    SF_TRY(sf_ntt_jobs(ctx, jobs.data(), (int)jobs.size(), true, st));
-    if (L->d_bq) SF_TRY(sf_add_bias(ctx, d_out, G, n, L->E_out, h_sigma_out ? d_sig : nullptr, L->d_bq, L->C_out, st));
     if (n_out) *n_out = G;
     // the permutation host copies must outlive their async uploads
     if (!h_pos.empty() || !h_sig.empty()) SF_CUDA_TRY(cudaStreamSynchronize(st));

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "sf_internal.h"
@@ -377,9 +378,22 @@ extern "C" sf_status sf_kernel_stats_reset(sf_ctx *ctx)
     return SF_OK;
 }
 
+uint64_t sf_next_generation()
+{
+    static std::atomic<uint64_t> g{1};
+    return g.fetch_add(1);
+}
+
+void sf_graph_cache_clear(sf_ctx *ctx)
+{
+    for (auto &e : ctx->graphs) cudaGraphExecDestroy(e.exec);
+    ctx->graphs.clear();
+}
+
 sf_status sf_scratch(sf_ctx *ctx, size_t bytes, void **out)
 {
     if (bytes > ctx->scratch_bytes) {
+        sf_graph_cache_clear(ctx);
         if (ctx->scratch) {
             SF_CUDA_TRY(cudaDeviceSynchronize());
             cudaFree(ctx->scratch);
@@ -438,7 +452,7 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
     ctx->scratch_bytes = 0;
     ctx->ks_batch = p->log_n >= 15 ? 8 : 16;
     ctx->leaf_chunk = 1 << 30;
-    ctx->use_graph = 0;
+    ctx->use_graph = 1;
     ctx->kernel_timing = 0;
     for (int k = 0; k < SFK_COUNT; ++k) ctx->stats.push_back({k_names[k], 0, 0.0});
 
@@ -572,6 +586,7 @@ extern "C" void sf_ctx_destroy(sf_ctx *ctx)
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     sf_collect_timings(ctx);
+    sf_graph_cache_clear(ctx);
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     for (void *d : ctx->owned) cudaFree(d);
     if (ctx->scratch) cudaFree(ctx->scratch);
@@ -584,12 +599,17 @@ extern "C" sf_status sf_ctx_set_option(sf_ctx *ctx, const char *name, int64_t va
     if (!strcmp(name, "ks_batch")) {
         if (value < 1 || value > 4096) return sf_set_error(SF_EINVAL, "ks_batch must be in [1, 4096]");
         ctx->ks_batch = (int)value;
+        sf_graph_cache_clear(ctx);
     } else if (!strcmp(name, "leaf_chunk")) {
         if (value < 1 || (value & (value - 1))) return sf_set_error(SF_EINVAL, "leaf_chunk must be a power of two");
         ctx->leaf_chunk = (int)std::min<int64_t>(value, 1 << 30);
     } else if (!strcmp(name, "use_graph")) {
         if (value != 0 && value != 1) return sf_set_error(SF_EINVAL, "use_graph must be 0 or 1");
         ctx->use_graph = (int)value;
+    } else if (!strcmp(name, "clear_graphs")) {
+        SF_CUDA_TRY(cudaSetDevice(ctx->device));
+        SF_CUDA_TRY(cudaDeviceSynchronize());
+        sf_graph_cache_clear(ctx);
     } else if (!strcmp(name, "kernel_timing")) {
         if (value != 0 && value != 1) return sf_set_error(SF_EINVAL, "kernel_timing must be 0 or 1");
         SF_CUDA_TRY(cudaSetDevice(ctx->device));

@@ -58,6 +58,13 @@ struct PendingEvent {
     cudaEvent_t a, b;
 };
 
+// A captured launch sequence of one layer round, replayed with one launch.
+struct SfGraphEntry {
+    uint64_t key[12];
+    cudaGraphExec_t exec;
+    std::vector<int64_t> launches;   // per kernel family, for the counters
+};
+
 struct sf_ctx {
     const sf_params *prm;
     int device;
@@ -77,7 +84,11 @@ struct sf_ctx {
     std::vector<PendingEvent> pending;
     std::vector<cudaEvent_t> event_pool;
     int *d_status;
+    std::vector<SfGraphEntry> graphs;
 };
+
+void sf_graph_cache_clear(sf_ctx *ctx);
+uint64_t sf_next_generation();
 
 struct sf_secret_key {
     sf_ctx *ctx;
@@ -87,6 +98,7 @@ struct sf_secret_key {
 
 struct sf_rotkeys {
     sf_ctx *ctx;
+    uint64_t gen;             // unique per handle (graph cache key)
     std::vector<int32_t> d;   // automorphism indices
     u64 *d_keys;              // [nd][dnum][2][nm][N], NTT domain, Montgomery form
     size_t key_words;         // words per key
@@ -94,6 +106,7 @@ struct sf_rotkeys {
 
 struct sf_layer {
     sf_ctx *ctx;
+    uint64_t gen;             // unique per handle (graph cache key)
     std::vector<sf_conv_term> terms;
     int E_in, E_out, H_out, W_out, C_out;
     int max_taps;             // upper bound of taps per output
