@@ -302,6 +302,29 @@ sf_status sf_permutation(uint64_t session_seed, uint32_t round, uint32_t n, uint
 sf_status sf_shuffle_cts(sf_ctx *ctx, const uint32_t *h_perm, const uint64_t *d_in, uint64_t *d_out,
                          int32_t count, void *stream);
 
+/* Same operation as sf_rotate, for callers that cannot allocate device
+ * memory: code running under a fixed device-memory budget owned by another
+ * allocator (a framework's caching allocator, a serving process that reserves
+ * the whole GPU up front), or latency-critical paths where an allocation, or
+ * the device-wide synchronisation of freeing a grown workspace, would stall.
+ * This call allocates nothing: its scratch is a fixed 32 MiB array compiled
+ * into the library, reserved on every GPU that loads the library and held
+ * until the process exits.  The paper has no counterpart; this is an
+ * integration variant only.
+ *  - Limit: 2 * count ciphertexts plus count key-switch workspaces must fit in
+ *    32 MiB (up to 5 ciphertexts at N = 2^14 with 3 data + 1 special primes);
+ *    larger requests fail with SF_EINVAL and a message giving the sizes.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture on the device.
+ *  - Every call uses the same array: calls whose work overlaps on the GPU
+ *    (different streams, or other threads) race and corrupt each other's
+ *    results; issue them on one stream or wait in between.  Each call writes
+ *    every scratch word before reading it, so nothing needs to start at zero.
+ * Arguments, layout and results are those of sf_rotate (bit-identical). */
+sf_status sf_rotate_noalloc(sf_ctx *ctx, const sf_rotkeys *rk, int32_t d, const uint64_t *d_ct, uint64_t *d_out,
+                            int32_t count, void *stream);
+
 /* Negacyclic product per limb (via the NTT): d_out[t] = d_a[t] * d_b[t] in
  * Z_{q_i}[X]/(X^N+1), arrays uint64[n_polys][L][N].  A test hook for the
  * transform kernels. */

@@ -81,6 +81,7 @@ _SIGS = {
     "sf_eval_linear_layer_host": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _i32, ctypes.POINTER(_i32), _vp]),
     "sf_linear_outputs": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp]),
     "sf_rotate": (_i32, [_vp, _vp, _i32, _vp, _vp, _i32, _vp]),
+    "sf_rotate_noalloc": (_i32, [_vp, _vp, _i32, _vp, _vp, _i32, _vp]),
     "sf_pack": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp]),
     "sf_extract": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp]),
     "sf_permutation": (_i32, [_u64, _u32, _u32, _vp]),
@@ -326,6 +327,12 @@ def sf_linear_outputs(ctx, layer, d_in, k_in: int, sigma_prev, outputs, d_out, s
 
 def sf_rotate(ctx, rk, d: int, d_ct, d_out, count: int, stream=None):
     _check(lib().sf_rotate(ctx, rk, d, _ptr(d_ct), _ptr(d_out), count, _stream(stream)))
+
+
+def sf_rotate_noalloc(ctx, rk, d: int, d_ct, d_out, count: int, stream=None):
+    """sf_rotate without any device allocation (fixed 32 MiB scratch compiled
+    into the library; see include/safhire.h for the limits)."""
+    _check(lib().sf_rotate_noalloc(ctx, rk, d, _ptr(d_ct), _ptr(d_out), count, _stream(stream)))
 
 
 def sf_pack(ctx, rk, d_leaves, n_leaves: int, n: int, d_out, stream=None):
