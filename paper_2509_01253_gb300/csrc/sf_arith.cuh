@@ -83,11 +83,15 @@ SF_HD u64 sf_mul_mont(u64 a, u64 b_mont, u64 q, u64 qinv_neg)
     return sf_redc(sf_mulhi(a, b_mont), a * b_mont, q, qinv_neg);
 }
 
-// Forward (Cooley-Tukey) lazy butterfly: X, Y in [0, 4q) -> X', Y' in [0, 4q).
+// Forward (Cooley-Tukey) butterfly without reduction: with Y*w mod q taken
+// lazily in [0, 2q) (valid for any Y < 2^64), X' = X + T and Y' = X - T + 2q
+// grow the bound by at most 2q per stage.  Starting below 4q, a whole
+// transform of at most 16 stages stays below 36q < 2^57 for q < 2^51, so no
+// conditional subtraction is needed until a consumer wants canonical values.
 SF_HD void sf_bfly_ct(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 two_q)
 {
-    u64 x = X >= two_q ? X - two_q : X;
     u64 t = sf_mul_shoup_lazy(Y, w, wp, q);
+    u64 x = X;
     X = x + t;
     Y = x - t + two_q;
 }
@@ -106,4 +110,11 @@ SF_HD u64 sf_reduce4(u64 x, u64 q, u64 two_q)
 {
     x = x >= two_q ? x - two_q : x;
     return x >= q ? x - q : x;
+}
+
+// Reduce any x < 2^64 to [0, q): Shoup multiplication by 1 (one_p =
+// floor(2^64 / q)) lands in [0, 2q), then one conditional subtraction.
+SF_HD u64 sf_reduce(u64 x, u64 q, u64 one_p)
+{
+    return sf_csub(x - sf_mulhi(x, one_p) * q, q);
 }

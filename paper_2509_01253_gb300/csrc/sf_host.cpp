@@ -484,6 +484,7 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
         M.r_mod_p = sf_shoup_companion(M.r_mod, q);
         M.ninv = sf_host_invmod((u64)N % q, q);
         M.ninv_p = sf_shoup_companion(M.ninv, q);
+        M.one_p = sf_shoup_companion(1, q);
         u64 root = sf_root_2n(q, 2 * (u64)N);
         u64 iroot = sf_host_invmod(root, q);
         for (int k = 0; k < N; ++k) {
@@ -500,6 +501,33 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
             pw_p[(size_t)m * 2 * N + k] = sf_shoup_companion(acc, q);
             acc = sf_host_mulmod(acc, root, q);
         }
+    }
+    // Staged twiddle pairs: column table k < R (global index k), and the
+    // row table of each 16-row tile, entry [k][b] = global index
+    // m(k) (R + r) + k - m(k) with r = 16 tile + b, m(k) = 2^floor(log2 k).
+    std::vector<ulonglong2> colT_f((size_t)nm * R.r), colT_i((size_t)nm * R.r);
+    std::vector<ulonglong2> rowT_f((size_t)nm * N), rowT_i((size_t)nm * N);
+    for (int m = 0; m < nm; ++m) {
+        const u64 *tf = psi.data() + (size_t)m * N, *tfp = psi_p.data() + (size_t)m * N;
+        const u64 *ti = ipsi.data() + (size_t)m * N, *tip = ipsi_p.data() + (size_t)m * N;
+        for (int k = 0; k < R.r; ++k) {
+            colT_f[(size_t)m * R.r + k] = make_ulonglong2(tf[k], tfp[k]);
+            colT_i[(size_t)m * R.r + k] = make_ulonglong2(ti[k], tip[k]);
+        }
+        for (int tile = 0; tile < R.r / 16; ++tile)
+            for (int k = 0; k < R.c; ++k)
+                for (int b = 0; b < 16; ++b) {
+                    size_t dst = (size_t)m * N + ((size_t)tile * R.c + k) * 16 + b;
+                    if (k == 0) {
+                        rowT_f[dst] = rowT_i[dst] = make_ulonglong2(0, 0);
+                        continue;
+                    }
+                    int mk = 1;
+                    while (mk * 2 <= k) mk *= 2;
+                    size_t gi = (size_t)mk * (R.r + 16 * tile + b) + (k - mk);
+                    rowT_f[dst] = make_ulonglong2(tf[gi], tfp[gi]);
+                    rowT_i[dst] = make_ulonglong2(ti[gi], tip[gi]);
+                }
     }
     // ModUp constants
     int dnum = p->dnum;
@@ -555,6 +583,7 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
 #define UP(v, f)                                      \
     if (st == SF_OK) st = upload(ctx, v, &R.f);
     UP(psi, psi) UP(psi_p, psi_p) UP(ipsi, ipsi) UP(ipsi_p, ipsi_p) UP(pw, pw) UP(pw_p, pw_p)
+    UP(colT_f, colT_f) UP(colT_i, colT_i) UP(rowT_f, rowT_f) UP(rowT_i, rowT_i)
     UP(mu_inv, mu_inv) UP(mu_inv_p, mu_inv_p) UP(mu_qhat, mu_qhat) UP(mu_qhat_p, mu_qhat_p)
     UP(md_inv, md_inv) UP(md_inv_p, md_inv_p) UP(md_phat, md_phat) UP(md_phat_p, md_phat_p)
     UP(md_pinv, md_pinv) UP(md_pinv_p, md_pinv_p)

@@ -18,6 +18,7 @@ struct SfMod {
     u64 r_mod;         // 2^64 mod q (to Montgomery form via Shoup)
     u64 r_mod_p;
     u64 ninv, ninv_p;  // N^-1 mod q (Shoup)
+    u64 one_p;         // floor(2^64 / q): Shoup companion of 1 (full reduction)
 };
 
 // Everything a kernel needs about the ring, by value.
@@ -27,6 +28,9 @@ struct SfRing {
     SfMod m[SF_MAX_MODULI];
     // twiddle tables, [nm][N] each (index 0 unused)
     const u64 *psi, *psi_p, *ipsi, *ipsi_p;
+    // staged twiddle pairs (w, w'): column tables [nm][R] (k < R) and row
+    // tables [nm][R/16][C][16] reordered per 16-row tile (see sf_tile.cuh)
+    const ulonglong2 *colT_f, *colT_i, *rowT_f, *rowT_i;
     // powers psi^k, k in [0, 2N), [nm][2N] (monomials in the NTT domain)
     const u64 *pw, *pw_p;
     // ModUp: for digit j, limb i in the digit: N^-1 (Qhat_i mod q_i)^-1 with
@@ -188,6 +192,9 @@ struct SfPolyJob {
     int mod;
 };
 sf_status sf_ntt_jobs(sf_ctx *ctx, const SfPolyJob *h_jobs, int n_jobs, bool inverse, cudaStream_t st);
+// dynamic shared memory: staged twiddles + `tiles` data tiles (sf_tile.cuh)
+size_t sf_smem_col(const SfRing &R, int tiles);
+size_t sf_smem_row(const SfRing &R, int tiles);
 
 // Elementwise helpers (sf_ntt.cu).  Polynomial t uses modulus offset + t % period.
 sf_status sf_to_mont(sf_ctx *ctx, u64 *d, int n_polys, int period, int offset, cudaStream_t st);

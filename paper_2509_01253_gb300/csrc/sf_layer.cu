@@ -22,18 +22,21 @@ __device__ __forceinline__ int leaf_output(const SfLeafParams &P, int slot)
     return P.sig_out ? P.sig_out[slot] : slot;
 }
 
-// leaf_col: grid (C/16 column tiles, k_in * L, slots)
+// leaf_col: grid (C/16 column tiles, k_in * L, slots).  smem: column twiddles + 1 tile.
 __global__ void __launch_bounds__(SF_THREADS) k_leaf_col(SfRing R, SfLeafParams P)
 {
-    extern __shared__ u64 sm[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const SfGeo g = ring_geo(R);
-    const int c0 = blockIdx.x * SF_TC;
+    const int c0 = blockIdx.x * SF_NB;
     const int j = blockIdx.y / R.L, i = blockIdx.y % R.L;
     const int slot = P.s0 + blockIdx.z;
     const int o = leaf_output(P, slot);
     if (o < 0) return;
-    const int ne = col_tile_elems(g);
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) sm[e] = 0;
+    sf_tw *tw = (sf_tw *)smem_raw;
+    u64 *sm = (u64 *)(tw + g.r);
+    const int ne = col_elems(g);
+    load_col_tw(tw, R.colT_f, g, i);
+    for (int e = threadIdx.x; e < tile_words(g.log_r); e += blockDim.x) sm[e] = 0;
     __syncthreads();
     const SfMod &M = R.m[i];
     const int co = o % P.C_out, hw = o / P.C_out;
@@ -42,38 +45,38 @@ __global__ void __launch_bounds__(SF_THREADS) k_leaf_col(SfRing R, SfLeafParams 
         const SfTermDev &T = P.t[ti];
         const int ntap = T.kh * T.kw * T.C_in;
         for (int tt = threadIdx.x; tt < ntap; tt += blockDim.x) {
-            int dh = tt / (T.kw * T.C_in), rem = tt % (T.kw * T.C_in);
-            int dw = rem / T.C_in, ci = rem % T.C_in;
-            int h = ho * T.stride - T.pad + dh, w = wo * T.stride - T.pad + dw;
+            const int dh = tt / (T.kw * T.C_in), rem = tt % (T.kw * T.C_in);
+            const int dw = rem / T.C_in, ci = rem % T.C_in;
+            const int h = ho * T.stride - T.pad + dh, w = wo * T.stride - T.pad + dw;
             if (h < 0 || h >= T.H || w < 0 || w >= T.W) continue;
-            int idx = T.in_offset + (h * T.W + w) * T.C_in + ci;
-            int p = P.pos_of ? P.pos_of[idx] : idx;
+            const int idx = T.in_offset + (h * T.W + w) * T.C_in + ci;
+            const int p = P.pos_of ? P.pos_of[idx] : idx;
             if ((p >> R.log_n) != j) continue;
-            int k = p & (R.n - 1);
-            int cidx = k ? R.n - k : 0;
-            int col = cidx & (g.c - 1);
-            if (col < c0 || col >= c0 + SF_TC) continue;
-            int64_t wq = P.wq[T.w_off + ((size_t)(co * T.kh + dh) * T.kw + dw) * T.C_in + ci];
-            int64_t r = wq % (int64_t)M.q;
+            const int k = p & (R.n - 1);
+            const int cidx = k ? R.n - k : 0;
+            const int col = cidx & (g.c - 1);
+            if (col < c0 || col >= c0 + SF_NB) continue;
+            const int64_t wq = P.wq[T.w_off + ((size_t)(co * T.kh + dh) * T.kw + dw) * T.C_in + ci];
+            const int64_t r = wq % (int64_t)M.q;
             u64 v = (u64)(r < 0 ? r + (int64_t)M.q : r);
             v = sf_mul_shoup(v, M.ninv, M.ninv_p, M.q);
             if (k && v) v = M.q - v;   // X^-k = -X^(N-k)
-            sm[(cidx >> g.log_c) * SF_TC + (col - c0)] = v;
+            sm[(cidx >> g.log_c) * SF_PAD + (col - c0)] = v;
         }
     }
     __syncthreads();
-    tile_forward(sm, col_tile_desc(g), R.psi + ((size_t)i << R.log_n), R.psi_p + ((size_t)i << R.log_n), M.q);
+    col_forward(sm, tw, g.log_r, M.q);
     u64 *dst = P.w1 + (((size_t)blockIdx.z * P.k_in + j) * R.L + i) * R.n;
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) dst[col_tile_gidx(g, c0, e)] = sm[e];
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) dst[col_gidx(g, c0, e)] = sm[col_slot(e)];
 }
 
-// leaf_row: grid (R/16 row tiles, L, slots)
+// leaf_row: grid (R/16 row tiles, L, slots).  smem: forward row twiddles + 1 tile.
 template <int EPT>
-__global__ void __launch_bounds__(SF_THREADS) k_leaf_row(SfRing R, SfLeafParams P)
+__global__ void __launch_bounds__(SF_THREADS, EPT >= 16 ? 1 : 3) k_leaf_row(SfRing R, SfLeafParams P)
 {
-    extern __shared__ u64 sm[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const SfGeo g = ring_geo(R);
-    const int r0 = blockIdx.x * SF_TR, i = blockIdx.y;
+    const int r0 = blockIdx.x * SF_NB, i = blockIdx.y;
     const int slot = P.s0 + blockIdx.z;
     const int o = leaf_output(P, slot);
     const size_t tile_off = (size_t)r0 * g.c;
@@ -83,38 +86,43 @@ __global__ void __launch_bounds__(SF_THREADS) k_leaf_row(SfRing R, SfLeafParams 
     if (o < 0) {
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
-            int e = threadIdx.x + k * SF_THREADS;
+            const int e = threadIdx.x + k * SF_THREADS;
             da[e] = 0;
             db[e] = 0;
         }
         return;
     }
+    sf_tw *tw = (sf_tw *)smem_raw;
+    u64 *sm = (u64 *)(tw + SF_NB * g.c);
     const SfMod M = R.m[i];
-    const TileDesc td = row_tile_desc(g, r0);
-    sf_u128 acc_a[EPT], acc_b[EPT];
+    load_row_tw(tw, R.rowT_f, g, i, r0);
+    // per input ciphertext w * ct (w < 36q lazy, ct < q, Montgomery form) is
+    // reduced into [0, 2q) and summed: below 2 q k_in < 2^56 for k_in < 32
+    u64 acc_a[EPT], acc_b[EPT];
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) acc_a[k] = acc_b[k] = {0, 0};
+    for (int k = 0; k < EPT; ++k) acc_a[k] = acc_b[k] = 0;
     for (int j = 0; j < P.k_in; ++j) {
         const u64 *src = P.w1 + (((size_t)blockIdx.z * P.k_in + j) * R.L + i) * R.n + tile_off;
-        for (int e = threadIdx.x; e < SF_TR * g.c; e += blockDim.x) sm[e] = src[e];
+        for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) sm[row_slot(g, e)] = src[e];
         __syncthreads();
-        tile_forward(sm, td, R.psi + ((size_t)i << R.log_n), R.psi_p + ((size_t)i << R.log_n), M.q);
+        row_forward(sm, tw, g.log_c, M.q);
         const u64 *ca = P.ct_mont + (((size_t)j * 2 + 0) * R.L + i) * R.n + tile_off;
         const u64 *cb = P.ct_mont + (((size_t)j * 2 + 1) * R.L + i) * R.n + tile_off;
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
-            int e = threadIdx.x + k * SF_THREADS;
-            u64 w = sm[e];
-            sf_mac128(acc_a[k], w, __ldg(ca + e));
-            sf_mac128(acc_b[k], w, __ldg(cb + e));
+            const int e = threadIdx.x + k * SF_THREADS;
+            const u64 w = sm[row_slot(g, e)];
+            const u64 xa = __ldg(ca + e), xb = __ldg(cb + e);
+            acc_a[k] += sf_redc_lazy(sf_mulhi(w, xa), w * xa, M.q, M.qinv_neg);
+            acc_b[k] += sf_redc_lazy(sf_mulhi(w, xb), w * xb, M.q, M.qinv_neg);
         }
         __syncthreads();
     }
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
-        int e = threadIdx.x + k * SF_THREADS;
-        da[e] = sf_redc(acc_a[k].hi, acc_a[k].lo, M.q, M.qinv_neg);
-        db[e] = sf_redc(acc_b[k].hi, acc_b[k].lo, M.q, M.qinv_neg);
+        const int e = threadIdx.x + k * SF_THREADS;
+        da[e] = sf_reduce(acc_a[k], M.q, M.one_p);
+        db[e] = sf_reduce(acc_b[k], M.q, M.one_p);
     }
 }
 
@@ -122,24 +130,24 @@ sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStre
 {
     const SfRing &R = ctx->ring;
     if (cnt <= 0) return SF_OK;
-    const size_t col_tile = sizeof(u64) * R.r * SF_TC, row_tile = sizeof(u64) * R.c * SF_TR;
+    const size_t smem_c = sf_smem_col(R, 1), smem_r = sf_smem_row(R, 1);
     cudaEvent_t ev;
     for (int off = 0; off < cnt; off += 65535) {
         SfLeafParams p = P;
-        int c = std::min(65535, cnt - off);
+        const int c = std::min(65535, cnt - off);
         p.s0 = P.s0 + off;
         p.w1 = P.w1;    // w1 holds `cnt` slots; reuse from its start for each sub-launch
         p.leaves = P.leaves + P.leaf_stride * off;
         sf_launch_begin(ctx, SFK_LEAF_COL, st, &ev);
-        k_leaf_col<<<dim3(R.c / SF_TC, P.k_in * R.L, c), SF_THREADS, col_tile, st>>>(R, p);
+        k_leaf_col<<<dim3(R.c / SF_NB, P.k_in * R.L, c), SF_THREADS, smem_c, st>>>(R, p);
         sf_launch_end(ctx, SFK_LEAF_COL, st, ev);
         sf_launch_begin(ctx, SFK_LEAF_ROW, st, &ev);
-        dim3 gr(R.r / SF_TR, R.L, c);
-        switch ((R.c * SF_TR) / SF_THREADS) {
-        case 2: k_leaf_row<2><<<gr, SF_THREADS, row_tile, st>>>(R, p); break;
-        case 4: k_leaf_row<4><<<gr, SF_THREADS, row_tile, st>>>(R, p); break;
-        case 8: k_leaf_row<8><<<gr, SF_THREADS, row_tile, st>>>(R, p); break;
-        case 16: k_leaf_row<16><<<gr, SF_THREADS, row_tile, st>>>(R, p); break;
+        const dim3 gr(R.r / SF_NB, R.L, c);
+        switch ((R.c * SF_NB) / SF_THREADS) {
+        case 2: k_leaf_row<2><<<gr, SF_THREADS, smem_r, st>>>(R, p); break;
+        case 4: k_leaf_row<4><<<gr, SF_THREADS, smem_r, st>>>(R, p); break;
+        case 8: k_leaf_row<8><<<gr, SF_THREADS, smem_r, st>>>(R, p); break;
+        case 16: k_leaf_row<16><<<gr, SF_THREADS, smem_r, st>>>(R, p); break;
         default: return sf_set_error(SF_EINVAL, "unsupported ring split");
         }
         sf_launch_end(ctx, SFK_LEAF_ROW, st, ev);

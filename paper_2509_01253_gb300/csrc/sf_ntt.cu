@@ -11,49 +11,52 @@
 template <bool INV, bool COLS>
 __global__ void __launch_bounds__(SF_THREADS) k_ntt_pass(SfRing R, SfJobList jobs)
 {
-    extern __shared__ u64 sm[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const SfPolyJob jb = jobs.j[blockIdx.y];
     const SfGeo g = ring_geo(R);
-    const u64 q = R.m[jb.mod].q;
+    const SfMod M = R.m[jb.mod];
     const bool first = (INV != COLS);   // forward starts with columns, inverse with rows
     const u64 *src = first ? jb.src : jb.dst;
-    const u64 *tw = (INV ? R.ipsi : R.psi) + (size_t)jb.mod * g.n;
-    const u64 *twp = (INV ? R.ipsi_p : R.psi_p) + (size_t)jb.mod * g.n;
+    sf_tw *tw = (sf_tw *)smem_raw;
     if (COLS) {
-        int c0 = blockIdx.x * SF_TC;
-        int ne = col_tile_elems(g);
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) sm[e] = src[col_tile_gidx(g, c0, e)];
+        u64 *s = (u64 *)(tw + g.r);
+        const int c0 = blockIdx.x * SF_NB;
+        load_col_tw(tw, INV ? R.colT_i : R.colT_f, g, jb.mod);
+        for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) s[col_slot(e)] = src[col_gidx(g, c0, e)];
         __syncthreads();
-        TileDesc t = col_tile_desc(g);
-        if (INV) tile_inverse(sm, t, tw, twp, q);
-        else tile_forward(sm, t, tw, twp, q);
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-            u64 v = sm[e];
-            if (INV) v = sf_csub(sf_mul_shoup_lazy(v, R.m[jb.mod].ninv, R.m[jb.mod].ninv_p, q), q);
-            jb.dst[col_tile_gidx(g, c0, e)] = v;
+        if (INV) col_inverse(s, tw, g.log_r, M.q);
+        else col_forward(s, tw, g.log_r, M.q);
+        for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) {
+            u64 v = s[col_slot(e)];
+            if (INV) v = sf_csub(sf_mul_shoup_lazy(v, M.ninv, M.ninv_p, M.q), M.q);
+            jb.dst[col_gidx(g, c0, e)] = v;
         }
     } else {
-        int r0 = blockIdx.x * SF_TR;
-        int ne = row_tile_elems(g);
+        u64 *s = (u64 *)(tw + SF_NB * g.c);
+        const int r0 = blockIdx.x * SF_NB;
+        load_row_tw(tw, INV ? R.rowT_i : R.rowT_f, g, jb.mod, r0);
         const u64 *s0 = src + (size_t)r0 * g.c;
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) sm[e] = s0[e];
+        for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) s[row_slot(g, e)] = s0[e];
         __syncthreads();
-        TileDesc t = row_tile_desc(g, r0);
-        if (INV) tile_inverse(sm, t, tw, twp, q);
-        else tile_forward(sm, t, tw, twp, q);
+        if (INV) row_inverse(s, tw, g.log_c, M.q);
+        else row_forward(s, tw, g.log_c, M.q);
         u64 *d0 = jb.dst + (size_t)r0 * g.c;
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-            u64 v = sm[e];
-            if (!INV) v = sf_reduce4(v, q, 2 * q);
+        for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) {
+            u64 v = s[row_slot(g, e)];
+            if (!INV) v = sf_reduce(v, M.q, M.one_p);
             d0[e] = v;
         }
     }
 }
 
+// dynamic shared memory of the pass kernels
+size_t sf_smem_col(const SfRing &R, int tiles) { return sizeof(sf_tw) * R.r + sizeof(u64) * tile_words(R.log_r) * tiles; }
+size_t sf_smem_row(const SfRing &R, int tiles) { return sizeof(sf_tw) * SF_NB * R.c + sizeof(u64) * tile_words(R.log_c) * tiles; }
+
 sf_status sf_ntt_jobs(sf_ctx *ctx, const SfPolyJob *h_jobs, int n_jobs, bool inverse, cudaStream_t st)
 {
     const SfRing &R = ctx->ring;
-    size_t smem_col = sizeof(u64) * R.r * SF_TC, smem_row = sizeof(u64) * R.c * SF_TR;
+    const size_t smem_col = sf_smem_col(R, 1), smem_row = sf_smem_row(R, 1);
     for (int off = 0; off < n_jobs; off += SF_MAX_JOBS) {
         int cnt = std::min(SF_MAX_JOBS, n_jobs - off);
         SfJobList jl;

@@ -8,181 +8,186 @@
 // Index j = r*C + c with N = R*C.  The forward stages with butterfly
 // distance >= C only mix elements of one column ("column pass"); the stages
 // with distance < C stay inside one row ("row pass").  Forward = column pass
-// then row pass; inverse = row pass then column pass.  A column tile is
-// R rows x SF_TC columns, a row tile SF_TR rows x C columns, both staged in
-// shared memory; each sweep fuses two stages (radix 4) per shared-memory
-// round trip.
+// then row pass; inverse = row pass then column pass.
 //
-// Within a tile, sub-transform b (a column or a row) of size S has element k
-// at s[b*bs + k*es].  The global twiddle index of local stage with m groups,
-// group g, is m*base(b) + g with base = 1 for every column and base = R + r
-// for row r (r the global row).
+// A tile holds SF_NB = 16 sub-transforms (16 columns of R elements, or 16
+// rows of C elements) in shared memory as [k][b]: element k of sub-transform
+// b sits at k*SF_PAD + b with SF_PAD = 17.  With that stride the coalesced
+// global loads of both tile kinds and every butterfly sweep (consecutive
+// threads on consecutive b) are free of bank conflicts.
+//
+// Twiddles are staged in shared memory as (w, w') pairs, w' = floor(w 2^64/q)
+// (Shoup).  Local stage with m groups, group g, uses local index k = m + g:
+//  * column pass: the global index is m + g for every column, so the tile
+//    reads colT[k] (k < R), one table shared by all 16 columns;
+//  * row pass: the global index is m*(R + r) + g for row r, so the host
+//    stores, per 16-row tile, rowT[tile][k][b] = psi_brev[m(k)(R + 16 tile + b)
+//    + k - m(k)] (m(k) the largest power of two <= k); the tile's 16*C pairs
+//    are one contiguous chunk copied straight into shared memory.
+// Each sweep runs 2 or 3 stages (radix 4 / radix 8) on register-resident
+// units with lazy Harvey butterflies.
 #pragma once
 #include "sf_arith.cuh"
 
-#define SF_TC 16
-#define SF_TR 16
+#define SF_NB 16
+#define SF_PAD 17
+#define SF_TC SF_NB
+#define SF_TR SF_NB
 #define SF_THREADS 256
 
 struct SfGeo {
     int log_n, n, log_r, r, log_c, c;
 };
 
-struct TileDesc {
-    int nb;      // sub-transforms in the tile
-    int bs, es;  // strides (elements) between sub-transforms / elements
-    int log_s;   // log2 sub-transform size
-    int base0, bstep;
-    bool b_fast; // thread mapping: consecutive threads on consecutive sub-transforms
-};
+typedef ulonglong2 sf_tw;   // (w, w')
 
-__device__ __forceinline__ TileDesc col_tile_desc(const SfGeo &g)
+// elements of a tile buffer in shared memory (S rows of SF_PAD words)
+__host__ __device__ __forceinline__ int tile_words(int log_s) { return (1 << log_s) * SF_PAD; }
+
+// One sweep of R_ST consecutive stages over every unit of the tile.
+// Forward: halves H0, H0/2, ..., H0 >> (R_ST-1).  Inverse: halves H0, ..., H0 << (R_ST-1).
+template <int LOG_S, int LOG_H0, int R_ST, bool INV, bool ROWTW>
+__device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
 {
-    TileDesc t;
-    t.nb = SF_TC; t.bs = 1; t.es = SF_TC; t.log_s = g.log_r; t.base0 = 1; t.bstep = 0; t.b_fast = true;
-    return t;
+    constexpr int S = 1 << LOG_S;
+    constexpr int U = 1 << R_ST;
+    constexpr int UNITS = SF_NB * S / U;
+    constexpr int ITER = (UNITS + SF_THREADS - 1) / SF_THREADS;
+    constexpr int LOG_STEP = INV ? LOG_H0 : (LOG_H0 - (R_ST - 1));
+    constexpr int LOG_BLK = INV ? (LOG_H0 + R_ST) : (LOG_H0 + 1);
+    const u64 two_q = 2 * q;
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+        const int idx = threadIdx.x + it * SF_THREADS;
+        if ((UNITS % SF_THREADS) != 0 && idx >= UNITS) break;
+        const int b = idx & (SF_NB - 1);
+        const int u = idx >> 4;
+        const int o = u & ((1 << LOG_STEP) - 1);
+        const int blk = u >> LOG_STEP;
+        const int first = (blk << LOG_BLK) + o;
+        u64 x[U];
+#pragma unroll
+        for (int t = 0; t < U; ++t) x[t] = s[(first + (t << LOG_STEP)) * SF_PAD + b];
+#pragma unroll
+        for (int sg = 0; sg < R_ST; ++sg) {
+            const int d = INV ? (1 << sg) : (1 << (R_ST - 1 - sg));
+            const int m = INV ? (S >> (LOG_H0 + 1 + sg)) : ((S >> (LOG_H0 + 1)) << sg);
+#pragma unroll
+            for (int t = 0; t < U; ++t) {
+                if (t & d) continue;
+                const int g = INV ? ((blk << (R_ST - sg - 1)) + (t >> (sg + 1))) : ((blk << sg) + (t >> (R_ST - sg)));
+                const sf_tw w = ROWTW ? tw[(m + g) * SF_NB + b] : tw[m + g];
+                if (INV) sf_bfly_gs(x[t], x[t + d], w.x, w.y, q, two_q);
+                else sf_bfly_ct(x[t], x[t + d], w.x, w.y, q, two_q);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < U; ++t) s[(first + (t << LOG_STEP)) * SF_PAD + b] = x[t];
+    }
+    __syncthreads();
 }
 
-__device__ __forceinline__ TileDesc row_tile_desc(const SfGeo &g, int r0)
+// Forward stages of all 16 sub-transforms of size 2^LOG_S; values in [0, 4q).
+template <int LOG_S, bool ROWTW>
+__device__ __forceinline__ void tile_forward_t(u64 *s, const sf_tw *tw, u64 q)
 {
-    TileDesc t;
-    t.nb = SF_TR; t.bs = g.c; t.es = 1; t.log_s = g.log_c; t.base0 = g.r + r0; t.bstep = 1; t.b_fast = false;
-    return t;
-}
-
-// decompose a unit index into (sub-transform b, unit-in-transform u)
-__device__ __forceinline__ void unit_split(const TileDesc &t, int idx, int log_units, int &b, int &u)
-{
-    if (t.b_fast) {
-        b = idx % t.nb;          // nb is a power of two
-        u = idx / t.nb;
+    if constexpr (LOG_S == 5) {
+        tile_sweep<5, 4, 3, false, ROWTW>(s, tw, q);
+        tile_sweep<5, 1, 2, false, ROWTW>(s, tw, q);
+    } else if constexpr (LOG_S == 6) {
+        tile_sweep<6, 5, 3, false, ROWTW>(s, tw, q);
+        tile_sweep<6, 2, 3, false, ROWTW>(s, tw, q);
+    } else if constexpr (LOG_S == 7) {
+        tile_sweep<7, 6, 3, false, ROWTW>(s, tw, q);
+        tile_sweep<7, 3, 2, false, ROWTW>(s, tw, q);
+        tile_sweep<7, 1, 2, false, ROWTW>(s, tw, q);
     } else {
-        u = idx & ((1 << log_units) - 1);
-        b = idx >> log_units;
+        tile_sweep<8, 7, 3, false, ROWTW>(s, tw, q);
+        tile_sweep<8, 4, 3, false, ROWTW>(s, tw, q);
+        tile_sweep<8, 1, 2, false, ROWTW>(s, tw, q);
     }
 }
 
-// Forward (CT) stages of every sub-transform in the tile.  Values in [0, 4q).
-static __device__ __forceinline__ void tile_forward(u64 *s, const TileDesc &t, const u64 *__restrict__ tw,
-                             const u64 *__restrict__ twp, u64 q)
+// Inverse stages (no N^-1 factor); values in [0, 2q).
+template <int LOG_S, bool ROWTW>
+__device__ __forceinline__ void tile_inverse_t(u64 *s, const sf_tw *tw, u64 q)
 {
-    const u64 two_q = 2 * q;
-    int log_s = t.log_s;
-    int S = 1 << log_s;
-    int h = S >> 1;  // current butterfly half-distance (local)
-    if (log_s & 1) {
-        // one radix-2 stage first (half S/2, a single group)
-        int units = S >> 1;
-        for (int idx = threadIdx.x; idx < t.nb * units; idx += blockDim.x) {
-            int b, u;
-            unit_split(t, idx, log_s - 1, b, u);
-            int base = t.base0 + b * t.bstep;
-            u64 *p = s + b * t.bs;
-            int i1 = base;  // m = 1, g = 0
-            u64 w = __ldg(tw + i1), wp = __ldg(twp + i1);
-            u64 x = p[u * t.es], y = p[(u + h) * t.es];
-            sf_bfly_ct(x, y, w, wp, q, two_q);
-            p[u * t.es] = x;
-            p[(u + h) * t.es] = y;
-        }
-        __syncthreads();
-        h >>= 1;
-    }
-    for (; h >= 2; h >>= 2) {
-        // radix-4: stages with half h and h/2; m = S / (2h) groups in the first
-        int m = S / (2 * h);
-        int hh = h >> 1;
-        int log_hh = __ffs(hh) - 1;
-        int units = S >> 2;
-        for (int idx = threadIdx.x; idx < t.nb * units; idx += blockDim.x) {
-            int b, u;
-            unit_split(t, idx, log_s - 2, b, u);
-            int g = u >> log_hh, o = u & (hh - 1);
-            int k0 = 2 * h * g + o;
-            int base = t.base0 + b * t.bstep;
-            u64 *p = s + b * t.bs;
-            u64 x0 = p[k0 * t.es], x1 = p[(k0 + hh) * t.es];
-            u64 x2 = p[(k0 + h) * t.es], x3 = p[(k0 + h + hh) * t.es];
-            int i1 = m * base + g;
-            u64 w1 = __ldg(tw + i1), w1p = __ldg(twp + i1);
-            sf_bfly_ct(x0, x2, w1, w1p, q, two_q);
-            sf_bfly_ct(x1, x3, w1, w1p, q, two_q);
-            int i2 = 2 * m * base + 2 * g;
-            u64 wa = __ldg(tw + i2), wap = __ldg(twp + i2);
-            u64 wb = __ldg(tw + i2 + 1), wbp = __ldg(twp + i2 + 1);
-            sf_bfly_ct(x0, x1, wa, wap, q, two_q);
-            sf_bfly_ct(x2, x3, wb, wbp, q, two_q);
-            p[k0 * t.es] = x0;
-            p[(k0 + hh) * t.es] = x1;
-            p[(k0 + h) * t.es] = x2;
-            p[(k0 + h + hh) * t.es] = x3;
-        }
-        __syncthreads();
+    if constexpr (LOG_S == 5) {
+        tile_sweep<5, 0, 2, true, ROWTW>(s, tw, q);
+        tile_sweep<5, 2, 3, true, ROWTW>(s, tw, q);
+    } else if constexpr (LOG_S == 6) {
+        tile_sweep<6, 0, 3, true, ROWTW>(s, tw, q);
+        tile_sweep<6, 3, 3, true, ROWTW>(s, tw, q);
+    } else if constexpr (LOG_S == 7) {
+        tile_sweep<7, 0, 2, true, ROWTW>(s, tw, q);
+        tile_sweep<7, 2, 2, true, ROWTW>(s, tw, q);
+        tile_sweep<7, 4, 3, true, ROWTW>(s, tw, q);
+    } else {
+        tile_sweep<8, 0, 2, true, ROWTW>(s, tw, q);
+        tile_sweep<8, 2, 3, true, ROWTW>(s, tw, q);
+        tile_sweep<8, 5, 3, true, ROWTW>(s, tw, q);
     }
 }
 
-// Inverse (GS) stages of every sub-transform in the tile.  Values in [0, 2q).
-static __device__ __forceinline__ void tile_inverse(u64 *s, const TileDesc &t, const u64 *__restrict__ tw,
-                             const u64 *__restrict__ twp, u64 q)
+// Runtime dispatch on the sub-transform size (R for columns, C for rows).
+__device__ __forceinline__ void col_forward(u64 *s, const sf_tw *tw, int log_r, u64 q)
 {
-    const u64 two_q = 2 * q;
-    int log_s = t.log_s;
-    int S = 1 << log_s;
-    int h = 1;
-    for (; 4 * h <= S; h <<= 2) {
-        // radix-4: halves h then 2h; m = S / (2h) groups in the first
-        int m = S / (2 * h);
-        int log_h = __ffs(h) - 1;
-        int units = S >> 2;
-        for (int idx = threadIdx.x; idx < t.nb * units; idx += blockDim.x) {
-            int b, u;
-            unit_split(t, idx, log_s - 2, b, u);
-            int g = u >> log_h, o = u & (h - 1);
-            int k0 = 4 * h * g + o;
-            int base = t.base0 + b * t.bstep;
-            u64 *p = s + b * t.bs;
-            u64 x0 = p[k0 * t.es], x1 = p[(k0 + h) * t.es];
-            u64 x2 = p[(k0 + 2 * h) * t.es], x3 = p[(k0 + 3 * h) * t.es];
-            int i1 = m * base + 2 * g;
-            u64 wa = __ldg(tw + i1), wap = __ldg(twp + i1);
-            u64 wb = __ldg(tw + i1 + 1), wbp = __ldg(twp + i1 + 1);
-            sf_bfly_gs(x0, x1, wa, wap, q, two_q);
-            sf_bfly_gs(x2, x3, wb, wbp, q, two_q);
-            int i2 = (m >> 1) * base + g;
-            u64 w2 = __ldg(tw + i2), w2p = __ldg(twp + i2);
-            sf_bfly_gs(x0, x2, w2, w2p, q, two_q);
-            sf_bfly_gs(x1, x3, w2, w2p, q, two_q);
-            p[k0 * t.es] = x0;
-            p[(k0 + h) * t.es] = x1;
-            p[(k0 + 2 * h) * t.es] = x2;
-            p[(k0 + 3 * h) * t.es] = x3;
-        }
-        __syncthreads();
+    switch (log_r) {
+    case 5: tile_forward_t<5, false>(s, tw, q); break;
+    case 6: tile_forward_t<6, false>(s, tw, q); break;
+    case 7: tile_forward_t<7, false>(s, tw, q); break;
+    default: tile_forward_t<8, false>(s, tw, q); break;
     }
-    if (h < S) {
-        // one radix-2 stage last (half S/2, a single group)
-        int units = S >> 1;
-        for (int idx = threadIdx.x; idx < t.nb * units; idx += blockDim.x) {
-            int b, u;
-            unit_split(t, idx, log_s - 1, b, u);
-            int base = t.base0 + b * t.bstep;
-            u64 *p = s + b * t.bs;
-            u64 w = __ldg(tw + base), wp = __ldg(twp + base);
-            u64 x = p[u * t.es], y = p[(u + h) * t.es];
-            sf_bfly_gs(x, y, w, wp, q, two_q);
-            p[u * t.es] = x;
-            p[(u + h) * t.es] = y;
-        }
-        __syncthreads();
+}
+__device__ __forceinline__ void col_inverse(u64 *s, const sf_tw *tw, int log_r, u64 q)
+{
+    switch (log_r) {
+    case 5: tile_inverse_t<5, false>(s, tw, q); break;
+    case 6: tile_inverse_t<6, false>(s, tw, q); break;
+    case 7: tile_inverse_t<7, false>(s, tw, q); break;
+    default: tile_inverse_t<8, false>(s, tw, q); break;
+    }
+}
+__device__ __forceinline__ void row_forward(u64 *s, const sf_tw *tw, int log_c, u64 q)
+{
+    switch (log_c) {
+    case 5: tile_forward_t<5, true>(s, tw, q); break;
+    case 6: tile_forward_t<6, true>(s, tw, q); break;
+    case 7: tile_forward_t<7, true>(s, tw, q); break;
+    default: tile_forward_t<8, true>(s, tw, q); break;
+    }
+}
+__device__ __forceinline__ void row_inverse(u64 *s, const sf_tw *tw, int log_c, u64 q)
+{
+    switch (log_c) {
+    case 5: tile_inverse_t<5, true>(s, tw, q); break;
+    case 6: tile_inverse_t<6, true>(s, tw, q); break;
+    case 7: tile_inverse_t<7, true>(s, tw, q); break;
+    default: tile_inverse_t<8, true>(s, tw, q); break;
     }
 }
 
-// Column tile c0..c0+SF_TC-1 of a polynomial stored as N contiguous words:
-// tile element (r, cc) sits at smem[r*SF_TC + cc].
-__device__ __forceinline__ int col_tile_elems(const SfGeo &g) { return g.r * SF_TC; }
-__device__ __forceinline__ int col_tile_gidx(const SfGeo &g, int c0, int e)
+// ---- tile <-> global ------------------------------------------------------
+// Thread-iteration index e enumerates a tile in global (coalesced) order;
+// these map it to the global offset and to the shared-memory slot.
+
+// column tile c0..c0+15: global r*C + c0 + b, e = r*16 + b
+__device__ __forceinline__ int col_elems(const SfGeo &g) { return g.r * SF_NB; }
+__device__ __forceinline__ int col_gidx(const SfGeo &g, int c0, int e) { return (e >> 4) * g.c + c0 + (e & 15); }
+__device__ __forceinline__ int col_slot(int e) { return (e >> 4) * SF_PAD + (e & 15); }
+// row tile r0..r0+15: global (r0 + b)*C + k, e = b*C + k
+__device__ __forceinline__ int row_elems(const SfGeo &g) { return SF_NB * g.c; }
+__device__ __forceinline__ int row_slot(const SfGeo &g, int e) { return (e & (g.c - 1)) * SF_PAD + (e >> g.log_c); }
+
+// Stage twiddles: column table (R pairs) or the row table of tile r0/16
+// (16*C pairs), for modulus `mod`; tables are [nm][...] in global memory.
+__device__ __forceinline__ void load_col_tw(sf_tw *dst, const sf_tw *__restrict__ table, const SfGeo &g, int mod)
 {
-    return (e / SF_TC) * g.c + c0 + (e % SF_TC);
+    const sf_tw *src = table + (size_t)mod * g.r;
+    for (int k = threadIdx.x; k < g.r; k += blockDim.x) dst[k] = src[k];
 }
-// Row tile r0..r0+SF_TR-1: tile element e sits at global r0*C + e.
-__device__ __forceinline__ int row_tile_elems(const SfGeo &g) { return SF_TR * g.c; }
+__device__ __forceinline__ void load_row_tw(sf_tw *dst, const sf_tw *__restrict__ table, const SfGeo &g, int mod, int r0)
+{
+    const sf_tw *src = table + ((size_t)mod << g.log_n) + (size_t)r0 * g.c;
+    for (int k = threadIdx.x; k < SF_NB * g.c; k += blockDim.x) dst[k] = src[k];
+}
