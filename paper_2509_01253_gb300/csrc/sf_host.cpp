@@ -448,9 +448,11 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
     sf_ctx *ctx = new sf_ctx();
     ctx->prm = p;
     ctx->device = device;
+    ctx->num_sms = 1;
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     ctx->scratch = nullptr;
     ctx->scratch_bytes = 0;
-    ctx->ks_batch = p->log_n >= 15 ? 8 : 16;
+    ctx->ks_batch = p->log_n >= 15 ? 64 : 128;
     ctx->leaf_chunk = 1 << 30;
     ctx->use_graph = 1;
     ctx->kernel_timing = 0;

@@ -72,6 +72,7 @@ struct SfGraphEntry {
 struct sf_ctx {
     const sf_params *prm;
     int device;
+    int num_sms;
     SfRing ring;
     // owned device allocations for the tables
     std::vector<void *> owned;

@@ -19,6 +19,7 @@
 //   K4 cols : inverse column pass of the P-limbs, times N^-1 -> coefficients;
 //             base conversion P -> each q_i; forward column pass
 //   K5 rows : forward row pass; (acc_Q - conv) * P^-1; add v and tau_d(u.b); store
+#include "sf_async.cuh"
 #include "sf_internal.h"
 #include "sf_kernels.cuh"
 #include "sf_ks.h"
@@ -28,6 +29,13 @@ size_t sf_ks_scratch_words(const SfRing &R)
 {
     int x1 = R.L > 2 * R.K ? R.L : 2 * R.K;
     int x2 = R.dnum * R.nm > 2 * R.L ? R.dnum * R.nm : 2 * R.L;
+    return (size_t)(R.L + x1 + x2 + 2 * R.L) << R.log_n;
+}
+
+__device__ __forceinline__ size_t sf_ks_scratch_words_dev(const SfRing &R)
+{
+    const int x1 = R.L > 2 * R.K ? R.L : 2 * R.K;
+    const int x2 = R.dnum * R.nm > 2 * R.L ? R.dnum * R.nm : 2 * R.L;
     return (size_t)(R.L + x1 + x2 + 2 * R.L) << R.log_n;
 }
 
@@ -102,261 +110,440 @@ __device__ __forceinline__ u64 merge_v(const SfRing &R, const SfKsBatch &B, cons
     return sf_add(e, xo, M.q);
 }
 
-// K1: grid (R/16 row tiles, L limbs, merges).  smem: inverse row twiddles + 1 tile.
-__global__ void __launch_bounds__(SF_THREADS) k_ks1(SfRing R, SfKsBatch B)
+// ---------------------------------------------------------------------------
+// Persistent transform kernels.  A block owns one group (a tile position and a
+// modulus or digit), stages that group's twiddles once, and loops over the
+// merges of the launch batch (items it = sub, sub + bpg, ...), prefetching the
+// next item's tiles with cp.async while it transforms the current one.
+// gridDim.x = n_groups * bpg.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void issue_row_tile(u64 *dst, const u64 *src, const SfGeo &g)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SfGeo g = ring_geo(R);
-    const int r0 = blockIdx.x * SF_NB, i = blockIdx.y, b = blockIdx.z;
-    sf_tw *tw = (sf_tw *)smem_raw;
-    u64 *s = (u64 *)(tw + SF_NB * g.c);
-    const u64 *E = merge_E(B, b), *O = merge_O(B, b);
-    KsLayout Lo = ks_layout(R, B, b);
-    const int ne = row_elems(g);
-    const size_t gbase = ((size_t)i << R.log_n) + (size_t)r0 * g.c;
-    load_row_tw(tw, R.rowT_i, g, i, r0);
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-        const int j = r0 * g.c + e;
-        const u64 u = merge_u(R, B, E, O, 0, i, auto_src(j, B.d, R.log_n));
-        s[row_slot(g, e)] = u;
-        Lo.ta[gbase + e] = u;
-    }
-    __syncthreads();
-    row_inverse(s, tw, g.log_c, R.m[i].q);
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) Lo.x1[gbase + e] = s[row_slot(g, e)];
+    for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) sf_cp8(dst + row_slot(g, e), src + e);
+}
+__device__ __forceinline__ void issue_col_tile(u64 *dst, const u64 *src, const SfGeo &g, int c0)
+{
+    for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) sf_cp8(dst + col_slot(e), src + col_gidx(g, c0, e));
 }
 
-// K2: grid (C/16 column tiles, dnum digits, merges).
-// smem: column twiddles + K source tiles + 1 work tile.
-__global__ void __launch_bounds__(SF_THREADS) k_ks2(SfRing R, SfKsBatch B)
+// Elementwise: TA[b][i][j] = tau_d(E - X^s O).a at slot j (a slot permutation).
+// grid (N/256, L, merges): no integer division on the element path.
+__global__ void k_ks_gather(SfRing R, SfKsBatch B)
+{
+    const int b = blockIdx.z, i = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 *E = merge_E(B, b), *O = merge_O(B, b);
+    ks_layout(R, B, b).ta[((size_t)i << R.log_n) + j] = merge_u(R, B, E, O, 0, i, auto_src(j, B.d, R.log_n));
+}
+
+// Generic row pass over a per-merge set of npoly polynomials in the scratch:
+// poly t reads scratch + src_off + t N, writes scratch + dst_off + t N, with
+// modulus mod_base + t % mod_period.  Groups: (row tile, t); items: merges.
+struct SfRowSet {
+    size_t src_off, dst_off;
+    int npoly, mod_base, mod_period;
+};
+
+template <bool INV>
+__global__ void __launch_bounds__(SF_THREADS) k_rows(SfRing R, SfKsBatch B, SfRowSet S, int bpg)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SfGeo g = ring_geo(R);
-    const int c0 = blockIdx.x * SF_NB, j = blockIdx.y, b = blockIdx.z;
-    KsLayout Lo = ks_layout(R, B, b);
-    const int ne = col_elems(g), tw_words = tile_words(g.log_r);
-    const int lo = j * R.K, hi = min((j + 1) * R.K, R.L), nd = hi - lo;
+    const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
+    const int t = grp % S.npoly, r0 = (grp / S.npoly) * SF_NB;
+    const int mod = S.mod_base + t % S.mod_period;
+    const SfMod M = R.m[mod];
+    const size_t per = sf_ks_scratch_words_dev(R);
+    const size_t off_s = S.src_off + ((size_t)t << R.log_n) + (size_t)r0 * g.c;
+    const size_t off_d = S.dst_off + ((size_t)t << R.log_n) + (size_t)r0 * g.c;
     sf_tw *tw = (sf_tw *)smem_raw;
-    u64 *src_t = (u64 *)(tw + g.r);
-    u64 *work = src_t + (size_t)nd * tw_words;
-    // inverse column pass of the digit's limbs, then y_i = x_i N^-1 Qhat_i^-1 mod q_i
-    for (int t = 0; t < nd; ++t) {
-        const int i = lo + t;
-        u64 *st = src_t + (size_t)t * tw_words;
-        const u64 *src = Lo.x1 + ((size_t)i << R.log_n);
-        load_col_tw(tw, R.colT_i, g, i);
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) st[col_slot(e)] = src[col_gidx(g, c0, e)];
+    u64 *buf0 = (u64 *)(tw + SF_NB * g.c);
+    u64 *buf1 = buf0 + tile_words(g.log_c);
+    load_row_tw(tw, INV ? R.rowT_i : R.rowT_f, g, mod, r0);
+    if (sub < B.count) issue_row_tile(buf0, B.scratch + per * sub + off_s, g);
+    sf_cp_commit();
+    for (int k = 0, b = sub; b < B.count; ++k, b += bpg) {
+        u64 *cur = (k & 1) ? buf1 : buf0, *nxt = (k & 1) ? buf0 : buf1;
+        if (b + bpg < B.count) issue_row_tile(nxt, B.scratch + per * (b + bpg) + off_s, g);
+        sf_cp_commit();
+        sf_cp_wait<1>();
         __syncthreads();
-        col_inverse(st, tw, g.log_r, R.m[i].q);
-        const u64 w = R.mu_inv[j * R.K + t], wp = R.mu_inv_p[j * R.K + t];
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) st[col_slot(e)] = sf_mul_shoup(st[col_slot(e)], w, wp, R.m[i].q);
+        if (INV) row_inverse(cur, tw, g.log_c, M.q);
+        else row_forward(cur, tw, g.log_c, M.q);
+        u64 *dst = B.scratch + per * b + off_d;
+        for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) dst[e] = cur[row_slot(g, e)];
         __syncthreads();
     }
-    // ModUp to every modulus outside the digit, then the forward column pass
+}
+
+// ModUp.  Groups: (column tile, digit j); items: merges.  smem: inverse and
+// forward column tables of every modulus, two buffers of nd source tiles, one
+// work tile.
+__global__ void __launch_bounds__(SF_THREADS) k_ks2(SfRing R, SfKsBatch B, int bpg)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SfGeo g = ring_geo(R);
+    const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
+    const int j = grp % R.dnum, c0 = (grp / R.dnum) * SF_NB;
+    const int lo = j * R.K, hi = min((j + 1) * R.K, R.L), nd = hi - lo;
+    const int tw_words = tile_words(g.log_r);
+    sf_tw *twi = (sf_tw *)smem_raw;                 // [nm][R] inverse
+    sf_tw *twf = twi + (size_t)R.nm * g.r;          // [nm][R] forward
+    u64 *bufs = (u64 *)(twf + (size_t)R.nm * g.r);  // 2 x nd tiles
+    u64 *work = bufs + (size_t)2 * nd * tw_words;
     for (int m = 0; m < R.nm; ++m) {
-        if (m >= lo && m < hi) continue;
-        const SfMod &M = R.m[m];
-        load_col_tw(tw, R.colT_f, g, m);
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-            const int sl = col_slot(e);
-            u64 acc = 0;
-            for (int t = 0; t < nd; ++t) {
-                const size_t ci = ((size_t)(j * R.K + t)) * R.nm + m;
-                acc = sf_add(acc, sf_mul_shoup(src_t[(size_t)t * tw_words + sl], R.mu_qhat[ci], R.mu_qhat_p[ci], M.q), M.q);
-            }
-            work[sl] = acc;
+        load_col_tw(twi + (size_t)m * g.r, R.colT_i, g, m);
+        load_col_tw(twf + (size_t)m * g.r, R.colT_f, g, m);
+    }
+    if (sub < B.count) {
+        const KsLayout Lo = ks_layout(R, B, sub);
+        for (int t = 0; t < nd; ++t) issue_col_tile(bufs + (size_t)t * tw_words, Lo.x1 + ((size_t)(lo + t) << R.log_n), g, c0);
+    }
+    sf_cp_commit();
+    for (int k = 0, b = sub; b < B.count; ++k, b += bpg) {
+        u64 *cur = bufs + (size_t)(k & 1) * nd * tw_words, *nxt = bufs + (size_t)((k + 1) & 1) * nd * tw_words;
+        if (b + bpg < B.count) {
+            const KsLayout Ln = ks_layout(R, B, b + bpg);
+            for (int t = 0; t < nd; ++t) issue_col_tile(nxt + (size_t)t * tw_words, Ln.x1 + ((size_t)(lo + t) << R.log_n), g, c0);
+        }
+        sf_cp_commit();
+        sf_cp_wait<1>();
+        __syncthreads();
+        // inverse column pass of the digit's limbs, then y_i = x_i N^-1 Qhat_i^-1 mod q_i
+        for (int t = 0; t < nd; ++t) {
+            const int i = lo + t;
+            u64 *st = cur + (size_t)t * tw_words;
+            col_inverse(st, twi + (size_t)i * g.r, g.log_r, R.m[i].q);
+            const u64 w = R.mu_inv[j * R.K + t], wp = R.mu_inv_p[j * R.K + t];
+            for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x)
+                st[col_slot(e)] = sf_mul_shoup(st[col_slot(e)], w, wp, R.m[i].q);
         }
         __syncthreads();
-        col_forward(work, tw, g.log_r, M.q);
-        u64 *dst = Lo.x2 + ((size_t)(j * R.nm + m) << R.log_n);
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) dst[col_gidx(g, c0, e)] = work[col_slot(e)];
-        __syncthreads();
+        const KsLayout Lo = ks_layout(R, B, b);
+        for (int m = 0; m < R.nm; ++m) {
+            if (m >= lo && m < hi) continue;
+            const SfMod &M = R.m[m];
+            for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) {
+                const int sl = col_slot(e);
+                u64 acc = 0;
+                for (int t = 0; t < nd; ++t) {
+                    const size_t ci = ((size_t)(j * R.K + t)) * R.nm + m;
+                    acc = sf_add(acc, sf_mul_shoup(cur[(size_t)t * tw_words + sl], R.mu_qhat[ci], R.mu_qhat_p[ci], M.q), M.q);
+                }
+                work[sl] = acc;
+            }
+            __syncthreads();
+            col_forward(work, twf + (size_t)m * g.r, g.log_r, M.q);
+            u64 *dst = Lo.x2 + ((size_t)(j * R.nm + m) << R.log_n);
+            for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) dst[col_gidx(g, c0, e)] = work[col_slot(e)];
+            __syncthreads();
+        }
     }
 }
 
-// K3: grid (R/16 row tiles, nm moduli, merges).  EPT = tile elements per thread.
-// smem: row twiddles (forward, then inverse for special moduli) + 1 tile.
+// Inner product with the key.  Groups: (row tile, modulus m); items: merges,
+// each taking dnum steps (one per digit) whose tiles are double-buffered.
+// Output: ACC (data moduli, NTT domain) or, for the special moduli, their NTT
+// values in the x1 region (the inverse row pass runs in k_rows<true>).
 template <int EPT>
-__global__ void __launch_bounds__(SF_THREADS, EPT >= 16 ? 1 : 3) k_ks3(SfRing R, SfKsBatch B)
+__global__ void __launch_bounds__(SF_THREADS, EPT >= 16 ? 1 : 3) k_ks3(SfRing R, SfKsBatch B, int bpg)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SfGeo g = ring_geo(R);
-    const int r0 = blockIdx.x * SF_NB, m = blockIdx.y, b = blockIdx.z;
-    sf_tw *tw = (sf_tw *)smem_raw;
-    u64 *s = (u64 *)(tw + SF_NB * g.c);
-    KsLayout Lo = ks_layout(R, B, b);
-    const int ne = row_elems(g);
+    const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
+    const int m = grp % R.nm, r0 = (grp / R.nm) * SF_NB;
     const SfMod M = R.m[m];
     const size_t tile_off = (size_t)r0 * g.c;
+    sf_tw *tw = (sf_tw *)smem_raw;
+    u64 *buf0 = (u64 *)(tw + SF_NB * g.c);
+    u64 *buf1 = buf0 + tile_words(g.log_c);
     load_row_tw(tw, R.rowT_f, g, m, r0);
-    // per digit c * key (c < 36q lazy, key < q) is Montgomery-reduced into
-    // [0, 2q) and summed: the sums stay below 2 q dnum < 2^55
+    const int n_mine = sub < B.count ? (B.count - sub + bpg - 1) / bpg : 0;
+    const int steps = n_mine * R.dnum;
+    // step k -> merge sub + (k / dnum) * bpg, digit k % dnum
+    if (steps > 0) {
+        const KsLayout Lo = ks_layout(R, B, sub);
+        const bool own = (m < min(R.K, R.L));
+        issue_row_tile(buf0, (own ? Lo.ta + ((size_t)m << R.log_n) : Lo.x2 + ((size_t)m << R.log_n)) + tile_off, g);
+    }
+    sf_cp_commit();
     u64 acc_a[EPT], acc_b[EPT];
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) acc_a[k] = acc_b[k] = 0;
-    for (int j = 0; j < R.dnum; ++j) {
-        const int lo = j * R.K, hi = min((j + 1) * R.K, R.L);
-        const bool own = (m >= lo && m < hi);
-        const u64 *src = (own ? Lo.ta + ((size_t)m << R.log_n) : Lo.x2 + ((size_t)(j * R.nm + m) << R.log_n)) + tile_off;
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) s[row_slot(g, e)] = src[e];
+    for (int x = 0; x < EPT; ++x) acc_a[x] = acc_b[x] = 0;
+    for (int k = 0; k < steps; ++k) {
+        const int b = sub + (k / R.dnum) * bpg, j = k % R.dnum;
+        u64 *cur = (k & 1) ? buf1 : buf0, *nxt = (k & 1) ? buf0 : buf1;
+        if (k + 1 < steps) {
+            const int bn = sub + ((k + 1) / R.dnum) * bpg, jn = (k + 1) % R.dnum;
+            const KsLayout Ln = ks_layout(R, B, bn);
+            const bool own_n = (m >= jn * R.K && m < min((jn + 1) * R.K, R.L));
+            issue_row_tile(nxt, (own_n ? Ln.ta + ((size_t)m << R.log_n) : Ln.x2 + ((size_t)(jn * R.nm + m) << R.log_n)) + tile_off, g);
+        }
+        sf_cp_commit();
+        sf_cp_wait<1>();
         __syncthreads();
-        if (!own) row_forward(s, tw, g.log_c, M.q);
+        const bool own = (m >= j * R.K && m < min((j + 1) * R.K, R.L));
+        if (!own) row_forward(cur, tw, g.log_c, M.q);
         const u64 *ka = B.key + ((((size_t)j * 2 + 0) * R.nm + m) << R.log_n) + tile_off;
         const u64 *kb = B.key + ((((size_t)j * 2 + 1) * R.nm + m) << R.log_n) + tile_off;
+        // per digit c * key (c lazy < 36q, key < q) is Montgomery-reduced into [0, 2q) and summed
 #pragma unroll
-        for (int k = 0; k < EPT; ++k) {
-            const int e = threadIdx.x + k * SF_THREADS;
-            const u64 c = s[row_slot(g, e)];
+        for (int x = 0; x < EPT; ++x) {
+            const int e = threadIdx.x + x * SF_THREADS;
+            const u64 c = cur[row_slot(g, e)];
             const u64 xa = __ldg(ka + e), xb = __ldg(kb + e);
-            acc_a[k] += sf_redc_lazy(sf_mulhi(c, xa), c * xa, M.q, M.qinv_neg);
-            acc_b[k] += sf_redc_lazy(sf_mulhi(c, xb), c * xb, M.q, M.qinv_neg);
+            acc_a[x] += sf_redc_lazy(sf_mulhi(c, xa), c * xa, M.q, M.qinv_neg);
+            acc_b[x] += sf_redc_lazy(sf_mulhi(c, xb), c * xb, M.q, M.qinv_neg);
+        }
+        if (j == R.dnum - 1) {
+            const KsLayout Lo = ks_layout(R, B, b);
+            u64 *da, *db;
+            if (m < R.L) {
+                da = Lo.accq + ((size_t)m << R.log_n) + tile_off;
+                db = Lo.accq + ((size_t)(R.L + m) << R.log_n) + tile_off;
+            } else {
+                da = Lo.x1 + ((size_t)(m - R.L) << R.log_n) + tile_off;
+                db = Lo.x1 + ((size_t)(R.K + m - R.L) << R.log_n) + tile_off;
+            }
+#pragma unroll
+            for (int x = 0; x < EPT; ++x) {
+                const int e = threadIdx.x + x * SF_THREADS;
+                da[e] = sf_reduce(acc_a[x], M.q, M.one_p);
+                db[e] = sf_reduce(acc_b[x], M.q, M.one_p);
+                acc_a[x] = acc_b[x] = 0;
+            }
         }
         __syncthreads();
     }
-    if (m < R.L) {
-        u64 *da = Lo.accq + ((size_t)m << R.log_n) + tile_off;
-        u64 *db = Lo.accq + ((size_t)(R.L + m) << R.log_n) + tile_off;
-#pragma unroll
-        for (int k = 0; k < EPT; ++k) {
-            const int e = threadIdx.x + k * SF_THREADS;
-            da[e] = sf_reduce(acc_a[k], M.q, M.one_p);
-            db[e] = sf_reduce(acc_b[k], M.q, M.one_p);
+}
+
+// ModDown conversion.  Groups: (column tile, part p); items: merges.  smem: K
+// inverse (special) + L forward (data) column tables, two buffers of K tiles,
+// one work tile.
+__global__ void __launch_bounds__(SF_THREADS) k_ks4(SfRing R, SfKsBatch B, int bpg)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SfGeo g = ring_geo(R);
+    const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
+    const int p = grp % 2, c0 = (grp / 2) * SF_NB;
+    const int tw_words = tile_words(g.log_r);
+    sf_tw *twi = (sf_tw *)smem_raw;                 // [K][R] inverse, special moduli
+    sf_tw *twf = twi + (size_t)R.K * g.r;           // [L][R] forward, data moduli
+    u64 *bufs = (u64 *)(twf + (size_t)R.L * g.r);   // 2 x K tiles
+    u64 *work = bufs + (size_t)2 * R.K * tw_words;
+    for (int k = 0; k < R.K; ++k) load_col_tw(twi + (size_t)k * g.r, R.colT_i, g, R.L + k);
+    for (int i = 0; i < R.L; ++i) load_col_tw(twf + (size_t)i * g.r, R.colT_f, g, i);
+    if (sub < B.count) {
+        const KsLayout Lo = ks_layout(R, B, sub);
+        for (int k = 0; k < R.K; ++k)
+            issue_col_tile(bufs + (size_t)k * tw_words, Lo.x1 + ((size_t)(p * R.K + k) << R.log_n), g, c0);
+    }
+    sf_cp_commit();
+    for (int kk = 0, b = sub; b < B.count; ++kk, b += bpg) {
+        u64 *cur = bufs + (size_t)(kk & 1) * R.K * tw_words, *nxt = bufs + (size_t)((kk + 1) & 1) * R.K * tw_words;
+        if (b + bpg < B.count) {
+            const KsLayout Ln = ks_layout(R, B, b + bpg);
+            for (int k = 0; k < R.K; ++k)
+                issue_col_tile(nxt + (size_t)k * tw_words, Ln.x1 + ((size_t)(p * R.K + k) << R.log_n), g, c0);
         }
-    } else {
-        // special prime: inverse row pass of both parts, into ACC_P (x1 region)
-        const int kk = m - R.L;
-        load_row_tw(tw, R.rowT_i, g, m, r0);
-        for (int p = 0; p < 2; ++p) {
-#pragma unroll
-            for (int k = 0; k < EPT; ++k) {
-                const int e = threadIdx.x + k * SF_THREADS;
-                s[row_slot(g, e)] = sf_reduce(p == 0 ? acc_a[k] : acc_b[k], M.q, M.one_p);
+        sf_cp_commit();
+        sf_cp_wait<1>();
+        __syncthreads();
+        for (int k = 0; k < R.K; ++k) {
+            const int m = R.L + k;
+            u64 *st = cur + (size_t)k * tw_words;
+            col_inverse(st, twi + (size_t)k * g.r, g.log_r, R.m[m].q);
+            const u64 w = R.md_inv[k], wp = R.md_inv_p[k];
+            for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x)
+                st[col_slot(e)] = sf_mul_shoup(st[col_slot(e)], w, wp, R.m[m].q);
+        }
+        __syncthreads();
+        const KsLayout Lo = ks_layout(R, B, b);
+        for (int i = 0; i < R.L; ++i) {
+            const SfMod &M = R.m[i];
+            for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) {
+                const int sl = col_slot(e);
+                u64 acc = 0;
+                for (int k = 0; k < R.K; ++k) {
+                    const size_t ci = (size_t)k * R.L + i;
+                    acc = sf_add(acc, sf_mul_shoup(cur[(size_t)k * tw_words + sl], R.md_phat[ci], R.md_phat_p[ci], M.q), M.q);
+                }
+                work[sl] = acc;
             }
             __syncthreads();
-            row_inverse(s, tw, g.log_c, M.q);
-            u64 *dst = Lo.x1 + ((size_t)(p * R.K + kk) << R.log_n) + tile_off;
-            for (int e = threadIdx.x; e < ne; e += blockDim.x) dst[e] = s[row_slot(g, e)];
+            col_forward(work, twf + (size_t)i * g.r, g.log_r, M.q);
+            u64 *dst = Lo.x2 + ((size_t)(p * R.L + i) << R.log_n);
+            for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) dst[col_gidx(g, c0, e)] = work[col_slot(e)];
             __syncthreads();
         }
     }
 }
 
-// K4: grid (C/16 column tiles, 2 parts, merges).
-// smem: column twiddles + K source tiles + 1 work tile.
-__global__ void __launch_bounds__(SF_THREADS) k_ks4(SfRing R, SfKsBatch B)
+// ModDown finish.  Groups: (row tile, limb i); items: (merge b, part p).
+// RES = (ACC - conv) P^-1 written over ACC.  smem: forward row twiddles, two
+// buffers of (conversion tile, ACC tile).
+__global__ void __launch_bounds__(SF_THREADS) k_ks5(SfRing R, SfKsBatch B, int bpg)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SfGeo g = ring_geo(R);
-    const int c0 = blockIdx.x * SF_NB, p = blockIdx.y, b = blockIdx.z;
-    KsLayout Lo = ks_layout(R, B, b);
-    const int ne = col_elems(g), tw_words = tile_words(g.log_r);
-    sf_tw *tw = (sf_tw *)smem_raw;
-    u64 *src_t = (u64 *)(tw + g.r);
-    u64 *work = src_t + (size_t)R.K * tw_words;
-    for (int k = 0; k < R.K; ++k) {
-        const int m = R.L + k;
-        u64 *st = src_t + (size_t)k * tw_words;
-        const u64 *src = Lo.x1 + ((size_t)(p * R.K + k) << R.log_n);
-        load_col_tw(tw, R.colT_i, g, m);
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) st[col_slot(e)] = src[col_gidx(g, c0, e)];
-        __syncthreads();
-        col_inverse(st, tw, g.log_r, R.m[m].q);
-        const u64 w = R.md_inv[k], wp = R.md_inv_p[k];
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) st[col_slot(e)] = sf_mul_shoup(st[col_slot(e)], w, wp, R.m[m].q);
-        __syncthreads();
-    }
-    for (int i = 0; i < R.L; ++i) {
-        const SfMod &M = R.m[i];
-        load_col_tw(tw, R.colT_f, g, i);
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-            const int sl = col_slot(e);
-            u64 acc = 0;
-            for (int k = 0; k < R.K; ++k) {
-                const size_t ci = (size_t)k * R.L + i;
-                acc = sf_add(acc, sf_mul_shoup(src_t[(size_t)k * tw_words + sl], R.md_phat[ci], R.md_phat_p[ci], M.q), M.q);
-            }
-            work[sl] = acc;
-        }
-        __syncthreads();
-        col_forward(work, tw, g.log_r, M.q);
-        u64 *dst = Lo.x2 + ((size_t)(p * R.L + i) << R.log_n);
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) dst[col_gidx(g, c0, e)] = work[col_slot(e)];
-        __syncthreads();
-    }
-}
-
-// K5: grid (R/16 row tiles, L limbs, 2 * merges).  smem: forward row twiddles + 1 tile.
-__global__ void __launch_bounds__(SF_THREADS) k_ks5(SfRing R, SfKsBatch B)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SfGeo g = ring_geo(R);
-    const int r0 = blockIdx.x * SF_NB, i = blockIdx.y, p = blockIdx.z & 1, b = blockIdx.z >> 1;
-    sf_tw *tw = (sf_tw *)smem_raw;
-    u64 *s = (u64 *)(tw + SF_NB * g.c);
-    KsLayout Lo = ks_layout(R, B, b);
-    const u64 *E = merge_E(B, b), *O = merge_O(B, b);
-    u64 *out = merge_out(B, b);
-    const int ne = row_elems(g);
+    const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
+    const int i = grp % R.L, r0 = (grp / R.L) * SF_NB;
     const SfMod M = R.m[i];
     const size_t tile_off = (size_t)r0 * g.c;
-    const u64 *src = Lo.x2 + ((size_t)(p * R.L + i) << R.log_n) + tile_off;
+    const int tw_words = tile_words(g.log_c);
+    sf_tw *tw = (sf_tw *)smem_raw;
+    u64 *bufs = (u64 *)(tw + SF_NB * g.c);          // 2 x (conv, acc)
     load_row_tw(tw, R.rowT_f, g, i, r0);
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) s[row_slot(g, e)] = src[e];
-    __syncthreads();
-    row_forward(s, tw, g.log_c, M.q);
-    const u64 *acc = Lo.accq + ((size_t)(p * R.L + i) << R.log_n) + tile_off;
-    u64 *dst = out + (((size_t)p * R.L + i) << R.log_n) + tile_off;
+    const int n_items = 2 * B.count;
+    if (sub < n_items) {
+        const KsLayout Lo = ks_layout(R, B, sub >> 1);
+        const int p = sub & 1;
+        issue_row_tile(bufs, Lo.x2 + ((size_t)(p * R.L + i) << R.log_n) + tile_off, g);
+        issue_row_tile(bufs + tw_words, Lo.accq + ((size_t)(p * R.L + i) << R.log_n) + tile_off, g);
+    }
+    sf_cp_commit();
     const u64 pinv = R.md_pinv[i], pinv_p = R.md_pinv_p[i];
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-        const u64 conv = sf_reduce(s[row_slot(g, e)], M.q, M.one_p);
-        u64 res = sf_mul_shoup(sf_sub(acc[e], conv, M.q), pinv, pinv_p, M.q);
-        const int j = r0 * g.c + e;
-        if (B.add_v) res = sf_add(res, merge_v(R, B, E, O, p, i, j), M.q);
-        if (p == 1) res = sf_add(res, merge_u(R, B, E, O, 1, i, auto_src(j, B.d, R.log_n)), M.q);
-        dst[e] = res;
+    for (int k = 0, it = sub; it < n_items; ++k, it += bpg) {
+        u64 *cur = bufs + (size_t)(k & 1) * 2 * tw_words, *nxt = bufs + (size_t)((k + 1) & 1) * 2 * tw_words;
+        if (it + bpg < n_items) {
+            const KsLayout Ln = ks_layout(R, B, (it + bpg) >> 1);
+            const int pn = (it + bpg) & 1;
+            issue_row_tile(nxt, Ln.x2 + ((size_t)(pn * R.L + i) << R.log_n) + tile_off, g);
+            issue_row_tile(nxt + tw_words, Ln.accq + ((size_t)(pn * R.L + i) << R.log_n) + tile_off, g);
+        }
+        sf_cp_commit();
+        sf_cp_wait<1>();
+        __syncthreads();
+        row_forward(cur, tw, g.log_c, M.q);
+        const int b = it >> 1, p = it & 1;
+        u64 *dst = ks_layout(R, B, b).accq + ((size_t)(p * R.L + i) << R.log_n) + tile_off;
+        for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) {
+            const int sl = row_slot(g, e);
+            const u64 conv = sf_reduce(cur[sl], M.q, M.one_p);
+            dst[e] = sf_mul_shoup(sf_sub(cur[tw_words + sl], conv, M.q), pinv, pinv_p, M.q);
+        }
+        __syncthreads();
     }
 }
 
-sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B, cudaStream_t st)
+// Elementwise merge: out = [add_v] (E + X^s O) + RES, plus tau_d(u.b) on part b.
+// grid (N/256, 2L, merges): no integer division on the element path.
+__global__ void k_ks_merge(SfRing R, SfKsBatch B)
+{
+    const int b = blockIdx.z, pi = blockIdx.y;
+    const int p = pi >= R.L ? 1 : 0, i = pi - p * R.L;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 *E = merge_E(B, b), *O = merge_O(B, b);
+    const size_t w = ((size_t)pi << R.log_n) + j;
+    const u64 q = R.m[i].q;
+    u64 res = ks_layout(R, B, b).accq[w];
+    if (B.add_v) res = sf_add(res, merge_v(R, B, E, O, p, i, j), q);
+    if (p == 1) res = sf_add(res, merge_u(R, B, E, O, 1, i, auto_src(j, B.d, R.log_n)), q);
+    merge_out(B, b)[w] = res;
+}
+
+// ------------------------------------------------------------ launching ----
+
+static size_t smem_rows(const SfRing &R, int tiles)
+{
+    return sizeof(sf_tw) * SF_NB * R.c + sizeof(u64) * tile_words(R.log_c) * tiles;
+}
+
+template <class K>
+static int occupancy(K kernel, size_t smem)
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, SF_THREADS, smem) != cudaSuccess) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return std::max(1, b);
+}
+
+// blocks per group: fill every SM at the kernel's occupancy, at most one block per item
+static int blocks_per_group(const sf_ctx *ctx, int occ, int n_groups, int n_items)
+{
+    const int target = ctx->num_sms * occ;
+    const int bpg = (target + n_groups - 1) / n_groups;
+    return std::max(1, std::min(bpg, n_items));
+}
+
+sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
 {
     const SfRing &R = ctx->ring;
-    if (B.count <= 0) return SF_OK;
+    if (B0.count <= 0) return SF_OK;
     const int maxd = std::min(R.K, R.L);
-    const size_t smem1 = sf_smem_row(R, 1), smem2 = sf_smem_col(R, maxd + 1), smem3 = sf_smem_row(R, 1),
-                 smem4 = sf_smem_col(R, R.K + 1), smem5 = sf_smem_row(R, 1);
+    const int rtiles = R.r / SF_NB, ctiles = R.c / SF_NB;
+    const size_t sm_rows = smem_rows(R, 2);
+    const size_t sm2 = sizeof(sf_tw) * 2 * R.nm * R.r + sizeof(u64) * tile_words(R.log_r) * (2 * maxd + 1);
+    const size_t sm3 = smem_rows(R, 2);
+    const size_t sm4 = sizeof(sf_tw) * (R.K + R.L) * R.r + sizeof(u64) * tile_words(R.log_r) * (2 * R.K + 1);
+    const size_t sm5 = smem_rows(R, 4);
+    const int ept = (R.c * SF_NB) / SF_THREADS;
     cudaEvent_t ev;
-    for (int off = 0; off < B.count; off += 16384) {
-        SfKsBatch b = B;
-        b.count = std::min(16384, B.count - off);
-        b.first = B.first + off;
+    for (int off = 0; off < B0.count; off += 32768) {
+        SfKsBatch b = B0;
+        b.count = std::min(32768, B0.count - off);
+        b.first = B0.first + off;
         b.scratch += sf_ks_scratch_words(R) * off;
+        const dim3 eg(R.n / 256, R.L, b.count), mg(R.n / 256, 2 * R.L, b.count);
 
         sf_launch_begin(ctx, SFK_KS1_GATHER_INV_ROW, st, &ev);
-        k_ks1<<<dim3(R.r / SF_NB, R.L, b.count), SF_THREADS, smem1, st>>>(R, b);
+        k_ks_gather<<<eg, 256, 0, st>>>(R, b);
+        {
+            const SfRowSet S{0, (size_t)R.L << R.log_n, R.L, 0, R.L};   // TA -> X1
+            const int ng = rtiles * S.npoly;
+            const int bpg = blocks_per_group(ctx, occupancy(k_rows<true>, sm_rows), ng, b.count);
+            k_rows<true><<<ng * bpg, SF_THREADS, sm_rows, st>>>(R, b, S, bpg);
+        }
         sf_launch_end(ctx, SFK_KS1_GATHER_INV_ROW, st, ev);
 
         sf_launch_begin(ctx, SFK_KS2_MODUP_COL, st, &ev);
-        k_ks2<<<dim3(R.c / SF_NB, R.dnum, b.count), SF_THREADS, smem2, st>>>(R, b);
+        {
+            const int ng = ctiles * R.dnum;
+            const int bpg = blocks_per_group(ctx, occupancy(k_ks2, sm2), ng, b.count);
+            k_ks2<<<ng * bpg, SF_THREADS, sm2, st>>>(R, b, bpg);
+        }
         sf_launch_end(ctx, SFK_KS2_MODUP_COL, st, ev);
 
         sf_launch_begin(ctx, SFK_KS3_INNER_ROW, st, &ev);
-        int ept = (R.c * SF_NB) / SF_THREADS;
-        dim3 g3(R.r / SF_NB, R.nm, b.count);
-        switch (ept) {
-        case 2: k_ks3<2><<<g3, SF_THREADS, smem3, st>>>(R, b); break;
-        case 4: k_ks3<4><<<g3, SF_THREADS, smem3, st>>>(R, b); break;
-        case 8: k_ks3<8><<<g3, SF_THREADS, smem3, st>>>(R, b); break;
-        case 16: k_ks3<16><<<g3, SF_THREADS, smem3, st>>>(R, b); break;
-        default: return sf_set_error(SF_EINVAL, "unsupported ring split");
+        {
+            const int ng = rtiles * R.nm;
+            switch (ept) {
+#define SF_KS3_CASE(E)                                                                 \
+    case E: {                                                                          \
+        const int bpg = blocks_per_group(ctx, occupancy(k_ks3<E>, sm3), ng, b.count);  \
+        k_ks3<E><<<ng * bpg, SF_THREADS, sm3, st>>>(R, b, bpg);                        \
+        break;                                                                         \
+    }
+                SF_KS3_CASE(2) SF_KS3_CASE(4) SF_KS3_CASE(8) SF_KS3_CASE(16)
+#undef SF_KS3_CASE
+            default: return sf_set_error(SF_EINVAL, "unsupported ring split");
+            }
+            // inverse row pass of the special limbs' accumulators, in place in x1
+            const SfRowSet S{(size_t)R.L << R.log_n, (size_t)R.L << R.log_n, 2 * R.K, R.L, R.K};
+            const int ng2 = rtiles * S.npoly;
+            const int bpg2 = blocks_per_group(ctx, occupancy(k_rows<true>, sm_rows), ng2, b.count);
+            k_rows<true><<<ng2 * bpg2, SF_THREADS, sm_rows, st>>>(R, b, S, bpg2);
         }
         sf_launch_end(ctx, SFK_KS3_INNER_ROW, st, ev);
 
         sf_launch_begin(ctx, SFK_KS4_MODDOWN_COL, st, &ev);
-        k_ks4<<<dim3(R.c / SF_NB, 2, b.count), SF_THREADS, smem4, st>>>(R, b);
+        {
+            const int ng = ctiles * 2;
+            const int bpg = blocks_per_group(ctx, occupancy(k_ks4, sm4), ng, b.count);
+            k_ks4<<<ng * bpg, SF_THREADS, sm4, st>>>(R, b, bpg);
+        }
         sf_launch_end(ctx, SFK_KS4_MODDOWN_COL, st, ev);
 
         sf_launch_begin(ctx, SFK_KS5_FINISH_ROW, st, &ev);
-        k_ks5<<<dim3(R.r / SF_NB, R.L, 2 * b.count), SF_THREADS, smem5, st>>>(R, b);
+        {
+            const int ng = rtiles * R.L;
+            const int bpg = blocks_per_group(ctx, occupancy(k_ks5, sm5), ng, 2 * b.count);
+            k_ks5<<<ng * bpg, SF_THREADS, sm5, st>>>(R, b, bpg);
+            k_ks_merge<<<mg, 256, 0, st>>>(R, b);
+        }
         sf_launch_end(ctx, SFK_KS5_FINISH_ROW, st, ev);
     }
     SF_CUDA_TRY(cudaGetLastError());
@@ -383,7 +570,8 @@ sf_status sf_ks_run(sf_ctx *ctx, SfKsBatch B, u64 *scratch, int batch, cudaStrea
 sf_status sf_ks_init_attributes()
 {
     const int mx = 227 * 1024;
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_ks1, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    SF_CUDA_TRY(cudaFuncSetAttribute(k_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    SF_CUDA_TRY(cudaFuncSetAttribute(k_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     SF_CUDA_TRY(cudaFuncSetAttribute(k_ks2, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     SF_CUDA_TRY(cudaFuncSetAttribute(k_ks3<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     SF_CUDA_TRY(cudaFuncSetAttribute(k_ks3<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
