@@ -111,6 +111,9 @@ void sf_ctx_destroy(sf_ctx *ctx);
 /* Tuning and instrumentation knobs (name, value):
  *   "ks_batch"      merges per key-switch batch (1..4096; default chosen per N)
  *   "leaf_chunk"    linear-layer outputs per leaf batch (power of two)
+ *   "mem_budget"    bytes of leaf and pack-tree buffers one round may hold
+ *                   (default 64 GiB); larger layers are packed group by group,
+ *                   and groups larger than the budget in chunks of leaves
  *   "use_graph"     1 = capture a layer's launch sequence in a CUDA graph and
  *                   replay it (default 1), 0 = launch directly
  *   "kernel_timing" 1 = bracket every launch with CUDA events on its stream

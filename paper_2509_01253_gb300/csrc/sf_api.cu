@@ -484,18 +484,35 @@ extern "C" sf_status sf_eval_linear_layer(sf_ctx *ctx, const sf_layer *L, const 
     const size_t ct = ct_words(ctx);
     const int LB = leaf_batch_slots(R, k_in);
     const int batch = ctx->ks_batch;
+    // Memory plan: Gc groups at once when their leaf and tree buffers fit the
+    // budget; otherwise one group at a time in chunks of CH leaves (a chunk is
+    // the residue class a mod n/CH, reduced to its root by the first log2 CH
+    // tree levels; the n/CH roots then finish the tree).
+    const size_t ct_bytes = ct * sizeof(u64);
+    const size_t per_group = (size_t)n * ct_bytes + (size_t)std::max(n / 2, 1) * ct_bytes;
+    int Gc = 1, CH = n;
+    if (per_group <= ctx->mem_budget) {
+        Gc = (int)std::max<size_t>(1, std::min<size_t>((size_t)G, ctx->mem_budget / per_group));
+    } else {
+        CH = n;
+        while (CH > 1 && ((size_t)CH * ct_bytes * 3 / 2 + (size_t)(n / CH) * ct_bytes * 3 / 2) > ctx->mem_budget) CH /= 2;
+    }
+    const int nch = n / CH;
     Carver cv;
     size_t o_ct = cv.take((size_t)k_in * ct);
     size_t o_pos = cv.take(((size_t)L->E_in + 1) / 2);
     size_t o_sig = cv.take(((size_t)L->E_out + 1) / 2);
     size_t o_w1 = cv.take((size_t)LB * k_in * R.L * R.n);
-    size_t o_A = cv.take((size_t)G * n * ct);
-    size_t o_B = cv.take((size_t)G * std::max(n / 2, 1) * ct);
+    size_t o_A = cv.take((size_t)Gc * CH * ct);
+    size_t o_B = cv.take((size_t)Gc * std::max(CH / 2, 1) * ct);
+    size_t o_RA = cv.take(nch > 1 ? (size_t)nch * ct : 0);
+    size_t o_RB = cv.take(nch > 1 ? (size_t)std::max(nch / 2, 1) * ct : 0);
     size_t o_ks = cv.take(sf_ks_scratch_words(R) * batch);
     void *w = nullptr;
     SF_TRY(sf_scratch(ctx, cv.words * sizeof(u64), &w));
     u64 *ws = (u64 *)w;
-    u64 *d_ct = ws + o_ct, *d_w1 = ws + o_w1, *A = ws + o_A, *B = ws + o_B, *d_ks = ws + o_ks;
+    u64 *d_ct = ws + o_ct, *d_w1 = ws + o_w1, *A = ws + o_A, *B = ws + o_B, *RA = ws + o_RA, *RB = ws + o_RB,
+        *d_ks = ws + o_ks;
     int *d_pos = (int *)(ws + o_pos), *d_sig = (int *)(ws + o_sig);
     std::vector<int> h_pos, h_sig;
     if (h_sigma_prev) SF_TRY(upload_perm_inverse(h_sigma_prev, L->E_in, d_pos, h_pos, st));
@@ -503,12 +520,13 @@ extern "C" sf_status sf_eval_linear_layer(sf_ctx *ctx, const sf_layer *L, const 
         h_sig.assign(h_sigma_out, h_sigma_out + L->E_out);
         SF_CUDA_TRY(cudaMemcpyAsync(d_sig, h_sig.data(), sizeof(int) * L->E_out, cudaMemcpyHostToDevice, st));
     }
+    int log_ch = 0;
+    while ((1 << log_ch) < CH) ++log_ch;
     // The launch sequence below depends only on pointers and shapes, so it is
     // captured once into a CUDA graph per (layer, keys, buffers, workspace)
     // and replayed; with kernel timing on it is launched directly.
     auto launch_all = [&](cudaStream_t s) -> sf_status {
         SF_TRY(prepare_inputs(ctx, d_in, k_in, d_ct, s));
-        // steps 6-9: leaves in slot order (slot = g n + l), only the E' real ones
         SfLeafParams P = leaf_params(L);
         P.k_in = k_in;
         P.pos_of = h_sigma_prev ? d_pos : nullptr;
@@ -517,25 +535,58 @@ extern "C" sf_status sf_eval_linear_layer(sf_ctx *ctx, const sf_layer *L, const 
         P.w1 = d_w1;
         P.n_slots_valid = L->E_out;
         P.leaf_stride = ct;
-        for (int s0 = 0; s0 < L->E_out; s0 += LB) {
-            int cnt = std::min(LB, L->E_out - s0);
-            SfLeafParams p = P;
-            p.s0 = s0;
-            p.leaves = A + (size_t)s0 * ct;
-            SF_TRY(sf_leaves_launch(ctx, p, cnt, s));
+        // leaves for slots s0 + t * stride, t < cnt, into dst
+        auto leaves = [&](int s0, int stride, int cnt, u64 *dst) -> sf_status {
+            for (int t0 = 0; t0 < cnt; t0 += LB) {
+                SfLeafParams p = P;
+                p.s0 = s0 + t0 * stride;
+                p.s_stride = stride;
+                p.leaves = dst + (size_t)t0 * ct;
+                SF_TRY(sf_leaves_launch(ctx, p, std::min(LB, cnt - t0), s));
+            }
+            return SF_OK;
+        };
+        for (int g0 = 0; g0 < G; g0 += Gc) {
+            const int gn = std::min(Gc, G - g0);
+            u64 *res = nullptr;
+            size_t res_stride = 0;
+            if (nch == 1) {
+                // steps 6-9: the real leaves of these groups in slot order (slot = g n + l)
+                const int s_end = std::min((g0 + gn) * n, L->E_out);
+                SF_TRY(leaves(g0 * n, 1, s_end - g0 * n, A));
+                // step 10: pack every group
+                std::vector<int> valid(gn);
+                for (int g = 0; g < gn; ++g) valid[g] = std::min(n, L->E_out - (g0 + g) * n);
+                SF_TRY(sf_pack_tree(ctx, rk->d_keys, rk->d, rk->key_words, A, B, gn, n, 0, valid, true, d_ks, batch,
+                                    &res, &res_stride, s));
+            } else {
+                const int g = g0;
+                const int live = L->E_out - g * n;   // valid slots of this group
+                for (int a = 0; a < nch; ++a) {
+                    const int va = live > a ? std::min(CH, (live - a + nch - 1) / nch) : 0;
+                    if (va == 0) {
+                        SF_CUDA_TRY(cudaMemsetAsync(RA + (size_t)a * ct, 0, ct_bytes, s));
+                        continue;
+                    }
+                    SF_TRY(leaves(g * n + a, nch, CH, A));
+                    u64 *cr = nullptr;
+                    size_t cs = 0;
+                    std::vector<int> v1(1, va);
+                    SF_TRY(sf_pack_tree(ctx, rk->d_keys, rk->d, rk->key_words, A, B, 1, CH, 0, v1, false, d_ks, batch,
+                                        &cr, &cs, s));
+                    SF_CUDA_TRY(cudaMemcpyAsync(RA + (size_t)a * ct, cr, ct_bytes, cudaMemcpyDeviceToDevice, s));
+                }
+                std::vector<int> vr(1, std::min(nch, std::max(live, 0)));
+                SF_TRY(sf_pack_tree(ctx, rk->d_keys, rk->d, rk->key_words, RA, RB, 1, nch, log_ch, vr, true, d_ks,
+                                    batch, &res, &res_stride, s));
+            }
+            std::vector<SfPolyJob> jobs;
+            for (int g = 0; g < gn; ++g)
+                for (int x = 0; x < 2 * R.L; ++x)
+                    jobs.push_back({res + res_stride * g + (size_t)x * R.n, d_out + ct * (g0 + g) + (size_t)x * R.n,
+                                    x % R.L});
+            SF_TRY(sf_ntt_jobs(ctx, jobs.data(), (int)jobs.size(), true, s));
         }
-        // step 10: pack every group
-        std::vector<int> valid(G);
-        for (int g = 0; g < G; ++g) valid[g] = std::min(n, L->E_out - g * n);
-        u64 *res = nullptr;
-        size_t res_stride = 0;
-        SF_TRY(sf_pack_tree(ctx, rk->d_keys, rk->d, rk->key_words, A, B, G, n, valid, d_ks, batch, &res, &res_stride,
-                            s));
-        std::vector<SfPolyJob> jobs;
-        for (int g = 0; g < G; ++g)
-            for (int x = 0; x < 2 * R.L; ++x)
-                jobs.push_back({res + res_stride * g + (size_t)x * R.n, d_out + ct * g + (size_t)x * R.n, x % R.L});
-        SF_TRY(sf_ntt_jobs(ctx, jobs.data(), (int)jobs.size(), true, s));
         if (L->d_bq) SF_TRY(sf_add_bias(ctx, d_out, G, n, L->E_out, h_sigma_out ? d_sig : nullptr, L->d_bq, L->C_out, s));
         return SF_OK;
     };
@@ -544,7 +595,7 @@ extern "C" sf_status sf_eval_linear_layer(sf_ctx *ctx, const sf_layer *L, const 
     } else {
         uint64_t key[12] = {L->gen, rk->gen, (uint64_t)(uintptr_t)d_in, (uint64_t)(uintptr_t)d_out, (uint64_t)k_in,
                             (uint64_t)(h_sigma_prev != nullptr), (uint64_t)(h_sigma_out != nullptr),
-                            (uint64_t)(uintptr_t)ws, (uint64_t)batch, (uint64_t)LB, 1, 0};
+                            (uint64_t)(uintptr_t)ws, (uint64_t)batch, (uint64_t)LB, (uint64_t)CH, (uint64_t)Gc};
         SfGraphEntry *hit = nullptr;
         for (auto &e : ctx->graphs)
             if (!memcmp(e.key, key, sizeof(key))) hit = &e;
@@ -560,6 +611,7 @@ extern "C" sf_status sf_eval_linear_layer(sf_ctx *ctx, const sf_layer *L, const 
             cudaStreamDestroy(cap);
             if (lst != SF_OK) {
                 if (graph) cudaGraphDestroy(graph);
+                for (int k = 0; k < SFK_COUNT; ++k) ctx->stats[k].launches = before[k];
                 return lst;
             }
             if (ee != cudaSuccess || !graph) return sf_set_error(SF_ECUDA, "graph capture failed: %s", cudaGetErrorString(ee));
@@ -647,6 +699,7 @@ extern "C" sf_status sf_linear_outputs(sf_ctx *ctx, const sf_layer *L, const uin
     P.w1 = ws + o_w1;
     P.n_slots_valid = n_outputs;
     P.leaf_stride = ct;
+    P.s_stride = 1;
     for (int s0 = 0; s0 < n_outputs; s0 += LB) {
         SfLeafParams p = P;
         p.s0 = s0;
@@ -723,8 +776,8 @@ extern "C" sf_status sf_pack(sf_ctx *ctx, const sf_rotkeys *rk, const uint64_t *
     std::vector<int> valid(1, n_leaves);
     u64 *res = nullptr;
     size_t rs = 0;
-    SF_TRY(sf_pack_tree(ctx, rk->d_keys, rk->d, rk->key_words, ws + o_A, ws + o_B, 1, n, valid, ws + o_ks, batch, &res, &rs,
-                        st));
+    SF_TRY(sf_pack_tree(ctx, rk->d_keys, rk->d, rk->key_words, ws + o_A, ws + o_B, 1, n, 0, valid, true, ws + o_ks, batch,
+                        &res, &rs, st));
     jobs.clear();
     for (int x = 0; x < 2 * R.L; ++x) jobs.push_back({res + (size_t)x * R.n, d_out + (size_t)x * R.n, x % R.L});
     SF_TRY(sf_ntt_jobs(ctx, jobs.data(), (int)jobs.size(), true, st));

@@ -454,6 +454,7 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
     ctx->scratch_bytes = 0;
     ctx->ks_batch = p->log_n >= 15 ? 64 : 128;
     ctx->leaf_chunk = 1 << 30;
+    ctx->mem_budget = (size_t)64 << 30;
     ctx->use_graph = 1;
     ctx->kernel_timing = 0;
     for (int k = 0; k < SFK_COUNT; ++k) ctx->stats.push_back({k_names[k], 0, 0.0});
@@ -634,6 +635,10 @@ extern "C" sf_status sf_ctx_set_option(sf_ctx *ctx, const char *name, int64_t va
     } else if (!strcmp(name, "leaf_chunk")) {
         if (value < 1 || (value & (value - 1))) return sf_set_error(SF_EINVAL, "leaf_chunk must be a power of two");
         ctx->leaf_chunk = (int)std::min<int64_t>(value, 1 << 30);
+    } else if (!strcmp(name, "mem_budget")) {
+        if (value < (1 << 20)) return sf_set_error(SF_EINVAL, "mem_budget must be at least 1 MiB");
+        ctx->mem_budget = (size_t)value;
+        sf_graph_cache_clear(ctx);
     } else if (!strcmp(name, "use_graph")) {
         if (value != 0 && value != 1) return sf_set_error(SF_EINVAL, "use_graph must be 0 or 1");
         ctx->use_graph = (int)value;

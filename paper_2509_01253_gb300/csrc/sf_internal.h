@@ -82,6 +82,7 @@ struct sf_ctx {
     // options
     int ks_batch;
     int leaf_chunk;
+    size_t mem_budget;        // bytes of leaf + tree buffers a round may use
     int use_graph;
     int kernel_timing;
     // instrumentation

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(SF_THREADS) k_leaf_col(SfRing R, SfLeafParams 
     const SfGeo g = ring_geo(R);
     const int c0 = blockIdx.x * SF_NB;
     const int j = blockIdx.y / R.L, i = blockIdx.y % R.L;
-    const int slot = P.s0 + blockIdx.z;
+    const int slot = P.s0 + blockIdx.z * P.s_stride;
     const int o = leaf_output(P, slot);
     if (o < 0) return;
     sf_tw *tw = (sf_tw *)smem_raw;
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(SF_THREADS, EPT >= 16 ? 1 : 3) k_leaf_row(SfRi
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SfGeo g = ring_geo(R);
     const int r0 = blockIdx.x * SF_NB, i = blockIdx.y;
-    const int slot = P.s0 + blockIdx.z;
+    const int slot = P.s0 + blockIdx.z * P.s_stride;
     const int o = leaf_output(P, slot);
     const size_t tile_off = (size_t)r0 * g.c;
     u64 *leaf = P.leaves + P.leaf_stride * blockIdx.z;
@@ -135,7 +135,7 @@ sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStre
     for (int off = 0; off < cnt; off += 65535) {
         SfLeafParams p = P;
         const int c = std::min(65535, cnt - off);
-        p.s0 = P.s0 + off;
+        p.s0 = P.s0 + off * P.s_stride;
         p.w1 = P.w1;    // w1 holds `cnt` slots; reuse from its start for each sub-launch
         p.leaves = P.leaves + P.leaf_stride * off;
         sf_launch_begin(ctx, SFK_LEAF_COL, st, &ev);
@@ -158,15 +158,14 @@ sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStre
 
 // ------------------------------------------------------------ pack tree --
 
-// G groups of n leaves in A ([G][n] ciphertexts, NTT domain); group g has
-// valid[g] non-zero leaves (the rest are zero).  B has room for [G][n/2].
-// Node i of a level is zero iff i >= valid[g]; a merge whose O-node is zero
-// runs without O (identical result, X^s * 0 = 0), and merges producing zero
-// nodes are skipped.  Result: G packed ciphertexts (NTT domain) at *res with
-// group stride *res_stride.
+// Pack-tree levels level0+1 .. level1 (see sf_layer.h).  Node i of a level
+// is zero iff i >= valid[g]; a merge whose O-node is zero runs without O
+// (identical result, X^s * 0 = 0), and merges producing zero nodes are
+// skipped.  Level lvl merges node t with node t + n_lvl/2 (n_lvl = nodes at
+// level lvl-1) using s = N / 2^lvl and d = 2^lvl + 1.
 sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int32_t> &key_d, size_t key_words,
-                       u64 *A, u64 *B, int G, int n, const std::vector<int> &valid, u64 *ks_scratch, int batch,
-                       u64 **res, size_t *res_stride, cudaStream_t st)
+                       u64 *A, u64 *B, int G, int n_nodes, int level0, const std::vector<int> &valid, bool trace,
+                       u64 *ks_scratch, int batch, u64 **res, size_t *res_stride, cudaStream_t st)
 {
     const SfRing &R = ctx->ring;
     const size_t ct = (size_t)2 * R.L * R.n;
@@ -178,14 +177,15 @@ sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int3
             }
         return sf_set_error(SF_EINVAL, "no rotation key for d = %d", d);
     };
+    int levels = 0;
+    while ((1 << levels) < n_nodes) ++levels;
+    const int level1 = level0 + levels;
     u64 *cur = A, *nxt = B;
-    size_t cur_gs = (size_t)n * ct, nxt_gs = (size_t)(n / 2 > 0 ? n / 2 : 1) * ct;
-    int log_n_grp = 0;
-    while ((1 << log_n_grp) < n) ++log_n_grp;
+    size_t cur_gs = (size_t)n_nodes * ct, nxt_gs = (size_t)(n_nodes / 2 > 0 ? n_nodes / 2 : 1) * ct;
     int full = 0;
-    while (full < G && valid[full] >= n) ++full;   // leading full groups
-    for (int lvl = 1; lvl <= log_n_grp; ++lvl) {
-        const int half = n >> lvl;
+    while (full < G && valid[full] >= n_nodes) ++full;   // leading full groups
+    for (int lvl = level0 + 1; lvl <= level1; ++lvl) {
+        const int half = n_nodes >> (lvl - level0);
         const int d = (1 << lvl) + 1;
         const u64 *key;
         SF_TRY(key_for(d, &key));
@@ -211,7 +211,7 @@ sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int3
             SF_TRY(sf_ks_run(ctx, b, ks_scratch, batch, st));
         }
         for (int gi = full; gi < G; ++gi) {
-            const int V = valid[gi];
+            const int V = std::min(valid[gi], 2 * half);
             const int active = std::min(V, half);
             const int with_o = std::max(0, std::min(active, V - half));
             SfKsBatch b = kb;
@@ -235,8 +235,8 @@ sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int3
         std::swap(cur, nxt);
         std::swap(cur_gs, nxt_gs);
     }
-    // field trace: for k = log2(n)+1 .. log2(N): ct <- ct + tau_{2^k+1}(ct)
-    for (int k = log_n_grp + 1; k <= R.log_n; ++k) {
+    // field trace: for k = level1+1 .. log2(N): ct <- ct + tau_{2^k+1}(ct)
+    for (int k = level1 + 1; trace && k <= R.log_n; ++k) {
         const int d = (1 << k) + 1;
         const u64 *key;
         SF_TRY(key_for(d, &key));

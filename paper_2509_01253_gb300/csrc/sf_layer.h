@@ -7,7 +7,7 @@ struct SfTermDev {
     int w_off;  // offset of this term's weights in the concatenated array
 };
 
-// Slot s (s0 <= s < s0 + count) of a leaf launch computes output sig_out[s]
+// Launch slot z computes slot s = s0 + z * s_stride, i.e. output sig_out[s]
 // (or s when sig_out is null); slots >= n_slots_valid are zero padding leaves.
 struct SfLeafParams {
     SfTermDev t[2];
@@ -15,6 +15,7 @@ struct SfLeafParams {
     int C_out, W_out;
     int k_in;
     int s0;
+    int s_stride;
     int n_slots_valid;
     const int64_t *wq;      // quantised weights (device)
     const int *pos_of;      // input index -> stream position (null = identity)
@@ -26,9 +27,14 @@ struct SfLeafParams {
 };
 
 sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStream_t st);
+// Pack-tree levels level0+1 .. level1 over G groups.  A holds, per group,
+// the n_nodes = 2^(level1 - level0) nodes of level `level0` (level 0 = leaves)
+// at group stride a_gs; B has room for half as many.  valid[g] = non-zero
+// nodes of group g.  With trace, the field-trace steps k = level1+1 .. log2 N
+// follow.  Result (G ciphertexts, NTT domain) at *res, group stride *res_stride.
 sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int32_t> &key_d, size_t key_words,
-                       u64 *A, u64 *B, int G, int n, const std::vector<int> &valid, u64 *ks_scratch, int batch,
-                       u64 **res, size_t *res_stride, cudaStream_t st);
+                       u64 *A, u64 *B, int G, int n_nodes, int level0, const std::vector<int> &valid, bool trace,
+                       u64 *ks_scratch, int batch, u64 **res, size_t *res_stride, cudaStream_t st);
 sf_status sf_add_bias(sf_ctx *ctx, u64 *out, int G, int n, int E_out, const int *d_sig_out, const int64_t *d_bq,
                       int C_out, cudaStream_t st);
 sf_status sf_shuffle_launch(sf_ctx *ctx, const u64 *in, u64 *out, const int *d_perm, int count, cudaStream_t st);

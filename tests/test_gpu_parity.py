@@ -370,3 +370,27 @@ def test_errors_are_reported():
         sf.sf_sync(s.ctx)
     finally:
         s.close()
+
+
+def test_memory_budget_chunking_is_exact(oracle):
+    """The same round under a budget that forces one group at a time, and a
+    smaller one that forces leaf chunks inside a group (residue classes
+    reduced to roots, then the roots finish the tree): bit-identical packed
+    ciphertexts, equal to the oracle's."""
+    log_n, L, bits, K, make, wsc, delta = SCALED["conv_ragged_two_groups"]
+    case = make()
+    s = Session(log_n, L, bits, K, sk_seed=51, rk_seed=52)
+    try:
+        outs = []
+        for budget in (None, 40 << 20, 10 << 20, 3 << 20):
+            if budget:
+                sf.sf_ctx_set_option(s.ctx, "mem_budget", budget)
+            lay, info, msg, _, got = _run_layer(s, case, delta, delta * wsc, wsc)
+            outs.append(got)
+            sf.sf_layer_destroy(lay)
+        prm = oracle_params(oracle, log_n, L, bits, K)
+        want, _, _ = _oracle_layer_run(oracle, prm, case, msg, wsc, delta * wsc, 51, 52, info["k_in"])
+        for o in outs:
+            assert (o == want).all()
+    finally:
+        s.close()
