@@ -110,7 +110,9 @@ void sf_ctx_destroy(sf_ctx *ctx);
 
 /* Tuning and instrumentation knobs (name, value):
  *   "ks_batch"      merges per key-switch batch (1..4096; default chosen per N)
- *   "leaf_chunk"    linear-layer outputs per leaf batch (power of two)
+ *   "leaf_chunk"    cap on the leaves per packing unit (power of two): a group
+ *                   of n leaves is packed as n/CH residue classes of CH leaves
+ *                   reduced to roots, then the roots finish the tree
  *   "mem_budget"    bytes of leaf and pack-tree buffers one round may hold
  *                   (default 64 GiB); larger layers are packed group by group,
  *                   and groups larger than the budget in chunks of leaves
@@ -258,6 +260,30 @@ sf_status sf_eval_linear_layer_host(sf_ctx *ctx, const sf_layer *layer, const sf
                                     const uint64_t *h_in, int32_t k_in, const uint32_t *h_sigma_prev,
                                     const uint32_t *h_sigma_out, uint64_t *h_out, int32_t out_capacity,
                                     int32_t *n_out, void *stream);
+
+/* Several rounds at once (batching of uneven layers): round x evaluates
+ * layers[x] with rks[x] on d_ins[x] (k_ins[x] ciphertexts) into d_outs[x],
+ * exactly as sf_eval_linear_layer would, each result bit-identical to the
+ * single call.  The layers' packing groups of equal size share their
+ * key-switch launches (one batch per tree level across all layers), and the
+ * whole launch sequence is captured once into one CUDA graph and replayed.
+ * h_sigma_prevs / h_sigma_outs may be NULL (no shuffles at all) or hold NULL
+ * entries.  n_outs[x] (may be NULL) receives the packed ciphertexts of round x.
+ * Errors: as sf_eval_linear_layer, for the first offending round. */
+sf_status sf_eval_layers(sf_ctx *ctx, int32_t n_layers, const sf_layer *const *layers, const sf_rotkeys *const *rks,
+                         const uint64_t *const *d_ins, const int32_t *k_ins, const uint32_t *const *h_sigma_prevs,
+                         const uint32_t *const *h_sigma_outs, uint64_t *const *d_outs, const int32_t *out_capacities,
+                         int32_t *n_outs, void *stream);
+
+/* Autotuner: times sf_eval_layers on the given rounds (which it evaluates,
+ * results valid) for each candidate key-switch launch batch (32 ... 512
+ * merges), `repeats` timed runs each after a warm-up, keeps the fastest in
+ * the context ("ks_batch") and reports it with its time in milliseconds.
+ * Synchronises `stream`. */
+sf_status sf_autotune_layers(sf_ctx *ctx, int32_t n_layers, const sf_layer *const *layers, const sf_rotkeys *const *rks,
+                             const uint64_t *const *d_ins, const int32_t *k_ins, const uint32_t *const *h_sigma_prevs,
+                             const uint32_t *const *h_sigma_outs, uint64_t *const *d_outs, const int32_t *out_capacities,
+                             int32_t repeats, int32_t *best_ks_batch, double *best_ms, void *stream);
 
 /* Steps 6-8 only, for selected outputs: d_out[t] = y_{outputs[t]} (the RLWE
  * row of that output before shuffling and packing), coefficient domain,

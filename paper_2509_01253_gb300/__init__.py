@@ -80,6 +80,9 @@ _SIGS = {
     "sf_eval_linear_layer": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _i32, ctypes.POINTER(_i32), _vp]),
     "sf_eval_linear_layer_host": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _i32, ctypes.POINTER(_i32), _vp]),
     "sf_linear_outputs": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp]),
+    "sf_eval_layers": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "sf_autotune_layers": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(_i32),
+                                  ctypes.POINTER(_dbl), _vp]),
     "sf_rotate": (_i32, [_vp, _vp, _i32, _vp, _vp, _i32, _vp]),
     "sf_rotate_noalloc": (_i32, [_vp, _vp, _i32, _vp, _vp, _i32, _vp]),
     "sf_pack": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp]),
@@ -314,6 +317,43 @@ def sf_eval_linear_layer_host(ctx, layer, rk, h_in: np.ndarray, k_in: int, sigma
     _check(lib().sf_eval_linear_layer_host(ctx, layer, rk, _ptr(h_in), k_in, _ptr(sp), _ptr(so), _ptr(h_out),
                                            out_capacity, ctypes.byref(n_out), _stream(stream)))
     return n_out.value
+
+
+def _round_arrays(layers, rks, d_ins, k_ins, sigma_prevs, sigma_outs, d_outs, out_capacities):
+    n = len(layers)
+    VP = ctypes.c_void_p * n
+    keep = []
+    def perms(ps):
+        if ps is None:
+            return None
+        arr = VP()
+        for i, p in enumerate(ps):
+            pp = _perm(p)
+            keep.append(pp)
+            arr[i] = _ptr(pp) if pp is not None else None
+        return arr
+    a = (VP(*layers), VP(*rks), VP(*[_ptr(x) for x in d_ins]), (ctypes.c_int32 * n)(*k_ins), perms(sigma_prevs),
+         perms(sigma_outs), VP(*[_ptr(x) for x in d_outs]), (ctypes.c_int32 * n)(*out_capacities))
+    return a, keep
+
+
+def sf_eval_layers(ctx, layers, rks, d_ins, k_ins, sigma_prevs, sigma_outs, d_outs, out_capacities, stream=None):
+    """Several layer rounds in one captured launch sequence; returns n_outs."""
+    a, keep = _round_arrays(layers, rks, d_ins, k_ins, sigma_prevs, sigma_outs, d_outs, out_capacities)
+    n_outs = (ctypes.c_int32 * len(layers))()
+    _check(lib().sf_eval_layers(ctx, len(layers), *a, n_outs, _stream(stream)))
+    return list(n_outs)
+
+
+def sf_autotune_layers(ctx, layers, rks, d_ins, k_ins, sigma_prevs, sigma_outs, d_outs, out_capacities, repeats=2,
+                       stream=None):
+    """Chooses the key-switch launch batch by timing; returns (ks_batch, ms)."""
+    a, keep = _round_arrays(layers, rks, d_ins, k_ins, sigma_prevs, sigma_outs, d_outs, out_capacities)
+    best = ctypes.c_int32()
+    ms = ctypes.c_double()
+    _check(lib().sf_autotune_layers(ctx, len(layers), *a, repeats, ctypes.byref(best), ctypes.byref(ms),
+                                    _stream(stream)))
+    return best.value, ms.value
 
 
 def sf_linear_outputs(ctx, layer, d_in, k_in: int, sigma_prev, outputs, d_out, stream=None):

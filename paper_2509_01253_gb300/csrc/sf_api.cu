@@ -11,26 +11,7 @@
 #include "sf_internal.h"
 #include "sf_ks.h"
 #include "sf_layer.h"
-
-#define SF_CHECK_CTX(ctx)                                                        \
-    do {                                                                         \
-        if (!(ctx)) return sf_set_error(SF_EINVAL, "%s: null context", __func__); \
-        SF_CUDA_TRY(cudaSetDevice((ctx)->device));                               \
-    } while (0)
-
-static inline size_t ct_words(const sf_ctx *ctx) { return (size_t)2 * ctx->ring.L * ctx->ring.n; }
-static inline size_t align_words(size_t w) { return (w + 31) & ~(size_t)31; }
-
-// Carves consecutive regions out of the context workspace.
-struct Carver {
-    size_t words = 0;
-    size_t take(size_t w)
-    {
-        size_t off = words;
-        words += align_words(w);
-        return off;
-    }
-};
+#include "sf_round.h"
 
 static sf_status device_buffer(void **p, size_t bytes)
 {
@@ -387,14 +368,6 @@ extern "C" void sf_layer_destroy(sf_layer *L)
     delete L;
 }
 
-static void layer_groups(const SfRing &R, int E_out, int *n, int *G)
-{
-    int g = 1;
-    while (g < E_out) g *= 2;
-    *n = std::min(R.n / 2, g);
-    *G = (E_out + *n - 1) / *n;
-}
-
 extern "C" sf_status sf_layer_get_info(const sf_ctx *ctx, const sf_layer *L, sf_layer_info *out)
 {
     if (!ctx || !L || !out) return sf_set_error(SF_EINVAL, "sf_layer_get_info: null argument");
@@ -409,258 +382,6 @@ extern "C" sf_status sf_layer_get_info(const sf_ctx *ctx, const sf_layer *L, sf_
     int lg = 0;
     while ((1 << lg) < n) ++lg;
     out->ks_count = (int64_t)G * ((n - 1) + (R.log_n - lg));
-    return SF_OK;
-}
-
-static sf_status check_perm(const uint32_t *perm, int n, const char *what)
-{
-    std::vector<char> seen(n, 0);
-    for (int k = 0; k < n; ++k) {
-        if (perm[k] >= (uint32_t)n || seen[perm[k]]) return sf_set_error(SF_EINVAL, "%s is not a permutation of [0, %d)", what, n);
-        seen[perm[k]] = 1;
-    }
-    return SF_OK;
-}
-
-static SfLeafParams leaf_params(const sf_layer *L)
-{
-    SfLeafParams P;
-    memset(&P, 0, sizeof(P));
-    size_t off = 0;
-    for (size_t t = 0; t < L->terms.size(); ++t) {
-        const sf_conv_term &T = L->terms[t];
-        P.t[t] = {T.in_offset, T.H, T.W, T.C_in, T.C_out, T.kh, T.kw, T.stride, T.pad, (int)off};
-        off += (size_t)T.C_out * T.kh * T.kw * T.C_in;
-    }
-    P.n_terms = (int)L->terms.size();
-    P.C_out = L->C_out;
-    P.W_out = L->W_out;
-    P.wq = L->d_wq;
-    return P;
-}
-
-// Input ciphertexts -> NTT domain, Montgomery form (for the leaf products).
-static sf_status prepare_inputs(sf_ctx *ctx, const u64 *d_in, int k_in, u64 *ct_mont, cudaStream_t st)
-{
-    const SfRing &R = ctx->ring;
-    std::vector<SfPolyJob> jobs;
-    for (int x = 0; x < k_in * 2 * R.L; ++x) jobs.push_back({d_in + (size_t)x * R.n, ct_mont + (size_t)x * R.n, x % R.L});
-    SF_TRY(sf_ntt_jobs(ctx, jobs.data(), (int)jobs.size(), false, st));
-    SF_TRY(sf_to_mont(ctx, ct_mont, k_in * 2 * R.L, R.L, 0, st));
-    return SF_OK;
-}
-
-static sf_status upload_perm_inverse(const uint32_t *perm, int n, int *d_dst, std::vector<int> &host, cudaStream_t st)
-{
-    host.assign(n, 0);
-    for (int k = 0; k < n; ++k) host[perm[k]] = k;
-    SF_CUDA_TRY(cudaMemcpyAsync(d_dst, host.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
-    return SF_OK;
-}
-
-static int leaf_batch_slots(const SfRing &R, int k_in)
-{
-    size_t per = (size_t)k_in * R.L * R.n * sizeof(u64);
-    size_t slots = ((size_t)256 << 20) / per;
-    return (int)std::max<size_t>(1, std::min<size_t>(slots, 4096));
-}
-
-extern "C" sf_status sf_eval_linear_layer(sf_ctx *ctx, const sf_layer *L, const sf_rotkeys *rk, const uint64_t *d_in,
-                                          int32_t k_in, const uint32_t *h_sigma_prev, const uint32_t *h_sigma_out,
-                                          uint64_t *d_out, int32_t out_capacity, int32_t *n_out, void *stream)
-{
-    SF_CHECK_CTX(ctx);
-    const SfRing &R = ctx->ring;
-    if (!L || !rk || !d_in || !d_out || L->ctx != ctx || rk->ctx != ctx)
-        return sf_set_error(SF_EINVAL, "sf_eval_linear_layer: bad arguments");
-    const int need_k = (L->E_in + R.n - 1) / R.n;
-    if (k_in != need_k) return sf_set_error(SF_EINVAL, "layer needs %d input ciphertexts, got %d", need_k, k_in);
-    int n, G;
-    layer_groups(R, L->E_out, &n, &G);
-    if (out_capacity < G) return sf_set_error(SF_EINVAL, "output capacity %d < %d packed ciphertexts", out_capacity, G);
-    if (h_sigma_prev) SF_TRY(check_perm(h_sigma_prev, L->E_in, "sigma_prev"));
-    if (h_sigma_out) SF_TRY(check_perm(h_sigma_out, L->E_out, "sigma_out"));
-    cudaStream_t st = (cudaStream_t)stream;
-    const size_t ct = ct_words(ctx);
-    const int LB = leaf_batch_slots(R, k_in);
-    const int batch = ctx->ks_batch;
-    // Memory plan: Gc groups at once when their leaf and tree buffers fit the
-    // budget; otherwise one group at a time in chunks of CH leaves (a chunk is
-    // the residue class a mod n/CH, reduced to its root by the first log2 CH
-    // tree levels; the n/CH roots then finish the tree).
-    const size_t ct_bytes = ct * sizeof(u64);
-    const size_t per_group = (size_t)n * ct_bytes + (size_t)std::max(n / 2, 1) * ct_bytes;
-    int Gc = 1, CH = n;
-    if (per_group <= ctx->mem_budget) {
-        Gc = (int)std::max<size_t>(1, std::min<size_t>((size_t)G, ctx->mem_budget / per_group));
-    } else {
-        CH = n;
-        while (CH > 1 && ((size_t)CH * ct_bytes * 3 / 2 + (size_t)(n / CH) * ct_bytes * 3 / 2) > ctx->mem_budget) CH /= 2;
-    }
-    const int nch = n / CH;
-    Carver cv;
-    size_t o_ct = cv.take((size_t)k_in * ct);
-    size_t o_pos = cv.take(((size_t)L->E_in + 1) / 2);
-    size_t o_sig = cv.take(((size_t)L->E_out + 1) / 2);
-    size_t o_w1 = cv.take((size_t)LB * k_in * R.L * R.n);
-    size_t o_A = cv.take((size_t)Gc * CH * ct);
-    size_t o_B = cv.take((size_t)Gc * std::max(CH / 2, 1) * ct);
-    size_t o_RA = cv.take(nch > 1 ? (size_t)nch * ct : 0);
-    size_t o_RB = cv.take(nch > 1 ? (size_t)std::max(nch / 2, 1) * ct : 0);
-    size_t o_ks = cv.take(sf_ks_scratch_words(R) * batch);
-    void *w = nullptr;
-    SF_TRY(sf_scratch(ctx, cv.words * sizeof(u64), &w));
-    u64 *ws = (u64 *)w;
-    u64 *d_ct = ws + o_ct, *d_w1 = ws + o_w1, *A = ws + o_A, *B = ws + o_B, *RA = ws + o_RA, *RB = ws + o_RB,
-        *d_ks = ws + o_ks;
-    int *d_pos = (int *)(ws + o_pos), *d_sig = (int *)(ws + o_sig);
-    std::vector<int> h_pos, h_sig;
-    if (h_sigma_prev) SF_TRY(upload_perm_inverse(h_sigma_prev, L->E_in, d_pos, h_pos, st));
-    if (h_sigma_out) {
-        h_sig.assign(h_sigma_out, h_sigma_out + L->E_out);
-        SF_CUDA_TRY(cudaMemcpyAsync(d_sig, h_sig.data(), sizeof(int) * L->E_out, cudaMemcpyHostToDevice, st));
-    }
-    int log_ch = 0;
-    while ((1 << log_ch) < CH) ++log_ch;
-    // The launch sequence below depends only on pointers and shapes, so it is
-    // captured once into a CUDA graph per (layer, keys, buffers, workspace)
-    // and replayed; with kernel timing on it is launched directly.
-    auto launch_all = [&](cudaStream_t s) -> sf_status {
-        SF_TRY(prepare_inputs(ctx, d_in, k_in, d_ct, s));
-        SfLeafParams P = leaf_params(L);
-        P.k_in = k_in;
-        P.pos_of = h_sigma_prev ? d_pos : nullptr;
-        P.sig_out = h_sigma_out ? d_sig : nullptr;
-        P.ct_mont = d_ct;
-        P.w1 = d_w1;
-        P.n_slots_valid = L->E_out;
-        P.leaf_stride = ct;
-        // leaves for slots s0 + t * stride, t < cnt, into dst
-        auto leaves = [&](int s0, int stride, int cnt, u64 *dst) -> sf_status {
-            for (int t0 = 0; t0 < cnt; t0 += LB) {
-                SfLeafParams p = P;
-                p.s0 = s0 + t0 * stride;
-                p.s_stride = stride;
-                p.leaves = dst + (size_t)t0 * ct;
-                SF_TRY(sf_leaves_launch(ctx, p, std::min(LB, cnt - t0), s));
-            }
-            return SF_OK;
-        };
-        for (int g0 = 0; g0 < G; g0 += Gc) {
-            const int gn = std::min(Gc, G - g0);
-            u64 *res = nullptr;
-            size_t res_stride = 0;
-            if (nch == 1) {
-                // steps 6-9: the real leaves of these groups in slot order (slot = g n + l)
-                const int s_end = std::min((g0 + gn) * n, L->E_out);
-                SF_TRY(leaves(g0 * n, 1, s_end - g0 * n, A));
-                // step 10: pack every group
-                std::vector<int> valid(gn);
-                for (int g = 0; g < gn; ++g) valid[g] = std::min(n, L->E_out - (g0 + g) * n);
-                SF_TRY(sf_pack_tree(ctx, rk->d_keys, rk->d, rk->key_words, A, B, gn, n, 0, valid, true, d_ks, batch,
-                                    &res, &res_stride, s));
-            } else {
-                const int g = g0;
-                const int live = L->E_out - g * n;   // valid slots of this group
-                for (int a = 0; a < nch; ++a) {
-                    const int va = live > a ? std::min(CH, (live - a + nch - 1) / nch) : 0;
-                    if (va == 0) {
-                        SF_CUDA_TRY(cudaMemsetAsync(RA + (size_t)a * ct, 0, ct_bytes, s));
-                        continue;
-                    }
-                    SF_TRY(leaves(g * n + a, nch, CH, A));
-                    u64 *cr = nullptr;
-                    size_t cs = 0;
-                    std::vector<int> v1(1, va);
-                    SF_TRY(sf_pack_tree(ctx, rk->d_keys, rk->d, rk->key_words, A, B, 1, CH, 0, v1, false, d_ks, batch,
-                                        &cr, &cs, s));
-                    SF_CUDA_TRY(cudaMemcpyAsync(RA + (size_t)a * ct, cr, ct_bytes, cudaMemcpyDeviceToDevice, s));
-                }
-                std::vector<int> vr(1, std::min(nch, std::max(live, 0)));
-                SF_TRY(sf_pack_tree(ctx, rk->d_keys, rk->d, rk->key_words, RA, RB, 1, nch, log_ch, vr, true, d_ks,
-                                    batch, &res, &res_stride, s));
-            }
-            std::vector<SfPolyJob> jobs;
-            for (int g = 0; g < gn; ++g)
-                for (int x = 0; x < 2 * R.L; ++x)
-                    jobs.push_back({res + res_stride * g + (size_t)x * R.n, d_out + ct * (g0 + g) + (size_t)x * R.n,
-                                    x % R.L});
-            SF_TRY(sf_ntt_jobs(ctx, jobs.data(), (int)jobs.size(), true, s));
-        }
-        if (L->d_bq) SF_TRY(sf_add_bias(ctx, d_out, G, n, L->E_out, h_sigma_out ? d_sig : nullptr, L->d_bq, L->C_out, s));
-        return SF_OK;
-    };
-    if (!ctx->use_graph || ctx->kernel_timing) {
-        SF_TRY(launch_all(st));
-    } else {
-        uint64_t key[12] = {L->gen, rk->gen, (uint64_t)(uintptr_t)d_in, (uint64_t)(uintptr_t)d_out, (uint64_t)k_in,
-                            (uint64_t)(h_sigma_prev != nullptr), (uint64_t)(h_sigma_out != nullptr),
-                            (uint64_t)(uintptr_t)ws, (uint64_t)batch, (uint64_t)LB, (uint64_t)CH, (uint64_t)Gc};
-        SfGraphEntry *hit = nullptr;
-        for (auto &e : ctx->graphs)
-            if (!memcmp(e.key, key, sizeof(key))) hit = &e;
-        if (!hit) {
-            std::vector<int64_t> before(SFK_COUNT);
-            for (int k = 0; k < SFK_COUNT; ++k) before[k] = ctx->stats[k].launches;
-            cudaStream_t cap;
-            SF_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-            cudaGraph_t graph = nullptr;
-            cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-            sf_status lst = ce == cudaSuccess ? launch_all(cap) : sf_set_error(SF_ECUDA, "stream capture failed");
-            cudaError_t ee = cudaStreamEndCapture(cap, &graph);
-            cudaStreamDestroy(cap);
-            if (lst != SF_OK) {
-                if (graph) cudaGraphDestroy(graph);
-                for (int k = 0; k < SFK_COUNT; ++k) ctx->stats[k].launches = before[k];
-                return lst;
-            }
-            if (ee != cudaSuccess || !graph) return sf_set_error(SF_ECUDA, "graph capture failed: %s", cudaGetErrorString(ee));
-            SfGraphEntry e;
-            memcpy(e.key, key, sizeof(key));
-            cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ie != cudaSuccess) return sf_set_error(SF_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ie));
-            e.launches.resize(SFK_COUNT);
-            for (int k = 0; k < SFK_COUNT; ++k) {
-                e.launches[k] = ctx->stats[k].launches - before[k];
-                ctx->stats[k].launches = before[k];
-            }
-            ctx->graphs.push_back(e);
-            hit = &ctx->graphs.back();
-        }
-        SF_CUDA_TRY(cudaGraphLaunch(hit->exec, st));
-        for (int k = 0; k < SFK_COUNT; ++k) ctx->stats[k].launches += hit->launches[k];
-    }
-    if (n_out) *n_out = G;
-    // the permutation host copies must outlive their async uploads
-    if (!h_pos.empty() || !h_sig.empty()) SF_CUDA_TRY(cudaStreamSynchronize(st));
-    return SF_OK;
-}
-
-extern "C" sf_status sf_eval_linear_layer_host(sf_ctx *ctx, const sf_layer *L, const sf_rotkeys *rk, const uint64_t *h_in,
-                                               int32_t k_in, const uint32_t *h_sigma_prev, const uint32_t *h_sigma_out,
-                                               uint64_t *h_out, int32_t out_capacity, int32_t *n_out, void *stream)
-{
-    SF_CHECK_CTX(ctx);
-    if (!h_in || !h_out || k_in < 1 || out_capacity < 1) return sf_set_error(SF_EINVAL, "sf_eval_linear_layer_host: bad arguments");
-    const size_t ct = ct_words(ctx);
-    cudaStream_t st = (cudaStream_t)stream;
-    static thread_local std::vector<std::pair<sf_ctx *, std::pair<void *, size_t>>> io;
-    void *dbuf = nullptr;
-    size_t need = sizeof(u64) * ct * ((size_t)k_in + out_capacity);
-    for (auto &e : io)
-        if (e.first == ctx && e.second.second >= need) dbuf = e.second.first;
-    if (!dbuf) {
-        SF_TRY(device_buffer(&dbuf, need));
-        io.push_back({ctx, {dbuf, need}});
-    }
-    u64 *d_in = (u64 *)dbuf, *d_out = d_in + ct * k_in;
-    SF_CUDA_TRY(cudaMemcpyAsync(d_in, h_in, sizeof(u64) * ct * k_in, cudaMemcpyHostToDevice, st));
-    int32_t got = 0;
-    SF_TRY(sf_eval_linear_layer(ctx, L, rk, d_in, k_in, h_sigma_prev, h_sigma_out, d_out, out_capacity, &got, stream));
-    SF_CUDA_TRY(cudaMemcpyAsync(h_out, d_out, sizeof(u64) * ct * got, cudaMemcpyDeviceToHost, st));
-    SF_CUDA_TRY(cudaStreamSynchronize(st));
-    if (n_out) *n_out = got;
     return SF_OK;
 }
 

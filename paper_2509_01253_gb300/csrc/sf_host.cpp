@@ -452,6 +452,8 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     ctx->scratch = nullptr;
     ctx->scratch_bytes = 0;
+    ctx->io_buf = nullptr;
+    ctx->io_bytes = 0;
     ctx->ks_batch = p->log_n >= 15 ? 64 : 128;
     ctx->leaf_chunk = 1 << 30;
     ctx->mem_budget = (size_t)64 << 30;
@@ -622,6 +624,7 @@ extern "C" void sf_ctx_destroy(sf_ctx *ctx)
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     for (void *d : ctx->owned) cudaFree(d);
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->io_buf) cudaFree(ctx->io_buf);
     delete ctx;
 }
 
@@ -635,6 +638,7 @@ extern "C" sf_status sf_ctx_set_option(sf_ctx *ctx, const char *name, int64_t va
     } else if (!strcmp(name, "leaf_chunk")) {
         if (value < 1 || (value & (value - 1))) return sf_set_error(SF_EINVAL, "leaf_chunk must be a power of two");
         ctx->leaf_chunk = (int)std::min<int64_t>(value, 1 << 30);
+        sf_graph_cache_clear(ctx);
     } else if (!strcmp(name, "mem_budget")) {
         if (value < (1 << 20)) return sf_set_error(SF_EINVAL, "mem_budget must be at least 1 MiB");
         ctx->mem_budget = (size_t)value;

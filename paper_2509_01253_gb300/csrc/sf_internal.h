@@ -79,6 +79,9 @@ struct sf_ctx {
     // scratch pool
     void *scratch;
     size_t scratch_bytes;
+    // device staging for the host-buffer round
+    void *io_buf;
+    size_t io_bytes;
     // options
     int ks_batch;
     int leaf_chunk;

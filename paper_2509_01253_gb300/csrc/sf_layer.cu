@@ -182,8 +182,6 @@ sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int3
     const int level1 = level0 + levels;
     u64 *cur = A, *nxt = B;
     size_t cur_gs = (size_t)n_nodes * ct, nxt_gs = (size_t)(n_nodes / 2 > 0 ? n_nodes / 2 : 1) * ct;
-    int full = 0;
-    while (full < G && valid[full] >= n_nodes) ++full;   // leading full groups
     for (int lvl = level0 + 1; lvl <= level1; ++lvl) {
         const int half = n_nodes >> (lvl - level0);
         const int d = (1 << lvl) + 1;
@@ -201,16 +199,22 @@ sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int3
         kb.s = (unsigned)(R.n >> lvl);
         kb.add_v = 1;
         kb.key = key;
-        if (full > 0) {
-            SfKsBatch b = kb;
-            b.E = cur;
-            b.O = cur + (size_t)half * ct;
-            b.out = nxt;
-            b.inner = half;
-            b.count = full * half;
-            SF_TRY(sf_ks_run(ctx, b, ks_scratch, batch, st));
-        }
-        for (int gi = full; gi < G; ++gi) {
+        int gi = 0;
+        while (gi < G) {
+            if (valid[gi] >= n_nodes) {
+                // a run of full groups: one batch with (group, merge) indexing
+                int g1 = gi;
+                while (g1 < G && valid[g1] >= n_nodes) ++g1;
+                SfKsBatch b = kb;
+                b.E = cur + gi * cur_gs;
+                b.O = b.E + (size_t)half * ct;
+                b.out = nxt + gi * nxt_gs;
+                b.inner = half;
+                b.count = (g1 - gi) * half;
+                SF_TRY(sf_ks_run(ctx, b, ks_scratch, batch, st));
+                gi = g1;
+                continue;
+            }
             const int V = std::min(valid[gi], 2 * half);
             const int active = std::min(V, half);
             const int with_o = std::max(0, std::min(active, V - half));
@@ -231,6 +235,7 @@ sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int3
                 b2.count = active - with_o;
                 SF_TRY(sf_ks_run(ctx, b2, ks_scratch, batch, st));
             }
+            ++gi;
         }
         std::swap(cur, nxt);
         std::swap(cur_gs, nxt_gs);

@@ -394,3 +394,49 @@ def test_memory_budget_chunking_is_exact(oracle):
             assert (o == want).all()
     finally:
         s.close()
+
+
+def _batch_cases():
+    return [wl.small_conv_case(11, 8, 8, 8, 8), wl.small_conv_case(12, 10, 10, 6, 7),
+            wl.fc_case(13, 300, 37, bias=True), wl.small_conv_case(14, 14, 14, 8, 6, stride=2, shortcut=True, bias=True)]
+
+
+def test_eval_layers_batch_matches_single_rounds():
+    """Batching of uneven layers: four rounds of different sizes (one and two
+    packing groups, an FC with bias, a strided shortcut over k_in = 3 inputs)
+    evaluated in one call give residues identical to the four single calls,
+    also when a small memory budget splits groups into units of leaves whose
+    roots are packed in a separate pass."""
+    log_n, L, bits, K = 11, 3, 50, 1
+    s = Session(log_n, L, bits, K, sk_seed=81, rk_seed=82)
+    try:
+        delta = wsc = 2.0 ** 20
+        cases = _batch_cases()
+        lays, infos, ins, single = [], [], [], []
+        for c in cases:
+            lay, info, msg, d_in, got = _run_layer(s, c, delta, delta * wsc, wsc)
+            lays.append(lay)
+            infos.append(info)
+            ins.append(d_in)
+            single.append(got)
+        for budget in (None, 6 << 20):
+            if budget:
+                sf.sf_ctx_set_option(s.ctx, "mem_budget", budget)
+            outs = [dev_zeros(i["n_groups"], 2, L, s.n) for i in infos]
+            n_outs = sf.sf_eval_layers(s.ctx, lays, [s.rk] * len(lays), ins, [i["k_in"] for i in infos],
+                                       [c.sigma_prev for c in cases], [c.sigma_out for c in cases], outs,
+                                       [i["n_groups"] for i in infos])
+            sf.sf_sync(s.ctx)
+            assert n_outs == [i["n_groups"] for i in infos]
+            for o, want in zip(outs, single):
+                assert (from_dev(o) == want).all()
+        best, ms = sf.sf_autotune_layers(s.ctx, lays, [s.rk] * len(lays), ins, [i["k_in"] for i in infos],
+                                         [c.sigma_prev for c in cases], [c.sigma_out for c in cases], outs,
+                                         [i["n_groups"] for i in infos], repeats=1)
+        assert best in (32, 64, 128, 256, 512) and ms > 0
+        for o, want in zip(outs, single):
+            assert (from_dev(o) == want).all()
+        for lay in lays:
+            sf.sf_layer_destroy(lay)
+    finally:
+        s.close()
