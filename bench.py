@@ -8,6 +8,15 @@ the output shuffle; 16384 leaf products, 16382 pack-tree merges and 2 trace
 steps (16384 automorphism + hybrid key switches), 2 packed output ciphertexts.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload conv16|resnet18|resnet34|serve]
+
+The default workload (conv16) prints the one-line benchmark record.  The
+other workloads are the network-scale measurements, each one JSON line:
+resnet18 (all 18 layer rounds of a ResNet-18 on 3x64x64 at N = 2^15, each
+with its own synthetic input: one sf_eval_layers batch vs one call per
+layer), resnet34 (every round of a ResNet-34 on 3x224x224 at N = 2^16, per
+layer and end to end) and serve (Poisson arrivals of encrypted ResNet-20 /
+ResNet-18 requests through the continuous-batching server).
 
 --impl reference times the CPU oracle (the plain schoolbook implementation
 under oracle/) on the host cores, on a bounded sample of the same workload
@@ -45,6 +54,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="conv16", choices=["conv16", "resnet18", "resnet34", "serve"])
+    ap.add_argument("--rates", default="5,20,200", help="serve: arrival rates (requests/s)")
+    ap.add_argument("--duration", type=float, default=20.0, help="serve: arrival window per rate (s)")
+    ap.add_argument("--drain", type=float, default=60.0, help="serve: time allowed after the window (s)")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: the same conv kernel shapes on 8x16x16 (2048 outputs, ~2 GB on device)")
     return ap.parse_args()
@@ -164,30 +177,51 @@ def launches(sf, ctx) -> dict:
 
 # ------------------------------------------------------------ roofline ----
 
-def algorithmic_bytes(kernel: str, info: dict, n: int, L: int, K: int, dnum: int, launches_per_layer: int) -> float:
-    """Algorithmic HBM bytes per launch for the key-switch kernels: every
-    merge must read its pair of ciphertexts (2 x [2][L][N] words), write one
-    ciphertext, and read the rotation key once per launch batch; per the
-    5-kernel pipeline, each kernel's share is its own unavoidable operands."""
-    w = 8
-    ct = 2 * L * n * w
-    nm = L + K
-    merges = info["ks_count"]
-    per_merge = {
-        # gather u.a (E, O: L limbs each) -> write partial iNTT (L limbs)
-        "ks1_gather_inv_row": (2 * L + L) * n * w,
-        # read partial (L limbs), write digit extensions dnum*(nm - K) limbs
-        "ks2_modup_col": (L + dnum * (nm - 1)) * n * w,
-        # read extensions + own limbs, key 2*dnum*nm limbs, write 2*nm accumulators
-        "ks3_inner_row": (dnum * nm + 2 * dnum * nm + 2 * nm) * n * w,
-        # read 2K P-limbs, write 2L converted limbs
-        "ks4_moddown_col": (2 * K + 2 * L) * n * w,
-        # read 2L converted + 2L accumulators + E, O, write the merged ciphertext
-        "ks5_finish_row": (4 * L) * n * w + 3 * ct,
+class RingShape:
+    """Sizes the work model needs: N = R x C split, moduli counts, digits."""
+
+    def __init__(self, p_info: dict):
+        self.n = p_info["n"]
+        self.L, self.K, self.dnum = p_info["n_data"], p_info["n_special"], p_info["dnum"]
+        self.nm = self.L + self.K
+        log_n = self.n.bit_length() - 1
+        self.lc = (log_n + 1) // 2
+        self.lr = log_n - self.lc
+        self.digits = [min(self.K, self.L - j * self.K) for j in range(self.dnum)]
+
+
+def kernel_work(kernel: str, g: RingShape, k_in: int = 1):
+    """Algorithmic work of one item of a kernel: (HBM bytes, modular
+    multiplications).  Items are merges (key switches) for the ks* kernels,
+    (output, input ciphertext) pairs for leaf_col and outputs for leaf_row.
+    Bytes are the operands that must cross HBM in the kernel's stage of the
+    pipeline (one read of each input limb, one write of each output limb,
+    8-byte words; the rotation key is read once per launch and not counted
+    per item); a modular multiplication is one butterfly, one
+    multiply-accumulate or one base-conversion product."""
+    N, L, K, nm, dnum, lr, lc, w = g.n, g.L, g.K, g.nm, g.dnum, g.lr, g.lc, 8
+    half = N // 2
+    fbc_up = sum(d * (nm - d) for d in g.digits) * N
+    table = {
+        "ks_gather": (3 * L * N * w, L * N),
+        "ks1_inv_row": (2 * L * N * w, L * half * lc),
+        "ks2_modup_col": (dnum * nm * N * w, L * half * lr + L * N + fbc_up + (dnum * nm - L) * half * lr),
+        "ks3_inner_row": ((dnum * nm + 2 * nm) * N * w, (dnum * nm - L) * half * lc + 2 * dnum * nm * N),
+        "ks3_inv_row_p": (4 * K * N * w, 2 * K * half * lc),
+        "ks4_moddown_col": ((2 * K + 2 * L) * N * w, 2 * K * half * lr + 2 * K * N + 2 * K * L * N + 2 * L * half * lr),
+        "ks5_finish_row": (6 * L * N * w, 2 * L * half * lc + 2 * L * N),
+        "ks_merge": (8 * L * N * w, 2 * L * N),
+        "leaf_col": (L * N * w, L * half * lr),
+        "leaf_row": ((k_in * L + 2 * L) * N * w, k_in * L * half * lc + 2 * k_in * L * N),
     }
-    if kernel not in per_merge:
-        return 0.0
-    return per_merge[kernel] * merges / launches_per_layer
+    return table.get(kernel)
+
+
+def alu_peak(sm_count: int, sm_mhz: float):
+    """Modular-multiplication peak from unit counts and clock: 64 32-bit
+    integer multiply-adds per clock per SM, and 10 of them per 64-bit Shoup
+    product (3 for each of the two low 64-bit products, 4 for the high one)."""
+    return sm_count * 64 * sm_mhz * 1e6 / 10.0
 
 
 def load_peaks():
@@ -198,6 +232,62 @@ def load_peaks():
         return d.get("hbm_gbs"), "measured"
     except (OSError, ValueError):
         return 6800.0, "fallback"
+
+
+# per-item DRAM bytes (read + write) from the ncu capture named in the
+# profiles folder, for kernels whose code has not changed since; else None
+TRAFFIC_PER_ITEM = {}
+
+
+def items_per_layer(kernel: str, info: dict, merges: int) -> int:
+    if kernel.startswith("ks"):
+        return merges
+    if kernel == "leaf_col":
+        return info["E_out"] * info["k_in"]
+    if kernel == "leaf_row":
+        return info["E_out"]
+    return 0
+
+
+def roofline_of(kstats: dict, k_steps: int, g: RingShape, info: dict, total_kernel_ms: float, clk: dict,
+                merges: int = None):
+    """Roofline record of the kernel with the largest device-time share:
+    algorithmic work per layer / its measured time per layer, against the
+    measured HBM copy bandwidth and the derived modular-multiplication peak;
+    `bound` is the one whose time at peak is larger."""
+    merges = info["ks_count"] if merges is None else merges
+    top = max((k for k in kstats if kernel_work(k, g, info["k_in"])), key=lambda k: kstats[k][1])
+    cnt, ms = kstats[top]
+    per_layer_s = ms / k_steps / 1e3
+    items = items_per_layer(top, info, merges)
+    b_item, m_item = kernel_work(top, g, info["k_in"])
+    hbm_peak, peak_kind = load_peaks()
+    alu_pk = alu_peak(152, 2070.0)
+    hbm_ach = b_item * items / per_layer_s / 1e9
+    alu_ach = m_item * items / per_layer_s / 1e9
+    t_hbm = b_item / (hbm_peak * 1e9)
+    t_alu = m_item / alu_pk
+    bound = "alu" if t_alu >= t_hbm else "hbm"
+    launches = cnt // k_steps
+    traffic = TRAFFIC_PER_ITEM.get(top)
+    rec = {"bound": bound, "kernel": top,
+           "achieved": alu_ach if bound == "alu" else hbm_ach,
+           "peak": alu_pk / 1e9 if bound == "alu" else hbm_peak,
+           "unit": "Gmodmul/s" if bound == "alu" else "GB/s"}
+    rec["frac"] = rec["achieved"] / rec["peak"]
+    rec["traffic"] = traffic * items / launches if traffic else None
+    rec.update({
+        "peak_source": ("derived: 152 SMs x 64 int32 multiply-adds/clk x 2070 MHz / 10 per 64-bit modmul"
+                        if bound == "alu" else f"{peak_kind} hbm_gbs"),
+        "hbm_view": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
+                     "peak_source": peak_kind},
+        "alu_view": {"achieved": alu_ach, "peak": alu_pk / 1e9, "unit": "Gmodmul/s", "frac": alu_ach * 1e9 / alu_pk,
+                     "at_median_clock": (alu_ach * 1e9 / alu_peak(152, clk["sm_mhz"])) if clk.get("sm_mhz") else None},
+        "algorithmic_bytes_per_launch": b_item * items / launches,
+        "algorithmic_modmul_per_launch": m_item * items / launches,
+        "avg_launch_us": per_layer_s / launches * 1e6, "launches_per_layer": launches,
+        "share_of_device_time": ms / total_kernel_ms if total_kernel_ms else None})
+    return rec
 
 
 # ------------------------------------------------------- CPU baseline ----
@@ -282,11 +372,158 @@ def run_reference(args, dist, ws, rank):
     return 0
 
 
+# ----------------------------------------------------- network workloads ----
+
+NET_PARAMS = {"resnet18": "r18", "resnet34": "r34", "resnet20": "conv16"}
+
+
+class NetworkWorkload:
+    """Every round of a network, each with its own seeded synthetic input
+    (U(0, 1), a post-ReLU activation), input and output permutations drawn
+    from the session seed (none before the first and after the last round),
+    encrypted and resident on the device."""
+
+    def __init__(self, kind: str, device: int, seed: int):
+        import torch
+        import paper_2509_01253_gb300 as sf
+        from paper_2509_01253_gb300 import network as nw
+        from paper_2509_01253_gb300 import workloads as wl
+        self.sf, self.torch = sf, torch
+        self.kind = kind
+        self.ps = ps = wl.PARAMS[NET_PARAMS[kind]]
+        self.params = sf.sf_params_create(ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits, ps.sigma)
+        self.ctx = sf.sf_ctx_create(self.params, device)
+        self.sk = sf.sf_keygen(self.ctx, seed + 3)
+        self.rk = sf.sf_gen_rotation_keys(self.ctx, self.sk, None, seed + 5)
+        self.net = nw.EncodedNetwork(self.params, self.ctx, ps, wl.resnet_rounds(kind))
+        self.n, self.L = 1 << ps.log_n, ps.n_data
+        dev = f"cuda:{device}"
+        self.stream = torch.cuda.current_stream(device)
+        self.d_ins, self.d_outs, self.sps, self.sos, self.k_ins, self.caps = [], [], [], [], [], []
+        last = len(self.net.rounds) - 1
+        for r, info in enumerate(self.net.infos):
+            x = np.random.default_rng(seed + 100 + r).uniform(0.0, 1.0, info["E_in"])
+            sp = None if r == 0 else sf.sf_permutation(seed + 4, r, info["E_in"])
+            so = None if r == last else sf.sf_permutation(seed + 4, r + 1, info["E_out"])
+            xs = x if sp is None else x[sp.astype(np.int64)]
+            d_in = torch.empty((info["k_in"], 2, self.L, self.n), dtype=torch.int64, device=dev)
+            sf.sf_encrypt(self.ctx, self.sk, sf.sf_encode_input(xs, ps.delta), seed + 1000 + r, d_in, info["k_in"])
+            self.d_ins.append(d_in)
+            self.d_outs.append(torch.empty((info["n_groups"], 2, self.L, self.n), dtype=torch.int64, device=dev))
+            self.sps.append(sp)
+            self.sos.append(so)
+            self.k_ins.append(info["k_in"])
+            self.caps.append(info["n_groups"])
+        self.ct_bytes = 2 * self.L * self.n * 8
+
+    def per_layer(self, r: int):
+        self.sf.sf_eval_linear_layer(self.ctx, self.net.layers[r], self.rk, self.d_ins[r], self.k_ins[r], self.sps[r],
+                                     self.sos[r], self.d_outs[r], self.caps[r], self.stream)
+
+    def batched(self, idx=None):
+        idx = list(range(len(self.net.rounds))) if idx is None else idx
+        return self.sf.sf_eval_layers(self.ctx, [self.net.layers[r] for r in idx], [self.rk] * len(idx),
+                                      [self.d_ins[r] for r in idx], [self.k_ins[r] for r in idx],
+                                      [self.sps[r] for r in idx], [self.sos[r] for r in idx],
+                                      [self.d_outs[r] for r in idx], [self.caps[r] for r in idx], self.stream)
+
+    def autotune(self, idx):
+        return self.sf.sf_autotune_layers(self.ctx, [self.net.layers[r] for r in idx], [self.rk] * len(idx),
+                                          [self.d_ins[r] for r in idx], [self.k_ins[r] for r in idx],
+                                          [self.sps[r] for r in idx], [self.sos[r] for r in idx],
+                                          [self.d_outs[r] for r in idx], [self.caps[r] for r in idx], 1, self.stream)
+
+    def max_err(self, rounds) -> float:
+        """Max |decoded - float64| over every output of the given rounds."""
+        from paper_2509_01253_gb300 import network as nw
+        sf = self.sf
+        worst = 0.0
+        for r in rounds:
+            info = self.net.infos[r]
+            res = np.zeros((info["n_groups"], self.L, self.n), dtype=np.uint64)
+            sf.sf_decrypt(self.ctx, self.sk, self.d_outs[r], info["n_groups"], res, self.stream)
+            vals = nw.decode_outputs(self.net, r, res)
+            x = np.random.default_rng(self._seed + 100 + r).uniform(0.0, 1.0, info["E_in"])
+            ref = nw.round_float_reference(self.net, r, x)
+            if self.sos[r] is not None:
+                ref = ref[self.sos[r].astype(np.int64)]
+            worst = max(worst, float(np.abs(vals - ref).max()))
+        return worst
+
+
+def timed(torch, stream, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_network(args, local: int) -> int:
+    """One JSON line: the network's rounds as one batched sf_eval_layers call
+    (after autotuning the key-switch batch on the three smallest rounds) and
+    as one sf_eval_linear_layer call per round, with per-round times."""
+    import torch
+    torch.cuda.set_device(local)
+    seed = 300 if args.workload == "resnet18" else 400
+    nw_ = NetworkWorkload(args.workload, local, seed)
+    nw_._seed = seed
+    torch_ = torch
+    sf = nw_.sf
+    R = len(nw_.net.rounds)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
+    clocks = ClockSampler(local)
+    clocks.start()
+    rec = {"metric": METRIC, "unit": UNIT, "workload": args.workload, "rounds": R,
+           "ks_total": nw_.net.total_ks(), "outputs_total": sum(i["E_out"] for i in nw_.net.infos),
+           "n": nw_.n, "L": nw_.L, "data": "synthetic: per-round inputs U(0,1), Kaiming-uniform weights"}
+    # one call per round (each round captured in its own graph on first use)
+    per_round = [0.0] * R
+    for rep in range(2):           # 0: warm-up (captures), 1: timed
+        for r in range(R):
+            flush_l2(flush)
+            t = timed(torch_, nw_.stream, lambda: nw_.per_layer(r))
+            if rep == 1:
+                per_round[r] = t
+    rec["per_layer_ms"] = {nw_.net.rounds[r].name: per_round[r] for r in range(R)}
+    rec["per_layer_form"] = {"total_ms": sum(per_round), "layers_per_s": R / (sum(per_round) / 1e3),
+                             "ks_batch": "default"}
+    err = nw_.max_err(range(R)) if args.workload == "resnet18" else nw_.max_err([R - 1, R - 2])
+    # autotune the launch batch on the smallest rounds, then the whole network as one batch
+    small = sorted(range(R), key=lambda r: nw_.net.infos[r]["E_out"])[:3]
+    best, best_ms = nw_.autotune(small)
+    rec["autotune"] = {"rounds": [nw_.net.rounds[r].name for r in small], "ks_batch": best, "ms": best_ms}
+    flush_l2(flush)
+    timed(torch_, nw_.stream, nw_.batched)        # capture + run
+    t_b = []
+    for _ in range(max(1, min(args.steps, 2))):
+        flush_l2(flush)
+        t_b.append(timed(torch_, nw_.stream, nw_.batched))
+    tb = min(t_b)
+    rec["batched_form"] = {"total_ms": tb, "layers_per_s": R / (tb / 1e3), "ks_batch": best,
+                           "calls": 1, "timed_runs": len(t_b)}
+    err_b = nw_.max_err(range(R)) if args.workload == "resnet18" else nw_.max_err([R - 1, R - 2])
+    rec["value"] = R / (tb / 1e3)
+    rec["speedup_batched_vs_per_layer"] = sum(per_round) / tb
+    rec["max_abs_err"] = {"per_layer": err, "batched": err_b,
+                          "rounds_checked": "all" if args.workload == "resnet18" else "last two"}
+    rec["clocks"] = clocks.stop()
+    print(json.dumps(rec), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     dist, ws, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, dist, ws, rank)
+    if args.workload in ("resnet18", "resnet34"):
+        return run_network(args, local) if rank == 0 else 0
+    if args.workload == "serve":
+        from paper_2509_01253_gb300 import serve
+        return serve.bench(args, local) if rank == 0 else 0
     import torch
     import paper_2509_01253_gb300 as sf
     torch.cuda.set_device(local)
@@ -363,18 +600,8 @@ def main():
     kstats = launches(sf, wl_.ctx)
     sf.sf_ctx_set_option(wl_.ctx, "kernel_timing", 0)
     total_kernel_ms = sum(ms for _, ms in kstats.values())
-    top = max(kstats, key=lambda k: kstats[k][1])
-    cnt, ms = kstats[top]
-    per_layer = cnt // k_steps
     p_info = sf.sf_params_get_info(wl_.params)
-    alg = algorithmic_bytes(top, wl_.info, wl_.n, wl_.L, p_info["n_special"], p_info["dnum"], per_layer)
-    avg_s = ms / cnt / 1e3
-    peak, peak_kind = load_peaks()
-    achieved = alg / avg_s / 1e9 if alg else None
-    roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "peak_source": peak_kind, "avg_launch_us": avg_s * 1e6, "launches_per_layer": per_layer,
-                "share_of_device_time": ms / total_kernel_ms if total_kernel_ms else None}
+    roofline = roofline_of(kstats, k_steps, RingShape(p_info), wl_.info, total_kernel_ms, clk)
     kernel_table = {k: {"launches_per_layer": c // k_steps, "ms_per_layer": m / k_steps} for k, (c, m) in kstats.items() if c}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,

@@ -302,7 +302,8 @@ extern "C" sf_status sf_decode(const sf_params *p, const uint64_t *res, int32_t 
 
 static const char *k_names[SFK_COUNT] = {
     "ntt_fwd_col", "ntt_fwd_row", "ntt_inv_row", "ntt_inv_col", "elementwise",
-    "ks1_gather_inv_row", "ks2_modup_col", "ks3_inner_row", "ks4_moddown_col", "ks5_finish_row",
+    "ks_gather", "ks1_inv_row", "ks2_modup_col", "ks3_inner_row", "ks3_inv_row_p", "ks4_moddown_col",
+    "ks5_finish_row", "ks_merge",
     "leaf_col", "leaf_row", "shuffle"};
 
 const char *sf_kernel_name(int kind) { return (kind >= 0 && kind < SFK_COUNT) ? k_names[kind] : "?"; }

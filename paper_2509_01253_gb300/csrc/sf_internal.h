@@ -170,11 +170,14 @@ enum SfKernelKind {
     SFK_NTT_INV_ROW,
     SFK_NTT_INV_COL,
     SFK_ELEMWISE,
-    SFK_KS1_GATHER_INV_ROW,
+    SFK_KS_GATHER,
+    SFK_KS1_INV_ROW,
     SFK_KS2_MODUP_COL,
     SFK_KS3_INNER_ROW,
+    SFK_KS3_INV_ROW_P,
     SFK_KS4_MODDOWN_COL,
     SFK_KS5_FINISH_ROW,
+    SFK_KS_MERGE,
     SFK_LEAF_COL,
     SFK_LEAF_ROW,
     SFK_SHUFFLE,

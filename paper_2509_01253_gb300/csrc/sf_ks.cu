@@ -489,15 +489,17 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
         b.scratch += sf_ks_scratch_words(R) * off;
         const dim3 eg(R.n / 256, R.L, b.count), mg(R.n / 256, 2 * R.L, b.count);
 
-        sf_launch_begin(ctx, SFK_KS1_GATHER_INV_ROW, st, &ev);
+        sf_launch_begin(ctx, SFK_KS_GATHER, st, &ev);
         k_ks_gather<<<eg, 256, 0, st>>>(R, b);
+        sf_launch_end(ctx, SFK_KS_GATHER, st, ev);
+        sf_launch_begin(ctx, SFK_KS1_INV_ROW, st, &ev);
         {
             const SfRowSet S{0, (size_t)R.L << R.log_n, R.L, 0, R.L};   // TA -> X1
             const int ng = rtiles * S.npoly;
             const int bpg = blocks_per_group(ctx, occupancy(k_rows<true>, sm_rows), ng, b.count);
             k_rows<true><<<ng * bpg, SF_THREADS, sm_rows, st>>>(R, b, S, bpg);
         }
-        sf_launch_end(ctx, SFK_KS1_GATHER_INV_ROW, st, ev);
+        sf_launch_end(ctx, SFK_KS1_INV_ROW, st, ev);
 
         sf_launch_begin(ctx, SFK_KS2_MODUP_COL, st, &ev);
         {
@@ -521,13 +523,17 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
 #undef SF_KS3_CASE
             default: return sf_set_error(SF_EINVAL, "unsupported ring split");
             }
+        }
+        sf_launch_end(ctx, SFK_KS3_INNER_ROW, st, ev);
+        sf_launch_begin(ctx, SFK_KS3_INV_ROW_P, st, &ev);
+        {
             // inverse row pass of the special limbs' accumulators, in place in x1
             const SfRowSet S{(size_t)R.L << R.log_n, (size_t)R.L << R.log_n, 2 * R.K, R.L, R.K};
             const int ng2 = rtiles * S.npoly;
             const int bpg2 = blocks_per_group(ctx, occupancy(k_rows<true>, sm_rows), ng2, b.count);
             k_rows<true><<<ng2 * bpg2, SF_THREADS, sm_rows, st>>>(R, b, S, bpg2);
         }
-        sf_launch_end(ctx, SFK_KS3_INNER_ROW, st, ev);
+        sf_launch_end(ctx, SFK_KS3_INV_ROW_P, st, ev);
 
         sf_launch_begin(ctx, SFK_KS4_MODDOWN_COL, st, &ev);
         {
@@ -542,9 +548,11 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
             const int ng = rtiles * R.L;
             const int bpg = blocks_per_group(ctx, occupancy(k_ks5, sm5), ng, 2 * b.count);
             k_ks5<<<ng * bpg, SF_THREADS, sm5, st>>>(R, b, bpg);
-            k_ks_merge<<<mg, 256, 0, st>>>(R, b);
         }
         sf_launch_end(ctx, SFK_KS5_FINISH_ROW, st, ev);
+        sf_launch_begin(ctx, SFK_KS_MERGE, st, &ev);
+        k_ks_merge<<<mg, 256, 0, st>>>(R, b);
+        sf_launch_end(ctx, SFK_KS_MERGE, st, ev);
     }
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;

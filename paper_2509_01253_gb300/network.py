@@ -1,0 +1,189 @@
+"""Encrypted inference over a network's rounds (Sec. 4.4 protocol, t = 2,
+gamma = 0), driven through the C ABI.
+
+The server side of every round is one ``sf_eval_linear_layer`` job (or one
+job inside an ``sf_eval_layers`` batch).  Between rounds a simulated client
+decrypts the packed outputs, applies ReLU (order-agnostic, so it works on the
+shuffled values), re-encodes at the input scale and encrypts the next round's
+input in the order the server's output permutation left it (Sec. 4.3,
+Sec. 4.5).  A round may read several earlier activations (the block input of
+a residual connection): the client concatenates them, and the round's input
+permutation is the concatenation of theirs.
+
+Everything here is host-side orchestration: all arithmetic on ciphertexts
+runs in the CUDA library; encryption randomness is drawn by the library from
+the seeds given here.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import paper_2509_01253_gb300 as sf
+from paper_2509_01253_gb300 import workloads as wl
+
+
+def _mix(*xs) -> int:
+    """SplitMix64-style finaliser over a tuple of ints (seed derivation)."""
+    h = 0x243F6A8885A308D3
+    for x in xs:
+        h = (h ^ (int(x) & 0xFFFFFFFFFFFFFFFF)) * 0x9E3779B97F4A7C15 & 0xFFFFFFFFFFFFFFFF
+        h ^= h >> 31
+        h = (h * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+        h ^= h >> 29
+    return h
+
+
+class EncodedNetwork:
+    """The rounds of one network with their quantised weights resident on a context."""
+
+    def __init__(self, params, ctx, ps: wl.ParamSet, rounds: list, integer: bool = False):
+        self.params, self.ctx, self.ps, self.rounds = params, ctx, ps, rounds
+        self.n = 1 << ps.log_n
+        self.layers, self.infos, self.weights = [], [], []
+        for spec in rounds:
+            ws = wl.round_weights(spec, integer)
+            W = np.concatenate([w.ravel() for w in ws])
+            lay = sf.sf_encode_weights(ctx, spec.terms, W, None, ps.delta, ps.delta ** 2)
+            self.layers.append(lay)
+            self.infos.append(sf.sf_layer_get_info(ctx, lay))
+            self.weights.append(ws)
+
+    def destroy(self):
+        for lay in self.layers:
+            sf.sf_layer_destroy(lay)
+        self.layers = []
+
+    def max_cts(self) -> int:
+        """Largest input + output ciphertext count over the rounds."""
+        return max(i["k_in"] + i["n_groups"] for i in self.infos)
+
+    def total_ks(self) -> int:
+        return sum(i["ks_count"] for i in self.infos)
+
+
+class ClientState:
+    """One request's client: its plaintext activations (in the order the
+    server's permutation left them) and its session seed.
+
+    acts[name] = (values, perm): values[p] is the activation of original
+    index perm[p] (perm None = identity order)."""
+
+    def __init__(self, net: EncodedNetwork, x: np.ndarray, session_seed: int, request_seed: int):
+        self.net = net
+        self.session_seed = session_seed
+        self.request_seed = request_seed
+        self.acts = {"x": (np.asarray(x, dtype=np.float64), None)}
+        self.round = 0
+        self.trace = []          # per round: (input values in original order, decoded outputs in original order)
+
+    @property
+    def done(self) -> bool:
+        return self.round >= len(self.net.rounds)
+
+    def sigma_out(self, r: int):
+        """Output permutation of round r: a fresh one per round from the session
+        seed, none for the last round (its outputs go to the client in order)."""
+        if r == len(self.net.rounds) - 1:
+            return None
+        E = self.net.infos[r]["E_out"]
+        return sf.sf_permutation(self.session_seed, r + 1, E)
+
+    def round_input(self, r: int):
+        """(stream values, sigma_prev or None) of round r's input."""
+        spec = self.net.rounds[r]
+        vals, perms, off, any_perm = [], [], 0, False
+        for name in spec.inputs:
+            v, p = self.acts[name]
+            vals.append(v)
+            perms.append((np.arange(len(v), dtype=np.int64) if p is None else p.astype(np.int64)) + off)
+            any_perm |= p is not None
+            off += len(v)
+        stream = np.concatenate(vals)
+        sigma = np.concatenate(perms).astype(np.uint32) if any_perm else None
+        return stream, sigma
+
+    def original_order(self, stream: np.ndarray, sigma) -> np.ndarray:
+        if sigma is None:
+            return stream.copy()
+        out = np.empty_like(stream)
+        out[sigma.astype(np.int64)] = stream
+        return out
+
+    def encode(self, r: int):
+        """Quantised message (int64, stream order) and sigma_prev of round r."""
+        stream, sigma = self.round_input(r)
+        return sf.sf_encode_input(stream, self.net.ps.delta), sigma, stream
+
+    def encrypt_seed(self, r: int) -> int:
+        return _mix(self.request_seed, r, 0xE)
+
+    def absorb(self, r: int, values: np.ndarray, sigma_out, stream_in=None, sigma_in=None):
+        """Store round r's decoded outputs (slot order) as the activation it names."""
+        spec = self.net.rounds[r]
+        if stream_in is not None:
+            y_orig = self.original_order(values, sigma_out)
+            self.trace.append((self.original_order(stream_in, sigma_in), y_orig))
+        v = np.maximum(values, 0.0) if spec.relu else values.copy()
+        self.acts[spec.out] = (v, sigma_out)
+        self.round = r + 1
+
+    def logits(self) -> np.ndarray:
+        v, p = self.acts[self.net.rounds[-1].out]
+        return self.original_order(v, p)
+
+
+def round_float_reference(net: EncodedNetwork, r: int, x_orig: np.ndarray) -> np.ndarray:
+    """f(x) = sum of the round's convolutions in float64 on the given input
+    (original order), output in original order."""
+    spec = net.rounds[r]
+    case = wl.LayerCase(spec.name, spec.terms, net.weights[r], None, x_orig, None, None)
+    return wl.float_reference(case)
+
+
+# ------------------------------------------------------------- one request --
+
+def decode_outputs(net: EncodedNetwork, r: int, residues: np.ndarray) -> np.ndarray:
+    info = net.infos[r]
+    return sf.sf_decode(net.params, residues, info["n_groups"], net.n // info["group_size"],
+                        info["E_out"], net.ps.delta ** 2)
+
+
+def run_request(net: EncodedNetwork, sk, rk, client: ClientState, stream=None, device: str = "cuda:0",
+                keep_trace: bool = False):
+    """All rounds of one request, one sf_eval_linear_layer call per round.
+    Returns per-round device milliseconds (server side only)."""
+    import torch
+    L, n = net.ps.n_data, net.n
+    ms = []
+    for r in range(len(net.rounds)):
+        info = net.infos[r]
+        msg, sigma_prev, stream_in = client.encode(r)
+        d_in = torch.empty((info["k_in"], 2, L, n), dtype=torch.int64, device=device)
+        sf.sf_encrypt(net.ctx, sk, msg, client.encrypt_seed(r), d_in, info["k_in"], stream)
+        d_out = torch.empty((info["n_groups"], 2, L, n), dtype=torch.int64, device=device)
+        so = client.sigma_out(r)
+        st = stream if stream is not None else torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        sf.sf_eval_linear_layer(net.ctx, net.layers[r], rk, d_in, info["k_in"], sigma_prev, so, d_out,
+                                info["n_groups"], st)
+        e1.record(st)
+        res = np.zeros((info["n_groups"], L, n), dtype=np.uint64)
+        sf.sf_decrypt(net.ctx, sk, d_out, info["n_groups"], res, st)
+        ms.append(e0.elapsed_time(e1))
+        vals = decode_outputs(net, r, res)
+        client.absorb(r, vals, so, stream_in if keep_trace else None, sigma_prev)
+    return ms
+
+
+def float_forward(net: EncodedNetwork, x: np.ndarray, trace: list = None) -> np.ndarray:
+    """The plaintext network in float64 with the same weights: rounds in
+    order, ReLU where the round applies it; returns the logits."""
+    acts = {"x": np.asarray(x, dtype=np.float64)}
+    for r, spec in enumerate(net.rounds):
+        inp = np.concatenate([acts[name] for name in spec.inputs])
+        y = round_float_reference(net, r, inp)
+        if trace is not None:
+            trace.append((inp, y))
+        acts[spec.out] = np.maximum(y, 0.0) if spec.relu else y
+    return acts[net.rounds[-1].out]

@@ -177,3 +177,140 @@ def float_reference(case: LayerCase) -> np.ndarray:
     if case.bias is not None:
         y += case.bias
     return y.ravel()
+
+
+# ---------------------------------------------------------------------------
+# ResNet-shaped networks as lists of layer rounds
+# ---------------------------------------------------------------------------
+
+@dataclass
+class RoundSpec:
+    """One server round: terms over named input tensors.
+
+    inputs: names of the activation tensors concatenated (in order) into the
+    round's flattened input; terms: (input index, Term with in_offset set)."""
+    name: str
+    inputs: list
+    terms: list
+    out: str
+    relu: bool = True
+    weights_seed: int = 0
+
+
+def _term_over(k, H, W, C, Co, kh, stride, pad):
+    return Term(k, H, W, C, Co, kh, kh, stride, pad)
+
+
+NETS = {
+    # image H (= W), image channels, stem (kernel, stride, channels), stage widths, blocks per stage, classes
+    "resnet20": dict(H=32, C=3, stem=(3, 1, 16), stages=[16, 32, 64], blocks=[3, 3, 3], ncls=10, seed=1000),
+    "resnet18": dict(H=64, C=3, stem=(3, 1, 64), stages=[64, 128, 256, 512], blocks=[2, 2, 2, 2], ncls=200,
+                     seed=3000),
+    "resnet34": dict(H=224, C=3, stem=(7, 2, 64), stages=[64, 128, 256, 512], blocks=[3, 4, 6, 3], ncls=1000,
+                     seed=4000, pool=True),
+    # small networks of the same structure, for tests
+    "tiny_a": dict(H=8, C=2, stem=(3, 1, 4), stages=[4], blocks=[1], ncls=10, seed=5000),
+    "tiny_b": dict(H=8, C=3, stem=(3, 1, 8), stages=[8, 8], blocks=[1, 1], ncls=5, seed=6000),
+}
+
+
+def resnet_rounds(kind: str) -> list:
+    """Round lists of ResNet-shaped networks.  Batch norm is folded (identity
+    on synthetic weights); ReLU runs on the client between rounds.  A basic
+    block is two rounds; its second conv takes the block input as a second
+    term (identity 1x1 for the same shape, 1x1 stride 2 to downsample).  The
+    first block of every stage after the first has stride 2.  The global
+    average pool is folded into the FC (a kernel as large as its input).
+
+    resnet20: 3x32x32, 16/32/64 channels, 3 blocks per stage, FC 64 -> 10.
+    resnet18: 3x64x64, 3x3 stem, no max-pool, 64/128/256/512, [2,2,2,2], FC -> 200.
+    resnet34: 3x224x224, 7x7 stride-2 stem to 64x112x112; the 3x3 stride-2
+      average pool is folded into the first block: its first conv becomes a
+      7x7 stride-2 kernel over the stem output and its shortcut the pool itself
+      (3x3 stride 2, per channel); [3,4,6,3] blocks, FC 512 -> 1000."""
+    cfg = NETS[kind]
+    seed = [cfg["seed"]]
+
+    def nxt():
+        seed[0] += 1
+        return seed[0]
+
+    sk, ss, sc_ = cfg["stem"]
+    H0 = cfg["H"]
+    rounds = [RoundSpec("stem", ["x"], [_term_over(0, H0, H0, cfg["C"], sc_, sk, ss, sk // 2)], "a0", True, nxt())]
+    cur, cH, cC = "a0", (H0 + 2 * (sk // 2) - sk) // ss + 1, sc_
+    for si, (Co, nb) in enumerate(zip(cfg["stages"], cfg["blocks"])):
+        for bi in range(nb):
+            pooled = cfg.get("pool", False) and si == 0 and bi == 0
+            stride = 2 if (si > 0 and bi == 0) else 1
+            mid, out = f"s{si}b{bi}m", f"s{si}b{bi}o"
+            if pooled:
+                oH = cH // 2
+                t1 = _term_over(0, cH, cH, cC, Co, 7, 2, 3)
+                sc = _term_over(oH * oH * Co, cH, cH, cC, Co, 3, 2, 1)
+            else:
+                oH = (cH - 1) // stride + 1
+                t1 = _term_over(0, cH, cH, cC, Co, 3, stride, 1)
+                sc = _term_over(oH * oH * Co, cH, cH, cC, Co, 1, stride, 0)
+            rounds.append(RoundSpec(f"s{si}b{bi}c1", [cur], [t1], mid, True, nxt()))
+            rounds.append(RoundSpec(f"s{si}b{bi}c2", [mid, cur], [_term_over(0, oH, oH, Co, Co, 3, 1, 1), sc],
+                                    out, True, nxt()))
+            cur, cH, cC = out, oH, Co
+    rounds.append(RoundSpec("fc", [cur], [_term_over(0, cH, cH, cC, cfg["ncls"], cH, 1, 0)], "logits", False,
+                            nxt()))
+    return rounds
+
+
+def network_input(kind: str, seed: int) -> np.ndarray:
+    """A synthetic image for the network, U(0, 1), flattened (h, w, c)."""
+    cfg = NETS[kind]
+    return np.random.default_rng(seed).uniform(0.0, 1.0, cfg["H"] * cfg["H"] * cfg["C"])
+
+
+def round_weights(spec: RoundSpec, integer: bool = False) -> list:
+    """Seeded weights per term, [C_out][kh][kw][C_in]: Kaiming-uniform
+    convolutions and downsampling shortcuts; the identity for a 1x1 stride-1
+    shortcut; the 3x3 average (1/9 on the diagonal) for a pooled shortcut; the
+    composition of a 3x3 conv with the 3x3 stride-2 average pool for the 7x7
+    stride-2 kernel that follows it; and an FC weight spread evenly over the
+    folded average pool.  ``integer``: small integers instead (exact mode)."""
+    rng = np.random.default_rng(spec.weights_seed)
+    ws = []
+    for ti, t in enumerate(spec.terms):
+        shape = (t.C_out, t.kh, t.kw, t.C_in)
+        if integer:
+            if ti == 1 and t.kh == 1 and t.stride == 1:
+                w = np.zeros(shape)
+                w[np.arange(t.C_out), 0, 0, np.arange(t.C_in)] = 1.0
+            else:
+                w = rng.integers(-2, 3, shape).astype(np.float64)
+        elif ti == 1 and t.kh == 1 and t.stride == 1 and t.C_in == t.C_out:
+            w = np.zeros(shape)
+            w[np.arange(t.C_out), 0, 0, np.arange(t.C_in)] = 1.0
+        elif ti == 1 and t.kh == 3:
+            w = np.zeros(shape)
+            w[np.arange(t.C_out), :, :, np.arange(t.C_in)] = 1.0 / 9.0
+        elif spec.name == "fc":
+            w = kaiming_uniform(rng, (t.C_out, 1, 1, t.C_in), t.C_in) / (t.kh * t.kw)
+            w = np.broadcast_to(w, shape).copy()
+        elif ti == 0 and t.kh == 7 and spec.name != "stem":
+            w3 = kaiming_uniform(rng, (t.C_out, 3, 3, t.C_in), 9 * t.C_in)
+            w = np.zeros(shape)
+            for a in range(3):
+                for e in range(3):
+                    for b in range(3):
+                        for f in range(3):
+                            w[:, 2 * a + e, 2 * b + f, :] += w3[:, a, b, :] / 9.0
+        else:
+            w = kaiming_uniform(rng, shape, t.fan_in)
+        ws.append(w)
+    return ws
+
+
+def round_input_size(spec: RoundSpec) -> int:
+    return max(t.in_offset + t.H * t.W * t.C_in for t in spec.terms)
+
+
+def round_output_size(spec: RoundSpec) -> int:
+    t = spec.terms[0]
+    return t.H_out * t.W_out * t.C_out

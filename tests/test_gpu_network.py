@@ -1,0 +1,69 @@
+"""Multi-round encrypted inference and the continuous-batching server on the
+GPU: a small ResNet-shaped network end to end against its float64 forward
+pass, and every request's result identical alone and inside a served mix of
+networks, parameter sets and client keys."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2509_01253_gb300 import network as nw  # noqa: E402
+from paper_2509_01253_gb300 import serve  # noqa: E402
+from paper_2509_01253_gb300 import workloads as wl  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def pools():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    p = {"p12": serve.Pool(wl.PARAMS["fc64"], ["tiny_a"], 2, 0, key_seed=11),
+         "p14": serve.Pool(wl.PARAMS["conv16"], ["tiny_a", "tiny_b"], 2, 0, key_seed=21)}
+    yield p
+    for x in p.values():
+        x.destroy()
+
+
+def _alone(pool, net, key, seed):
+    req = serve.make_request(0, net, key, seed)
+    client = nw.ClientState(pool.nets[net], req.x, req.session_seed, req.request_seed)
+    nw.run_request(pool.nets[net], pool.sks[key], pool.rks[key], client, keep_trace=True)
+    return client
+
+
+@pytest.mark.parametrize("pool_name,net", [("p12", "tiny_a"), ("p14", "tiny_b")])
+def test_network_rounds_match_float64(pools, pool_name, net):
+    pool = pools[pool_name]
+    client = _alone(pool, net, 1, 5)
+    encnet = pool.nets[net]
+    assert len(client.trace) == len(encnet.rounds)
+    # every round against the plaintext layer on the client's actual input
+    for r, (x_in, y) in enumerate(client.trace):
+        ref = nw.round_float_reference(encnet, r, x_in)
+        assert np.abs(y - ref).max() <= 1e-3, (net, r)
+    # and the whole chain against the float64 network
+    ref = nw.float_forward(encnet, wl.network_input(net, 5))
+    assert np.abs(client.logits() - ref).max() <= 1e-3
+
+
+def test_served_results_equal_alone(pools):
+    route = {"tiny_a": "p12", "tiny_b": "p14"}
+    specs = [("tiny_a", 0, 31), ("tiny_b", 1, 32), ("tiny_a", 1, 33), ("tiny_b", 0, 34), ("tiny_b", 1, 35),
+             ("tiny_a", 0, 36), ("tiny_b", 0, 37)]
+    alone = {seed: _alone(pools[route[net]], net, key, seed).logits() for net, key, seed in specs}
+    srv = serve.Server(pools, route, mem_budget=1 << 34, max_queue=16, max_active=3, max_batch=2)
+    srv.start()
+    import time
+    for i, (net, key, seed) in enumerate(specs):
+        assert srv.submit(serve.make_request(i, net, key, seed))
+        if i == 3:
+            time.sleep(0.05)        # the rest arrive while the first are on the device
+    t_end = time.perf_counter() + 300
+    while not srv.idle() and time.perf_counter() < t_end and not srv.errors:
+        time.sleep(0.01)
+    srv.shutdown()
+    assert len(srv.completed) == len(specs)
+    assert max(b[1] for b in srv.batches) == 2        # calls held several requests
+    for req in srv.completed:
+        assert np.array_equal(req.logits, alone[req.request_seed]), req.request_seed
