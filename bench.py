@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reference-sample-s", type=float, default=8.0,
+                    help="--impl reference: CPU seconds bound of each step's oracle sample")
     ap.add_argument("--workload", default="conv16", choices=["conv16", "resnet18", "resnet34", "serve"])
     ap.add_argument("--rates", default="5,20,200", help="serve: arrival rates (requests/s)")
     ap.add_argument("--duration", type=float, default=20.0, help="serve: arrival window per rate (s)")
@@ -339,6 +341,21 @@ def oracle_sample(max_seconds: float = 20.0):
 
 # ----------------------------------------------------------------- main ----
 
+def max_over_ranks(dist, x: float) -> float:
+    """The slowest rank's time (replicas run independently; only timings meet)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def replicas_value(ws: int, steps: int, total_s: float) -> float:
+    """Whole-job throughput: every rank ran `steps` layer rounds; the job took the slowest rank's time."""
+    return ws * steps / total_s
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -356,7 +373,7 @@ def run_reference(args, dist, ws, rank):
     times = []
     cores = desc = None
     for i in range(args.warmup + args.steps):
-        v, cores, desc = oracle_sample(max_seconds=8.0)
+        v, cores, desc = oracle_sample(max_seconds=args.reference_sample_s)
         if i >= args.warmup:
             times.append(1.0 / v)
     sec = sum(times) / len(times)
@@ -558,11 +575,8 @@ def main():
     total_s = sum(step_ms) / 1e3
     stats = launches(sf, wl_.ctx)
     n_launch = sum(c for c, _ in stats.values())
-    if dist:
-        t = torch.tensor([total_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t[0])
-    value = ws * args.steps / total_s
+    total_s = max_over_ranks(dist, total_s)
+    value = replicas_value(ws, args.steps, total_s)
     # ---- end to end: host buffers through the C ABI, copies inside the timed region
     pin_in = torch.empty((wl_.k_in, 2, wl_.L, wl_.n), dtype=torch.int64, pin_memory=True)
     pin_in.copy_(wl_.d_in.cpu())
@@ -582,11 +596,8 @@ def main():
         sf.sf_eval_linear_layer_host(wl_.ctx, wl_.layer, wl_.rk, h_in, wl_.k_in, wl_.case.sigma_prev,
                                      wl_.case.sigma_out, h_out, wl_.G, stream)
         e2e_s += time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t[0])
-    e2e_value = ws * args.steps / e2e_s
+    e2e_s = max_over_ranks(dist, e2e_s)
+    e2e_value = replicas_value(ws, args.steps, e2e_s)
     h2d = wl_.k_in * wl_.ct_bytes + 4 * (wl_.info["E_in"] + wl_.info["E_out"])
     d2h = wl_.G * wl_.ct_bytes
     # ---- per-kernel device time (instrumented pass: events around every launch)
