@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--rates", default="5,20,200", help="serve: arrival rates (requests/s)")
     ap.add_argument("--duration", type=float, default=20.0, help="serve: arrival window per rate (s)")
     ap.add_argument("--drain", type=float, default=60.0, help="serve: time allowed after the window (s)")
+    ap.add_argument("--layer-stats", default="",
+                    help="resnet18/resnet34: only a per-kernel breakdown of these rounds (comma-separated names)")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: the same conv kernel shapes on 8x16x16 (2048 outputs, ~2 GB on device)")
     return ap.parse_args()
@@ -211,8 +213,8 @@ def kernel_work(kernel: str, g: RingShape, k_in: int = 1):
         "ks3_inner_row": ((dnum * nm + 2 * nm) * N * w, (dnum * nm - L) * half * lc + 2 * dnum * nm * N),
         "ks3_inv_row_p": (4 * K * N * w, 2 * K * half * lc),
         "ks4_moddown_col": ((2 * K + 2 * L) * N * w, 2 * K * half * lr + 2 * K * N + 2 * K * L * N + 2 * L * half * lr),
-        "ks5_finish_row": (6 * L * N * w, 2 * L * half * lc + 2 * L * N),
-        "ks_merge": (8 * L * N * w, 2 * L * N),
+        # read conv + acc (2L each), E and O (2L each), write the merged ciphertext (2L)
+        "ks5_finish_row": (10 * L * N * w, 2 * L * half * lc + 2 * L * N + 2 * L * N),
         "leaf_col": (L * N * w, L * half * lr),
         "leaf_row": ((k_in * L + 2 * L) * N * w, k_in * L * half * lc + 2 * k_in * L * N),
     }
@@ -493,6 +495,28 @@ def run_network(args, local: int) -> int:
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
     clocks = ClockSampler(local)
     clocks.start()
+    if args.layer_stats:
+        g = RingShape(sf.sf_params_get_info(nw_.params))
+        out = {"workload": args.workload, "n": nw_.n, "L": nw_.L, "layer_stats": {}}
+        names = [r.name for r in nw_.net.rounds]
+        for name in args.layer_stats.split(","):
+            r = names.index(name)
+            timed(torch_, nw_.stream, lambda: nw_.per_layer(r))
+            sf.sf_kernel_stats_reset(nw_.ctx)
+            sf.sf_ctx_set_option(nw_.ctx, "kernel_timing", 1)
+            flush_l2(flush)
+            t = timed(torch_, nw_.stream, lambda: nw_.per_layer(r))
+            sf.sf_ctx_set_option(nw_.ctx, "kernel_timing", 0)
+            ks = launches(sf, nw_.ctx)
+            tot = sum(ms for _, ms in ks.values())
+            info = nw_.net.infos[r]
+            out["layer_stats"][name] = {
+                "info": info, "ms_instrumented": t,
+                "kernels": {k: {"launches": c, "ms": m} for k, (c, m) in ks.items() if c},
+                "roofline": roofline_of(ks, 1, g, info, tot, {"sm_mhz": None})}
+        out["clocks"] = clocks.stop()
+        print(json.dumps(out), flush=True)
+        return 0
     rec = {"metric": METRIC, "unit": UNIT, "workload": args.workload, "rounds": R,
            "ks_total": nw_.net.total_ks(), "outputs_total": sum(i["E_out"] for i in nw_.net.infos),
            "n": nw_.n, "L": nw_.L, "data": "synthetic: per-round inputs U(0,1), Kaiming-uniform weights"}

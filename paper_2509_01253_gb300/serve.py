@@ -73,7 +73,7 @@ class Pool:
             sf.sf_ctx_set_option(self.ctx, "ks_batch", ks_batch)
         self.device = f"cuda:{device}"
         self.sks = [sf.sf_keygen(self.ctx, key_seed + 2 * c) for c in range(n_clients)]
-        self.rks = [sf.sf_gen_rotation_keys(self.ctx, sk, None, key_seed + 2 * c + 1) for sk in self.sks]
+        self.rks = [sf.sf_gen_rotation_keys(self.ctx, sk, None, key_seed + 2 * c + 1) for c, sk in enumerate(self.sks)]
         self.nets = {name: nw.EncodedNetwork(self.params, self.ctx, ps, wl.resnet_rounds(name)) for name in nets}
         self.stream = torch.cuda.Stream(device=device)
         self.n, self.L = 1 << ps.log_n, ps.n_data
