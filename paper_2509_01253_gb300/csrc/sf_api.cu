@@ -324,6 +324,16 @@ extern "C" sf_status sf_encode_weights(sf_ctx *ctx, const sf_conv_term *terms, i
     L->d_wq = nullptr;
     L->d_bq = nullptr;
     L->d_terms = nullptr;
+    L->d_taps = nullptr;
+    std::vector<int4> taps;
+    for (int t = 0; t < n_terms; ++t) {
+        const sf_conv_term &T = terms[t];
+        L->tap_off.push_back((int)taps.size());
+        for (int dh = 0; dh < T.kh; ++dh)
+            for (int dw = 0; dw < T.kw; ++dw)
+                for (int ci = 0; ci < T.C_in; ++ci)
+                    taps.push_back(make_int4(dh, dw, (dh * T.W + dw) * T.C_in + ci, (dh * T.kw + dw) * T.C_in + ci));
+    }
     for (size_t x = 0; x < nw; ++x) {
         double v = weight_scale * W[x];
         if (!(fabs(v) < 4.6e18)) {
@@ -346,6 +356,9 @@ extern "C" sf_status sf_encode_weights(sf_ctx *ctx, const sf_conv_term *terms, i
     sf_status st = device_buffer((void **)&L->d_wq, sizeof(int64_t) * nw);
     if (st == SF_OK && cudaMemcpy(L->d_wq, L->wq.data(), sizeof(int64_t) * nw, cudaMemcpyHostToDevice) != cudaSuccess)
         st = sf_set_error(SF_ECUDA, "weight upload failed");
+    if (st == SF_OK) st = device_buffer((void **)&L->d_taps, sizeof(int4) * taps.size());
+    if (st == SF_OK && cudaMemcpy(L->d_taps, taps.data(), sizeof(int4) * taps.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        st = sf_set_error(SF_ECUDA, "tap table upload failed");
     if (st == SF_OK && bias) {
         st = device_buffer((void **)&L->d_bq, sizeof(int64_t) * Co);
         if (st == SF_OK && cudaMemcpy(L->d_bq, L->bq.data(), sizeof(int64_t) * Co, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -365,6 +378,7 @@ extern "C" void sf_layer_destroy(sf_layer *L)
     cudaSetDevice(L->ctx->device);
     if (L->d_wq) cudaFree(L->d_wq);
     if (L->d_bq) cudaFree(L->d_bq);
+    if (L->d_taps) cudaFree(L->d_taps);
     delete L;
 }
 

@@ -271,6 +271,11 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
                 e.launches[k] = ctx->stats[k].launches - before[k];
                 ctx->stats[k].launches = before[k];
             }
+            // bounded cache: a serving loop sees a new combination of rounds at every call
+            if (ctx->graphs.size() >= 32) {
+                cudaGraphExecDestroy(ctx->graphs.front().exec);
+                ctx->graphs.erase(ctx->graphs.begin());
+            }
             ctx->graphs.push_back(e);
             hit = &ctx->graphs.back();
         }

@@ -535,6 +535,13 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
                     rowT_i[dst] = make_ulonglong2(ti[gi], tip[gi]);
                 }
     }
+    // powers psi^(C e), e < 2R (closed-form column pass of a sparse polynomial)
+    std::vector<ulonglong2> pwc((size_t)nm * 2 * R.r);
+    for (int m = 0; m < nm; ++m)
+        for (int e = 0; e < 2 * R.r; ++e) {
+            const size_t k = (size_t)m * 2 * N + (size_t)e * R.c;
+            pwc[(size_t)m * 2 * R.r + e] = make_ulonglong2(pw[k], pw_p[k]);
+        }
     // ModUp constants
     int dnum = p->dnum;
     std::vector<u64> mu_inv((size_t)dnum * K, 0), mu_inv_p((size_t)dnum * K, 0);
@@ -589,7 +596,7 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
 #define UP(v, f)                                      \
     if (st == SF_OK) st = upload(ctx, v, &R.f);
     UP(psi, psi) UP(psi_p, psi_p) UP(ipsi, ipsi) UP(ipsi_p, ipsi_p) UP(pw, pw) UP(pw_p, pw_p)
-    UP(colT_f, colT_f) UP(colT_i, colT_i) UP(rowT_f, rowT_f) UP(rowT_i, rowT_i)
+    UP(colT_f, colT_f) UP(colT_i, colT_i) UP(rowT_f, rowT_f) UP(rowT_i, rowT_i) UP(pwc, pwc)
     UP(mu_inv, mu_inv) UP(mu_inv_p, mu_inv_p) UP(mu_qhat, mu_qhat) UP(mu_qhat_p, mu_qhat_p)
     UP(md_inv, md_inv) UP(md_inv_p, md_inv_p) UP(md_phat, md_phat) UP(md_phat_p, md_phat_p)
     UP(md_pinv, md_pinv) UP(md_pinv_p, md_pinv_p)

@@ -33,6 +33,8 @@ struct SfRing {
     const ulonglong2 *colT_f, *colT_i, *rowT_f, *rowT_i;
     // powers psi^k, k in [0, 2N), [nm][2N] (monomials in the NTT domain)
     const u64 *pw, *pw_p;
+    // pairs (psi^(C e), companion), e < 2R, [nm][2R] (sparse column pass)
+    const ulonglong2 *pwc;
     // ModUp: for digit j, limb i in the digit: N^-1 (Qhat_i mod q_i)^-1 with
     //        Shoup (N^-1 finishes the inverse NTT); Qhat_i mod m for every m.
     const u64 *mu_inv, *mu_inv_p;   // [dnum][K]
@@ -124,6 +126,9 @@ struct sf_layer {
     int64_t *d_wq;            // device copy of the quantised weights
     int64_t *d_bq;            // device copy of the bias (or null)
     sf_conv_term *d_terms;
+    // per term, per tap t = (dh kw + dw) C_in + ci: {dh, dw, (dh W + dw) C_in + ci, t}
+    int4 *d_taps;
+    std::vector<int> tap_off; // first tap of each term in d_taps
 };
 
 // ------------------------------------------------------------------ errors --

@@ -145,8 +145,8 @@ struct SfRowSet {
     int npoly, mod_base, mod_period;
 };
 
-template <bool INV>
-__global__ void __launch_bounds__(SF_THREADS) k_rows(SfRing R, SfKsBatch B, SfRowSet S, int bpg)
+template <bool INV, int NT>
+__global__ void __launch_bounds__(NT) k_rows(SfRing R, SfKsBatch B, SfRowSet S, int bpg)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SfGeo g = ring_geo(R);
@@ -169,8 +169,8 @@ __global__ void __launch_bounds__(SF_THREADS) k_rows(SfRing R, SfKsBatch B, SfRo
         sf_cp_commit();
         sf_cp_wait<1>();
         __syncthreads();
-        if (INV) row_inverse(cur, tw, g.log_c, M.q);
-        else row_forward(cur, tw, g.log_c, M.q);
+        if (INV) row_inverse<NT>(cur, tw, g.log_c, M.q);
+        else row_forward<NT>(cur, tw, g.log_c, M.q);
         u64 *dst = B.scratch + per * b + off_d;
         for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) dst[e] = cur[row_slot(g, e)];
         __syncthreads();
@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(SF_THREADS) k_rows(SfRing R, SfKsBatch B, SfRo
 // ModUp.  Groups: (column tile, digit j); items: merges.  smem: inverse and
 // forward column tables of every modulus, two buffers of nd source tiles, one
 // work tile.
-__global__ void __launch_bounds__(SF_THREADS) k_ks2(SfRing R, SfKsBatch B, int bpg)
+template <int NT>
+__global__ void __launch_bounds__(NT) k_ks2(SfRing R, SfKsBatch B, int bpg)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SfGeo g = ring_geo(R);
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(SF_THREADS) k_ks2(SfRing R, SfKsBatch B, int b
         for (int t = 0; t < nd; ++t) {
             const int i = lo + t;
             u64 *st = cur + (size_t)t * tw_words;
-            col_inverse(st, twi + (size_t)i * g.r, g.log_r, R.m[i].q);
+            col_inverse<NT>(st, twi + (size_t)i * g.r, g.log_r, R.m[i].q);
             const u64 w = R.mu_inv[j * R.K + t], wp = R.mu_inv_p[j * R.K + t];
             for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x)
                 st[col_slot(e)] = sf_mul_shoup(st[col_slot(e)], w, wp, R.m[i].q);
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(SF_THREADS) k_ks2(SfRing R, SfKsBatch B, int b
                 work[sl] = acc;
             }
             __syncthreads();
-            col_forward(work, twf + (size_t)m * g.r, g.log_r, M.q);
+            col_forward<NT>(work, twf + (size_t)m * g.r, g.log_r, M.q);
             u64 *dst = Lo.x2 + ((size_t)(j * R.nm + m) << R.log_n);
             for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) dst[col_gidx(g, c0, e)] = work[col_slot(e)];
             __syncthreads();
@@ -246,8 +247,8 @@ __global__ void __launch_bounds__(SF_THREADS) k_ks2(SfRing R, SfKsBatch B, int b
 // each taking dnum steps (one per digit) whose tiles are double-buffered.
 // Output: ACC (data moduli, NTT domain) or, for the special moduli, their NTT
 // values in the x1 region (the inverse row pass runs in k_rows<true>).
-template <int EPT>
-__global__ void __launch_bounds__(SF_THREADS, EPT >= 16 ? 1 : 3) k_ks3(SfRing R, SfKsBatch B, int bpg)
+template <int EPT, int NT>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (EPT >= 16 ? 1 : 3)) k_ks3(SfRing R, SfKsBatch B, int bpg)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SfGeo g = ring_geo(R);
@@ -284,13 +285,13 @@ __global__ void __launch_bounds__(SF_THREADS, EPT >= 16 ? 1 : 3) k_ks3(SfRing R,
         sf_cp_wait<1>();
         __syncthreads();
         const bool own = (m >= j * R.K && m < min((j + 1) * R.K, R.L));
-        if (!own) row_forward(cur, tw, g.log_c, M.q);
+        if (!own) row_forward<NT>(cur, tw, g.log_c, M.q);
         const u64 *ka = B.key + ((((size_t)j * 2 + 0) * R.nm + m) << R.log_n) + tile_off;
         const u64 *kb = B.key + ((((size_t)j * 2 + 1) * R.nm + m) << R.log_n) + tile_off;
         // per digit c * key (c lazy < 36q, key < q) is Montgomery-reduced into [0, 2q) and summed
 #pragma unroll
         for (int x = 0; x < EPT; ++x) {
-            const int e = threadIdx.x + x * SF_THREADS;
+            const int e = threadIdx.x + x * NT;
             const u64 c = cur[row_slot(g, e)];
             const u64 xa = __ldg(ka + e), xb = __ldg(kb + e);
             acc_a[x] += sf_redc_lazy(sf_mulhi(c, xa), c * xa, M.q, M.qinv_neg);
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(SF_THREADS, EPT >= 16 ? 1 : 3) k_ks3(SfRing R,
             }
 #pragma unroll
             for (int x = 0; x < EPT; ++x) {
-                const int e = threadIdx.x + x * SF_THREADS;
+                const int e = threadIdx.x + x * NT;
                 da[e] = sf_reduce(acc_a[x], M.q, M.one_p);
                 db[e] = sf_reduce(acc_b[x], M.q, M.one_p);
                 acc_a[x] = acc_b[x] = 0;
@@ -321,7 +322,8 @@ __global__ void __launch_bounds__(SF_THREADS, EPT >= 16 ? 1 : 3) k_ks3(SfRing R,
 // ModDown conversion.  Groups: (column tile, part p); items: merges.  smem: K
 // inverse (special) + L forward (data) column tables, two buffers of K tiles,
 // one work tile.
-__global__ void __launch_bounds__(SF_THREADS) k_ks4(SfRing R, SfKsBatch B, int bpg)
+template <int NT>
+__global__ void __launch_bounds__(NT) k_ks4(SfRing R, SfKsBatch B, int bpg)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SfGeo g = ring_geo(R);
@@ -353,7 +355,7 @@ __global__ void __launch_bounds__(SF_THREADS) k_ks4(SfRing R, SfKsBatch B, int b
         for (int k = 0; k < R.K; ++k) {
             const int m = R.L + k;
             u64 *st = cur + (size_t)k * tw_words;
-            col_inverse(st, twi + (size_t)k * g.r, g.log_r, R.m[m].q);
+            col_inverse<NT>(st, twi + (size_t)k * g.r, g.log_r, R.m[m].q);
             const u64 w = R.md_inv[k], wp = R.md_inv_p[k];
             for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x)
                 st[col_slot(e)] = sf_mul_shoup(st[col_slot(e)], w, wp, R.m[m].q);
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(SF_THREADS) k_ks4(SfRing R, SfKsBatch B, int b
                 work[sl] = acc;
             }
             __syncthreads();
-            col_forward(work, twf + (size_t)i * g.r, g.log_r, M.q);
+            col_forward<NT>(work, twf + (size_t)i * g.r, g.log_r, M.q);
             u64 *dst = Lo.x2 + ((size_t)(p * R.L + i) << R.log_n);
             for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) dst[col_gidx(g, c0, e)] = work[col_slot(e)];
             __syncthreads();
@@ -383,7 +385,8 @@ __global__ void __launch_bounds__(SF_THREADS) k_ks4(SfRing R, SfKsBatch B, int b
 // ModDown finish.  Groups: (row tile, limb i); items: (merge b, part p).
 // RES = (ACC - conv) P^-1 written over ACC.  smem: forward row twiddles, two
 // buffers of (conversion tile, ACC tile).
-__global__ void __launch_bounds__(SF_THREADS) k_ks5(SfRing R, SfKsBatch B, int bpg)
+template <int NT>
+__global__ void __launch_bounds__(NT) k_ks5(SfRing R, SfKsBatch B, int bpg)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SfGeo g = ring_geo(R);
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(SF_THREADS) k_ks5(SfRing R, SfKsBatch B, int b
         sf_cp_commit();
         sf_cp_wait<1>();
         __syncthreads();
-        row_forward(cur, tw, g.log_c, M.q);
+        row_forward<NT>(cur, tw, g.log_c, M.q);
         const int b = it >> 1, p = it & 1;
         u64 *dst = ks_layout(R, B, b).accq + ((size_t)(p * R.L + i) << R.log_n) + tile_off;
         for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) {
@@ -451,23 +454,33 @@ static size_t smem_rows(const SfRing &R, int tiles)
 }
 
 template <class K>
-static int occupancy(K kernel, size_t smem)
+static int occupancy(K kernel, int threads, size_t smem)
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, SF_THREADS, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         b = 1;
     }
     return std::max(1, b);
 }
 
-// blocks per group: fill every SM at the kernel's occupancy, at most one block per item
+// blocks per group: as many as one resident wave holds (num_sms x occupancy
+// blocks in all), at most one block per item.  Rounding up instead would
+// leave a second wave of a few blocks that starts only when the first wave
+// ends, doubling the kernel's time.
 static int blocks_per_group(const sf_ctx *ctx, int occ, int n_groups, int n_items)
 {
     const int target = ctx->num_sms * occ;
-    const int bpg = (target + n_groups - 1) / n_groups;
+    const int bpg = target / n_groups;
     return std::max(1, std::min(bpg, n_items));
 }
+
+#define SF_KS3_CASE(E)                                                                        \
+    case E: {                                                                                 \
+        const int bpg = blocks_per_group(ctx, occupancy(k_ks3<E, NT>, NT, sm3), ng, b.count); \
+        k_ks3<E, NT><<<ng * bpg, NT, sm3, st>>>(R, b, bpg);                                   \
+        break;                                                                                \
+    }
 
 sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
 {
@@ -480,7 +493,8 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
     const size_t sm3 = smem_rows(R, 2);
     const size_t sm4 = sizeof(sf_tw) * (R.K + R.L) * R.r + sizeof(u64) * tile_words(R.log_r) * (2 * R.K + 1);
     const size_t sm5 = smem_rows(R, 4);
-    const int ept = (R.c * SF_NB) / SF_THREADS;
+    const int ntr = sf_tile_threads(R.log_c), ntc = sf_tile_threads(R.log_r);
+    const int ept = (R.c * SF_NB) / ntr;
     cudaEvent_t ev;
     for (int off = 0; off < B0.count; off += 32768) {
         SfKsBatch b = B0;
@@ -493,62 +507,59 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
         k_ks_gather<<<eg, 256, 0, st>>>(R, b);
         sf_launch_end(ctx, SFK_KS_GATHER, st, ev);
         sf_launch_begin(ctx, SFK_KS1_INV_ROW, st, &ev);
-        {
+        SF_NT_DISPATCH(ntr, {
             const SfRowSet S{0, (size_t)R.L << R.log_n, R.L, 0, R.L};   // TA -> X1
             const int ng = rtiles * S.npoly;
-            const int bpg = blocks_per_group(ctx, occupancy(k_rows<true>, sm_rows), ng, b.count);
-            k_rows<true><<<ng * bpg, SF_THREADS, sm_rows, st>>>(R, b, S, bpg);
-        }
+            const int bpg = blocks_per_group(ctx, occupancy(k_rows<true, NT>, NT, sm_rows), ng, b.count);
+            k_rows<true, NT><<<ng * bpg, NT, sm_rows, st>>>(R, b, S, bpg);
+        });
         sf_launch_end(ctx, SFK_KS1_INV_ROW, st, ev);
 
         sf_launch_begin(ctx, SFK_KS2_MODUP_COL, st, &ev);
-        {
+        SF_NT_DISPATCH(ntc, {
             const int ng = ctiles * R.dnum;
-            const int bpg = blocks_per_group(ctx, occupancy(k_ks2, sm2), ng, b.count);
-            k_ks2<<<ng * bpg, SF_THREADS, sm2, st>>>(R, b, bpg);
-        }
+            const int bpg = blocks_per_group(ctx, occupancy(k_ks2<NT>, NT, sm2), ng, b.count);
+            k_ks2<NT><<<ng * bpg, NT, sm2, st>>>(R, b, bpg);
+        });
         sf_launch_end(ctx, SFK_KS2_MODUP_COL, st, ev);
 
         sf_launch_begin(ctx, SFK_KS3_INNER_ROW, st, &ev);
         {
             const int ng = rtiles * R.nm;
-            switch (ept) {
-#define SF_KS3_CASE(E)                                                                 \
-    case E: {                                                                          \
-        const int bpg = blocks_per_group(ctx, occupancy(k_ks3<E>, sm3), ng, b.count);  \
-        k_ks3<E><<<ng * bpg, SF_THREADS, sm3, st>>>(R, b, bpg);                        \
-        break;                                                                         \
-    }
-                SF_KS3_CASE(2) SF_KS3_CASE(4) SF_KS3_CASE(8) SF_KS3_CASE(16)
-#undef SF_KS3_CASE
-            default: return sf_set_error(SF_EINVAL, "unsupported ring split");
-            }
+            sf_status bad = SF_OK;
+            SF_NT_DISPATCH(ntr, {
+                switch (ept) {
+                    SF_KS3_CASE(2) SF_KS3_CASE(4) SF_KS3_CASE(8)
+                default: bad = SF_EINVAL;
+                }
+            });
+            if (bad != SF_OK) return sf_set_error(SF_EINVAL, "unsupported ring split");
         }
         sf_launch_end(ctx, SFK_KS3_INNER_ROW, st, ev);
         sf_launch_begin(ctx, SFK_KS3_INV_ROW_P, st, &ev);
-        {
+        SF_NT_DISPATCH(ntr, {
             // inverse row pass of the special limbs' accumulators, in place in x1
             const SfRowSet S{(size_t)R.L << R.log_n, (size_t)R.L << R.log_n, 2 * R.K, R.L, R.K};
             const int ng2 = rtiles * S.npoly;
-            const int bpg2 = blocks_per_group(ctx, occupancy(k_rows<true>, sm_rows), ng2, b.count);
-            k_rows<true><<<ng2 * bpg2, SF_THREADS, sm_rows, st>>>(R, b, S, bpg2);
-        }
+            const int bpg2 = blocks_per_group(ctx, occupancy(k_rows<true, NT>, NT, sm_rows), ng2, b.count);
+            k_rows<true, NT><<<ng2 * bpg2, NT, sm_rows, st>>>(R, b, S, bpg2);
+        });
         sf_launch_end(ctx, SFK_KS3_INV_ROW_P, st, ev);
 
         sf_launch_begin(ctx, SFK_KS4_MODDOWN_COL, st, &ev);
-        {
+        SF_NT_DISPATCH(ntc, {
             const int ng = ctiles * 2;
-            const int bpg = blocks_per_group(ctx, occupancy(k_ks4, sm4), ng, b.count);
-            k_ks4<<<ng * bpg, SF_THREADS, sm4, st>>>(R, b, bpg);
-        }
+            const int bpg = blocks_per_group(ctx, occupancy(k_ks4<NT>, NT, sm4), ng, b.count);
+            k_ks4<NT><<<ng * bpg, NT, sm4, st>>>(R, b, bpg);
+        });
         sf_launch_end(ctx, SFK_KS4_MODDOWN_COL, st, ev);
 
         sf_launch_begin(ctx, SFK_KS5_FINISH_ROW, st, &ev);
-        {
+        SF_NT_DISPATCH(ntr, {
             const int ng = rtiles * R.L;
-            const int bpg = blocks_per_group(ctx, occupancy(k_ks5, sm5), ng, 2 * b.count);
-            k_ks5<<<ng * bpg, SF_THREADS, sm5, st>>>(R, b, bpg);
-        }
+            const int bpg = blocks_per_group(ctx, occupancy(k_ks5<NT>, NT, sm5), ng, 2 * b.count);
+            k_ks5<NT><<<ng * bpg, NT, sm5, st>>>(R, b, bpg);
+        });
         sf_launch_end(ctx, SFK_KS5_FINISH_ROW, st, ev);
         sf_launch_begin(ctx, SFK_KS_MERGE, st, &ev);
         k_ks_merge<<<mg, 256, 0, st>>>(R, b);
@@ -557,6 +568,8 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
 }
+
+#undef SF_KS3_CASE
 
 // Runs `count` merges sharing (d, s, add_v, key) in launch batches.
 sf_status sf_ks_run(sf_ctx *ctx, SfKsBatch B, u64 *scratch, int batch, cudaStream_t st)
@@ -578,14 +591,14 @@ sf_status sf_ks_run(sf_ctx *ctx, SfKsBatch B, u64 *scratch, int batch, cudaStrea
 sf_status sf_ks_init_attributes()
 {
     const int mx = 227 * 1024;
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_ks2, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_ks3<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_ks3<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_ks3<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_ks3<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_ks4, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_ks5, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+#define SF_KS_ATTR(K) SF_CUDA_TRY(cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+#define SF_KS_ATTRS(NT)                                                                                  \
+    SF_KS_ATTR((k_rows<true, NT>)) SF_KS_ATTR((k_rows<false, NT>)) SF_KS_ATTR(k_ks2<NT>)                 \
+    SF_KS_ATTR((k_ks3<2, NT>)) SF_KS_ATTR((k_ks3<4, NT>)) SF_KS_ATTR((k_ks3<8, NT>)) SF_KS_ATTR(k_ks4<NT>) \
+    SF_KS_ATTR(k_ks5<NT>)
+    SF_KS_ATTRS(256)
+    SF_KS_ATTRS(512)
+#undef SF_KS_ATTRS
+#undef SF_KS_ATTR
     return SF_OK;
 }

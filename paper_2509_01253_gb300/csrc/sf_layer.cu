@@ -22,57 +22,144 @@ __device__ __forceinline__ int leaf_output(const SfLeafParams &P, int slot)
     return P.sig_out ? P.sig_out[slot] : slot;
 }
 
-// leaf_col: grid (C/16 column tiles, k_in * L, slots).  smem: column twiddles + 1 tile.
-__global__ void __launch_bounds__(SF_THREADS) k_leaf_col(SfRing R, SfLeafParams P)
+// Taps of one column tile kept for the closed-form column pass.  A tile
+// with few taps skips the sweep: the column pass maps column c of a
+// polynomial to its values at the R roots of Y^R = -1, z_k =
+// phi^(2 brev(k) + 1) with phi = psi^C, so a single tap v at row r
+// contributes v * psi^(C r (2 brev(k) + 1) mod 2N) to row k -- R products per
+// tap instead of (R/2) log2 R butterflies per column.
+#define SF_LEAF_TAPS 128
+
+size_t sf_smem_leaf_col(const SfRing &R) { return sf_smem_col(R, 1) + sizeof(sf_tw) * 2 * R.r; }
+
+// Calls f(row, column in tile, signed Wq) for every tap of output o that
+// lands in ciphertext j inside the 16 columns from c0; the sign carries the
+// X^-k = -X^(N-k) of the extraction.  Threads split the taps.
+template <class F>
+__device__ __forceinline__ void leaf_taps(const SfRing &R, const SfGeo &g, const SfLeafParams &P, int o, int j, int c0,
+                                          F f)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SfGeo g = ring_geo(R);
-    const int c0 = blockIdx.x * SF_NB;
-    const int j = blockIdx.y / R.L, i = blockIdx.y % R.L;
-    const int slot = P.s0 + blockIdx.z * P.s_stride;
-    const int o = leaf_output(P, slot);
-    if (o < 0) return;
-    sf_tw *tw = (sf_tw *)smem_raw;
-    u64 *sm = (u64 *)(tw + g.r);
-    const int ne = col_elems(g);
-    load_col_tw(tw, R.colT_f, g, i);
-    for (int e = threadIdx.x; e < tile_words(g.log_r); e += blockDim.x) sm[e] = 0;
-    __syncthreads();
-    const SfMod &M = R.m[i];
     const int co = o % P.C_out, hw = o / P.C_out;
     const int ho = hw / P.W_out, wo = hw % P.W_out;
     for (int ti = 0; ti < P.n_terms; ++ti) {
         const SfTermDev &T = P.t[ti];
         const int ntap = T.kh * T.kw * T.C_in;
+        const int h0 = ho * T.stride - T.pad, w0 = wo * T.stride - T.pad;
+        const int base = T.in_offset + (h0 * T.W + w0) * T.C_in;
+        const int64_t *wrow = P.wq + T.w_off + (size_t)co * ntap;
         for (int tt = threadIdx.x; tt < ntap; tt += blockDim.x) {
-            const int dh = tt / (T.kw * T.C_in), rem = tt % (T.kw * T.C_in);
-            const int dw = rem / T.C_in, ci = rem % T.C_in;
-            const int h = ho * T.stride - T.pad + dh, w = wo * T.stride - T.pad + dw;
+            const int4 tp = P.taps[T.tap_off + tt];
+            const int h = h0 + tp.x, w = w0 + tp.y;
             if (h < 0 || h >= T.H || w < 0 || w >= T.W) continue;
-            const int idx = T.in_offset + (h * T.W + w) * T.C_in + ci;
+            const int idx = base + tp.z;
             const int p = P.pos_of ? P.pos_of[idx] : idx;
             if ((p >> R.log_n) != j) continue;
             const int k = p & (R.n - 1);
             const int cidx = k ? R.n - k : 0;
             const int col = cidx & (g.c - 1);
             if (col < c0 || col >= c0 + SF_NB) continue;
-            const int64_t wq = P.wq[T.w_off + ((size_t)(co * T.kh + dh) * T.kw + dw) * T.C_in + ci];
-            const int64_t r = wq % (int64_t)M.q;
-            u64 v = (u64)(r < 0 ? r + (int64_t)M.q : r);
-            v = sf_mul_shoup(v, M.ninv, M.ninv_p, M.q);
-            if (k && v) v = M.q - v;   // X^-k = -X^(N-k)
-            sm[(cidx >> g.log_c) * SF_PAD + (col - c0)] = v;
+            const int64_t wq = wrow[tp.w];
+            f(cidx >> g.log_c, col - c0, k ? -wq : wq);
         }
     }
-    __syncthreads();
-    col_forward(sm, tw, g.log_r, M.q);
+}
+
+// N^-1 * wq mod q, canonical (|wq| < 2^63)
+__device__ __forceinline__ u64 leaf_coeff(const SfMod &M, int64_t wq)
+{
+    const u64 a = sf_reduce((u64)(wq < 0 ? -wq : wq), M.q, M.one_p);
+    const u64 v = sf_mul_shoup(a, M.ninv, M.ninv_p, M.q);
+    return (wq < 0 && v) ? M.q - v : v;
+}
+
+// leaf_col: grid (C/16 column tiles, k_in * L, slots).  smem: column
+// twiddles + 1 tile + the powers psi^(C e), e < 2R.
+template <int NT>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 4) k_leaf_col(SfRing R, SfLeafParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ u64 tap_v[SF_LEAF_TAPS];
+    __shared__ int tap_rc[SF_LEAF_TAPS];
+    __shared__ int tap_n;
+    // sparse form: taps sorted by column (start[b] .. start[b+1])
+    __shared__ int col_start[SF_NB + 1];
+    __shared__ int col_fill[SF_NB];
+    __shared__ int srt_t[SF_LEAF_TAPS];
+    const SfGeo g = ring_geo(R);
+    const int c0 = blockIdx.x * SF_NB;
+    const int j = blockIdx.y / R.L, i = blockIdx.y % R.L;
+    const int slot = P.s0 + blockIdx.z * P.s_stride;
+    const int o = leaf_output(P, slot);
+    if (o < 0) return;
+    const SfMod &M = R.m[i];
+    sf_tw *tw = (sf_tw *)smem_raw;
+    u64 *sm = (u64 *)(tw + g.r);
+    sf_tw *pwc = (sf_tw *)(sm + tile_words(g.log_r));
+    const int ne = col_elems(g);
     u64 *dst = P.w1 + (((size_t)blockIdx.z * P.k_in + j) * R.L + i) * R.n;
+    if (threadIdx.x == 0) tap_n = 0;
+    if (threadIdx.x < SF_NB) col_fill[threadIdx.x] = 0;
+    {
+        // stage the powers for the closed form while the taps are gathered
+        const sf_tw *src = R.pwc + (size_t)i * 2 * g.r;
+        for (int e = threadIdx.x; e < 2 * g.r; e += blockDim.x) pwc[e] = src[e];
+    }
+    __syncthreads();
+    leaf_taps(R, g, P, o, j, c0, [&](int row, int col, int64_t wq) {
+        const int t = atomicAdd(&tap_n, 1);
+        if (t < SF_LEAF_TAPS) {
+            tap_v[t] = leaf_coeff(M, wq);
+            tap_rc[t] = (row << 4) | col;
+            atomicAdd(&col_fill[col], 1);
+        }
+    });
+    __syncthreads();
+    const int nt = tap_n;
+    // closed form while nt * R products cost less than the tile's 16 (R/2) log2 R butterflies
+    if (nt <= SF_LEAF_TAPS && nt * 2 <= SF_NB * g.log_r) {
+        // counting sort by column; the order inside a column does not matter (exact sums)
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int b = 0; b < SF_NB; ++b) {
+                col_start[b] = acc;
+                acc += col_fill[b];
+                col_fill[b] = col_start[b];
+            }
+            col_start[SF_NB] = acc;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) srt_t[atomicAdd(&col_fill[tap_rc[t] & 15], 1)] = t;
+        __syncthreads();
+        const unsigned emask = 2u * g.r - 1;
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+            const int k = e >> 4, b = e & 15;
+            const unsigned br2 = 2u * (__brev((unsigned)k) >> (32 - g.log_r)) + 1u;
+            u64 acc = 0;
+            for (int t = col_start[b]; t < col_start[b + 1]; ++t) {
+                const int tt = srt_t[t];
+                const sf_tw z = pwc[(((unsigned)tap_rc[tt] >> 4) * br2) & emask];
+                acc += sf_mul_shoup_lazy(tap_v[tt], z.x, z.y, M.q);
+            }
+            dst[col_gidx(g, c0, e)] = sf_reduce(acc, M.q, M.one_p);
+        }
+        return;
+    }
+    for (int e = threadIdx.x; e < tile_words(g.log_r); e += blockDim.x) sm[e] = 0;
+    load_col_tw(tw, R.colT_f, g, i);
+    __syncthreads();
+    if (nt <= SF_LEAF_TAPS) {
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) sm[(tap_rc[t] >> 4) * SF_PAD + (tap_rc[t] & 15)] = tap_v[t];
+    } else {
+        leaf_taps(R, g, P, o, j, c0, [&](int row, int col, int64_t wq) { sm[row * SF_PAD + col] = leaf_coeff(M, wq); });
+    }
+    __syncthreads();
+    col_forward<NT>(sm, tw, g.log_r, M.q);
     for (int e = threadIdx.x; e < ne; e += blockDim.x) dst[col_gidx(g, c0, e)] = sm[col_slot(e)];
 }
 
 // leaf_row: grid (R/16 row tiles, L, slots).  smem: forward row twiddles + 1 tile.
-template <int EPT>
-__global__ void __launch_bounds__(SF_THREADS, EPT >= 16 ? 1 : 3) k_leaf_row(SfRing R, SfLeafParams P)
+template <int EPT, int NT>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (EPT >= 16 ? 1 : 3)) k_leaf_row(SfRing R, SfLeafParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SfGeo g = ring_geo(R);
@@ -86,7 +173,7 @@ __global__ void __launch_bounds__(SF_THREADS, EPT >= 16 ? 1 : 3) k_leaf_row(SfRi
     if (o < 0) {
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
-            const int e = threadIdx.x + k * SF_THREADS;
+            const int e = threadIdx.x + k * NT;
             da[e] = 0;
             db[e] = 0;
         }
@@ -105,12 +192,12 @@ __global__ void __launch_bounds__(SF_THREADS, EPT >= 16 ? 1 : 3) k_leaf_row(SfRi
         const u64 *src = P.w1 + (((size_t)blockIdx.z * P.k_in + j) * R.L + i) * R.n + tile_off;
         for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) sm[row_slot(g, e)] = src[e];
         __syncthreads();
-        row_forward(sm, tw, g.log_c, M.q);
+        row_forward<NT>(sm, tw, g.log_c, M.q);
         const u64 *ca = P.ct_mont + (((size_t)j * 2 + 0) * R.L + i) * R.n + tile_off;
         const u64 *cb = P.ct_mont + (((size_t)j * 2 + 1) * R.L + i) * R.n + tile_off;
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
-            const int e = threadIdx.x + k * SF_THREADS;
+            const int e = threadIdx.x + k * NT;
             const u64 w = sm[row_slot(g, e)];
             const u64 xa = __ldg(ca + e), xb = __ldg(cb + e);
             acc_a[k] += sf_redc_lazy(sf_mulhi(w, xa), w * xa, M.q, M.qinv_neg);
@@ -120,7 +207,7 @@ __global__ void __launch_bounds__(SF_THREADS, EPT >= 16 ? 1 : 3) k_leaf_row(SfRi
     }
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
-        const int e = threadIdx.x + k * SF_THREADS;
+        const int e = threadIdx.x + k * NT;
         da[e] = sf_reduce(acc_a[k], M.q, M.one_p);
         db[e] = sf_reduce(acc_b[k], M.q, M.one_p);
     }
@@ -130,7 +217,7 @@ sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStre
 {
     const SfRing &R = ctx->ring;
     if (cnt <= 0) return SF_OK;
-    const size_t smem_c = sf_smem_col(R, 1), smem_r = sf_smem_row(R, 1);
+    const size_t smem_c = sf_smem_leaf_col(R), smem_r = sf_smem_row(R, 1);
     cudaEvent_t ev;
     for (int off = 0; off < cnt; off += 65535) {
         SfLeafParams p = P;
@@ -139,17 +226,21 @@ sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStre
         p.w1 = P.w1;    // w1 holds `cnt` slots; reuse from its start for each sub-launch
         p.leaves = P.leaves + P.leaf_stride * off;
         sf_launch_begin(ctx, SFK_LEAF_COL, st, &ev);
-        k_leaf_col<<<dim3(R.c / SF_NB, P.k_in * R.L, c), SF_THREADS, smem_c, st>>>(R, p);
+        SF_NT_DISPATCH(sf_tile_threads(R.log_r), k_leaf_col<NT><<<dim3(R.c / SF_NB, P.k_in * R.L, c), NT, smem_c, st>>>(R, p););
         sf_launch_end(ctx, SFK_LEAF_COL, st, ev);
         sf_launch_begin(ctx, SFK_LEAF_ROW, st, &ev);
         const dim3 gr(R.r / SF_NB, R.L, c);
-        switch ((R.c * SF_NB) / SF_THREADS) {
-        case 2: k_leaf_row<2><<<gr, SF_THREADS, smem_r, st>>>(R, p); break;
-        case 4: k_leaf_row<4><<<gr, SF_THREADS, smem_r, st>>>(R, p); break;
-        case 8: k_leaf_row<8><<<gr, SF_THREADS, smem_r, st>>>(R, p); break;
-        case 16: k_leaf_row<16><<<gr, SF_THREADS, smem_r, st>>>(R, p); break;
-        default: return sf_set_error(SF_EINVAL, "unsupported ring split");
-        }
+        const int ntr = sf_tile_threads(R.log_c);
+        sf_status bad = SF_OK;
+        SF_NT_DISPATCH(ntr, {
+            switch ((R.c * SF_NB) / NT) {
+            case 2: k_leaf_row<2, NT><<<gr, NT, smem_r, st>>>(R, p); break;
+            case 4: k_leaf_row<4, NT><<<gr, NT, smem_r, st>>>(R, p); break;
+            case 8: k_leaf_row<8, NT><<<gr, NT, smem_r, st>>>(R, p); break;
+            default: bad = SF_EINVAL;
+            }
+        });
+        if (bad != SF_OK) return sf_set_error(SF_EINVAL, "unsupported ring split");
         sf_launch_end(ctx, SFK_LEAF_ROW, st, ev);
     }
     SF_CUDA_TRY(cudaGetLastError());
@@ -355,10 +446,19 @@ sf_status sf_extract_launch(sf_ctx *ctx, const u64 *ct, u64 *out, int i, cudaStr
 sf_status sf_layer_init_attributes()
 {
     const int mx = 227 * 1024;
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_leaf_col, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_leaf_row<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_leaf_row<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_leaf_row<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_leaf_row<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+#define SF_LEAF_ATTRS(NT)                                                                                    \
+    {                                                                                                        \
+        /* the tap list is static shared memory: the dynamic part gets the rest */                          \
+        cudaFuncAttributes fa;                                                                               \
+        SF_CUDA_TRY(cudaFuncGetAttributes(&fa, k_leaf_col<NT>));                                             \
+        SF_CUDA_TRY(cudaFuncSetAttribute(k_leaf_col<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                                         mx - (int)fa.sharedSizeBytes));                                     \
+        SF_CUDA_TRY(cudaFuncSetAttribute((k_leaf_row<2, NT>), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)); \
+        SF_CUDA_TRY(cudaFuncSetAttribute((k_leaf_row<4, NT>), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)); \
+        SF_CUDA_TRY(cudaFuncSetAttribute((k_leaf_row<8, NT>), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)); \
+    }
+    SF_LEAF_ATTRS(256)
+    SF_LEAF_ATTRS(512)
+#undef SF_LEAF_ATTRS
     return SF_OK;
 }

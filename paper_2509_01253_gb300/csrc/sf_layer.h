@@ -5,6 +5,7 @@
 struct SfTermDev {
     int in_offset, H, W, C_in, C_out, kh, kw, stride, pad;
     int w_off;  // offset of this term's weights in the concatenated array
+    int tap_off; // first entry of this term in the tap table
 };
 
 // Launch slot z computes slot s = s0 + z * s_stride, i.e. output sig_out[s]
@@ -18,6 +19,7 @@ struct SfLeafParams {
     int s_stride;
     int n_slots_valid;
     const int64_t *wq;      // quantised weights (device)
+    const int4 *taps;       // tap geometry table (see sf_layer)
     const int *pos_of;      // input index -> stream position (null = identity)
     const int *sig_out;     // slot -> output index (null = identity)
     const u64 *ct_mont;     // [k_in][2][L][N] NTT domain, Montgomery form

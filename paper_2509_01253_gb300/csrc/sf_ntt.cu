@@ -8,8 +8,8 @@
 // the tile.  Forward = column pass (reads job.src) then row pass (reduces to
 // [0, q)); inverse = row pass (reads job.src) then column pass (multiplies by
 // N^-1 and reduces).  Later passes work in place on job.dst.
-template <bool INV, bool COLS>
-__global__ void __launch_bounds__(SF_THREADS) k_ntt_pass(SfRing R, SfJobList jobs)
+template <bool INV, bool COLS, int NT>
+__global__ void __launch_bounds__(NT) k_ntt_pass(SfRing R, SfJobList jobs)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SfPolyJob jb = jobs.j[blockIdx.y];
@@ -24,8 +24,8 @@ __global__ void __launch_bounds__(SF_THREADS) k_ntt_pass(SfRing R, SfJobList job
         load_col_tw(tw, INV ? R.colT_i : R.colT_f, g, jb.mod);
         for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) s[col_slot(e)] = src[col_gidx(g, c0, e)];
         __syncthreads();
-        if (INV) col_inverse(s, tw, g.log_r, M.q);
-        else col_forward(s, tw, g.log_r, M.q);
+        if (INV) col_inverse<NT>(s, tw, g.log_r, M.q);
+        else col_forward<NT>(s, tw, g.log_r, M.q);
         for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) {
             u64 v = s[col_slot(e)];
             if (INV) v = sf_csub(sf_mul_shoup_lazy(v, M.ninv, M.ninv_p, M.q), M.q);
@@ -38,8 +38,8 @@ __global__ void __launch_bounds__(SF_THREADS) k_ntt_pass(SfRing R, SfJobList job
         const u64 *s0 = src + (size_t)r0 * g.c;
         for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) s[row_slot(g, e)] = s0[e];
         __syncthreads();
-        if (INV) row_inverse(s, tw, g.log_c, M.q);
-        else row_forward(s, tw, g.log_c, M.q);
+        if (INV) row_inverse<NT>(s, tw, g.log_c, M.q);
+        else row_forward<NT>(s, tw, g.log_c, M.q);
         u64 *d0 = jb.dst + (size_t)r0 * g.c;
         for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) {
             u64 v = s[row_slot(g, e)];
@@ -63,19 +63,20 @@ sf_status sf_ntt_jobs(sf_ctx *ctx, const SfPolyJob *h_jobs, int n_jobs, bool inv
         for (int i = 0; i < cnt; ++i) jl.j[i] = h_jobs[off + i];
         dim3 gc(R.c / SF_TC, cnt), gr(R.r / SF_TR, cnt);
         cudaEvent_t ev;
+        const int ntc = sf_tile_threads(R.log_r), ntr = sf_tile_threads(R.log_c);
         if (!inverse) {
             sf_launch_begin(ctx, SFK_NTT_FWD_COL, st, &ev);
-            k_ntt_pass<false, true><<<gc, SF_THREADS, smem_col, st>>>(R, jl);
+            SF_NT_DISPATCH(ntc, k_ntt_pass<false, true, NT><<<gc, NT, smem_col, st>>>(R, jl););
             sf_launch_end(ctx, SFK_NTT_FWD_COL, st, ev);
             sf_launch_begin(ctx, SFK_NTT_FWD_ROW, st, &ev);
-            k_ntt_pass<false, false><<<gr, SF_THREADS, smem_row, st>>>(R, jl);
+            SF_NT_DISPATCH(ntr, k_ntt_pass<false, false, NT><<<gr, NT, smem_row, st>>>(R, jl););
             sf_launch_end(ctx, SFK_NTT_FWD_ROW, st, ev);
         } else {
             sf_launch_begin(ctx, SFK_NTT_INV_ROW, st, &ev);
-            k_ntt_pass<true, false><<<gr, SF_THREADS, smem_row, st>>>(R, jl);
+            SF_NT_DISPATCH(ntr, k_ntt_pass<true, false, NT><<<gr, NT, smem_row, st>>>(R, jl););
             sf_launch_end(ctx, SFK_NTT_INV_ROW, st, ev);
             sf_launch_begin(ctx, SFK_NTT_INV_COL, st, &ev);
-            k_ntt_pass<true, true><<<gc, SF_THREADS, smem_col, st>>>(R, jl);
+            SF_NT_DISPATCH(ntc, k_ntt_pass<true, true, NT><<<gc, NT, smem_col, st>>>(R, jl););
             sf_launch_end(ctx, SFK_NTT_INV_COL, st, ev);
         }
     }
@@ -265,9 +266,13 @@ sf_status sf_rotkey_finish(sf_ctx *ctx, const u64 *alpha, const u64 *e, const u6
 sf_status sf_ntt_init_attributes()
 {
     const int mx = 227 * 1024;
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_ntt_pass<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_ntt_pass<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_ntt_pass<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_ntt_pass<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+#define SF_NTT_ATTR(NT)                                                                                             \
+    SF_CUDA_TRY(cudaFuncSetAttribute(k_ntt_pass<false, true, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));  \
+    SF_CUDA_TRY(cudaFuncSetAttribute(k_ntt_pass<false, false, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)); \
+    SF_CUDA_TRY(cudaFuncSetAttribute(k_ntt_pass<true, true, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));   \
+    SF_CUDA_TRY(cudaFuncSetAttribute(k_ntt_pass<true, false, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    SF_NTT_ATTR(256)
+    SF_NTT_ATTR(512)
+#undef SF_NTT_ATTR
     return SF_OK;
 }

@@ -53,13 +53,14 @@ static inline SfLeafParams leaf_params(const sf_layer *L)
     size_t off = 0;
     for (size_t t = 0; t < L->terms.size(); ++t) {
         const sf_conv_term &T = L->terms[t];
-        P.t[t] = {T.in_offset, T.H, T.W, T.C_in, T.C_out, T.kh, T.kw, T.stride, T.pad, (int)off};
+        P.t[t] = {T.in_offset, T.H, T.W, T.C_in, T.C_out, T.kh, T.kw, T.stride, T.pad, (int)off, L->tap_off[t]};
         off += (size_t)T.C_out * T.kh * T.kw * T.C_in;
     }
     P.n_terms = (int)L->terms.size();
     P.C_out = L->C_out;
     P.W_out = L->W_out;
     P.wq = L->d_wq;
+    P.taps = L->d_taps;
     return P;
 }
 

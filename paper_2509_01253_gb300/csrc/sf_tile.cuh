@@ -34,6 +34,21 @@
 #define SF_TC SF_NB
 #define SF_TR SF_NB
 #define SF_THREADS 256
+// threads per block of a kernel whose tiles hold sub-transforms of 2^log_s
+// points: 256 (8 warps) up to 128 points, 512 for 256 points, so that every
+// tile size gives each thread the same 8 elements
+__host__ __device__ __forceinline__ int sf_tile_threads(int log_s) { return log_s >= 8 ? 512 : SF_THREADS; }
+// runs the statements with the compile-time block size NT = nt (256 or 512)
+#define SF_NT_DISPATCH(nt, ...)          \
+    do {                                 \
+        if ((nt) == 512) {               \
+            constexpr int NT = 512;      \
+            __VA_ARGS__                  \
+        } else {                         \
+            constexpr int NT = SF_THREADS; \
+            __VA_ARGS__                  \
+        }                                \
+    } while (0)
 
 struct SfGeo {
     int log_n, n, log_r, r, log_c, c;
@@ -46,20 +61,20 @@ __host__ __device__ __forceinline__ int tile_words(int log_s) { return (1 << log
 
 // One sweep of R_ST consecutive stages over every unit of the tile.
 // Forward: halves H0, H0/2, ..., H0 >> (R_ST-1).  Inverse: halves H0, ..., H0 << (R_ST-1).
-template <int LOG_S, int LOG_H0, int R_ST, bool INV, bool ROWTW>
+template <int LOG_S, int LOG_H0, int R_ST, bool INV, bool ROWTW, int NT>
 __device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
 {
     constexpr int S = 1 << LOG_S;
     constexpr int U = 1 << R_ST;
     constexpr int UNITS = SF_NB * S / U;
-    constexpr int ITER = (UNITS + SF_THREADS - 1) / SF_THREADS;
+    constexpr int ITER = (UNITS + NT - 1) / NT;
     constexpr int LOG_STEP = INV ? LOG_H0 : (LOG_H0 - (R_ST - 1));
     constexpr int LOG_BLK = INV ? (LOG_H0 + R_ST) : (LOG_H0 + 1);
     const u64 two_q = 2 * q;
 #pragma unroll
     for (int it = 0; it < ITER; ++it) {
-        const int idx = threadIdx.x + it * SF_THREADS;
-        if ((UNITS % SF_THREADS) != 0 && idx >= UNITS) break;
+        const int idx = threadIdx.x + it * NT;
+        if ((UNITS % NT) != 0 && idx >= UNITS) break;
         const int b = idx & (SF_NB - 1);
         const int u = idx >> 4;
         const int o = u & ((1 << LOG_STEP) - 1);
@@ -88,82 +103,86 @@ __device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
 }
 
 // Forward stages of all 16 sub-transforms of size 2^LOG_S; values in [0, 4q).
-template <int LOG_S, bool ROWTW>
+template <int LOG_S, bool ROWTW, int NT>
 __device__ __forceinline__ void tile_forward_t(u64 *s, const sf_tw *tw, u64 q)
 {
     if constexpr (LOG_S == 5) {
-        tile_sweep<5, 4, 3, false, ROWTW>(s, tw, q);
-        tile_sweep<5, 1, 2, false, ROWTW>(s, tw, q);
+        tile_sweep<5, 4, 3, false, ROWTW, NT>(s, tw, q);
+        tile_sweep<5, 1, 2, false, ROWTW, NT>(s, tw, q);
     } else if constexpr (LOG_S == 6) {
-        tile_sweep<6, 5, 3, false, ROWTW>(s, tw, q);
-        tile_sweep<6, 2, 3, false, ROWTW>(s, tw, q);
+        tile_sweep<6, 5, 3, false, ROWTW, NT>(s, tw, q);
+        tile_sweep<6, 2, 3, false, ROWTW, NT>(s, tw, q);
     } else if constexpr (LOG_S == 7) {
-        tile_sweep<7, 6, 3, false, ROWTW>(s, tw, q);
-        tile_sweep<7, 3, 2, false, ROWTW>(s, tw, q);
-        tile_sweep<7, 1, 2, false, ROWTW>(s, tw, q);
+        tile_sweep<7, 6, 3, false, ROWTW, NT>(s, tw, q);
+        tile_sweep<7, 3, 2, false, ROWTW, NT>(s, tw, q);
+        tile_sweep<7, 1, 2, false, ROWTW, NT>(s, tw, q);
     } else {
-        tile_sweep<8, 7, 3, false, ROWTW>(s, tw, q);
-        tile_sweep<8, 4, 3, false, ROWTW>(s, tw, q);
-        tile_sweep<8, 1, 2, false, ROWTW>(s, tw, q);
+        tile_sweep<8, 7, 3, false, ROWTW, NT>(s, tw, q);
+        tile_sweep<8, 4, 3, false, ROWTW, NT>(s, tw, q);
+        tile_sweep<8, 1, 2, false, ROWTW, NT>(s, tw, q);
     }
 }
 
 // Inverse stages (no N^-1 factor); values in [0, 2q).
-template <int LOG_S, bool ROWTW>
+template <int LOG_S, bool ROWTW, int NT>
 __device__ __forceinline__ void tile_inverse_t(u64 *s, const sf_tw *tw, u64 q)
 {
     if constexpr (LOG_S == 5) {
-        tile_sweep<5, 0, 2, true, ROWTW>(s, tw, q);
-        tile_sweep<5, 2, 3, true, ROWTW>(s, tw, q);
+        tile_sweep<5, 0, 2, true, ROWTW, NT>(s, tw, q);
+        tile_sweep<5, 2, 3, true, ROWTW, NT>(s, tw, q);
     } else if constexpr (LOG_S == 6) {
-        tile_sweep<6, 0, 3, true, ROWTW>(s, tw, q);
-        tile_sweep<6, 3, 3, true, ROWTW>(s, tw, q);
+        tile_sweep<6, 0, 3, true, ROWTW, NT>(s, tw, q);
+        tile_sweep<6, 3, 3, true, ROWTW, NT>(s, tw, q);
     } else if constexpr (LOG_S == 7) {
-        tile_sweep<7, 0, 2, true, ROWTW>(s, tw, q);
-        tile_sweep<7, 2, 2, true, ROWTW>(s, tw, q);
-        tile_sweep<7, 4, 3, true, ROWTW>(s, tw, q);
+        tile_sweep<7, 0, 2, true, ROWTW, NT>(s, tw, q);
+        tile_sweep<7, 2, 2, true, ROWTW, NT>(s, tw, q);
+        tile_sweep<7, 4, 3, true, ROWTW, NT>(s, tw, q);
     } else {
-        tile_sweep<8, 0, 2, true, ROWTW>(s, tw, q);
-        tile_sweep<8, 2, 3, true, ROWTW>(s, tw, q);
-        tile_sweep<8, 5, 3, true, ROWTW>(s, tw, q);
+        tile_sweep<8, 0, 2, true, ROWTW, NT>(s, tw, q);
+        tile_sweep<8, 2, 3, true, ROWTW, NT>(s, tw, q);
+        tile_sweep<8, 5, 3, true, ROWTW, NT>(s, tw, q);
     }
 }
 
 // Runtime dispatch on the sub-transform size (R for columns, C for rows).
+template <int NT = SF_THREADS>
 __device__ __forceinline__ void col_forward(u64 *s, const sf_tw *tw, int log_r, u64 q)
 {
     switch (log_r) {
-    case 5: tile_forward_t<5, false>(s, tw, q); break;
-    case 6: tile_forward_t<6, false>(s, tw, q); break;
-    case 7: tile_forward_t<7, false>(s, tw, q); break;
-    default: tile_forward_t<8, false>(s, tw, q); break;
+    case 5: tile_forward_t<5, false, NT>(s, tw, q); break;
+    case 6: tile_forward_t<6, false, NT>(s, tw, q); break;
+    case 7: tile_forward_t<7, false, NT>(s, tw, q); break;
+    default: tile_forward_t<8, false, NT>(s, tw, q); break;
     }
 }
+template <int NT = SF_THREADS>
 __device__ __forceinline__ void col_inverse(u64 *s, const sf_tw *tw, int log_r, u64 q)
 {
     switch (log_r) {
-    case 5: tile_inverse_t<5, false>(s, tw, q); break;
-    case 6: tile_inverse_t<6, false>(s, tw, q); break;
-    case 7: tile_inverse_t<7, false>(s, tw, q); break;
-    default: tile_inverse_t<8, false>(s, tw, q); break;
+    case 5: tile_inverse_t<5, false, NT>(s, tw, q); break;
+    case 6: tile_inverse_t<6, false, NT>(s, tw, q); break;
+    case 7: tile_inverse_t<7, false, NT>(s, tw, q); break;
+    default: tile_inverse_t<8, false, NT>(s, tw, q); break;
     }
 }
+template <int NT = SF_THREADS>
 __device__ __forceinline__ void row_forward(u64 *s, const sf_tw *tw, int log_c, u64 q)
 {
     switch (log_c) {
-    case 5: tile_forward_t<5, true>(s, tw, q); break;
-    case 6: tile_forward_t<6, true>(s, tw, q); break;
-    case 7: tile_forward_t<7, true>(s, tw, q); break;
-    default: tile_forward_t<8, true>(s, tw, q); break;
+    case 5: tile_forward_t<5, true, NT>(s, tw, q); break;
+    case 6: tile_forward_t<6, true, NT>(s, tw, q); break;
+    case 7: tile_forward_t<7, true, NT>(s, tw, q); break;
+    default: tile_forward_t<8, true, NT>(s, tw, q); break;
     }
 }
+template <int NT = SF_THREADS>
 __device__ __forceinline__ void row_inverse(u64 *s, const sf_tw *tw, int log_c, u64 q)
 {
     switch (log_c) {
-    case 5: tile_inverse_t<5, true>(s, tw, q); break;
-    case 6: tile_inverse_t<6, true>(s, tw, q); break;
-    case 7: tile_inverse_t<7, true>(s, tw, q); break;
-    default: tile_inverse_t<8, true>(s, tw, q); break;
+    case 5: tile_inverse_t<5, true, NT>(s, tw, q); break;
+    case 6: tile_inverse_t<6, true, NT>(s, tw, q); break;
+    case 7: tile_inverse_t<7, true, NT>(s, tw, q); break;
+    default: tile_inverse_t<8, true, NT>(s, tw, q); break;
     }
 }
 

@@ -147,12 +147,14 @@ class Pool:
 class Server:
     """Admission queue + one continuous-batching worker per pool."""
 
-    def __init__(self, pools: dict, route: dict, mem_budget: int, max_queue: int = 64, max_active: int = 16,
+    def __init__(self, pools: dict, route: dict, mem_budget: int, max_queue: int = 64, max_active=16,
                  max_batch: int = 32):
         self.pools = pools                 # pool name -> Pool
         self.route = route                 # network name -> pool name
         self.mem_budget = mem_budget
-        self.max_queue, self.max_active, self.max_batch = max_queue, max_active, max_batch
+        self.max_queue, self.max_batch = max_queue, max_batch
+        # requests a worker may hold: one number for every pool, or per pool
+        self.max_active = max_active if isinstance(max_active, dict) else {p: max_active for p in pools}
         self.lock = threading.Condition()
         self.queue = collections.deque()
         self.inbox = {p: [] for p in pools}
@@ -186,7 +188,7 @@ class Server:
         while self.queue:
             req = self.queue[0]
             p = self.route[req.net]
-            if self.used + req.reserve > self.mem_budget or self.held[p] >= self.max_active:
+            if self.used + req.reserve > self.mem_budget or self.held[p] >= self.max_active[p]:
                 break
             self.queue.popleft()
             self.used += req.reserve
@@ -297,7 +299,13 @@ def run_arrivals(server: Server, arrivals: list, drain: float) -> dict:
     server.shutdown()
     lat = np.array([r.finished - r.arrival for r in server.completed]) if server.completed else np.array([])
     rounds = sum(r.rounds_run for r in server.admitted)
-    per_net = collections.Counter(r.net for r in server.completed)
+    per_net = {}
+    for net in sorted({r.net for r in server.admitted}):
+        ln = np.array([r.finished - r.arrival for r in server.completed if r.net == net])
+        per_net[net] = {"completed": int(ln.size),
+                        "admitted": sum(1 for r in server.admitted if r.net == net),
+                        "p50_latency_s": float(np.percentile(ln, 50)) if ln.size else None,
+                        "p99_latency_s": float(np.percentile(ln, 99)) if ln.size else None}
     return {"arrivals": len(arrivals), "admitted": len(server.admitted), "rejected": len(server.rejected),
             "completed": len(server.completed), "unfinished_at_end": unfinished,
             "rejection_rate": len(server.rejected) / max(1, len(arrivals)),
@@ -306,7 +314,7 @@ def run_arrivals(server: Server, arrivals: list, drain: float) -> dict:
             "layers_per_s": rounds / elapsed, "rounds_run": rounds, "window_s": window, "elapsed_s": elapsed,
             "engine_calls": len(server.batches),
             "mean_rounds_per_call": float(np.mean([b[1] for b in server.batches])) if server.batches else None,
-            "completed_per_network": dict(per_net)}
+            "per_network": per_net}
 
 
 SERVE_MIX = {"resnet20": 0.7, "resnet18": 0.3}
@@ -315,26 +323,25 @@ SERVE_MIX = {"resnet20": 0.7, "resnet18": 0.3}
 def bench(args, device: int) -> int:
     """Serving measurement: ResNet-20 requests at N = 2^14 (3 x 50-bit + 1)
     and ResNet-18 requests at N = 2^15 (4 x 50-bit + 2), 70/30, 4 client keys,
-    Poisson arrivals at each rate of --rates for --duration seconds; then the
-    one-request-at-a-time form of the same networks for comparison."""
+    Poisson arrivals at each rate of --rates for --duration seconds, then up to
+    --drain seconds for admitted requests to finish.  Beside it, one ResNet-20
+    request alone with one engine call per round (the plain form)."""
     import torch
     torch.cuda.set_device(device)
     pools = {"c2": Pool(wl.PARAMS["conv16"], ["resnet20"], 4, device, key_seed=7000),
              "c3": Pool(wl.PARAMS["r18"], ["resnet18"], 4, device, key_seed=8000)}
     route = {"resnet20": "c2", "resnet18": "c3"}
     budget = 48 << 30
+    max_active = {"c2": 16, "c3": 2}
     out = {"metric": "served encrypted layers/s; p50/p99 latency", "unit": "layers/s", "workload": "serve",
-           "mix": SERVE_MIX, "client_keys": 4, "mem_budget_bytes": budget, "rates": {}}
-    # alone: one request of each network, rounds one engine call each
-    alone = {}
-    for net, p in route.items():
-        srv = Server(pools, route, budget, max_active=1, max_batch=1)
-        stats = run_arrivals(srv, [(0.0, net, 0, 99)], drain=600.0)
-        alone[net] = {"latency_s": stats["p50_latency_s"], "layers_per_s": stats["layers_per_s"]}
-    out["alone"] = alone
+           "mix": SERVE_MIX, "client_keys": 4, "mem_budget_bytes": budget, "max_active": max_active,
+           "duration_s": args.duration, "drain_s": args.drain, "rates": {}}
+    srv = Server({"c2": pools["c2"]}, {"resnet20": "c2"}, budget, max_active=1, max_batch=1)
+    stats = run_arrivals(srv, [(0.0, "resnet20", 0, 99)], drain=600.0)
+    out["alone"] = {"resnet20": {"latency_s": stats["p50_latency_s"], "layers_per_s": stats["layers_per_s"]}}
     for rate in [float(r) for r in args.rates.split(",")]:
         arr = poisson_arrivals(rate, args.duration, SERVE_MIX, 4, seed=int(rate * 1000) + 17)
-        srv = Server(pools, route, budget)
+        srv = Server(pools, route, budget, max_active=max_active)
         out["rates"][str(rate)] = run_arrivals(srv, arr, args.drain)
     for p in pools.values():
         p.destroy()

@@ -19,7 +19,8 @@ def pools():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
     torch.cuda.set_device(0)
     p = {"p12": serve.Pool(wl.PARAMS["fc64"], ["tiny_a"], 2, 0, key_seed=11),
-         "p14": serve.Pool(wl.PARAMS["conv16"], ["tiny_a", "tiny_b"], 2, 0, key_seed=21)}
+         "p14": serve.Pool(wl.PARAMS["conv16"], ["tiny_a", "tiny_b", "resnet20"], 2, 0, key_seed=21,
+                           engine_budget=1 << 30)}
     yield p
     for x in p.values():
         x.destroy()
@@ -67,3 +68,27 @@ def test_served_results_equal_alone(pools):
     assert max(b[1] for b in srv.batches) == 2        # calls held several requests
     for req in srv.completed:
         assert np.array_equal(req.logits, alone[req.request_seed]), req.request_seed
+
+
+def test_served_resnet20_mix_equals_alone(pools):
+    """Full ResNet-20 requests (N = 2^14, groups of 8192 split into units of
+    leaves under a 1 GiB engine budget) under two client keys, three at a time
+    in one engine call: identical to each request alone."""
+    route = {"resnet20": "p14"}
+    specs = [("resnet20", 0, 41), ("resnet20", 1, 42), ("resnet20", 0, 43)]
+    alone = {seed: _alone(pools["p14"], net, key, seed).logits() for net, key, seed in specs}
+    srv = serve.Server({"p14": pools["p14"]}, route, mem_budget=1 << 36, max_queue=8, max_active=3, max_batch=3)
+    srv.start()
+    import time
+    for i, (net, key, seed) in enumerate(specs):
+        assert srv.submit(serve.make_request(i, net, key, seed))
+    t_end = time.perf_counter() + 600
+    while not srv.idle() and time.perf_counter() < t_end and not srv.errors:
+        time.sleep(0.02)
+    srv.shutdown()
+    assert len(srv.completed) == 3
+    assert max(b[1] for b in srv.batches) == 3
+    for req in srv.completed:
+        assert np.array_equal(req.logits, alone[req.request_seed]), req.request_seed
+    ref = nw.float_forward(pools["p14"].nets["resnet20"], wl.network_input("resnet20", 41))
+    assert np.abs(alone[41] - ref).max() <= 1e-3

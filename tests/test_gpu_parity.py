@@ -430,6 +430,28 @@ def test_eval_layers_batch_matches_single_rounds():
             assert n_outs == [i["n_groups"] for i in infos]
             for o, want in zip(outs, single):
                 assert (from_dev(o) == want).all()
+        # rounds under two different client keys in one call (one class of units per key)
+        sk2 = sf.sf_keygen(s.ctx, 83)
+        rk2 = sf.sf_gen_rotation_keys(s.ctx, sk2, None, 84)
+        rks = [s.rk if x % 2 == 0 else rk2 for x in range(len(lays))]
+        sf.sf_ctx_set_option(s.ctx, "mem_budget", 64 << 30)
+        single2 = []
+        for x in range(len(lays)):
+            o = dev_zeros(infos[x]["n_groups"], 2, L, s.n)
+            sf.sf_eval_linear_layer(s.ctx, lays[x], rks[x], ins[x], infos[x]["k_in"], cases[x].sigma_prev,
+                                    cases[x].sigma_out, o, infos[x]["n_groups"])
+            single2.append(from_dev(o))
+        for budget in (None, 6 << 20):
+            if budget:
+                sf.sf_ctx_set_option(s.ctx, "mem_budget", budget)
+            outs = [dev_zeros(i["n_groups"], 2, L, s.n) for i in infos]
+            sf.sf_eval_layers(s.ctx, lays, rks, ins, [i["k_in"] for i in infos], [c.sigma_prev for c in cases],
+                              [c.sigma_out for c in cases], outs, [i["n_groups"] for i in infos])
+            sf.sf_sync(s.ctx)
+            for x, (o, want) in enumerate(zip(outs, single2)):
+                assert (from_dev(o) == want).all(), (budget, x)
+        sf.sf_rotkeys_destroy(rk2)
+        sf.sf_secret_key_destroy(sk2)
         best, ms = sf.sf_autotune_layers(s.ctx, lays, [s.rk] * len(lays), ins, [i["k_in"] for i in infos],
                                          [c.sigma_prev for c in cases], [c.sigma_out for c in cases], outs,
                                          [i["n_groups"] for i in infos], repeats=1)
@@ -438,5 +460,70 @@ def test_eval_layers_batch_matches_single_rounds():
             assert (from_dev(o) == want).all()
         for lay in lays:
             sf.sf_layer_destroy(lay)
+    finally:
+        s.close()
+
+
+# ------------------------------------------------------ large rings (2^15, 2^16) --
+# Rings whose tiles hold 256-point sub-transforms run the 512-thread kernel
+# variants (rows at N = 2^15; rows and columns at N = 2^16).
+
+def test_large_ring_layer_bit_exact(oracle):
+    """A small FC round on the ResNet-18 ring (N = 2^15, 4 x 50-bit + 2
+    special, two-limb digits) end to end: 4 outputs packed into one ciphertext
+    (3 tree merges + 13 trace steps), every residue against the oracle."""
+    ps = wl.PARAMS["r18"]
+    case = wl.fc_case(61, 24, 4, bias=True)
+    delta = wsc = 2.0 ** 20           # bias at scale 2^40 fits int64
+    s = Session.from_set(ps, sk_seed=63, rk_seed=65)
+    try:
+        lay, info, msg, _, got = _run_layer(s, case, delta, delta * wsc, wsc)
+        assert info["group_size"] == 4 and info["ks_count"] == 3 + 13
+        prm = oracle_params(oracle, ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits)
+        want, _, ks = _oracle_layer_run(oracle, prm, case, msg, wsc, delta * wsc, 63, 65, info["k_in"])
+        assert ks == 16
+        assert (got == want).all()
+        vals = sf.sf_decode(s.params, s.decrypt(to_dev(got), 1), 1, s.n // 4, 4, delta * wsc)
+        assert np.abs(vals - wl.float_reference(case)[case.sigma_out.astype(np.int64)]).max() <= 1e-3
+        sf.sf_layer_destroy(lay)
+    finally:
+        s.close()
+
+
+def test_largest_ring_rotate_and_leaves(oracle):
+    """The ResNet-34 ring (N = 2^16, 5 x 50-bit + 2 special, uneven last
+    digit): one rotation against the oracle's textbook key switch, and sampled
+    leaves of a conv round with three input ciphertexts against its direct
+    product."""
+    ps = wl.PARAMS["r34"]
+    s = Session.from_set(ps, sk_seed=71, rk_seed=72, rot_d=[3])
+    try:
+        prm = oracle_params(oracle, ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits)
+        s_o = oracle.keygen(prm, 71)
+        keys = oracle.rotation_keys(prm, s_o, 72, [3])
+        msg = np.random.default_rng(5).integers(-2 ** 40, 2 ** 40, s.n)
+        d_ct = s.encrypt(msg, 73, 1)
+        ct = from_dev(d_ct).reshape(2, s.L, s.n)
+        out = dev_zeros(1, 2, s.L, s.n)
+        sf.sf_rotate(s.ctx, s.rk, 3, d_ct, out, 1)
+        assert (from_dev(out)[0] == oracle.rotate(prm, keys, 3, ct)).all()
+        # leaves: stride-2 3x3 conv 16 -> 8 on 96x96x16 plus a 1x1 stride-2 shortcut term: 5 input cts
+        case = wl.small_conv_case(75, 96, 96, 16, 8, stride=2, shortcut=True)
+        lay = gpu_layer(s, case, ps.delta, ps.delta ** 2)
+        info = sf.sf_layer_get_info(s.ctx, lay)
+        assert info["k_in"] == 5
+        xs = stream_input(case)
+        qmsg = sf.sf_encode_input(xs, ps.delta)
+        d_in = s.encrypt(qmsg, 77, info["k_in"])
+        cts = from_dev(d_in).reshape(info["k_in"], 2, s.L, s.n)
+        olay = oracle_layer(oracle, case, ps.delta, ps.delta ** 2)
+        sample = np.random.default_rng(11).choice(info["E_out"], 6, replace=False).astype(np.int32)
+        sample[0] = 0
+        d_leaf = dev_zeros(len(sample), 2, s.L, s.n)
+        sf.sf_linear_outputs(s.ctx, lay, d_in, info["k_in"], case.sigma_prev, sample, d_leaf)
+        leaves = from_dev(d_leaf)
+        for t, o in enumerate(sample):
+            assert (leaves[t] == oracle.linear_output(prm, olay, cts, int(o), case.sigma_prev)).all(), o
+        sf.sf_layer_destroy(lay)
     finally:
         s.close()
