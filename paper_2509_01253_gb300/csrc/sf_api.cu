@@ -326,6 +326,8 @@ extern "C" sf_status sf_encode_weights(sf_ctx *ctx, const sf_conv_term *terms, i
     L->d_terms = nullptr;
     L->d_taps = nullptr;
     std::vector<int4> taps;
+    L->max_taps = 0;
+    for (int t = 0; t < n_terms; ++t) L->max_taps += terms[t].kh * terms[t].kw * terms[t].C_in;
     for (int t = 0; t < n_terms; ++t) {
         const sf_conv_term &T = terms[t];
         L->tap_off.push_back((int)taps.size());
@@ -413,11 +415,11 @@ extern "C" sf_status sf_linear_outputs(sf_ctx *ctx, const sf_layer *L, const uin
     if (h_sigma_prev) SF_TRY(check_perm(h_sigma_prev, L->E_in, "sigma_prev"));
     cudaStream_t st = (cudaStream_t)stream;
     const size_t ct = ct_words(ctx);
-    const int LB = std::min(leaf_batch_slots(R, k_in), n_outputs);
+    const int LB = std::min(leaf_batch_slots(R, k_in, L->max_taps), n_outputs);
     Carver cv;
     size_t o_ct = cv.take((size_t)k_in * ct), o_pos = cv.take(((size_t)L->E_in + 1) / 2),
            o_sig = cv.take(((size_t)n_outputs + 1) / 2), o_w1 = cv.take((size_t)LB * k_in * R.L * R.n),
-           o_lv = cv.take((size_t)n_outputs * ct);
+           o_lv = cv.take((size_t)n_outputs * ct), o_tap = cv.take(sf_leaf_tap_words(R, k_in, L->max_taps, LB));
     void *w = nullptr;
     SF_TRY(sf_scratch(ctx, cv.words * sizeof(u64), &w));
     u64 *ws = (u64 *)w;
@@ -432,6 +434,7 @@ extern "C" sf_status sf_linear_outputs(sf_ctx *ctx, const sf_layer *L, const uin
     P.sig_out = d_sig;
     P.ct_mont = ws + o_ct;
     P.w1 = ws + o_w1;
+    sf_leaf_tap_bind(R, P, ws + o_tap, LB);
     P.n_slots_valid = n_outputs;
     P.leaf_stride = ct;
     P.s_stride = 1;

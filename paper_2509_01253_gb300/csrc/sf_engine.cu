@@ -71,9 +71,12 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
     const SfRing &R = ctx->ring;
     const size_t ct = ct_words(ctx), ct_bytes = ct * sizeof(u64);
     const int batch = ctx->ks_batch;
-    int max_k_in = 1;
-    for (auto &j : jobs) max_k_in = std::max(max_k_in, j.k_in);
-    const int LB = leaf_batch_slots(R, max_k_in);
+    int max_k_in = 1, max_taps = 1;
+    for (auto &j : jobs) {
+        max_k_in = std::max(max_k_in, j.k_in);
+        max_taps = std::max(max_taps, j.L->max_taps);
+    }
+    const int LB = leaf_batch_slots(R, max_k_in, max_taps);
     // ---- classes and units
     std::vector<Class> classes;
     for (int x = 0; x < (int)jobs.size(); ++x) {
@@ -113,6 +116,7 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
         o_sig[x] = cv.take(((size_t)jobs[x].L->E_out + 1) / 2);
     }
     const size_t o_w1 = cv.take((size_t)LB * max_k_in * R.L * R.n);
+    const size_t o_tap = cv.take(sf_leaf_tap_words(R, max_k_in, max_taps, LB));
     size_t roots_bytes = 0;
     for (auto &c : classes)
         if (c.nch > 1) roots_bytes += (size_t)c.groups.size() * c.nch * ct_bytes * 3 / 2;
@@ -160,6 +164,7 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
             P.sig_out = j.so ? j.d_sig : nullptr;
             P.ct_mont = j.d_ct;
             P.w1 = d_w1;
+            sf_leaf_tap_bind(R, P, ws + o_tap, LB);
             P.n_slots_valid = j.L->E_out;
             P.leaf_stride = ct;
             for (int t0 = 0; t0 < cnt; t0 += LB) {

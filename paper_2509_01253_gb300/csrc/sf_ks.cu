@@ -118,23 +118,23 @@ __device__ __forceinline__ u64 merge_v(const SfRing &R, const SfKsBatch &B, cons
 // gridDim.x = n_groups * bpg.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void issue_row_tile(u64 *dst, const u64 *src, const SfGeo &g)
-{
-    for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) sf_cp8(dst + row_slot(g, e), src + e);
-}
-__device__ __forceinline__ void issue_col_tile(u64 *dst, const u64 *src, const SfGeo &g, int c0)
-{
-    for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) sf_cp8(dst + col_slot(e), src + col_gidx(g, c0, e));
-}
 
 // Elementwise: TA[b][i][j] = tau_d(E - X^s O).a at slot j (a slot permutation).
-// grid (N/256, L, merges): no integer division on the element path.
-__global__ void k_ks_gather(SfRing R, SfKsBatch B)
+// grid (N / (256 SF_EW), L, merges): each thread does SF_EW slots, so the
+// per-merge pointers are set up once per thread.
+#define SF_EW 8
+__global__ void __launch_bounds__(256) k_ks_gather(SfRing R, SfKsBatch B)
 {
     const int b = blockIdx.z, i = blockIdx.y;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const u64 *E = merge_E(B, b), *O = merge_O(B, b);
-    ks_layout(R, B, b).ta[((size_t)i << R.log_n) + j] = merge_u(R, B, E, O, 0, i, auto_src(j, B.d, R.log_n));
+    u64 *ta = ks_layout(R, B, b).ta + ((size_t)i << R.log_n);
+    const int j0 = blockIdx.x * (256 * SF_EW) + threadIdx.x;
+#pragma unroll
+    for (int x = 0; x < SF_EW; ++x) {
+        const int j = j0 + x * 256;
+        if (j >= R.n) break;   // rings smaller than one block's 256 SF_EW slots
+        ta[j] = merge_u(R, B, E, O, 0, i, auto_src(j, B.d, R.log_n));
+    }
 }
 
 // Generic row pass over a per-merge set of npoly polynomials in the scratch:
@@ -145,34 +145,36 @@ struct SfRowSet {
     int npoly, mod_base, mod_period;
 };
 
-template <bool INV, int NT>
-__global__ void __launch_bounds__(NT) k_rows(SfRing R, SfKsBatch B, SfRowSet S, int bpg)
+template <bool INV, int LR, int LC>
+__global__ void __launch_bounds__(SfThreads<LC>::value) k_rows(SfRing R, SfKsBatch B, SfRowSet S, int bpg)
 {
+    constexpr int NT = SfThreads<LC>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SfGeo g = ring_geo(R);
+    constexpr SfGeoT<LR, LC> g{};
     const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
     const int t = grp % S.npoly, r0 = (grp / S.npoly) * SF_NB;
     const int mod = S.mod_base + t % S.mod_period;
     const SfMod M = R.m[mod];
     const size_t per = sf_ks_scratch_words_dev(R);
-    const size_t off_s = S.src_off + ((size_t)t << R.log_n) + (size_t)r0 * g.c;
-    const size_t off_d = S.dst_off + ((size_t)t << R.log_n) + (size_t)r0 * g.c;
+    const size_t off_s = S.src_off + ((size_t)t << (LR + LC)) + (size_t)r0 * g.c;
+    const size_t off_d = S.dst_off + ((size_t)t << (LR + LC)) + (size_t)r0 * g.c;
     sf_tw *tw = (sf_tw *)smem_raw;
     u64 *buf0 = (u64 *)(tw + SF_NB * g.c);
     u64 *buf1 = buf0 + tile_words(g.log_c);
-    load_row_tw(tw, INV ? R.rowT_i : R.rowT_f, g, mod, r0);
-    if (sub < B.count) issue_row_tile(buf0, B.scratch + per * sub + off_s, g);
+    load_row_tw_t<LR, LC, NT>(tw, INV ? R.rowT_i : R.rowT_f, mod, r0);
+    if (sub < B.count) issue_row_tile_t<LC, NT>(buf0, B.scratch + per * sub + off_s);
     sf_cp_commit();
     for (int k = 0, b = sub; b < B.count; ++k, b += bpg) {
         u64 *cur = (k & 1) ? buf1 : buf0, *nxt = (k & 1) ? buf0 : buf1;
-        if (b + bpg < B.count) issue_row_tile(nxt, B.scratch + per * (b + bpg) + off_s, g);
+        if (b + bpg < B.count) issue_row_tile_t<LC, NT>(nxt, B.scratch + per * (b + bpg) + off_s);
         sf_cp_commit();
         sf_cp_wait<1>();
         __syncthreads();
-        if (INV) row_inverse<NT>(cur, tw, g.log_c, M.q);
-        else row_forward<NT>(cur, tw, g.log_c, M.q);
+        if (INV) tile_inverse_t<LC, true, NT>(cur, tw, M.q);
+        else tile_forward_t<LC, true, NT>(cur, tw, M.q);
         u64 *dst = B.scratch + per * b + off_d;
-        for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) dst[e] = cur[row_slot(g, e)];
+        #pragma unroll
+        for (int e = threadIdx.x; e < (SF_NB << LC); e += NT) dst[e] = cur[row_slot_t<LC>(e)];
         __syncthreads();
     }
 }
@@ -180,11 +182,12 @@ __global__ void __launch_bounds__(NT) k_rows(SfRing R, SfKsBatch B, SfRowSet S, 
 // ModUp.  Groups: (column tile, digit j); items: merges.  smem: inverse and
 // forward column tables of every modulus, two buffers of nd source tiles, one
 // work tile.
-template <int NT>
-__global__ void __launch_bounds__(NT) k_ks2(SfRing R, SfKsBatch B, int bpg)
+template <int LR, int LC>
+__global__ void __launch_bounds__(SfThreads<LR>::value) k_ks2(SfRing R, SfKsBatch B, int bpg)
 {
+    constexpr int NT = SfThreads<LR>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SfGeo g = ring_geo(R);
+    constexpr SfGeoT<LR, LC> g{};
     const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
     const int j = grp % R.dnum, c0 = (grp / R.dnum) * SF_NB;
     const int lo = j * R.K, hi = min((j + 1) * R.K, R.L), nd = hi - lo;
@@ -194,19 +197,19 @@ __global__ void __launch_bounds__(NT) k_ks2(SfRing R, SfKsBatch B, int bpg)
     u64 *bufs = (u64 *)(twf + (size_t)R.nm * g.r);  // 2 x nd tiles
     u64 *work = bufs + (size_t)2 * nd * tw_words;
     for (int m = 0; m < R.nm; ++m) {
-        load_col_tw(twi + (size_t)m * g.r, R.colT_i, g, m);
-        load_col_tw(twf + (size_t)m * g.r, R.colT_f, g, m);
+        load_col_tw_t<LR, NT>(twi + (size_t)m * g.r, R.colT_i, m);
+        load_col_tw_t<LR, NT>(twf + (size_t)m * g.r, R.colT_f, m);
     }
     if (sub < B.count) {
         const KsLayout Lo = ks_layout(R, B, sub);
-        for (int t = 0; t < nd; ++t) issue_col_tile(bufs + (size_t)t * tw_words, Lo.x1 + ((size_t)(lo + t) << R.log_n), g, c0);
+        for (int t = 0; t < nd; ++t) issue_col_tile_t<LR, LC, NT>(bufs + (size_t)t * tw_words, Lo.x1 + ((size_t)(lo + t) << (LR + LC)), c0);
     }
     sf_cp_commit();
     for (int k = 0, b = sub; b < B.count; ++k, b += bpg) {
         u64 *cur = bufs + (size_t)(k & 1) * nd * tw_words, *nxt = bufs + (size_t)((k + 1) & 1) * nd * tw_words;
         if (b + bpg < B.count) {
             const KsLayout Ln = ks_layout(R, B, b + bpg);
-            for (int t = 0; t < nd; ++t) issue_col_tile(nxt + (size_t)t * tw_words, Ln.x1 + ((size_t)(lo + t) << R.log_n), g, c0);
+            for (int t = 0; t < nd; ++t) issue_col_tile_t<LR, LC, NT>(nxt + (size_t)t * tw_words, Ln.x1 + ((size_t)(lo + t) << (LR + LC)), c0);
         }
         sf_cp_commit();
         sf_cp_wait<1>();
@@ -215,9 +218,10 @@ __global__ void __launch_bounds__(NT) k_ks2(SfRing R, SfKsBatch B, int bpg)
         for (int t = 0; t < nd; ++t) {
             const int i = lo + t;
             u64 *st = cur + (size_t)t * tw_words;
-            col_inverse<NT>(st, twi + (size_t)i * g.r, g.log_r, R.m[i].q);
+            tile_inverse_t<LR, false, NT>(st, twi + (size_t)i * g.r, R.m[i].q);
             const u64 w = R.mu_inv[j * R.K + t], wp = R.mu_inv_p[j * R.K + t];
-            for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x)
+            #pragma unroll
+            for (int e = threadIdx.x; e < (SF_NB << LR); e += NT)
                 st[col_slot(e)] = sf_mul_shoup(st[col_slot(e)], w, wp, R.m[i].q);
         }
         __syncthreads();
@@ -225,7 +229,8 @@ __global__ void __launch_bounds__(NT) k_ks2(SfRing R, SfKsBatch B, int bpg)
         for (int m = 0; m < R.nm; ++m) {
             if (m >= lo && m < hi) continue;
             const SfMod &M = R.m[m];
-            for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) {
+            #pragma unroll
+            for (int e = threadIdx.x; e < (SF_NB << LR); e += NT) {
                 const int sl = col_slot(e);
                 u64 acc = 0;
                 for (int t = 0; t < nd; ++t) {
@@ -235,9 +240,10 @@ __global__ void __launch_bounds__(NT) k_ks2(SfRing R, SfKsBatch B, int bpg)
                 work[sl] = acc;
             }
             __syncthreads();
-            col_forward<NT>(work, twf + (size_t)m * g.r, g.log_r, M.q);
-            u64 *dst = Lo.x2 + ((size_t)(j * R.nm + m) << R.log_n);
-            for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) dst[col_gidx(g, c0, e)] = work[col_slot(e)];
+            tile_forward_t<LR, false, NT>(work, twf + (size_t)m * g.r, M.q);
+            u64 *dst = Lo.x2 + ((size_t)(j * R.nm + m) << (LR + LC));
+            #pragma unroll
+            for (int e = threadIdx.x; e < (SF_NB << LR); e += NT) dst[col_gidx_t<LC>(c0, e)] = work[col_slot(e)];
             __syncthreads();
         }
     }
@@ -247,11 +253,12 @@ __global__ void __launch_bounds__(NT) k_ks2(SfRing R, SfKsBatch B, int bpg)
 // each taking dnum steps (one per digit) whose tiles are double-buffered.
 // Output: ACC (data moduli, NTT domain) or, for the special moduli, their NTT
 // values in the x1 region (the inverse row pass runs in k_rows<true>).
-template <int EPT, int NT>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (EPT >= 16 ? 1 : 3)) k_ks3(SfRing R, SfKsBatch B, int bpg)
+template <int LR, int LC>
+__global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 512 ? 1 : 3) k_ks3(SfRing R, SfKsBatch B, int bpg)
 {
+    constexpr int NT = SfThreads<LC>::value, EPT = (SF_NB << LC) / NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SfGeo g = ring_geo(R);
+    constexpr SfGeoT<LR, LC> g{};
     const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
     const int m = grp % R.nm, r0 = (grp / R.nm) * SF_NB;
     const SfMod M = R.m[m];
@@ -259,14 +266,14 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (EPT >= 16 ? 1 : 3)) k_ks3
     sf_tw *tw = (sf_tw *)smem_raw;
     u64 *buf0 = (u64 *)(tw + SF_NB * g.c);
     u64 *buf1 = buf0 + tile_words(g.log_c);
-    load_row_tw(tw, R.rowT_f, g, m, r0);
+    load_row_tw_t<LR, LC, NT>(tw, R.rowT_f, m, r0);
     const int n_mine = sub < B.count ? (B.count - sub + bpg - 1) / bpg : 0;
     const int steps = n_mine * R.dnum;
     // step k -> merge sub + (k / dnum) * bpg, digit k % dnum
     if (steps > 0) {
         const KsLayout Lo = ks_layout(R, B, sub);
         const bool own = (m < min(R.K, R.L));
-        issue_row_tile(buf0, (own ? Lo.ta + ((size_t)m << R.log_n) : Lo.x2 + ((size_t)m << R.log_n)) + tile_off, g);
+        issue_row_tile_t<LC, NT>(buf0, (own ? Lo.ta + ((size_t)m << (LR + LC)) : Lo.x2 + ((size_t)m << (LR + LC))) + tile_off);
     }
     sf_cp_commit();
     u64 acc_a[EPT], acc_b[EPT];
@@ -279,20 +286,20 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (EPT >= 16 ? 1 : 3)) k_ks3
             const int bn = sub + ((k + 1) / R.dnum) * bpg, jn = (k + 1) % R.dnum;
             const KsLayout Ln = ks_layout(R, B, bn);
             const bool own_n = (m >= jn * R.K && m < min((jn + 1) * R.K, R.L));
-            issue_row_tile(nxt, (own_n ? Ln.ta + ((size_t)m << R.log_n) : Ln.x2 + ((size_t)(jn * R.nm + m) << R.log_n)) + tile_off, g);
+            issue_row_tile_t<LC, NT>(nxt, (own_n ? Ln.ta + ((size_t)m << (LR + LC)) : Ln.x2 + ((size_t)(jn * R.nm + m) << (LR + LC))) + tile_off);
         }
         sf_cp_commit();
         sf_cp_wait<1>();
         __syncthreads();
         const bool own = (m >= j * R.K && m < min((j + 1) * R.K, R.L));
-        if (!own) row_forward<NT>(cur, tw, g.log_c, M.q);
-        const u64 *ka = B.key + ((((size_t)j * 2 + 0) * R.nm + m) << R.log_n) + tile_off;
-        const u64 *kb = B.key + ((((size_t)j * 2 + 1) * R.nm + m) << R.log_n) + tile_off;
+        if (!own) tile_forward_t<LC, true, NT>(cur, tw, M.q);
+        const u64 *ka = B.key + ((((size_t)j * 2 + 0) * R.nm + m) << (LR + LC)) + tile_off;
+        const u64 *kb = B.key + ((((size_t)j * 2 + 1) * R.nm + m) << (LR + LC)) + tile_off;
         // per digit c * key (c lazy < 36q, key < q) is Montgomery-reduced into [0, 2q) and summed
 #pragma unroll
         for (int x = 0; x < EPT; ++x) {
             const int e = threadIdx.x + x * NT;
-            const u64 c = cur[row_slot(g, e)];
+            const u64 c = cur[row_slot_t<LC>(e)];
             const u64 xa = __ldg(ka + e), xb = __ldg(kb + e);
             acc_a[x] += sf_redc_lazy(sf_mulhi(c, xa), c * xa, M.q, M.qinv_neg);
             acc_b[x] += sf_redc_lazy(sf_mulhi(c, xb), c * xb, M.q, M.qinv_neg);
@@ -301,11 +308,11 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (EPT >= 16 ? 1 : 3)) k_ks3
             const KsLayout Lo = ks_layout(R, B, b);
             u64 *da, *db;
             if (m < R.L) {
-                da = Lo.accq + ((size_t)m << R.log_n) + tile_off;
-                db = Lo.accq + ((size_t)(R.L + m) << R.log_n) + tile_off;
+                da = Lo.accq + ((size_t)m << (LR + LC)) + tile_off;
+                db = Lo.accq + ((size_t)(R.L + m) << (LR + LC)) + tile_off;
             } else {
-                da = Lo.x1 + ((size_t)(m - R.L) << R.log_n) + tile_off;
-                db = Lo.x1 + ((size_t)(R.K + m - R.L) << R.log_n) + tile_off;
+                da = Lo.x1 + ((size_t)(m - R.L) << (LR + LC)) + tile_off;
+                db = Lo.x1 + ((size_t)(R.K + m - R.L) << (LR + LC)) + tile_off;
             }
 #pragma unroll
             for (int x = 0; x < EPT; ++x) {
@@ -322,11 +329,12 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (EPT >= 16 ? 1 : 3)) k_ks3
 // ModDown conversion.  Groups: (column tile, part p); items: merges.  smem: K
 // inverse (special) + L forward (data) column tables, two buffers of K tiles,
 // one work tile.
-template <int NT>
-__global__ void __launch_bounds__(NT) k_ks4(SfRing R, SfKsBatch B, int bpg)
+template <int LR, int LC>
+__global__ void __launch_bounds__(SfThreads<LR>::value) k_ks4(SfRing R, SfKsBatch B, int bpg)
 {
+    constexpr int NT = SfThreads<LR>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SfGeo g = ring_geo(R);
+    constexpr SfGeoT<LR, LC> g{};
     const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
     const int p = grp % 2, c0 = (grp / 2) * SF_NB;
     const int tw_words = tile_words(g.log_r);
@@ -334,12 +342,12 @@ __global__ void __launch_bounds__(NT) k_ks4(SfRing R, SfKsBatch B, int bpg)
     sf_tw *twf = twi + (size_t)R.K * g.r;           // [L][R] forward, data moduli
     u64 *bufs = (u64 *)(twf + (size_t)R.L * g.r);   // 2 x K tiles
     u64 *work = bufs + (size_t)2 * R.K * tw_words;
-    for (int k = 0; k < R.K; ++k) load_col_tw(twi + (size_t)k * g.r, R.colT_i, g, R.L + k);
-    for (int i = 0; i < R.L; ++i) load_col_tw(twf + (size_t)i * g.r, R.colT_f, g, i);
+    for (int k = 0; k < R.K; ++k) load_col_tw_t<LR, NT>(twi + (size_t)k * g.r, R.colT_i, R.L + k);
+    for (int i = 0; i < R.L; ++i) load_col_tw_t<LR, NT>(twf + (size_t)i * g.r, R.colT_f, i);
     if (sub < B.count) {
         const KsLayout Lo = ks_layout(R, B, sub);
         for (int k = 0; k < R.K; ++k)
-            issue_col_tile(bufs + (size_t)k * tw_words, Lo.x1 + ((size_t)(p * R.K + k) << R.log_n), g, c0);
+            issue_col_tile_t<LR, LC, NT>(bufs + (size_t)k * tw_words, Lo.x1 + ((size_t)(p * R.K + k) << (LR + LC)), c0);
     }
     sf_cp_commit();
     for (int kk = 0, b = sub; b < B.count; ++kk, b += bpg) {
@@ -347,7 +355,7 @@ __global__ void __launch_bounds__(NT) k_ks4(SfRing R, SfKsBatch B, int bpg)
         if (b + bpg < B.count) {
             const KsLayout Ln = ks_layout(R, B, b + bpg);
             for (int k = 0; k < R.K; ++k)
-                issue_col_tile(nxt + (size_t)k * tw_words, Ln.x1 + ((size_t)(p * R.K + k) << R.log_n), g, c0);
+                issue_col_tile_t<LR, LC, NT>(nxt + (size_t)k * tw_words, Ln.x1 + ((size_t)(p * R.K + k) << (LR + LC)), c0);
         }
         sf_cp_commit();
         sf_cp_wait<1>();
@@ -355,16 +363,18 @@ __global__ void __launch_bounds__(NT) k_ks4(SfRing R, SfKsBatch B, int bpg)
         for (int k = 0; k < R.K; ++k) {
             const int m = R.L + k;
             u64 *st = cur + (size_t)k * tw_words;
-            col_inverse<NT>(st, twi + (size_t)k * g.r, g.log_r, R.m[m].q);
+            tile_inverse_t<LR, false, NT>(st, twi + (size_t)k * g.r, R.m[m].q);
             const u64 w = R.md_inv[k], wp = R.md_inv_p[k];
-            for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x)
+            #pragma unroll
+            for (int e = threadIdx.x; e < (SF_NB << LR); e += NT)
                 st[col_slot(e)] = sf_mul_shoup(st[col_slot(e)], w, wp, R.m[m].q);
         }
         __syncthreads();
         const KsLayout Lo = ks_layout(R, B, b);
         for (int i = 0; i < R.L; ++i) {
             const SfMod &M = R.m[i];
-            for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) {
+            #pragma unroll
+            for (int e = threadIdx.x; e < (SF_NB << LR); e += NT) {
                 const int sl = col_slot(e);
                 u64 acc = 0;
                 for (int k = 0; k < R.K; ++k) {
@@ -374,9 +384,10 @@ __global__ void __launch_bounds__(NT) k_ks4(SfRing R, SfKsBatch B, int bpg)
                 work[sl] = acc;
             }
             __syncthreads();
-            col_forward<NT>(work, twf + (size_t)i * g.r, g.log_r, M.q);
-            u64 *dst = Lo.x2 + ((size_t)(p * R.L + i) << R.log_n);
-            for (int e = threadIdx.x; e < col_elems(g); e += blockDim.x) dst[col_gidx(g, c0, e)] = work[col_slot(e)];
+            tile_forward_t<LR, false, NT>(work, twf + (size_t)i * g.r, M.q);
+            u64 *dst = Lo.x2 + ((size_t)(p * R.L + i) << (LR + LC));
+            #pragma unroll
+            for (int e = threadIdx.x; e < (SF_NB << LR); e += NT) dst[col_gidx_t<LC>(c0, e)] = work[col_slot(e)];
             __syncthreads();
         }
     }
@@ -385,11 +396,12 @@ __global__ void __launch_bounds__(NT) k_ks4(SfRing R, SfKsBatch B, int bpg)
 // ModDown finish.  Groups: (row tile, limb i); items: (merge b, part p).
 // RES = (ACC - conv) P^-1 written over ACC.  smem: forward row twiddles, two
 // buffers of (conversion tile, ACC tile).
-template <int NT>
-__global__ void __launch_bounds__(NT) k_ks5(SfRing R, SfKsBatch B, int bpg)
+template <int LR, int LC>
+__global__ void __launch_bounds__(SfThreads<LC>::value) k_ks5(SfRing R, SfKsBatch B, int bpg)
 {
+    constexpr int NT = SfThreads<LC>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SfGeo g = ring_geo(R);
+    constexpr SfGeoT<LR, LC> g{};
     const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
     const int i = grp % R.L, r0 = (grp / R.L) * SF_NB;
     const SfMod M = R.m[i];
@@ -397,13 +409,13 @@ __global__ void __launch_bounds__(NT) k_ks5(SfRing R, SfKsBatch B, int bpg)
     const int tw_words = tile_words(g.log_c);
     sf_tw *tw = (sf_tw *)smem_raw;
     u64 *bufs = (u64 *)(tw + SF_NB * g.c);          // 2 x (conv, acc)
-    load_row_tw(tw, R.rowT_f, g, i, r0);
+    load_row_tw_t<LR, LC, NT>(tw, R.rowT_f, i, r0);
     const int n_items = 2 * B.count;
     if (sub < n_items) {
         const KsLayout Lo = ks_layout(R, B, sub >> 1);
         const int p = sub & 1;
-        issue_row_tile(bufs, Lo.x2 + ((size_t)(p * R.L + i) << R.log_n) + tile_off, g);
-        issue_row_tile(bufs + tw_words, Lo.accq + ((size_t)(p * R.L + i) << R.log_n) + tile_off, g);
+        issue_row_tile_t<LC, NT>(bufs, Lo.x2 + ((size_t)(p * R.L + i) << (LR + LC)) + tile_off);
+        issue_row_tile_t<LC, NT>(bufs + tw_words, Lo.accq + ((size_t)(p * R.L + i) << (LR + LC)) + tile_off);
     }
     sf_cp_commit();
     const u64 pinv = R.md_pinv[i], pinv_p = R.md_pinv_p[i];
@@ -412,17 +424,18 @@ __global__ void __launch_bounds__(NT) k_ks5(SfRing R, SfKsBatch B, int bpg)
         if (it + bpg < n_items) {
             const KsLayout Ln = ks_layout(R, B, (it + bpg) >> 1);
             const int pn = (it + bpg) & 1;
-            issue_row_tile(nxt, Ln.x2 + ((size_t)(pn * R.L + i) << R.log_n) + tile_off, g);
-            issue_row_tile(nxt + tw_words, Ln.accq + ((size_t)(pn * R.L + i) << R.log_n) + tile_off, g);
+            issue_row_tile_t<LC, NT>(nxt, Ln.x2 + ((size_t)(pn * R.L + i) << (LR + LC)) + tile_off);
+            issue_row_tile_t<LC, NT>(nxt + tw_words, Ln.accq + ((size_t)(pn * R.L + i) << (LR + LC)) + tile_off);
         }
         sf_cp_commit();
         sf_cp_wait<1>();
         __syncthreads();
-        row_forward<NT>(cur, tw, g.log_c, M.q);
+        tile_forward_t<LC, true, NT>(cur, tw, M.q);
         const int b = it >> 1, p = it & 1;
-        u64 *dst = ks_layout(R, B, b).accq + ((size_t)(p * R.L + i) << R.log_n) + tile_off;
-        for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) {
-            const int sl = row_slot(g, e);
+        u64 *dst = ks_layout(R, B, b).accq + ((size_t)(p * R.L + i) << (LR + LC)) + tile_off;
+        #pragma unroll
+        for (int e = threadIdx.x; e < (SF_NB << LC); e += NT) {
+            const int sl = row_slot_t<LC>(e);
             const u64 conv = sf_reduce(cur[sl], M.q, M.one_p);
             dst[e] = sf_mul_shoup(sf_sub(cur[tw_words + sl], conv, M.q), pinv, pinv_p, M.q);
         }
@@ -431,19 +444,26 @@ __global__ void __launch_bounds__(NT) k_ks5(SfRing R, SfKsBatch B, int bpg)
 }
 
 // Elementwise merge: out = [add_v] (E + X^s O) + RES, plus tau_d(u.b) on part b.
-// grid (N/256, 2L, merges): no integer division on the element path.
-__global__ void k_ks_merge(SfRing R, SfKsBatch B)
+// grid (N / (256 SF_EW), 2L, merges), SF_EW slots per thread.
+__global__ void __launch_bounds__(256) k_ks_merge(SfRing R, SfKsBatch B)
 {
     const int b = blockIdx.z, pi = blockIdx.y;
     const int p = pi >= R.L ? 1 : 0, i = pi - p * R.L;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const u64 *E = merge_E(B, b), *O = merge_O(B, b);
-    const size_t w = ((size_t)pi << R.log_n) + j;
     const u64 q = R.m[i].q;
-    u64 res = ks_layout(R, B, b).accq[w];
-    if (B.add_v) res = sf_add(res, merge_v(R, B, E, O, p, i, j), q);
-    if (p == 1) res = sf_add(res, merge_u(R, B, E, O, 1, i, auto_src(j, B.d, R.log_n)), q);
-    merge_out(B, b)[w] = res;
+    const size_t base = (size_t)pi << R.log_n;
+    const u64 *res_in = ks_layout(R, B, b).accq + base;
+    u64 *out = merge_out(B, b) + base;
+    const int j0 = blockIdx.x * (256 * SF_EW) + threadIdx.x;
+#pragma unroll
+    for (int x = 0; x < SF_EW; ++x) {
+        const int j = j0 + x * 256;
+        if (j >= R.n) break;
+        u64 res = res_in[j];
+        if (B.add_v) res = sf_add(res, merge_v(R, B, E, O, p, i, j), q);
+        if (p == 1) res = sf_add(res, merge_u(R, B, E, O, 1, i, auto_src(j, B.d, R.log_n)), q);
+        out[j] = res;
+    }
 }
 
 // ------------------------------------------------------------ launching ----
@@ -475,13 +495,6 @@ static int blocks_per_group(const sf_ctx *ctx, int occ, int n_groups, int n_item
     return std::max(1, std::min(bpg, n_items));
 }
 
-#define SF_KS3_CASE(E)                                                                        \
-    case E: {                                                                                 \
-        const int bpg = blocks_per_group(ctx, occupancy(k_ks3<E, NT>, NT, sm3), ng, b.count); \
-        k_ks3<E, NT><<<ng * bpg, NT, sm3, st>>>(R, b, bpg);                                   \
-        break;                                                                                \
-    }
-
 sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
 {
     const SfRing &R = ctx->ring;
@@ -493,83 +506,77 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
     const size_t sm3 = smem_rows(R, 2);
     const size_t sm4 = sizeof(sf_tw) * (R.K + R.L) * R.r + sizeof(u64) * tile_words(R.log_r) * (2 * R.K + 1);
     const size_t sm5 = smem_rows(R, 4);
-    const int ntr = sf_tile_threads(R.log_c), ntc = sf_tile_threads(R.log_r);
-    const int ept = (R.c * SF_NB) / ntr;
     cudaEvent_t ev;
     for (int off = 0; off < B0.count; off += 32768) {
         SfKsBatch b = B0;
         b.count = std::min(32768, B0.count - off);
         b.first = B0.first + off;
         b.scratch += sf_ks_scratch_words(R) * off;
-        const dim3 eg(R.n / 256, R.L, b.count), mg(R.n / 256, 2 * R.L, b.count);
+        const int ew_blocks = (R.n + 256 * SF_EW - 1) / (256 * SF_EW);
+        const dim3 eg(ew_blocks, R.L, b.count), mg(ew_blocks, 2 * R.L, b.count);
+        SF_GEO_DISPATCH(R.log_n, {
+            constexpr int NTR = SfThreads<LC>::value, NTC = SfThreads<LR>::value;
+            sf_launch_begin(ctx, SFK_KS_GATHER, st, &ev);
+            k_ks_gather<<<eg, 256, 0, st>>>(R, b);
+            sf_launch_end(ctx, SFK_KS_GATHER, st, ev);
 
-        sf_launch_begin(ctx, SFK_KS_GATHER, st, &ev);
-        k_ks_gather<<<eg, 256, 0, st>>>(R, b);
-        sf_launch_end(ctx, SFK_KS_GATHER, st, ev);
-        sf_launch_begin(ctx, SFK_KS1_INV_ROW, st, &ev);
-        SF_NT_DISPATCH(ntr, {
-            const SfRowSet S{0, (size_t)R.L << R.log_n, R.L, 0, R.L};   // TA -> X1
-            const int ng = rtiles * S.npoly;
-            const int bpg = blocks_per_group(ctx, occupancy(k_rows<true, NT>, NT, sm_rows), ng, b.count);
-            k_rows<true, NT><<<ng * bpg, NT, sm_rows, st>>>(R, b, S, bpg);
-        });
-        sf_launch_end(ctx, SFK_KS1_INV_ROW, st, ev);
+            sf_launch_begin(ctx, SFK_KS1_INV_ROW, st, &ev);
+            {
+                const SfRowSet S{0, (size_t)R.L << R.log_n, R.L, 0, R.L};   // TA -> X1
+                const int ng = rtiles * S.npoly;
+                const int bpg = blocks_per_group(ctx, occupancy(k_rows<true, LR, LC>, NTR, sm_rows), ng, b.count);
+                k_rows<true, LR, LC><<<ng * bpg, NTR, sm_rows, st>>>(R, b, S, bpg);
+            }
+            sf_launch_end(ctx, SFK_KS1_INV_ROW, st, ev);
 
-        sf_launch_begin(ctx, SFK_KS2_MODUP_COL, st, &ev);
-        SF_NT_DISPATCH(ntc, {
-            const int ng = ctiles * R.dnum;
-            const int bpg = blocks_per_group(ctx, occupancy(k_ks2<NT>, NT, sm2), ng, b.count);
-            k_ks2<NT><<<ng * bpg, NT, sm2, st>>>(R, b, bpg);
-        });
-        sf_launch_end(ctx, SFK_KS2_MODUP_COL, st, ev);
+            sf_launch_begin(ctx, SFK_KS2_MODUP_COL, st, &ev);
+            {
+                const int ng = ctiles * R.dnum;
+                const int bpg = blocks_per_group(ctx, occupancy(k_ks2<LR, LC>, NTC, sm2), ng, b.count);
+                k_ks2<LR, LC><<<ng * bpg, NTC, sm2, st>>>(R, b, bpg);
+            }
+            sf_launch_end(ctx, SFK_KS2_MODUP_COL, st, ev);
 
-        sf_launch_begin(ctx, SFK_KS3_INNER_ROW, st, &ev);
-        {
-            const int ng = rtiles * R.nm;
-            sf_status bad = SF_OK;
-            SF_NT_DISPATCH(ntr, {
-                switch (ept) {
-                    SF_KS3_CASE(2) SF_KS3_CASE(4) SF_KS3_CASE(8)
-                default: bad = SF_EINVAL;
-                }
-            });
-            if (bad != SF_OK) return sf_set_error(SF_EINVAL, "unsupported ring split");
-        }
-        sf_launch_end(ctx, SFK_KS3_INNER_ROW, st, ev);
-        sf_launch_begin(ctx, SFK_KS3_INV_ROW_P, st, &ev);
-        SF_NT_DISPATCH(ntr, {
-            // inverse row pass of the special limbs' accumulators, in place in x1
-            const SfRowSet S{(size_t)R.L << R.log_n, (size_t)R.L << R.log_n, 2 * R.K, R.L, R.K};
-            const int ng2 = rtiles * S.npoly;
-            const int bpg2 = blocks_per_group(ctx, occupancy(k_rows<true, NT>, NT, sm_rows), ng2, b.count);
-            k_rows<true, NT><<<ng2 * bpg2, NT, sm_rows, st>>>(R, b, S, bpg2);
-        });
-        sf_launch_end(ctx, SFK_KS3_INV_ROW_P, st, ev);
+            sf_launch_begin(ctx, SFK_KS3_INNER_ROW, st, &ev);
+            {
+                const int ng = rtiles * R.nm;
+                const int bpg = blocks_per_group(ctx, occupancy(k_ks3<LR, LC>, NTR, sm3), ng, b.count);
+                k_ks3<LR, LC><<<ng * bpg, NTR, sm3, st>>>(R, b, bpg);
+            }
+            sf_launch_end(ctx, SFK_KS3_INNER_ROW, st, ev);
+            sf_launch_begin(ctx, SFK_KS3_INV_ROW_P, st, &ev);
+            {
+                // inverse row pass of the special limbs' accumulators, in place in x1
+                const SfRowSet S{(size_t)R.L << R.log_n, (size_t)R.L << R.log_n, 2 * R.K, R.L, R.K};
+                const int ng2 = rtiles * S.npoly;
+                const int bpg2 = blocks_per_group(ctx, occupancy(k_rows<true, LR, LC>, NTR, sm_rows), ng2, b.count);
+                k_rows<true, LR, LC><<<ng2 * bpg2, NTR, sm_rows, st>>>(R, b, S, bpg2);
+            }
+            sf_launch_end(ctx, SFK_KS3_INV_ROW_P, st, ev);
 
-        sf_launch_begin(ctx, SFK_KS4_MODDOWN_COL, st, &ev);
-        SF_NT_DISPATCH(ntc, {
-            const int ng = ctiles * 2;
-            const int bpg = blocks_per_group(ctx, occupancy(k_ks4<NT>, NT, sm4), ng, b.count);
-            k_ks4<NT><<<ng * bpg, NT, sm4, st>>>(R, b, bpg);
-        });
-        sf_launch_end(ctx, SFK_KS4_MODDOWN_COL, st, ev);
+            sf_launch_begin(ctx, SFK_KS4_MODDOWN_COL, st, &ev);
+            {
+                const int ng = ctiles * 2;
+                const int bpg = blocks_per_group(ctx, occupancy(k_ks4<LR, LC>, NTC, sm4), ng, b.count);
+                k_ks4<LR, LC><<<ng * bpg, NTC, sm4, st>>>(R, b, bpg);
+            }
+            sf_launch_end(ctx, SFK_KS4_MODDOWN_COL, st, ev);
 
-        sf_launch_begin(ctx, SFK_KS5_FINISH_ROW, st, &ev);
-        SF_NT_DISPATCH(ntr, {
-            const int ng = rtiles * R.L;
-            const int bpg = blocks_per_group(ctx, occupancy(k_ks5<NT>, NT, sm5), ng, 2 * b.count);
-            k_ks5<NT><<<ng * bpg, NT, sm5, st>>>(R, b, bpg);
+            sf_launch_begin(ctx, SFK_KS5_FINISH_ROW, st, &ev);
+            {
+                const int ng = rtiles * R.L;
+                const int bpg = blocks_per_group(ctx, occupancy(k_ks5<LR, LC>, NTR, sm5), ng, 2 * b.count);
+                k_ks5<LR, LC><<<ng * bpg, NTR, sm5, st>>>(R, b, bpg);
+            }
+            sf_launch_end(ctx, SFK_KS5_FINISH_ROW, st, ev);
+            sf_launch_begin(ctx, SFK_KS_MERGE, st, &ev);
+            k_ks_merge<<<mg, 256, 0, st>>>(R, b);
+            sf_launch_end(ctx, SFK_KS_MERGE, st, ev);
         });
-        sf_launch_end(ctx, SFK_KS5_FINISH_ROW, st, ev);
-        sf_launch_begin(ctx, SFK_KS_MERGE, st, &ev);
-        k_ks_merge<<<mg, 256, 0, st>>>(R, b);
-        sf_launch_end(ctx, SFK_KS_MERGE, st, ev);
     }
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
 }
-
-#undef SF_KS3_CASE
 
 // Runs `count` merges sharing (d, s, add_v, key) in launch batches.
 sf_status sf_ks_run(sf_ctx *ctx, SfKsBatch B, u64 *scratch, int batch, cudaStream_t st)
@@ -592,12 +599,11 @@ sf_status sf_ks_init_attributes()
 {
     const int mx = 227 * 1024;
 #define SF_KS_ATTR(K) SF_CUDA_TRY(cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-#define SF_KS_ATTRS(NT)                                                                                  \
-    SF_KS_ATTR((k_rows<true, NT>)) SF_KS_ATTR((k_rows<false, NT>)) SF_KS_ATTR(k_ks2<NT>)                 \
-    SF_KS_ATTR((k_ks3<2, NT>)) SF_KS_ATTR((k_ks3<4, NT>)) SF_KS_ATTR((k_ks3<8, NT>)) SF_KS_ATTR(k_ks4<NT>) \
-    SF_KS_ATTR(k_ks5<NT>)
-    SF_KS_ATTRS(256)
-    SF_KS_ATTRS(512)
+#define SF_KS_ATTRS(LR, LC)                                                                                  \
+    SF_KS_ATTR((k_rows<true, LR, LC>)) SF_KS_ATTR((k_ks2<LR, LC>)) SF_KS_ATTR((k_ks3<LR, LC>))               \
+    SF_KS_ATTR((k_ks4<LR, LC>)) SF_KS_ATTR((k_ks5<LR, LC>))
+    SF_KS_ATTRS(5, 5) SF_KS_ATTRS(5, 6) SF_KS_ATTRS(6, 6) SF_KS_ATTRS(6, 7) SF_KS_ATTRS(7, 7) SF_KS_ATTRS(7, 8)
+    SF_KS_ATTRS(8, 8)
 #undef SF_KS_ATTRS
 #undef SF_KS_ATTR
     return SF_OK;

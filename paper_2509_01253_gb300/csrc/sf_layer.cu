@@ -32,12 +32,12 @@ __device__ __forceinline__ int leaf_output(const SfLeafParams &P, int slot)
 
 size_t sf_smem_leaf_col(const SfRing &R) { return sf_smem_col(R, 1) + sizeof(sf_tw) * 2 * R.r; }
 
-// Calls f(row, column in tile, signed Wq) for every tap of output o that
-// lands in ciphertext j inside the 16 columns from c0; the sign carries the
-// X^-k = -X^(N-k) of the extraction.  Threads split the taps.
+// Calls f(j, row, column, signed Wq) for every tap of output o: input
+// ciphertext j, and the coefficient N - k (or 0) of w_{o,j} it lands on as
+// (row, column) of the R x C split; the sign carries the X^-k = -X^(N-k) of
+// the extraction.  Threads split the taps.
 template <class F>
-__device__ __forceinline__ void leaf_taps(const SfRing &R, const SfGeo &g, const SfLeafParams &P, int o, int j, int c0,
-                                          F f)
+__device__ __forceinline__ void leaf_taps_all(const SfRing &R, const SfGeo &g, const SfLeafParams &P, int o, F f)
 {
     const int co = o % P.C_out, hw = o / P.C_out;
     const int ho = hw / P.W_out, wo = hw % P.W_out;
@@ -53,15 +53,53 @@ __device__ __forceinline__ void leaf_taps(const SfRing &R, const SfGeo &g, const
             if (h < 0 || h >= T.H || w < 0 || w >= T.W) continue;
             const int idx = base + tp.z;
             const int p = P.pos_of ? P.pos_of[idx] : idx;
-            if ((p >> R.log_n) != j) continue;
             const int k = p & (R.n - 1);
             const int cidx = k ? R.n - k : 0;
-            const int col = cidx & (g.c - 1);
-            if (col < c0 || col >= c0 + SF_NB) continue;
             const int64_t wq = wrow[tp.w];
-            f(cidx >> g.log_c, col - c0, k ? -wq : wq);
+            f(p >> R.log_n, cidx >> g.log_c, cidx & (g.c - 1), k ? -wq : wq);
         }
     }
+}
+
+size_t sf_leaf_tap_words(const SfRing &R, int k_in, int max_taps, int slots)
+{
+    const size_t nb = (size_t)k_in * (R.c / SF_NB) + 1;
+    return (size_t)slots * max_taps * 2 + (slots * nb + 1) / 2;
+}
+
+// leaf_prep: grid (slots).  Buckets the taps of each slot's output by
+// (input ciphertext, column tile) with a counting sort, so that a column
+// block reads its own taps instead of scanning the whole receptive field.
+#define SF_MAX_BUCKETS 4096
+__global__ void __launch_bounds__(256) k_leaf_prep(SfRing R, SfLeafParams P)
+{
+    __shared__ int cnt[SF_MAX_BUCKETS + 1];
+    const SfGeo g = ring_geo(R);
+    const int z = blockIdx.x;
+    const int o = leaf_output(P, P.s0 + z * P.s_stride);
+    if (o < 0) return;   // leaf_col skips this slot as well
+    const int nb = P.n_buckets, tiles = g.c / SF_NB;
+    int *off = P.tap_off + (size_t)z * (nb + 1);
+    for (int b = threadIdx.x; b <= nb; b += blockDim.x) cnt[b] = 0;
+    __syncthreads();
+    leaf_taps_all(R, g, P, o, [&](int j, int row, int col, int64_t) { atomicAdd(&cnt[j * tiles + (col >> 4)], 1); });
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int b = 0; b < nb; ++b) {
+            const int c = cnt[b];
+            cnt[b] = acc;
+            off[b] = acc;
+            acc += c;
+        }
+        off[nb] = acc;
+    }
+    __syncthreads();
+    longlong2 *dst = P.tap_buf + (size_t)z * P.max_taps;
+    leaf_taps_all(R, g, P, o, [&](int j, int row, int col, int64_t wq) {
+        const int pos = atomicAdd(&cnt[j * tiles + (col >> 4)], 1);
+        dst[pos] = make_longlong2((row << 4) | (col & 15), wq);
+    });
 }
 
 // N^-1 * wq mod q, canonical (|wq| < 2^63)
@@ -74,18 +112,18 @@ __device__ __forceinline__ u64 leaf_coeff(const SfMod &M, int64_t wq)
 
 // leaf_col: grid (C/16 column tiles, k_in * L, slots).  smem: column
 // twiddles + 1 tile + the powers psi^(C e), e < 2R.
-template <int NT>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 4) k_leaf_col(SfRing R, SfLeafParams P)
+template <int LR, int LC>
+__global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 512 ? 2 : 4) k_leaf_col(SfRing R, SfLeafParams P)
 {
+    constexpr int NT = SfThreads<LR>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ u64 tap_v[SF_LEAF_TAPS];
     __shared__ int tap_rc[SF_LEAF_TAPS];
-    __shared__ int tap_n;
     // sparse form: taps sorted by column (start[b] .. start[b+1])
     __shared__ int col_start[SF_NB + 1];
     __shared__ int col_fill[SF_NB];
     __shared__ int srt_t[SF_LEAF_TAPS];
-    const SfGeo g = ring_geo(R);
+    constexpr SfGeoT<LR, LC> g{};
     const int c0 = blockIdx.x * SF_NB;
     const int j = blockIdx.y / R.L, i = blockIdx.y % R.L;
     const int slot = P.s0 + blockIdx.z * P.s_stride;
@@ -95,26 +133,29 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 4) k_leaf_col(SfRing R, Sf
     sf_tw *tw = (sf_tw *)smem_raw;
     u64 *sm = (u64 *)(tw + g.r);
     sf_tw *pwc = (sf_tw *)(sm + tile_words(g.log_r));
-    const int ne = col_elems(g);
-    u64 *dst = P.w1 + (((size_t)blockIdx.z * P.k_in + j) * R.L + i) * R.n;
-    if (threadIdx.x == 0) tap_n = 0;
+    constexpr int ne = SF_NB << LR;
+    u64 *dst = P.w1 + (((size_t)blockIdx.z * P.k_in + j) * R.L + i) * (size_t)(1 << (LR + LC));
+    // this block's bucket of taps (built by leaf_prep)
+    const int *off = P.tap_off + (size_t)blockIdx.z * (P.n_buckets + 1);
+    const int bk = j * (g.c / SF_NB) + blockIdx.x;
+    const int t0 = off[bk], nt = off[bk + 1] - t0;
+    const longlong2 *src = P.tap_buf + (size_t)blockIdx.z * P.max_taps + t0;
     if (threadIdx.x < SF_NB) col_fill[threadIdx.x] = 0;
     {
-        // stage the powers for the closed form while the taps are gathered
-        const sf_tw *src = R.pwc + (size_t)i * 2 * g.r;
-        for (int e = threadIdx.x; e < 2 * g.r; e += blockDim.x) pwc[e] = src[e];
+        // stage the powers for the closed form while the taps load
+        const sf_tw *pw = R.pwc + (size_t)i * 2 * g.r;
+        for (int e = threadIdx.x; e < 2 * g.r; e += blockDim.x) pwc[e] = pw[e];
     }
     __syncthreads();
-    leaf_taps(R, g, P, o, j, c0, [&](int row, int col, int64_t wq) {
-        const int t = atomicAdd(&tap_n, 1);
-        if (t < SF_LEAF_TAPS) {
-            tap_v[t] = leaf_coeff(M, wq);
-            tap_rc[t] = (row << 4) | col;
-            atomicAdd(&col_fill[col], 1);
+    if (nt <= SF_LEAF_TAPS) {
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+            const longlong2 e = src[t];
+            tap_v[t] = leaf_coeff(M, e.y);
+            tap_rc[t] = (int)e.x;
+            atomicAdd(&col_fill[e.x & 15], 1);
         }
-    });
+    }
     __syncthreads();
-    const int nt = tap_n;
     // closed form while nt * R products cost less than the tile's 16 (R/2) log2 R butterflies
     if (nt <= SF_LEAF_TAPS && nt * 2 <= SF_NB * g.log_r) {
         // counting sort by column; the order inside a column does not matter (exact sums)
@@ -131,7 +172,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 4) k_leaf_col(SfRing R, Sf
         for (int t = threadIdx.x; t < nt; t += blockDim.x) srt_t[atomicAdd(&col_fill[tap_rc[t] & 15], 1)] = t;
         __syncthreads();
         const unsigned emask = 2u * g.r - 1;
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        for (int e = threadIdx.x; e < ne; e += NT) {
             const int k = e >> 4, b = e & 15;
             const unsigned br2 = 2u * (__brev((unsigned)k) >> (32 - g.log_r)) + 1u;
             u64 acc = 0;
@@ -140,36 +181,40 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 4) k_leaf_col(SfRing R, Sf
                 const sf_tw z = pwc[(((unsigned)tap_rc[tt] >> 4) * br2) & emask];
                 acc += sf_mul_shoup_lazy(tap_v[tt], z.x, z.y, M.q);
             }
-            dst[col_gidx(g, c0, e)] = sf_reduce(acc, M.q, M.one_p);
+            dst[col_gidx_t<LC>(c0, e)] = sf_reduce(acc, M.q, M.one_p);
         }
         return;
     }
     for (int e = threadIdx.x; e < tile_words(g.log_r); e += blockDim.x) sm[e] = 0;
-    load_col_tw(tw, R.colT_f, g, i);
+    load_col_tw_t<LR, NT>(tw, R.colT_f, i);
     __syncthreads();
     if (nt <= SF_LEAF_TAPS) {
         for (int t = threadIdx.x; t < nt; t += blockDim.x) sm[(tap_rc[t] >> 4) * SF_PAD + (tap_rc[t] & 15)] = tap_v[t];
     } else {
-        leaf_taps(R, g, P, o, j, c0, [&](int row, int col, int64_t wq) { sm[row * SF_PAD + col] = leaf_coeff(M, wq); });
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+            const longlong2 e = src[t];
+            sm[(e.x >> 4) * SF_PAD + (e.x & 15)] = leaf_coeff(M, e.y);
+        }
     }
     __syncthreads();
-    col_forward<NT>(sm, tw, g.log_r, M.q);
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) dst[col_gidx(g, c0, e)] = sm[col_slot(e)];
+    tile_forward_t<LR, false, NT>(sm, tw, M.q);
+    for (int e = threadIdx.x; e < ne; e += NT) dst[col_gidx_t<LC>(c0, e)] = sm[col_slot(e)];
 }
 
 // leaf_row: grid (R/16 row tiles, L, slots).  smem: forward row twiddles + 1 tile.
-template <int EPT, int NT>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (EPT >= 16 ? 1 : 3)) k_leaf_row(SfRing R, SfLeafParams P)
+template <int LR, int LC>
+__global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 512 ? 1 : 3) k_leaf_row(SfRing R, SfLeafParams P)
 {
+    constexpr int NT = SfThreads<LC>::value, EPT = (SF_NB << LC) / NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SfGeo g = ring_geo(R);
+    constexpr SfGeoT<LR, LC> g{};
     const int r0 = blockIdx.x * SF_NB, i = blockIdx.y;
     const int slot = P.s0 + blockIdx.z * P.s_stride;
     const int o = leaf_output(P, slot);
     const size_t tile_off = (size_t)r0 * g.c;
     u64 *leaf = P.leaves + P.leaf_stride * blockIdx.z;
-    u64 *da = leaf + ((size_t)i << R.log_n) + tile_off;
-    u64 *db = leaf + ((size_t)(R.L + i) << R.log_n) + tile_off;
+    u64 *da = leaf + ((size_t)i << (LR + LC)) + tile_off;
+    u64 *db = leaf + ((size_t)(R.L + i) << (LR + LC)) + tile_off;
     if (o < 0) {
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
@@ -182,23 +227,27 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : (EPT >= 16 ? 1 : 3)) k_lea
     sf_tw *tw = (sf_tw *)smem_raw;
     u64 *sm = (u64 *)(tw + SF_NB * g.c);
     const SfMod M = R.m[i];
-    load_row_tw(tw, R.rowT_f, g, i, r0);
+    load_row_tw_t<LR, LC, NT>(tw, R.rowT_f, i, r0);
     // per input ciphertext w * ct (w < 36q lazy, ct < q, Montgomery form) is
     // reduced into [0, 2q) and summed: below 2 q k_in < 2^56 for k_in < 32
     u64 acc_a[EPT], acc_b[EPT];
 #pragma unroll
     for (int k = 0; k < EPT; ++k) acc_a[k] = acc_b[k] = 0;
     for (int j = 0; j < P.k_in; ++j) {
-        const u64 *src = P.w1 + (((size_t)blockIdx.z * P.k_in + j) * R.L + i) * R.n + tile_off;
-        for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) sm[row_slot(g, e)] = src[e];
+        const u64 *src = P.w1 + (((size_t)blockIdx.z * P.k_in + j) * R.L + i) * (size_t)(1 << (LR + LC)) + tile_off;
+#pragma unroll
+        for (int x = 0; x < EPT; ++x) {
+            const int e = threadIdx.x + x * NT;
+            sm[row_slot_t<LC>(e)] = src[e];
+        }
         __syncthreads();
-        row_forward<NT>(sm, tw, g.log_c, M.q);
-        const u64 *ca = P.ct_mont + (((size_t)j * 2 + 0) * R.L + i) * R.n + tile_off;
-        const u64 *cb = P.ct_mont + (((size_t)j * 2 + 1) * R.L + i) * R.n + tile_off;
+        tile_forward_t<LC, true, NT>(sm, tw, M.q);
+        const u64 *ca = P.ct_mont + (((size_t)j * 2 + 0) * R.L + i) * (size_t)(1 << (LR + LC)) + tile_off;
+        const u64 *cb = P.ct_mont + (((size_t)j * 2 + 1) * R.L + i) * (size_t)(1 << (LR + LC)) + tile_off;
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
             const int e = threadIdx.x + k * NT;
-            const u64 w = sm[row_slot(g, e)];
+            const u64 w = sm[row_slot_t<LC>(e)];
             const u64 xa = __ldg(ca + e), xb = __ldg(cb + e);
             acc_a[k] += sf_redc_lazy(sf_mulhi(w, xa), w * xa, M.q, M.qinv_neg);
             acc_b[k] += sf_redc_lazy(sf_mulhi(w, xb), w * xb, M.q, M.qinv_neg);
@@ -225,22 +274,14 @@ sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStre
         p.s0 = P.s0 + off * P.s_stride;
         p.w1 = P.w1;    // w1 holds `cnt` slots; reuse from its start for each sub-launch
         p.leaves = P.leaves + P.leaf_stride * off;
+        if (P.n_buckets > SF_MAX_BUCKETS) return sf_set_error(SF_EINVAL, "too many input ciphertexts for one round");
         sf_launch_begin(ctx, SFK_LEAF_COL, st, &ev);
-        SF_NT_DISPATCH(sf_tile_threads(R.log_r), k_leaf_col<NT><<<dim3(R.c / SF_NB, P.k_in * R.L, c), NT, smem_c, st>>>(R, p););
+        k_leaf_prep<<<c, 256, 0, st>>>(R, p);
+        SF_GEO_DISPATCH(R.log_n, k_leaf_col<LR, LC><<<dim3(R.c / SF_NB, P.k_in * R.L, c), SfThreads<LR>::value, smem_c, st>>>(R, p););
         sf_launch_end(ctx, SFK_LEAF_COL, st, ev);
         sf_launch_begin(ctx, SFK_LEAF_ROW, st, &ev);
         const dim3 gr(R.r / SF_NB, R.L, c);
-        const int ntr = sf_tile_threads(R.log_c);
-        sf_status bad = SF_OK;
-        SF_NT_DISPATCH(ntr, {
-            switch ((R.c * SF_NB) / NT) {
-            case 2: k_leaf_row<2, NT><<<gr, NT, smem_r, st>>>(R, p); break;
-            case 4: k_leaf_row<4, NT><<<gr, NT, smem_r, st>>>(R, p); break;
-            case 8: k_leaf_row<8, NT><<<gr, NT, smem_r, st>>>(R, p); break;
-            default: bad = SF_EINVAL;
-            }
-        });
-        if (bad != SF_OK) return sf_set_error(SF_EINVAL, "unsupported ring split");
+        SF_GEO_DISPATCH(R.log_n, k_leaf_row<LR, LC><<<gr, SfThreads<LC>::value, smem_r, st>>>(R, p););
         sf_launch_end(ctx, SFK_LEAF_ROW, st, ev);
     }
     SF_CUDA_TRY(cudaGetLastError());
@@ -446,19 +487,21 @@ sf_status sf_extract_launch(sf_ctx *ctx, const u64 *ct, u64 *out, int i, cudaStr
 sf_status sf_layer_init_attributes()
 {
     const int mx = 227 * 1024;
-#define SF_LEAF_ATTRS(NT)                                                                                    \
+#define SF_LEAF_ATTRS(LR, LC)                                                                               \
     {                                                                                                        \
         /* the tap list is static shared memory: the dynamic part gets the rest */                          \
         cudaFuncAttributes fa;                                                                               \
-        SF_CUDA_TRY(cudaFuncGetAttributes(&fa, k_leaf_col<NT>));                                             \
-        SF_CUDA_TRY(cudaFuncSetAttribute(k_leaf_col<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+        SF_CUDA_TRY(cudaFuncGetAttributes(&fa, k_leaf_col<LR, LC>));                                         \
+        SF_CUDA_TRY(cudaFuncSetAttribute(k_leaf_col<LR, LC>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                          mx - (int)fa.sharedSizeBytes));                                     \
-        SF_CUDA_TRY(cudaFuncSetAttribute((k_leaf_row<2, NT>), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)); \
-        SF_CUDA_TRY(cudaFuncSetAttribute((k_leaf_row<4, NT>), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)); \
-        SF_CUDA_TRY(cudaFuncSetAttribute((k_leaf_row<8, NT>), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)); \
     }
-    SF_LEAF_ATTRS(256)
-    SF_LEAF_ATTRS(512)
+    SF_LEAF_ATTRS(5, 5) SF_LEAF_ATTRS(5, 6) SF_LEAF_ATTRS(6, 6) SF_LEAF_ATTRS(6, 7) SF_LEAF_ATTRS(7, 7)
+    SF_LEAF_ATTRS(7, 8) SF_LEAF_ATTRS(8, 8)
 #undef SF_LEAF_ATTRS
+#define SF_LEAF_ROW_ATTR(LR, LC) \
+    SF_CUDA_TRY(cudaFuncSetAttribute((k_leaf_row<LR, LC>), cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    SF_LEAF_ROW_ATTR(5, 5) SF_LEAF_ROW_ATTR(5, 6) SF_LEAF_ROW_ATTR(6, 6) SF_LEAF_ROW_ATTR(6, 7) SF_LEAF_ROW_ATTR(7, 7)
+    SF_LEAF_ROW_ATTR(7, 8) SF_LEAF_ROW_ATTR(8, 8)
+#undef SF_LEAF_ROW_ATTR
     return SF_OK;
 }

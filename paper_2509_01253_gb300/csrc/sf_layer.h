@@ -24,11 +24,18 @@ struct SfLeafParams {
     const int *sig_out;     // slot -> output index (null = identity)
     const u64 *ct_mont;     // [k_in][2][L][N] NTT domain, Montgomery form
     u64 *w1;                // [slots][k_in][L][N] column-pass scratch
+    // taps of each slot's output bucketed by (input ciphertext j, column tile):
+    // bucket j (C/16) + tile holds entries (row << 4 | column in tile, signed Wq)
+    longlong2 *tap_buf;     // [slots][max_taps]
+    int *tap_off;           // [slots][n_buckets + 1] bucket starts
+    int max_taps, n_buckets;
     u64 *leaves;            // leaf of slot s0 + z at leaves + z * leaf_stride
     size_t leaf_stride;
 };
 
 sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStream_t st);
+// scratch words of the tap buckets for `slots` slots
+size_t sf_leaf_tap_words(const SfRing &R, int k_in, int max_taps, int slots);
 // Pack-tree levels level0+1 .. level1 over G groups.  A holds, per group,
 // the n_nodes = 2^(level1 - level0) nodes of level `level0` (level 0 = leaves)
 // at group stride a_gs; B has room for half as many.  valid[g] = non-zero

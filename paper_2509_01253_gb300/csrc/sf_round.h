@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "sf_internal.h"
+#include "sf_tile.cuh"
 #include "sf_layer.h"
 
 #define SF_CHECK_CTX(ctx)                                                        \
@@ -61,6 +62,7 @@ static inline SfLeafParams leaf_params(const sf_layer *L)
     P.W_out = L->W_out;
     P.wq = L->d_wq;
     P.taps = L->d_taps;
+    P.max_taps = L->max_taps;
     return P;
 }
 
@@ -83,10 +85,21 @@ static inline sf_status upload_perm_inverse(const uint32_t *perm, int n, int *d_
     return SF_OK;
 }
 
-static inline int leaf_batch_slots(const SfRing &R, int k_in)
+// slots per leaf launch: the column-pass scratch and the tap buckets stay
+// within 256 MiB each
+static inline int leaf_batch_slots(const SfRing &R, int k_in, int max_taps)
 {
     size_t per = (size_t)k_in * R.L * R.n * sizeof(u64);
     size_t slots = ((size_t)256 << 20) / per;
+    slots = std::min(slots, ((size_t)256 << 20) / ((size_t)std::max(1, max_taps) * 16));
     return (int)std::max<size_t>(1, std::min<size_t>(slots, 4096));
+}
+
+// points the tap buckets of P at words (sized by sf_leaf_tap_words)
+static inline void sf_leaf_tap_bind(const SfRing &R, SfLeafParams &P, u64 *words, int slots)
+{
+    P.n_buckets = P.k_in * (R.c / SF_NB);
+    P.tap_buf = (longlong2 *)words;
+    P.tap_off = (int *)(words + (size_t)slots * P.max_taps * 2);
 }
 

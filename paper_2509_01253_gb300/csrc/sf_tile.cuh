@@ -28,6 +28,7 @@
 // units with lazy Harvey butterflies.
 #pragma once
 #include "sf_arith.cuh"
+#include "sf_async.cuh"
 
 #define SF_NB 16
 #define SF_PAD 17
@@ -210,3 +211,102 @@ __device__ __forceinline__ void load_row_tw(sf_tw *dst, const sf_tw *__restrict_
     const sf_tw *src = table + ((size_t)mod << g.log_n) + (size_t)r0 * g.c;
     for (int k = threadIdx.x; k < SF_NB * g.c; k += blockDim.x) dst[k] = src[k];
 }
+
+// ---- compile-time geometry -------------------------------------------------
+// The same helpers with the R x C split as template parameters, for kernels
+// instantiated per ring size: loops unroll and slot arithmetic folds into
+// constants.  LR = log2 R, LC = log2 C, NT = threads per block.
+
+template <int LR, int LC>
+struct SfGeoT {
+    static constexpr int log_r = LR, r = 1 << LR, log_c = LC, c = 1 << LC, log_n = LR + LC, n = 1 << (LR + LC);
+};
+
+// threads per block for tiles of 2^log_s-point sub-transforms (constexpr twin of sf_tile_threads)
+template <int LOG_S>
+struct SfThreads {
+    static constexpr int value = LOG_S >= 8 ? 512 : SF_THREADS;
+};
+
+template <int LC>
+__device__ __forceinline__ int row_slot_t(int e) { return (e & ((1 << LC) - 1)) * SF_PAD + (e >> LC); }
+template <int LC>
+__device__ __forceinline__ int col_gidx_t(int c0, int e) { return ((e >> 4) << LC) + c0 + (e & 15); }
+
+// row tile (16 rows of C) global -> shared via 8-byte cp.async
+template <int LC, int NT>
+__device__ __forceinline__ void issue_row_tile_t(u64 *dst, const u64 *src)
+{
+    constexpr int E = (SF_NB << LC) / NT;
+#pragma unroll
+    for (int x = 0; x < E; ++x) {
+        const int e = threadIdx.x + x * NT;
+        sf_cp8(dst + row_slot_t<LC>(e), src + e);
+    }
+}
+
+// column tile (R rows of 16 columns from c0) global -> shared via 8-byte cp.async
+template <int LR, int LC, int NT>
+__device__ __forceinline__ void issue_col_tile_t(u64 *dst, const u64 *src, int c0)
+{
+    constexpr int E = (SF_NB << LR) / NT;
+    const u64 *s0 = src + c0 + (threadIdx.x & 15) + (size_t)(threadIdx.x >> 4) * (1 << LC);
+    u64 *d0 = dst + (threadIdx.x >> 4) * SF_PAD + (threadIdx.x & 15);
+#pragma unroll
+    for (int x = 0; x < E; ++x) sf_cp8(d0 + x * (NT / 16) * SF_PAD, s0 + (size_t)x * (NT / 16) * (1 << LC));
+}
+
+// shared row tile -> global (16 rows of C), with an optional per-value map
+template <int LC, int NT, class F>
+__device__ __forceinline__ void store_row_tile_t(u64 *dst, const u64 *src, F f)
+{
+    constexpr int E = (SF_NB << LC) / NT;
+#pragma unroll
+    for (int x = 0; x < E; ++x) {
+        const int e = threadIdx.x + x * NT;
+        dst[e] = f(src[row_slot_t<LC>(e)]);
+    }
+}
+
+// shared column tile -> global (R rows of 16 columns from c0)
+template <int LR, int LC, int NT, class F>
+__device__ __forceinline__ void store_col_tile_t(u64 *dst, const u64 *src, int c0, F f)
+{
+    constexpr int E = (SF_NB << LR) / NT;
+    u64 *g0 = dst + c0 + (threadIdx.x & 15) + (size_t)(threadIdx.x >> 4) * (1 << LC);
+    const u64 *s0 = src + (threadIdx.x >> 4) * SF_PAD + (threadIdx.x & 15);
+#pragma unroll
+    for (int x = 0; x < E; ++x) g0[(size_t)x * (NT / 16) * (1 << LC)] = f(s0[x * (NT / 16) * SF_PAD]);
+}
+
+// twiddles of the row tile starting at row r0 for modulus mod ([nm][R/16][C][16] table)
+template <int LR, int LC, int NT>
+__device__ __forceinline__ void load_row_tw_t(sf_tw *dst, const sf_tw *__restrict__ table, int mod, int r0)
+{
+    constexpr int E = (SF_NB << LC) / NT;
+    const sf_tw *src = table + ((size_t)mod << (LR + LC)) + ((size_t)r0 << LC);
+#pragma unroll
+    for (int x = 0; x < E; ++x) dst[threadIdx.x + x * NT] = src[threadIdx.x + x * NT];
+}
+
+// column twiddles (R pairs) of modulus mod
+template <int LR, int NT>
+__device__ __forceinline__ void load_col_tw_t(sf_tw *dst, const sf_tw *__restrict__ table, int mod)
+{
+    const sf_tw *src = table + ((size_t)mod << LR);
+    for (int k = threadIdx.x; k < (1 << LR); k += NT) dst[k] = src[k];
+}
+
+// runs the statements with constexpr LR, LC for the ring size log_n (10..16)
+#define SF_GEO_DISPATCH(log_n, ...)                       \
+    do {                                                  \
+        switch (log_n) {                                  \
+        case 10: { constexpr int LR = 5, LC = 5; __VA_ARGS__ } break; \
+        case 11: { constexpr int LR = 5, LC = 6; __VA_ARGS__ } break; \
+        case 12: { constexpr int LR = 6, LC = 6; __VA_ARGS__ } break; \
+        case 13: { constexpr int LR = 6, LC = 7; __VA_ARGS__ } break; \
+        case 14: { constexpr int LR = 7, LC = 7; __VA_ARGS__ } break; \
+        case 15: { constexpr int LR = 7, LC = 8; __VA_ARGS__ } break; \
+        default: { constexpr int LR = 8, LC = 8; __VA_ARGS__ } break; \
+        }                                                 \
+    } while (0)

@@ -61,7 +61,7 @@ class Pool:
     """One parameter set: context, stream, resident weights and client keys."""
 
     def __init__(self, ps: wl.ParamSet, nets: list, n_clients: int, device: int = 0, key_seed: int = 7000,
-                 engine_budget: int = 16 << 30, ks_batch: int = None):
+                 engine_budget: int = 16 << 30, ks_batch: int = None, priority: int = 0):
         import torch
         self.torch = torch
         self.ps = ps
@@ -75,9 +75,14 @@ class Pool:
         self.sks = [sf.sf_keygen(self.ctx, key_seed + 2 * c) for c in range(n_clients)]
         self.rks = [sf.sf_gen_rotation_keys(self.ctx, sk, None, key_seed + 2 * c + 1) for c, sk in enumerate(self.sks)]
         self.nets = {name: nw.EncodedNetwork(self.params, self.ctx, ps, wl.resnet_rounds(name)) for name in nets}
-        self.stream = torch.cuda.Stream(device=device)
+        # CUDA stream priority (lower = higher): the pool of short requests runs
+        # above the pool of long ones, so its launches take SMs as they free up
+        self.stream = torch.cuda.Stream(device=device, priority=priority)
         self.n, self.L = 1 << ps.log_n, ps.n_data
         self.ct_bytes = 2 * self.L * self.n * 8
+        # decoded values beyond this are decryption garbage, not activations
+        self.activation_bound = 1e9
+        self.last_call = []
 
     def reserve_of(self, net: str) -> int:
         return self.nets[net].max_cts() * self.ct_bytes
@@ -111,6 +116,10 @@ class Pool:
         res = np.zeros((info["n_groups"], self.L, self.n), dtype=np.uint64)
         sf.sf_decrypt(self.ctx, self.sks[req.key], req.d_out, info["n_groups"], res, self.stream)
         vals = nw.decode_outputs(net, r, res)
+        if not np.all(np.abs(vals) < self.activation_bound):
+            raise RuntimeError(f"request {req.rid} ({req.net}, key {req.key}) round {r}: decoded |value| "
+                               f"{np.abs(vals).max():.3g} is not a plausible activation; engine call held "
+                               f"{self.last_call}")
         req.client.absorb(r, vals, req.sigma_out)
         req.rounds_run += 1
         req.d_in = req.d_out = None
@@ -130,6 +139,7 @@ class Pool:
             sos.append(req.sigma_out)
             d_outs.append(req.d_out)
             caps.append(info["n_groups"])
+        self.last_call = [(req.rid, req.net, req.key, req.client.round) for req in batch]
         sf.sf_eval_layers(self.ctx, layers, rks, d_ins, k_ins, sps, sos, d_outs, caps, self.stream)
         self.stream.synchronize()
 
@@ -280,7 +290,7 @@ def poisson_arrivals(rate: float, duration: float, mix: dict, n_clients: int, se
         i += 1
 
 
-def run_arrivals(server: Server, arrivals: list, drain: float) -> dict:
+def run_arrivals(server: Server, arrivals: list, drain: float, verify: bool = False) -> dict:
     """Replays the arrivals in real time, then waits up to `drain` seconds for
     admitted requests to finish.  Returns the run's statistics."""
     server.start()
@@ -306,7 +316,15 @@ def run_arrivals(server: Server, arrivals: list, drain: float) -> dict:
                         "admitted": sum(1 for r in server.admitted if r.net == net),
                         "p50_latency_s": float(np.percentile(ln, 50)) if ln.size else None,
                         "p99_latency_s": float(np.percentile(ln, 99)) if ln.size else None}
+    errs = {}
+    if verify:
+        # every completed request against the plaintext network in float64
+        for req in server.completed:
+            net = server.pools[server.route[req.net]].nets[req.net]
+            e = float(np.abs(req.logits - nw.float_forward(net, req.x)).max())
+            errs[req.net] = max(errs.get(req.net, 0.0), e)
     return {"arrivals": len(arrivals), "admitted": len(server.admitted), "rejected": len(server.rejected),
+            "max_abs_err_vs_float64": errs if verify else None,
             "completed": len(server.completed), "unfinished_at_end": unfinished,
             "rejection_rate": len(server.rejected) / max(1, len(arrivals)),
             "p50_latency_s": float(np.percentile(lat, 50)) if lat.size else None,
@@ -328,13 +346,14 @@ def bench(args, device: int) -> int:
     request alone with one engine call per round (the plain form)."""
     import torch
     torch.cuda.set_device(device)
-    pools = {"c2": Pool(wl.PARAMS["conv16"], ["resnet20"], 4, device, key_seed=7000),
-             "c3": Pool(wl.PARAMS["r18"], ["resnet18"], 4, device, key_seed=8000)}
+    pools = {"c2": Pool(wl.PARAMS["conv16"], ["resnet20"], 4, device, key_seed=7000, priority=-1),
+             "c3": Pool(wl.PARAMS["r18"], ["resnet18"], 4, device, key_seed=8000, priority=0)}
     route = {"resnet20": "c2", "resnet18": "c3"}
     budget = 48 << 30
     max_active = {"c2": 16, "c3": 2}
     out = {"metric": "served encrypted layers/s; p50/p99 latency", "unit": "layers/s", "workload": "serve",
            "mix": SERVE_MIX, "client_keys": 4, "mem_budget_bytes": budget, "max_active": max_active,
+           "stream_priority": {"c2": -1, "c3": 0},
            "duration_s": args.duration, "drain_s": args.drain, "rates": {}}
     srv = Server({"c2": pools["c2"]}, {"resnet20": "c2"}, budget, max_active=1, max_batch=1)
     stats = run_arrivals(srv, [(0.0, "resnet20", 0, 99)], drain=600.0)
@@ -342,7 +361,7 @@ def bench(args, device: int) -> int:
     for rate in [float(r) for r in args.rates.split(",")]:
         arr = poisson_arrivals(rate, args.duration, SERVE_MIX, 4, seed=int(rate * 1000) + 17)
         srv = Server(pools, route, budget, max_active=max_active)
-        out["rates"][str(rate)] = run_arrivals(srv, arr, args.drain)
+        out["rates"][str(rate)] = run_arrivals(srv, arr, args.drain, verify=True)
     for p in pools.values():
         p.destroy()
     print(json.dumps(out), flush=True)
