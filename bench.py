@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--rates", default="5,20,200", help="serve: arrival rates (requests/s)")
     ap.add_argument("--duration", type=float, default=20.0, help="serve: arrival window per rate (s)")
     ap.add_argument("--drain", type=float, default=60.0, help="serve: time allowed after the window (s)")
+    ap.add_argument("--low-rate", type=float, default=0.3, help="serve: ResNet-20-only rate below capacity (0 = skip)")
+    ap.add_argument("--low-duration", type=float, default=30.0, help="serve: window of the low-rate run (s)")
+    ap.add_argument("--ctx-opt", action="append", default=[],
+                    help="context option NAME=VALUE for the measured context (sf_ctx_set_option)")
     ap.add_argument("--layer-stats", default="",
                     help="resnet18/resnet34: only a per-kernel breakdown of these rounds (comma-separated names)")
     ap.add_argument("--small", action="store_true",
@@ -614,12 +618,20 @@ def main():
     import paper_2509_01253_gb300 as sf
     torch.cuda.set_device(local)
     wl_ = Workload(local, small=args.small)
+    for kv in args.ctx_opt:
+        name, val = kv.split("=", 1)
+        sf.sf_ctx_set_option(wl_.ctx, name, int(val))
     stream = wl_.stream
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
-    for _ in range(max(3, args.warmup)):
+    err = None
+    for w in range(max(3, args.warmup)):
         wl_.step()
+        if w == 0:
+            # decryption check after the first round (it may grow the context's
+            # workspace, which drops captured graphs: the later warm-up steps recapture)
+            torch.cuda.synchronize()
+            err = wl_.check()
     torch.cuda.synchronize()
-    err = wl_.check()
     # ---- timed region: device-resident inputs
     clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
@@ -689,8 +701,8 @@ def main():
             "config": {"workload": WORKLOAD if not args.small else "conv16-small (profiling case): " + WORKLOAD.replace(
                 "16x32x32 (E = E' = 16384)", "8x16x16 (E = E' = 2048)"), "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                       "ks_batch": None, "max_abs_err": err},
-            "clocks": clk, "gpu_launches": n_launch // 1,
+                       "ks_batch": None, "ctx_options": args.ctx_opt, "max_abs_err": err},
+            "clocks": clk, "gpu_launches": n_launch // 1, "step_ms": step_ms,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roofline, "kernels": kernel_table}
     if rank == 0 and not args.no_cpu_baseline:

@@ -110,6 +110,10 @@ void sf_ctx_destroy(sf_ctx *ctx);
 
 /* Tuning and instrumentation knobs (name, value):
  *   "ks_batch"      merges per key-switch batch (1..4096; default chosen per N)
+ *   "leaf_sparse"   taps per 16-column tile up to which the leaf column pass
+ *                   evaluates the sparse weight polynomial in closed form
+ *                   instead of running the transform (-1: 8 log2 R, the
+ *                   default; 0: always transform; at most 128)
  *   "leaf_chunk"    cap on the leaves per packing unit (power of two): a group
  *                   of n leaves is packed as n/CH residue classes of CH leaves
  *                   reduced to roots, then the roots finish the tree

@@ -95,7 +95,8 @@ extern "C" sf_status sf_gen_rotation_keys(sf_ctx *ctx, const sf_secret_key *sk, 
     rk->ctx = ctx;
     rk->gen = sf_next_generation();
     rk->d = ds;
-    rk->key_words = (size_t)R.dnum * 2 * R.nm * R.n;
+    // per key: values [dnum][2][nm][N] (NTT domain), then their Shoup companions
+    rk->key_words = (size_t)2 * R.dnum * 2 * R.nm * R.n;
     sf_status st = device_buffer((void **)&rk->d_keys, sizeof(u64) * rk->key_words * ds.size());
     u64 *d_alpha = nullptr, *d_e = nullptr;
     int64_t *d_ei = nullptr;
@@ -132,7 +133,7 @@ extern "C" sf_status sf_gen_rotation_keys(sf_ctx *ctx, const sf_secret_key *sk, 
             if (st == SF_OK) st = sf_signed_to_residues(ctx, d_ei, d_e, R.nm, R.nm, 0, 0);
             if (st == SF_OK) st = sf_ntt_jobs(ctx, jobs_a.data(), R.nm, false, 0);
             if (st == SF_OK) st = sf_ntt_jobs(ctx, jobs_e.data(), R.nm, false, 0);
-            if (st == SF_OK) st = sf_rotkey_finish(ctx, d_alpha, d_e, sk->d_s_mont, pg, ds[t], ka, kb, 0);
+            if (st == SF_OK) st = sf_rotkey_finish(ctx, d_alpha, d_e, sk->d_s_mont, pg, ds[t], ka, kb, rk->key_words / 2, 0);
             if (st == SF_OK && cudaDeviceSynchronize() != cudaSuccess) st = sf_set_error(SF_ECUDA, "keygen kernel failed");
         }
     }
@@ -169,16 +170,16 @@ extern "C" sf_status sf_rotkeys_export(sf_ctx *ctx, const sf_rotkeys *rk, int32_
     int t = key_slot(rk, d);
     if (t < 0) return sf_set_error(SF_EINVAL, "no rotation key for d = %d", d);
     const SfRing &R = ctx->ring;
+    const size_t vals = rk->key_words / 2;   // the values; the companions follow
     void *w = nullptr;
-    SF_TRY(sf_scratch(ctx, sizeof(u64) * rk->key_words, &w));
+    SF_TRY(sf_scratch(ctx, sizeof(u64) * vals, &w));
     u64 *tmp = (u64 *)w;
-    SF_CUDA_TRY(cudaMemcpy(tmp, rk->d_keys + rk->key_words * t, sizeof(u64) * rk->key_words, cudaMemcpyDeviceToDevice));
+    SF_CUDA_TRY(cudaMemcpy(tmp, rk->d_keys + rk->key_words * t, sizeof(u64) * vals, cudaMemcpyDeviceToDevice));
     int npol = R.dnum * 2 * R.nm;
-    SF_TRY(sf_from_mont(ctx, tmp, npol, R.nm, 0, 0));
     std::vector<SfPolyJob> jobs;
     for (int x = 0; x < npol; ++x) jobs.push_back({tmp + (size_t)x * R.n, tmp + (size_t)x * R.n, x % R.nm});
     SF_TRY(sf_ntt_jobs(ctx, jobs.data(), npol, true, 0));
-    SF_CUDA_TRY(cudaMemcpy(h_key, tmp, sizeof(u64) * rk->key_words, cudaMemcpyDeviceToHost));
+    SF_CUDA_TRY(cudaMemcpy(h_key, tmp, sizeof(u64) * vals, cudaMemcpyDeviceToHost));
     return SF_OK;
 }
 
@@ -417,7 +418,7 @@ extern "C" sf_status sf_linear_outputs(sf_ctx *ctx, const sf_layer *L, const uin
     const size_t ct = ct_words(ctx);
     const int LB = std::min(leaf_batch_slots(R, k_in, L->max_taps), n_outputs);
     Carver cv;
-    size_t o_ct = cv.take((size_t)k_in * ct), o_pos = cv.take(((size_t)L->E_in + 1) / 2),
+    size_t o_ct = cv.take((size_t)2 * k_in * ct), o_pos = cv.take(((size_t)L->E_in + 1) / 2),
            o_sig = cv.take(((size_t)n_outputs + 1) / 2), o_w1 = cv.take((size_t)LB * k_in * R.L * R.n),
            o_lv = cv.take((size_t)n_outputs * ct), o_tap = cv.take(sf_leaf_tap_words(R, k_in, L->max_taps, LB));
     void *w = nullptr;
@@ -432,7 +433,7 @@ extern "C" sf_status sf_linear_outputs(sf_ctx *ctx, const sf_layer *L, const uin
     P.k_in = k_in;
     P.pos_of = h_sigma_prev ? d_pos : nullptr;
     P.sig_out = d_sig;
-    P.ct_mont = ws + o_ct;
+    P.ct = ws + o_ct;
     P.w1 = ws + o_w1;
     sf_leaf_tap_bind(R, P, ws + o_tap, LB);
     P.n_slots_valid = n_outputs;

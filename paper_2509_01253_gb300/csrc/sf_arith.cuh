@@ -83,17 +83,40 @@ SF_HD u64 sf_mul_mont(u64 a, u64 b_mont, u64 q, u64 qinv_neg)
     return sf_redc(sf_mulhi(a, b_mont), a * b_mont, q, qinv_neg);
 }
 
+// High 64 bits of a*b from three of the four 32 x 32-bit partial products:
+// the low x low product and the carries out of the two cross products are
+// dropped, so the result is the exact high part minus 0, 1 or 2.
+SF_HD u64 sf_mulhi_trunc(u64 a, u64 b)
+{
+#if defined(__CUDA_ARCH__)
+    const uint32_t al = (uint32_t)a, ah = (uint32_t)(a >> 32), bl = (uint32_t)b, bh = (uint32_t)(b >> 32);
+    return (u64)ah * bh + __umulhi(ah, bl) + __umulhi(al, bh);
+#else
+    const u64 al = (uint32_t)a, ah = a >> 32, bl = (uint32_t)b, bh = b >> 32;
+    return ah * bh + ((ah * bl) >> 32) + ((al * bh) >> 32);
+#endif
+}
+
+// Shoup's product with the truncated quotient: qhat is the exact
+// floor(x w' / 2^64) minus at most 2, so x*w - qhat*q lies in [0, 4q).
+SF_HD u64 sf_mul_shoup_lazy4(u64 x, u64 w, u64 wp, u64 q)
+{
+    return x * w - sf_mulhi_trunc(x, wp) * q;
+}
+
 // Forward (Cooley-Tukey) butterfly without reduction: with Y*w mod q taken
-// lazily in [0, 2q) (valid for any Y < 2^64), X' = X + T and Y' = X - T + 2q
-// grow the bound by at most 2q per stage.  Starting below 4q, a whole
-// transform of at most 16 stages stays below 36q < 2^57 for q < 2^51, so no
-// conditional subtraction is needed until a consumer wants canonical values.
+// lazily in [0, 4q) (valid for any Y < 2^64), X' = X + T and Y' = X - T + 4q
+// grow the bound by at most 4q per stage.  Starting below 4q, a whole
+// transform of at most 16 stages stays below 68q < 2^58 for q < 2^51, so no
+// conditional subtraction is needed until a consumer wants canonical values
+// (every consumer reduces inputs below 2^64, or multiplies them by a residue
+// below q with a Montgomery reduction that accepts products below q 2^64).
 SF_HD void sf_bfly_ct(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 two_q)
 {
-    u64 t = sf_mul_shoup_lazy(Y, w, wp, q);
+    u64 t = sf_mul_shoup_lazy4(Y, w, wp, q);
     u64 x = X;
     X = x + t;
-    Y = x - t + two_q;
+    Y = x - t + 2 * two_q;
 }
 
 // Inverse (Gentleman-Sande) lazy butterfly: X, Y in [0, 2q) -> X', Y' in [0, 2q).

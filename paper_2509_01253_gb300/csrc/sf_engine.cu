@@ -111,7 +111,7 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
     Carver cv;
     std::vector<size_t> o_ct(jobs.size()), o_pos(jobs.size()), o_sig(jobs.size());
     for (size_t x = 0; x < jobs.size(); ++x) {
-        o_ct[x] = cv.take((size_t)jobs[x].k_in * ct);
+        o_ct[x] = cv.take((size_t)2 * jobs[x].k_in * ct);
         o_pos[x] = cv.take(((size_t)jobs[x].L->E_in + 1) / 2);
         o_sig[x] = cv.take(((size_t)jobs[x].L->E_out + 1) / 2);
     }
@@ -162,7 +162,7 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
             P.k_in = j.k_in;
             P.pos_of = j.sp ? j.d_pos : nullptr;
             P.sig_out = j.so ? j.d_sig : nullptr;
-            P.ct_mont = j.d_ct;
+            P.ct = j.d_ct;
             P.w1 = d_w1;
             sf_leaf_tap_bind(R, P, ws + o_tap, LB);
             P.n_slots_valid = j.L->E_out;

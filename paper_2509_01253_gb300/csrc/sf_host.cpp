@@ -457,6 +457,7 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
     ctx->io_bytes = 0;
     ctx->ks_batch = p->log_n >= 15 ? 64 : 128;
     ctx->leaf_chunk = 1 << 30;
+    ctx->leaf_sparse = -1;
     ctx->mem_budget = (size_t)64 << 30;
     ctx->use_graph = 1;
     ctx->kernel_timing = 0;
@@ -642,6 +643,10 @@ extern "C" sf_status sf_ctx_set_option(sf_ctx *ctx, const char *name, int64_t va
     if (!strcmp(name, "ks_batch")) {
         if (value < 1 || value > 4096) return sf_set_error(SF_EINVAL, "ks_batch must be in [1, 4096]");
         ctx->ks_batch = (int)value;
+        sf_graph_cache_clear(ctx);
+    } else if (!strcmp(name, "leaf_sparse")) {
+        if (value < -1 || value > 128) return sf_set_error(SF_EINVAL, "leaf_sparse must be in [-1, 128]");
+        ctx->leaf_sparse = (int)value;
         sf_graph_cache_clear(ctx);
     } else if (!strcmp(name, "leaf_chunk")) {
         if (value < 1 || (value & (value - 1))) return sf_set_error(SF_EINVAL, "leaf_chunk must be a power of two");

@@ -87,6 +87,7 @@ struct sf_ctx {
     // options
     int ks_batch;
     int leaf_chunk;
+    int leaf_sparse;          // taps per column tile up to which the leaf column pass uses the closed form (-1: default rule)
     size_t mem_budget;        // bytes of leaf + tree buffers a round may use
     int use_graph;
     int kernel_timing;
@@ -222,7 +223,9 @@ sf_status sf_decrypt_finish(sf_ctx *ctx, const u64 *cts, const u64 *p, u64 *out,
 sf_status sf_signed_to_residues(sf_ctx *ctx, const int64_t *v, u64 *out, int n_polys, int period, int offset,
                                 cudaStream_t st);
 sf_status sf_rotkey_finish(sf_ctx *ctx, const u64 *alpha, const u64 *e, const u64 *s_mont, const u64 *pg, int d,
-                           u64 *key_a, u64 *key_b, cudaStream_t st);
+                           u64 *key_a, u64 *key_b, size_t comp, cudaStream_t st);
+// Shoup companions floor(x 2^64 / q) of residues x (poly t uses modulus offset + t % period)
+sf_status sf_companions(sf_ctx *ctx, const u64 *x, u64 *dst, int n_polys, int period, int offset, cudaStream_t st);
 
 // Raise the dynamic shared-memory limit of every kernel (once per device).
 sf_status sf_ntt_init_attributes();

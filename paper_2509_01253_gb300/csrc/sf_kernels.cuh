@@ -38,3 +38,14 @@ __device__ __forceinline__ unsigned mono_index(int j, unsigned s, int log_n)
 struct SfJobList {
     SfPolyJob j[SF_MAX_JOBS];
 };
+
+// floor(x 2^64 / q) for a canonical residue x: 2^64 = one_p q + r_mod, so
+// x 2^64 = (x one_p + h) q + (x r_mod - h q) with h = floor(x r_mod / q),
+// which Shoup's product by r_mod gives up to one correction.
+__device__ __forceinline__ u64 sf_shoup_companion_dev(u64 x, const SfMod &M)
+{
+    u64 h = sf_mulhi(x, M.r_mod_p);
+    const u64 rem = x * M.r_mod - h * M.q;
+    if (rem >= M.q) ++h;
+    return x * M.one_p + h;
+}

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(SfThreads<LC>::value) k_rows(SfRing R, SfKsBat
 // forward column tables of every modulus, two buffers of nd source tiles, one
 // work tile.
 template <int LR, int LC>
-__global__ void __launch_bounds__(SfThreads<LR>::value) k_ks2(SfRing R, SfKsBatch B, int bpg)
+__global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 512 ? 1 : 3) k_ks2(SfRing R, SfKsBatch B, int bpg)
 {
     constexpr int NT = SfThreads<LR>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -230,13 +230,22 @@ __global__ void __launch_bounds__(SfThreads<LR>::value) k_ks2(SfRing R, SfKsBatc
             if (m >= lo && m < hi) continue;
             const SfMod &M = R.m[m];
             #pragma unroll
+            // base conversion, lazy: each term in [0, 2q), the sum below 2q * nd
+            // (digits hold at most 4 limbs: K <= 4)
+            u64 qh[4], qhp[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const size_t ci = ((size_t)(j * R.K + t)) * R.nm + m;
+                qh[t] = t < nd ? R.mu_qhat[ci] : 0;
+                qhp[t] = t < nd ? R.mu_qhat_p[ci] : 0;
+            }
+#pragma unroll
             for (int e = threadIdx.x; e < (SF_NB << LR); e += NT) {
                 const int sl = col_slot(e);
                 u64 acc = 0;
-                for (int t = 0; t < nd; ++t) {
-                    const size_t ci = ((size_t)(j * R.K + t)) * R.nm + m;
-                    acc = sf_add(acc, sf_mul_shoup(cur[(size_t)t * tw_words + sl], R.mu_qhat[ci], R.mu_qhat_p[ci], M.q), M.q);
-                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (t < nd) acc += sf_mul_shoup_lazy(cur[(size_t)t * tw_words + sl], qh[t], qhp[t], M.q);
                 work[sl] = acc;
             }
             __syncthreads();
@@ -293,16 +302,16 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 
         __syncthreads();
         const bool own = (m >= j * R.K && m < min((j + 1) * R.K, R.L));
         if (!own) tile_forward_t<LC, true, NT>(cur, tw, M.q);
+        const size_t comp = (size_t)R.dnum * 2 * R.nm << (LR + LC);   // companions follow the key values
         const u64 *ka = B.key + ((((size_t)j * 2 + 0) * R.nm + m) << (LR + LC)) + tile_off;
         const u64 *kb = B.key + ((((size_t)j * 2 + 1) * R.nm + m) << (LR + LC)) + tile_off;
-        // per digit c * key (c lazy < 36q, key < q) is Montgomery-reduced into [0, 2q) and summed
+        // per digit c * key (c lazy < 68q, key < q with its Shoup companion) lands in [0, 4q) and is summed
 #pragma unroll
         for (int x = 0; x < EPT; ++x) {
             const int e = threadIdx.x + x * NT;
             const u64 c = cur[row_slot_t<LC>(e)];
-            const u64 xa = __ldg(ka + e), xb = __ldg(kb + e);
-            acc_a[x] += sf_redc_lazy(sf_mulhi(c, xa), c * xa, M.q, M.qinv_neg);
-            acc_b[x] += sf_redc_lazy(sf_mulhi(c, xb), c * xb, M.q, M.qinv_neg);
+            acc_a[x] += sf_mul_shoup_lazy4(c, __ldg(ka + e), __ldg(ka + comp + e), M.q);
+            acc_b[x] += sf_mul_shoup_lazy4(c, __ldg(kb + e), __ldg(kb + comp + e), M.q);
         }
         if (j == R.dnum - 1) {
             const KsLayout Lo = ks_layout(R, B, b);
@@ -330,7 +339,7 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 
 // inverse (special) + L forward (data) column tables, two buffers of K tiles,
 // one work tile.
 template <int LR, int LC>
-__global__ void __launch_bounds__(SfThreads<LR>::value) k_ks4(SfRing R, SfKsBatch B, int bpg)
+__global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 512 ? 1 : 3) k_ks4(SfRing R, SfKsBatch B, int bpg)
 {
     constexpr int NT = SfThreads<LR>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -374,13 +383,20 @@ __global__ void __launch_bounds__(SfThreads<LR>::value) k_ks4(SfRing R, SfKsBatc
         for (int i = 0; i < R.L; ++i) {
             const SfMod &M = R.m[i];
             #pragma unroll
+            // base conversion, lazy: each term in [0, 2q), the sum below 2q * K
+            u64 ph[4], php[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                ph[k] = k < R.K ? R.md_phat[(size_t)k * R.L + i] : 0;
+                php[k] = k < R.K ? R.md_phat_p[(size_t)k * R.L + i] : 0;
+            }
+#pragma unroll
             for (int e = threadIdx.x; e < (SF_NB << LR); e += NT) {
                 const int sl = col_slot(e);
                 u64 acc = 0;
-                for (int k = 0; k < R.K; ++k) {
-                    const size_t ci = (size_t)k * R.L + i;
-                    acc = sf_add(acc, sf_mul_shoup(cur[(size_t)k * tw_words + sl], R.md_phat[ci], R.md_phat_p[ci], M.q), M.q);
-                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < R.K) acc += sf_mul_shoup_lazy(cur[(size_t)k * tw_words + sl], ph[k], php[k], M.q);
                 work[sl] = acc;
             }
             __syncthreads();

@@ -156,8 +156,7 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
         }
     }
     __syncthreads();
-    // closed form while nt * R products cost less than the tile's 16 (R/2) log2 R butterflies
-    if (nt <= SF_LEAF_TAPS && nt * 2 <= SF_NB * g.log_r) {
+    if (nt <= P.sparse_max) {
         // counting sort by column; the order inside a column does not matter (exact sums)
         if (threadIdx.x == 0) {
             int acc = 0;
@@ -228,8 +227,8 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 
     u64 *sm = (u64 *)(tw + SF_NB * g.c);
     const SfMod M = R.m[i];
     load_row_tw_t<LR, LC, NT>(tw, R.rowT_f, i, r0);
-    // per input ciphertext w * ct (w < 36q lazy, ct < q, Montgomery form) is
-    // reduced into [0, 2q) and summed: below 2 q k_in < 2^56 for k_in < 32
+    // per input ciphertext w * ct (w < 68q lazy, ct < q with its Shoup
+    // companion) lands in [0, 4q) and is summed: below 4 q k_in < 2^63 for k_in < 1024
     u64 acc_a[EPT], acc_b[EPT];
 #pragma unroll
     for (int k = 0; k < EPT; ++k) acc_a[k] = acc_b[k] = 0;
@@ -242,15 +241,15 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 
         }
         __syncthreads();
         tile_forward_t<LC, true, NT>(sm, tw, M.q);
-        const u64 *ca = P.ct_mont + (((size_t)j * 2 + 0) * R.L + i) * (size_t)(1 << (LR + LC)) + tile_off;
-        const u64 *cb = P.ct_mont + (((size_t)j * 2 + 1) * R.L + i) * (size_t)(1 << (LR + LC)) + tile_off;
+        const size_t comp = (size_t)P.k_in * 2 * R.L << (LR + LC);
+        const u64 *ca = P.ct + (((size_t)j * 2 + 0) * R.L + i) * (size_t)(1 << (LR + LC)) + tile_off;
+        const u64 *cb = P.ct + (((size_t)j * 2 + 1) * R.L + i) * (size_t)(1 << (LR + LC)) + tile_off;
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
             const int e = threadIdx.x + k * NT;
             const u64 w = sm[row_slot_t<LC>(e)];
-            const u64 xa = __ldg(ca + e), xb = __ldg(cb + e);
-            acc_a[k] += sf_redc_lazy(sf_mulhi(w, xa), w * xa, M.q, M.qinv_neg);
-            acc_b[k] += sf_redc_lazy(sf_mulhi(w, xb), w * xb, M.q, M.qinv_neg);
+            acc_a[k] += sf_mul_shoup_lazy4(w, __ldg(ca + e), __ldg(ca + comp + e), M.q);
+            acc_b[k] += sf_mul_shoup_lazy4(w, __ldg(cb + e), __ldg(cb + comp + e), M.q);
         }
         __syncthreads();
     }
@@ -267,9 +266,12 @@ sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStre
     const SfRing &R = ctx->ring;
     if (cnt <= 0) return SF_OK;
     const size_t smem_c = sf_smem_leaf_col(R), smem_r = sf_smem_row(R, 1);
+    // closed form while nt R products cost less than the tile's 16 (R/2) log2 R butterflies
+    const int sparse_max = std::min(SF_LEAF_TAPS, ctx->leaf_sparse >= 0 ? ctx->leaf_sparse : SF_NB * R.log_r / 2);
     cudaEvent_t ev;
     for (int off = 0; off < cnt; off += 65535) {
         SfLeafParams p = P;
+        p.sparse_max = sparse_max;
         const int c = std::min(65535, cnt - off);
         p.s0 = P.s0 + off * P.s_stride;
         p.w1 = P.w1;    // w1 holds `cnt` slots; reuse from its start for each sub-launch

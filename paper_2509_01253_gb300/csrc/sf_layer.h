@@ -22,13 +22,14 @@ struct SfLeafParams {
     const int4 *taps;       // tap geometry table (see sf_layer)
     const int *pos_of;      // input index -> stream position (null = identity)
     const int *sig_out;     // slot -> output index (null = identity)
-    const u64 *ct_mont;     // [k_in][2][L][N] NTT domain, Montgomery form
+    const u64 *ct;          // [k_in][2][L][N] NTT domain, then the same shape of Shoup companions
     u64 *w1;                // [slots][k_in][L][N] column-pass scratch
     // taps of each slot's output bucketed by (input ciphertext j, column tile):
     // bucket j (C/16) + tile holds entries (row << 4 | column in tile, signed Wq)
     longlong2 *tap_buf;     // [slots][max_taps]
     int *tap_off;           // [slots][n_buckets + 1] bucket starts
     int max_taps, n_buckets;
+    int sparse_max;         // closed-form column pass for tiles with at most this many taps
     u64 *leaves;            // leaf of slot s0 + z at leaves + z * leaf_stride
     size_t leaf_stride;
 };

@@ -182,7 +182,7 @@ struct SfPg {
     u64 v[SF_MAX_MODULI];
 };
 __global__ void k_rotkey_finish(SfRing R, const u64 *alpha, const u64 *e, const u64 *s_mont, SfPg pg, int d,
-                                u64 *key_a, u64 *key_b)
+                                u64 *key_a, u64 *key_b, size_t comp)
 {
     SF_GRID_STRIDE(i, (size_t)R.nm * R.n)
     {
@@ -193,8 +193,11 @@ __global__ void k_rotkey_finish(SfRing R, const u64 *alpha, const u64 *e, const 
         int js = auto_src(j, d, R.log_n);
         u64 sd = sf_mul_mont(pg.v[m], s_mont[((size_t)m << R.log_n) + js], M.q, M.qinv_neg);
         u64 b = sf_sub(sf_add(as, e[i], M.q), sd, M.q);
-        key_a[i] = sf_mul_shoup(alpha[i], M.r_mod, M.r_mod_p, M.q);
-        key_b[i] = sf_mul_shoup(b, M.r_mod, M.r_mod_p, M.q);
+        // plain values, then their Shoup companions `comp` words later
+        key_a[i] = alpha[i];
+        key_b[i] = b;
+        key_a[i + comp] = sf_shoup_companion_dev(alpha[i], M);
+        key_b[i + comp] = sf_shoup_companion_dev(b, M);
     }
 }
 
@@ -255,11 +258,27 @@ sf_status sf_signed_to_residues(sf_ctx *ctx, const int64_t *v, u64 *out, int n_p
 }
 
 sf_status sf_rotkey_finish(sf_ctx *ctx, const u64 *alpha, const u64 *e, const u64 *s_mont, const u64 *pg, int d,
-                           u64 *key_a, u64 *key_b, cudaStream_t st)
+                           u64 *key_a, u64 *key_b, size_t comp, cudaStream_t st)
 {
     SfPg p;
     for (int m = 0; m < SF_MAX_MODULI; ++m) p.v[m] = m < ctx->ring.nm ? pg[m] : 0;
-    SF_ELEM_LAUNCH(k_rotkey_finish, (size_t)ctx->ring.nm * ctx->ring.n, alpha, e, s_mont, p, d, key_a, key_b);
+    SF_ELEM_LAUNCH(k_rotkey_finish, (size_t)ctx->ring.nm * ctx->ring.n, alpha, e, s_mont, p, d, key_a, key_b, comp);
+    return SF_OK;
+}
+
+// Shoup companions of NTT-domain residues, in place into dst: dst[i] = floor(x[i] 2^64 / q)
+__global__ void k_shoup_companions(SfRing R, const u64 *x, u64 *dst, int n_polys, int period, int offset)
+{
+    SF_GRID_STRIDE(i, (size_t)n_polys * R.n)
+    {
+        const SfMod &M = R.m[offset + (int)((i >> R.log_n) % period)];
+        dst[i] = sf_shoup_companion_dev(x[i], M);
+    }
+}
+
+sf_status sf_companions(sf_ctx *ctx, const u64 *x, u64 *dst, int n_polys, int period, int offset, cudaStream_t st)
+{
+    SF_ELEM_LAUNCH(k_shoup_companions, (size_t)n_polys * ctx->ring.n, x, dst, n_polys, period, offset);
     return SF_OK;
 }
 

@@ -66,14 +66,15 @@ static inline SfLeafParams leaf_params(const sf_layer *L)
     return P;
 }
 
-// Input ciphertexts -> NTT domain, Montgomery form (for the leaf products).
-static inline sf_status prepare_inputs(sf_ctx *ctx, const u64 *d_in, int k_in, u64 *ct_mont, cudaStream_t st)
+// Input ciphertexts -> NTT domain (canonical), followed by their Shoup
+// companions (for the leaf products): ct holds 2 k_in ciphertexts' words.
+static inline sf_status prepare_inputs(sf_ctx *ctx, const u64 *d_in, int k_in, u64 *ct, cudaStream_t st)
 {
     const SfRing &R = ctx->ring;
     std::vector<SfPolyJob> jobs;
-    for (int x = 0; x < k_in * 2 * R.L; ++x) jobs.push_back({d_in + (size_t)x * R.n, ct_mont + (size_t)x * R.n, x % R.L});
+    for (int x = 0; x < k_in * 2 * R.L; ++x) jobs.push_back({d_in + (size_t)x * R.n, ct + (size_t)x * R.n, x % R.L});
     SF_TRY(sf_ntt_jobs(ctx, jobs.data(), (int)jobs.size(), false, st));
-    SF_TRY(sf_to_mont(ctx, ct_mont, k_in * 2 * R.L, R.L, 0, st));
+    SF_TRY(sf_companions(ctx, ct, ct + (size_t)k_in * 2 * R.L * R.n, k_in * 2 * R.L, R.L, 0, st));
     return SF_OK;
 }
 

@@ -362,6 +362,12 @@ def bench(args, device: int) -> int:
         arr = poisson_arrivals(rate, args.duration, SERVE_MIX, 4, seed=int(rate * 1000) + 17)
         srv = Server(pools, route, budget, max_active=max_active)
         out["rates"][str(rate)] = run_arrivals(srv, arr, args.drain, verify=True)
+    # below capacity: ResNet-20 requests alone at a low rate
+    if args.low_rate > 0:
+        arr = poisson_arrivals(args.low_rate, args.low_duration, {"resnet20": 1.0}, 4, seed=31)
+        srv = Server({"c2": pools["c2"]}, {"resnet20": "c2"}, budget, max_active=16)
+        out["resnet20_only"] = dict(rate=args.low_rate, duration_s=args.low_duration,
+                                    **run_arrivals(srv, arr, args.drain, verify=True))
     for p in pools.values():
         p.destroy()
     print(json.dumps(out), flush=True)
