@@ -493,6 +493,9 @@ def run_network(args, local: int) -> int:
     seed = 300 if args.workload == "resnet18" else 400
     nw_ = NetworkWorkload(args.workload, local, seed)
     nw_._seed = seed
+    for kv in args.ctx_opt:
+        name, val = kv.split("=", 1)
+        nw_.sf.sf_ctx_set_option(nw_.ctx, name, int(val))
     torch_ = torch
     sf = nw_.sf
     R = len(nw_.net.rounds)

@@ -112,8 +112,9 @@ void sf_ctx_destroy(sf_ctx *ctx);
  *   "ks_batch"      merges per key-switch batch (1..4096; default chosen per N)
  *   "leaf_sparse"   taps per 16-column tile up to which the leaf column pass
  *                   evaluates the sparse weight polynomial in closed form
- *                   instead of running the transform (-1: 8 log2 R, the
- *                   default; 0: always transform; at most 128)
+ *                   instead of running the transform (-1: 8 log2 R, where the
+ *                   closed form has fewer multiplications; 0: always the
+ *                   transform, the default; at most 128)
  *   "leaf_chunk"    cap on the leaves per packing unit (power of two): a group
  *                   of n leaves is packed as n/CH residue classes of CH leaves
  *                   reduced to roots, then the roots finish the tree
@@ -280,9 +281,11 @@ sf_status sf_eval_layers(sf_ctx *ctx, int32_t n_layers, const sf_layer *const *l
                          int32_t *n_outs, void *stream);
 
 /* Autotuner: times sf_eval_layers on the given rounds (which it evaluates,
- * results valid) for each candidate key-switch launch batch (32 ... 512
- * merges), `repeats` timed runs each after a warm-up, keeps the fastest in
- * the context ("ks_batch") and reports it with its time in milliseconds.
+ * results valid), `repeats` timed runs per candidate after a warm-up:
+ * first each key-switch launch batch (32 ... 512 merges), then, with the
+ * best batch, the leaf column pass of sparse tiles in closed form or as a
+ * transform ("leaf_sparse" -1 or 0).  Keeps the fastest choices in the
+ * context and reports the batch with the best time in milliseconds.
  * Synchronises `stream`. */
 sf_status sf_autotune_layers(sf_ctx *ctx, int32_t n_layers, const sf_layer *const *layers, const sf_rotkeys *const *rks,
                              const uint64_t *const *d_ins, const int32_t *k_ins, const uint32_t *const *h_sigma_prevs,

@@ -352,40 +352,61 @@ extern "C" sf_status sf_autotune_layers(sf_ctx *ctx, int32_t n_layers, const sf_
     cudaStream_t st = (cudaStream_t)stream;
     const int saved_timing = ctx->kernel_timing;
     ctx->kernel_timing = 0;
-    static const int cand[] = {32, 64, 128, 256, 512};
-    int best = ctx->ks_batch;
-    double best_t = 1e30;
     cudaEvent_t e0, e1;
     SF_CUDA_TRY(cudaEventCreate(&e0));
     SF_CUDA_TRY(cudaEventCreate(&e1));
     sf_status status = SF_OK;
-    for (int c : cand) {
-        ctx->ks_batch = c;
+    // times the batch under the current options: one warm-up (also captures the graph), best of `repeats`
+    auto measure = [&](double *out_ms) -> sf_status {
         sf_graph_cache_clear(ctx);
-        // warm-up (also captures the graph)
-        status = sf_eval_layers(ctx, n_layers, layers, rks, d_ins, k_ins, h_sigma_prevs, h_sigma_outs, d_outs,
-                                out_capacities, nullptr, stream);
-        if (status != SF_OK) break;
+        SF_TRY(sf_eval_layers(ctx, n_layers, layers, rks, d_ins, k_ins, h_sigma_prevs, h_sigma_outs, d_outs,
+                              out_capacities, nullptr, stream));
         double tmin = 1e30;
-        for (int r = 0; r < repeats && status == SF_OK; ++r) {
+        for (int r = 0; r < repeats; ++r) {
             cudaEventRecord(e0, st);
-            status = sf_eval_layers(ctx, n_layers, layers, rks, d_ins, k_ins, h_sigma_prevs, h_sigma_outs, d_outs,
-                                    out_capacities, nullptr, stream);
+            SF_TRY(sf_eval_layers(ctx, n_layers, layers, rks, d_ins, k_ins, h_sigma_prevs, h_sigma_outs, d_outs,
+                                  out_capacities, nullptr, stream));
             cudaEventRecord(e1, st);
             cudaEventSynchronize(e1);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
             tmin = std::min(tmin, (double)ms);
         }
-        if (status != SF_OK) break;
-        if (tmin < best_t) {
-            best_t = tmin;
+        *out_ms = tmin;
+        return SF_OK;
+    };
+    // 1) merges per key-switch launch
+    static const int cand[] = {32, 64, 128, 256, 512};
+    int best = ctx->ks_batch;
+    double best_t = 1e30;
+    for (int c : cand) {
+        ctx->ks_batch = c;
+        double t = 0;
+        if ((status = measure(&t)) != SF_OK) break;
+        if (t < best_t) {
+            best_t = t;
             best = c;
         }
     }
+    ctx->ks_batch = best;
+    // 2) leaf column pass of sparse tiles: closed form (default rule) or always the transform
+    if (status == SF_OK) {
+        const int saved_sparse = ctx->leaf_sparse;
+        int best_sparse = saved_sparse;
+        for (int sp : {-1, 0}) {
+            if (sp == saved_sparse) continue;
+            ctx->leaf_sparse = sp;
+            double t = 0;
+            if ((status = measure(&t)) != SF_OK) break;
+            if (t < best_t) {
+                best_t = t;
+                best_sparse = sp;
+            }
+        }
+        ctx->leaf_sparse = best_sparse;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->ks_batch = best;
     sf_graph_cache_clear(ctx);
     ctx->kernel_timing = saved_timing;
     if (status != SF_OK) return status;

@@ -457,7 +457,7 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
     ctx->io_bytes = 0;
     ctx->ks_batch = p->log_n >= 15 ? 64 : 128;
     ctx->leaf_chunk = 1 << 30;
-    ctx->leaf_sparse = -1;
+    ctx->leaf_sparse = 0;   // the transform measured faster than the closed form on GB300
     ctx->mem_budget = (size_t)64 << 30;
     ctx->use_graph = 1;
     ctx->kernel_timing = 0;

@@ -141,10 +141,10 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
     const int t0 = off[bk], nt = off[bk + 1] - t0;
     const longlong2 *src = P.tap_buf + (size_t)blockIdx.z * P.max_taps + t0;
     if (threadIdx.x < SF_NB) col_fill[threadIdx.x] = 0;
-    {
+    if (nt <= P.sparse_max) {
         // stage the powers for the closed form while the taps load
         const sf_tw *pw = R.pwc + (size_t)i * 2 * g.r;
-        for (int e = threadIdx.x; e < 2 * g.r; e += blockDim.x) pwc[e] = pw[e];
+        for (int e = threadIdx.x; e < 2 * g.r; e += NT) pwc[e] = pw[e];
     }
     __syncthreads();
     if (nt <= SF_LEAF_TAPS) {

@@ -527,3 +527,23 @@ def test_largest_ring_rotate_and_leaves(oracle):
         sf.sf_layer_destroy(lay)
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("name", ["conv_ragged_two_groups", "shortcut_bias_k_in_3"])
+def test_leaf_closed_form_matches_transform(name):
+    """The leaf column pass of sparse weight tiles in closed form
+    ("leaf_sparse" -1) and as a transform (0, the default) give identical
+    residues."""
+    log_n, L, bits, K, make, wsc, delta = SCALED[name]
+    case = make()
+    s = Session(log_n, L, bits, K, sk_seed=91, rk_seed=92)
+    try:
+        outs = []
+        for sp in (0, -1, 128):
+            sf.sf_ctx_set_option(s.ctx, "leaf_sparse", sp)
+            lay, info, msg, _, got = _run_layer(s, case, delta, delta * wsc, wsc)
+            outs.append(got)
+            sf.sf_layer_destroy(lay)
+        assert (outs[0] == outs[1]).all() and (outs[0] == outs[2]).all()
+    finally:
+        s.close()
