@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch batch")
     ap.add_argument("--reference-sample-s", type=float, default=8.0,
                     help="--impl reference: CPU seconds bound of each step's oracle sample")
     ap.add_argument("--workload", default="conv16", choices=["conv16", "resnet18", "resnet34", "serve"])
@@ -162,6 +163,14 @@ class Workload:
         self.sf.sf_eval_linear_layer(self.ctx, self.layer, self.rk, self.d_in, self.k_in, self.case.sigma_prev,
                                      self.case.sigma_out, self.d_out, self.G, self.stream)
 
+    def autotune(self):
+        """The library's autotuner on this layer: keeps the fastest key-switch
+        launch batch and leaf column pass in the context."""
+        best, ms = self.sf.sf_autotune_layers(self.ctx, [self.layer], [self.rk], [self.d_in], [self.k_in],
+                                              [self.case.sigma_prev], [self.case.sigma_out], [self.d_out], [self.G],
+                                              2, self.stream)
+        return {"ks_batch": best, "ms": ms}
+
     def check(self) -> float:
         """Max |decoded - float64| over all outputs (not timed)."""
         from paper_2509_01253_gb300 import workloads as wl
@@ -242,9 +251,11 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-# per-item DRAM bytes (read + write) from the ncu capture named in the
-# profiles folder, for kernels whose code has not changed since; else None
-TRAFFIC_PER_ITEM = {}
+# per-item DRAM bytes (read + write) from an ncu capture of the small conv16
+# case (dram__bytes_read.sum + dram__bytes_write.sum of one launch of 128
+# merges), for kernels whose code has not changed since; scaled to a launch
+# by its items
+TRAFFIC_PER_ITEM = {"ks3_inner_row": (209.290496e6 + 96.387584e6) / 128}
 
 
 def items_per_layer(kernel: str, info: dict, merges: int) -> int:
@@ -627,6 +638,7 @@ def main():
     stream = wl_.stream
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
     err = None
+    tuned = None
     for w in range(max(3, args.warmup)):
         wl_.step()
         if w == 0:
@@ -634,6 +646,8 @@ def main():
             # workspace, which drops captured graphs: the later warm-up steps recapture)
             torch.cuda.synchronize()
             err = wl_.check()
+            if not args.no_autotune:
+                tuned = wl_.autotune()
     torch.cuda.synchronize()
     # ---- timed region: device-resident inputs
     clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
@@ -704,7 +718,7 @@ def main():
             "config": {"workload": WORKLOAD if not args.small else "conv16-small (profiling case): " + WORKLOAD.replace(
                 "16x32x32 (E = E' = 16384)", "8x16x16 (E = E' = 2048)"), "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                       "ks_batch": None, "ctx_options": args.ctx_opt, "max_abs_err": err},
+                       "autotuned": tuned, "ctx_options": args.ctx_opt, "max_abs_err": err},
             "clocks": clk, "gpu_launches": n_launch // 1, "step_ms": step_ms,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roofline, "kernels": kernel_table}

@@ -410,10 +410,10 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
 }
 
 // ModDown finish.  Groups: (row tile, limb i); items: (merge b, part p).
-// RES = (ACC - conv) P^-1 written over ACC.  smem: forward row twiddles, two
-// buffers of (conversion tile, ACC tile).
+// RES = (ACC - conv) P^-1 written over ACC.  smem: forward row twiddles and
+// two conversion tiles (double-buffered); ACC is read elementwise from global.
 template <int LR, int LC>
-__global__ void __launch_bounds__(SfThreads<LC>::value) k_ks5(SfRing R, SfKsBatch B, int bpg)
+__global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 512 ? 1 : 3) k_ks5(SfRing R, SfKsBatch B, int bpg)
 {
     constexpr int NT = SfThreads<LC>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -424,36 +424,33 @@ __global__ void __launch_bounds__(SfThreads<LC>::value) k_ks5(SfRing R, SfKsBatc
     const size_t tile_off = (size_t)r0 * g.c;
     const int tw_words = tile_words(g.log_c);
     sf_tw *tw = (sf_tw *)smem_raw;
-    u64 *bufs = (u64 *)(tw + SF_NB * g.c);          // 2 x (conv, acc)
+    u64 *bufs = (u64 *)(tw + SF_NB * g.c);          // 2 conversion tiles
     load_row_tw_t<LR, LC, NT>(tw, R.rowT_f, i, r0);
     const int n_items = 2 * B.count;
     if (sub < n_items) {
         const KsLayout Lo = ks_layout(R, B, sub >> 1);
         const int p = sub & 1;
         issue_row_tile_t<LC, NT>(bufs, Lo.x2 + ((size_t)(p * R.L + i) << (LR + LC)) + tile_off);
-        issue_row_tile_t<LC, NT>(bufs + tw_words, Lo.accq + ((size_t)(p * R.L + i) << (LR + LC)) + tile_off);
     }
     sf_cp_commit();
     const u64 pinv = R.md_pinv[i], pinv_p = R.md_pinv_p[i];
     for (int k = 0, it = sub; it < n_items; ++k, it += bpg) {
-        u64 *cur = bufs + (size_t)(k & 1) * 2 * tw_words, *nxt = bufs + (size_t)((k + 1) & 1) * 2 * tw_words;
+        u64 *cur = bufs + (size_t)(k & 1) * tw_words, *nxt = bufs + (size_t)((k + 1) & 1) * tw_words;
         if (it + bpg < n_items) {
             const KsLayout Ln = ks_layout(R, B, (it + bpg) >> 1);
             const int pn = (it + bpg) & 1;
             issue_row_tile_t<LC, NT>(nxt, Ln.x2 + ((size_t)(pn * R.L + i) << (LR + LC)) + tile_off);
-            issue_row_tile_t<LC, NT>(nxt + tw_words, Ln.accq + ((size_t)(pn * R.L + i) << (LR + LC)) + tile_off);
         }
         sf_cp_commit();
         sf_cp_wait<1>();
         __syncthreads();
         tile_forward_t<LC, true, NT>(cur, tw, M.q);
         const int b = it >> 1, p = it & 1;
-        u64 *dst = ks_layout(R, B, b).accq + ((size_t)(p * R.L + i) << (LR + LC)) + tile_off;
+        u64 *acc = ks_layout(R, B, b).accq + ((size_t)(p * R.L + i) << (LR + LC)) + tile_off;
         #pragma unroll
         for (int e = threadIdx.x; e < (SF_NB << LC); e += NT) {
-            const int sl = row_slot_t<LC>(e);
-            const u64 conv = sf_reduce(cur[sl], M.q, M.one_p);
-            dst[e] = sf_mul_shoup(sf_sub(cur[tw_words + sl], conv, M.q), pinv, pinv_p, M.q);
+            const u64 conv = sf_reduce(cur[row_slot_t<LC>(e)], M.q, M.one_p);
+            acc[e] = sf_mul_shoup(sf_sub(acc[e], conv, M.q), pinv, pinv_p, M.q);
         }
         __syncthreads();
     }
@@ -521,7 +518,7 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
     const size_t sm2 = sizeof(sf_tw) * 2 * R.nm * R.r + sizeof(u64) * tile_words(R.log_r) * (2 * maxd + 1);
     const size_t sm3 = smem_rows(R, 2);
     const size_t sm4 = sizeof(sf_tw) * (R.K + R.L) * R.r + sizeof(u64) * tile_words(R.log_r) * (2 * R.K + 1);
-    const size_t sm5 = smem_rows(R, 4);
+    const size_t sm5 = smem_rows(R, 2);
     cudaEvent_t ev;
     for (int off = 0; off < B0.count; off += 32768) {
         SfKsBatch b = B0;
