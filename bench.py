@@ -220,14 +220,15 @@ def kernel_work(kernel: str, g: RingShape, k_in: int = 1):
     half = N // 2
     fbc_up = sum(d * (nm - d) for d in g.digits) * N
     table = {
-        "ks_gather": (3 * L * N * w, L * N),
+        # read E and O (both parts), write TA and the merge's v + tau(u.b)
+        "ks_gather": (7 * L * N * w, 4 * L * N),
         "ks1_inv_row": (2 * L * N * w, L * half * lc),
         "ks2_modup_col": (dnum * nm * N * w, L * half * lr + L * N + fbc_up + (dnum * nm - L) * half * lr),
         "ks3_inner_row": ((dnum * nm + 2 * nm) * N * w, (dnum * nm - L) * half * lc + 2 * dnum * nm * N),
         "ks3_inv_row_p": (4 * K * N * w, 2 * K * half * lc),
         "ks4_moddown_col": ((2 * K + 2 * L) * N * w, 2 * K * half * lr + 2 * K * N + 2 * K * L * N + 2 * L * half * lr),
-        "ks5_finish_row": (6 * L * N * w, 2 * L * half * lc + 2 * L * N),
-        "ks_merge": (8 * L * N * w, 2 * L * N),
+        # read conv, acc and out (2L limbs each), write out
+        "ks5_finish_row": (8 * L * N * w, 2 * L * half * lc + 2 * L * N),
         "leaf_col": (L * N * w, L * half * lr),
         "leaf_row": ((k_in * L + 2 * L) * N * w, k_in * L * half * lc + 2 * k_in * L * N),
     }
@@ -252,10 +253,10 @@ def load_peaks():
 
 
 # per-item DRAM bytes (read + write) from an ncu capture of the small conv16
-# case (dram__bytes_read.sum + dram__bytes_write.sum of one launch of 128
+# case (dram__bytes_read.sum + dram__bytes_write.sum of one launch of 256
 # merges), for kernels whose code has not changed since; scaled to a launch
 # by its items
-TRAFFIC_PER_ITEM = {"ks3_inner_row": (209.290496e6 + 96.387584e6) / 128}
+TRAFFIC_PER_ITEM = {"ks3_inner_row": (411.15776e6 + 232.500224e6) / 256}
 
 
 def items_per_layer(kernel: str, info: dict, merges: int) -> int:

@@ -501,7 +501,7 @@ extern "C" sf_status sf_pack(sf_ctx *ctx, const sf_rotkeys *rk, const uint64_t *
         return sf_set_error(SF_EINVAL, "sf_pack: need 1 <= n_leaves <= n <= N/2, n a power of two");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t ct = ct_words(ctx);
-    const int batch = ctx->ks_batch;
+    const int batch = std::min(ctx->ks_batch, std::max(1, n / 2));   // the widest level has n/2 merges
     Carver cv;
     size_t o_A = cv.take((size_t)n * ct), o_B = cv.take((size_t)std::max(n / 2, 1) * ct),
            o_ks = cv.take(sf_ks_scratch_words(R) * batch);

@@ -70,7 +70,6 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
 {
     const SfRing &R = ctx->ring;
     const size_t ct = ct_words(ctx), ct_bytes = ct * sizeof(u64);
-    const int batch = ctx->ks_batch;
     int max_k_in = 1, max_taps = 1;
     for (auto &j : jobs) {
         max_k_in = std::max(max_k_in, j.k_in);
@@ -129,6 +128,14 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
         maxU = std::max(maxU, c.U);
         wave_words = std::max(wave_words, (size_t)c.U * c.CH * ct);
     }
+    // merges per key-switch launch: the context's batch, or fewer when no tree
+    // level of this call has that many merges
+    int widest = 1;
+    for (auto &c : classes) {
+        widest = std::max(widest, c.U * c.CH / 2);
+        widest = std::max(widest, (int)c.groups.size() * std::max(1, c.nch / 2));
+    }
+    const int batch = std::min(ctx->ks_batch, widest);
     const size_t o_A = cv.take(wave_words);
     const size_t o_B = cv.take(wave_words / 2 + ct);
     for (auto &c : classes) {

@@ -112,7 +112,7 @@ struct sf_rotkeys {
     sf_ctx *ctx;
     uint64_t gen;             // unique per handle (graph cache key)
     std::vector<int32_t> d;   // automorphism indices
-    u64 *d_keys;              // [nd][dnum][2][nm][N], NTT domain, Montgomery form
+    u64 *d_keys;              // per key: [dnum][2][nm][N] NTT-domain values, then their Shoup companions
     size_t key_words;         // words per key
 };
 
@@ -183,7 +183,6 @@ enum SfKernelKind {
     SFK_KS3_INV_ROW_P,
     SFK_KS4_MODDOWN_COL,
     SFK_KS5_FINISH_ROW,
-    SFK_KS_MERGE,
     SFK_LEAF_COL,
     SFK_LEAF_ROW,
     SFK_SHUFFLE,

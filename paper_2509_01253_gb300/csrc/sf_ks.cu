@@ -8,17 +8,19 @@
 //     out = (A',        tau_d(u.b) + B')                [add_v = 0: plain rotate]
 // Without O, u = v = E (the trace step ct + tau_d(ct), or a rotation).
 //
-// Five kernels per batch of merges that share d (and so the key), with the
-// NTT split into a row pass and a column pass (see sf_tile.cuh):
-//   K1 rows : gather tau_d(u.a) (a permutation of NTT slots) -> TA, inverse row pass
+// Kernels per batch of merges that share d (and so the key), with the NTT
+// split into a row pass and a column pass (see sf_tile.cuh):
+//   gather  : TA = tau_d(u.a) (a permutation of NTT slots); out = v, plus tau_d(u.b) on b
+//   K1 rows : inverse row pass of TA
 //   K2 cols : inverse column pass, times N^-1 -> coefficients; ModUp of each
 //             digit to the other moduli (fast base conversion); forward column pass
 //   K3 rows : forward row pass of each digit's extension, inner product with
-//             the key over all digits (128-bit accumulation, one Montgomery
-//             reduction); P-limbs continue with the inverse row pass
+//             the key over all digits (Shoup products with the key's stored
+//             companions, lazy sums, one reduction); the P-limbs' inverse row
+//             pass follows in a second row kernel
 //   K4 cols : inverse column pass of the P-limbs, times N^-1 -> coefficients;
 //             base conversion P -> each q_i; forward column pass
-//   K5 rows : forward row pass; (acc_Q - conv) * P^-1; add v and tau_d(u.b); store
+//   K5 rows : forward row pass; out += (acc_Q - conv) * P^-1
 #include "sf_async.cuh"
 #include "sf_internal.h"
 #include "sf_kernels.cuh"
@@ -119,7 +121,12 @@ __device__ __forceinline__ u64 merge_v(const SfRing &R, const SfKsBatch &B, cons
 // ---------------------------------------------------------------------------
 
 
-// Elementwise: TA[b][i][j] = tau_d(E - X^s O).a at slot j (a slot permutation).
+// Elementwise, one pass over E and O per merge (a slot permutation and
+// monomial products in the NTT domain):
+//   TA[b][i][j] = tau_d(u.a)[j],  u = E - X^s O
+//   out.a[j]    = v.a[j]                      (0 for a plain rotation)
+//   out.b[j]    = v.b[j] + tau_d(u.b)[j],     v = E + X^s O
+// The ModDown finish (k_ks5) then adds the key-switch result into out.
 // grid (N / (256 SF_EW), L, merges): each thread does SF_EW slots, so the
 // per-merge pointers are set up once per thread.
 #define SF_EW 8
@@ -128,12 +135,19 @@ __global__ void __launch_bounds__(256) k_ks_gather(SfRing R, SfKsBatch B)
     const int b = blockIdx.z, i = blockIdx.y;
     const u64 *E = merge_E(B, b), *O = merge_O(B, b);
     u64 *ta = ks_layout(R, B, b).ta + ((size_t)i << R.log_n);
+    u64 *out = merge_out(B, b);
+    u64 *oa = out + ((size_t)i << R.log_n), *ob = out + ((size_t)(R.L + i) << R.log_n);
+    const u64 q = R.m[i].q;
     const int j0 = blockIdx.x * (256 * SF_EW) + threadIdx.x;
 #pragma unroll
     for (int x = 0; x < SF_EW; ++x) {
         const int j = j0 + x * 256;
         if (j >= R.n) break;   // rings smaller than one block's 256 SF_EW slots
-        ta[j] = merge_u(R, B, E, O, 0, i, auto_src(j, B.d, R.log_n));
+        const int src = auto_src(j, B.d, R.log_n);
+        ta[j] = merge_u(R, B, E, O, 0, i, src);
+        const u64 ub = merge_u(R, B, E, O, 1, i, src);
+        oa[j] = B.add_v ? merge_v(R, B, E, O, 0, i, j) : 0;
+        ob[j] = B.add_v ? sf_add(merge_v(R, B, E, O, 1, i, j), ub, q) : ub;
     }
 }
 
@@ -146,7 +160,7 @@ struct SfRowSet {
 };
 
 template <bool INV, int LR, int LC>
-__global__ void __launch_bounds__(SfThreads<LC>::value) k_rows(SfRing R, SfKsBatch B, SfRowSet S, int bpg)
+__global__ void __launch_bounds__(SfThreads<LC>::value, LC >= 8 ? 2 : 3) k_rows(SfRing R, SfKsBatch B, SfRowSet S, int bpg)
 {
     constexpr int NT = SfThreads<LC>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -158,17 +172,24 @@ __global__ void __launch_bounds__(SfThreads<LC>::value) k_rows(SfRing R, SfKsBat
     const size_t per = sf_ks_scratch_words_dev(R);
     const size_t off_s = S.src_off + ((size_t)t << (LR + LC)) + (size_t)r0 * g.c;
     const size_t off_d = S.dst_off + ((size_t)t << (LR + LC)) + (size_t)r0 * g.c;
+    constexpr bool DB = sf_rows_double_buffered(LC);
     sf_tw *tw = (sf_tw *)smem_raw;
     u64 *buf0 = (u64 *)(tw + SF_NB * g.c);
-    u64 *buf1 = buf0 + tile_words(g.log_c);
+    u64 *buf1 = DB ? buf0 + tile_words(g.log_c) : buf0;
     load_row_tw_t<LR, LC, NT>(tw, INV ? R.rowT_i : R.rowT_f, mod, r0);
-    if (sub < B.count) issue_row_tile_t<LC, NT>(buf0, B.scratch + per * sub + off_s);
+    if (DB && sub < B.count) issue_row_tile_t<LC, NT>(buf0, B.scratch + per * sub + off_s);
     sf_cp_commit();
     for (int k = 0, b = sub; b < B.count; ++k, b += bpg) {
         u64 *cur = (k & 1) ? buf1 : buf0, *nxt = (k & 1) ? buf0 : buf1;
-        if (b + bpg < B.count) issue_row_tile_t<LC, NT>(nxt, B.scratch + per * (b + bpg) + off_s);
-        sf_cp_commit();
-        sf_cp_wait<1>();
+        if (DB) {
+            if (b + bpg < B.count) issue_row_tile_t<LC, NT>(nxt, B.scratch + per * (b + bpg) + off_s);
+            sf_cp_commit();
+            sf_cp_wait<1>();
+        } else {
+            issue_row_tile_t<LC, NT>(cur, B.scratch + per * b + off_s);
+            sf_cp_commit();
+            sf_cp_wait<0>();
+        }
         __syncthreads();
         if (INV) tile_inverse_t<LC, true, NT>(cur, tw, M.q);
         else tile_forward_t<LC, true, NT>(cur, tw, M.q);
@@ -272,18 +293,22 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 
     const int m = grp % R.nm, r0 = (grp / R.nm) * SF_NB;
     const SfMod M = R.m[m];
     const size_t tile_off = (size_t)r0 * g.c;
+    constexpr bool DB = true;   // registers, not shared memory, bound these kernels to one 512-thread block per SM
     sf_tw *tw = (sf_tw *)smem_raw;
     u64 *buf0 = (u64 *)(tw + SF_NB * g.c);
-    u64 *buf1 = buf0 + tile_words(g.log_c);
+    u64 *buf1 = DB ? buf0 + tile_words(g.log_c) : buf0;
     load_row_tw_t<LR, LC, NT>(tw, R.rowT_f, m, r0);
     const int n_mine = sub < B.count ? (B.count - sub + bpg - 1) / bpg : 0;
     const int steps = n_mine * R.dnum;
-    // step k -> merge sub + (k / dnum) * bpg, digit k % dnum
-    if (steps > 0) {
-        const KsLayout Lo = ks_layout(R, B, sub);
-        const bool own = (m < min(R.K, R.L));
-        issue_row_tile_t<LC, NT>(buf0, (own ? Lo.ta + ((size_t)m << (LR + LC)) : Lo.x2 + ((size_t)m << (LR + LC))) + tile_off);
-    }
+    // step k -> merge sub + (k / dnum) * bpg, digit k % dnum; its tile is TA's
+    // limb m when m is one of digit j's own limbs, else the digit's extension
+    auto step_src = [&](int kk) -> const u64 * {
+        const int bb = sub + (kk / R.dnum) * bpg, jj = kk % R.dnum;
+        const KsLayout Ls = ks_layout(R, B, bb);
+        const bool own_s = (m >= jj * R.K && m < min((jj + 1) * R.K, R.L));
+        return (own_s ? Ls.ta + ((size_t)m << (LR + LC)) : Ls.x2 + ((size_t)(jj * R.nm + m) << (LR + LC))) + tile_off;
+    };
+    if (DB && steps > 0) issue_row_tile_t<LC, NT>(buf0, step_src(0));
     sf_cp_commit();
     u64 acc_a[EPT], acc_b[EPT];
 #pragma unroll
@@ -291,14 +316,15 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 
     for (int k = 0; k < steps; ++k) {
         const int b = sub + (k / R.dnum) * bpg, j = k % R.dnum;
         u64 *cur = (k & 1) ? buf1 : buf0, *nxt = (k & 1) ? buf0 : buf1;
-        if (k + 1 < steps) {
-            const int bn = sub + ((k + 1) / R.dnum) * bpg, jn = (k + 1) % R.dnum;
-            const KsLayout Ln = ks_layout(R, B, bn);
-            const bool own_n = (m >= jn * R.K && m < min((jn + 1) * R.K, R.L));
-            issue_row_tile_t<LC, NT>(nxt, (own_n ? Ln.ta + ((size_t)m << (LR + LC)) : Ln.x2 + ((size_t)(jn * R.nm + m) << (LR + LC))) + tile_off);
+        if (DB) {
+            if (k + 1 < steps) issue_row_tile_t<LC, NT>(nxt, step_src(k + 1));
+            sf_cp_commit();
+            sf_cp_wait<1>();
+        } else {
+            issue_row_tile_t<LC, NT>(cur, step_src(k));
+            sf_cp_commit();
+            sf_cp_wait<0>();
         }
-        sf_cp_commit();
-        sf_cp_wait<1>();
         __syncthreads();
         const bool own = (m >= j * R.K && m < min((j + 1) * R.K, R.L));
         if (!own) tile_forward_t<LC, true, NT>(cur, tw, M.q);
@@ -410,8 +436,8 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
 }
 
 // ModDown finish.  Groups: (row tile, limb i); items: (merge b, part p).
-// RES = (ACC - conv) P^-1 written over ACC.  smem: forward row twiddles and
-// two conversion tiles (double-buffered); ACC is read elementwise from global.
+// out += (ACC - conv) P^-1.  smem: forward row twiddles and two conversion
+// tiles (double-buffered); ACC and out are read elementwise from global.
 template <int LR, int LC>
 __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 512 ? 1 : 3) k_ks5(SfRing R, SfKsBatch B, int bpg)
 {
@@ -423,59 +449,42 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 
     const SfMod M = R.m[i];
     const size_t tile_off = (size_t)r0 * g.c;
     const int tw_words = tile_words(g.log_c);
+    constexpr bool DB = true;   // registers, not shared memory, bound these kernels to one 512-thread block per SM
     sf_tw *tw = (sf_tw *)smem_raw;
-    u64 *bufs = (u64 *)(tw + SF_NB * g.c);          // 2 conversion tiles
+    u64 *bufs = (u64 *)(tw + SF_NB * g.c);          // 2 conversion tiles (1 when single-buffered)
     load_row_tw_t<LR, LC, NT>(tw, R.rowT_f, i, r0);
     const int n_items = 2 * B.count;
-    if (sub < n_items) {
-        const KsLayout Lo = ks_layout(R, B, sub >> 1);
-        const int p = sub & 1;
-        issue_row_tile_t<LC, NT>(bufs, Lo.x2 + ((size_t)(p * R.L + i) << (LR + LC)) + tile_off);
-    }
+    auto item_src = [&](int it2) -> const u64 * {
+        const KsLayout Ls = ks_layout(R, B, it2 >> 1);
+        return Ls.x2 + ((size_t)((it2 & 1) * R.L + i) << (LR + LC)) + tile_off;
+    };
+    if (DB && sub < n_items) issue_row_tile_t<LC, NT>(bufs, item_src(sub));
     sf_cp_commit();
     const u64 pinv = R.md_pinv[i], pinv_p = R.md_pinv_p[i];
     for (int k = 0, it = sub; it < n_items; ++k, it += bpg) {
-        u64 *cur = bufs + (size_t)(k & 1) * tw_words, *nxt = bufs + (size_t)((k + 1) & 1) * tw_words;
-        if (it + bpg < n_items) {
-            const KsLayout Ln = ks_layout(R, B, (it + bpg) >> 1);
-            const int pn = (it + bpg) & 1;
-            issue_row_tile_t<LC, NT>(nxt, Ln.x2 + ((size_t)(pn * R.L + i) << (LR + LC)) + tile_off);
+        u64 *cur = bufs + (DB ? (size_t)(k & 1) * tw_words : 0), *nxt = bufs + (DB ? (size_t)((k + 1) & 1) * tw_words : 0);
+        if (DB) {
+            if (it + bpg < n_items) issue_row_tile_t<LC, NT>(nxt, item_src(it + bpg));
+            sf_cp_commit();
+            sf_cp_wait<1>();
+        } else {
+            issue_row_tile_t<LC, NT>(cur, item_src(it));
+            sf_cp_commit();
+            sf_cp_wait<0>();
         }
-        sf_cp_commit();
-        sf_cp_wait<1>();
         __syncthreads();
         tile_forward_t<LC, true, NT>(cur, tw, M.q);
         const int b = it >> 1, p = it & 1;
-        u64 *acc = ks_layout(R, B, b).accq + ((size_t)(p * R.L + i) << (LR + LC)) + tile_off;
+        const size_t off = ((size_t)(p * R.L + i) << (LR + LC)) + tile_off;
+        const u64 *acc = ks_layout(R, B, b).accq + off;
+        u64 *out = merge_out(B, b) + off;   // holds v (+ tau_d(u.b)) from k_ks_gather
         #pragma unroll
         for (int e = threadIdx.x; e < (SF_NB << LC); e += NT) {
             const u64 conv = sf_reduce(cur[row_slot_t<LC>(e)], M.q, M.one_p);
-            acc[e] = sf_mul_shoup(sf_sub(acc[e], conv, M.q), pinv, pinv_p, M.q);
+            const u64 res = sf_mul_shoup(sf_sub(acc[e], conv, M.q), pinv, pinv_p, M.q);
+            out[e] = sf_add(out[e], res, M.q);
         }
         __syncthreads();
-    }
-}
-
-// Elementwise merge: out = [add_v] (E + X^s O) + RES, plus tau_d(u.b) on part b.
-// grid (N / (256 SF_EW), 2L, merges), SF_EW slots per thread.
-__global__ void __launch_bounds__(256) k_ks_merge(SfRing R, SfKsBatch B)
-{
-    const int b = blockIdx.z, pi = blockIdx.y;
-    const int p = pi >= R.L ? 1 : 0, i = pi - p * R.L;
-    const u64 *E = merge_E(B, b), *O = merge_O(B, b);
-    const u64 q = R.m[i].q;
-    const size_t base = (size_t)pi << R.log_n;
-    const u64 *res_in = ks_layout(R, B, b).accq + base;
-    u64 *out = merge_out(B, b) + base;
-    const int j0 = blockIdx.x * (256 * SF_EW) + threadIdx.x;
-#pragma unroll
-    for (int x = 0; x < SF_EW; ++x) {
-        const int j = j0 + x * 256;
-        if (j >= R.n) break;
-        u64 res = res_in[j];
-        if (B.add_v) res = sf_add(res, merge_v(R, B, E, O, p, i, j), q);
-        if (p == 1) res = sf_add(res, merge_u(R, B, E, O, 1, i, auto_src(j, B.d, R.log_n)), q);
-        out[j] = res;
     }
 }
 
@@ -514,7 +523,8 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
     if (B0.count <= 0) return SF_OK;
     const int maxd = std::min(R.K, R.L);
     const int rtiles = R.r / SF_NB, ctiles = R.c / SF_NB;
-    const size_t sm_rows = smem_rows(R, 2);
+    const int row_bufs = sf_rows_double_buffered(R.log_c) ? 2 : 1;
+    const size_t sm_rows = smem_rows(R, row_bufs);
     const size_t sm2 = sizeof(sf_tw) * 2 * R.nm * R.r + sizeof(u64) * tile_words(R.log_r) * (2 * maxd + 1);
     const size_t sm3 = smem_rows(R, 2);
     const size_t sm4 = sizeof(sf_tw) * (R.K + R.L) * R.r + sizeof(u64) * tile_words(R.log_r) * (2 * R.K + 1);
@@ -526,7 +536,7 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
         b.first = B0.first + off;
         b.scratch += sf_ks_scratch_words(R) * off;
         const int ew_blocks = (R.n + 256 * SF_EW - 1) / (256 * SF_EW);
-        const dim3 eg(ew_blocks, R.L, b.count), mg(ew_blocks, 2 * R.L, b.count);
+        const dim3 eg(ew_blocks, R.L, b.count);
         SF_GEO_DISPATCH(R.log_n, {
             constexpr int NTR = SfThreads<LC>::value, NTC = SfThreads<LR>::value;
             sf_launch_begin(ctx, SFK_KS_GATHER, st, &ev);
@@ -582,9 +592,6 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
                 k_ks5<LR, LC><<<ng * bpg, NTR, sm5, st>>>(R, b, bpg);
             }
             sf_launch_end(ctx, SFK_KS5_FINISH_ROW, st, ev);
-            sf_launch_begin(ctx, SFK_KS_MERGE, st, &ev);
-            k_ks_merge<<<mg, 256, 0, st>>>(R, b);
-            sf_launch_end(ctx, SFK_KS_MERGE, st, ev);
         });
     }
     SF_CUDA_TRY(cudaGetLastError());

@@ -19,7 +19,7 @@ struct SfKsBatch {
     int d;          // automorphism X -> X^d
     unsigned s;     // O is multiplied by X^s
     int add_v;      // 1: out = v + KS(...), 0: plain rotation
-    const u64 *key; // [dnum][2][nm][N], NTT domain, Montgomery form
+    const u64 *key; // [dnum][2][nm][N] NTT-domain values, then the same shape of Shoup companions
     u64 *scratch;   // sf_ks_scratch_words(R) words per merge of one launch batch
 };
 

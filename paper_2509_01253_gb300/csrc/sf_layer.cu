@@ -4,11 +4,13 @@
 // extracted for stream position p = jN + k is N^-1 X^-k ct_j, so output o is
 //     y_o = sum_j w_{o,j}(X) * ct_j,   w_{o,j} = N^-1 sum_{taps i in ct j} Wq[o,i] X^-k(i)
 // with k(i) the in-ciphertext position of input i after unshuffling
-// (p = sigma_prev^-1(i)).  Two kernels per batch of outputs:
-//   leaf_col : builds the sparse w_{o,j} column tile straight in shared memory
-//              (no global read) and runs the forward column pass,
+// (p = sigma_prev^-1(i)).  Three kernels per batch of outputs:
+//   leaf_prep: walks each output's receptive field once and buckets its taps
+//              by (input ciphertext, 16-column tile),
+//   leaf_col : builds the sparse w_{o,j} column tile in shared memory from its
+//              bucket and runs the forward column pass (or its closed form),
 //   leaf_row : forward row pass, then the product with every input ciphertext
-//              (NTT domain, Montgomery form) accumulated in 128 bits -> leaf.
+//              (NTT domain, Shoup companions stored beside it), lazy sums -> leaf.
 // Step 9 (shuffle) is the slot -> output map sigma_out; step 10 (packing) is
 // the PackLWEs tree plus field trace driven by sf_pack_tree below.
 #include "sf_internal.h"

@@ -39,6 +39,11 @@
 // points: 256 (8 warps) up to 128 points, 512 for 256 points, so that every
 // tile size gives each thread the same 8 elements
 __host__ __device__ __forceinline__ int sf_tile_threads(int log_s) { return log_s >= 8 ? 512 : SF_THREADS; }
+// The generic row pass double-buffers its tiles with cp.async, except for
+// 256-point rows: there the staged twiddles (64 KiB) and one tile already
+// take 98 KiB, and a single buffer lets two 16-warp blocks share an SM.
+__host__ __device__ constexpr bool sf_rows_double_buffered(int log_c) { return log_c < 8; }
+
 // runs the statements with the compile-time block size NT = nt (256 or 512)
 #define SF_NT_DISPATCH(nt, ...)          \
     do {                                 \
