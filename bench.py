@@ -638,17 +638,14 @@ def main():
         sf.sf_ctx_set_option(wl_.ctx, name, int(val))
     stream = wl_.stream
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
-    err = None
-    tuned = None
-    for w in range(max(3, args.warmup)):
+    # one round, its decryption check (it may grow the context's workspace,
+    # which drops captured graphs) and the autotuner, then the warm-up proper
+    wl_.step()
+    torch.cuda.synchronize()
+    err = wl_.check()
+    tuned = None if args.no_autotune else wl_.autotune()
+    for _ in range(max(3, args.warmup)):
         wl_.step()
-        if w == 0:
-            # decryption check after the first round (it may grow the context's
-            # workspace, which drops captured graphs: the later warm-up steps recapture)
-            torch.cuda.synchronize()
-            err = wl_.check()
-            if not args.no_autotune:
-                tuned = wl_.autotune()
     torch.cuda.synchronize()
     # ---- timed region: device-resident inputs
     clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])

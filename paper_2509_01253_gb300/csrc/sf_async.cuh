@@ -28,3 +28,9 @@ __device__ __forceinline__ void sf_cp_wait()
 {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
+
+// Hint: bring the 128-byte line holding p into L2 (no data returned).
+__device__ __forceinline__ void sf_prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}

@@ -139,15 +139,32 @@ __global__ void __launch_bounds__(256) k_ks_gather(SfRing R, SfKsBatch B)
     u64 *oa = out + ((size_t)i << R.log_n), *ob = out + ((size_t)(R.L + i) << R.log_n);
     const u64 q = R.m[i].q;
     const int j0 = blockIdx.x * (256 * SF_EW) + threadIdx.x;
+    const SfMod &M = R.m[i];
+    const size_t ea = (size_t)i << R.log_n, eb = (size_t)(R.L + i) << R.log_n;
+    const size_t pb = (size_t)i << (R.log_n + 1);
 #pragma unroll
     for (int x = 0; x < SF_EW; ++x) {
         const int j = j0 + x * 256;
         if (j >= R.n) break;   // rings smaller than one block's 256 SF_EW slots
         const int src = auto_src(j, B.d, R.log_n);
-        ta[j] = merge_u(R, B, E, O, 0, i, src);
-        const u64 ub = merge_u(R, B, E, O, 1, i, src);
-        oa[j] = B.add_v ? merge_v(R, B, E, O, 0, i, j) : 0;
-        ob[j] = B.add_v ? sf_add(merge_v(R, B, E, O, 1, i, j), ub, q) : ub;
+        // every load before any store (the stores could alias nothing, but the
+        // compiler cannot know): 4 coalesced, 4 gathered, 2 monomial pairs
+        u64 Eaj = E[ea + j], Ebj = E[eb + j], Eas = E[ea + src], Ebs = E[eb + src];
+        if (O) {
+            const unsigned kj = mono_index(j, B.s, R.log_n), ks = mono_index(src, B.s, R.log_n);
+            const u64 wj = R.pw[pb + kj], wjp = R.pw_p[pb + kj], ws = R.pw[pb + ks], wsp = R.pw_p[pb + ks];
+            const u64 Oaj = O[ea + j], Obj = O[eb + j], Oas = O[ea + src], Obs = O[eb + src];
+            const u64 xaj = sf_mul_shoup(Oaj, wj, wjp, M.q), xbj = sf_mul_shoup(Obj, wj, wjp, M.q);
+            const u64 xas = sf_mul_shoup(Oas, ws, wsp, M.q), xbs = sf_mul_shoup(Obs, ws, wsp, M.q);
+            ta[j] = sf_sub(Eas, xas, M.q);
+            const u64 ub = sf_sub(Ebs, xbs, M.q);
+            oa[j] = B.add_v ? sf_add(Eaj, xaj, M.q) : 0;
+            ob[j] = B.add_v ? sf_add(sf_add(Ebj, xbj, M.q), ub, q) : ub;
+        } else {
+            ta[j] = Eas;
+            oa[j] = B.add_v ? Eaj : 0;
+            ob[j] = B.add_v ? sf_add(Ebj, Ebs, q) : Ebs;
+        }
     }
 }
 
@@ -472,12 +489,20 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 
             sf_cp_commit();
             sf_cp_wait<0>();
         }
-        __syncthreads();
-        tile_forward_t<LC, true, NT>(cur, tw, M.q);
         const int b = it >> 1, p = it & 1;
         const size_t off = ((size_t)(p * R.L + i) << (LR + LC)) + tile_off;
         const u64 *acc = ks_layout(R, B, b).accq + off;
         u64 *out = merge_out(B, b) + off;   // holds v (+ tau_d(u.b)) from k_ks_gather
+        // pull this item's accumulator and output rows toward L2 while the row pass runs
+        if ((threadIdx.x & 15) == 0) {
+#pragma unroll
+            for (int e = threadIdx.x; e < (SF_NB << LC); e += NT) {
+                sf_prefetch_l2(acc + e);
+                sf_prefetch_l2(out + e);
+            }
+        }
+        __syncthreads();
+        tile_forward_t<LC, true, NT>(cur, tw, M.q);
         #pragma unroll
         for (int e = threadIdx.x; e < (SF_NB << LC); e += NT) {
             const u64 conv = sf_reduce(cur[row_slot_t<LC>(e)], M.q, M.one_p);
