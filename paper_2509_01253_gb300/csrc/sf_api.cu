@@ -180,6 +180,16 @@ extern "C" sf_status sf_rotkeys_export(sf_ctx *ctx, const sf_rotkeys *rk, int32_
     for (int x = 0; x < npol; ++x) jobs.push_back({tmp + (size_t)x * R.n, tmp + (size_t)x * R.n, x % R.nm});
     SF_TRY(sf_ntt_jobs(ctx, jobs.data(), npol, true, 0));
     SF_CUDA_TRY(cudaMemcpy(h_key, tmp, sizeof(u64) * vals, cudaMemcpyDeviceToHost));
+    // the stored data limbs carry P^-1 (see the key-switch kernels): export the key itself
+    const sf_params *p = ctx->prm;
+    for (int x = 0; x < npol; ++x) {
+        const int m = x % R.nm;
+        if (m >= R.L) continue;
+        u64 pm = 1;
+        for (int k = 0; k < R.K; ++k) pm = sf_host_mulmod(pm, p->mods[R.L + k] % p->mods[m], p->mods[m]);
+        u64 *row = h_key + (size_t)x * R.n;
+        for (int k = 0; k < R.n; ++k) row[k] = sf_host_mulmod(row[k], pm, p->mods[m]);
+    }
     return SF_OK;
 }
 

@@ -7,8 +7,8 @@
 //  * Montgomery (1985) REDC with R = 2^64 for products of two variable
 //    residues: for T < q*2^64, (T + m q)/2^64 with m = T * (-q^-1) mod 2^64
 //    lies in [0, 2q) and equals T * 2^-64 mod q.
-//  * Harvey's lazy butterflies keep NTT values in [0, 4q) (forward) and
-//    [0, 2q) (inverse); 4q < 2^53 leaves ample headroom in 64 bits.
+//  * Harvey's lazy butterflies keep inverse-NTT values in [0, 4q); forward
+//    values grow by at most 4q per stage (see sf_bfly_ct), far below 2^64.
 #pragma once
 #include <stdint.h>
 
@@ -119,13 +119,19 @@ SF_HD void sf_bfly_ct(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 two_q)
     Y = x - t + 2 * two_q;
 }
 
-// Inverse (Gentleman-Sande) lazy butterfly: X, Y in [0, 2q) -> X', Y' in [0, 2q).
+// Inverse (Gentleman-Sande) lazy butterfly: X, Y in [0, 4q) -> X', Y' in
+// [0, 4q).  The sum is brought back below 4q by one conditional subtraction;
+// the difference X - Y + 4q (below 8q) is multiplied with the truncated
+// quotient, which lands in [0, 4q) for any input.  Every consumer of an
+// inverse pass either runs more of these butterflies or finishes with a full
+// Shoup product (any input below 2^64, canonical output).
 SF_HD void sf_bfly_gs(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 two_q)
 {
+    const u64 four_q = 2 * two_q;
     u64 x = X + Y;
-    u64 t = X - Y + two_q;
-    X = x >= two_q ? x - two_q : x;
-    Y = sf_mul_shoup_lazy(t, w, wp, q);
+    u64 t = X - Y + four_q;
+    X = x >= four_q ? x - four_q : x;
+    Y = sf_mul_shoup_lazy4(t, w, wp, q);
 }
 
 // Reduce a lazy value in [0, 4q) to [0, q).

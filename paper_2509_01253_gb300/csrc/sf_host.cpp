@@ -478,6 +478,10 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
     R.K = K;
     R.nm = nm;
     R.dnum = p->dnum;
+    R.modup_copy = 1;
+    for (int a = 0; a < nm; ++a)
+        for (int b = 0; b < nm; ++b)
+            if (p->mods[a] / 4 >= p->mods[b]) R.modup_copy = 0;
     std::vector<u64> psi((size_t)nm * N), psi_p((size_t)nm * N), ipsi((size_t)nm * N), ipsi_p((size_t)nm * N);
     std::vector<u64> pw((size_t)nm * 2 * N), pw_p((size_t)nm * 2 * N);
     for (int m = 0; m < nm; ++m) {
@@ -570,8 +574,18 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
             }
         }
     }
-    // ModDown constants
+    // ModDown constants.  ModDown(x) = (x_Q - conv_P(x_P)) P^-1: the factor
+    // P^-1 is carried by the conversion constants (Phat_k P^-1 mod q_i) and by
+    // the reduction of the key products of the data limbs (times P^-1 mod
+    // q_i), so the finish is one subtraction; every residue is unchanged.
     std::vector<u64> md_inv(K), md_inv_p(K), md_phat((size_t)K * L), md_phat_p((size_t)K * L), md_pinv(L), md_pinv_p(L);
+    for (int i = 0; i < L; ++i) {
+        u64 qi = p->mods[i];
+        u64 pm = 1;
+        for (int k = 0; k < K; ++k) pm = sf_host_mulmod(pm, p->mods[L + k] % qi, qi);
+        md_pinv[i] = sf_host_invmod(pm, qi);
+        md_pinv_p[i] = sf_shoup_companion(md_pinv[i], qi);
+    }
     for (int k = 0; k < K; ++k) {
         u64 pk = p->mods[L + k];
         u64 ph = 1;
@@ -584,16 +598,10 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
             u64 v = 1;
             for (int k2 = 0; k2 < K; ++k2)
                 if (k2 != k) v = sf_host_mulmod(v, p->mods[L + k2] % qi, qi);
+            v = sf_host_mulmod(v, md_pinv[i], qi);
             md_phat[(size_t)k * L + i] = v;
             md_phat_p[(size_t)k * L + i] = sf_shoup_companion(v, qi);
         }
-    }
-    for (int i = 0; i < L; ++i) {
-        u64 qi = p->mods[i];
-        u64 pm = 1;
-        for (int k = 0; k < K; ++k) pm = sf_host_mulmod(pm, p->mods[L + k] % qi, qi);
-        md_pinv[i] = sf_host_invmod(pm, qi);
-        md_pinv_p[i] = sf_shoup_companion(md_pinv[i], qi);
     }
     sf_status st = SF_OK;
 #define UP(v, f)                                      \

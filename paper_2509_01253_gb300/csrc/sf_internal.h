@@ -25,6 +25,10 @@ struct SfMod {
 struct SfRing {
     int log_n, n, log_r, r, log_c, c;
     int L, K, nm, dnum;
+    // every modulus is below 4x every other one: a one-limb digit's ModUp
+    // (its residue itself, Qhat = 1) is a valid lazy input of the forward NTT
+    // modulo any other modulus, with no reduction
+    int modup_copy;
     SfMod m[SF_MAX_MODULI];
     // twiddle tables, [nm][N] each (index 0 unused)
     const u64 *psi, *psi_p, *ipsi, *ipsi_p;
@@ -39,7 +43,8 @@ struct SfRing {
     //        Shoup (N^-1 finishes the inverse NTT); Qhat_i mod m for every m.
     const u64 *mu_inv, *mu_inv_p;   // [dnum][K]
     const u64 *mu_qhat, *mu_qhat_p; // [dnum][K][nm]
-    // ModDown: N^-1 (Phat_k mod p_k)^-1, Phat_k mod q_i, P^-1 mod q_i (all Shoup)
+    // ModDown: N^-1 (Phat_k mod p_k)^-1; Phat_k P^-1 mod q_i (the conversion
+    // carries the final factor P^-1); P^-1 mod q_i (all Shoup)
     const u64 *md_inv, *md_inv_p;   // [K]
     const u64 *md_phat, *md_phat_p; // [K][L]
     const u64 *md_pinv, *md_pinv_p; // [L]

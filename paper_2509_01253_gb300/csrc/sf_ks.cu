@@ -16,11 +16,13 @@
 //             digit to the other moduli (fast base conversion); forward column pass
 //   K3 rows : forward row pass of each digit's extension, inner product with
 //             the key over all digits (Shoup products with the key's stored
-//             companions, lazy sums, one reduction); the P-limbs' inverse row
-//             pass follows in a second row kernel
+//             companions, lazy sums, one reduction; the key's data limbs
+//             carry the ModDown factor P^-1); the P-limbs' inverse row pass
+//             follows in a second row kernel
 //   K4 cols : inverse column pass of the P-limbs, times N^-1 -> coefficients;
-//             base conversion P -> each q_i; forward column pass
-//   K5 rows : forward row pass; out += (acc_Q - conv) * P^-1
+//             base conversion P -> each q_i (constants Phat_k P^-1 mod q_i);
+//             forward column pass
+//   K5 rows : forward row pass; out += acc_Q P^-1 - conv P^-1
 #include "sf_async.cuh"
 #include "sf_internal.h"
 #include "sf_kernels.cuh"
@@ -267,24 +269,30 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
         for (int m = 0; m < R.nm; ++m) {
             if (m >= lo && m < hi) continue;
             const SfMod &M = R.m[m];
-            #pragma unroll
-            // base conversion, lazy: each term in [0, 2q), the sum below 2q * nd
-            // (digits hold at most 4 limbs: K <= 4)
-            u64 qh[4], qhp[4];
+            if (nd == 1 && R.modup_copy) {
+                // one-limb digit: Qhat = 1, so the conversion is the canonical
+                // residue itself, below 4 q_m and taken as it is by the transform
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const size_t ci = ((size_t)(j * R.K + t)) * R.nm + m;
-                qh[t] = t < nd ? R.mu_qhat[ci] : 0;
-                qhp[t] = t < nd ? R.mu_qhat_p[ci] : 0;
-            }
+                for (int e = threadIdx.x; e < (SF_NB << LR); e += NT) work[col_slot(e)] = cur[col_slot(e)];
+            } else {
+                // base conversion, lazy: each term in [0, 2q), the sum below 2q * nd
+                // (digits hold at most 4 limbs: K <= 4)
+                u64 qh[4], qhp[4];
 #pragma unroll
-            for (int e = threadIdx.x; e < (SF_NB << LR); e += NT) {
-                const int sl = col_slot(e);
-                u64 acc = 0;
+                for (int t = 0; t < 4; ++t) {
+                    const size_t ci = ((size_t)(j * R.K + t)) * R.nm + m;
+                    qh[t] = t < nd ? R.mu_qhat[ci] : 0;
+                    qhp[t] = t < nd ? R.mu_qhat_p[ci] : 0;
+                }
 #pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (t < nd) acc += sf_mul_shoup_lazy(cur[(size_t)t * tw_words + sl], qh[t], qhp[t], M.q);
-                work[sl] = acc;
+                for (int e = threadIdx.x; e < (SF_NB << LR); e += NT) {
+                    const int sl = col_slot(e);
+                    u64 acc = 0;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (t < nd) acc += sf_mul_shoup_lazy(cur[(size_t)t * tw_words + sl], qh[t], qhp[t], M.q);
+                    work[sl] = acc;
+                }
             }
             __syncthreads();
             tile_forward_t<LR, false, NT>(work, twf + (size_t)m * g.r, M.q);
@@ -453,7 +461,7 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
 }
 
 // ModDown finish.  Groups: (row tile, limb i); items: (merge b, part p).
-// out += (ACC - conv) P^-1.  smem: forward row twiddles and two conversion
+// out += ACC - conv, both already multiplied by P^-1.  smem: forward row twiddles and two conversion
 // tiles (double-buffered); ACC and out are read elementwise from global.
 template <int LR, int LC>
 __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 512 ? 1 : 3) k_ks5(SfRing R, SfKsBatch B, int bpg)
@@ -477,7 +485,9 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 
     };
     if (DB && sub < n_items) issue_row_tile_t<LC, NT>(bufs, item_src(sub));
     sf_cp_commit();
-    const u64 pinv = R.md_pinv[i], pinv_p = R.md_pinv_p[i];
+    // conv leaves the lazy forward transform below 72 q (inputs below 2 K q <= 8 q,
+    // at most 16 stages adding 4 q each); 128 q keeps the sum positive
+    const u64 conv_off = 128 * M.q;
     for (int k = 0, it = sub; it < n_items; ++k, it += bpg) {
         u64 *cur = bufs + (DB ? (size_t)(k & 1) * tw_words : 0), *nxt = bufs + (DB ? (size_t)((k + 1) & 1) * tw_words : 0);
         if (DB) {
@@ -503,12 +513,10 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 
         }
         __syncthreads();
         tile_forward_t<LC, true, NT>(cur, tw, M.q);
+        // acc and conv both carry P^-1 already: out += acc - conv, one reduction
         #pragma unroll
-        for (int e = threadIdx.x; e < (SF_NB << LC); e += NT) {
-            const u64 conv = sf_reduce(cur[row_slot_t<LC>(e)], M.q, M.one_p);
-            const u64 res = sf_mul_shoup(sf_sub(acc[e], conv, M.q), pinv, pinv_p, M.q);
-            out[e] = sf_add(out[e], res, M.q);
-        }
+        for (int e = threadIdx.x; e < (SF_NB << LC); e += NT)
+            out[e] = sf_reduce(out[e] + acc[e] + conv_off - cur[row_slot_t<LC>(e)], M.q, M.one_p);
         __syncthreads();
     }
 }

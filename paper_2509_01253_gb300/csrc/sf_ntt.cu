@@ -193,10 +193,18 @@ __global__ void k_rotkey_finish(SfRing R, const u64 *alpha, const u64 *e, const 
         int js = auto_src(j, d, R.log_n);
         u64 sd = sf_mul_mont(pg.v[m], s_mont[((size_t)m << R.log_n) + js], M.q, M.qinv_neg);
         u64 b = sf_sub(sf_add(as, e[i], M.q), sd, M.q);
+        u64 a = alpha[i];
+        // The data limbs are stored times P^-1 mod q_m: the inner product
+        // then yields ACC_Q P^-1, the term ModDown needs, with no product of
+        // its own (sf_rotkeys_export multiplies the factor back out).
+        if (m < R.L) {
+            a = sf_mul_shoup(a, R.md_pinv[m], R.md_pinv_p[m], M.q);
+            b = sf_mul_shoup(b, R.md_pinv[m], R.md_pinv_p[m], M.q);
+        }
         // plain values, then their Shoup companions `comp` words later
-        key_a[i] = alpha[i];
+        key_a[i] = a;
         key_b[i] = b;
-        key_a[i + comp] = sf_shoup_companion_dev(alpha[i], M);
+        key_a[i + comp] = sf_shoup_companion_dev(a, M);
         key_b[i + comp] = sf_shoup_companion_dev(b, M);
     }
 }

@@ -129,7 +129,7 @@ __device__ __forceinline__ void tile_forward_t(u64 *s, const sf_tw *tw, u64 q)
     }
 }
 
-// Inverse stages (no N^-1 factor); values in [0, 2q).
+// Inverse stages (no N^-1 factor); inputs and values in [0, 4q).
 template <int LOG_S, bool ROWTW, int NT>
 __device__ __forceinline__ void tile_inverse_t(u64 *s, const sf_tw *tw, u64 q)
 {
