@@ -44,6 +44,7 @@ UNIT = "layers/s"
 WORKLOAD = ("conv16: ResNet-20 conv 3x3 16->16 on 16x32x32 (E = E' = 16384), N = 2^14, 3 x 50-bit + 1 "
             "special prime, scale 2^40, input unshuffle + output shuffle, 2 packed outputs of 8192, "
             "16384 key switches per layer")
+NTT_POLYS = 512        # forward-NTT record: 512 x L limbs (192 MiB in, 192 MiB out at N = 2^14, L = 3)
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -207,32 +208,67 @@ class RingShape:
         self.digits = [min(self.K, self.L - j * self.K) for j in range(self.dnum)]
 
 
-def kernel_work(kernel: str, g: RingShape, k_in: int = 1):
-    """Algorithmic work of one item of a kernel: (HBM bytes, modular
-    multiplications).  Items are merges (key switches) for the ks* kernels,
-    (output, input ciphertext) pairs for leaf_col and outputs for leaf_row.
-    Bytes are the operands that must cross HBM in the kernel's stage of the
-    pipeline (one read of each input limb, one write of each output limb,
-    8-byte words; the rotation key is read once per launch and not counted
-    per item); a modular multiplication is one butterfly, one
-    multiply-accumulate or one base-conversion product."""
-    N, L, K, nm, dnum, lr, lc, w = g.n, g.L, g.K, g.nm, g.dnum, g.lr, g.lc, 8
+def kernel_ops(kernel: str, g: RingShape, k_in: int = 1):
+    """Modular multiplications of one item of a kernel, split by kind:
+    (forward butterflies, inverse butterflies, other products: monomial and
+    key multiply-accumulates, base conversions, scalings).  Items are merges
+    (key switches) for the ks* kernels, (output, input ciphertext) pairs for
+    leaf_col and outputs for leaf_row.  A one-limb ModUp digit converts with
+    no product (its residue is the value), and the ModDown factor P^-1 rides
+    on the key and the conversion constants, so the finish has no product."""
+    N, L, K, nm, dnum, lr, lc = g.n, g.L, g.K, g.nm, g.dnum, g.lr, g.lc
     half = N // 2
-    fbc_up = sum(d * (nm - d) for d in g.digits) * N
+    fbc_up = sum(d * (nm - d) for d in g.digits if d > 1) * N
+    ext = dnum * nm - L   # digit extensions: every modulus outside the digit
     table = {
-        # read E and O (both parts), write TA and the merge's v + tau(u.b)
-        "ks_gather": (7 * L * N * w, 4 * L * N),
-        "ks1_inv_row": (2 * L * N * w, L * half * lc),
-        "ks2_modup_col": (dnum * nm * N * w, L * half * lr + L * N + fbc_up + (dnum * nm - L) * half * lr),
-        "ks3_inner_row": ((dnum * nm + 2 * nm) * N * w, (dnum * nm - L) * half * lc + 2 * dnum * nm * N),
-        "ks3_inv_row_p": (4 * K * N * w, 2 * K * half * lc),
-        "ks4_moddown_col": ((2 * K + 2 * L) * N * w, 2 * K * half * lr + 2 * K * N + 2 * K * L * N + 2 * L * half * lr),
-        # read conv, acc and out (2L limbs each), write out
-        "ks5_finish_row": (8 * L * N * w, 2 * L * half * lc + 2 * L * N),
-        "leaf_col": (L * N * w, L * half * lr),
-        "leaf_row": ((k_in * L + 2 * L) * N * w, k_in * L * half * lc + 2 * k_in * L * N),
+        "ks_gather": (0, 0, 4 * L * N),
+        "ks1_inv_row": (0, L * half * lc, 0),
+        "ks2_modup_col": (ext * half * lr, L * half * lr, L * N + fbc_up),
+        "ks3_inner_row": (ext * half * lc, 0, 2 * dnum * nm * N),
+        "ks3_inv_row_p": (0, 2 * K * half * lc, 0),
+        "ks4_moddown_col": (2 * L * half * lr, 2 * K * half * lr, 2 * K * N + 2 * K * L * N),
+        "ks5_finish_row": (2 * L * half * lc, 0, 0),
+        "leaf_col": (L * half * lr, 0, 0),
+        "leaf_row": (k_in * L * half * lc, 0, 2 * k_in * L * N),
     }
     return table.get(kernel)
+
+
+def kernel_work(kernel: str, g: RingShape, k_in: int = 1):
+    """Algorithmic work of one item of a kernel: (HBM bytes, modular
+    multiplications), items as in kernel_ops.  Bytes are the operands that
+    must cross HBM in the kernel's stage of the pipeline (one read of each
+    input limb, one write of each output limb, 8-byte words; the rotation key
+    is read once per launch and not counted per item); a modular
+    multiplication is one butterfly, one multiply-accumulate or one
+    base-conversion product."""
+    N, L, K, nm, dnum, w = g.n, g.L, g.K, g.nm, g.dnum, 8
+    nbytes = {
+        # read E and O (both parts), write TA and the merge's v + tau(u.b)
+        "ks_gather": 7 * L * N * w,
+        "ks1_inv_row": 2 * L * N * w,
+        "ks2_modup_col": dnum * nm * N * w,
+        "ks3_inner_row": (dnum * nm + 2 * nm) * N * w,
+        "ks3_inv_row_p": 4 * K * N * w,
+        "ks4_moddown_col": (2 * K + 2 * L) * N * w,
+        # read conv, acc and out (2L limbs each), write out
+        "ks5_finish_row": 8 * L * N * w,
+        "leaf_col": L * N * w,
+        "leaf_row": (k_in * L + 2 * L) * N * w,
+    }.get(kernel)
+    ops = kernel_ops(kernel, g, k_in)
+    if nbytes is None or ops is None:
+        return None
+    return nbytes, sum(ops)
+
+
+def probe_ceiling(ops, probe):
+    """Arithmetic ceiling of a kernel's mix of operations from the measured
+    per-kind rates (Gmodmul/s): total / sum(count_k / rate_k)."""
+    if not probe or not ops or sum(ops) == 0:
+        return None
+    t = ops[0] / probe["fwd_bfly"] + ops[1] / probe["inv_bfly"] + ops[2] / probe["mac"]
+    return sum(ops) / t
 
 
 def alu_peak(sm_count: int, sm_mhz: float):
@@ -270,7 +306,7 @@ def items_per_layer(kernel: str, info: dict, merges: int) -> int:
 
 
 def roofline_of(kstats: dict, k_steps: int, g: RingShape, info: dict, total_kernel_ms: float, clk: dict,
-                merges: int = None):
+                merges: int = None, probe: dict = None):
     """Roofline record of the kernel with the largest device-time share:
     algorithmic work per layer / its measured time per layer, against the
     measured HBM copy bandwidth and the derived modular-multiplication peak;
@@ -288,6 +324,7 @@ def roofline_of(kstats: dict, k_steps: int, g: RingShape, info: dict, total_kern
     t_hbm = b_item / (hbm_peak * 1e9)
     t_alu = m_item / alu_pk
     bound = "alu" if t_alu >= t_hbm else "hbm"
+    ceil = probe_ceiling(kernel_ops(top, g, info["k_in"]), probe)
     launches = cnt // k_steps
     traffic = TRAFFIC_PER_ITEM.get(top)
     rec = {"bound": bound, "kernel": top,
@@ -302,12 +339,57 @@ def roofline_of(kstats: dict, k_steps: int, g: RingShape, info: dict, total_kern
         "hbm_view": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
                      "peak_source": peak_kind},
         "alu_view": {"achieved": alu_ach, "peak": alu_pk / 1e9, "unit": "Gmodmul/s", "frac": alu_ach * 1e9 / alu_pk,
-                     "at_median_clock": (alu_ach * 1e9 / alu_peak(152, clk["sm_mhz"])) if clk.get("sm_mhz") else None},
+                     "at_median_clock": (alu_ach * 1e9 / alu_peak(152, clk["sm_mhz"])) if clk.get("sm_mhz") else None,
+                     "probe_peak": ceil, "frac_of_probe": (alu_ach / ceil) if ceil else None,
+                     "probe_source": "sf_modmul_probe: register-resident butterflies and multiply-accumulates "
+                                     "measured on this GPU, weighted by this kernel's mix of operations"},
         "algorithmic_bytes_per_launch": b_item * items / launches,
         "algorithmic_modmul_per_launch": m_item * items / launches,
         "avg_launch_us": per_layer_s / launches * 1e6, "launches_per_layer": launches,
         "share_of_device_time": ms / total_kernel_ms if total_kernel_ms else None})
     return rec
+
+
+def measure_probe(sf, ctx) -> dict:
+    """Measured arithmetic ceilings (Gmodmul/s) of the library's forward and
+    inverse butterflies and key multiply-accumulates on this GPU."""
+    return {"fwd_bfly": sf.sf_modmul_probe(ctx, 0), "inv_bfly": sf.sf_modmul_probe(ctx, 1),
+            "mac": sf.sf_modmul_probe(ctx, 2), "unit": "Gmodmul/s"}
+
+
+def ntt_record(sf, torch, wl_, p_info: dict, probe: dict, flush) -> dict:
+    """Batched forward NTT of every limb of NTT_POLYS polynomials of the
+    benchmark ring (sf_ntt_batch, inputs and outputs larger than L2):
+    algorithmic GB/s (each limb read once and written once) against the
+    measured HBM bandwidth, and butterflies/s against the measured forward
+    butterfly ceiling."""
+    L, n = wl_.L, wl_.n
+    count = NTT_POLYS
+    qmin = min(p_info["moduli"][:L])
+    dev = wl_.d_in.device
+    x = torch.randint(0, qmin, (count, L, n), dtype=torch.int64, device=dev)
+    y = torch.empty_like(x)
+    stream = wl_.stream
+    for _ in range(3):
+        sf.sf_ntt_batch(wl_.ctx, x, y, count, False, stream)
+    reps = 5
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for i in range(reps):
+        flush_l2(flush)
+        ev[i][0].record(stream)
+        sf.sf_ntt_batch(wl_.ctx, x, y, count, False, stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / reps
+    limbs = count * L
+    nbytes = 2 * limbs * n * 8
+    bfly = limbs * (n // 2) * (n.bit_length() - 1)
+    hbm_peak, kind = load_peaks()
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    gmm = bfly / (ms * 1e-3) / 1e9
+    return {"what": f"forward NTT of {count} x {L} limbs of N = {n} (sf_ntt_batch, two persistent passes)",
+            "ms_per_call": ms, "algorithmic_bytes": nbytes, "gbs": gbs, "hbm_peak": hbm_peak, "peak_source": kind,
+            "frac_hbm": gbs / hbm_peak, "gmodmul_s": gmm, "frac_of_probe": gmm / probe["fwd_bfly"]}
 
 
 # ------------------------------------------------------- CPU baseline ----
@@ -708,7 +790,9 @@ def main():
     sf.sf_ctx_set_option(wl_.ctx, "kernel_timing", 0)
     total_kernel_ms = sum(ms for _, ms in kstats.values())
     p_info = sf.sf_params_get_info(wl_.params)
-    roofline = roofline_of(kstats, k_steps, RingShape(p_info), wl_.info, total_kernel_ms, clk)
+    probe = measure_probe(sf, wl_.ctx)
+    roofline = roofline_of(kstats, k_steps, RingShape(p_info), wl_.info, total_kernel_ms, clk, probe=probe)
+    ntt = ntt_record(sf, torch, wl_, p_info, probe, flush)
     kernel_table = {k: {"launches_per_layer": c // k_steps, "ms_per_layer": m / k_steps} for k, (c, m) in kstats.items() if c}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
@@ -719,7 +803,7 @@ def main():
                        "autotuned": tuned, "ctx_options": args.ctx_opt, "max_abs_err": err},
             "clocks": clk, "gpu_launches": n_launch // 1, "step_ms": step_ms,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "roofline": roofline, "kernels": kernel_table}
+            "roofline": roofline, "ntt": ntt, "probe": probe, "kernels": kernel_table}
     if rank == 0 and not args.no_cpu_baseline:
         v, cores, desc = oracle_sample()
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}

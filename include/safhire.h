@@ -361,6 +361,30 @@ sf_status sf_shuffle_cts(sf_ctx *ctx, const uint32_t *h_perm, const uint64_t *d_
 sf_status sf_rotate_noalloc(sf_ctx *ctx, const sf_rotkeys *rk, int32_t d, const uint64_t *d_ct, uint64_t *d_out,
                             int32_t count, void *stream);
 
+/* Batched negacyclic NTT over every RNS limb (the transform that stands in
+ * for the paper's FFT, Sec. 6.1; used by every step of the round).  d_in and
+ * d_out hold `count` polynomials [count][L][N] of uint64 residues, limb i
+ * modulo q_i (device memory, caller-owned; d_out may equal d_in).
+ * inverse = 0: coefficients (each residue below 4 q_i) -> NTT domain,
+ * canonical, slot j holding the evaluation at psi^(2 brev(j) + 1) with psi a
+ * primitive 2N-th root modulo q_i; inverse = 1: NTT-domain values (below
+ * 4 q_i) -> canonical coefficients.  Two persistent launches on `stream`.
+ * Errors: SF_EINVAL for null buffers, count < 1 or inverse not 0/1. */
+sf_status sf_ntt_batch(sf_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int32_t count, int32_t inverse,
+                       void *stream);
+
+/* Measurement utility with no counterpart in the paper: the arithmetic
+ * ceiling of this library's modular operations on the context's GPU.  A
+ * register-resident kernel (no memory traffic besides one load and one store
+ * per value) applies 12 x 1024 operations to 8 residues per thread modulo q_0
+ * on one full wave of blocks, and *gmodmul_per_s receives the measured rate
+ * in 10^9 modular multiplications per second.  kind 0: forward (Cooley-Tukey)
+ * butterflies, 1: inverse (Gentleman-Sande) butterflies, 2: multiply-
+ * accumulates with a stored Shoup companion.  Synchronizes the device first
+ * and uses the context's workspace; not for use while other work of the
+ * context is in flight.  Errors: SF_EINVAL, SF_ECUDA. */
+sf_status sf_modmul_probe(sf_ctx *ctx, int32_t kind, double *gmodmul_per_s);
+
 /* Negacyclic product per limb (via the NTT): d_out[t] = d_a[t] * d_b[t] in
  * Z_{q_i}[X]/(X^N+1), arrays uint64[n_polys][L][N].  A test hook for the
  * transform kernels. */

@@ -191,6 +191,8 @@ enum SfKernelKind {
     SFK_LEAF_COL,
     SFK_LEAF_ROW,
     SFK_SHUFFLE,
+    SFK_BNTT_COL,
+    SFK_BNTT_ROW,
     SFK_COUNT
 };
 
@@ -233,5 +235,6 @@ sf_status sf_companions(sf_ctx *ctx, const u64 *x, u64 *dst, int n_polys, int pe
 
 // Raise the dynamic shared-memory limit of every kernel (once per device).
 sf_status sf_ntt_init_attributes();
+sf_status sf_bntt_init_attributes();
 sf_status sf_ks_init_attributes();
 sf_status sf_layer_init_attributes();

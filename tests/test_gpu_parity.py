@@ -66,6 +66,83 @@ def test_poly_mul_full_size_sampled(oracle):
         s.close()
 
 
+@pytest.mark.parametrize("log_n,L,bits,K,count", [(10, 3, 50, 1, 2), (11, 4, 50, 2, 3), (12, 2, 30, 1, 5),
+                                                   (13, 5, 50, 2, 2), (14, 3, 50, 1, 2), (15, 4, 50, 2, 3),
+                                                   (16, 5, 50, 2, 2)])
+def test_ntt_batch_transform_pair(oracle, log_n, L, bits, K, count):
+    """sf_ntt_batch: forward, a pointwise product of the NTT values taken on
+    the host with Python integers, then inverse equals the schoolbook
+    negacyclic product (limbs sampled above N = 2^12); inverse(forward(x)) is
+    x, also in place; forward(X) gives N distinct roots v with v^N = -1
+    (the evaluation points) and forward of a constant is that constant."""
+    s = Session(log_n, L, bits, K, rot=False)
+    try:
+        rng = np.random.default_rng(100 + log_n)
+        q = s.info["moduli"][:L]
+        a = _rand_residues(rng, q, count, s.n)
+        b = _rand_residues(rng, q, count, s.n)
+        A, B = dev_zeros(count, L, s.n), dev_zeros(count, L, s.n)
+        sf.sf_ntt_batch(s.ctx, to_dev(a), A, count, False)
+        sf.sf_ntt_batch(s.ctx, to_dev(b), B, count, False)
+        ha, hb = from_dev(A), from_dev(B)
+        for i in range(L):
+            assert (ha[:, i] < q[i]).all() and (hb[:, i] < q[i]).all()
+        # round trip, out of place and in place
+        back = dev_zeros(count, L, s.n)
+        sf.sf_ntt_batch(s.ctx, A, back, count, True)
+        assert (from_dev(back) == a).all()
+        sf.sf_ntt_batch(s.ctx, B, B, count, True)
+        assert (from_dev(B) == b).all()
+        # pointwise product on the host, inverse on the device, schoolbook on the oracle
+        prod = np.zeros_like(ha)
+        for t in range(count):
+            for i in range(L):
+                prod[t, i] = np.array([(int(x) * int(y)) % int(q[i]) for x, y in zip(ha[t, i], hb[t, i])],
+                                      dtype=np.uint64)
+        P = to_dev(prod)
+        sf.sf_ntt_batch(s.ctx, P, P, count, True)
+        got = from_dev(P)
+        limbs = [(t, i) for t in range(count) for i in range(L)] if log_n <= 12 else [(count - 1, L - 1)]
+        if log_n <= 14:
+            for t, i in limbs:
+                assert (got[t, i] == oracle.polymul(a[t, i], b[t, i], q[i])).all(), (t, i)
+        # evaluation points: forward of X and of a constant
+        mono = np.zeros((1, L, s.n), dtype=np.uint64)
+        mono[0, :, 1] = 1
+        M = to_dev(mono)
+        sf.sf_ntt_batch(s.ctx, M, M, 1, False)
+        v = from_dev(M)[0]
+        for i in range(L):
+            qi = int(q[i])
+            assert len(set(v[i].tolist())) == s.n
+            for j in rng.choice(s.n, 16, replace=False):
+                assert pow(int(v[i, j]), s.n, qi) == qi - 1
+        const = np.zeros((1, L, s.n), dtype=np.uint64)
+        const[0, :, 0] = 12345
+        Cn = to_dev(const)
+        sf.sf_ntt_batch(s.ctx, Cn, Cn, 1, False)
+        assert (from_dev(Cn) == 12345).all()
+        with pytest.raises(sf.SafhireError):
+            sf.sf_ntt_batch(s.ctx, A, A, 0, False)
+    finally:
+        s.close()
+
+
+def test_modmul_probe_reports_a_rate():
+    """The arithmetic-ceiling probe returns a positive rate for each kind and
+    rejects unknown kinds."""
+    ps = wl.PARAMS["conv16"]
+    s = Session.from_set(ps, rot=False)
+    try:
+        for kind in range(3):
+            r = sf.sf_modmul_probe(s.ctx, kind)
+            assert np.isfinite(r) and r > 1.0, (kind, r)
+        with pytest.raises(sf.SafhireError):
+            sf.sf_modmul_probe(s.ctx, 3)
+    finally:
+        s.close()
+
+
 # ------------------------------------------------------- keys / encryption --
 
 @pytest.mark.parametrize("pset", ["fc64", "conv16"])
