@@ -282,7 +282,8 @@ sf_status sf_eval_layers(sf_ctx *ctx, int32_t n_layers, const sf_layer *const *l
 
 /* Autotuner: times sf_eval_layers on the given rounds (which it evaluates,
  * results valid), `repeats` timed runs per candidate after a warm-up:
- * first each key-switch launch batch (32 ... 512 merges), then, with the
+ * first each key-switch launch batch (32 ... 4096 merges; those above 512
+ * only while their key-switch workspace stays within 16 GiB), then, with the
  * best batch, the leaf column pass of sparse tiles in closed form or as a
  * transform ("leaf_sparse" -1 or 0).  Keeps the fastest choices in the
  * context and reports the batch with the best time in milliseconds.

@@ -348,6 +348,8 @@ extern "C" sf_status sf_eval_layers(sf_ctx *ctx, int32_t n_layers, const sf_laye
     return SF_OK;
 }
 
+#define SF_AUTOTUNE_KS_SCRATCH ((size_t)16 << 30)
+
 extern "C" sf_status sf_autotune_layers(sf_ctx *ctx, int32_t n_layers, const sf_layer *const *layers,
                                         const sf_rotkeys *const *rks, const uint64_t *const *d_ins, const int32_t *k_ins,
                                         const uint32_t *const *h_sigma_prevs, const uint32_t *const *h_sigma_outs,
@@ -382,11 +384,14 @@ extern "C" sf_status sf_autotune_layers(sf_ctx *ctx, int32_t n_layers, const sf_
         *out_ms = tmin;
         return SF_OK;
     };
-    // 1) merges per key-switch launch
-    static const int cand[] = {32, 64, 128, 256, 512};
+    // 1) merges per key-switch launch; larger batches amortise each kernel's
+    // twiddle staging and tail over more merges, at ks_scratch x batch bytes of
+    // workspace, which is capped at SF_AUTOTUNE_KS_SCRATCH
+    static const int cand[] = {32, 64, 128, 256, 512, 1024, 2048, 4096};
     int best = ctx->ks_batch;
     double best_t = 1e30;
     for (int c : cand) {
+        if (c > 512 && sf_ks_scratch_words(ctx->ring) * sizeof(u64) * c > SF_AUTOTUNE_KS_SCRATCH) continue;
         ctx->ks_batch = c;
         double t = 0;
         if ((status = measure(&t)) != SF_OK) break;

@@ -462,11 +462,12 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
 
 // ModDown finish.  Groups: (row tile, limb i); items: (merge b, part p).
 // out += ACC - conv, both already multiplied by P^-1.  smem: forward row twiddles and two conversion
-// tiles (double-buffered); ACC and out are read elementwise from global.
+// tiles (double-buffered); ACC and out are read elementwise from global into
+// registers before the row pass.
 template <int LR, int LC>
 __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 512 ? 1 : 3) k_ks5(SfRing R, SfKsBatch B, int bpg)
 {
-    constexpr int NT = SfThreads<LC>::value;
+    constexpr int NT = SfThreads<LC>::value, EPT = (SF_NB << LC) / NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr SfGeoT<LR, LC> g{};
     const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
@@ -503,20 +504,22 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 
         const size_t off = ((size_t)(p * R.L + i) << (LR + LC)) + tile_off;
         const u64 *acc = ks_layout(R, B, b).accq + off;
         u64 *out = merge_out(B, b) + off;   // holds v (+ tau_d(u.b)) from k_ks_gather
-        // pull this item's accumulator and output rows toward L2 while the row pass runs
-        if ((threadIdx.x & 15) == 0) {
+        // this thread's accumulator and output words, loaded into registers
+        // before the row pass so that the loads are in flight while it runs
+        u64 va[EPT], vo[EPT];
 #pragma unroll
-            for (int e = threadIdx.x; e < (SF_NB << LC); e += NT) {
-                sf_prefetch_l2(acc + e);
-                sf_prefetch_l2(out + e);
-            }
+        for (int x = 0; x < EPT; ++x) {
+            va[x] = acc[threadIdx.x + x * NT];
+            vo[x] = out[threadIdx.x + x * NT];
         }
         __syncthreads();
         tile_forward_t<LC, true, NT>(cur, tw, M.q);
         // acc and conv both carry P^-1 already: out += acc - conv, one reduction
-        #pragma unroll
-        for (int e = threadIdx.x; e < (SF_NB << LC); e += NT)
-            out[e] = sf_reduce(out[e] + acc[e] + conv_off - cur[row_slot_t<LC>(e)], M.q, M.one_p);
+#pragma unroll
+        for (int x = 0; x < EPT; ++x) {
+            const int e = threadIdx.x + x * NT;
+            out[e] = sf_reduce(vo[x] + va[x] + conv_off - cur[row_slot_t<LC>(e)], M.q, M.one_p);
+        }
         __syncthreads();
     }
 }
