@@ -749,6 +749,9 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
+    # the decryption check again, on the output of the last timed step (the
+    # autotuned configuration), outside the timed region
+    err_final = wl_.check()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1e3
     stats = launches(sf, wl_.ctx)
@@ -800,7 +803,8 @@ def main():
             "config": {"workload": WORKLOAD if not args.small else "conv16-small (profiling case): " + WORKLOAD.replace(
                 "16x32x32 (E = E' = 16384)", "8x16x16 (E = E' = 2048)"), "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                       "autotuned": tuned, "ctx_options": args.ctx_opt, "max_abs_err": err},
+                       "autotuned": tuned, "ctx_options": args.ctx_opt, "max_abs_err": err,
+                       "max_abs_err_final": err_final},
             "clocks": clk, "gpu_launches": n_launch // 1, "step_ms": step_ms,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roofline, "ntt": ntt, "probe": probe, "kernels": kernel_table}

@@ -330,7 +330,7 @@ def test_ks_batch_size_does_not_change_results(oracle):
     s = Session(log_n, L, bits, K, sk_seed=61, rk_seed=62)
     try:
         outs = []
-        for b in (1, 3, 64):
+        for b in (1, 3, 64, 4096):
             sf.sf_ctx_set_option(s.ctx, "ks_batch", b)
             lay, info, msg, _, got = _run_layer(s, case, delta, delta * wsc, wsc)
             outs.append(got)
@@ -532,7 +532,7 @@ def test_eval_layers_batch_matches_single_rounds():
         best, ms = sf.sf_autotune_layers(s.ctx, lays, [s.rk] * len(lays), ins, [i["k_in"] for i in infos],
                                          [c.sigma_prev for c in cases], [c.sigma_out for c in cases], outs,
                                          [i["n_groups"] for i in infos], repeats=1)
-        assert best in (32, 64, 128, 256, 512) and ms > 0
+        assert best in (32, 64, 128, 256, 512, 1024, 2048, 4096) and ms > 0
         for o, want in zip(outs, single):
             assert (from_dev(o) == want).all()
         for lay in lays:
