@@ -304,7 +304,7 @@ static const char *k_names[SFK_COUNT] = {
     "ntt_fwd_col", "ntt_fwd_row", "ntt_inv_row", "ntt_inv_col", "elementwise",
     "ks_gather", "ks1_inv_row", "ks2_modup_col", "ks3_inner_row", "ks3_inv_row_p", "ks4_moddown_col",
     "ks5_finish_row",
-    "leaf_col", "leaf_row", "shuffle", "bntt_col", "bntt_row"};
+    "leaf_col", "leaf_row", "shuffle", "bntt_col", "bntt_row", "leaf_prep"};
 
 const char *sf_kernel_name(int kind) { return (kind >= 0 && kind < SFK_COUNT) ? k_names[kind] : "?"; }
 

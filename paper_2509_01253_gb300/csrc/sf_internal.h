@@ -193,6 +193,7 @@ enum SfKernelKind {
     SFK_SHUFFLE,
     SFK_BNTT_COL,
     SFK_BNTT_ROW,
+    SFK_LEAF_PREP,
     SFK_COUNT
 };
 

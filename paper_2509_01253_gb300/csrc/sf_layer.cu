@@ -279,8 +279,10 @@ sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStre
         p.w1 = P.w1;    // w1 holds `cnt` slots; reuse from its start for each sub-launch
         p.leaves = P.leaves + P.leaf_stride * off;
         if (P.n_buckets > SF_MAX_BUCKETS) return sf_set_error(SF_EINVAL, "too many input ciphertexts for one round");
-        sf_launch_begin(ctx, SFK_LEAF_COL, st, &ev);
+        sf_launch_begin(ctx, SFK_LEAF_PREP, st, &ev);
         k_leaf_prep<<<c, 256, 0, st>>>(R, p);
+        sf_launch_end(ctx, SFK_LEAF_PREP, st, ev);
+        sf_launch_begin(ctx, SFK_LEAF_COL, st, &ev);
         SF_GEO_DISPATCH(R.log_n, k_leaf_col<LR, LC><<<dim3(R.c / SF_NB, P.k_in * R.L, c), SfThreads<LR>::value, smem_c, st>>>(R, p););
         sf_launch_end(ctx, SFK_LEAF_COL, st, ev);
         sf_launch_begin(ctx, SFK_LEAF_ROW, st, &ev);
