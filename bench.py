@@ -170,7 +170,9 @@ class Workload:
         best, ms = self.sf.sf_autotune_layers(self.ctx, [self.layer], [self.rk], [self.d_in], [self.k_in],
                                               [self.case.sigma_prev], [self.case.sigma_out], [self.d_out], [self.G],
                                               2, self.stream)
-        return {"ks_batch": best, "ms": ms}
+        return {"ks_batch": best, "ms": ms,
+                "ks3_threads": self.sf.sf_ctx_get_option(self.ctx, "ks3_threads"),
+                "leaf_sparse": self.sf.sf_ctx_get_option(self.ctx, "leaf_sparse")}
 
     def check(self) -> float:
         """Max |decoded - float64| over all outputs (not timed)."""

@@ -115,6 +115,10 @@ void sf_ctx_destroy(sf_ctx *ctx);
  *                   instead of running the transform (-1: 8 log2 R, where the
  *                   closed form has fewer multiplications; 0: always the
  *                   transform, the default; at most 128)
+ *   "ks3_threads"   threads per block of the key-switch inner product when
+ *                   the NTT's rows have 128 points (N = 2^13, 2^14): 256
+ *                   (8 residues per thread, the default) or 512 (4 per
+ *                   thread, radix-4 row sweeps)
  *   "leaf_chunk"    cap on the leaves per packing unit (power of two): a group
  *                   of n leaves is packed as n/CH residue classes of CH leaves
  *                   reduced to roots, then the roots finish the tree
@@ -127,6 +131,12 @@ void sf_ctx_destroy(sf_ctx *ctx);
  *                   and accumulate per-kernel times (read with sf_kernel_stats)
  * Errors: SF_EINVAL for an unknown name or value. */
 sf_status sf_ctx_set_option(sf_ctx *ctx, const char *name, int64_t value);
+
+/* Reads the current value of one of the options above that holds a value
+ * ("ks_batch", "ks3_threads", "leaf_sparse", "leaf_chunk", "mem_budget",
+ * "use_graph", "kernel_timing"), e.g. after sf_autotune_layers.  Errors:
+ * SF_EINVAL for a null argument or an unknown name. */
+sf_status sf_ctx_get_option(const sf_ctx *ctx, const char *name, int64_t *value);
 
 /* Waits for `stream`, then reports (and clears) the context's device status
  * word: SF_OK, or the first error a kernel latched (SF_ETIMEOUT, SF_EINVAL). */
@@ -285,8 +295,10 @@ sf_status sf_eval_layers(sf_ctx *ctx, int32_t n_layers, const sf_layer *const *l
  * first each key-switch launch batch (32 ... 4096 merges; those above 512
  * only while their key-switch workspace stays within 16 GiB), then, with the
  * best batch, the leaf column pass of sparse tiles in closed form or as a
- * transform ("leaf_sparse" -1 or 0).  Keeps the fastest choices in the
- * context and reports the batch with the best time in milliseconds.
+ * transform ("leaf_sparse" -1 or 0), then, for rings with 128-point rows,
+ * the block shape of the key-switch inner product ("ks3_threads" 256 or
+ * 512).  Keeps the fastest choices in the context and reports the batch
+ * with the best time in milliseconds.
  * Synchronises `stream`. */
 sf_status sf_autotune_layers(sf_ctx *ctx, int32_t n_layers, const sf_layer *const *layers, const sf_rotkeys *const *rks,
                              const uint64_t *const *d_ins, const int32_t *k_ins, const uint32_t *const *h_sigma_prevs,

@@ -60,6 +60,7 @@ _SIGS = {
     "sf_ctx_create": (_i32, [_vp, _i32, _pp]),
     "sf_ctx_destroy": (None, [_vp]),
     "sf_ctx_set_option": (_i32, [_vp, ctypes.c_char_p, _i64]),
+    "sf_ctx_get_option": (_i32, [_vp, ctypes.c_char_p, ctypes.POINTER(_i64)]),
     "sf_sync": (_i32, [_vp, _vp]),
     "sf_kernel_stats": (_i32, [_vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(_i64),
                                ctypes.POINTER(_dbl), _i32, ctypes.POINTER(_i32)]),
@@ -187,6 +188,12 @@ def sf_ctx_destroy(ctx):
 
 def sf_ctx_set_option(ctx, name: str, value: int):
     _check(lib().sf_ctx_set_option(ctx, name.encode(), int(value)))
+
+
+def sf_ctx_get_option(ctx, name: str) -> int:
+    out = _i64()
+    _check(lib().sf_ctx_get_option(ctx, name.encode(), ctypes.byref(out)))
+    return out.value
 
 
 def sf_sync(ctx, stream=None):

@@ -417,6 +417,23 @@ extern "C" sf_status sf_autotune_layers(sf_ctx *ctx, int32_t n_layers, const sf_
         }
         ctx->leaf_sparse = best_sparse;
     }
+    // 3) block shape of the key-switch inner product for 128-point rows:
+    //    256 threads x 8 elements or 512 threads x 4 elements
+    if (status == SF_OK && ctx->ring.log_c == 7) {
+        const int saved = ctx->ks3_threads;
+        int best_nt = saved;
+        for (int nt : {256, 512}) {
+            if (nt == saved) continue;
+            ctx->ks3_threads = nt;
+            double t = 0;
+            if ((status = measure(&t)) != SF_OK) break;
+            if (t < best_t) {
+                best_t = t;
+                best_nt = nt;
+            }
+        }
+        ctx->ks3_threads = best_nt;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     sf_graph_cache_clear(ctx);

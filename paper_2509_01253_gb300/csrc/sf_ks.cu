@@ -308,10 +308,13 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
 // each taking dnum steps (one per digit) whose tiles are double-buffered.
 // Output: ACC (data moduli, NTT domain) or, for the special moduli, their NTT
 // values in the x1 region (the inverse row pass runs in k_rows<true>).
-template <int LR, int LC>
-__global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 512 ? 1 : 3) k_ks3(SfRing R, SfKsBatch B, int bpg)
+// NT: 256 (8 elements per thread, three blocks per SM) or, for 128-point
+// rows, 512 (4 elements per thread, half the accumulator registers, two
+// 16-warp blocks per SM); 256-point rows always run 512.
+template <int LR, int LC, int NT>
+__global__ void __launch_bounds__(NT, NT >= 512 ? (LC >= 8 ? 1 : 2) : 3) k_ks3(SfRing R, SfKsBatch B, int bpg)
 {
-    constexpr int NT = SfThreads<LC>::value, EPT = (SF_NB << LC) / NT;
+    constexpr int EPT = (SF_NB << LC) / NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr SfGeoT<LR, LC> g{};
     const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
@@ -599,8 +602,18 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
             sf_launch_begin(ctx, SFK_KS3_INNER_ROW, st, &ev);
             {
                 const int ng = rtiles * R.nm;
-                const int bpg = blocks_per_group(ctx, occupancy(k_ks3<LR, LC>, NTR, sm3), ng, b.count);
-                k_ks3<LR, LC><<<ng * bpg, NTR, sm3, st>>>(R, b, bpg);
+                bool wide = false;
+                if constexpr (LC == 7) {
+                    if (ctx->ks3_threads == 512) {
+                        const int bpg = blocks_per_group(ctx, occupancy(k_ks3<LR, LC, 512>, 512, sm3), ng, b.count);
+                        k_ks3<LR, LC, 512><<<ng * bpg, 512, sm3, st>>>(R, b, bpg);
+                        wide = true;
+                    }
+                }
+                if (!wide) {
+                    const int bpg = blocks_per_group(ctx, occupancy(k_ks3<LR, LC, NTR>, NTR, sm3), ng, b.count);
+                    k_ks3<LR, LC, NTR><<<ng * bpg, NTR, sm3, st>>>(R, b, bpg);
+                }
             }
             sf_launch_end(ctx, SFK_KS3_INNER_ROW, st, ev);
             sf_launch_begin(ctx, SFK_KS3_INV_ROW_P, st, &ev);
@@ -656,10 +669,11 @@ sf_status sf_ks_init_attributes()
     const int mx = 227 * 1024;
 #define SF_KS_ATTR(K) SF_CUDA_TRY(cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
 #define SF_KS_ATTRS(LR, LC)                                                                                  \
-    SF_KS_ATTR((k_rows<true, LR, LC>)) SF_KS_ATTR((k_ks2<LR, LC>)) SF_KS_ATTR((k_ks3<LR, LC>))               \
+    SF_KS_ATTR((k_rows<true, LR, LC>)) SF_KS_ATTR((k_ks2<LR, LC>)) SF_KS_ATTR((k_ks3<LR, LC, SfThreads<LC>::value>)) \
     SF_KS_ATTR((k_ks4<LR, LC>)) SF_KS_ATTR((k_ks5<LR, LC>))
     SF_KS_ATTRS(5, 5) SF_KS_ATTRS(5, 6) SF_KS_ATTRS(6, 6) SF_KS_ATTRS(6, 7) SF_KS_ATTRS(7, 7) SF_KS_ATTRS(7, 8)
     SF_KS_ATTRS(8, 8)
+    SF_KS_ATTR((k_ks3<6, 7, 512>)) SF_KS_ATTR((k_ks3<7, 7, 512>))
 #undef SF_KS_ATTRS
 #undef SF_KS_ATTR
     return SF_OK;

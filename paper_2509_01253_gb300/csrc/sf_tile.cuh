@@ -109,10 +109,17 @@ __device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
 }
 
 // Forward stages of all 16 sub-transforms of size 2^LOG_S; values in [0, 4q).
+// 128-point sub-transforms in 512-thread blocks (4 elements per thread) run
+// radix-4 sweeps so that every thread holds one unit.
 template <int LOG_S, bool ROWTW, int NT>
 __device__ __forceinline__ void tile_forward_t(u64 *s, const sf_tw *tw, u64 q)
 {
-    if constexpr (LOG_S == 5) {
+    if constexpr (LOG_S == 7 && NT == 512) {
+        tile_sweep<7, 6, 2, false, ROWTW, NT>(s, tw, q);
+        tile_sweep<7, 4, 2, false, ROWTW, NT>(s, tw, q);
+        tile_sweep<7, 2, 2, false, ROWTW, NT>(s, tw, q);
+        tile_sweep<7, 0, 1, false, ROWTW, NT>(s, tw, q);
+    } else if constexpr (LOG_S == 5) {
         tile_sweep<5, 4, 3, false, ROWTW, NT>(s, tw, q);
         tile_sweep<5, 1, 2, false, ROWTW, NT>(s, tw, q);
     } else if constexpr (LOG_S == 6) {
@@ -133,7 +140,12 @@ __device__ __forceinline__ void tile_forward_t(u64 *s, const sf_tw *tw, u64 q)
 template <int LOG_S, bool ROWTW, int NT>
 __device__ __forceinline__ void tile_inverse_t(u64 *s, const sf_tw *tw, u64 q)
 {
-    if constexpr (LOG_S == 5) {
+    if constexpr (LOG_S == 7 && NT == 512) {
+        tile_sweep<7, 0, 2, true, ROWTW, NT>(s, tw, q);
+        tile_sweep<7, 2, 2, true, ROWTW, NT>(s, tw, q);
+        tile_sweep<7, 4, 2, true, ROWTW, NT>(s, tw, q);
+        tile_sweep<7, 6, 1, true, ROWTW, NT>(s, tw, q);
+    } else if constexpr (LOG_S == 5) {
         tile_sweep<5, 0, 2, true, ROWTW, NT>(s, tw, q);
         tile_sweep<5, 2, 3, true, ROWTW, NT>(s, tw, q);
     } else if constexpr (LOG_S == 6) {

@@ -201,13 +201,17 @@ def test_rotate_bit_exact_all_keys(oracle, log_n, L, bits, K):
         s.close()
 
 
-def test_rotate_full_size(oracle):
+@pytest.mark.parametrize("ks3_threads", [256, 512])
+def test_rotate_full_size(oracle, ks3_threads):
     """Benchmark ring N = 2^14, 3 x 50-bit + 1 special, the first-level and
-    the last trace automorphisms."""
+    the last trace automorphisms, with either block shape of the key-switch
+    inner product."""
     ps = wl.PARAMS["conv16"]
     ds = [3, 16385]
     s = Session.from_set(ps, sk_seed=31, rk_seed=32, rot_d=ds)
     try:
+        sf.sf_ctx_set_option(s.ctx, "ks3_threads", ks3_threads)
+        assert sf.sf_ctx_get_option(s.ctx, "ks3_threads") == ks3_threads
         prm = oracle_params(oracle, ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits)
         s_o = oracle.keygen(prm, 31)
         keys = oracle.rotation_keys(prm, s_o, 32, ds)
@@ -369,6 +373,28 @@ def test_conv16_full_size(oracle):
         for t, o in enumerate(sample):
             assert (leaves[t] == oracle.linear_output(prm, olay, cts, int(o), case.sigma_prev)).all(), o
         sf.sf_layer_destroy(lay)
+    finally:
+        s.close()
+
+
+def test_conv16_launch_shapes_identical():
+    """The benchmark round gives the same residues under every launch shape
+    the autotuner can pick: key-switch launch batches of 512 and 4096 merges
+    and both block shapes of the inner product (256 x 8 and 512 x 4)."""
+    ps = wl.PARAMS["conv16"]
+    case = wl.conv16_case()
+    s = Session.from_set(ps, sk_seed=203, rk_seed=205)
+    try:
+        outs = []
+        for batch, nt in ((512, 256), (4096, 256), (512, 512), (4096, 512)):
+            sf.sf_ctx_set_option(s.ctx, "ks_batch", batch)
+            sf.sf_ctx_set_option(s.ctx, "ks3_threads", nt)
+            lay, info, msg, d_in, got = _run_layer(s, case, ps.delta, ps.delta ** 2, ps.delta)
+            outs.append(got)
+            sf.sf_layer_destroy(lay)
+        assert all((o == outs[0]).all() for o in outs[1:])
+        with pytest.raises(sf.SafhireError):
+            sf.sf_ctx_set_option(s.ctx, "ks3_threads", 384)
     finally:
         s.close()
 
