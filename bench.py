@@ -681,8 +681,10 @@ def run_request_e2e(args, local: int) -> int:
     clocks = ClockSampler(local)
     clocks.start()
     torch.cuda.synchronize()
+    from paper_2509_01253_gb300 import protocol
+    log = protocol.CommLog()
     t0 = time.perf_counter()
-    ms = nw.run_request(net, sk, rk, client, keep_trace=True)
+    ms = nw.run_request(net, sk, rk, client, keep_trace=True, log=log)
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     errs = []
@@ -696,6 +698,7 @@ def run_request_e2e(args, local: int) -> int:
            "device_total_s": sum(ms) / 1e3, "request_wall_s": wall,
            "layers_per_s_device": R / (sum(ms) / 1e3), "value": R / wall,
            "max_abs_err_per_round": errs, "max_abs_err": max(errs), "clocks": clk,
+           "protocol": log.summary(),
            "note": "each round's first call includes its graph capture"}
     print(json.dumps(rec), flush=True)
     return 0

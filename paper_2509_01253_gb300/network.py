@@ -16,9 +16,12 @@ the seeds given here.
 """
 from __future__ import annotations
 
+import time
+
 import numpy as np
 
 import paper_2509_01253_gb300 as sf
+from paper_2509_01253_gb300 import protocol
 from paper_2509_01253_gb300 import workloads as wl
 
 
@@ -149,30 +152,48 @@ def decode_outputs(net: EncodedNetwork, r: int, residues: np.ndarray) -> np.ndar
 
 
 def run_request(net: EncodedNetwork, sk, rk, client: ClientState, stream=None, device: str = "cuda:0",
-                keep_trace: bool = False):
+                keep_trace: bool = False, log: protocol.CommLog = None, session: protocol.ServerSession = None):
     """All rounds of one request, one sf_eval_linear_layer call per round.
-    Returns per-round device milliseconds (server side only)."""
+    Each upload goes through the server's session checks (its session id is
+    the client's session seed); `log`, when given, receives every round's
+    bytes, server (device) time and client time (encode, encrypt, decrypt,
+    decode, activation).  Returns per-round device milliseconds."""
     import torch
     L, n = net.ps.n_data, net.n
+    st = stream if stream is not None else torch.cuda.current_stream()
+    session = session or protocol.ServerSession(client.session_seed, len(net.rounds))
     ms = []
     for r in range(len(net.rounds)):
         info = net.infos[r]
+        t0 = time.perf_counter()
         msg, sigma_prev, stream_in = client.encode(r)
         d_in = torch.empty((info["k_in"], 2, L, n), dtype=torch.int64, device=device)
         sf.sf_encrypt(net.ctx, sk, msg, client.encrypt_seed(r), d_in, info["k_in"], stream)
-        d_out = torch.empty((info["n_groups"], 2, L, n), dtype=torch.int64, device=device)
+        st.synchronize()
+        t_client = time.perf_counter() - t0
         so = client.sigma_out(r)
-        st = stream if stream is not None else torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        sf.sf_eval_linear_layer(net.ctx, net.layers[r], rk, d_in, info["k_in"], sigma_prev, so, d_out,
-                                info["n_groups"], st)
-        e1.record(st)
+
+        def evaluate(rr, payload):
+            d_out = torch.empty((info["n_groups"], 2, L, n), dtype=torch.int64, device=device)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            sf.sf_eval_linear_layer(net.ctx, net.layers[rr], rk, payload, info["k_in"], sigma_prev, so, d_out,
+                                    info["n_groups"], st)
+            e1.record(st)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            return d_out
+
+        d_out = session.submit(client.session_seed, r, d_in, evaluate)
+        t0 = time.perf_counter()
         res = np.zeros((info["n_groups"], L, n), dtype=np.uint64)
         sf.sf_decrypt(net.ctx, sk, d_out, info["n_groups"], res, st)
-        ms.append(e0.elapsed_time(e1))
         vals = decode_outputs(net, r, res)
         client.absorb(r, vals, so, stream_in if keep_trace else None, sigma_prev)
+        t_client += time.perf_counter() - t0
+        if log is not None:
+            up, down = protocol.round_bytes(info, L, n)
+            log.add(r, up, down, ms[-1] / 1e3, t_client)
     return ms
 
 

@@ -31,6 +31,7 @@ import numpy as np
 
 import paper_2509_01253_gb300 as sf
 from paper_2509_01253_gb300 import network as nw
+from paper_2509_01253_gb300 import protocol
 from paper_2509_01253_gb300 import workloads as wl
 
 
@@ -49,6 +50,10 @@ class Request:
     client: nw.ClientState = None
     logits: np.ndarray = None
     rounds_run: int = 0
+    # the server's view of the session: round checks and bytes moved
+    session: protocol.ServerSession = None
+    up_bytes: int = 0
+    down_bytes: int = 0
     # the pending round on the device
     d_in: object = None
     d_out: object = None
@@ -88,6 +93,7 @@ class Pool:
         return self.nets[net].max_cts() * self.ct_bytes
 
     def new_client(self, req: Request) -> nw.ClientState:
+        req.session = protocol.ServerSession(req.session_seed, len(self.nets[req.net].rounds))
         return nw.ClientState(self.nets[req.net], req.x, req.session_seed, req.request_seed)
 
     def bind_thread(self):
@@ -101,6 +107,10 @@ class Pool:
         r = req.client.round
         info = net.infos[r]
         msg, sp, _ = req.client.encode(r)
+        # the upload of round r: checked against the session's next round
+        if not req.session.begin(req.session_seed, r):
+            raise protocol.ProtocolError("order", f"request {req.rid}: round {r} was evaluated already")
+        req.up_bytes += protocol.round_bytes(info, self.L, self.n)[0]
         req.d_in = torch.empty((info["k_in"], 2, self.L, self.n), dtype=torch.int64, device=self.device)
         sf.sf_encrypt(self.ctx, self.sks[req.key], msg, req.client.encrypt_seed(r), req.d_in, info["k_in"],
                       self.stream)
@@ -121,6 +131,9 @@ class Pool:
                                f"{np.abs(vals).max():.3g} is not a plausible activation; engine call held "
                                f"{self.last_call}")
         req.client.absorb(r, vals, req.sigma_out)
+        # the simulated client never loses a download here: nothing is kept to resend
+        req.session.complete(r, None)
+        req.down_bytes += protocol.round_bytes(info, self.L, self.n)[1]
         req.rounds_run += 1
         req.d_in = req.d_out = None
 
@@ -331,6 +344,8 @@ def run_arrivals(server: Server, arrivals: list, drain: float, verify: bool = Fa
             "p99_latency_s": float(np.percentile(lat, 99)) if lat.size else None,
             "layers_per_s": rounds / elapsed, "rounds_run": rounds, "window_s": window, "elapsed_s": elapsed,
             "engine_calls": len(server.batches),
+            "bytes_up": sum(r.up_bytes for r in server.admitted),
+            "bytes_down": sum(r.down_bytes for r in server.admitted),
             "mean_rounds_per_call": float(np.mean([b[1] for b in server.batches])) if server.batches else None,
             "per_network": per_net}
 

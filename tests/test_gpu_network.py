@@ -10,6 +10,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 from paper_2509_01253_gb300 import network as nw  # noqa: E402
+from paper_2509_01253_gb300 import protocol  # noqa: E402
 from paper_2509_01253_gb300 import serve  # noqa: E402
 from paper_2509_01253_gb300 import workloads as wl  # noqa: E402
 
@@ -26,11 +27,35 @@ def pools():
         x.destroy()
 
 
-def _alone(pool, net, key, seed):
+def _alone(pool, net, key, seed, log=None, session=None):
     req = serve.make_request(0, net, key, seed)
     client = nw.ClientState(pool.nets[net], req.x, req.session_seed, req.request_seed)
-    nw.run_request(pool.nets[net], pool.sks[key], pool.rks[key], client, keep_trace=True)
+    nw.run_request(pool.nets[net], pool.sks[key], pool.rks[key], client, keep_trace=True, log=log, session=session)
     return client
+
+
+def test_request_protocol_accounting(pools):
+    """One request through the session checks: every round evaluated once,
+    the communication log equal to the rounds' ciphertext counts, and the
+    host-side round shapes equal to the library's layer info."""
+    pool, net = pools["p14"], "tiny_b"
+    encnet = pool.nets[net]
+    req = serve.make_request(0, net, 0, 51)
+    session = protocol.ServerSession(req.session_seed, len(encnet.rounds))
+    log = protocol.CommLog()
+    _alone(pool, net, 0, 51, log=log, session=session)
+    assert session.finished and session.evaluations == len(encnet.rounds) and session.resends == 0
+    ct = protocol.ciphertext_bytes(pool.L, pool.n)
+    assert log.up_bytes == sum(i["k_in"] for i in encnet.infos) * ct
+    assert log.down_bytes == sum(i["n_groups"] for i in encnet.infos) * ct
+    assert all(x.server_s > 0 and x.client_s > 0 for x in log.rounds)
+    for spec, info in zip(encnet.rounds, encnet.infos):
+        sh = protocol.round_shape(wl.round_input_size(spec), wl.round_output_size(spec), pool.n)
+        assert (sh["k_in"], sh["group_size"], sh["n_groups"]) == (info["k_in"], info["group_size"], info["n_groups"])
+    # a resend of the last round is answered from the kept result
+    last = len(encnet.rounds) - 1
+    assert session.submit(req.session_seed, last, None, lambda r, p: pytest.fail("evaluated again")) is \
+        session.last_result
 
 
 @pytest.mark.parametrize("pool_name,net", [("p12", "tiny_a"), ("p14", "tiny_b")])
@@ -66,6 +91,9 @@ def test_served_results_equal_alone(pools):
     srv.shutdown()
     assert len(srv.completed) == len(specs)
     assert max(b[1] for b in srv.batches) == 2        # calls held several requests
+    for req in srv.completed:                         # the server's session of every request ran to the end
+        assert req.session.finished and req.session.evaluations == len(pools[route[req.net]].nets[req.net].rounds)
+        assert req.up_bytes > 0 and req.down_bytes > 0
     for req in srv.completed:
         assert np.array_equal(req.logits, alone[req.request_seed]), req.request_seed
 
