@@ -183,3 +183,22 @@ def test_client_and_server_ranks_with_a_lost_reply():
         want.append(y)
         v = y % 1000
     assert res["results"] == want
+
+
+@pytest.mark.parametrize("kind,pset", [("resnet20", "conv16"), ("resnet18", "r18"), ("resnet34", "r34")])
+def test_round_shapes_agree_with_the_oracle(oracle, kind, pset):
+    """The protocol's round shapes (what it counts as bytes) against the
+    oracle's own packing rule, round by round: group size, packed ciphertexts
+    and the key switches those groups cost."""
+    ps = wl.PARAMS[pset]
+    N = 1 << ps.log_n
+    prm = oracle.Params(ps.log_n, N, ps.n_data, ps.n_special, [], [])
+    for spec in wl.resnet_rounds(kind):
+        e_in, e_out = wl.round_input_size(spec), wl.round_output_size(spec)
+        sh = P.round_shape(e_in, e_out, N)
+        n = oracle.group_size(prm, e_out)
+        assert sh["group_size"] == n, spec.name
+        assert sh["n_groups"] * n >= e_out > (sh["n_groups"] - 1) * n, spec.name
+        assert sh["k_in"] * N >= e_in > (sh["k_in"] - 1) * N, spec.name
+        log_n_over_n = ps.log_n - (n.bit_length() - 1)
+        assert oracle.ks_count(prm, e_out) == sh["n_groups"] * ((n - 1) + log_n_over_n), spec.name
