@@ -436,7 +436,6 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
         const KsLayout Lo = ks_layout(R, B, b);
         for (int i = 0; i < R.L; ++i) {
             const SfMod &M = R.m[i];
-            #pragma unroll
             // base conversion, lazy: each term in [0, 2q), the sum below 2q * K
             u64 ph[4], php[4];
 #pragma unroll
@@ -556,6 +555,22 @@ static int blocks_per_group(const sf_ctx *ctx, int occ, int n_groups, int n_item
     return std::max(1, std::min(bpg, n_items));
 }
 
+// The 512-thread inner product (128-point rows only, when the context asks
+// for it); false when the default block shape is to run.  A template, so
+// that the discarded branch instantiates nothing for the other ring splits.
+template <int LR, int LC>
+static bool ks3_launch_wide(sf_ctx *ctx, const SfKsBatch &b, size_t sm3, int ng, cudaStream_t st)
+{
+    if constexpr (LC == 7) {
+        if (ctx->ks3_threads != 512) return false;
+        const int bpg = blocks_per_group(ctx, occupancy(k_ks3<LR, LC, 512>, 512, sm3), ng, b.count);
+        k_ks3<LR, LC, 512><<<ng * bpg, 512, sm3, st>>>(ctx->ring, b, bpg);
+        return true;
+    } else {
+        return false;
+    }
+}
+
 sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
 {
     const SfRing &R = ctx->ring;
@@ -602,15 +617,7 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
             sf_launch_begin(ctx, SFK_KS3_INNER_ROW, st, &ev);
             {
                 const int ng = rtiles * R.nm;
-                bool wide = false;
-                if constexpr (LC == 7) {
-                    if (ctx->ks3_threads == 512) {
-                        const int bpg = blocks_per_group(ctx, occupancy(k_ks3<LR, LC, 512>, 512, sm3), ng, b.count);
-                        k_ks3<LR, LC, 512><<<ng * bpg, 512, sm3, st>>>(R, b, bpg);
-                        wide = true;
-                    }
-                }
-                if (!wide) {
+                if (!ks3_launch_wide<LR, LC>(ctx, b, sm3, ng, st)) {
                     const int bpg = blocks_per_group(ctx, occupancy(k_ks3<LR, LC, NTR>, NTR, sm3), ng, b.count);
                     k_ks3<LR, LC, NTR><<<ng * bpg, NTR, sm3, st>>>(R, b, bpg);
                 }
