@@ -1,6 +1,8 @@
 """The bench's work model (host logic, no GPU): per-kernel operation counts
 against closed forms of the key switch at the benchmark ring, and the
 probe-weighted arithmetic ceiling."""
+import pytest
+
 import bench
 
 
@@ -35,3 +37,29 @@ def test_work_totals_and_probe_ceiling():
     assert bench.probe_ceiling(bench.kernel_ops("ks1_inv_row", g), probe) == 800.0
     assert bench.probe_ceiling((0, 0, 0), probe) is None
     assert bench.kernel_work("no_such_kernel", g) is None
+
+
+def test_roofline_record_arithmetic():
+    """roofline_of on synthetic per-kernel statistics: the top kernel by device
+    time, achieved = algorithmic work x items / time per layer, the derived and
+    measured ceilings, and DRAM traffic scaled to one launch."""
+    g = _ring(1 << 14, 3, 1)
+    info = {"k_in": 1, "ks_count": 16384, "E_out": 16384}
+    k_steps = 10
+    kstats = {"ks3_inner_row": (15 * k_steps, 250.0), "ks2_modup_col": (15 * k_steps, 170.0),
+              "elementwise": (k_steps, 999.0)}          # no work model: never the top kernel
+    probe = {"fwd_bfly": 1000.0, "inv_bfly": 800.0, "mac": 1100.0}
+    rec = bench.roofline_of(kstats, k_steps, g, info, 420.0, {"sm_mhz": 2070.0}, probe=probe)
+    assert rec["kernel"] == "ks3_inner_row" and rec["bound"] == "alu"
+    per_layer_s = 250.0 / k_steps / 1e3
+    nbytes, mm = bench.kernel_work("ks3_inner_row", g)
+    assert rec["achieved"] == pytest.approx(mm * 16384 / per_layer_s / 1e9)
+    assert rec["peak"] == pytest.approx(bench.alu_peak(152, 2070.0) / 1e9)
+    assert rec["frac"] == pytest.approx(rec["achieved"] / rec["peak"])
+    assert rec["hbm_view"]["achieved"] == pytest.approx(nbytes * 16384 / per_layer_s / 1e9)
+    ceil = bench.probe_ceiling(bench.kernel_ops("ks3_inner_row", g), probe)
+    assert rec["alu_view"]["probe_peak"] == pytest.approx(ceil)
+    assert rec["alu_view"]["frac_of_probe"] == pytest.approx(rec["achieved"] / ceil)
+    assert rec["launches_per_layer"] == 15
+    assert rec["traffic"] == pytest.approx(bench.TRAFFIC_PER_ITEM["ks3_inner_row"] * 16384 / 15)
+    assert rec["share_of_device_time"] == pytest.approx(250.0 / 420.0)
