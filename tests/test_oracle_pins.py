@@ -468,7 +468,7 @@ def test_layer_on_trivial_ciphertexts_equals_integer_matvec(oracle, case):
 
 
 def test_encrypted_layer_integer_mode_is_exact(oracle):
-    """P:531-535 correctness check: decrypting and rounding gives exactly the
+    """Sec. 6.1 correctness check: decrypting and rounding gives exactly the
     quantised cleartext result A xq, in the shuffled order."""
     prm = oracle.make_params(8, 3, 50, 1, 50)
     s = oracle.keygen(prm, 21)
@@ -510,3 +510,245 @@ def test_encrypted_layer_float_mode_error(oracle):
     got = oracle.read_outputs(prm, lay, oracle.decrypt(prm, s, out), 2.0 ** 50)
     ref = (W[:, 0, 0, :] @ x)[so]
     assert np.abs(got - ref).max() <= 1e-3
+
+
+# ------------------------------------------------------ conv geometry ------
+# The layer's geometry (receptive field, padding, stride, the channels-last
+# flatten order (h W + w) C + c of Sec. 4.3, segment offsets of a second input)
+# is checked against a convolution written out here from its definition:
+# reshape the segment to an H x W x C_in image, zero-pad it, and for every
+# kernel offset (dh, dw) add W[:, dh, dw, :] times the strided window of the
+# padded image.  Nothing below calls the oracle's tap walk.
+
+def _conv_direct(x, term, w):
+    """y[ho, wo, co] = sum_{dh, dw, c} w[co, dh, dw, c] xpad[ho s + dh, wo s + dw, c],
+    flattened channels last; x and w hold Python ints (object arrays)."""
+    H, W, C, s, p = term.H, term.W, term.C_in, term.stride, term.pad
+    img = np.asarray(x[term.in_offset:term.in_offset + H * W * C], dtype=object).reshape(H, W, C)
+    xpad = np.zeros((H + 2 * p, W + 2 * p, C), dtype=object)
+    xpad[p:p + H, p:p + W, :] = img
+    Ho = (H + 2 * p - term.kh) // s + 1
+    Wo = (W + 2 * p - term.kw) // s + 1
+    y = np.zeros((Ho, Wo, term.C_out), dtype=object)
+    for dh in range(term.kh):
+        for dw in range(term.kw):
+            win = xpad[dh:dh + s * (Ho - 1) + 1:s, dw:dw + s * (Wo - 1) + 1:s, :]   # Ho x Wo x C
+            y += np.einsum("hwc,oc->hwo", win, np.asarray(w[:, dh, dw, :], dtype=object))
+    return y.reshape(-1)
+
+
+def _geometry_case(name):
+    """(terms as tuples, weight shapes) of the geometry cases: a 3x3 stride-1
+    pad-1 conv on a non-square input, a 3x3 stride-2 pad-1 conv on an odd
+    non-square input, the 7x7 stride-2 pad-3 stem, and a block's second conv
+    with a 1x1 stride-2 shortcut over a second input segment."""
+    if name == "3x3s1p1":
+        return [(0, 5, 6, 3, 4, 3, 1, 1)]
+    if name == "3x3s2p1":
+        return [(0, 7, 5, 2, 3, 3, 2, 1)]
+    if name == "7x7s2p3":
+        return [(0, 11, 9, 3, 4, 7, 2, 3)]
+    if name == "3x3+1x1s2":
+        # main conv over segment 0 (4x4x3 -> 4x4x5), shortcut 1x1 stride 2
+        # over segment 1 (8x8x2 -> 4x4x5) starting at flat index 48
+        return [(0, 4, 4, 3, 5, 3, 1, 1), (48, 8, 8, 2, 5, 1, 2, 0)]
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["3x3s1p1", "3x3s2p1", "7x7s2p3", "3x3+1x1s2"])
+def test_layer_matrix_equals_direct_convolution(oracle, name):
+    """The oracle's layer as a matrix (dense_matrix, built from its tap walk)
+    times x equals the direct convolution of x, term by term, for every
+    output; integer weights and inputs, compared exactly."""
+    rng = np.random.default_rng(sum(map(ord, name)))
+    terms, ws = [], []
+    for (off, H, W, C, Co, k, s, p) in _geometry_case(name):
+        terms.append(oracle.ConvTerm(off, H, W, C, Co, k, k, s, p))
+        ws.append(rng.integers(-7, 8, (Co, k, k, C)).astype(np.float64))
+    lay = oracle.make_layer(terms, ws, None, 1.0, 1.0)
+    x = rng.integers(-100, 101, lay.E_in)
+    xo = np.array([int(v) for v in x], dtype=object)
+    want = sum(_conv_direct(xo, t, w.astype(np.int64)) for t, w in zip(terms, ws))
+    got = oracle.dense_matrix(lay).dot(xo)
+    assert list(got) == list(want)
+
+
+def test_layer_round_over_several_ciphertexts_equals_direct_convolution(oracle):
+    """A whole round on trivial ciphertexts whose input spans k_in = 3
+    ciphertexts (positions j N + k after the unshuffle), with a strided 1x1
+    shortcut over a second segment, bias, input unshuffle and output shuffle:
+    the packed values read by the client equal the direct convolution plus
+    bias, in shuffled order."""
+    prm = oracle.make_params(6, 2, 50, 1, 50)             # N = 64
+    s = oracle.keygen(prm, 41)
+    keys = oracle.rotation_keys(prm, s, 42)
+    rng = np.random.default_rng(43)
+    terms = [oracle.ConvTerm(0, 5, 4, 4, 3, 3, 3, 2, 1),   # 5x4x4 -> 3x2x3
+             oracle.ConvTerm(80, 6, 3, 5, 3, 1, 1, 2, 0)]  # 6x3x5 -> 3x2x3, second segment
+    ws = [rng.integers(-5, 6, (3, 3, 3, 4)).astype(np.float64),
+          rng.integers(-5, 6, (3, 1, 1, 5)).astype(np.float64)]
+    b = rng.integers(-9, 10, 3).astype(np.float64)
+    lay = oracle.make_layer(terms, ws, b, 1.0, 1.0)
+    assert lay.E_in == 170 and -(-lay.E_in // prm.n) == 3
+    x = rng.integers(-60, 61, lay.E_in)
+    sp = oracle.permutation(44, 1, lay.E_in)
+    so = oracle.permutation(44, 2, lay.E_out)
+    stream = np.zeros(3 * prm.n, dtype=np.int64)
+    stream[:lay.E_in] = x[sp]                               # position k holds x[sigma_prev(k)]
+    cts = np.stack([_trivial(prm, stream[j * prm.n:(j + 1) * prm.n]) for j in range(3)])
+    out = oracle.eval_linear_layer(prm, lay, keys, cts, sp, so)
+    n = oracle.group_size(prm, lay.E_out)
+    vals = []
+    for g in range(out.shape[0]):
+        cent = oracle.crt_centered(prm, out[g, 1])
+        vals.extend(cent[l * (prm.n // n)] for l in range(min(n, lay.E_out - g * n)))
+    xo = np.array([int(v) for v in x], dtype=object)
+    y = sum(_conv_direct(xo, t, w.astype(np.int64)) for t, w in zip(terms, ws))
+    y = y + np.array([int(b[o % 3]) for o in range(lay.E_out)], dtype=object)
+    assert vals == [int(v) for v in y[so]]
+
+
+# ---------------------------------------------------------------- noise ------
+# The paper reports that the noise fast packing puts on each packed output is
+# Gaussian-shaped and far inside the decryption bound (Sec. 5, Remark on DP
+# amplification; appendix "FHE Noise").  These pins derive the first two
+# moments of that noise from the key-switching definition and compare them
+# with the oracle over many seeds.
+#
+# One key switch of tau_d(c) adds, per coefficient,
+#     e_ks = sum_j ct_j * e_j / P  -  IH_B  +  IH_A * s          (real, then floored)
+# where ct_j is the ModUp of digit j (an integer in [0, |D_j| Q_j), sum of
+# |D_j| uniform terms), e_j the key noise (rounded Gaussian, variance
+# sigma^2 + 1/12), and IH_A, IH_B the ModDown remainders x_P / P plus the
+# fast-base-conversion overflow: a sum of K uniforms on [0, 1) (Irwin-Hall).
+# With s uniform ternary (E s^2 = 2/3):
+#     mean  -K/2
+#     var   N (sigma^2 + 1/12) sum_j E[ct_j^2] / P^2 + N (K/12 + K^2/4) (2/3) + K/12
+#     E[ct_j^2] = |D_j| Q_j^2 / 3 + |D_j| (|D_j| - 1) Q_j^2 / 4.
+# Across two key switches under the same secret with independent masks only
+# the IH_A * s terms correlate: E IH_A = K/2, and for positions p, p'
+#     cov = (K^2 / 4)(2/3) sum_i F_p(i) F_p'(i) = (K^2 / 6)(N - 2 |p - p'|),
+# F_p(i) = +1 for i <= p, -1 otherwise (the negacyclic signs of 1 * s).
+#
+# Packing (t = 2, gamma = 0): at a packed position the tree gives
+# e <- e_ks + 2 e_child (tau_{m+1} fixes even lattice points and negates odd
+# ones, which the X^s shift of the odd half cancels) and every trace step
+# gives e <- 2 e + e_ks (tau_{2^k+1} fixes the whole lattice).  So the
+# noise at position l N / n is sum_k w_k e_ks,k[p_k] over the log2 n tree
+# merges on leaf l's path (weights 2^T, 2^(T+1), ..., positions moving down
+# by N/m where leaf l's bit at that level is odd) and the T = log2(N/n) trace
+# steps (weights 2^(T-1), ..., 1, all at l N / n), each key switch under its
+# own key.
+
+def _ks_noise_moments(prm):
+    """(mean, variance) of one key switch's noise per coefficient."""
+    N, K = prm.n, prm.K
+    sig2 = prm.sigma ** 2 + 1.0 / 12
+    ct2 = 0.0
+    for j in range(prm.dnum):
+        D = list(prm.digit(j))
+        Qj = math.prod(prm.q[i] for i in D)
+        ct2 += (len(D) * Qj ** 2 / 3 + len(D) * (len(D) - 1) * Qj ** 2 / 4) / prm.P ** 2
+    return -K / 2, N * sig2 * ct2 + N * (K / 12 + K * K / 4) * (2.0 / 3) + K / 12
+
+
+def _packed_noise_moments(prm, n, l):
+    """(mean, variance) of the noise at packed position l N / n."""
+    N, K = prm.n, prm.K
+    T = prm.log_n - int(math.log2(n))
+    p = l * N // n
+    path = [(2 ** (T - t), p) for t in range(1, T + 1)]          # trace steps
+    m, lm, w = n, l, 2 ** T
+    while m >= 2:                                                 # tree merges, root first
+        path.append((w, p))
+        if lm % 2:
+            p -= N // m
+        lm, m, w = lm // 2, m // 2, 2 * w
+    mu, v = _ks_noise_moments(prm)
+    var = v * sum(wk * wk for wk, _ in path)
+    for a, (wa, pa) in enumerate(path):
+        for b, (wb, pb) in enumerate(path):
+            if a != b:
+                var += wa * wb * (K * K / 6.0) * (N - 2 * abs(pa - pb))
+    return mu * sum(wk for wk, _ in path), var
+
+
+def _noise_free(oracle, prm, s, msg, seed):
+    """A ciphertext (a, a s + m) with uniform mask and no noise."""
+    import dataclasses
+    return oracle.encrypt(dataclasses.replace(prm, sigma=0.0), s, msg, seed, 1)[0]
+
+
+def _seed_stats(samples):
+    """Pooled mean and second central moment over seeds, with standard errors
+    from the spread of the per-seed values (seeds are independent)."""
+    x = np.array(samples, dtype=np.float64)           # [seeds][values per seed]
+    m1 = x.mean(axis=1)
+    mean = m1.mean()
+    m2 = (x ** 2).mean(axis=1)
+    var = m2.mean() - mean ** 2
+    return mean, m1.std() / np.sqrt(len(x)), var, m2.std() / np.sqrt(len(x))
+
+
+@pytest.mark.parametrize("L,qbits,K,pbits", [(3, 50, 1, 50), (3, 50, 2, 50), (2, 30, 1, 60), (2, 30, 2, 60)])
+def test_keyswitch_noise_moments(oracle, L, qbits, K, pbits):
+    """Mean and variance of the noise one key switch adds (rotation of a
+    noise-free ciphertext by tau_3) match the analytic model above, for
+    one-limb and two-limb digits, with P about Q_j (key noise dominates) and
+    with P >> Q (ModDown remainders dominate); 600 seeds of key and mask."""
+    prm = oracle.make_params(8, L, qbits, K, pbits)
+    d = 3
+    samples = []
+    for sd in range(600):
+        s = oracle.keygen(prm, 1000 + sd)
+        keys = oracle.rotation_keys(prm, s, 2000 + sd, [d])
+        m = np.random.default_rng(sd).integers(-1000, 1001, prm.n)
+        r = oracle.rotate(prm, keys, d, _noise_free(oracle, prm, s, m, 3000 + sd))
+        got = oracle.crt_centered(prm, oracle.decrypt(prm, s, r)[0])
+        tm = [0] * prm.n                               # tau_d(m) by its definition
+        for i in range(prm.n):
+            e = i * d % (2 * prm.n)
+            if e < prm.n:
+                tm[e] += int(m[i])
+            else:
+                tm[e - prm.n] -= int(m[i])
+        samples.append([g - t for g, t in zip(got, tm)])
+    mean, se_mean, var, se_var = _seed_stats(samples)
+    mu, v = _ks_noise_moments(prm)
+    assert abs(mean - mu) <= 4 * se_mean + 0.05, (mean, mu, se_mean)
+    assert abs(var - v) <= 4 * se_var, (var, v, se_var)
+    assert abs(var / v - 1) <= 0.12
+
+
+@pytest.mark.parametrize("L,qbits,K,pbits", [(3, 50, 2, 50), (2, 30, 1, 60)])
+def test_packed_noise_moments_shape_and_bound(oracle, L, qbits, K, pbits):
+    """Noise of fast packing on noise-free leaves (N = 256, n = 8, 300 seeds):
+    at every packed position its mean and variance match the path model
+    above; pooled over positions it is Gaussian-shaped (skewness and excess
+    kurtosis near 0); and every coefficient of every output lies far inside
+    the decryption bound Q/2."""
+    prm = oracle.make_params(8, L, qbits, K, pbits)
+    n = 8
+    per_pos = [[] for _ in range(n)]
+    worst = 0
+    for sd in range(300):
+        s = oracle.keygen(prm, 5000 + sd)
+        keys = oracle.rotation_keys(prm, s, 6000 + sd)
+        leaves = [_noise_free(oracle, prm, s, np.zeros(1, dtype=np.int64), 7000 + 100 * sd + l) for l in range(n)]
+        dec = oracle.crt_centered(prm, oracle.decrypt(prm, s, oracle.pack(prm, keys, leaves))[0])
+        worst = max(worst, max(abs(v) for v in dec))
+        for l in range(n):
+            per_pos[l].append([dec[l * prm.n // n]])
+    z = []
+    for l in range(n):
+        mean, se_mean, var, se_var = _seed_stats(per_pos[l])
+        mu, v = _packed_noise_moments(prm, n, l)
+        assert abs(mean - mu) <= 4 * se_mean, (l, mean, mu, se_mean)
+        assert abs(var - v) <= 4 * se_var, (l, var, v, se_var)
+        z.extend((np.array(per_pos[l])[:, 0] - mu) / math.sqrt(v))
+    z = np.array(z)
+    skew = np.mean(z ** 3) / np.mean(z ** 2) ** 1.5
+    exkurt = np.mean(z ** 4) / np.mean(z ** 2) ** 2 - 3
+    assert abs(skew) < 0.2 and abs(exkurt) < 0.5, (skew, exkurt)
+    std_max = max(math.sqrt(_packed_noise_moments(prm, n, l)[1]) for l in range(n))
+    assert worst < 8 * std_max < prm.Q / 2 ** 20
