@@ -1,25 +1,34 @@
 """Benchmark: encrypted linear layers per second on one GB300 (or N replicas).
 
 One step = one full server round of the benchmark layer through the C ABI
-(sf_eval_linear_layer): a ResNet-20 stage-1 convolution, 3x3, 16 -> 16
-channels on a 16x32x32 input, ring N = 2^14 with 3 x 50-bit data primes and
-one 50-bit special prime, fixed-point scale 2^40, with the input unshuffle and
-the output shuffle; 16384 leaf products, 16382 pack-tree merges and 2 trace
-steps (16384 automorphism + hybrid key switches), 2 packed output ciphertexts.
+(sf_eval_linear_layer).  The default layer (``--workload r34``) is a round of
+the ResNet-34-shaped network at the largest parameter set: the first conv of
+its last stage, 3x3 stride 2, 256 -> 512 channels on a 14x14x256 input, ring
+N = 2^16 with 5 x 50-bit data primes and 2 special primes, fixed-point scale
+2^40, with the input unshuffle and the output shuffle: 25088 leaf products
+over 2304 taps each, 32767 pack-tree merges and 1 trace step (32768
+automorphism + hybrid key switches), 1 packed output ciphertext.
+``--workload conv16`` is the ResNet-20 stage-1 conv (3x3, 16 -> 16 on
+16x32x32) at N = 2^14 with 3 x 50-bit + 1 special prime.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload conv16|resnet18|resnet34|serve]
+                  [--workload r34|conv16|resnet18|resnet34|serve] [--no-extras]
 
-The default workload (conv16) prints the one-line benchmark record.  The
-other workloads are the network-scale measurements, each one JSON line:
-resnet18 (all 18 layer rounds of a ResNet-18 on 3x64x64 at N = 2^15, each
-with its own synthetic input: one sf_eval_layers batch vs one call per
-layer), resnet34 (every round of a ResNet-34 on 3x224x224 at N = 2^16, per
-layer and end to end) and serve (Poisson arrivals of encrypted ResNet-20 /
-ResNet-18 requests through the continuous-batching server).
+The one-layer workloads print the one-line benchmark record.  Unless
+--no-extras is given, the r34 line also carries, measured after its timed
+region: the conv16 round (``conv16``), a bounded serving run of ResNet-20
+requests below capacity with p50/p99 latency (``serving``), and the last five
+rounds of the ResNet-18 network at N = 2^15 as one batched call against one
+call per round (``batched_vs_per_layer``).  The other workloads are the
+network-scale measurements, each one JSON line: resnet18 (all 18 layer rounds
+of a ResNet-18 on 3x64x64 at N = 2^15, each with its own synthetic input: one
+sf_eval_layers batch vs one call per layer), resnet34 (every round of a
+ResNet-34 on 3x224x224 at N = 2^16, per layer and end to end) and serve
+(Poisson arrivals of encrypted ResNet-20 / ResNet-18 requests through the
+continuous-batching server).
 
 --impl reference times the CPU oracle (the plain schoolbook implementation
-under oracle/) on the host cores, on a bounded sample of the same workload
+under oracle/) on the host cores, on a bounded sample of the same layer
 extrapolated to whole layers.  Under torchrun each rank runs an independent
 replica (the round has no cross-GPU exchange); rank 0 prints one JSON line.
 """
@@ -41,10 +50,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "encrypted linear layers/s"
 UNIT = "layers/s"
-WORKLOAD = ("conv16: ResNet-20 conv 3x3 16->16 on 16x32x32 (E = E' = 16384), N = 2^14, 3 x 50-bit + 1 "
-            "special prime, scale 2^40, input unshuffle + output shuffle, 2 packed outputs of 8192, "
-            "16384 key switches per layer")
-NTT_POLYS = 512        # forward-NTT record: 512 x L limbs (192 MiB in, 192 MiB out at N = 2^14, L = 3)
+LAYERS = {
+    # name: (parameter set, case factory name, keygen / encrypt / rotation-key seeds, description)
+    "r34": ("r34", ("resnet34", "s3b0c1", 401), (403, 404, 405),
+            "r34.s3b0c1: ResNet-34 conv 3x3 stride 2, 256 -> 512 channels on 14x14x256 (E = 50176, "
+            "E' = 25088, 2304 taps per output), N = 2^16, 5 x 50-bit + 2 special primes, scale 2^40, input "
+            "unshuffle + output shuffle, 1 packed output of 32768 slots, 32768 key switches per layer"),
+    "conv16": ("conv16", None, (203, 204, 205),
+               "conv16: ResNet-20 conv 3x3 16->16 on 16x32x32 (E = E' = 16384), N = 2^14, 3 x 50-bit + 1 "
+               "special prime, scale 2^40, input unshuffle + output shuffle, 2 packed outputs of 8192, "
+               "16384 key switches per layer"),
+}
+WORKLOAD = LAYERS["r34"][3]
+NTT_POLYS = 512        # forward-NTT record: 512 x L limbs of the benchmark ring
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -58,7 +76,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch batch")
     ap.add_argument("--reference-sample-s", type=float, default=8.0,
                     help="--impl reference: CPU seconds bound of each step's oracle sample")
-    ap.add_argument("--workload", default="conv16", choices=["conv16", "resnet18", "resnet34", "serve"])
+    ap.add_argument("--workload", default="r34", choices=["r34", "conv16", "resnet18", "resnet34", "serve"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="r34: skip the conv16, serving and batched-vs-per-layer sub-records")
     ap.add_argument("--rates", default="5,20,200", help="serve: arrival rates (requests/s)")
     ap.add_argument("--duration", type=float, default=20.0, help="serve: arrival window per rate (s)")
     ap.add_argument("--drain", type=float, default=60.0, help="serve: time allowed after the window (s)")
@@ -69,7 +89,8 @@ def parse():
     ap.add_argument("--layer-stats", default="",
                     help="resnet18/resnet34: only a per-kernel breakdown of these rounds (comma-separated names)")
     ap.add_argument("--small", action="store_true",
-                    help="profiling case: the same conv kernel shapes on 8x16x16 (2048 outputs, ~2 GB on device)")
+                    help="profiling case: the same kernel shapes on a smaller layer (conv16: 8x16x16, 2048 "
+                         "outputs; r34: 64x7x7 -> 256 channels, 12544 outputs; a few GB on the device)")
     return ap.parse_args()
 
 
@@ -133,32 +154,50 @@ class ClockSampler:
 # ------------------------------------------------------------ workload ----
 
 class Workload:
-    """Keys, weights and the encrypted input of the benchmark layer, resident on the device."""
+    """Keys, weights and the encrypted input of a benchmark layer, resident on the device."""
 
-    def __init__(self, device: int, small: bool = False):
+    def __init__(self, device: int, kind: str = "r34", small: bool = False):
         import torch
         import paper_2509_01253_gb300 as sf
         from paper_2509_01253_gb300 import workloads as wl
         self.sf, self.torch = sf, torch
-        self.ps = ps = wl.PARAMS["conv16"]
-        self.case = case = wl.small_conv_case(201, 8, 16, 16, 16) if small else wl.conv16_case()
+        pset, case_of, (s_key, s_enc, s_rot), desc = LAYERS[kind]
+        self.kind, self.desc = kind, desc
+        self.ps = ps = wl.PARAMS[pset]
+        if kind == "conv16":
+            self.case = case = wl.small_conv_case(201, 8, 16, 16, 16) if small else wl.conv16_case()
+        elif small:
+            self.case = case = wl.small_conv_case(401, 7, 7, 64, 256, x_range=(0.0, 1.0))
+        else:
+            self.case = case = wl.round_case(*case_of)
+        if small:
+            self.desc = f"{kind}-small (profiling case, same ring and kernels): {case.name}, E' = {case.E_out}"
         self.params = sf.sf_params_create(ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits, ps.sigma)
         self.ctx = sf.sf_ctx_create(self.params, device)
-        self.sk = sf.sf_keygen(self.ctx, 203)
-        self.rk = sf.sf_gen_rotation_keys(self.ctx, self.sk, None, 205)
+        self.sk = sf.sf_keygen(self.ctx, s_key)
+        self.rk = sf.sf_gen_rotation_keys(self.ctx, self.sk, None, s_rot)
         W = np.concatenate([w.ravel() for w in case.weights])
         self.layer = sf.sf_encode_weights(self.ctx, case.terms, W, None, ps.delta, ps.delta ** 2)
         self.info = sf.sf_layer_get_info(self.ctx, self.layer)
         self.n, self.L = 1 << ps.log_n, ps.n_data
-        xs = case.x[case.sigma_prev.astype(np.int64)]
+        xs = case.x if case.sigma_prev is None else case.x[case.sigma_prev.astype(np.int64)]
         self.msg = sf.sf_encode_input(xs, ps.delta)
         self.k_in, self.G = self.info["k_in"], self.info["n_groups"]
         dev = f"cuda:{device}"
         self.d_in = torch.zeros((self.k_in, 2, self.L, self.n), dtype=torch.int64, device=dev)
-        sf.sf_encrypt(self.ctx, self.sk, self.msg, 204, self.d_in, self.k_in)
+        sf.sf_encrypt(self.ctx, self.sk, self.msg, s_enc, self.d_in, self.k_in)
         self.d_out = torch.zeros((self.G, 2, self.L, self.n), dtype=torch.int64, device=dev)
         self.stream = torch.cuda.current_stream(device)
         self.ct_bytes = 2 * self.L * self.n * 8
+
+    def destroy(self):
+        sf = self.sf
+        sf.sf_layer_destroy(self.layer)
+        sf.sf_rotkeys_destroy(self.rk)
+        sf.sf_secret_key_destroy(self.sk)
+        sf.sf_ctx_destroy(self.ctx)
+        sf.sf_params_destroy(self.params)
+        self.d_in = self.d_out = None
 
     def step(self):
         self.sf.sf_eval_linear_layer(self.ctx, self.layer, self.rk, self.d_in, self.k_in, self.case.sigma_prev,
@@ -183,7 +222,9 @@ class Workload:
         sf.sf_decrypt(self.ctx, self.sk, self.d_out, self.G, res, self.stream)
         vals = sf.sf_decode(self.params, res, self.G, self.n // self.info["group_size"], self.info["E_out"],
                             self.ps.delta ** 2)
-        ref = wl.float_reference(self.case)[self.case.sigma_out.astype(np.int64)]
+        ref = wl.float_reference(self.case)
+        if self.case.sigma_out is not None:
+            ref = ref[self.case.sigma_out.astype(np.int64)]
         return float(np.abs(vals - ref).max())
 
 
@@ -290,11 +331,12 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-# per-item DRAM bytes (read + write) from an ncu capture of the small conv16
-# case (dram__bytes_read.sum + dram__bytes_write.sum of one launch of 256
-# merges), for kernels whose code has not changed since; scaled to a launch
-# by its items
-TRAFFIC_PER_ITEM = {"ks3_inner_row": (410.9696e6 + 231.995904e6) / 256}
+# per-item DRAM bytes (read + write) of a kernel at a ring size (log2 N), from
+# an ncu capture of a small case of the same kernel and ring
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch divided by its
+# items), kept only while the kernel's code is unchanged since the capture;
+# scaled to a full launch by its items
+TRAFFIC_PER_ITEM = {}
 
 
 def items_per_layer(kernel: str, info: dict, merges: int) -> int:
@@ -308,7 +350,7 @@ def items_per_layer(kernel: str, info: dict, merges: int) -> int:
 
 
 def roofline_of(kstats: dict, k_steps: int, g: RingShape, info: dict, total_kernel_ms: float, clk: dict,
-                merges: int = None, probe: dict = None):
+                merges: int = None, probe: dict = None, sm_count: int = 152):
     """Roofline record of the kernel with the largest device-time share:
     algorithmic work per layer / its measured time per layer, against the
     measured HBM copy bandwidth and the derived modular-multiplication peak;
@@ -320,7 +362,7 @@ def roofline_of(kstats: dict, k_steps: int, g: RingShape, info: dict, total_kern
     items = items_per_layer(top, info, merges)
     b_item, m_item = kernel_work(top, g, info["k_in"])
     hbm_peak, peak_kind = load_peaks()
-    alu_pk = alu_peak(152, 2070.0)
+    alu_pk = alu_peak(sm_count, 2070.0)
     hbm_ach = b_item * items / per_layer_s / 1e9
     alu_ach = m_item * items / per_layer_s / 1e9
     t_hbm = b_item / (hbm_peak * 1e9)
@@ -328,7 +370,7 @@ def roofline_of(kstats: dict, k_steps: int, g: RingShape, info: dict, total_kern
     bound = "alu" if t_alu >= t_hbm else "hbm"
     ceil = probe_ceiling(kernel_ops(top, g, info["k_in"]), probe)
     launches = cnt // k_steps
-    traffic = TRAFFIC_PER_ITEM.get(top)
+    traffic = TRAFFIC_PER_ITEM.get((top, g.n.bit_length() - 1))
     rec = {"bound": bound, "kernel": top,
            "achieved": alu_ach if bound == "alu" else hbm_ach,
            "peak": alu_pk / 1e9 if bound == "alu" else hbm_peak,
@@ -336,12 +378,12 @@ def roofline_of(kstats: dict, k_steps: int, g: RingShape, info: dict, total_kern
     rec["frac"] = rec["achieved"] / rec["peak"]
     rec["traffic"] = traffic * items / launches if traffic else None
     rec.update({
-        "peak_source": ("derived: 152 SMs x 64 int32 multiply-adds/clk x 2070 MHz / 10 per 64-bit modmul"
+        "peak_source": (f"derived: {sm_count} SMs x 64 int32 multiply-adds/clk x 2070 MHz / 10 per 64-bit modmul"
                         if bound == "alu" else f"{peak_kind} hbm_gbs"),
         "hbm_view": {"achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
                      "peak_source": peak_kind},
         "alu_view": {"achieved": alu_ach, "peak": alu_pk / 1e9, "unit": "Gmodmul/s", "frac": alu_ach * 1e9 / alu_pk,
-                     "at_median_clock": (alu_ach * 1e9 / alu_peak(152, clk["sm_mhz"])) if clk.get("sm_mhz") else None,
+                     "at_median_clock": (alu_ach * 1e9 / alu_peak(sm_count, clk["sm_mhz"])) if clk.get("sm_mhz") else None,
                      "probe_peak": ceil, "frac_of_probe": (alu_ach / ceil) if ceil else None,
                      "probe_source": "sf_modmul_probe: register-resident butterflies and multiply-accumulates "
                                      "measured on this GPU, weighted by this kernel's mix of operations"},
@@ -396,38 +438,7 @@ def ntt_record(sf, torch, wl_, p_info: dict, probe: dict, flush) -> dict:
 
 # ------------------------------------------------------- CPU baseline ----
 
-def oracle_sample(max_seconds: float = 20.0):
-    """Times the oracle on a bounded sample of the benchmark layer: key
-    switches (rotate at N = 2^14) and leaf outputs, extrapolated to one layer
-    (16384 of each).  Returns (layers/s, cores, sample description)."""
-    import oracle as O
-    from paper_2509_01253_gb300 import workloads as wl
-    ps = wl.PARAMS["conv16"]
-    case = wl.conv16_case()
-    prm = O.make_params(ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits)
-    s_o = O.keygen(prm, 203)
-    keys = O.rotation_keys(prm, s_o, 205, [3])
-    xs = case.x[case.sigma_prev.astype(np.int64)]
-    cts = O.encrypt(prm, s_o, O.quantize(xs, ps.delta), 204, 1)
-    terms = [O.ConvTerm(t.in_offset, t.H, t.W, t.C_in, t.C_out, t.kh, t.kw, t.stride, t.pad) for t in case.terms]
-    lay = O.make_layer(terms, case.weights, None, ps.delta, ps.delta ** 2)
-    t0 = time.perf_counter()
-    n_leaf = 0
-    while True:
-        O.linear_output(prm, lay, cts, int(case.sigma_out[n_leaf % 16384]), case.sigma_prev)
-        n_leaf += 1
-        if n_leaf >= 8 or time.perf_counter() - t0 > max_seconds / 4:
-            break
-    t_leaf = (time.perf_counter() - t0) / n_leaf
-    t0 = time.perf_counter()
-    n_ks = 0
-    while True:
-        O.rotate(prm, keys, 3, cts[0])
-        n_ks += 1
-        if n_ks >= 2 or time.perf_counter() - t0 > max_seconds / 2:
-            break
-    t_ks = (time.perf_counter() - t0) / n_ks
-    t_layer = 16384 * t_leaf + 16384 * t_ks
+def host_cores() -> int:
     cores = os.cpu_count()
     try:
         cores = len(os.sched_getaffinity(0))
@@ -436,9 +447,81 @@ def oracle_sample(max_seconds: float = 20.0):
     omp = os.environ.get("OMP_NUM_THREADS")
     if omp:
         cores = min(cores, int(omp))
-    desc = (f"{n_leaf} leaf outputs ({t_leaf:.3f} s each) + {n_ks} key switches ({t_ks:.2f} s each) of the "
-            f"conv16 layer at full size, extrapolated x16384 each (packing additions not counted)")
-    return 1.0 / t_layer, cores, desc
+    return cores
+
+
+class OracleSample:
+    """The oracle on a bounded sample of a benchmark layer, on the host cores.
+
+    Set-up (outside any timing): parameters, secret key, the encrypted layer
+    input and the quantised layer.  Each sample times (a) leaf outputs, one
+    output's extraction + unshuffle + linear step over all its taps at full
+    size (oracle.linear_output), and (b) one schoolbook negacyclic limb product
+    at full size per host core, run concurrently (oracle.polymul; ctypes
+    releases the interpreter lock).  A layer is then E' leaf outputs plus
+    ks_count key switches of 2 * dnum * (L + K) limb products each (the
+    oracle's inner product with the key, spread over the host cores); the
+    key switch's base conversions, automorphism and the packing additions
+    (O(N) work each) are not counted, so the estimate is a lower bound on the
+    oracle's time per layer."""
+
+    def __init__(self, kind: str = "r34"):
+        import oracle as O
+        from paper_2509_01253_gb300 import workloads as wl
+        self.O = O
+        pset, case_of, (s_key, s_enc, _), _ = LAYERS[kind]
+        ps = wl.PARAMS[pset]
+        self.case = case = wl.conv16_case() if kind == "conv16" else wl.round_case(*case_of)
+        self.prm = prm = O.make_params(ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits)
+        s_o = O.keygen(prm, s_key)
+        xs = case.x if case.sigma_prev is None else case.x[case.sigma_prev.astype(np.int64)]
+        self.k_in = -(-xs.size // prm.n)
+        self.cts = O.encrypt(prm, s_o, O.quantize(xs, ps.delta), s_enc, self.k_in)
+        terms = [O.ConvTerm(t.in_offset, t.H, t.W, t.C_in, t.C_out, t.kh, t.kw, t.stride, t.pad) for t in case.terms]
+        self.lay = O.make_layer(terms, case.weights, None, ps.delta, ps.delta ** 2)
+        self.e_out = self.lay.E_out
+        self.ks = O.ks_count(prm, self.e_out)
+        self.prods_per_ks = 2 * prm.dnum * (prm.L + prm.K)
+        self.cores = host_cores()
+        rng = np.random.default_rng(7)
+        q0 = prm.q[0]
+        self.pa = [rng.integers(0, q0, prm.n, dtype=np.uint64) for _ in range(self.cores)]
+        self.pb = [rng.integers(0, q0, prm.n, dtype=np.uint64) for _ in range(self.cores)]
+        self.name = kind
+
+    def run(self, max_seconds: float = 8.0):
+        """Returns (layers/s, description) of one bounded sample."""
+        from concurrent.futures import ThreadPoolExecutor
+        O, case = self.O, self.case
+        t0 = time.perf_counter()
+        n_leaf = 0
+        while True:
+            o = int(case.sigma_out[n_leaf % self.e_out]) if case.sigma_out is not None else n_leaf % self.e_out
+            O.linear_output(self.prm, self.lay, self.cts, o, case.sigma_prev)
+            n_leaf += 1
+            if n_leaf >= 8 or time.perf_counter() - t0 > max_seconds / 3:
+                break
+        t_leaf = (time.perf_counter() - t0) / n_leaf
+        q0 = self.prm.q[0]
+        with ThreadPoolExecutor(self.cores) as ex:
+            t0 = time.perf_counter()
+            list(ex.map(lambda i: O.polymul(self.pa[i], self.pb[i], q0), range(self.cores)))
+            t_batch = time.perf_counter() - t0
+        t_ks = self.prods_per_ks / self.cores * t_batch
+        t_layer = self.e_out * t_leaf + self.ks * t_ks
+        desc = (f"{self.name} layer at full size: {n_leaf} leaf outputs ({t_leaf:.3f} s each, x{self.e_out}) and "
+                f"{self.cores} concurrent limb products of N = {self.prm.n} ({t_batch:.2f} s), i.e. "
+                f"{t_ks:.2f} s per key switch of {self.prods_per_ks} limb products on {self.cores} cores "
+                f"(x{self.ks}); base conversions, automorphisms and packing additions not counted; "
+                f"extrapolated to one layer")
+        return 1.0 / t_layer, desc
+
+
+def oracle_sample(kind: str = "r34", max_seconds: float = 20.0):
+    """One bounded oracle sample of the benchmark layer: (layers/s, cores, description)."""
+    smp = OracleSample(kind)
+    v, desc = smp.run(max_seconds)
+    return v, smp.cores, desc
 
 
 # ----------------------------------------------------------------- main ----
@@ -472,10 +555,12 @@ def dist_setup():
 def run_reference(args, dist, ws, rank):
     if rank != 0:
         return 0
+    kind = args.workload if args.workload in LAYERS else "r34"
+    smp = OracleSample(kind)
     times = []
-    cores = desc = None
+    desc = None
     for i in range(args.warmup + args.steps):
-        v, cores, desc = oracle_sample(max_seconds=args.reference_sample_s)
+        v, desc = smp.run(max_seconds=args.reference_sample_s)
         if i >= args.warmup:
             times.append(1.0 / v)
     sec = sum(times) / len(times)
@@ -483,9 +568,8 @@ def run_reference(args, dist, ws, rank):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD if not args.small else "conv16-small (profiling case): " + WORKLOAD.replace(
-                "16x32x32 (E = E' = 16384)", "8x16x16 (E = E' = 2048)"), "parallelism": "host cores (OpenMP)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "config": {"workload": LAYERS[kind][3], "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": smp.cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -502,7 +586,7 @@ class NetworkWorkload:
     from the session seed (none before the first and after the last round),
     encrypted and resident on the device."""
 
-    def __init__(self, kind: str, device: int, seed: int):
+    def __init__(self, kind: str, device: int, seed: int, names=None):
         import torch
         import paper_2509_01253_gb300 as sf
         from paper_2509_01253_gb300 import network as nw
@@ -514,16 +598,19 @@ class NetworkWorkload:
         self.ctx = sf.sf_ctx_create(self.params, device)
         self.sk = sf.sf_keygen(self.ctx, seed + 3)
         self.rk = sf.sf_gen_rotation_keys(self.ctx, self.sk, None, seed + 5)
-        self.net = nw.EncodedNetwork(self.params, self.ctx, ps, wl.resnet_rounds(kind))
+        rounds = wl.resnet_rounds(kind)
+        if names is not None:
+            rounds = [r for r in rounds if r.name in names]
+        self.net = nw.EncodedNetwork(self.params, self.ctx, ps, rounds)
         self.n, self.L = 1 << ps.log_n, ps.n_data
         dev = f"cuda:{device}"
         self.stream = torch.cuda.current_stream(device)
         self.d_ins, self.d_outs, self.sps, self.sos, self.k_ins, self.caps = [], [], [], [], [], []
-        last = len(self.net.rounds) - 1
         for r, info in enumerate(self.net.infos):
+            first, last = self.net.rounds[r].name == "stem", self.net.rounds[r].name == "fc"
             x = np.random.default_rng(seed + 100 + r).uniform(0.0, 1.0, info["E_in"])
-            sp = None if r == 0 else sf.sf_permutation(seed + 4, r, info["E_in"])
-            so = None if r == last else sf.sf_permutation(seed + 4, r + 1, info["E_out"])
+            sp = None if first else sf.sf_permutation(seed + 4, r, info["E_in"])
+            so = None if last else sf.sf_permutation(seed + 4, r + 1, info["E_out"])
             xs = x if sp is None else x[sp.astype(np.int64)]
             d_in = torch.empty((info["k_in"], 2, self.L, self.n), dtype=torch.int64, device=dev)
             sf.sf_encrypt(self.ctx, self.sk, sf.sf_encode_input(xs, ps.delta), seed + 1000 + r, d_in, info["k_in"])
@@ -551,6 +638,15 @@ class NetworkWorkload:
                                           [self.d_ins[r] for r in idx], [self.k_ins[r] for r in idx],
                                           [self.sps[r] for r in idx], [self.sos[r] for r in idx],
                                           [self.d_outs[r] for r in idx], [self.caps[r] for r in idx], 1, self.stream)
+
+    def destroy(self):
+        sf = self.sf
+        self.net.destroy()
+        sf.sf_rotkeys_destroy(self.rk)
+        sf.sf_secret_key_destroy(self.sk)
+        sf.sf_ctx_destroy(self.ctx)
+        sf.sf_params_destroy(self.params)
+        self.d_ins = self.d_outs = []
 
     def max_err(self, rounds) -> float:
         """Max |decoded - float64| over every output of the given rounds."""
@@ -704,6 +800,112 @@ def run_request_e2e(args, local: int) -> int:
     return 0
 
 
+def conv16_record(local: int, steps: int = 5) -> dict:
+    """The conv16 round (N = 2^14, 3 x 50-bit + 1): autotuned, warmed up, then
+    `steps` timed rounds with the L2 flushed between them, and its decryption
+    check; the kernel with the largest device time from an instrumented pass."""
+    import torch
+    wl_ = Workload(local, "conv16")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
+    wl_.step()
+    tuned = wl_.autotune()
+    for _ in range(3):
+        wl_.step()
+    ms = []
+    for _ in range(steps):
+        flush_l2(flush)
+        ms.append(timed(torch, wl_.stream, wl_.step))
+    err = wl_.check()
+    sf = wl_.sf
+    sf.sf_kernel_stats_reset(wl_.ctx)
+    sf.sf_ctx_set_option(wl_.ctx, "kernel_timing", 1)
+    for _ in range(2):
+        flush_l2(flush)
+        wl_.step()
+    torch.cuda.synchronize()
+    ks = launches(sf, wl_.ctx)
+    sf.sf_ctx_set_option(wl_.ctx, "kernel_timing", 0)
+    g = RingShape(sf.sf_params_get_info(wl_.params))
+    tot = sum(m for _, m in ks.values())
+    top = roofline_of(ks, 2, g, wl_.info, tot, {"sm_mhz": None}, sm_count=sm_count_of(local))
+    wl_.destroy()
+    t = sum(ms) / len(ms)
+    return {"workload": LAYERS["conv16"][3], "value": 1e3 / t, "unit": UNIT, "ms_per_step": t, "step_ms": ms,
+            "steps": steps, "autotuned": tuned, "max_abs_err": err,
+            "top_kernel": {k: top[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac",
+                                              "share_of_device_time")},
+            "kernels": {k: {"launches_per_layer": c // 2, "ms_per_layer": m / 2} for k, (c, m) in ks.items() if c}}
+
+
+def serving_record(local: int, rate: float = 0.3, duration: float = 30.0, drain: float = 60.0) -> dict:
+    """Continuous-batching server below capacity: ResNet-20 requests at
+    N = 2^14 from 4 client keys, Poisson arrivals at `rate` per second for
+    `duration` seconds; p50/p99 latency of the completed requests (each
+    checked against the float64 network), and one request alone."""
+    from paper_2509_01253_gb300 import serve
+    from paper_2509_01253_gb300 import workloads as wl
+    pool = serve.Pool(wl.PARAMS["conv16"], ["resnet20"], 4, local, key_seed=7000, priority=-1)
+    budget = 48 << 30
+    srv = serve.Server({"c2": pool}, {"resnet20": "c2"}, budget, max_active=1, max_batch=1)
+    alone = serve.run_arrivals(srv, [(0.0, "resnet20", 0, 99)], drain=600.0)
+    arr = serve.poisson_arrivals(rate, duration, {"resnet20": 1.0}, 4, seed=31)
+    srv = serve.Server({"c2": pool}, {"resnet20": "c2"}, budget, max_active=16)
+    st = serve.run_arrivals(srv, arr, drain, verify=True)
+    pool.destroy()
+    return {"what": f"ResNet-20 (3x32x32, 20 rounds, N = 2^14) requests, Poisson {rate} req/s for {duration:.0f} s, "
+                    f"4 client keys, continuous batching; latency = arrival to logits, client steps included",
+            "rate_req_s": rate, "p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
+            "arrivals": st["arrivals"], "completed": st["completed"], "rejected": st["rejected"],
+            "served_layers_per_s": st["layers_per_s"], "mean_rounds_per_call": st["mean_rounds_per_call"],
+            "max_abs_err_vs_float64": st["max_abs_err_vs_float64"],
+            "alone_latency_s": alone["p50_latency_s"]}
+
+
+BATCH_ROUNDS = ["s3b0c1", "s3b0c2", "s3b1c1", "s3b1c2", "fc"]
+
+
+def batched_record(local: int, reps: int = 2) -> dict:
+    """The last five rounds of the ResNet-18 network at N = 2^15 (4 x 50-bit
+    + 2), each with its own encrypted input: one sf_eval_layers call against
+    one sf_eval_linear_layer call per round (both captured once, L2 flushed
+    before each timed run, best of `reps`), with the decryption check of
+    every output of both forms."""
+    import torch
+    nw_ = NetworkWorkload("resnet18", local, 300, names=BATCH_ROUNDS)
+    nw_._seed = 300
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
+    R = len(nw_.net.rounds)
+
+    def per_layer_all():
+        for r in range(R):
+            nw_.per_layer(r)
+
+    per_layer_all()
+    t_p = []
+    for _ in range(reps):
+        flush_l2(flush)
+        t_p.append(timed(torch, nw_.stream, per_layer_all))
+    err_p = nw_.max_err(range(R))
+    nw_.batched()
+    t_b = []
+    for _ in range(reps):
+        flush_l2(flush)
+        t_b.append(timed(torch, nw_.stream, nw_.batched))
+    err_b = nw_.max_err(range(R))
+    ks = nw_.net.total_ks()
+    nw_.destroy()
+    return {"what": "ResNet-18 (3x64x64) rounds " + ", ".join(BATCH_ROUNDS) + " at N = 2^15, 4 x 50-bit + 2, "
+                    "each with its own synthetic input; default launch batch",
+            "key_switches": ks, "per_layer_ms": min(t_p), "batched_ms": min(t_b),
+            "speedup_batched_vs_per_layer": min(t_p) / min(t_b), "layers_per_s_batched": R / (min(t_b) / 1e3),
+            "max_abs_err": {"per_layer": err_p, "batched": err_b}}
+
+
+def sm_count_of(local: int) -> int:
+    import torch
+    return torch.cuda.get_device_properties(local).multi_processor_count
+
+
 def main():
     args = parse()
     dist, ws, rank, local = dist_setup()
@@ -719,7 +921,8 @@ def main():
     import torch
     import paper_2509_01253_gb300 as sf
     torch.cuda.set_device(local)
-    wl_ = Workload(local, small=args.small)
+    n_sm = sm_count_of(local)
+    wl_ = Workload(local, args.workload, small=args.small)
     for kv in args.ctx_opt:
         name, val = kv.split("=", 1)
         sf.sf_ctx_set_option(wl_.ctx, name, int(val))
@@ -764,6 +967,7 @@ def main():
     total_s = max_over_ranks(dist, total_s)
     value = replicas_value(ws, args.steps, total_s)
     # ---- end to end: host buffers through the C ABI, copies inside the timed region
+    e2e_steps = max(1, min(args.steps, 5))
     pin_in = torch.empty((wl_.k_in, 2, wl_.L, wl_.n), dtype=torch.int64, pin_memory=True)
     pin_in.copy_(wl_.d_in.cpu())
     pin_out = torch.empty((wl_.G, 2, wl_.L, wl_.n), dtype=torch.int64, pin_memory=True)
@@ -775,7 +979,7 @@ def main():
     if dist:
         dist.barrier()
     e2e_s = 0.0
-    for i in range(args.steps):
+    for i in range(e2e_steps):
         flush_l2(flush)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -783,13 +987,13 @@ def main():
                                      wl_.case.sigma_out, h_out, wl_.G, stream)
         e2e_s += time.perf_counter() - t0
     e2e_s = max_over_ranks(dist, e2e_s)
-    e2e_value = replicas_value(ws, args.steps, e2e_s)
+    e2e_value = replicas_value(ws, e2e_steps, e2e_s)
     h2d = wl_.k_in * wl_.ct_bytes + 4 * (wl_.info["E_in"] + wl_.info["E_out"])
     d2h = wl_.G * wl_.ct_bytes
     # ---- per-kernel device time (instrumented pass: events around every launch)
     sf.sf_kernel_stats_reset(wl_.ctx)
     sf.sf_ctx_set_option(wl_.ctx, "kernel_timing", 1)
-    k_steps = max(2, min(args.steps, 5))
+    k_steps = max(2, min(args.steps, 3))
     for _ in range(k_steps):
         flush_l2(flush)
         wl_.step()
@@ -799,23 +1003,37 @@ def main():
     total_kernel_ms = sum(ms for _, ms in kstats.values())
     p_info = sf.sf_params_get_info(wl_.params)
     probe = measure_probe(sf, wl_.ctx)
-    roofline = roofline_of(kstats, k_steps, RingShape(p_info), wl_.info, total_kernel_ms, clk, probe=probe)
+    roofline = roofline_of(kstats, k_steps, RingShape(p_info), wl_.info, total_kernel_ms, clk, probe=probe,
+                           sm_count=n_sm)
     ntt = ntt_record(sf, torch, wl_, p_info, probe, flush)
     kernel_table = {k: {"launches_per_layer": c // k_steps, "ms_per_layer": m / k_steps} for k, (c, m) in kstats.items() if c}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD if not args.small else "conv16-small (profiling case): " + WORKLOAD.replace(
-                "16x32x32 (E = E' = 16384)", "8x16x16 (E = E' = 2048)"), "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+            "config": {"workload": wl_.desc, "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "autotuned": tuned, "ctx_options": args.ctx_opt, "max_abs_err": err,
-                       "max_abs_err_final": err_final},
+                       "max_abs_err_final": err_final, "e2e_steps": e2e_steps},
             "clocks": clk, "gpu_launches": n_launch // 1, "step_ms": step_ms,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roofline, "ntt": ntt, "probe": probe, "kernels": kernel_table}
+    wl_.destroy()
+    torch.cuda.empty_cache()
     if rank == 0 and not args.no_cpu_baseline:
-        v, cores, desc = oracle_sample()
+        v, cores, desc = oracle_sample(args.workload if not args.small else args.workload)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0 and args.workload == "r34" and not args.no_extras and not args.small:
+        extras = {}
+        for name, fn in (("conv16", lambda: conv16_record(local)), ("serving", lambda: serving_record(local)),
+                         ("batched_vs_per_layer", lambda: batched_record(local))):
+            t0 = time.perf_counter()
+            try:
+                extras[name] = fn()
+            except Exception as exc:    # a sub-record must not lose the main line
+                extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            extras[name]["wall_s"] = time.perf_counter() - t0
+            torch.cuda.empty_cache()
+        line.update(extras)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

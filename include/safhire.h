@@ -51,11 +51,10 @@ typedef int32_t sf_status;
 #define SF_EINVAL 1   /* invalid argument: null pointer, size or index out of range, unknown key */
 #define SF_ENOMEM 2   /* host or device allocation failed, or a memory budget was exceeded */
 #define SF_ECUDA 3    /* a CUDA runtime call failed, or no usable device */
-#define SF_ETIMEOUT 4 /* a bounded device-side wait ran out (status word set by a kernel) */
-#define SF_ESTALE 5   /* serving: message for a stale or mismatched (session, round) */
-#define SF_ERANGE 6   /* a value does not fit the requested representation */
-#define SF_EBUSY 7    /* serving: admission refused (no slot or memory free) */
+#define SF_ERANGE 6   /* a value does not fit the requested representation, or (latched on the
+                         device, see sf_sync) an input residue is not below its modulus */
 #define SF_ENOTSUP 8  /* valid request that this build does not implement */
+/* (codes 4, 5 and 7 are not used) */
 
 /* Copies the calling thread's last error message into buf (always
  * NUL-terminated when len > 0) and returns the status that set it. */
@@ -139,7 +138,12 @@ sf_status sf_ctx_set_option(sf_ctx *ctx, const char *name, int64_t value);
 sf_status sf_ctx_get_option(const sf_ctx *ctx, const char *name, int64_t *value);
 
 /* Waits for `stream`, then reports (and clears) the context's device status
- * word: SF_OK, or the first error a kernel latched (SF_ETIMEOUT, SF_EINVAL). */
+ * word: SF_OK, or the first error a kernel latched since the last sf_sync.
+ * The one device-side check: sf_eval_linear_layer(_host), sf_eval_layers,
+ * sf_autotune_layers, sf_linear_outputs and sf_rotate read the caller's input
+ * ciphertexts once more to check that every residue is below its modulus;
+ * if one is not, SF_ERANGE is latched (the call itself returned SF_OK, and
+ * the outputs it wrote are unspecified). */
 sf_status sf_sync(sf_ctx *ctx, void *stream);
 
 /* Per-kernel counters since the last reset: for each kernel family, the
@@ -182,6 +186,14 @@ sf_status sf_rotkeys_export(sf_ctx *ctx, const sf_rotkeys *rk, int32_t d, uint64
 /* Fixed-point encoding of inputs: out[i] = round(scale * x[i]), half away
  * from zero.  Errors: SF_ERANGE if a result does not fit int64. */
 sf_status sf_encode_input(const double *x, int64_t count, double scale, int64_t *out);
+
+/* Client side, Sec. 4.3 "Power computations" at t = 2: for each of n_cts
+ * chunks of N integer message coefficients (h_msg: int64[n_cts][N]) writes
+ * m(X^d) mod X^N + 1 to h_out (same shape; d odd and positive, so every
+ * output coefficient is plus or minus one input coefficient).  d = 3 gives
+ * the power the client encrypts for gamma = 2.  Errors: SF_EINVAL (bad
+ * arguments, even d), SF_ERANGE (a coefficient equal to INT64_MIN). */
+sf_status sf_client_power(const sf_params *p, const int64_t *h_msg, int32_t n_cts, int32_t d, int64_t *h_out);
 
 /* Sec. 4.3 "Flatten and chunk" + Sec. 2.1: encrypts h_msg[0..count) (int64,
  * count <= n_cts * N, zero-padded) into n_cts ciphertexts at d_cts
@@ -268,6 +280,26 @@ sf_status sf_eval_linear_layer(sf_ctx *ctx, const sf_layer *layer, const sf_rotk
                                const uint32_t *h_sigma_out, uint64_t *d_out, int32_t out_capacity,
                                int32_t *n_out, void *stream);
 
+/* The same round at partial trace extraction level gamma (Sec. 4.3, 4.4,
+ * Lemma 1 at t = 2, where K_1 = K_0).  gamma 0 or 1: identical to
+ * sf_eval_linear_layer (d_powers must be NULL).  gamma 2: d_powers holds the
+ * client's powers, uint64[k_in][2][L][N], chunk j an encryption under the same
+ * secret of m_j(X^3) (sf_client_power with d = 3); the row of position
+ * p = jN + k is (N/2)^-1 (X^-k ct_j + X^-3k ct3_j), Lemma 1's sum over the
+ * automorphisms {1, 3} scaled by [K_2 : K_0] = 2, and the packing skips the
+ * tau_3 level: the bottom level of every tree merges E + X^(N/2) O with no key
+ * switch (the field trace starts at k = 2 when a group holds one value), so a
+ * group of n values costs n/2 - 1 + log2(N/n) key switches instead of
+ * n - 1 + log2(N/n).  The packed values (and the bias added there) carry the
+ * factor 2 = [K_2 : K_0]: the client halves them after decryption (output
+ * scale 2 S).  Leaves read 2 k_in ciphertexts, so the linear step costs twice
+ * its gamma = 0 work.  Errors: those of sf_eval_linear_layer, and SF_EINVAL for
+ * gamma outside [0, 2], missing powers at gamma = 2 or powers at gamma < 2. */
+sf_status sf_eval_linear_layer_gamma(sf_ctx *ctx, const sf_layer *layer, const sf_rotkeys *rk, int32_t gamma,
+                                     const uint64_t *d_in, const uint64_t *d_powers, int32_t k_in,
+                                     const uint32_t *h_sigma_prev, const uint32_t *h_sigma_out, uint64_t *d_out,
+                                     int32_t out_capacity, int32_t *n_out, void *stream);
+
 /* Same round with HOST buffers: copies h_in to the device, evaluates, and
  * copies the packed ciphertexts back to h_out (uint64[out_capacity][2][L][N]).
  * Synchronises `stream`.  Pinned host memory gives the fastest copies. */
@@ -333,10 +365,23 @@ sf_status sf_rotate(sf_ctx *ctx, const sf_rotkeys *rk, int32_t d, const uint64_t
 sf_status sf_pack(sf_ctx *ctx, const sf_rotkeys *rk, const uint64_t *d_leaves, int32_t n_leaves, int32_t n,
                   uint64_t *d_out, void *stream);
 
-/* Sec. 4.4 "Partial trace extraction" (Lemma 1) at gamma = 0 and t = 2: the
- * RLWE row for coefficient i is N^-1 X^-i ct (its trace is an encryption of
- * coefficient i).  gamma > 0 (client-supplied powers, d_powers) returns
- * SF_ENOTSUP.  d_ct, d_out: uint64[2][L][N]. */
+/* sf_pack at partial trace extraction level gamma (Sec. 4.4 "Fast Packing"):
+ * gamma 0 and 1 are sf_pack; gamma 2 expects leaves that encrypt
+ * y + tau_3(y) (rows extracted at gamma = 2) and merges the tau_3 level with
+ * no key switch (n/2 fewer key switches, one fewer when n = 1); coefficient
+ * l*N/n of the result then holds N times coefficient 0 of y_l.
+ * Errors: those of sf_pack, SF_EINVAL for gamma outside [0, 2]. */
+sf_status sf_pack_gamma(sf_ctx *ctx, const sf_rotkeys *rk, const uint64_t *d_leaves, int32_t n_leaves, int32_t n,
+                        int32_t gamma, uint64_t *d_out, void *stream);
+
+/* Sec. 4.4 "Partial trace extraction" (Lemma 1) at t = 2: the RLWE row for
+ * coefficient i.  gamma 0 (and 1, identical at t = 2): N^-1 X^-i ct, whose
+ * trace is an encryption of coefficient i.  gamma 2: (N/2)^-1 (X^-i ct +
+ * X^-3i ct3) with d_powers = ct3 an encryption of m(X^3) (Lemma 1's sum
+ * scaled by [K_2 : K_0] = 2; its trace over K / K_2, sf_pack_gamma with
+ * gamma = 2, holds 2 times coefficient i).  d_ct, d_powers, d_out:
+ * uint64[2][L][N], coefficient domain.  Errors: SF_EINVAL (gamma outside
+ * [0, 2], i out of range, missing power at gamma = 2). */
 sf_status sf_extract(sf_ctx *ctx, const uint64_t *d_ct, int32_t i, int32_t gamma, const uint64_t *d_powers,
                      uint64_t *d_out, void *stream);
 
@@ -360,9 +405,12 @@ sf_status sf_shuffle_cts(sf_ctx *ctx, const uint32_t *h_perm, const uint64_t *d_
  * into the library, reserved on every GPU that loads the library and held
  * until the process exits.  The paper has no counterpart; this is an
  * integration variant only.
- *  - Limit: 2 * count ciphertexts plus count key-switch workspaces must fit in
- *    32 MiB (up to 5 ciphertexts at N = 2^14 with 3 data + 1 special primes);
- *    larger requests fail with SF_EINVAL and a message giving the sizes.
+ *  - Limit: 2 * count ciphertexts plus min(count, ks_batch) key-switch
+ *    workspaces (ks_batch: the context option, as in sf_rotate) must fit in
+ *    32 MiB: up to 7 ciphertexts at N = 2^14 with 3 data + 1 special primes
+ *    (768 KiB each, 3 MiB of workspace per key switch) at the default
+ *    ks_batch; larger requests fail with SF_EINVAL and a message giving the
+ *    sizes, before anything is enqueued.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture on the device.

@@ -12,7 +12,8 @@ below, which follow the paper's algorithms step by step:
 * Sec. 2.3   trace, evaluated as a tower of automorphism-and-add steps
 * Sec. 2.4   packing: PackLWEs tree, then the field trace that zeroes all
              non-packed coefficients
-* Sec. 4.4   server round: extraction (gamma = 0), unshuffle, linear layer,
+* Sec. 4.4   server round: extraction (gamma = 0, and gamma = 2 from the
+             client's power m(X^3), Lemma 1 at t = 2), unshuffle, linear layer,
              shuffle, fast packing
 
 Parity status of every function: pinned by tests/test_oracle_pins.py (see the
@@ -405,36 +406,51 @@ def zero_ct(prm: Params) -> np.ndarray:
 # packing (Sec. 2.4; Sec. 4.4 "Fast Packing") at t = 2
 # ---------------------------------------------------------------------------
 
-def pack_tree(prm: Params, keys: dict, leaves: list, counter: Counter | None = None) -> np.ndarray:
+def pack_tree(prm: Params, keys: dict, leaves: list, counter: Counter | None = None,
+              gamma: int = 0) -> np.ndarray:
     """PackLWEs recursion on n = 2^k ciphertexts:
         Pack(ct_0..ct_{n-1}) = (E + X^{N/n} O) + tau_{n+1}(E - X^{N/n} O)
     with E = Pack(even-indexed), O = Pack(odd-indexed), tau followed by key
-    switching.  Coefficient 0 of leaf l ends, times n, at X^{l N/n}."""
+    switching.  Coefficient 0 of leaf l ends, times n, at X^{l N/n}.
+
+    gamma = 2 (Sec. 4.4, Lemma 1 at t = 2): each leaf already encrypts
+    y + tau_3(y), its image under the partial trace over K_2 / K_0 (the
+    automorphisms {1, 3}).  The merge of two leaves is then
+    (E + tau_3 E) + X^{N/2} (O + tau_3 O) = E' + X^{N/2} O' with no key
+    switch: the level whose automorphism tau_3 the client has applied."""
     n = len(leaves)
     assert n >= 1 and (n & (n - 1)) == 0
     if n == 1:
         return _u64(leaves[0]).reshape(2, prm.L, prm.n)
-    E = pack_tree(prm, keys, leaves[0::2], counter)
-    O = pack_tree(prm, keys, leaves[1::2], counter)
+    E = pack_tree(prm, keys, leaves[0::2], counter, gamma)
+    O = pack_tree(prm, keys, leaves[1::2], counter, gamma)
     XO = ct_monomial(prm, O, prm.n // n)
+    if gamma == 2 and n == 2:
+        return ct_add(prm, E, XO)
     return ct_add(prm, ct_add(prm, E, XO), rotate(prm, keys, n + 1, ct_sub(prm, E, XO), counter))
 
 
-def field_trace(prm: Params, keys: dict, ct: np.ndarray, n: int, counter: Counter | None = None) -> np.ndarray:
+def field_trace(prm: Params, keys: dict, ct: np.ndarray, n: int, counter: Counter | None = None,
+                gamma: int = 0) -> np.ndarray:
     """The remaining trace levels after packing n values (Sec. 2.3, 2.4):
     for k = log2(n)+1 .. log2(N):  ct <- ct + tau_{2^k+1}(ct).  Zeroes every
-    coefficient outside the stride-N/n lattice and multiplies the rest by N/n."""
+    coefficient outside the stride-N/n lattice and multiplies the rest by N/n.
+    gamma = 2 with a single value (n = 1) starts at k = 2: the client's
+    partial trace supplied the tau_3 step (Tr over K_2 / K_1)."""
     k0 = int(math.log2(n))
-    for k in range(k0 + 1, prm.log_n + 1):
+    start = max(k0 + 1, 2) if gamma == 2 else k0 + 1
+    for k in range(start, prm.log_n + 1):
         ct = ct_add(prm, ct, rotate(prm, keys, (1 << k) + 1, ct, counter))
     return ct
 
 
 def pack(prm: Params, keys: dict, leaves: list, counter: Counter | None = None,
-         n: int | None = None) -> np.ndarray:
+         n: int | None = None, gamma: int = 0) -> np.ndarray:
     """Fast packing of len(leaves) <= n <= N/2 ciphertexts, zero-padded to n
     (default: the next power of two): output coefficient l*N/n holds
-    N * (coefficient 0 of leaf l)."""
+    N * (coefficient 0 of leaf l) at gamma = 0, and N * (coefficient 0 of y_l)
+    at gamma = 2 when leaf l encrypts y_l + tau_3(y_l)."""
+    assert gamma in (0, 2)
     m = len(leaves)
     if n is None:
         n = 1
@@ -443,7 +459,7 @@ def pack(prm: Params, keys: dict, leaves: list, counter: Counter | None = None,
     assert m <= n and (n & (n - 1)) == 0
     assert n <= prm.n // 2, "at t = 2 a ciphertext packs at most N/2 values (beta <= alpha - 1)"
     leaves = list(leaves) + [zero_ct(prm)] * (n - m)
-    return field_trace(prm, keys, pack_tree(prm, keys, leaves, counter), n, counter)
+    return field_trace(prm, keys, pack_tree(prm, keys, leaves, counter, gamma), n, counter, gamma)
 
 
 def group_size(prm: Params, e_out: int) -> int:
@@ -454,12 +470,16 @@ def group_size(prm: Params, e_out: int) -> int:
     return min(prm.n // 2, n)
 
 
-def ks_count(prm: Params, e_out: int) -> int:
+def ks_count(prm: Params, e_out: int, gamma: int = 0) -> int:
     """Key switches for one layer round: per group (n - 1) tree merges plus
-    log2(N/n) trace steps."""
+    log2(N/n) trace steps; at gamma = 2 the tau_3 level costs none (n/2 merges
+    of the bottom level, or the first trace step when n = 1)."""
     n = group_size(prm, e_out)
     groups = -(-e_out // n)
-    return groups * ((n - 1) + (prm.log_n - int(math.log2(n))))
+    per = (n - 1) + (prm.log_n - int(math.log2(n)))
+    if gamma == 2:
+        per -= n // 2 if n >= 2 else 1
+    return groups * per
 
 
 def ks_per_coefficient_general(t: int, alpha: int, gamma: int) -> float:
@@ -597,10 +617,55 @@ def inverse_perm(perm) -> np.ndarray:
     return inv
 
 
-def linear_output(prm: Params, layer: Layer, cts: np.ndarray, o: int, sigma_prev=None) -> np.ndarray:
+def extract(prm: Params, ct: np.ndarray, i: int, gamma: int = 0, power=None) -> np.ndarray:
+    """Lemma 1 (Sec. 4.4 "Partial trace extraction") at t = 2: the RLWE row
+    whose partial trace over K_gamma / K_0 holds coefficient i, with
+    Omega_i^*-bar(X^d) = X^(-d i) / N.  gamma 0 (and 1, the same at t = 2
+    since K_1 = K_0): N^-1 X^-i ct, and the full trace (degree N) returns
+    m_i.  gamma 2: (N/2)^-1 (X^-i ct + X^-3i ct3), ct3 = RLWE_s(m(X^3)) the
+    client's power (Sec. 4.3, j = 1, k in {0, 1}): Lemma 1's sum scaled by
+    [K_2 : K_0] = 2, so that the server's trace over K / K_2 (degree N/2)
+    cancels the scalar exactly and the packed value is 2 m_i, which the
+    client halves after decryption (the paper removes this factor with
+    M^-1 mod p in its torus encoding, which a fixed-point encoding cannot
+    do without multiplying the fresh noise of ct3 by 2^-1 mod Q)."""
+    inv = (lambda qi: pow(prm.n, -1, qi)) if gamma == 0 else (lambda qi: pow(prm.n // 2, -1, qi))
+
+    def term(c, e):
+        c = ct_monomial(prm, c, -e)
+        for li, qi in enumerate(prm.q):
+            c[:, li] = np.array([int(v) * inv(qi) % qi for v in c[:, li].ravel()],
+                                dtype=np.uint64).reshape(c[:, li].shape)
+        return c
+    row = term(_u64(ct).reshape(2, prm.L, prm.n), i)
+    if gamma == 2:
+        row = ct_add(prm, row, term(_u64(power).reshape(2, prm.L, prm.n), 3 * i))
+    return row
+
+
+def client_power(prm: Params, m) -> np.ndarray:
+    """The client's power for gamma = 2 at t = 2 (Sec. 4.3): m(X^3) of one
+    chunk of N integer message coefficients, as integers."""
+    m = np.asarray(m, dtype=np.int64)
+    out = np.zeros(prm.n, dtype=object)
+    for k, v in enumerate(m):
+        e = 3 * k % (2 * prm.n)
+        if e < prm.n:
+            out[e] += int(v)
+        else:
+            out[e - prm.n] -= int(v)
+    return np.array([int(v) for v in out], dtype=np.int64)
+
+
+def linear_output(prm: Params, layer: Layer, cts: np.ndarray, o: int, sigma_prev=None,
+                  powers: np.ndarray | None = None) -> np.ndarray:
     """RLWE row of output o before shuffling and packing:
     y_o = sum_i W[o,i] * (extracted row of input i), where input i sits at
-    stream position sigma_prev^-1(i) (Sec. 4.4 "Unshuffle")."""
+    stream position sigma_prev^-1(i) (Sec. 4.4 "Unshuffle").  With the
+    client's powers (gamma = 2, one per input ciphertext) the extracted row
+    is (N/2)^-1 (X^-k ct_j + X^(-3k) ct3_j) (see extract): the taps count
+    twice (weights 2 Wq against N^-1) and again at exponent 3k on ct3_j,
+    where X^-e = -X^-(e - N) for N <= e < 2N."""
     cts = _u64(cts).reshape(-1, 2, prm.L, prm.n)
     idx, wts = output_taps(layer, o)
     if sigma_prev is None:
@@ -608,11 +673,20 @@ def linear_output(prm: Params, layer: Layer, cts: np.ndarray, o: int, sigma_prev
     else:
         pos = inverse_perm(sigma_prev)[idx]
     pos = _i64(pos)
-    wts = _i64(wts)
+    wts = _i64(wts if powers is None else 2 * wts)
     q = _u64(prm.q)
     out = np.zeros((2, prm.L, prm.n), dtype=np.uint64)
     lib().or_linear_output(prm.n, prm.L, _p(q, _u64p), cts.shape[0], _p(cts, _u64p), pos.size,
                            _p(pos, _i64p), _p(wts, _i64p), _p(out, _u64p))
+    if powers is not None:
+        pw = _u64(powers).reshape(-1, 2, prm.L, prm.n)
+        e = 3 * (pos % prm.n) % (2 * prm.n)
+        pos3 = _i64((pos // prm.n) * prm.n + np.where(e < prm.n, e, e - prm.n))
+        w3 = _i64(np.where(e < prm.n, wts, -wts))
+        out3 = np.zeros_like(out)
+        lib().or_linear_output(prm.n, prm.L, _p(q, _u64p), pw.shape[0], _p(pw, _u64p), pos3.size,
+                               _p(pos3, _i64p), _p(w3, _i64p), _p(out3, _u64p))
+        out = ct_add(prm, out, out3)
     return out
 
 
@@ -626,11 +700,14 @@ def add_bias(prm: Params, ct: np.ndarray, values, stride: int) -> np.ndarray:
 
 
 def eval_linear_layer(prm: Params, layer: Layer, keys: dict, cts: np.ndarray,
-                      sigma_prev=None, sigma_out=None, counter: Counter | None = None) -> np.ndarray:
+                      sigma_prev=None, sigma_out=None, counter: Counter | None = None,
+                      powers: np.ndarray | None = None) -> np.ndarray:
     """One server round (Sec. 4.4): for every output group g (n values per
     packed ciphertext, the same n for every group; the last group is padded
     with zero ciphertexts), leaf l = y_{sigma_out(g n + l)}, pack, add bias.
-    Returns [groups][2][L][N]."""
+    With the client's powers (gamma = 2) the leaves use them and the packing
+    skips the tau_3 level.  Returns [groups][2][L][N]."""
+    gamma = 0 if powers is None else 2
     e_out = layer.E_out
     n = group_size(prm, e_out)
     groups = -(-e_out // n)
@@ -638,8 +715,8 @@ def eval_linear_layer(prm: Params, layer: Layer, keys: dict, cts: np.ndarray,
     out = []
     for g in range(groups):
         members = [int(perm[g * n + l]) for l in range(min(n, e_out - g * n))]
-        leaves = [linear_output(prm, layer, cts, o, sigma_prev) for o in members]
-        ct = pack(prm, keys, leaves, counter, n=n)
+        leaves = [linear_output(prm, layer, cts, o, sigma_prev, powers) for o in members]
+        ct = pack(prm, keys, leaves, counter, n=n, gamma=gamma)
         if layer.bias_q is not None:
             co = np.array(members) % layer.C_out
             ct = add_bias(prm, ct, [int(layer.bias_q[c]) for c in co], prm.n // n)
@@ -647,9 +724,12 @@ def eval_linear_layer(prm: Params, layer: Layer, keys: dict, cts: np.ndarray,
     return np.stack(out)
 
 
-def read_outputs(prm: Params, layer: Layer, residues: np.ndarray, scale: float) -> np.ndarray:
+def read_outputs(prm: Params, layer: Layer, residues: np.ndarray, scale: float, gamma: int = 0) -> np.ndarray:
     """Client side (Sec. 4.5): read the packed positions l*N/n of each group
-    and drop the padding; the result is in shuffled order sigma_out."""
+    and drop the padding; the result is in shuffled order sigma_out.  At
+    gamma = 2 the packed values carry the factor [K_2 : K_0] = 2 (see extract)."""
+    if gamma == 2:
+        scale = 2 * scale
     e_out = layer.E_out
     n = group_size(prm, e_out)
     stride = prm.n // n

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import build as _build
 
-SF_OK, SF_EINVAL, SF_ENOMEM, SF_ECUDA, SF_ETIMEOUT, SF_ESTALE, SF_ERANGE, SF_EBUSY, SF_ENOTSUP = range(9)
+SF_OK, SF_EINVAL, SF_ENOMEM, SF_ECUDA, SF_ERANGE, SF_ENOTSUP = 0, 1, 2, 3, 6, 8
 SF_MAX_MODULI = 12
 
 
@@ -72,6 +72,7 @@ _SIGS = {
     "sf_rotkeys_destroy": (None, [_vp]),
     "sf_rotkeys_export": (_i32, [_vp, _vp, _i32, _vp]),
     "sf_encode_input": (_i32, [_vp, _i64, _dbl, _vp]),
+    "sf_client_power": (_i32, [_vp, _vp, _i32, _i32, _vp]),
     "sf_encrypt": (_i32, [_vp, _vp, _vp, _i64, _u64, _vp, _i32, _vp]),
     "sf_decrypt": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp]),
     "sf_decode": (_i32, [_vp, _vp, _i32, _i32, _i32, _dbl, _vp]),
@@ -79,6 +80,8 @@ _SIGS = {
     "sf_layer_destroy": (None, [_vp]),
     "sf_layer_get_info": (_i32, [_vp, _vp, ctypes.POINTER(sf_layer_info)]),
     "sf_eval_linear_layer": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _i32, ctypes.POINTER(_i32), _vp]),
+    "sf_eval_linear_layer_gamma": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _i32,
+                                          ctypes.POINTER(_i32), _vp]),
     "sf_eval_linear_layer_host": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _i32, ctypes.POINTER(_i32), _vp]),
     "sf_linear_outputs": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp]),
     "sf_eval_layers": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -87,6 +90,7 @@ _SIGS = {
     "sf_rotate": (_i32, [_vp, _vp, _i32, _vp, _vp, _i32, _vp]),
     "sf_rotate_noalloc": (_i32, [_vp, _vp, _i32, _vp, _vp, _i32, _vp]),
     "sf_pack": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp]),
+    "sf_pack_gamma": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "sf_extract": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp]),
     "sf_permutation": (_i32, [_u64, _u32, _u32, _vp]),
     "sf_shuffle_cts": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
@@ -255,6 +259,17 @@ def sf_encode_input(x, scale: float) -> np.ndarray:
     return out
 
 
+def sf_client_power(params, msg, n_cts: int, d: int = 3) -> np.ndarray:
+    """m(X^d) of each of n_cts chunks of N integer coefficients (Sec. 4.3)."""
+    n = sf_params_get_info(params)["n"]
+    m = np.zeros(n_cts * n, dtype=np.int64)
+    v = np.ascontiguousarray(msg, dtype=np.int64).ravel()
+    m[:v.size] = v
+    out = np.zeros_like(m)
+    _check(lib().sf_client_power(params, _ptr(m), n_cts, d, _ptr(out)))
+    return out
+
+
 def sf_encrypt(ctx, sk, msg, seed: int, d_cts, n_cts: int, stream=None):
     msg = np.ascontiguousarray(msg, dtype=np.int64).ravel()
     _check(lib().sf_encrypt(ctx, sk, _ptr(msg) if msg.size else None, msg.size, seed, _ptr(d_cts), n_cts,
@@ -316,6 +331,15 @@ def sf_eval_linear_layer(ctx, layer, rk, d_in, k_in: int, sigma_prev, sigma_out,
     n_out = ctypes.c_int32()
     _check(lib().sf_eval_linear_layer(ctx, layer, rk, _ptr(d_in), k_in, _ptr(sp), _ptr(so), _ptr(d_out),
                                       out_capacity, ctypes.byref(n_out), _stream(stream)))
+    return n_out.value
+
+
+def sf_eval_linear_layer_gamma(ctx, layer, rk, gamma: int, d_in, d_powers, k_in: int, sigma_prev, sigma_out, d_out,
+                               out_capacity: int, stream=None) -> int:
+    sp, so = _perm(sigma_prev), _perm(sigma_out)
+    n_out = ctypes.c_int32()
+    _check(lib().sf_eval_linear_layer_gamma(ctx, layer, rk, gamma, _ptr(d_in), _ptr(d_powers), k_in, _ptr(sp),
+                                            _ptr(so), _ptr(d_out), out_capacity, ctypes.byref(n_out), _stream(stream)))
     return n_out.value
 
 
@@ -386,6 +410,10 @@ def sf_rotate_noalloc(ctx, rk, d: int, d_ct, d_out, count: int, stream=None):
 
 def sf_pack(ctx, rk, d_leaves, n_leaves: int, n: int, d_out, stream=None):
     _check(lib().sf_pack(ctx, rk, _ptr(d_leaves), n_leaves, n, _ptr(d_out), _stream(stream)))
+
+
+def sf_pack_gamma(ctx, rk, d_leaves, n_leaves: int, n: int, gamma: int, d_out, stream=None):
+    _check(lib().sf_pack_gamma(ctx, rk, _ptr(d_leaves), n_leaves, n, gamma, _ptr(d_out), _stream(stream)))
 
 
 def sf_extract(ctx, d_ct, i: int, gamma: int, d_powers, d_out, stream=None):

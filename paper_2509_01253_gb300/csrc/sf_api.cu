@@ -438,7 +438,7 @@ extern "C" sf_status sf_linear_outputs(sf_ctx *ctx, const sf_layer *L, const uin
     std::vector<int> h_pos, h_sig(h_outputs, h_outputs + n_outputs);
     if (h_sigma_prev) SF_TRY(upload_perm_inverse(h_sigma_prev, L->E_in, d_pos, h_pos, st));
     SF_CUDA_TRY(cudaMemcpyAsync(d_sig, h_sig.data(), sizeof(int) * n_outputs, cudaMemcpyHostToDevice, st));
-    SF_TRY(prepare_inputs(ctx, d_in, k_in, ws + o_ct, st));
+    SF_TRY(prepare_inputs(ctx, d_in, nullptr, k_in, ws + o_ct, st));
     SfLeafParams P = leaf_params(L);
     P.k_in = k_in;
     P.pos_of = h_sigma_prev ? d_pos : nullptr;
@@ -482,6 +482,7 @@ extern "C" sf_status sf_rotate(sf_ctx *ctx, const sf_rotkeys *rk, int32_t d, con
     void *w = nullptr;
     SF_TRY(sf_scratch(ctx, cv.words * sizeof(u64), &w));
     u64 *ws = (u64 *)w;
+    SF_TRY(sf_check_residues(ctx, d_ct, count * 2 * R.L, R.L, 0, st));
     std::vector<SfPolyJob> jobs;
     for (int x = 0; x < count * 2 * R.L; ++x) jobs.push_back({d_ct + (size_t)x * R.n, ws + o_in + (size_t)x * R.n, x % R.L});
     SF_TRY(sf_ntt_jobs(ctx, jobs.data(), (int)jobs.size(), false, st));
@@ -502,10 +503,11 @@ extern "C" sf_status sf_rotate(sf_ctx *ctx, const sf_rotkeys *rk, int32_t d, con
     return SF_OK;
 }
 
-extern "C" sf_status sf_pack(sf_ctx *ctx, const sf_rotkeys *rk, const uint64_t *d_leaves, int32_t n_leaves, int32_t n,
-                             uint64_t *d_out, void *stream)
+static sf_status pack_impl(sf_ctx *ctx, const sf_rotkeys *rk, const uint64_t *d_leaves, int32_t n_leaves, int32_t n,
+                           int32_t gamma, uint64_t *d_out, void *stream)
 {
     SF_CHECK_CTX(ctx);
+    if (gamma < 0 || gamma > 2) return sf_set_error(SF_EINVAL, "sf_pack_gamma: gamma must be 0, 1 or 2");
     const SfRing &R = ctx->ring;
     if (!rk || rk->ctx != ctx || !d_leaves || !d_out || n_leaves < 1 || n < n_leaves || n > R.n / 2 || (n & (n - 1)))
         return sf_set_error(SF_EINVAL, "sf_pack: need 1 <= n_leaves <= n <= N/2, n a power of two");
@@ -526,20 +528,36 @@ extern "C" sf_status sf_pack(sf_ctx *ctx, const sf_rotkeys *rk, const uint64_t *
     u64 *res = nullptr;
     size_t rs = 0;
     SF_TRY(sf_pack_tree(ctx, rk->d_keys, rk->d, rk->key_words, ws + o_A, ws + o_B, 1, n, 0, valid, true, ws + o_ks, batch,
-                        &res, &rs, st));
+                        &res, &rs, st, gamma == 2));
     jobs.clear();
     for (int x = 0; x < 2 * R.L; ++x) jobs.push_back({res + (size_t)x * R.n, d_out + (size_t)x * R.n, x % R.L});
     SF_TRY(sf_ntt_jobs(ctx, jobs.data(), (int)jobs.size(), true, st));
     return SF_OK;
 }
 
+extern "C" sf_status sf_pack(sf_ctx *ctx, const sf_rotkeys *rk, const uint64_t *d_leaves, int32_t n_leaves, int32_t n,
+                             uint64_t *d_out, void *stream)
+{
+    return pack_impl(ctx, rk, d_leaves, n_leaves, n, 0, d_out, stream);
+}
+
+extern "C" sf_status sf_pack_gamma(sf_ctx *ctx, const sf_rotkeys *rk, const uint64_t *d_leaves, int32_t n_leaves,
+                                   int32_t n, int32_t gamma, uint64_t *d_out, void *stream)
+{
+    return pack_impl(ctx, rk, d_leaves, n_leaves, n, gamma, d_out, stream);
+}
+
 extern "C" sf_status sf_extract(sf_ctx *ctx, const uint64_t *d_ct, int32_t i, int32_t gamma, const uint64_t *d_powers,
                                 uint64_t *d_out, void *stream)
 {
     SF_CHECK_CTX(ctx);
-    (void)d_powers;
-    if (gamma != 0) return sf_set_error(SF_ENOTSUP, "partial trace extraction with gamma > 0 is not implemented");
+    if (gamma < 0 || gamma > 2) return sf_set_error(SF_EINVAL, "sf_extract: gamma must be 0, 1 or 2");
     if (!d_ct || !d_out || i < 0 || i >= ctx->ring.n) return sf_set_error(SF_EINVAL, "sf_extract: bad arguments");
+    if (gamma == 2) {
+        if (!d_powers) return sf_set_error(SF_EINVAL, "sf_extract: gamma = 2 needs the client's power");
+        return sf_extract2_launch(ctx, d_ct, d_powers, d_out, i, (cudaStream_t)stream);
+    }
+    // gamma = 1 equals gamma = 0 at t = 2 (K_1 = K_0: the power m(X^1) is m itself)
     return sf_extract_launch(ctx, d_ct, d_out, i, (cudaStream_t)stream);
 }
 

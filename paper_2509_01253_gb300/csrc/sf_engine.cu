@@ -39,6 +39,10 @@ struct Job {
     // workspace
     u64 *d_ct;
     int *d_pos, *d_sig;
+    // gamma = 2: the client's powers RLWE(m_j(X^3)), [k_in][2][L][N] (null at gamma = 0)
+    const u64 *d_pow;
+    int k_leaf() const { return d_pow ? 2 * k_in : k_in; }
+    int taps() const { return d_pow ? 2 * L->max_taps : L->max_taps; }
 };
 
 struct Unit {
@@ -47,6 +51,7 @@ struct Unit {
 
 struct Class {
     const sf_rotkeys *rk;
+    bool gamma2;
     int n, CH, nch, log_ch;
     std::vector<Unit> units;           // ordered (job, group, a)
     std::vector<std::pair<int, int>> groups;   // (job, g) in unit order
@@ -72,8 +77,8 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
     const size_t ct = ct_words(ctx), ct_bytes = ct * sizeof(u64);
     int max_k_in = 1, max_taps = 1;
     for (auto &j : jobs) {
-        max_k_in = std::max(max_k_in, j.k_in);
-        max_taps = std::max(max_taps, j.L->max_taps);
+        max_k_in = std::max(max_k_in, j.k_leaf());
+        max_taps = std::max(max_taps, j.taps());
     }
     const int LB = leaf_batch_slots(R, max_k_in, max_taps);
     // ---- classes and units
@@ -81,13 +86,15 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
     for (int x = 0; x < (int)jobs.size(); ++x) {
         Job &j = jobs[x];
         Class *c = nullptr;
+        // a class shares its tree levels, so it holds rounds of one gamma only
         for (auto &cc : classes)
-            if (cc.rk == j.rk && cc.n == j.n) c = &cc;
+            if (cc.rk == j.rk && cc.n == j.n && cc.gamma2 == (j.d_pow != nullptr)) c = &cc;
         if (!c) {
             classes.push_back(Class());
             c = &classes.back();
             c->rk = j.rk;
             c->n = j.n;
+            c->gamma2 = j.d_pow != nullptr;
             // CH: largest power of two <= n such that 16 units of CH leaves
             // (plus their tree buffer) fit the budget, or the leaf_chunk cap
             int ch = j.n;
@@ -110,7 +117,7 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
     Carver cv;
     std::vector<size_t> o_ct(jobs.size()), o_pos(jobs.size()), o_sig(jobs.size());
     for (size_t x = 0; x < jobs.size(); ++x) {
-        o_ct[x] = cv.take((size_t)2 * jobs[x].k_in * ct);
+        o_ct[x] = cv.take((size_t)2 * jobs[x].k_leaf() * ct);
         o_pos[x] = cv.take(((size_t)jobs[x].L->E_in + 1) / 2);
         o_sig[x] = cv.take(((size_t)jobs[x].L->E_out + 1) / 2);
     }
@@ -163,10 +170,13 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
     u64 *A = ws + o_A, *B = ws + o_B, *d_w1 = ws + o_w1, *d_ks = ws + o_ks;
 
     auto launch_all = [&](cudaStream_t s) -> sf_status {
-        for (auto &j : jobs) SF_TRY(prepare_inputs(ctx, j.d_in, j.k_in, j.d_ct, s));
+        for (auto &j : jobs) SF_TRY(prepare_inputs(ctx, j.d_in, j.d_pow, j.k_in, j.d_ct, s));
         auto leaves = [&](const Job &j, int s0, int stride, int cnt, u64 *dst) -> sf_status {
             SfLeafParams P = leaf_params(j.L);
-            P.k_in = j.k_in;
+            P.k_in = j.k_leaf();
+            P.k_src = j.k_in;
+            P.gamma2 = j.d_pow != nullptr;
+            P.max_taps = j.taps();
             P.pos_of = j.sp ? j.d_pos : nullptr;
             P.sig_out = j.so ? j.d_sig : nullptr;
             P.ct = j.d_ct;
@@ -204,7 +214,7 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
                 u64 *res = nullptr;
                 size_t rs = 0;
                 SF_TRY(sf_pack_tree(ctx, c.rk->d_keys, kd, c.rk->key_words, A, B, wn, c.CH, 0, valid, c.nch == 1, d_ks,
-                                    batch, &res, &rs, s));
+                                    batch, &res, &rs, s, c.gamma2));
                 if (c.nch == 1) {
                     for (int u = 0; u < wn; ++u) {
                         const Unit &un = c.units[u0 + u];
@@ -226,14 +236,15 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
                 u64 *res = nullptr;
                 size_t rs = 0;
                 SF_TRY(sf_pack_tree(ctx, c.rk->d_keys, kd, c.rk->key_words, RA, RB, (int)c.groups.size(), c.nch, c.log_ch,
-                                    valid, true, d_ks, batch, &res, &rs, s));
+                                    valid, true, d_ks, batch, &res, &rs, s, c.gamma2));
                 for (size_t gi = 0; gi < c.groups.size(); ++gi)
                     SF_TRY(output(res + rs * gi, jobs[c.groups[gi].first], c.groups[gi].second));
             }
         }
         for (auto &j : jobs)
             if (j.L->d_bq)
-                SF_TRY(sf_add_bias(ctx, j.d_out, j.G, j.n, j.L->E_out, j.so ? j.d_sig : nullptr, j.L->d_bq, j.L->C_out, s));
+                SF_TRY(sf_add_bias(ctx, j.d_out, j.G, j.n, j.L->E_out, j.so ? j.d_sig : nullptr, j.L->d_bq, j.L->C_out, s,
+                                   j.d_pow ? 2 : 1));
         return SF_OK;
     };
 
@@ -248,6 +259,7 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
             h = fnv(h, (uint64_t)(uintptr_t)j.d_out);
             h = fnv(h, (uint64_t)j.k_in);
             h = fnv(h, (uint64_t)(j.sp != nullptr) * 2 + (j.so != nullptr));
+            h = fnv(h, (uint64_t)(uintptr_t)j.d_pow);
         }
         for (auto &c : classes) {
             h = fnv(h, (uint64_t)c.CH);
@@ -314,7 +326,26 @@ static sf_status make_job(sf_ctx *ctx, const sf_layer *L, const sf_rotkeys *rk, 
     if (out_capacity < G) return sf_set_error(SF_EINVAL, "output capacity %d < %d packed ciphertexts", out_capacity, G);
     if (sp) SF_TRY(check_perm(sp, L->E_in, "sigma_prev"));
     if (so) SF_TRY(check_perm(so, L->E_out, "sigma_out"));
-    *j = Job{L, rk, d_in, k_in, sp, so, d_out, n, G, nullptr, nullptr, nullptr};
+    *j = Job{L, rk, d_in, k_in, sp, so, d_out, n, G, nullptr, nullptr, nullptr, nullptr};
+    return SF_OK;
+}
+
+extern "C" sf_status sf_eval_linear_layer_gamma(sf_ctx *ctx, const sf_layer *L, const sf_rotkeys *rk, int32_t gamma,
+                                                const uint64_t *d_in, const uint64_t *d_powers, int32_t k_in,
+                                                const uint32_t *h_sigma_prev, const uint32_t *h_sigma_out,
+                                                uint64_t *d_out, int32_t out_capacity, int32_t *n_out, void *stream)
+{
+    SF_CHECK_CTX(ctx);
+    if (gamma < 0 || gamma > 2) return sf_set_error(SF_EINVAL, "gamma must be 0, 1 or 2");
+    if (gamma == 2 && !d_powers) return sf_set_error(SF_EINVAL, "gamma = 2 needs the client's powers");
+    if (gamma < 2 && d_powers) return sf_set_error(SF_EINVAL, "powers are only read at gamma = 2");
+    std::vector<Job> jobs(1);
+    SF_TRY(make_job(ctx, L, rk, d_in, k_in, h_sigma_prev, h_sigma_out, d_out, out_capacity, &jobs[0]));
+    if (gamma == 2 && 2 * k_in * (ctx->ring.c / SF_NB) > 4096)
+        return sf_set_error(SF_EINVAL, "too many input ciphertexts for one round at gamma = 2");
+    jobs[0].d_pow = gamma == 2 ? d_powers : nullptr;
+    SF_TRY(eval_jobs(ctx, jobs, (cudaStream_t)stream));
+    if (n_out) *n_out = jobs[0].G;
     return SF_OK;
 }
 

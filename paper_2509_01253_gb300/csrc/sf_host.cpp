@@ -162,6 +162,27 @@ extern "C" sf_status sf_encode_input(const double *x, int64_t count, double scal
     return SF_OK;
 }
 
+// Sec. 4.3 "Power computations" at t = 2: m(X^d) of each N-coefficient chunk.
+// For odd d, X^k -> X^(k d mod 2N) folded by X^N = -1 is a signed permutation
+// of the coefficients, so every output is plus or minus one input.
+extern "C" sf_status sf_client_power(const sf_params *p, const int64_t *h_msg, int32_t n_cts, int32_t d, int64_t *h_out)
+{
+    if (!p || !h_msg || !h_out || n_cts < 1) return sf_set_error(SF_EINVAL, "sf_client_power: bad arguments");
+    if (d <= 0 || (d & 1) == 0) return sf_set_error(SF_EINVAL, "sf_client_power: d must be odd and positive");
+    const int64_t n = p->n, two_n = 2 * n, dd = d % two_n;
+    for (int32_t c = 0; c < n_cts; ++c) {
+        const int64_t *m = h_msg + (size_t)c * n;
+        int64_t *o = h_out + (size_t)c * n;
+        for (int64_t k = 0; k < n; ++k) {
+            if (m[k] == INT64_MIN) return sf_set_error(SF_ERANGE, "sf_client_power: coefficient out of range");
+            const int64_t e = k * dd % two_n;
+            if (e < n) o[e] = m[k];
+            else o[e - n] = -m[k];
+        }
+    }
+    return SF_OK;
+}
+
 // ---------------------------------------------------------------- params ----
 
 extern "C" sf_status sf_params_create(int32_t log_n, int32_t n_data, int32_t data_bits, int32_t n_special,

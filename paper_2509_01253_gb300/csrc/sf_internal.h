@@ -232,6 +232,9 @@ sf_status sf_signed_to_residues(sf_ctx *ctx, const int64_t *v, u64 *out, int n_p
                                 cudaStream_t st);
 sf_status sf_rotkey_finish(sf_ctx *ctx, const u64 *alpha, const u64 *e, const u64 *s_mont, const u64 *pg, int d,
                            u64 *key_a, u64 *key_b, size_t comp, cudaStream_t st);
+// device-side range check of caller input: latches SF_ERANGE in the status
+// word (reported by sf_sync) if a residue of poly t is >= modulus offset + t % period
+sf_status sf_check_residues(sf_ctx *ctx, const u64 *x, int n_polys, int period, int offset, cudaStream_t st);
 // Shoup companions floor(x 2^64 / q) of residues x (poly t uses modulus offset + t % period)
 sf_status sf_companions(sf_ctx *ctx, const u64 *x, u64 *dst, int n_polys, int period, int offset, cudaStream_t st);
 

@@ -57,8 +57,17 @@ __device__ __forceinline__ void leaf_taps_all(const SfRing &R, const SfGeo &g, c
             const int p = P.pos_of ? P.pos_of[idx] : idx;
             const int k = p & (R.n - 1);
             const int cidx = k ? R.n - k : 0;
-            const int64_t wq = wrow[tp.w];
+            const int64_t wq = P.gamma2 ? 2 * wrow[tp.w] : wrow[tp.w];
             f(p >> R.log_n, cidx >> g.log_c, cidx & (g.c - 1), k ? -wq : wq);
+            if (P.gamma2) {
+                // gamma = 2 (Lemma 1 at t = 2): the row is (N/2)^-1 (X^-k ct_j + X^-3k ct3_j), so
+                // the tap also lands at X^-3k of the power ct3_j.  With e = 3k mod 2N,
+                // X^-e = 1 (e = 0), -X^(N - e) (0 < e <= N), X^(2N - e) (N < e < 2N).
+                const int e = (3 * k) & (2 * R.n - 1);
+                const int c3 = e == 0 ? 0 : (e <= R.n ? R.n - e : 2 * R.n - e);
+                const bool neg = e != 0 && e <= R.n;
+                f(P.k_src + (p >> R.log_n), c3 >> g.log_c, c3 & (g.c - 1), neg ? -wq : wq);
+            }
         }
     }
 }
@@ -296,6 +305,51 @@ sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStre
 
 // ------------------------------------------------------------ pack tree --
 
+// Level-1 merge at gamma = 2, NTT domain: out = E + X^s O (out = E without O).
+// grid (N / (256 SF_EW), L, merges), SfKsBatch indexing as in the key switch.
+#define SF_EW2 8
+__global__ void __launch_bounds__(256) k_merge_plain(SfRing R, SfKsBatch B)
+{
+    const int b = blockIdx.z, i = blockIdx.y;
+    int g = (B.first + b) / B.inner, t = (B.first + b) - g * B.inner;
+    const u64 *E = B.E + B.E_outer * g + B.E_stride * t;
+    const u64 *O = B.O ? B.O + B.O_outer * g + B.O_stride * t : nullptr;
+    u64 *out = B.out + B.out_outer * g + B.out_stride * t;
+    const SfMod &M = R.m[i];
+    const size_t pb = (size_t)i << (R.log_n + 1);
+    const int j0 = blockIdx.x * (256 * SF_EW2) + threadIdx.x;
+#pragma unroll
+    for (int x = 0; x < SF_EW2; ++x) {
+        const int j = j0 + x * 256;
+        if (j >= R.n) break;
+        for (int part = 0; part < 2; ++part) {
+            const size_t off = ((size_t)(part * R.L + i) << R.log_n) + j;
+            u64 v = E[off];
+            if (O) {
+                const unsigned kk = mono_index(j, B.s, R.log_n);
+                v = sf_add(v, sf_mul_shoup(O[off], R.pw[pb + kk], R.pw_p[pb + kk], M.q), M.q);
+            }
+            out[off] = v;
+        }
+    }
+}
+
+static sf_status merge_plain_run(sf_ctx *ctx, const SfKsBatch &B, cudaStream_t st)
+{
+    const SfRing &R = ctx->ring;
+    cudaEvent_t ev;
+    for (int off = 0; off < B.count; off += 32768) {
+        SfKsBatch b = B;
+        b.count = std::min(32768, B.count - off);
+        b.first = B.first + off;
+        sf_launch_begin(ctx, SFK_ELEMWISE, st, &ev);
+        k_merge_plain<<<dim3((R.n + 256 * SF_EW2 - 1) / (256 * SF_EW2), R.L, b.count), 256, 0, st>>>(R, b);
+        sf_launch_end(ctx, SFK_ELEMWISE, st, ev);
+    }
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
 // Pack-tree levels level0+1 .. level1 (see sf_layer.h).  Node i of a level
 // is zero iff i >= valid[g]; a merge whose O-node is zero runs without O
 // (identical result, X^s * 0 = 0), and merges producing zero nodes are
@@ -303,7 +357,7 @@ sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStre
 // level lvl-1) using s = N / 2^lvl and d = 2^lvl + 1.
 sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int32_t> &key_d, size_t key_words,
                        u64 *A, u64 *B, int G, int n_nodes, int level0, const std::vector<int> &valid, bool trace,
-                       u64 *ks_scratch, int batch, u64 **res, size_t *res_stride, cudaStream_t st)
+                       u64 *ks_scratch, int batch, u64 **res, size_t *res_stride, cudaStream_t st, bool tau3_done)
 {
     const SfRing &R = ctx->ring;
     const size_t ct = (size_t)2 * R.L * R.n;
@@ -323,8 +377,13 @@ sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int3
     for (int lvl = level0 + 1; lvl <= level1; ++lvl) {
         const int half = n_nodes >> (lvl - level0);
         const int d = (1 << lvl) + 1;
-        const u64 *key;
-        SF_TRY(key_for(d, &key));
+        // gamma = 2: the tau_3 level is a plain merge (no key, no key switch)
+        const bool plain = tau3_done && lvl == 1;
+        auto run = [&](const SfKsBatch &b) -> sf_status {
+            return plain ? merge_plain_run(ctx, b, st) : sf_ks_run(ctx, b, ks_scratch, batch, st);
+        };
+        const u64 *key = nullptr;
+        if (!plain) SF_TRY(key_for(d, &key));
         SfKsBatch kb;
         memset(&kb, 0, sizeof(kb));
         kb.E_stride = ct;
@@ -349,7 +408,7 @@ sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int3
                 b.out = nxt + gi * nxt_gs;
                 b.inner = half;
                 b.count = (g1 - gi) * half;
-                SF_TRY(sf_ks_run(ctx, b, ks_scratch, batch, st));
+                SF_TRY(run(b));
                 gi = g1;
                 continue;
             }
@@ -364,14 +423,14 @@ sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int3
                 SfKsBatch b1 = b;
                 b1.O = b.E + (size_t)half * ct;
                 b1.count = with_o;
-                SF_TRY(sf_ks_run(ctx, b1, ks_scratch, batch, st));
+                SF_TRY(run(b1));
             }
             if (active > with_o) {
                 SfKsBatch b2 = b;
                 b2.O = nullptr;
                 b2.first = with_o;
                 b2.count = active - with_o;
-                SF_TRY(sf_ks_run(ctx, b2, ks_scratch, batch, st));
+                SF_TRY(run(b2));
             }
             ++gi;
         }
@@ -379,7 +438,8 @@ sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int3
         std::swap(cur_gs, nxt_gs);
     }
     // field trace: for k = level1+1 .. log2(N): ct <- ct + tau_{2^k+1}(ct)
-    for (int k = level1 + 1; trace && k <= R.log_n; ++k) {
+    // (from k = 2 at gamma = 2: the client's power supplied the tau_3 term)
+    for (int k = std::max(level1 + 1, tau3_done ? 2 : 1); trace && k <= R.log_n; ++k) {
         const int d = (1 << k) + 1;
         const u64 *key;
         SF_TRY(key_for(d, &key));
@@ -408,7 +468,7 @@ sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int3
 // Bias (the affine part b of f(x) = Ax + b): b-part coefficient l*N/n of
 // group g gets bq[channel(sigma_out(g n + l))].
 __global__ void k_add_bias(SfRing R, u64 *out, int G, int n, int E_out, const int *sig_out, const int64_t *bq,
-                           int C_out)
+                           int C_out, int scale)
 {
     const size_t ct = (size_t)2 * R.L * R.n;
     const int stride = R.n / n;
@@ -421,6 +481,8 @@ __global__ void k_add_bias(SfRing R, u64 *out, int G, int n, int E_out, const in
             int64_t q = (int64_t)R.m[i].q;
             int64_t r = v % q;
             if (r < 0) r += q;
+            const u64 r1 = (u64)r;
+            for (int k = 1; k < scale; ++k) r = (int64_t)sf_add((u64)r, r1, (u64)q);
             u64 *p = out + g * ct + ((size_t)(R.L + i) << R.log_n) + (size_t)l * stride;
             *p = sf_add(*p, (u64)r, (u64)q);
         }
@@ -428,13 +490,13 @@ __global__ void k_add_bias(SfRing R, u64 *out, int G, int n, int E_out, const in
 }
 
 sf_status sf_add_bias(sf_ctx *ctx, u64 *out, int G, int n, int E_out, const int *d_sig_out, const int64_t *d_bq,
-                      int C_out, cudaStream_t st)
+                      int C_out, cudaStream_t st, int scale)
 {
     cudaEvent_t ev;
     sf_launch_begin(ctx, SFK_ELEMWISE, st, &ev);
     int total = G * n;
     k_add_bias<<<std::max(1, std::min((total + 255) / 256, 1024)), 256, 0, st>>>(ctx->ring, out, G, n, E_out, d_sig_out,
-                                                                                 d_bq, C_out);
+                                                                                 d_bq, C_out, scale);
     sf_launch_end(ctx, SFK_ELEMWISE, st, ev);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
@@ -456,7 +518,7 @@ sf_status sf_shuffle_launch(sf_ctx *ctx, const u64 *in, u64 *out, const int *d_p
     cudaEvent_t ev;
     sf_launch_begin(ctx, SFK_SHUFFLE, st, &ev);
     size_t total = (size_t)count * ct;
-    k_shuffle_cts<<<(int)std::min<size_t>((total + 255) / 256, 152 * 32), 256, 0, st>>>(in, out, d_perm, count, ct);
+    k_shuffle_cts<<<(int)std::min<size_t>((total + 255) / 256, (size_t)ctx->num_sms * 32), 256, 0, st>>>(in, out, d_perm, count, ct);
     sf_launch_end(ctx, SFK_SHUFFLE, st, ev);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
@@ -477,6 +539,40 @@ __global__ void k_extract(SfRing R, const u64 *ct, u64 *out, int i)
         if (src >= R.n && v) v = M.q - v;
         out[x] = sf_mul_shoup(v, M.ninv, M.ninv_p, M.q);
     }
+}
+
+// Extraction at gamma = 2 (Lemma 1 at t = 2, scaled by [K_2 : K_0] = 2):
+// out = (N/2)^-1 (X^-i ct + X^-3i ct3), coefficient domain.
+__global__ void k_extract2(SfRing R, const u64 *ct, const u64 *ct3, u64 *out, int i)
+{
+    const size_t total = (size_t)2 * R.L * R.n;
+    const int two_n = 2 * R.n;
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
+        int limb = (int)((x >> R.log_n) % R.L);
+        int k = (int)(x & (R.n - 1));
+        size_t base = x - k;
+        const SfMod &M = R.m[limb];
+        // coefficient k of X^-e a is a[(k + e) mod 2N] folded by X^N = -1
+        auto coef = [&](const u64 *a, int e) -> u64 {
+            const int src = (k + e) % two_n;
+            u64 v = a[base + (src & (R.n - 1))];
+            return (src >= R.n && v) ? M.q - v : v;
+        };
+        const u64 v = sf_add(coef(ct, i), coef(ct3, (3 * i) % two_n), M.q);
+        // (N/2)^-1 = 2 N^-1
+        out[x] = sf_add(sf_mul_shoup(v, M.ninv, M.ninv_p, M.q), sf_mul_shoup(v, M.ninv, M.ninv_p, M.q), M.q);
+    }
+}
+
+sf_status sf_extract2_launch(sf_ctx *ctx, const u64 *ct, const u64 *ct3, u64 *out, int i, cudaStream_t st)
+{
+    cudaEvent_t ev;
+    sf_launch_begin(ctx, SFK_ELEMWISE, st, &ev);
+    size_t total = (size_t)2 * ctx->ring.L * ctx->ring.n;
+    k_extract2<<<(int)((total + 255) / 256), 256, 0, st>>>(ctx->ring, ct, ct3, out, i);
+    sf_launch_end(ctx, SFK_ELEMWISE, st, ev);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
 }
 
 sf_status sf_extract_launch(sf_ctx *ctx, const u64 *ct, u64 *out, int i, cudaStream_t st)

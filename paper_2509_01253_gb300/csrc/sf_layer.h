@@ -14,7 +14,9 @@ struct SfLeafParams {
     SfTermDev t[2];
     int n_terms;
     int C_out, W_out;
-    int k_in;
+    int k_in;               // input ciphertexts the leaves read (2 k_src with the client's powers)
+    int k_src;              // input ciphertexts of the round (chunks of the layer input)
+    int gamma2;             // gamma = 2: ciphertexts k_src .. 2 k_src - 1 are the powers RLWE(m_j(X^3))
     int s0;
     int s_stride;
     int n_slots_valid;
@@ -42,10 +44,16 @@ size_t sf_leaf_tap_words(const SfRing &R, int k_in, int max_taps, int slots);
 // at group stride a_gs; B has room for half as many.  valid[g] = non-zero
 // nodes of group g.  With trace, the field-trace steps k = level1+1 .. log2 N
 // follow.  Result (G ciphertexts, NTT domain) at *res, group stride *res_stride.
+// tau3_done (gamma = 2): the leaves already hold y + tau_3(y), so level 1
+// merges are E + X^(N/2) O with no key switch and the trace starts at k = 2.
 sf_status sf_pack_tree(sf_ctx *ctx, const u64 *keys_base, const std::vector<int32_t> &key_d, size_t key_words,
                        u64 *A, u64 *B, int G, int n_nodes, int level0, const std::vector<int> &valid, bool trace,
-                       u64 *ks_scratch, int batch, u64 **res, size_t *res_stride, cudaStream_t st);
+                       u64 *ks_scratch, int batch, u64 **res, size_t *res_stride, cudaStream_t st,
+                       bool tau3_done = false);
+// bias times `scale` (2 at gamma = 2, where packed values carry [K_2 : K_0] = 2)
 sf_status sf_add_bias(sf_ctx *ctx, u64 *out, int G, int n, int E_out, const int *d_sig_out, const int64_t *d_bq,
-                      int C_out, cudaStream_t st);
+                      int C_out, cudaStream_t st, int scale = 1);
+// gamma = 2 extraction: out = (N/2)^-1 (X^-i ct + X^-3i ct3), coefficient domain
+sf_status sf_extract2_launch(sf_ctx *ctx, const u64 *ct, const u64 *ct3, u64 *out, int i, cudaStream_t st);
 sf_status sf_shuffle_launch(sf_ctx *ctx, const u64 *in, u64 *out, const int *d_perm, int count, cudaStream_t st);
 sf_status sf_extract_launch(sf_ctx *ctx, const u64 *ct, u64 *out, int i, cudaStream_t st);

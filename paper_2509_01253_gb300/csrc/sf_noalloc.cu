@@ -8,6 +8,7 @@
 // workspace implies) would stall.  sf_rotate_noalloc serves them: its scratch
 // is the fixed array below, reserved once per GPU when the library's module
 // is loaded on that GPU, and every call reuses it.
+#include <algorithm>
 #include <mutex>
 
 #include "sf_internal.h"
@@ -53,7 +54,9 @@ extern "C" sf_status sf_rotate_noalloc(sf_ctx *ctx, const sf_rotkeys *rk, int32_
         if (rk->d[t] == d) slot = (int)t;
     if (slot < 0) return sf_set_error(SF_EINVAL, "no rotation key for d = %d", d);
     const size_t ct = (size_t)2 * R.L * R.n;
-    const size_t need = 2 * round_words((size_t)count * ct) + round_words(sf_ks_scratch_words(R) * count);
+    // key switches run in launch batches of the context's size, as in sf_rotate
+    const int batch = std::min(ctx->ks_batch, (int)count);
+    const size_t need = 2 * round_words((size_t)count * ct) + round_words(sf_ks_scratch_words(R) * batch);
     if (need > SF_NOALLOC_SCRATCH_WORDS)
         return sf_set_error(SF_EINVAL,
                             "sf_rotate_noalloc: %d ciphertexts need %zu bytes of scratch, the fixed maximum is %zu bytes",
@@ -87,7 +90,7 @@ extern "C" sf_status sf_rotate_noalloc(sf_ctx *ctx, const sf_rotkeys *rk, int32_
             b.d = d;
             b.add_v = 0;
             b.key = rk->d_keys + rk->key_words * slot;
-            s = sf_ks_run(ctx, b, ks, count, st);
+            s = sf_ks_run(ctx, b, ks, batch, st);
         }
         for (int x0 = 0; x0 < count * 2 * R.L && s == SF_OK; x0 += 64) {
             int cnt = 0;

@@ -209,13 +209,17 @@ __global__ void k_rotkey_finish(SfRing R, const u64 *alpha, const u64 *e, const 
     }
 }
 
-static int grid_for(size_t total) { return (int)std::min<size_t>((total + 255) / 256, 152 * 16); }
+// grid-stride launches: at most 16 resident 256-thread blocks per SM
+static int grid_for(const sf_ctx *ctx, size_t total)
+{
+    return (int)std::min<size_t>((total + 255) / 256, (size_t)ctx->num_sms * 16);
+}
 
 #define SF_ELEM_LAUNCH(kernel, total, ...)                                           \
     do {                                                                             \
         cudaEvent_t ev__;                                                            \
         sf_launch_begin(ctx, SFK_ELEMWISE, st, &ev__);                               \
-        kernel<<<grid_for(total), 256, 0, st>>>(ctx->ring, __VA_ARGS__);             \
+        kernel<<<grid_for(ctx, total), 256, 0, st>>>(ctx->ring, __VA_ARGS__);             \
         sf_launch_end(ctx, SFK_ELEMWISE, st, ev__);                                  \
         SF_CUDA_TRY(cudaGetLastError());                                             \
     } while (0)
@@ -282,6 +286,24 @@ __global__ void k_shoup_companions(SfRing R, const u64 *x, u64 *dst, int n_polys
         const SfMod &M = R.m[offset + (int)((i >> R.log_n) % period)];
         dst[i] = sf_shoup_companion_dev(x[i], M);
     }
+}
+
+// Latches SF_ERANGE in the device status word when a residue of the caller's
+// input is not below its modulus (the words are read, never written).
+__global__ void k_check_residues(SfRing R, const u64 *x, int n_polys, int period, int offset)
+{
+    bool bad = false;
+    SF_GRID_STRIDE(i, (size_t)n_polys * R.n)
+    {
+        bad |= x[i] >= R.m[offset + (int)((i >> R.log_n) % period)].q;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0 && R.status) atomicCAS(R.status, 0, SF_ERANGE);
+}
+
+sf_status sf_check_residues(sf_ctx *ctx, const u64 *x, int n_polys, int period, int offset, cudaStream_t st)
+{
+    SF_ELEM_LAUNCH(k_check_residues, (size_t)n_polys * ctx->ring.n, x, n_polys, period, offset);
+    return SF_OK;
 }
 
 sf_status sf_companions(sf_ctx *ctx, const u64 *x, u64 *dst, int n_polys, int period, int offset, cudaStream_t st)

@@ -67,14 +67,24 @@ static inline SfLeafParams leaf_params(const sf_layer *L)
 }
 
 // Input ciphertexts -> NTT domain (canonical), followed by their Shoup
-// companions (for the leaf products): ct holds 2 k_in ciphertexts' words.
-static inline sf_status prepare_inputs(sf_ctx *ctx, const u64 *d_in, int k_in, u64 *ct, cudaStream_t st)
+// companions (for the leaf products).  With the client's powers (gamma = 2,
+// d_pow non-null) the k_in powers follow the k_in inputs, so the leaves see
+// 2 k_in ciphertexts; ct holds twice the words of the ciphertexts it takes.
+static inline sf_status prepare_inputs(sf_ctx *ctx, const u64 *d_in, const u64 *d_pow, int k_in, u64 *ct,
+                                       cudaStream_t st)
 {
     const SfRing &R = ctx->ring;
+    const int k_all = d_pow ? 2 * k_in : k_in;
+    const size_t words = (size_t)k_in * 2 * R.L * R.n;
+    SF_TRY(sf_check_residues(ctx, d_in, k_in * 2 * R.L, R.L, 0, st));
+    if (d_pow) SF_TRY(sf_check_residues(ctx, d_pow, k_in * 2 * R.L, R.L, 0, st));
     std::vector<SfPolyJob> jobs;
-    for (int x = 0; x < k_in * 2 * R.L; ++x) jobs.push_back({d_in + (size_t)x * R.n, ct + (size_t)x * R.n, x % R.L});
+    for (int x = 0; x < k_all * 2 * R.L; ++x) {
+        const u64 *src = x < k_in * 2 * R.L ? d_in + (size_t)x * R.n : d_pow + (size_t)x * R.n - words;
+        jobs.push_back({src, ct + (size_t)x * R.n, x % R.L});
+    }
     SF_TRY(sf_ntt_jobs(ctx, jobs.data(), (int)jobs.size(), false, st));
-    SF_TRY(sf_companions(ctx, ct, ct + (size_t)k_in * 2 * R.L * R.n, k_in * 2 * R.L, R.L, 0, st));
+    SF_TRY(sf_companions(ctx, ct, ct + (size_t)k_all * 2 * R.L * R.n, k_all * 2 * R.L, R.L, 0, st));
     return SF_OK;
 }
 

@@ -10,6 +10,15 @@ Sec. 4.5).  A round may read several earlier activations (the block input of
 a residual connection): the client concatenates them, and the round's input
 permutation is the concatenation of theirs.
 
+Two client modes.  Fixed point (the default): activations are re-encoded at
+the input scale Delta.  Quantised (``act_bits`` set; the paper's integer
+setting, Sec. 2 "Quantization" and Sec. 4.5): weights are small integers
+encoded at scale 1, activations are unsigned act_bits-bit integers encoded at
+Delta, and after ReLU the client requantises every output with the round's
+public scale eta, y -> clip(round(y / eta), 0, 2^act_bits - 1), so the
+encrypted chain reproduces the quantised cleartext network exactly
+(Sec. 6.1's correctness check).
+
 Everything here is host-side orchestration: all arithmetic on ciphertexts
 runs in the CUDA library; encryption randomness is drawn by the library from
 the seeds given here.
@@ -36,17 +45,45 @@ def _mix(*xs) -> int:
     return h
 
 
-class EncodedNetwork:
-    """The rounds of one network with their quantised weights resident on a context."""
+def requant_scale(spec: wl.RoundSpec) -> int:
+    """The round's public requantisation scale eta (Sec. 4.5), a power of
+    two: 2^floor(log2(fan_in)), fan_in summed over the round's terms.  With
+    weights in {-2..2} and 4-bit inputs an output's spread grows like
+    sqrt(fan_in), so this keeps requantised activations inside a few bits."""
+    fan = sum(t.kh * t.kw * t.C_in for t in spec.terms)
+    return 1 << (fan.bit_length() - 1)
 
-    def __init__(self, params, ctx, ps: wl.ParamSet, rounds: list, integer: bool = False):
+
+def round_half_away(v: np.ndarray) -> np.ndarray:
+    """Round half away from zero (the encoding's rounding rule)."""
+    return np.sign(v) * np.floor(np.abs(v) + 0.5)
+
+
+def requantize(y: np.ndarray, eta: int, act_bits: int) -> np.ndarray:
+    """y -> clip(round(y / eta), 0, 2^act_bits - 1) on ReLU outputs (Sec. 4.5)."""
+    return np.clip(round_half_away(np.asarray(y, dtype=np.float64) / eta), 0, (1 << act_bits) - 1)
+
+
+class EncodedNetwork:
+    """The rounds of one network with their quantised weights resident on a context.
+
+    act_bits None: fixed point (weights at scale Delta, outputs at Delta^2).
+    act_bits set: quantised mode (integer weights at scale 1, outputs at
+    Delta, requantisation scale eta per round)."""
+
+    def __init__(self, params, ctx, ps: wl.ParamSet, rounds: list, integer: bool = False, act_bits: int = None):
         self.params, self.ctx, self.ps, self.rounds = params, ctx, ps, rounds
         self.n = 1 << ps.log_n
+        self.act_bits = act_bits
+        self.quant = act_bits is not None
+        wscale = 1.0 if self.quant else ps.delta
+        self.out_scale = ps.delta * wscale
+        self.etas = [requant_scale(spec) for spec in rounds] if self.quant else None
         self.layers, self.infos, self.weights = [], [], []
         for spec in rounds:
-            ws = wl.round_weights(spec, integer)
+            ws = wl.round_weights(spec, integer or self.quant)
             W = np.concatenate([w.ravel() for w in ws])
-            lay = sf.sf_encode_weights(ctx, spec.terms, W, None, ps.delta, ps.delta ** 2)
+            lay = sf.sf_encode_weights(ctx, spec.terms, W, None, wscale, self.out_scale)
             self.layers.append(lay)
             self.infos.append(sf.sf_layer_get_info(ctx, lay))
             self.weights.append(ws)
@@ -75,7 +112,11 @@ class ClientState:
         self.net = net
         self.session_seed = session_seed
         self.request_seed = request_seed
-        self.acts = {"x": (np.asarray(x, dtype=np.float64), None)}
+        x = np.asarray(x, dtype=np.float64)
+        if net.quant:
+            # the image in [0, 1] quantised to act_bits-bit integers
+            x = np.clip(round_half_away(x * ((1 << net.act_bits) - 1)), 0, (1 << net.act_bits) - 1)
+        self.acts = {"x": (x, None)}
         self.round = 0
         self.trace = []          # per round: (input values in original order, decoded outputs in original order)
 
@@ -113,8 +154,11 @@ class ClientState:
         return out
 
     def encode(self, r: int):
-        """Quantised message (int64, stream order) and sigma_prev of round r."""
+        """Quantised message (int64, stream order) and sigma_prev of round r
+        (integer activations times Delta, exactly, in quantised mode)."""
         stream, sigma = self.round_input(r)
+        if self.net.quant:
+            return stream.astype(np.int64) * int(self.net.ps.delta), sigma, stream
         return sf.sf_encode_input(stream, self.net.ps.delta), sigma, stream
 
     def encrypt_seed(self, r: int) -> int:
@@ -126,7 +170,11 @@ class ClientState:
         if stream_in is not None:
             y_orig = self.original_order(values, sigma_out)
             self.trace.append((self.original_order(stream_in, sigma_in), y_orig))
-        v = np.maximum(values, 0.0) if spec.relu else values.copy()
+        if self.net.quant:
+            y = round_half_away(values)             # outputs are integers at scale Delta
+            v = requantize(np.maximum(y, 0.0), self.net.etas[r], self.net.act_bits) if spec.relu else y
+        else:
+            v = np.maximum(values, 0.0) if spec.relu else values.copy()
         self.acts[spec.out] = (v, sigma_out)
         self.round = r + 1
 
@@ -148,11 +196,12 @@ def round_float_reference(net: EncodedNetwork, r: int, x_orig: np.ndarray) -> np
 def decode_outputs(net: EncodedNetwork, r: int, residues: np.ndarray) -> np.ndarray:
     info = net.infos[r]
     return sf.sf_decode(net.params, residues, info["n_groups"], net.n // info["group_size"],
-                        info["E_out"], net.ps.delta ** 2)
+                        info["E_out"], net.out_scale)
 
 
 def run_request(net: EncodedNetwork, sk, rk, client: ClientState, stream=None, device: str = "cuda:0",
-                keep_trace: bool = False, log: protocol.CommLog = None, session: protocol.ServerSession = None):
+                keep_trace: bool = False, log: protocol.CommLog = None, session: protocol.ServerSession = None,
+                io: list = None):
     """All rounds of one request, one sf_eval_linear_layer call per round.
     Each upload goes through the server's session checks (its session id is
     the client's session seed); `log`, when given, receives every round's
@@ -185,6 +234,9 @@ def run_request(net: EncodedNetwork, sk, rk, client: ClientState, stream=None, d
             return d_out
 
         d_out = session.submit(client.session_seed, r, d_in, evaluate)
+        if io is not None:
+            # (uploaded ciphertexts, packed results, sigma_prev, sigma_out) of the round, for parity checks
+            io.append((d_in.cpu().numpy().view(np.uint64), d_out.cpu().numpy().view(np.uint64), sigma_prev, so))
         t0 = time.perf_counter()
         res = np.zeros((info["n_groups"], L, n), dtype=np.uint64)
         sf.sf_decrypt(net.ctx, sk, d_out, info["n_groups"], res, st)
@@ -195,6 +247,22 @@ def run_request(net: EncodedNetwork, sk, rk, client: ClientState, stream=None, d
             up, down = protocol.round_bytes(info, L, n)
             log.add(r, up, down, ms[-1] / 1e3, t_client)
     return ms
+
+
+def quant_forward(net: EncodedNetwork, x: np.ndarray, trace: list = None) -> np.ndarray:
+    """The quantised cleartext network (Sec. 6.1's reference): the image
+    quantised to act_bits bits, each round's integer convolution computed
+    exactly, then ReLU and requantisation by the round's eta; returns the
+    integer logits.  `trace` receives (input, output) per round, original order."""
+    top = (1 << net.act_bits) - 1
+    acts = {"x": np.clip(round_half_away(np.asarray(x, dtype=np.float64) * top), 0, top)}
+    for r, spec in enumerate(net.rounds):
+        inp = np.concatenate([acts[name] for name in spec.inputs])
+        y = round_float_reference(net, r, inp)      # integers below 2^53: exact in float64
+        if trace is not None:
+            trace.append((inp, y))
+        acts[spec.out] = requantize(np.maximum(y, 0.0), net.etas[r], net.act_bits) if spec.relu else y
+    return acts[net.rounds[-1].out]
 
 
 def float_forward(net: EncodedNetwork, x: np.ndarray, trace: list = None) -> np.ndarray:

@@ -314,3 +314,17 @@ def round_input_size(spec: RoundSpec) -> int:
 def round_output_size(spec: RoundSpec) -> int:
     t = spec.terms[0]
     return t.H_out * t.W_out * t.C_out
+
+
+def round_case(kind: str, name: str, seed: int, shuffle: bool = True) -> LayerCase:
+    """One round of a ResNet-shaped network as a stand-alone layer: the
+    round's terms and seeded weights, an input U(0, 1) (a post-ReLU
+    activation) and random input and output permutations."""
+    spec = next(r for r in resnet_rounds(kind) if r.name == name)
+    ws = round_weights(spec)
+    e_in, e_out = round_input_size(spec), round_output_size(spec)
+    x = np.random.default_rng(seed + 1).uniform(0.0, 1.0, e_in)
+    prng = np.random.default_rng(seed + 4)
+    sp = random_permutation(prng, e_in) if shuffle else None
+    so = random_permutation(prng, e_out) if shuffle and spec.name != "fc" else None
+    return LayerCase(f"{kind}.{name}", list(spec.terms), ws, None, x, sp, so)

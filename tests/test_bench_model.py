@@ -61,5 +61,14 @@ def test_roofline_record_arithmetic():
     assert rec["alu_view"]["probe_peak"] == pytest.approx(ceil)
     assert rec["alu_view"]["frac_of_probe"] == pytest.approx(rec["achieved"] / ceil)
     assert rec["launches_per_layer"] == 15
-    assert rec["traffic"] == pytest.approx(bench.TRAFFIC_PER_ITEM["ks3_inner_row"] * 16384 / 15)
+    assert rec["traffic"] is None                      # no capture of this kernel at this ring
     assert rec["share_of_device_time"] == pytest.approx(250.0 / 420.0)
+    # traffic scales a per-item capture to a launch; the SM count sets the derived peak
+    bench.TRAFFIC_PER_ITEM[("ks3_inner_row", 14)] = 2.5e6
+    try:
+        rec2 = bench.roofline_of(kstats, k_steps, g, info, 420.0, {"sm_mhz": 2070.0}, probe=probe, sm_count=148)
+    finally:
+        del bench.TRAFFIC_PER_ITEM[("ks3_inner_row", 14)]
+    assert rec2["traffic"] == pytest.approx(2.5e6 * 16384 / 15)
+    assert rec2["peak"] == pytest.approx(148 * 64 * 2070e6 / 10 / 1e9)
+    assert "148 SMs" in rec2["peak_source"]

@@ -120,3 +120,43 @@ def test_served_resnet20_mix_equals_alone(pools):
         assert np.array_equal(req.logits, alone[req.request_seed]), req.request_seed
     ref = nw.float_forward(pools["p14"].nets["resnet20"], wl.network_input("resnet20", 41))
     assert np.abs(alone[41] - ref).max() <= 1e-3
+
+
+@pytest.mark.gpu
+def test_quantised_request_matches_oracle_rounds_and_cleartext(oracle):
+    """Integer mode over a whole request (tiny_a at N = 2^12, 2 x 30-bit + 1,
+    4-bit activations, integer weights at scale 1, Delta = 2^25): every round's
+    packed residues equal the oracle's round on the same uploaded ciphertexts
+    (extraction, unshuffle, linear step, shuffle, packing), every round's
+    decrypted outputs equal the quantised cleartext round exactly, and so do
+    the final logits (Sec. 6.1's check), with the client requantising by each
+    round's eta between rounds (Sec. 4.5)."""
+    import paper_2509_01253_gb300 as sf
+    from _gpu import Session, oracle_params
+    ps = wl.PARAMS["fc64"]
+    s = Session.from_set(ps, sk_seed=91, rk_seed=92)
+    net = None
+    try:
+        net = nw.EncodedNetwork(s.params, s.ctx, ps, wl.resnet_rounds("tiny_a"), act_bits=4)
+        x = wl.network_input("tiny_a", 93)
+        client = nw.ClientState(net, x, session_seed=94, request_seed=95)
+        io = []
+        nw.run_request(net, s.sk, s.rk, client, keep_trace=True, io=io)
+        trace = []
+        logits = nw.quant_forward(net, x, trace)
+        assert np.array_equal(client.logits(), logits)
+        prm = oracle_params(oracle, ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits)
+        s_o = oracle.keygen(prm, 91)
+        keys = oracle.rotation_keys(prm, s_o, 92)
+        for r, (spec, (cts, out, sp, so)) in enumerate(zip(net.rounds, io)):
+            x_in, y = client.trace[r]
+            assert np.array_equal(x_in, trace[r][0]) and np.array_equal(np.floor(y + 0.5), trace[r][1]), spec.name
+            terms = [oracle.ConvTerm(t.in_offset, t.H, t.W, t.C_in, t.C_out, t.kh, t.kw, t.stride, t.pad)
+                     for t in spec.terms]
+            lay = oracle.make_layer(terms, net.weights[r], None, 1.0, ps.delta)
+            want = oracle.eval_linear_layer(prm, lay, keys, cts, sp, so)
+            assert (out == want).all(), spec.name
+    finally:
+        if net is not None:
+            net.destroy()
+        s.close()

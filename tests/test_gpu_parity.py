@@ -6,6 +6,8 @@ seconds, spanning several tiles and ragged groups; at the full benchmark size
 (conv16: N = 2^14, 16384 outputs) on sampled outputs the oracle computes one
 by one, plus decrypted error <= 1e-3 against float64 on every output.
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -246,6 +248,99 @@ def test_pack_bit_exact(oracle, n_leaves, n):
         s.close()
 
 
+@pytest.mark.gpu
+def test_pack_full_size_conv16_ring(oracle):
+    """Fast packing of 4 encrypted leaves at the conv16 ring (N = 2^14, 3 x
+    50-bit + 1): 3 tree merges and 12 trace steps, every residue equal to the
+    oracle's."""
+    ps = wl.PARAMS["conv16"]
+    s = Session.from_set(ps, sk_seed=51, rk_seed=52)
+    try:
+        prm = oracle_params(oracle, ps.log_n, ps.n_data, ps.data_bits, ps.n_special, ps.special_bits)
+        s_o = oracle.keygen(prm, 51)
+        keys = oracle.rotation_keys(prm, s_o, 52)
+        msg = np.random.default_rng(53).integers(-2 ** 40, 2 ** 40, 4 * s.n)
+        d_ct = s.encrypt(msg, 54, 4)
+        leaves = list(from_dev(d_ct).reshape(4, 2, s.L, s.n))
+        out = dev_zeros(2, s.L, s.n)
+        sf.sf_pack(s.ctx, s.rk, d_ct, 4, 4, out)
+        assert (from_dev(out) == oracle.pack(prm, keys, leaves, n=4)).all()
+    finally:
+        s.close()
+
+
+def _read_pack_digest():
+    path = os.path.join(os.path.dirname(__file__), "golden", "pack_n65536_l5k2_n4.txt")
+    digest, rows = None, {}
+    with open(path) as f:
+        for line in f:
+            w = line.split()
+            if not w or w[0].startswith("#"):
+                continue
+            if w[0] == "sha256":
+                digest = w[1]
+            elif w[0] == "residues":
+                rows[(int(w[1]), int(w[2]))] = [int(v) for v in w[3:]]
+    return digest, rows
+
+
+@pytest.mark.gpu
+def test_pack_largest_ring_matches_stored_oracle_result():
+    """Fast packing of 4 encrypted leaves at N = 2^16, 5 x 50-bit + 2 (3 tree
+    merges, 14 trace steps): the SHA-256 of every output residue equals the
+    one tests/golden/make_pack_largest_ring.py wrote from the CPU oracle on
+    the same seeded keys and leaves (the oracle needs minutes at this size)."""
+    import hashlib
+    digest, rows = _read_pack_digest()
+    s = Session(16, 5, 50, 2, sk_seed=61, rk_seed=62)
+    try:
+        msg = np.random.default_rng(63).integers(-2 ** 40, 2 ** 40, 4 * s.n)
+        d_ct = s.encrypt(msg, 64, 4)
+        out = dev_zeros(2, s.L, s.n)
+        sf.sf_pack(s.ctx, s.rk, d_ct, 4, 4, out)
+        got = from_dev(out).reshape(2, s.L, s.n)
+        for (part, limb), vals in rows.items():
+            assert [int(v) for v in got[part, limb, :len(vals)]] == vals, (part, limb)
+        assert hashlib.sha256(np.ascontiguousarray(got, dtype="<u8").tobytes()).hexdigest() == digest
+    finally:
+        s.close()
+
+
+@pytest.mark.gpu
+def test_status_word_reports_out_of_range_input_residue():
+    """An input ciphertext with a residue equal to its modulus: sf_rotate and
+    sf_eval_linear_layer return SF_OK (the work is enqueued), the device check
+    latches SF_ERANGE, sf_sync reports it once and clears it; valid input
+    leaves the status clean."""
+    ps = wl.PARAMS["fc64"]
+    s = Session.from_set(ps, sk_seed=71, rk_seed=72)
+    try:
+        q = sf.sf_params_get_info(s.params)["moduli"]
+        d_ct = s.encrypt(np.arange(64), 73, 1)
+        out = dev_zeros(1, 2, s.L, s.n)
+        sf.sf_rotate(s.ctx, s.rk, 3, d_ct, out, 1)
+        sf.sf_sync(s.ctx)                                   # valid input: clean
+        bad = d_ct.clone()
+        bad[0, 1, 1, 17] = int(q[1])                        # b-part, limb 1: residue == q_1
+        sf.sf_rotate(s.ctx, s.rk, 3, bad, out, 1)
+        with pytest.raises(sf.SafhireError) as e:
+            sf.sf_sync(s.ctx)
+        assert e.value.status == sf.SF_ERANGE
+        sf.sf_sync(s.ctx)                                   # cleared
+        case = wl.fc64_case()
+        lay = gpu_layer(s, case, ps.delta, ps.delta ** 2)
+        d_out = dev_zeros(1, 2, s.L, s.n)
+        sf.sf_eval_linear_layer(s.ctx, lay, s.rk, bad, 1, case.sigma_prev, case.sigma_out, d_out, 1)
+        with pytest.raises(sf.SafhireError) as e:
+            sf.sf_sync(s.ctx)
+        assert e.value.status == sf.SF_ERANGE
+        sf.sf_eval_linear_layer(s.ctx, lay, s.rk, d_ct, 1, case.sigma_prev, case.sigma_out, d_out, 1)
+        sf.sf_sync(s.ctx)
+        sf.sf_layer_destroy(lay)
+    finally:
+        s.close()
+
+
 # ---------------------------------------------------------- linear layer -----
 
 def _run_layer(sess, case, delta, out_scale, weight_scale, n_capacity=64, integer_input=False):
@@ -413,6 +508,126 @@ def test_conv16_integer_mode_exact(oracle):
         assert (np.rint(vals) == ref).all()
         # pack-tree noise (about N * n * key-switch noise) stays far below scale / 2
         assert np.abs(vals - ref).max() < 1e-3
+        sf.sf_layer_destroy(lay)
+    finally:
+        s.close()
+
+
+# ----------------------------------------- partial trace extraction, gamma = 2 --
+
+def _gamma2_inputs(s, msg, k_in, seed):
+    """The client's two uploads at gamma = 2: RLWE(m_j) and RLWE(m_j(X^3))."""
+    d_in = s.encrypt(msg, seed, k_in)
+    d_pow = s.encrypt(sf.sf_client_power(s.params, msg, k_in, 3), seed + 1, k_in)
+    return d_in, d_pow
+
+
+def test_client_power_matches_oracle(oracle):
+    """sf_client_power (m(X^3) per chunk) equals the oracle's client power."""
+    p = sf.sf_params_create(10, 2, 50, 1, 50)
+    try:
+        prm = oracle_params(oracle, 10, 2, 50, 1)
+        m = np.random.default_rng(5).integers(-2 ** 40, 2 ** 40, 3 * prm.n)
+        got = sf.sf_client_power(p, m, 3, 3).reshape(3, prm.n)
+        for j in range(3):
+            assert (got[j] == oracle.client_power(prm, m[j * prm.n:(j + 1) * prm.n])).all()
+    finally:
+        sf.sf_params_destroy(p)
+
+
+def test_extract_and_pack_gamma2_bit_exact(oracle):
+    """gamma = 2 extraction rows and their packing (the tau_3 level merged with
+    no key switch) equal the oracle's, residue by residue, for several leaf
+    counts (one value: the trace starts at k = 2)."""
+    log_n, L, K = 10, 3, 1
+    s = Session(log_n, L, 50, K, sk_seed=81, rk_seed=82)
+    try:
+        prm = oracle_params(oracle, log_n, L, 50, K)
+        s_o = oracle.keygen(prm, 81)
+        keys = oracle.rotation_keys(prm, s_o, 82)
+        msg = np.random.default_rng(83).integers(-2 ** 30, 2 ** 30, s.n)
+        d_ct, d_pow = _gamma2_inputs(s, msg, 1, 84)
+        ct, ct3 = from_dev(d_ct).reshape(2, L, s.n), from_dev(d_pow).reshape(2, L, s.n)
+        rows = []
+        for i in (0, 1, 5, s.n // 2, s.n - 1):
+            d_row = dev_zeros(2, L, s.n)
+            sf.sf_extract(s.ctx, d_ct, i, 2, d_pow, d_row)
+            row = from_dev(d_row).reshape(2, L, s.n)
+            assert (row == oracle.extract(prm, ct, i, 2, ct3)).all(), i
+            rows.append(row)
+        d_rows = to_dev(np.stack(rows))
+        for n_leaves, n in ((1, 1), (2, 2), (3, 4), (5, 8)):
+            out = dev_zeros(2, L, s.n)
+            sf.sf_pack_gamma(s.ctx, s.rk, d_rows, n_leaves, n, 2, out)
+            want = oracle.pack(prm, keys, rows[:n_leaves], n=n, gamma=2)
+            assert (from_dev(out).reshape(2, L, s.n) == want).all(), (n_leaves, n)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("name", ["conv_ragged_two_groups", "shortcut_bias_k_in_3"])
+def test_scaled_layer_gamma2_bit_exact(oracle, name):
+    """Whole rounds at gamma = 2 on scaled rings (ragged groups, k_in = 3 inputs
+    with a shortcut term and bias): every residue equals the oracle's round
+    with the client's powers, with n/2 fewer key switches per group, and the
+    halved decryption equals the gamma = 0 one."""
+    log_n, L, bits, K, make, wsc, delta = SCALED[name]
+    case = make()
+    s = Session(log_n, L, bits, K, sk_seed=51, rk_seed=52)
+    try:
+        lay = gpu_layer(s, case, wsc, delta * wsc)
+        info = sf.sf_layer_get_info(s.ctx, lay)
+        k_in = info["k_in"]
+        msg = sf.sf_encode_input(stream_input(case), delta)
+        d_in, d_pow = _gamma2_inputs(s, msg, k_in, 77)
+        d_out = dev_zeros(info["n_groups"], 2, s.L, s.n)
+        n_out = sf.sf_eval_linear_layer_gamma(s.ctx, lay, s.rk, 2, d_in, d_pow, k_in, case.sigma_prev,
+                                              case.sigma_out, d_out, info["n_groups"])
+        sf.sf_sync(s.ctx)
+        assert n_out == info["n_groups"]
+        got = from_dev(d_out)
+        prm = oracle_params(oracle, log_n, L, bits, K)
+        s_o = oracle.keygen(prm, 51)
+        keys = oracle.rotation_keys(prm, s_o, 52)
+        cts = from_dev(d_in).reshape(k_in, 2, L, s.n)
+        pw = from_dev(d_pow).reshape(k_in, 2, L, s.n)
+        c = oracle.Counter()
+        want = oracle.eval_linear_layer(prm, oracle_layer(oracle, case, wsc, delta * wsc), keys, cts,
+                                        case.sigma_prev, case.sigma_out, c, powers=pw)
+        assert (got == want).all()
+        assert c.ks == oracle.ks_count(prm, case.E_out, gamma=2) < info["ks_count"]
+        # halved decryption against the gamma = 0 round on the same input
+        d0 = dev_zeros(info["n_groups"], 2, s.L, s.n)
+        sf.sf_eval_linear_layer(s.ctx, lay, s.rk, d_in, k_in, case.sigma_prev, case.sigma_out, d0, info["n_groups"])
+        g, stride = info["n_groups"], s.n // info["group_size"]
+        v2 = sf.sf_decode(s.params, s.decrypt(d_out, g), g, stride, case.E_out, 2 * delta * wsc)
+        v0 = sf.sf_decode(s.params, s.decrypt(d0, g), g, stride, case.E_out, delta * wsc)
+        assert np.abs(v2 - v0).max() <= 1e-3
+        sf.sf_layer_destroy(lay)
+    finally:
+        s.close()
+
+
+def test_conv16_gamma2_full_size():
+    """The benchmark layer at gamma = 2 (N = 2^14): 2 groups of 8192 values at
+    4095 + 1 key switches each (8192 instead of 16384), decrypted (halved)
+    outputs within 1e-3 of float64 on all 16384 outputs."""
+    ps = wl.PARAMS["conv16"]
+    case = wl.conv16_case()
+    s = Session.from_set(ps, sk_seed=203, rk_seed=205)
+    try:
+        lay = gpu_layer(s, case, ps.delta, ps.delta ** 2)
+        info = sf.sf_layer_get_info(s.ctx, lay)
+        msg = sf.sf_encode_input(stream_input(case), ps.delta)
+        d_in, d_pow = _gamma2_inputs(s, msg, 1, 204)
+        d_out = dev_zeros(2, 2, s.L, s.n)
+        sf.sf_eval_linear_layer_gamma(s.ctx, lay, s.rk, 2, d_in, d_pow, 1, case.sigma_prev, case.sigma_out, d_out, 2)
+        vals = sf.sf_decode(s.params, s.decrypt(d_out, 2), 2, 2, 16384, 2 * ps.delta ** 2)
+        ref = wl.float_reference(case)[case.sigma_out.astype(np.int64)]
+        err = np.abs(vals - ref).max()
+        assert err <= 1e-3, err
+        with pytest.raises(sf.SafhireError):
+            sf.sf_eval_linear_layer_gamma(s.ctx, lay, s.rk, 2, d_in, None, 1, None, None, d_out, 2)
         sf.sf_layer_destroy(lay)
     finally:
         s.close()

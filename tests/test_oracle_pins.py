@@ -752,3 +752,113 @@ def test_packed_noise_moments_shape_and_bound(oracle, L, qbits, K, pbits):
     assert abs(skew) < 0.2 and abs(exkurt) < 0.5, (skew, exkurt)
     std_max = max(math.sqrt(_packed_noise_moments(prm, n, l)[1]) for l in range(n))
     assert worst < 8 * std_max < prm.Q / 2 ** 20
+
+
+# ------------------------------------------------ partial trace, gamma = 2 ---
+# At t = 2 the tower is K_0 = K_1 = Q, K_2 = Q(i), ..., K_alpha = K.  The
+# partial trace over K_2 / K_0 sums the automorphisms {1, 3} (Lemma 1, j in
+# {0, 1}, k = 1), and the rest of the full trace is the sum over
+# Gal(K / K_2) = {d = 1 mod 4}, generated by the tau_{2^k+1} with k >= 2.
+
+def _tau_int(v, d, n):
+    """tau_d on an integer coefficient vector, from its definition
+    X^i -> X^(i d mod 2N) with X^N = -1."""
+    out = [0] * n
+    for i, c in enumerate(v):
+        e = i * d % (2 * n)
+        if e < n:
+            out[e] += int(c)
+        else:
+            out[e - n] -= int(c)
+    return out
+
+
+def test_client_power_is_evaluation_at_cubes(oracle):
+    """The client's power m(X^3) (Sec. 4.3, gamma = 2, t = 2) evaluates at every
+    odd power of psi to m at the cube of that point."""
+    prm = oracle.make_params(5, 1, 50, 1, 50)
+    q = prm.q[0]
+    psi = oracle.lib().or_primitive_root_2n(q, 2 * prm.n)
+    m = np.random.default_rng(1).integers(-1000, 1001, prm.n)
+    m3 = oracle.client_power(prm, m)
+    for e in range(1, 2 * prm.n, 2):
+        x = pow(psi, e, q)
+        assert _poly_eval([int(v) % q for v in m3], x, q) == _poly_eval([int(v) % q for v in m], pow(x, 3, q), q)
+
+
+def test_lemma1_gamma2_extraction(oracle):
+    """Lemma 1 at t = 2, gamma = 2: the constant coefficient of
+    X^-i m(X) + X^-3i m(X^3) is 2 m_i, so the extracted row (its scaling by
+    (N/2)^-1) has constant coefficient 4 m_i / N; the remaining trace over
+    K / K_2 (packing one value, log2 N - 1 key switches) maps the row to
+    exactly 2 m_i = [K_2 : K_0] m_i with every other coefficient zero."""
+    prm = oracle.make_params(6, 2, 50, 1, 50)
+    s = oracle.keygen(prm, 1)
+    keys = oracle.rotation_keys(prm, s, 2)
+    m = np.random.default_rng(3).integers(-10 ** 6, 10 ** 6, prm.n)
+    ct, ct3 = _trivial(prm, m), _trivial(prm, oracle.client_power(prm, m))
+    for i in (0, 1, 7, prm.n - 1):
+        row = oracle.extract(prm, ct, i, 2, ct3)
+        for li, qi in enumerate(prm.q):
+            assert int(row[1, li, 0]) == 4 * int(m[i]) * pow(prm.n, -1, qi) % qi
+        c = oracle.Counter()
+        out = oracle.pack(prm, keys, [row], c, gamma=2)
+        assert oracle.crt_centered(prm, out[1]) == [2 * int(m[i]) if k == 0 else 0 for k in range(prm.n)]
+        assert c.ks == prm.log_n - 1
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 32])
+def test_pack_gamma2_of_partial_traces(oracle, n):
+    """Packing leaves that hold y_l + tau_3(y_l) at gamma = 2 gives exactly the
+    gamma = 0 packing of the y_l, N sum_l y_l[0] X^(l N / n), with n/2 fewer
+    key switches (one fewer when n = 1)."""
+    prm = oracle.make_params(7, 2, 50, 1, 50)
+    s = oracle.keygen(prm, 1)
+    keys = oracle.rotation_keys(prm, s, 2)
+    rng = np.random.default_rng(100 + n)
+    ys = [rng.integers(-10 ** 5, 10 ** 5, prm.n) for _ in range(n)]
+    y2 = [[int(a) + b for a, b in zip(y, _tau_int(y, 3, prm.n))] for y in ys]
+    c0, c2 = oracle.Counter(), oracle.Counter()
+    out0 = oracle.pack(prm, keys, [_trivial(prm, y) for y in ys], c0)
+    out2 = oracle.pack(prm, keys, [_trivial(prm, y) for y in y2], c2, gamma=2)
+    assert (out0 == out2).all()
+    want = [0] * prm.n
+    for l in range(n):
+        want[l * prm.n // n] = prm.n * int(ys[l][0])
+    assert oracle.crt_centered(prm, out2[1]) == want
+    assert c0.ks - c2.ks == (n // 2 if n >= 2 else 1)
+    assert c2.ks == oracle.ks_count(prm, n, gamma=2)
+
+
+def test_encrypted_layer_gamma2_integer_mode_is_exact(oracle):
+    """A whole encrypted round at gamma = 2 (the client also sends RLWE(m(X^3))
+    per input ciphertext): decrypting and halving (the [K_2 : K_0] factor)
+    gives exactly the quantised A x in shuffled order, with the gamma = 2
+    key-switch count."""
+    prm = oracle.make_params(8, 3, 50, 1, 50)
+    s = oracle.keygen(prm, 21)
+    keys = oracle.rotation_keys(prm, s, 22)
+    terms, ws, _ = _layer_case(oracle, prm, 5, H=5, W=5, C=4, Co=6)
+    lay = oracle.make_layer(terms, ws, None, 1.0, 1.0)
+    rng = np.random.default_rng(23)
+    x = rng.integers(0, 16, lay.E_in)
+    delta = 2 ** 30
+    sp = oracle.permutation(24, 3, lay.E_in)
+    so = oracle.permutation(24, 4, lay.E_out)
+    k_in = -(-lay.E_in // prm.n)
+    stream = np.zeros(k_in * prm.n, dtype=np.int64)
+    stream[:lay.E_in] = x[sp] * delta
+    cts = oracle.encrypt(prm, s, stream, 25, k_in)
+    powers = np.stack([oracle.encrypt(prm, s, oracle.client_power(prm, stream[j * prm.n:(j + 1) * prm.n]),
+                                      26 + j, 1)[0] for j in range(k_in)])
+    c = oracle.Counter()
+    out = oracle.eval_linear_layer(prm, lay, keys, cts, sp, so, c, powers=powers)
+    assert c.ks == oracle.ks_count(prm, lay.E_out, gamma=2) < oracle.ks_count(prm, lay.E_out)
+    res = oracle.decrypt(prm, s, out)
+    n = oracle.group_size(prm, lay.E_out)
+    got = []
+    for g in range(res.shape[0]):
+        cent = oracle.crt_centered(prm, res[g])
+        got.extend(round(cent[l * (prm.n // n)] / (2 * delta)) for l in range(min(n, lay.E_out - g * n)))
+    y = oracle.dense_matrix(lay).dot(np.array([int(v) for v in x], dtype=object))
+    assert got == [int(v) for v in y[so]]

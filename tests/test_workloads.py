@@ -100,6 +100,7 @@ class _Net:
         class _PS:
             delta = 2.0 ** 20
         self.ps = _PS()
+        self.quant = False
 
 
 def test_client_concatenates_inputs_and_permutations():
@@ -127,3 +128,46 @@ def test_client_concatenates_inputs_and_permutations():
     # unshuffling the stream gives the original-order concatenation
     orig = c.original_order(stream, sigma)
     assert np.array_equal(orig[:E0], np.maximum(y1, 0)) and np.array_equal(orig[E0:], np.maximum(y0, 0))
+
+
+def test_requantisation_rule():
+    """Sec. 4.5: after ReLU, y -> clip(round(y / eta), 0, 2^bits - 1), rounding
+    half away from zero; eta is 2^floor(log2 fan_in) of the round."""
+    from paper_2509_01253_gb300 import network as nw
+    y = np.array([-5.0, 0.0, 5.0, 6.0, 9.0, 10.0, 100.0])
+    assert nw.requantize(np.maximum(y, 0), 4, 4).tolist() == [0, 0, 1, 2, 2, 3, 15]
+    assert nw.round_half_away(np.array([-2.5, -1.5, -0.4, 0.5, 1.5, 2.49])).tolist() == [-3, -2, 0, 1, 2, 2]
+    rounds = wl.resnet_rounds("tiny_a")
+    fans = [sum(t.kh * t.kw * t.C_in for t in r.terms) for r in rounds]
+    assert fans[0] == 18 and nw.requant_scale(rounds[0]) == 16
+    for r, f in zip(rounds, fans):
+        e = nw.requant_scale(r)
+        assert e <= f < 2 * e and (e & (e - 1)) == 0
+
+
+def test_quantised_client_encodes_integers_and_requantises():
+    """Quantised client: the image becomes 4-bit integers, a round's message is
+    the integer stream times Delta exactly, and decoded outputs are rounded,
+    passed through ReLU and requantised with the round's eta (the FC's
+    outputs are kept as integer logits)."""
+    from paper_2509_01253_gb300 import network as nw
+    net = _Net("tiny_a")
+    net.quant, net.act_bits = True, 4
+    net.etas = [nw.requant_scale(r) for r in net.rounds]
+    x = np.linspace(0.0, 1.0, wl.NETS["tiny_a"]["H"] ** 2 * wl.NETS["tiny_a"]["C"])
+    c = nw.ClientState(net, x, session_seed=5, request_seed=6)
+    xq = c.acts["x"][0]
+    assert xq.min() == 0 and xq.max() == 15 and np.array_equal(xq, np.floor(x * 15 + 0.5))
+    msg, sigma, stream = c.encode(0)
+    assert sigma is None and msg.dtype == np.int64 and np.array_equal(msg, xq.astype(np.int64) * 2 ** 20)
+    E0 = net.infos[0]["E_out"]
+    y = np.arange(E0, dtype=np.float64) - E0 / 2 + 0.2        # decoded values: integers plus decoding error
+    c.absorb(0, y, None)
+    want = np.clip(np.floor(np.maximum(np.floor(y + 0.5), 0) / net.etas[0] + 0.5), 0, 15)
+    assert np.array_equal(c.acts["a0"][0], want)
+    # the last round (FC, no ReLU) keeps rounded integer logits
+    last = len(net.rounds) - 1
+    c.round = last
+    logits = np.array([-3.2, 7.9, 0.4])
+    c.absorb(last, logits, None)
+    assert c.logits().tolist() == [-3, 8, 0]
