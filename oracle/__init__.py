@@ -718,8 +718,9 @@ def eval_linear_layer(prm: Params, layer: Layer, keys: dict, cts: np.ndarray,
         leaves = [linear_output(prm, layer, cts, o, sigma_prev, powers) for o in members]
         ct = pack(prm, keys, leaves, counter, n=n, gamma=gamma)
         if layer.bias_q is not None:
+            # at gamma = 2 the packed values carry [K_2 : K_0] = 2, the bias too
             co = np.array(members) % layer.C_out
-            ct = add_bias(prm, ct, [int(layer.bias_q[c]) for c in co], prm.n // n)
+            ct = add_bias(prm, ct, [(1 + (gamma == 2)) * int(layer.bias_q[c]) for c in co], prm.n // n)
         out.append(ct)
     return np.stack(out)
 

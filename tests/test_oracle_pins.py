@@ -833,16 +833,16 @@ def test_pack_gamma2_of_partial_traces(oracle, n):
 def test_encrypted_layer_gamma2_integer_mode_is_exact(oracle):
     """A whole encrypted round at gamma = 2 (the client also sends RLWE(m(X^3))
     per input ciphertext): decrypting and halving (the [K_2 : K_0] factor)
-    gives exactly the quantised A x in shuffled order, with the gamma = 2
+    gives exactly the quantised A x + b in shuffled order, with the gamma = 2
     key-switch count."""
     prm = oracle.make_params(8, 3, 50, 1, 50)
     s = oracle.keygen(prm, 21)
     keys = oracle.rotation_keys(prm, s, 22)
-    terms, ws, _ = _layer_case(oracle, prm, 5, H=5, W=5, C=4, Co=6)
-    lay = oracle.make_layer(terms, ws, None, 1.0, 1.0)
+    terms, ws, b = _layer_case(oracle, prm, 5, H=5, W=5, C=4, Co=6, bias=True)
+    delta = 2 ** 30
+    lay = oracle.make_layer(terms, ws, b, 1.0, float(delta))
     rng = np.random.default_rng(23)
     x = rng.integers(0, 16, lay.E_in)
-    delta = 2 ** 30
     sp = oracle.permutation(24, 3, lay.E_in)
     so = oracle.permutation(24, 4, lay.E_out)
     k_in = -(-lay.E_in // prm.n)
@@ -861,4 +861,5 @@ def test_encrypted_layer_gamma2_integer_mode_is_exact(oracle):
         cent = oracle.crt_centered(prm, res[g])
         got.extend(round(cent[l * (prm.n // n)] / (2 * delta)) for l in range(min(n, lay.E_out - g * n)))
     y = oracle.dense_matrix(lay).dot(np.array([int(v) for v in x], dtype=object))
+    y = y + np.array([int(b[o % lay.C_out]) for o in range(lay.E_out)], dtype=object)
     assert got == [int(v) for v in y[so]]
