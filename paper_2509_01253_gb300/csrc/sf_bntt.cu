@@ -17,19 +17,19 @@
 #include "sf_round.h"
 
 template <bool INV, int LR, int LC>
-__global__ void __launch_bounds__(SfThreads<LC>::value, LC >= 8 ? 2 : 3)
+__global__ void __launch_bounds__(SfRow<LC>::NT, 3)
     k_bntt_row(SfRing R, const u64 *src, u64 *dst, int count, int bpg)
 {
-    constexpr int NT = SfThreads<LC>::value;
+    constexpr int NT = SfRow<LC>::NT, NB = SfRow<LC>::NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr SfGeoT<LR, LC> g{};
     const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
-    const int i = grp % R.L, r0 = (grp / R.L) * SF_NB;
+    const int i = grp % R.L, r0 = (grp / R.L) * NB;
     const SfMod M = R.m[i];
     constexpr bool DB = sf_rows_double_buffered(LC);
     sf_tw *tw = (sf_tw *)smem_raw;
-    u64 *buf0 = (u64 *)(tw + SF_NB * g.c);
-    u64 *buf1 = DB ? buf0 + tile_words(g.log_c) : buf0;
+    u64 *buf0 = (u64 *)(tw + NB * g.c);
+    u64 *buf1 = DB ? buf0 + SfRow<LC>::WORDS : buf0;
     load_row_tw_t<LR, LC, NT>(tw, INV ? R.rowT_i : R.rowT_f, i, r0);
     const size_t per = (size_t)R.L << (LR + LC);
     const size_t off = ((size_t)i << (LR + LC)) + (size_t)r0 * g.c;
@@ -47,8 +47,8 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, LC >= 8 ? 2 : 3)
             sf_cp_wait<0>();
         }
         __syncthreads();
-        if (INV) tile_inverse_t<LC, true, NT>(cur, tw, M.q);
-        else tile_forward_t<LC, true, NT>(cur, tw, M.q);
+        if (INV) row_inverse_t<LC, NT>(cur, tw, M.q);
+        else row_forward_t<LC, NT>(cur, tw, M.q);
         // forward: the last pass, canonical output; inverse: lazy in [0, 4q), the column pass follows
         store_row_tile_t<LC, NT>(dst + per * p + off, cur, [&](u64 v) { return INV ? v : sf_reduce(v, M.q, M.one_p); });
         __syncthreads();
@@ -107,7 +107,7 @@ static int bntt_bpg(const sf_ctx *ctx, int occ, int n_groups, int count)
 
 static size_t bntt_smem_row(const SfRing &R)
 {
-    return sizeof(sf_tw) * SF_NB * R.c + sizeof(u64) * tile_words(R.log_c) * (sf_rows_double_buffered(R.log_c) ? 2 : 1);
+    return sizeof(sf_tw) * sf_row_nb(R.log_c) * R.c + sizeof(u64) * row_tile_words(R.log_c) * (sf_rows_double_buffered(R.log_c) ? 2 : 1);
 }
 static size_t bntt_smem_col(const SfRing &R) { return sizeof(sf_tw) * R.r + sizeof(u64) * tile_words(R.log_r) * 2; }
 
@@ -119,11 +119,11 @@ extern "C" sf_status sf_ntt_batch(sf_ctx *ctx, const uint64_t *d_in, uint64_t *d
         return sf_set_error(SF_EINVAL, "sf_ntt_batch: bad arguments");
     const SfRing &R = ctx->ring;
     cudaStream_t st = (cudaStream_t)stream;
-    const int rg = (R.r / SF_NB) * R.L, cg = (R.c / SF_NB) * R.L;
+    const int rg = (R.r / sf_row_nb(R.log_c)) * R.L, cg = (R.c / SF_NB) * R.L;
     const size_t smr = bntt_smem_row(R), smc = bntt_smem_col(R);
     cudaEvent_t ev;
     SF_GEO_DISPATCH(R.log_n, {
-        constexpr int NTR = SfThreads<LC>::value, NTC = SfThreads<LR>::value;
+        constexpr int NTR = SfRow<LC>::NT, NTC = SfThreads<LR>::value;
         if (!inverse) {
             const int bc = bntt_bpg(ctx, bntt_occupancy(k_bntt_col<false, LR, LC>, NTC, smc), cg, count);
             sf_launch_begin(ctx, SFK_BNTT_COL, st, &ev);

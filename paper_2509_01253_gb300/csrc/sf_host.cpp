@@ -549,17 +549,19 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
             colT_f[(size_t)m * R.r + k] = make_ulonglong2(tf[k], tfp[k]);
             colT_i[(size_t)m * R.r + k] = make_ulonglong2(ti[k], tip[k]);
         }
-        for (int tile = 0; tile < R.r / 16; ++tile)
+        // row tiles of nb rows (sf_row_nb: 16, or 8 for 256-point rows)
+        const int nb = sf_row_nb(R.log_c);
+        for (int tile = 0; tile < R.r / nb; ++tile)
             for (int k = 0; k < R.c; ++k)
-                for (int b = 0; b < 16; ++b) {
-                    size_t dst = (size_t)m * N + ((size_t)tile * R.c + k) * 16 + b;
+                for (int b = 0; b < nb; ++b) {
+                    size_t dst = (size_t)m * N + ((size_t)tile * R.c + k) * nb + b;
                     if (k == 0) {
                         rowT_f[dst] = rowT_i[dst] = make_ulonglong2(0, 0);
                         continue;
                     }
                     int mk = 1;
                     while (mk * 2 <= k) mk *= 2;
-                    size_t gi = (size_t)mk * (R.r + 16 * tile + b) + (k - mk);
+                    size_t gi = (size_t)mk * (R.r + nb * tile + b) + (k - mk);
                     rowT_f[dst] = make_ulonglong2(tf[gi], tfp[gi]);
                     rowT_i[dst] = make_ulonglong2(ti[gi], tip[gi]);
                 }

@@ -179,13 +179,13 @@ struct SfRowSet {
 };
 
 template <bool INV, int LR, int LC>
-__global__ void __launch_bounds__(SfThreads<LC>::value, LC >= 8 ? 2 : 3) k_rows(SfRing R, SfKsBatch B, SfRowSet S, int bpg)
+__global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_rows(SfRing R, SfKsBatch B, SfRowSet S, int bpg)
 {
-    constexpr int NT = SfThreads<LC>::value;
+    constexpr int NT = SfRow<LC>::NT, NB = SfRow<LC>::NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr SfGeoT<LR, LC> g{};
     const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
-    const int t = grp % S.npoly, r0 = (grp / S.npoly) * SF_NB;
+    const int t = grp % S.npoly, r0 = (grp / S.npoly) * NB;
     const int mod = S.mod_base + t % S.mod_period;
     const SfMod M = R.m[mod];
     const size_t per = sf_ks_scratch_words_dev(R);
@@ -193,8 +193,8 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, LC >= 8 ? 2 : 3) k_rows(
     const size_t off_d = S.dst_off + ((size_t)t << (LR + LC)) + (size_t)r0 * g.c;
     constexpr bool DB = sf_rows_double_buffered(LC);
     sf_tw *tw = (sf_tw *)smem_raw;
-    u64 *buf0 = (u64 *)(tw + SF_NB * g.c);
-    u64 *buf1 = DB ? buf0 + tile_words(g.log_c) : buf0;
+    u64 *buf0 = (u64 *)(tw + NB * g.c);
+    u64 *buf1 = DB ? buf0 + SfRow<LC>::WORDS : buf0;
     load_row_tw_t<LR, LC, NT>(tw, INV ? R.rowT_i : R.rowT_f, mod, r0);
     if (DB && sub < B.count) issue_row_tile_t<LC, NT>(buf0, B.scratch + per * sub + off_s);
     sf_cp_commit();
@@ -210,11 +210,11 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, LC >= 8 ? 2 : 3) k_rows(
             sf_cp_wait<0>();
         }
         __syncthreads();
-        if (INV) tile_inverse_t<LC, true, NT>(cur, tw, M.q);
-        else tile_forward_t<LC, true, NT>(cur, tw, M.q);
+        if (INV) row_inverse_t<LC, NT>(cur, tw, M.q);
+        else row_forward_t<LC, NT>(cur, tw, M.q);
         u64 *dst = B.scratch + per * b + off_d;
         #pragma unroll
-        for (int e = threadIdx.x; e < (SF_NB << LC); e += NT) dst[e] = cur[row_slot_t<LC>(e)];
+        for (int e = threadIdx.x; e < SfRow<LC>::ELEMS; e += NT) dst[e] = cur[row_slot_t<LC>(e)];
         __syncthreads();
     }
 }
@@ -312,19 +312,19 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
 // rows, 512 (4 elements per thread, half the accumulator registers, two
 // 16-warp blocks per SM); 256-point rows always run 512.
 template <int LR, int LC, int NT>
-__global__ void __launch_bounds__(NT, NT >= 512 ? (LC >= 8 ? 1 : 2) : 3) k_ks3(SfRing R, SfKsBatch B, int bpg)
+__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) k_ks3(SfRing R, SfKsBatch B, int bpg)
 {
-    constexpr int EPT = (SF_NB << LC) / NT;
+    constexpr int NB = SfRow<LC>::NB, EPT = SfRow<LC>::ELEMS / NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr SfGeoT<LR, LC> g{};
     const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
-    const int m = grp % R.nm, r0 = (grp / R.nm) * SF_NB;
+    const int m = grp % R.nm, r0 = (grp / R.nm) * NB;
     const SfMod M = R.m[m];
     const size_t tile_off = (size_t)r0 * g.c;
-    constexpr bool DB = true;   // registers, not shared memory, bound these kernels to one 512-thread block per SM
+    constexpr bool DB = true;
     sf_tw *tw = (sf_tw *)smem_raw;
-    u64 *buf0 = (u64 *)(tw + SF_NB * g.c);
-    u64 *buf1 = DB ? buf0 + tile_words(g.log_c) : buf0;
+    u64 *buf0 = (u64 *)(tw + NB * g.c);
+    u64 *buf1 = DB ? buf0 + SfRow<LC>::WORDS : buf0;
     load_row_tw_t<LR, LC, NT>(tw, R.rowT_f, m, r0);
     const int n_mine = sub < B.count ? (B.count - sub + bpg - 1) / bpg : 0;
     const int steps = n_mine * R.dnum;
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? (LC >= 8 ? 1 : 2) : 3) k_ks3(S
         }
         __syncthreads();
         const bool own = (m >= j * R.K && m < min((j + 1) * R.K, R.L));
-        if (!own) tile_forward_t<LC, true, NT>(cur, tw, M.q);
+        if (!own) tile_forward_t<LC, true, NT, NB>(cur, tw, M.q);
         const size_t comp = (size_t)R.dnum * 2 * R.nm << (LR + LC);   // companions follow the key values
         const u64 *ka = B.key + ((((size_t)j * 2 + 0) * R.nm + m) << (LR + LC)) + tile_off;
         const u64 *kb = B.key + ((((size_t)j * 2 + 1) * R.nm + m) << (LR + LC)) + tile_off;
@@ -467,19 +467,19 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
 // tiles (double-buffered); ACC and out are read elementwise from global into
 // registers before the row pass.
 template <int LR, int LC>
-__global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 512 ? 1 : 3) k_ks5(SfRing R, SfKsBatch B, int bpg)
+__global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_ks5(SfRing R, SfKsBatch B, int bpg)
 {
-    constexpr int NT = SfThreads<LC>::value, EPT = (SF_NB << LC) / NT;
+    constexpr int NT = SfRow<LC>::NT, NB = SfRow<LC>::NB, EPT = SfRow<LC>::ELEMS / NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr SfGeoT<LR, LC> g{};
     const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
-    const int i = grp % R.L, r0 = (grp / R.L) * SF_NB;
+    const int i = grp % R.L, r0 = (grp / R.L) * NB;
     const SfMod M = R.m[i];
     const size_t tile_off = (size_t)r0 * g.c;
-    const int tw_words = tile_words(g.log_c);
-    constexpr bool DB = true;   // registers, not shared memory, bound these kernels to one 512-thread block per SM
+    const int tw_words = SfRow<LC>::WORDS;
+    constexpr bool DB = true;
     sf_tw *tw = (sf_tw *)smem_raw;
-    u64 *bufs = (u64 *)(tw + SF_NB * g.c);          // 2 conversion tiles (1 when single-buffered)
+    u64 *bufs = (u64 *)(tw + NB * g.c);             // 2 conversion tiles
     load_row_tw_t<LR, LC, NT>(tw, R.rowT_f, i, r0);
     const int n_items = 2 * B.count;
     auto item_src = [&](int it2) -> const u64 * {
@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 
             vo[x] = out[threadIdx.x + x * NT];
         }
         __syncthreads();
-        tile_forward_t<LC, true, NT>(cur, tw, M.q);
+        row_forward_t<LC, NT>(cur, tw, M.q);
         // acc and conv both carry P^-1 already: out += acc - conv, one reduction
 #pragma unroll
         for (int x = 0; x < EPT; ++x) {
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 
 
 static size_t smem_rows(const SfRing &R, int tiles)
 {
-    return sizeof(sf_tw) * SF_NB * R.c + sizeof(u64) * tile_words(R.log_c) * tiles;
+    return sizeof(sf_tw) * sf_row_nb(R.log_c) * R.c + sizeof(u64) * row_tile_words(R.log_c) * tiles;
 }
 
 template <class K>
@@ -576,7 +576,7 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
     const SfRing &R = ctx->ring;
     if (B0.count <= 0) return SF_OK;
     const int maxd = std::min(R.K, R.L);
-    const int rtiles = R.r / SF_NB, ctiles = R.c / SF_NB;
+    const int rtiles = R.r / sf_row_nb(R.log_c), ctiles = R.c / SF_NB;
     const int row_bufs = sf_rows_double_buffered(R.log_c) ? 2 : 1;
     const size_t sm_rows = smem_rows(R, row_bufs);
     const size_t sm2 = sizeof(sf_tw) * 2 * R.nm * R.r + sizeof(u64) * tile_words(R.log_r) * (2 * maxd + 1);
@@ -592,7 +592,7 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
         const int ew_blocks = (R.n + 256 * SF_EW - 1) / (256 * SF_EW);
         const dim3 eg(ew_blocks, R.L, b.count);
         SF_GEO_DISPATCH(R.log_n, {
-            constexpr int NTR = SfThreads<LC>::value, NTC = SfThreads<LR>::value;
+            constexpr int NTR = SfRow<LC>::NT, NTC = SfThreads<LR>::value;
             sf_launch_begin(ctx, SFK_KS_GATHER, st, &ev);
             k_ks_gather<<<eg, 256, 0, st>>>(R, b);
             sf_launch_end(ctx, SFK_KS_GATHER, st, ev);
@@ -676,7 +676,7 @@ sf_status sf_ks_init_attributes()
     const int mx = 227 * 1024;
 #define SF_KS_ATTR(K) SF_CUDA_TRY(cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
 #define SF_KS_ATTRS(LR, LC)                                                                                  \
-    SF_KS_ATTR((k_rows<true, LR, LC>)) SF_KS_ATTR((k_ks2<LR, LC>)) SF_KS_ATTR((k_ks3<LR, LC, SfThreads<LC>::value>)) \
+    SF_KS_ATTR((k_rows<true, LR, LC>)) SF_KS_ATTR((k_ks2<LR, LC>)) SF_KS_ATTR((k_ks3<LR, LC, SfRow<LC>::NT>)) \
     SF_KS_ATTR((k_ks4<LR, LC>)) SF_KS_ATTR((k_ks5<LR, LC>))
     SF_KS_ATTRS(5, 5) SF_KS_ATTRS(5, 6) SF_KS_ATTRS(6, 6) SF_KS_ATTRS(6, 7) SF_KS_ATTRS(7, 7) SF_KS_ATTRS(7, 8)
     SF_KS_ATTRS(8, 8)

@@ -213,12 +213,12 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
 
 // leaf_row: grid (R/16 row tiles, L, slots).  smem: forward row twiddles + 1 tile.
 template <int LR, int LC>
-__global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 512 ? 1 : 3) k_leaf_row(SfRing R, SfLeafParams P)
+__global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_leaf_row(SfRing R, SfLeafParams P)
 {
-    constexpr int NT = SfThreads<LC>::value, EPT = (SF_NB << LC) / NT;
+    constexpr int NT = SfRow<LC>::NT, NB = SfRow<LC>::NB, EPT = SfRow<LC>::ELEMS / NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr SfGeoT<LR, LC> g{};
-    const int r0 = blockIdx.x * SF_NB, i = blockIdx.y;
+    const int r0 = blockIdx.x * NB, i = blockIdx.y;
     const int slot = P.s0 + blockIdx.z * P.s_stride;
     const int o = leaf_output(P, slot);
     const size_t tile_off = (size_t)r0 * g.c;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 
         return;
     }
     sf_tw *tw = (sf_tw *)smem_raw;
-    u64 *sm = (u64 *)(tw + SF_NB * g.c);
+    u64 *sm = (u64 *)(tw + NB * g.c);
     const SfMod M = R.m[i];
     load_row_tw_t<LR, LC, NT>(tw, R.rowT_f, i, r0);
     // per input ciphertext w * ct (w < 68q lazy, ct < q with its Shoup
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(SfThreads<LC>::value, SfThreads<LC>::value >= 
             sm[row_slot_t<LC>(e)] = src[e];
         }
         __syncthreads();
-        tile_forward_t<LC, true, NT>(sm, tw, M.q);
+        row_forward_t<LC, NT>(sm, tw, M.q);
         const size_t comp = (size_t)P.k_in * 2 * R.L << (LR + LC);
         const u64 *ca = P.ct + (((size_t)j * 2 + 0) * R.L + i) * (size_t)(1 << (LR + LC)) + tile_off;
         const u64 *cb = P.ct + (((size_t)j * 2 + 1) * R.L + i) * (size_t)(1 << (LR + LC)) + tile_off;
@@ -295,8 +295,8 @@ sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStre
         SF_GEO_DISPATCH(R.log_n, k_leaf_col<LR, LC><<<dim3(R.c / SF_NB, P.k_in * R.L, c), SfThreads<LR>::value, smem_c, st>>>(R, p););
         sf_launch_end(ctx, SFK_LEAF_COL, st, ev);
         sf_launch_begin(ctx, SFK_LEAF_ROW, st, &ev);
-        const dim3 gr(R.r / SF_NB, R.L, c);
-        SF_GEO_DISPATCH(R.log_n, k_leaf_row<LR, LC><<<gr, SfThreads<LC>::value, smem_r, st>>>(R, p););
+        const dim3 gr(R.r / sf_row_nb(R.log_c), R.L, c);
+        SF_GEO_DISPATCH(R.log_n, k_leaf_row<LR, LC><<<gr, SfRow<LC>::NT, smem_r, st>>>(R, p););
         sf_launch_end(ctx, SFK_LEAF_ROW, st, ev);
     }
     SF_CUDA_TRY(cudaGetLastError());

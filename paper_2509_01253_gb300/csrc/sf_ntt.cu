@@ -32,8 +32,8 @@ __global__ void __launch_bounds__(NT) k_ntt_pass(SfRing R, SfJobList jobs)
             jb.dst[col_gidx(g, c0, e)] = v;
         }
     } else {
-        u64 *s = (u64 *)(tw + SF_NB * g.c);
-        const int r0 = blockIdx.x * SF_NB;
+        u64 *s = (u64 *)(tw + sf_row_nb(g.log_c) * g.c);
+        const int r0 = blockIdx.x * sf_row_nb(g.log_c);
         load_row_tw(tw, INV ? R.rowT_i : R.rowT_f, g, jb.mod, r0);
         const u64 *s0 = src + (size_t)r0 * g.c;
         for (int e = threadIdx.x; e < row_elems(g); e += blockDim.x) s[row_slot(g, e)] = s0[e];
@@ -51,7 +51,10 @@ __global__ void __launch_bounds__(NT) k_ntt_pass(SfRing R, SfJobList jobs)
 
 // dynamic shared memory of the pass kernels
 size_t sf_smem_col(const SfRing &R, int tiles) { return sizeof(sf_tw) * R.r + sizeof(u64) * tile_words(R.log_r) * tiles; }
-size_t sf_smem_row(const SfRing &R, int tiles) { return sizeof(sf_tw) * SF_NB * R.c + sizeof(u64) * tile_words(R.log_c) * tiles; }
+size_t sf_smem_row(const SfRing &R, int tiles)
+{
+    return sizeof(sf_tw) * sf_row_nb(R.log_c) * R.c + sizeof(u64) * row_tile_words(R.log_c) * tiles;
+}
 
 sf_status sf_ntt_jobs(sf_ctx *ctx, const SfPolyJob *h_jobs, int n_jobs, bool inverse, cudaStream_t st)
 {
@@ -61,9 +64,9 @@ sf_status sf_ntt_jobs(sf_ctx *ctx, const SfPolyJob *h_jobs, int n_jobs, bool inv
         int cnt = std::min(SF_MAX_JOBS, n_jobs - off);
         SfJobList jl;
         for (int i = 0; i < cnt; ++i) jl.j[i] = h_jobs[off + i];
-        dim3 gc(R.c / SF_TC, cnt), gr(R.r / SF_TR, cnt);
+        dim3 gc(R.c / SF_TC, cnt), gr(R.r / sf_row_nb(R.log_c), cnt);
         cudaEvent_t ev;
-        const int ntc = sf_tile_threads(R.log_r), ntr = sf_tile_threads(R.log_c);
+        const int ntc = sf_tile_threads(R.log_r), ntr = SF_THREADS;   // row tiles: 256 threads
         if (!inverse) {
             sf_launch_begin(ctx, SFK_NTT_FWD_COL, st, &ev);
             SF_NT_DISPATCH(ntc, k_ntt_pass<false, true, NT><<<gc, NT, smem_col, st>>>(R, jl););

@@ -10,19 +10,21 @@
 // with distance < C stay inside one row ("row pass").  Forward = column pass
 // then row pass; inverse = row pass then column pass.
 //
-// A tile holds SF_NB = 16 sub-transforms (16 columns of R elements, or 16
-// rows of C elements) in shared memory as [k][b]: element k of sub-transform
-// b sits at k*SF_PAD + b with SF_PAD = 17.  With that stride the coalesced
-// global loads of both tile kinds and every butterfly sweep (consecutive
-// threads on consecutive b) are free of bank conflicts.
+// A tile holds NB sub-transforms (16 columns of R elements, or NB rows of C
+// elements: NB = 16, or 8 for 256-point rows) in shared memory as [k][b]:
+// element k of sub-transform b sits at k*(NB + 1) + b.  With that stride the
+// coalesced global loads of both tile kinds are free of bank conflicts, and so
+// is every butterfly sweep of a 16-wide tile (consecutive threads on
+// consecutive b); an 8-wide tile puts two units in a half-warp, which share
+// one bank pair once.
 //
 // Twiddles are staged in shared memory as (w, w') pairs, w' = floor(w 2^64/q)
 // (Shoup).  Local stage with m groups, group g, uses local index k = m + g:
 //  * column pass: the global index is m + g for every column, so the tile
 //    reads colT[k] (k < R), one table shared by all 16 columns;
 //  * row pass: the global index is m*(R + r) + g for row r, so the host
-//    stores, per 16-row tile, rowT[tile][k][b] = psi_brev[m(k)(R + 16 tile + b)
-//    + k - m(k)] (m(k) the largest power of two <= k); the tile's 16*C pairs
+//    stores, per NB-row tile, rowT[tile][k][b] = psi_brev[m(k)(R + NB tile + b)
+//    + k - m(k)] (m(k) the largest power of two <= k); the tile's NB*C pairs
 //    are one contiguous chunk copied straight into shared memory.
 // Each sweep runs 2 or 3 stages (radix 4 / radix 8) on register-resident
 // units with lazy Harvey butterflies.
@@ -35,14 +37,14 @@
 #define SF_TC SF_NB
 #define SF_TR SF_NB
 #define SF_THREADS 256
-// threads per block of a kernel whose tiles hold sub-transforms of 2^log_s
-// points: 256 (8 warps) up to 128 points, 512 for 256 points, so that every
-// tile size gives each thread the same 8 elements
+// threads per block of a kernel whose column tiles (16 columns) hold
+// sub-transforms of 2^log_s points: 256 (8 warps) up to 128 points, 512 for
+// 256 points, so that every thread holds 8 elements; row tiles always run
+// 256 threads (their width halves instead, see SfRow)
 __host__ __device__ __forceinline__ int sf_tile_threads(int log_s) { return log_s >= 8 ? 512 : SF_THREADS; }
-// The generic row pass double-buffers its tiles with cp.async, except for
-// 256-point rows: there the staged twiddles (64 KiB) and one tile already
-// take 98 KiB, and a single buffer lets two 16-warp blocks share an SM.
-__host__ __device__ constexpr bool sf_rows_double_buffered(int log_c) { return log_c < 8; }
+// Row passes double-buffer their tiles with cp.async: a row tile (at most
+// 2048 residues) and its staged twiddles leave room for three blocks per SM.
+__host__ __device__ constexpr bool sf_rows_double_buffered(int) { return true; }
 
 // runs the statements with the compile-time block size NT = nt (256 or 512)
 #define SF_NT_DISPATCH(nt, ...)          \
@@ -64,15 +66,19 @@ typedef ulonglong2 sf_tw;   // (w, w')
 
 // elements of a tile buffer in shared memory (S rows of SF_PAD words)
 __host__ __device__ __forceinline__ int tile_words(int log_s) { return (1 << log_s) * SF_PAD; }
+// words of a row tile buffer (2^log_c rows of sf_row_nb(log_c) + 1 words)
+__host__ __device__ __forceinline__ int row_tile_words(int log_c) { return (1 << log_c) * (sf_row_nb(log_c) + 1); }
 
 // One sweep of R_ST consecutive stages over every unit of the tile.
 // Forward: halves H0, H0/2, ..., H0 >> (R_ST-1).  Inverse: halves H0, ..., H0 << (R_ST-1).
-template <int LOG_S, int LOG_H0, int R_ST, bool INV, bool ROWTW, int NT>
+template <int LOG_S, int LOG_H0, int R_ST, bool INV, bool ROWTW, int NT, int NB = SF_NB>
 __device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
 {
     constexpr int S = 1 << LOG_S;
     constexpr int U = 1 << R_ST;
-    constexpr int UNITS = SF_NB * S / U;
+    constexpr int UNITS = NB * S / U;
+    constexpr int PAD = NB + 1;
+    constexpr int LOG_NB = NB == 8 ? 3 : 4;
     constexpr int ITER = (UNITS + NT - 1) / NT;
     constexpr int LOG_STEP = INV ? LOG_H0 : (LOG_H0 - (R_ST - 1));
     constexpr int LOG_BLK = INV ? (LOG_H0 + R_ST) : (LOG_H0 + 1);
@@ -81,14 +87,14 @@ __device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
     for (int it = 0; it < ITER; ++it) {
         const int idx = threadIdx.x + it * NT;
         if ((UNITS % NT) != 0 && idx >= UNITS) break;
-        const int b = idx & (SF_NB - 1);
-        const int u = idx >> 4;
+        const int b = idx & (NB - 1);
+        const int u = idx >> LOG_NB;
         const int o = u & ((1 << LOG_STEP) - 1);
         const int blk = u >> LOG_STEP;
         const int first = (blk << LOG_BLK) + o;
         u64 x[U];
 #pragma unroll
-        for (int t = 0; t < U; ++t) x[t] = s[(first + (t << LOG_STEP)) * SF_PAD + b];
+        for (int t = 0; t < U; ++t) x[t] = s[(first + (t << LOG_STEP)) * PAD + b];
 #pragma unroll
         for (int sg = 0; sg < R_ST; ++sg) {
             const int d = INV ? (1 << sg) : (1 << (R_ST - 1 - sg));
@@ -97,68 +103,68 @@ __device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
             for (int t = 0; t < U; ++t) {
                 if (t & d) continue;
                 const int g = INV ? ((blk << (R_ST - sg - 1)) + (t >> (sg + 1))) : ((blk << sg) + (t >> (R_ST - sg)));
-                const sf_tw w = ROWTW ? tw[(m + g) * SF_NB + b] : tw[m + g];
+                const sf_tw w = ROWTW ? tw[(m + g) * NB + b] : tw[m + g];
                 if (INV) sf_bfly_gs(x[t], x[t + d], w.x, w.y, q, two_q);
                 else sf_bfly_ct(x[t], x[t + d], w.x, w.y, q, two_q);
             }
         }
 #pragma unroll
-        for (int t = 0; t < U; ++t) s[(first + (t << LOG_STEP)) * SF_PAD + b] = x[t];
+        for (int t = 0; t < U; ++t) s[(first + (t << LOG_STEP)) * PAD + b] = x[t];
     }
     __syncthreads();
 }
 
-// Forward stages of all 16 sub-transforms of size 2^LOG_S; values in [0, 4q).
+// Forward stages of all NB sub-transforms of size 2^LOG_S; values in [0, 4q).
 // 128-point sub-transforms in 512-thread blocks (4 elements per thread) run
 // radix-4 sweeps so that every thread holds one unit.
-template <int LOG_S, bool ROWTW, int NT>
+template <int LOG_S, bool ROWTW, int NT, int NB = SF_NB>
 __device__ __forceinline__ void tile_forward_t(u64 *s, const sf_tw *tw, u64 q)
 {
     if constexpr (LOG_S == 7 && NT == 512) {
-        tile_sweep<7, 6, 2, false, ROWTW, NT>(s, tw, q);
-        tile_sweep<7, 4, 2, false, ROWTW, NT>(s, tw, q);
-        tile_sweep<7, 2, 2, false, ROWTW, NT>(s, tw, q);
-        tile_sweep<7, 0, 1, false, ROWTW, NT>(s, tw, q);
+        tile_sweep<7, 6, 2, false, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<7, 4, 2, false, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<7, 2, 2, false, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<7, 0, 1, false, ROWTW, NT, NB>(s, tw, q);
     } else if constexpr (LOG_S == 5) {
-        tile_sweep<5, 4, 3, false, ROWTW, NT>(s, tw, q);
-        tile_sweep<5, 1, 2, false, ROWTW, NT>(s, tw, q);
+        tile_sweep<5, 4, 3, false, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<5, 1, 2, false, ROWTW, NT, NB>(s, tw, q);
     } else if constexpr (LOG_S == 6) {
-        tile_sweep<6, 5, 3, false, ROWTW, NT>(s, tw, q);
-        tile_sweep<6, 2, 3, false, ROWTW, NT>(s, tw, q);
+        tile_sweep<6, 5, 3, false, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<6, 2, 3, false, ROWTW, NT, NB>(s, tw, q);
     } else if constexpr (LOG_S == 7) {
-        tile_sweep<7, 6, 3, false, ROWTW, NT>(s, tw, q);
-        tile_sweep<7, 3, 2, false, ROWTW, NT>(s, tw, q);
-        tile_sweep<7, 1, 2, false, ROWTW, NT>(s, tw, q);
+        tile_sweep<7, 6, 3, false, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<7, 3, 2, false, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<7, 1, 2, false, ROWTW, NT, NB>(s, tw, q);
     } else {
-        tile_sweep<8, 7, 3, false, ROWTW, NT>(s, tw, q);
-        tile_sweep<8, 4, 3, false, ROWTW, NT>(s, tw, q);
-        tile_sweep<8, 1, 2, false, ROWTW, NT>(s, tw, q);
+        tile_sweep<8, 7, 3, false, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<8, 4, 3, false, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<8, 1, 2, false, ROWTW, NT, NB>(s, tw, q);
     }
 }
 
 // Inverse stages (no N^-1 factor); inputs and values in [0, 4q).
-template <int LOG_S, bool ROWTW, int NT>
+template <int LOG_S, bool ROWTW, int NT, int NB = SF_NB>
 __device__ __forceinline__ void tile_inverse_t(u64 *s, const sf_tw *tw, u64 q)
 {
     if constexpr (LOG_S == 7 && NT == 512) {
-        tile_sweep<7, 0, 2, true, ROWTW, NT>(s, tw, q);
-        tile_sweep<7, 2, 2, true, ROWTW, NT>(s, tw, q);
-        tile_sweep<7, 4, 2, true, ROWTW, NT>(s, tw, q);
-        tile_sweep<7, 6, 1, true, ROWTW, NT>(s, tw, q);
+        tile_sweep<7, 0, 2, true, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<7, 2, 2, true, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<7, 4, 2, true, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<7, 6, 1, true, ROWTW, NT, NB>(s, tw, q);
     } else if constexpr (LOG_S == 5) {
-        tile_sweep<5, 0, 2, true, ROWTW, NT>(s, tw, q);
-        tile_sweep<5, 2, 3, true, ROWTW, NT>(s, tw, q);
+        tile_sweep<5, 0, 2, true, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<5, 2, 3, true, ROWTW, NT, NB>(s, tw, q);
     } else if constexpr (LOG_S == 6) {
-        tile_sweep<6, 0, 3, true, ROWTW, NT>(s, tw, q);
-        tile_sweep<6, 3, 3, true, ROWTW, NT>(s, tw, q);
+        tile_sweep<6, 0, 3, true, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<6, 3, 3, true, ROWTW, NT, NB>(s, tw, q);
     } else if constexpr (LOG_S == 7) {
-        tile_sweep<7, 0, 2, true, ROWTW, NT>(s, tw, q);
-        tile_sweep<7, 2, 2, true, ROWTW, NT>(s, tw, q);
-        tile_sweep<7, 4, 3, true, ROWTW, NT>(s, tw, q);
+        tile_sweep<7, 0, 2, true, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<7, 2, 2, true, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<7, 4, 3, true, ROWTW, NT, NB>(s, tw, q);
     } else {
-        tile_sweep<8, 0, 2, true, ROWTW, NT>(s, tw, q);
-        tile_sweep<8, 2, 3, true, ROWTW, NT>(s, tw, q);
-        tile_sweep<8, 5, 3, true, ROWTW, NT>(s, tw, q);
+        tile_sweep<8, 0, 2, true, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<8, 2, 3, true, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<8, 5, 3, true, ROWTW, NT, NB>(s, tw, q);
     }
 }
 
@@ -190,7 +196,7 @@ __device__ __forceinline__ void row_forward(u64 *s, const sf_tw *tw, int log_c, 
     case 5: tile_forward_t<5, true, NT>(s, tw, q); break;
     case 6: tile_forward_t<6, true, NT>(s, tw, q); break;
     case 7: tile_forward_t<7, true, NT>(s, tw, q); break;
-    default: tile_forward_t<8, true, NT>(s, tw, q); break;
+    default: tile_forward_t<8, true, NT, 8>(s, tw, q); break;
     }
 }
 template <int NT = SF_THREADS>
@@ -200,7 +206,7 @@ __device__ __forceinline__ void row_inverse(u64 *s, const sf_tw *tw, int log_c, 
     case 5: tile_inverse_t<5, true, NT>(s, tw, q); break;
     case 6: tile_inverse_t<6, true, NT>(s, tw, q); break;
     case 7: tile_inverse_t<7, true, NT>(s, tw, q); break;
-    default: tile_inverse_t<8, true, NT>(s, tw, q); break;
+    default: tile_inverse_t<8, true, NT, 8>(s, tw, q); break;
     }
 }
 
@@ -212,12 +218,15 @@ __device__ __forceinline__ void row_inverse(u64 *s, const sf_tw *tw, int log_c, 
 __device__ __forceinline__ int col_elems(const SfGeo &g) { return g.r * SF_NB; }
 __device__ __forceinline__ int col_gidx(const SfGeo &g, int c0, int e) { return (e >> 4) * g.c + c0 + (e & 15); }
 __device__ __forceinline__ int col_slot(int e) { return (e >> 4) * SF_PAD + (e & 15); }
-// row tile r0..r0+15: global (r0 + b)*C + k, e = b*C + k
-__device__ __forceinline__ int row_elems(const SfGeo &g) { return SF_NB * g.c; }
-__device__ __forceinline__ int row_slot(const SfGeo &g, int e) { return (e & (g.c - 1)) * SF_PAD + (e >> g.log_c); }
+// row tile r0..r0+NB-1: global (r0 + b)*C + k, e = b*C + k
+__device__ __forceinline__ int row_elems(const SfGeo &g) { return sf_row_nb(g.log_c) * g.c; }
+__device__ __forceinline__ int row_slot(const SfGeo &g, int e)
+{
+    return (e & (g.c - 1)) * (sf_row_nb(g.log_c) + 1) + (e >> g.log_c);
+}
 
-// Stage twiddles: column table (R pairs) or the row table of tile r0/16
-// (16*C pairs), for modulus `mod`; tables are [nm][...] in global memory.
+// Stage twiddles: column table (R pairs) or the row table of tile r0/NB
+// (NB*C pairs), for modulus `mod`; tables are [nm][...] in global memory.
 __device__ __forceinline__ void load_col_tw(sf_tw *dst, const sf_tw *__restrict__ table, const SfGeo &g, int mod)
 {
     const sf_tw *src = table + (size_t)mod * g.r;
@@ -226,7 +235,7 @@ __device__ __forceinline__ void load_col_tw(sf_tw *dst, const sf_tw *__restrict_
 __device__ __forceinline__ void load_row_tw(sf_tw *dst, const sf_tw *__restrict__ table, const SfGeo &g, int mod, int r0)
 {
     const sf_tw *src = table + ((size_t)mod << g.log_n) + (size_t)r0 * g.c;
-    for (int k = threadIdx.x; k < SF_NB * g.c; k += blockDim.x) dst[k] = src[k];
+    for (int k = threadIdx.x; k < sf_row_nb(g.log_c) * g.c; k += blockDim.x) dst[k] = src[k];
 }
 
 // ---- compile-time geometry -------------------------------------------------
@@ -245,16 +254,27 @@ struct SfThreads {
     static constexpr int value = LOG_S >= 8 ? 512 : SF_THREADS;
 };
 
+// Row tiles: NB rows of 2^LC points (NB = 16, or 8 for 256-point rows),
+// always processed by 256-thread blocks (NB 2^LC / 256 residues per thread).
 template <int LC>
-__device__ __forceinline__ int row_slot_t(int e) { return (e & ((1 << LC) - 1)) * SF_PAD + (e >> LC); }
+struct SfRow {
+    static constexpr int NB = LC >= 8 ? 8 : 16;
+    static constexpr int PAD = NB + 1;
+    static constexpr int NT = SF_THREADS;
+    static constexpr int ELEMS = NB << LC;
+    static constexpr int WORDS = (1 << LC) * PAD;   // words of one tile buffer
+};
+
+template <int LC>
+__device__ __forceinline__ int row_slot_t(int e) { return (e & ((1 << LC) - 1)) * SfRow<LC>::PAD + (e >> LC); }
 template <int LC>
 __device__ __forceinline__ int col_gidx_t(int c0, int e) { return ((e >> 4) << LC) + c0 + (e & 15); }
 
-// row tile (16 rows of C) global -> shared via 8-byte cp.async
+// row tile (NB rows of C) global -> shared via 8-byte cp.async
 template <int LC, int NT>
 __device__ __forceinline__ void issue_row_tile_t(u64 *dst, const u64 *src)
 {
-    constexpr int E = (SF_NB << LC) / NT;
+    constexpr int E = SfRow<LC>::ELEMS / NT;
 #pragma unroll
     for (int x = 0; x < E; ++x) {
         const int e = threadIdx.x + x * NT;
@@ -273,11 +293,11 @@ __device__ __forceinline__ void issue_col_tile_t(u64 *dst, const u64 *src, int c
     for (int x = 0; x < E; ++x) sf_cp8(d0 + x * (NT / 16) * SF_PAD, s0 + (size_t)x * (NT / 16) * (1 << LC));
 }
 
-// shared row tile -> global (16 rows of C), with an optional per-value map
+// shared row tile -> global (NB rows of C), with an optional per-value map
 template <int LC, int NT, class F>
 __device__ __forceinline__ void store_row_tile_t(u64 *dst, const u64 *src, F f)
 {
-    constexpr int E = (SF_NB << LC) / NT;
+    constexpr int E = SfRow<LC>::ELEMS / NT;
 #pragma unroll
     for (int x = 0; x < E; ++x) {
         const int e = threadIdx.x + x * NT;
@@ -296,14 +316,26 @@ __device__ __forceinline__ void store_col_tile_t(u64 *dst, const u64 *src, int c
     for (int x = 0; x < E; ++x) g0[(size_t)x * (NT / 16) * (1 << LC)] = f(s0[x * (NT / 16) * SF_PAD]);
 }
 
-// twiddles of the row tile starting at row r0 for modulus mod ([nm][R/16][C][16] table)
+// twiddles of the row tile starting at row r0 for modulus mod ([nm][R/NB][C][NB] table)
 template <int LR, int LC, int NT>
 __device__ __forceinline__ void load_row_tw_t(sf_tw *dst, const sf_tw *__restrict__ table, int mod, int r0)
 {
-    constexpr int E = (SF_NB << LC) / NT;
+    constexpr int E = SfRow<LC>::ELEMS / NT;
     const sf_tw *src = table + ((size_t)mod << (LR + LC)) + ((size_t)r0 << LC);
 #pragma unroll
     for (int x = 0; x < E; ++x) dst[threadIdx.x + x * NT] = src[threadIdx.x + x * NT];
+}
+
+// forward / inverse row pass of a row tile (its width from the row length)
+template <int LC, int NT>
+__device__ __forceinline__ void row_forward_t(u64 *s, const sf_tw *tw, u64 q)
+{
+    tile_forward_t<LC, true, NT, SfRow<LC>::NB>(s, tw, q);
+}
+template <int LC, int NT>
+__device__ __forceinline__ void row_inverse_t(u64 *s, const sf_tw *tw, u64 q)
+{
+    tile_inverse_t<LC, true, NT, SfRow<LC>::NB>(s, tw, q);
 }
 
 // column twiddles (R pairs) of modulus mod

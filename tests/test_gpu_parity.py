@@ -653,9 +653,15 @@ def test_extract_and_shuffle(oracle):
                     want = oracle.monomial_mul(cts[0, part, li], -i, q)
                     want = np.array([oracle.lib().or_mulmod(int(v), ninv, q) for v in want], dtype=np.uint64)
                     assert (got[part, li] == want).all()
-        with pytest.raises(sf.SafhireError) as e:
-            sf.sf_extract(s.ctx, d_ct, 0, 1, None, out)
-        assert e.value.status == sf.SF_ENOTSUP
+        # gamma = 1 is gamma = 0 at t = 2 (K_1 = K_0); gamma = 2 needs the power; gamma 3 does not exist
+        out1 = dev_zeros(2, L, s.n)
+        sf.sf_extract(s.ctx, d_ct, 5, 0, None, out)
+        sf.sf_extract(s.ctx, d_ct, 5, 1, None, out1)
+        assert (from_dev(out1) == from_dev(out)).all()
+        for gamma in (2, 3):
+            with pytest.raises(sf.SafhireError) as e:
+                sf.sf_extract(s.ctx, d_ct, 0, gamma, None, out)
+            assert e.value.status == sf.SF_EINVAL
         perm = np.array([2, 0, 3, 1], dtype=np.uint32)
         sh = dev_zeros(4, 2, L, s.n)
         sf.sf_shuffle_cts(s.ctx, perm, d_ct, sh, 4)
