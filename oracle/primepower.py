@@ -1,0 +1,219 @@
+"""Plain CPU oracle for the paper's prime-power cyclotomic rings (Sec. 2.1,
+2.3, 2.4; Table 2 lists M in {3^7, 7^4, 5^5}).
+
+TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``: only ``tests/`` may
+import it; the product path never does.  Everything here is exact (Python
+integers, and fractions where the dual basis needs them) and follows the
+definitions literally:
+
+* K = Q[X] / Phi_M(X), M = t^alpha with t prime, N = phi(M) = (t - 1) t^(alpha-1);
+  Phi_M(X) = sum_{k < t} X^(k M / t), so X^N = -sum_{k < t-1} X^(k M / t).
+* tau_d: P(X) -> P(X^d) mod Phi_M for gcd(d, M) = 1 (Sec. 2.2).
+* Tr(P) = sum over gcd(d, M) = 1 of tau_d(P) (Sec. 2.3), and the partial
+  traces Tr_{K / K_i} over Gal(K / K_i) = {d = 1 mod t^i}, K_i = Q(zeta_{t^i}).
+* The tower evaluation of the full trace (Sec. 2.3): for i = alpha-1 down to
+  1 the step Tr_{K_{i+1} / K_i} sums the t powers of tau_{1 + t^i} (t - 1
+  automorphisms each), then Tr_{K_1 / K_0} over the cyclic group
+  (Z / tZ)^* is taken one prime factor l of t - 1 at a time, each step
+  summing l powers of one automorphism (l - 1 of them): in all
+  (alpha - 1)(t - 1) + sum_{l in omega(t - 1)} (l - 1) automorphisms.
+* The dual basis Omega_i^* of the power basis X^i for the pairing
+  <P, Q> = Tr(P Q-bar), Q-bar(X) = Q(X^(M-1)), so that coefficient i of m is
+  Tr(m Omega_i^*-bar) (Sec. 4.4), and Lemma 1's partial-trace rows.
+"""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+
+
+def prime_factors(x: int) -> list:
+    """Prime factors of x with multiplicity (omega_x in Sec. 2.3)."""
+    out, d = [], 2
+    while d * d <= x:
+        while x % d == 0:
+            out.append(d)
+            x //= d
+        d += 1
+    if x > 1:
+        out.append(x)
+    return out
+
+
+class Ring:
+    """K = Q[X] / Phi_M(X), M = t^alpha, elements as length-N coefficient lists
+    (Python ints or Fractions)."""
+
+    def __init__(self, t: int, alpha: int):
+        assert prime_factors(t) == [t] and alpha >= 1
+        self.t, self.alpha = t, alpha
+        self.M = t ** alpha
+        self.m = self.M // t                       # Phi_M(X) = Phi_t(X^m)
+        self.N = (t - 1) * self.m                  # phi(M)
+
+    # ---------------------------------------------------------- reduction
+    def reduce(self, coeffs) -> list:
+        """A polynomial of any degree -> its residue mod Phi_M: first mod
+        X^M - 1 (Phi_M divides it), then every X^e with e >= N is replaced by
+        -sum_{k < t-1} X^(e - N + k m)."""
+        c = [0] * self.M
+        for e, v in enumerate(coeffs):
+            c[e % self.M] += v
+        for e in range(self.M - 1, self.N - 1, -1):
+            v = c[e]
+            if v:
+                c[e] = 0
+                for k in range(self.t - 1):
+                    c[e - self.N + k * self.m] -= v
+        return c[:self.N]
+
+    def monomial(self, e: int) -> list:
+        """X^e (any integer e; X^M = 1)."""
+        c = [0] * self.M
+        c[e % self.M] = 1
+        return self.reduce(c)
+
+    # --------------------------------------------------------- arithmetic
+    def add(self, a, b) -> list:
+        return [x + y for x, y in zip(a, b)]
+
+    def scale(self, a, c) -> list:
+        return [c * x for x in a]
+
+    def mul(self, a, b) -> list:
+        """Schoolbook product, then reduction mod Phi_M."""
+        prod = [0] * (len(a) + len(b) - 1)
+        for i, x in enumerate(a):
+            if x:
+                for j, y in enumerate(b):
+                    prod[i + j] += x * y
+        return self.reduce(prod)
+
+    def mod(self, a, q: int) -> list:
+        return [x % q for x in a]
+
+    # --------------------------------------------------------- Galois group
+    def units(self) -> list:
+        """(Z / MZ)^*: the automorphism indices d of Sec. 2.2."""
+        return [d for d in range(1, self.M) if math.gcd(d, self.M) == 1]
+
+    def automorphism(self, a, d: int) -> list:
+        """tau_d(P) = P(X^d) mod Phi_M, gcd(d, M) = 1."""
+        assert math.gcd(d, self.M) == 1
+        c = [0] * self.M
+        for i, v in enumerate(a):
+            c[i * d % self.M] += v
+        return self.reduce(c)
+
+    def conj(self, a) -> list:
+        """P-bar(X) = P(X^(M-1)) (Sec. 4.4)."""
+        return self.automorphism(a, self.M - 1)
+
+    def trace(self, a) -> list:
+        """Tr(P) = sum over gcd(d, M) = 1 of P(X^d) mod Phi_M (Sec. 2.3, the definition)."""
+        acc = [0] * self.N
+        for d in self.units():
+            acc = self.add(acc, self.automorphism(a, d))
+        return acc
+
+    def partial_trace(self, a, i: int) -> list:
+        """Tr_{K / K_i}: the sum over Gal(K / K_i) = {d = 1 mod t^i} (by definition)."""
+        acc = [0] * self.N
+        for d in self.units():
+            if d % (self.t ** i) == 1 % (self.t ** i):
+                acc = self.add(acc, self.automorphism(a, d))
+        return acc
+
+    def primitive_root(self) -> int:
+        """A generator of the cyclic group (Z / MZ)^* (t odd)."""
+        assert self.t > 2
+        n = self.N
+        fac = sorted(set(prime_factors(n)))
+        for g in range(2, self.M):
+            if math.gcd(g, self.M) == 1 and all(pow(g, n // f, self.M) != 1 for f in fac):
+                return g
+        raise ValueError("no primitive root")
+
+    def tower_trace(self, a, gamma: int = 0, counter: list | None = None) -> list:
+        """The full trace by the tower of Sec. 2.3 (t odd), or, with gamma >= 1,
+        only Tr_{K / K_gamma} (the levels the server still computes when the
+        client supplied Tr_{K_gamma / K_0}).  counter[0] is incremented once
+        per automorphism (one key switch each on ciphertexts)."""
+        t, M = self.t, self.M
+
+        def step(x, h, length):
+            # sum_{k < length} tau_h^k(x), with length - 1 automorphisms
+            acc, cur = list(x), list(x)
+            for _ in range(length - 1):
+                cur = self.automorphism(cur, h)
+                if counter is not None:
+                    counter[0] += 1
+                acc = self.add(acc, cur)
+            return acc
+
+        x = list(a)
+        # Tr_{K_{i+1} / K_i} for i = alpha - 1 .. max(gamma, 1): the subgroup
+        # {d = 1 mod t^i} / {d = 1 mod t^(i+1)} is cyclic of order t,
+        # generated by 1 + t^i
+        for i in range(self.alpha - 1, max(gamma, 1) - 1, -1):
+            x = step(x, (1 + t ** i) % M, t)
+        if gamma >= 1:
+            return x
+        # Tr_{K_1 / K_0}: (Z / tZ)^* is cyclic of order t - 1, generated by a
+        # primitive root g mod M; it is taken one prime factor l of t - 1 at a
+        # time
+        g = self.primitive_root()
+        rest = t - 1
+        for l in prime_factors(t - 1):
+            # (the sum over a cyclic group of order n factors as
+            # prod_i sum_{j < l_i} g^(j n / (l_1 ... l_i))): h = g^rest acts
+            # on K_1 with order l
+            rest //= l
+            x = step(x, pow(g, rest, M), l)
+        return x
+
+    def tower_ks_count(self, gamma: int = 0) -> int:
+        """Automorphisms (key switches) of tower_trace: (alpha - 1)(t - 1)
+        levels above K_1 (fewer when gamma > 1) plus sum (l - 1) over the
+        prime factors of t - 1 when gamma = 0 (Sec. 2.3)."""
+        top = (self.alpha - max(gamma, 1)) * (self.t - 1)
+        return top + (sum(l - 1 for l in prime_factors(self.t - 1)) if gamma == 0 else 0)
+
+    # --------------------------------------------------------- dual basis
+    def trace_of_monomial(self, j: int) -> int:
+        """Tr(X^j) by the definition (sum of the automorphisms of X^j), read at
+        coefficient 0 (the trace of X^j is a rational constant)."""
+        tr = self.trace(self.monomial(j))
+        assert all(v == 0 for v in tr[1:])
+        return tr[0]
+
+    def dual_basis(self) -> list:
+        """Omega_i^* for 0 <= i < N: Tr(X^k Omega_i^*-bar) = [k = i] for k < N.
+        Written Omega_i^*-bar = sum_l c_l X^l, the condition is
+        sum_l c_l Tr(X^(k + l)) = [k = i]: an N x N linear system in exact
+        rationals (Gauss-Jordan).  Returns Omega_i^* (not its conjugate)."""
+        N = self.N
+        tr = [self.trace_of_monomial(j) for j in range(2 * N)]
+        A = [[Fraction(tr[k + l]) for l in range(N)] for k in range(N)]
+        inv = _invert(A)
+        out = []
+        for i in range(N):
+            cbar = [inv[l][i] for l in range(N)]     # column i: solves A c = e_i
+            out.append(self.conj(cbar))
+        return out
+
+
+def _invert(A):
+    """Inverse of a square matrix of Fractions (Gauss-Jordan)."""
+    n = len(A)
+    M = [list(row) + [Fraction(int(i == j)) for j in range(n)] for i, row in enumerate(A)]
+    for col in range(n):
+        piv = next(r for r in range(col, n) if M[r][col] != 0)
+        M[col], M[piv] = M[piv], M[col]
+        p = M[col][col]
+        M[col] = [v / p for v in M[col]]
+        for r in range(n):
+            if r != col and M[r][col] != 0:
+                f = M[r][col]
+                M[r] = [a - f * b for a, b in zip(M[r], M[col])]
+    return [row[n:] for row in M]
