@@ -620,15 +620,40 @@ class NetworkWorkload:
             self.sos.append(so)
             self.k_ins.append(info["k_in"])
             self.caps.append(info["n_groups"])
+        self.layer_of = list(range(len(self.net.rounds)))   # input slot -> round
+        self.x_seed_of = [seed + 100 + r for r in range(len(self.net.rounds))]   # input slot -> input seed
         self.ct_bytes = 2 * self.L * self.n * 8
 
+    def add_requests(self, r: int, copies: int):
+        """copies more encrypted inputs of round r, as if from other requests
+        (fresh inputs and encryption seeds under the same client key); their
+        slots are appended to the round lists (weights shared with round r)."""
+        sf, torch = self.sf, self.torch
+        info = self.net.infos[r]
+        for c in range(copies):
+            x_seed = self._seed + 7000 + 31 * r + c
+            self.x_seed_of.append(x_seed)
+            x = np.random.default_rng(x_seed).uniform(0.0, 1.0, info["E_in"])
+            sp = self.sps[r]
+            xs = x if sp is None else x[sp.astype(np.int64)]
+            d_in = torch.empty_like(self.d_ins[r])
+            sf.sf_encrypt(self.ctx, self.sk, sf.sf_encode_input(xs, self.ps.delta), self._seed + 9000 + c, d_in,
+                          info["k_in"])
+            self.d_ins.append(d_in)
+            self.d_outs.append(torch.empty_like(self.d_outs[r]))
+            self.sps.append(sp)
+            self.sos.append(self.sos[r])
+            self.k_ins.append(info["k_in"])
+            self.caps.append(info["n_groups"])
+            self.layer_of.append(r)
+
     def per_layer(self, r: int):
-        self.sf.sf_eval_linear_layer(self.ctx, self.net.layers[r], self.rk, self.d_ins[r], self.k_ins[r], self.sps[r],
-                                     self.sos[r], self.d_outs[r], self.caps[r], self.stream)
+        self.sf.sf_eval_linear_layer(self.ctx, self.net.layers[self.layer_of[r]], self.rk, self.d_ins[r], self.k_ins[r],
+                                     self.sps[r], self.sos[r], self.d_outs[r], self.caps[r], self.stream)
 
     def batched(self, idx=None):
-        idx = list(range(len(self.net.rounds))) if idx is None else idx
-        return self.sf.sf_eval_layers(self.ctx, [self.net.layers[r] for r in idx], [self.rk] * len(idx),
+        idx = list(range(len(self.d_ins))) if idx is None else idx
+        return self.sf.sf_eval_layers(self.ctx, [self.net.layers[self.layer_of[r]] for r in idx], [self.rk] * len(idx),
                                       [self.d_ins[r] for r in idx], [self.k_ins[r] for r in idx],
                                       [self.sps[r] for r in idx], [self.sos[r] for r in idx],
                                       [self.d_outs[r] for r in idx], [self.caps[r] for r in idx], self.stream)
@@ -648,20 +673,21 @@ class NetworkWorkload:
         sf.sf_params_destroy(self.params)
         self.d_ins = self.d_outs = []
 
-    def max_err(self, rounds) -> float:
-        """Max |decoded - float64| over every output of the given rounds."""
+    def max_err(self, slots) -> float:
+        """Max |decoded - float64| over every output of the given input slots."""
         from paper_2509_01253_gb300 import network as nw
         sf = self.sf
         worst = 0.0
-        for r in rounds:
+        for k in slots:
+            r = self.layer_of[k]
             info = self.net.infos[r]
             res = np.zeros((info["n_groups"], self.L, self.n), dtype=np.uint64)
-            sf.sf_decrypt(self.ctx, self.sk, self.d_outs[r], info["n_groups"], res, self.stream)
+            sf.sf_decrypt(self.ctx, self.sk, self.d_outs[k], info["n_groups"], res, self.stream)
             vals = nw.decode_outputs(self.net, r, res)
-            x = np.random.default_rng(self._seed + 100 + r).uniform(0.0, 1.0, info["E_in"])
+            x = np.random.default_rng(self.x_seed_of[k]).uniform(0.0, 1.0, info["E_in"])
             ref = nw.round_float_reference(self.net, r, x)
-            if self.sos[r] is not None:
-                ref = ref[self.sos[r].astype(np.int64)]
+            if self.sos[k] is not None:
+                ref = ref[self.sos[k].astype(np.int64)]
             worst = max(worst, float(np.abs(vals - ref).max()))
         return worst
 
@@ -864,41 +890,50 @@ def serving_record(local: int, rate: float = 0.3, duration: float = 30.0, drain:
 BATCH_ROUNDS = ["s3b0c1", "s3b0c2", "s3b1c1", "s3b1c2", "fc"]
 
 
-def batched_record(local: int, reps: int = 2) -> dict:
-    """The last five rounds of the ResNet-18 network at N = 2^15 (4 x 50-bit
-    + 2), each with its own encrypted input: one sf_eval_layers call against
-    one sf_eval_linear_layer call per round (both captured once, L2 flushed
-    before each timed run, best of `reps`), with the decryption check of
-    every output of both forms."""
+def batched_record(local: int, kind: str, names: list, copies: int = 0, reps: int = 2) -> dict:
+    """Rounds of a network (`names`, each with its own encrypted input, plus
+    `copies` more inputs of the first named round, as from concurrent
+    requests): one sf_eval_layers call against one sf_eval_linear_layer call
+    per round (both captured once, L2 flushed before each timed run, best of
+    `reps`), with the decryption check of every output of both forms."""
     import torch
-    nw_ = NetworkWorkload("resnet18", local, 300, names=BATCH_ROUNDS)
-    nw_._seed = 300
+    seed = {"resnet18": 300, "resnet20": 500}[kind]
+    nw_ = NetworkWorkload(kind, local, seed, names=names)
+    nw_._seed = seed
+    if copies:
+        nw_.add_requests(0, copies)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
-    R = len(nw_.net.rounds)
+    S = len(nw_.d_ins)
 
     def per_layer_all():
-        for r in range(R):
-            nw_.per_layer(r)
+        for k in range(S):
+            nw_.per_layer(k)
 
     per_layer_all()
     t_p = []
     for _ in range(reps):
         flush_l2(flush)
         t_p.append(timed(torch, nw_.stream, per_layer_all))
-    err_p = nw_.max_err(range(R))
+    err_p = nw_.max_err(range(S))
     nw_.batched()
     t_b = []
     for _ in range(reps):
         flush_l2(flush)
         t_b.append(timed(torch, nw_.stream, nw_.batched))
-    err_b = nw_.max_err(range(R))
-    ks = nw_.net.total_ks()
+    err_b = nw_.max_err(range(S))
+    ks = sum(nw_.net.infos[r]["ks_count"] for r in nw_.layer_of)
+    n_ring = nw_.n
     nw_.destroy()
-    return {"what": "ResNet-18 (3x64x64) rounds " + ", ".join(BATCH_ROUNDS) + " at N = 2^15, 4 x 50-bit + 2, "
-                    "each with its own synthetic input; default launch batch",
-            "key_switches": ks, "per_layer_ms": min(t_p), "batched_ms": min(t_b),
-            "speedup_batched_vs_per_layer": min(t_p) / min(t_b), "layers_per_s_batched": R / (min(t_b) / 1e3),
-            "max_abs_err": {"per_layer": err_p, "batched": err_b}}
+    what = f"{kind} rounds {', '.join(names)} at N = {n_ring}"
+    if copies:
+        what += f", the first round for {copies + 1} concurrent requests"
+    return {"what": what + "; each input its own synthetic encryption; default launch batch",
+            "round_evaluations": S, "key_switches": ks, "per_layer_ms": min(t_p), "batched_ms": min(t_b),
+            "speedup_batched_vs_per_layer": min(t_p) / min(t_b), "layers_per_s_batched": S / (min(t_b) / 1e3),
+            "layers_per_s_per_layer": S / (min(t_p) / 1e3), "max_abs_err": {"per_layer": err_p, "batched": err_b}}
+
+
+R20_LATE = ["s2b0c1", "s2b0c2", "s2b1c1", "s2b1c2", "s2b2c1", "s2b2c2", "fc"]
 
 
 def sm_count_of(local: int) -> int:
@@ -1025,7 +1060,9 @@ def main():
     if rank == 0 and args.workload == "r34" and not args.no_extras and not args.small:
         extras = {}
         for name, fn in (("conv16", lambda: conv16_record(local)), ("serving", lambda: serving_record(local)),
-                         ("batched_vs_per_layer", lambda: batched_record(local))):
+                         ("batched_vs_per_layer", lambda: batched_record(local, "resnet18", BATCH_ROUNDS)),
+                         ("batched_small_rounds", lambda: batched_record(local, "resnet20", R20_LATE)),
+                         ("batched_requests", lambda: batched_record(local, "resnet20", ["s2b1c1"], copies=7))):
             t0 = time.perf_counter()
             try:
                 extras[name] = fn()

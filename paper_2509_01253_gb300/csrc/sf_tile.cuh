@@ -64,10 +64,26 @@ struct SfGeo {
 
 typedef ulonglong2 sf_tw;   // (w, w')
 
+// Shared-memory word of element k of sub-transform b in a tile of NB
+// sub-transforms.  NB = 16: a padded row of 17 words per k (conflict-free for
+// the sweeps and the coalesced copies).  NB = 8: rows of 8 words with the
+// sub-transform index XOR-swizzled by bits 1..3 of k, so that 16 consecutive
+// k of one b (a coalesced copy) hit 16 distinct bank pairs, and so do the two
+// units of a half-warp in every sweep whose units start an odd distance apart.
+template <int NB>
+__device__ __forceinline__ int tile_slot(int k, int b)
+{
+    if constexpr (NB == 8) return (k << 3) + (b ^ ((k >> 1) & 7));
+    else return k * (NB + 1) + b;
+}
+
 // elements of a tile buffer in shared memory (S rows of SF_PAD words)
 __host__ __device__ __forceinline__ int tile_words(int log_s) { return (1 << log_s) * SF_PAD; }
 // words of a row tile buffer (2^log_c rows of sf_row_nb(log_c) + 1 words)
-__host__ __device__ __forceinline__ int row_tile_words(int log_c) { return (1 << log_c) * (sf_row_nb(log_c) + 1); }
+__host__ __device__ __forceinline__ int row_tile_words(int log_c)
+{
+    return (1 << log_c) * (sf_row_nb(log_c) == 8 ? 8 : sf_row_nb(log_c) + 1);
+}
 
 // One sweep of R_ST consecutive stages over every unit of the tile.
 // Forward: halves H0, H0/2, ..., H0 >> (R_ST-1).  Inverse: halves H0, ..., H0 << (R_ST-1).
@@ -77,7 +93,6 @@ __device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
     constexpr int S = 1 << LOG_S;
     constexpr int U = 1 << R_ST;
     constexpr int UNITS = NB * S / U;
-    constexpr int PAD = NB + 1;
     constexpr int LOG_NB = NB == 8 ? 3 : 4;
     constexpr int ITER = (UNITS + NT - 1) / NT;
     constexpr int LOG_STEP = INV ? LOG_H0 : (LOG_H0 - (R_ST - 1));
@@ -94,7 +109,7 @@ __device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
         const int first = (blk << LOG_BLK) + o;
         u64 x[U];
 #pragma unroll
-        for (int t = 0; t < U; ++t) x[t] = s[(first + (t << LOG_STEP)) * PAD + b];
+        for (int t = 0; t < U; ++t) x[t] = s[tile_slot<NB>(first + (t << LOG_STEP), b)];
 #pragma unroll
         for (int sg = 0; sg < R_ST; ++sg) {
             const int d = INV ? (1 << sg) : (1 << (R_ST - 1 - sg));
@@ -109,7 +124,7 @@ __device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
             }
         }
 #pragma unroll
-        for (int t = 0; t < U; ++t) s[(first + (t << LOG_STEP)) * PAD + b] = x[t];
+        for (int t = 0; t < U; ++t) s[tile_slot<NB>(first + (t << LOG_STEP), b)] = x[t];
     }
     __syncthreads();
 }
@@ -222,7 +237,8 @@ __device__ __forceinline__ int col_slot(int e) { return (e >> 4) * SF_PAD + (e &
 __device__ __forceinline__ int row_elems(const SfGeo &g) { return sf_row_nb(g.log_c) * g.c; }
 __device__ __forceinline__ int row_slot(const SfGeo &g, int e)
 {
-    return (e & (g.c - 1)) * (sf_row_nb(g.log_c) + 1) + (e >> g.log_c);
+    return sf_row_nb(g.log_c) == 8 ? tile_slot<8>(e & (g.c - 1), e >> g.log_c)
+                                   : tile_slot<16>(e & (g.c - 1), e >> g.log_c);
 }
 
 // Stage twiddles: column table (R pairs) or the row table of tile r0/NB
@@ -259,14 +275,13 @@ struct SfThreads {
 template <int LC>
 struct SfRow {
     static constexpr int NB = LC >= 8 ? 8 : 16;
-    static constexpr int PAD = NB + 1;
     static constexpr int NT = SF_THREADS;
     static constexpr int ELEMS = NB << LC;
-    static constexpr int WORDS = (1 << LC) * PAD;   // words of one tile buffer
+    static constexpr int WORDS = (1 << LC) * (NB == 8 ? 8 : NB + 1);   // words of one tile buffer (see tile_slot)
 };
 
 template <int LC>
-__device__ __forceinline__ int row_slot_t(int e) { return (e & ((1 << LC) - 1)) * SfRow<LC>::PAD + (e >> LC); }
+__device__ __forceinline__ int row_slot_t(int e) { return tile_slot<SfRow<LC>::NB>(e & ((1 << LC) - 1), e >> LC); }
 template <int LC>
 __device__ __forceinline__ int col_gidx_t(int c0, int e) { return ((e >> 4) << LC) + c0 + (e & 15); }
 
