@@ -211,7 +211,8 @@ class Workload:
                                               2, self.stream)
         return {"ks_batch": best, "ms": ms,
                 "ks3_threads": self.sf.sf_ctx_get_option(self.ctx, "ks3_threads"),
-                "leaf_sparse": self.sf.sf_ctx_get_option(self.ctx, "leaf_sparse")}
+                "leaf_sparse": self.sf.sf_ctx_get_option(self.ctx, "leaf_sparse"),
+                "row_radix": self.sf.sf_ctx_get_option(self.ctx, "row_radix")}
 
     def check(self) -> float:
         """Max |decoded - float64| over all outputs (not timed)."""
@@ -336,7 +337,11 @@ def load_peaks():
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch divided by its
 # items), kept only while the kernel's code is unchanged since the capture;
 # scaled to a full launch by its items
-TRAFFIC_PER_ITEM = {}
+TRAFFIC_PER_ITEM = {
+    # k_ks2 at N = 2^16 (5 + 2 primes), one launch of 128 merges of the small
+    # r34 case (--small, ks_batch=128): 0.315303 GB read + 947.246336 MB written
+    ("ks2_modup_col", 16): (0.315303e9 + 947.246336e6) / 128,
+}
 
 
 def items_per_layer(kernel: str, info: dict, merges: int) -> int:
@@ -863,6 +868,54 @@ def conv16_record(local: int, steps: int = 5) -> dict:
             "kernels": {k: {"launches_per_layer": c // 2, "ms_per_layer": m / 2} for k, (c, m) in ks.items() if c}}
 
 
+def gamma2_record(local: int, kind: str = "r34", steps: int = 3) -> dict:
+    """The same layer at partial trace extraction level gamma = 2 (Sec. 4.3,
+    4.4, Lemma 1 at t = 2): the client also uploads RLWE(m(X^3)) per input
+    ciphertext, the leaves read twice the ciphertexts and the packing skips
+    the tau_3 level.  Time per layer (L2 flushed between steps) against the
+    gamma = 0 layer, key switches, upload bytes, and the decryption check
+    (packed values halved)."""
+    import torch
+    wl_ = Workload(local, kind)
+    sf = wl_.sf
+    from paper_2509_01253_gb300 import workloads as wlm
+    d_pow = torch.zeros_like(wl_.d_in)
+    sf.sf_encrypt(wl_.ctx, wl_.sk, sf.sf_client_power(wl_.params, wl_.msg, wl_.k_in, 3), 7404, d_pow, wl_.k_in)
+    case = wl_.case
+
+    def step2():
+        sf.sf_eval_linear_layer_gamma(wl_.ctx, wl_.layer, wl_.rk, 2, wl_.d_in, d_pow, wl_.k_in, case.sigma_prev,
+                                      case.sigma_out, wl_.d_out, wl_.G, wl_.stream)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
+    out = {}
+    for name, fn in (("gamma0", wl_.step), ("gamma2", step2)):
+        fn()
+        for _ in range(2):
+            fn()
+        ms = []
+        for _ in range(steps):
+            flush_l2(flush)
+            ms.append(timed(torch, wl_.stream, fn))
+        out[name] = {"ms_per_layer": sum(ms) / len(ms), "step_ms": ms}
+    sf.sf_sync(wl_.ctx, wl_.stream)
+    res = np.zeros((wl_.G, wl_.L, wl_.n), dtype=np.uint64)
+    sf.sf_decrypt(wl_.ctx, wl_.sk, wl_.d_out, wl_.G, res, wl_.stream)
+    vals = sf.sf_decode(wl_.params, res, wl_.G, wl_.n // wl_.info["group_size"], wl_.info["E_out"],
+                        2 * wl_.ps.delta ** 2)
+    ref = wlm.float_reference(case)
+    if case.sigma_out is not None:
+        ref = ref[case.sigma_out.astype(np.int64)]
+    n, G = wl_.info["group_size"], wl_.G
+    ks2 = G * (n // 2 - 1 + (wl_.n.bit_length() - 1) - (n.bit_length() - 1))
+    rec = {"workload": wl_.desc, "key_switches": {"gamma0": wl_.info["ks_count"], "gamma2": ks2},
+           "upload_bytes": {"gamma0": wl_.k_in * wl_.ct_bytes, "gamma2": 2 * wl_.k_in * wl_.ct_bytes},
+           "max_abs_err_gamma2": float(np.abs(vals - ref).max()),
+           "speedup_gamma2_vs_gamma0": out["gamma0"]["ms_per_layer"] / out["gamma2"]["ms_per_layer"], **out}
+    wl_.destroy()
+    return rec
+
+
 def serving_record(local: int, rate: float = 0.3, duration: float = 30.0, drain: float = 60.0) -> dict:
     """Continuous-batching server below capacity: ResNet-20 requests at
     N = 2^14 from 4 client keys, Poisson arrivals at `rate` per second for
@@ -1059,7 +1112,8 @@ def main():
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
     if rank == 0 and args.workload == "r34" and not args.no_extras and not args.small:
         extras = {}
-        for name, fn in (("conv16", lambda: conv16_record(local)), ("serving", lambda: serving_record(local)),
+        for name, fn in (("conv16", lambda: conv16_record(local)), ("gamma2", lambda: gamma2_record(local)),
+                         ("serving", lambda: serving_record(local)),
                          ("batched_vs_per_layer", lambda: batched_record(local, "resnet18", BATCH_ROUNDS)),
                          ("batched_small_rounds", lambda: batched_record(local, "resnet20", R20_LATE)),
                          ("batched_requests", lambda: batched_record(local, "resnet20", ["s2b1c1"], copies=7))):

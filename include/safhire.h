@@ -322,6 +322,20 @@ sf_status sf_eval_layers(sf_ctx *ctx, int32_t n_layers, const sf_layer *const *l
                          const uint32_t *const *h_sigma_outs, uint64_t *const *d_outs, const int32_t *out_capacities,
                          int32_t *n_outs, void *stream);
 
+/* sf_eval_layers with partial trace extraction per round (Sec. 4.3, 4.4):
+ * d_powers NULL evaluates every round at gamma = 0 (exactly sf_eval_layers);
+ * otherwise round x runs at gamma = 2 when d_powers[x] is non-NULL (the
+ * client's powers RLWE(m_j(X^3)), uint64[k_ins[x]][2][L][N], as in
+ * sf_eval_linear_layer_gamma) and at gamma = 0 when it is NULL.  Rounds of the
+ * two kinds never share tree levels (the gamma = 2 bottom level has no key
+ * switch).  Each result is bit-identical to the single-round call.
+ * Errors: those of sf_eval_layers. */
+sf_status sf_eval_layers_gamma(sf_ctx *ctx, int32_t n_layers, const sf_layer *const *layers,
+                               const sf_rotkeys *const *rks, const uint64_t *const *d_ins,
+                               const uint64_t *const *d_powers, const int32_t *k_ins,
+                               const uint32_t *const *h_sigma_prevs, const uint32_t *const *h_sigma_outs,
+                               uint64_t *const *d_outs, const int32_t *out_capacities, int32_t *n_outs, void *stream);
+
 /* Autotuner: times sf_eval_layers on the given rounds (which it evaluates,
  * results valid), `repeats` timed runs per candidate after a warm-up:
  * first each key-switch launch batch (32 ... 4096 merges; those above 512

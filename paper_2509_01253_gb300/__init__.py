@@ -85,6 +85,7 @@ _SIGS = {
     "sf_eval_linear_layer_host": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _i32, ctypes.POINTER(_i32), _vp]),
     "sf_linear_outputs": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i32, _vp, _vp]),
     "sf_eval_layers": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "sf_eval_layers_gamma": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sf_autotune_layers": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, ctypes.POINTER(_i32),
                                   ctypes.POINTER(_dbl), _vp]),
     "sf_rotate": (_i32, [_vp, _vp, _i32, _vp, _vp, _i32, _vp]),
@@ -375,6 +376,18 @@ def sf_eval_layers(ctx, layers, rks, d_ins, k_ins, sigma_prevs, sigma_outs, d_ou
     a, keep = _round_arrays(layers, rks, d_ins, k_ins, sigma_prevs, sigma_outs, d_outs, out_capacities)
     n_outs = (ctypes.c_int32 * len(layers))()
     _check(lib().sf_eval_layers(ctx, len(layers), *a, n_outs, _stream(stream)))
+    return list(n_outs)
+
+
+def sf_eval_layers_gamma(ctx, layers, rks, d_ins, d_powers, k_ins, sigma_prevs, sigma_outs, d_outs, out_capacities,
+                         stream=None):
+    """sf_eval_layers where round x runs at gamma = 2 when d_powers[x] is a
+    buffer of the client's powers (None: gamma = 0); returns n_outs."""
+    a, keep = _round_arrays(layers, rks, d_ins, k_ins, sigma_prevs, sigma_outs, d_outs, out_capacities)
+    n = len(layers)
+    pw = None if d_powers is None else (ctypes.c_void_p * n)(*[_ptr(x) for x in d_powers])
+    n_outs = (ctypes.c_int32 * n)()
+    _check(lib().sf_eval_layers_gamma(ctx, n, a[0], a[1], a[2], pw, *a[3:], n_outs, _stream(stream)))
     return list(n_outs)
 
 

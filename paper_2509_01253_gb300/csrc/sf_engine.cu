@@ -75,12 +75,18 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
 {
     const SfRing &R = ctx->ring;
     const size_t ct = ct_words(ctx), ct_bytes = ct * sizeof(u64);
-    int max_k_in = 1, max_taps = 1;
-    for (auto &j : jobs) {
-        max_k_in = std::max(max_k_in, j.k_leaf());
-        max_taps = std::max(max_taps, j.taps());
+    // leaf slots per launch, per round (its own ciphertexts and taps: a round
+    // with a huge fan-in does not shrink the launches of the others); the
+    // workspace holds the largest of them
+    std::vector<int> lb(jobs.size());
+    size_t w1_words = 0, tap_words = 0;
+    for (size_t x = 0; x < jobs.size(); ++x) {
+        const Job &j = jobs[x];
+        lb[x] = leaf_batch_slots(R, j.k_leaf(), j.taps());
+        w1_words = std::max(w1_words, (size_t)lb[x] * j.k_leaf() * R.L * R.n);
+        tap_words = std::max(tap_words, sf_leaf_tap_words(R, j.k_leaf(), j.taps(), lb[x]));
     }
-    const int LB = leaf_batch_slots(R, max_k_in, max_taps);
+    const int LB = *std::max_element(lb.begin(), lb.end());
     // ---- classes and units
     std::vector<Class> classes;
     for (int x = 0; x < (int)jobs.size(); ++x) {
@@ -121,8 +127,8 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
         o_pos[x] = cv.take(((size_t)jobs[x].L->E_in + 1) / 2);
         o_sig[x] = cv.take(((size_t)jobs[x].L->E_out + 1) / 2);
     }
-    const size_t o_w1 = cv.take((size_t)LB * max_k_in * R.L * R.n);
-    const size_t o_tap = cv.take(sf_leaf_tap_words(R, max_k_in, max_taps, LB));
+    const size_t o_w1 = cv.take(w1_words);
+    const size_t o_tap = cv.take(tap_words);
     size_t roots_bytes = 0;
     for (auto &c : classes)
         if (c.nch > 1) roots_bytes += (size_t)c.groups.size() * c.nch * ct_bytes * 3 / 2;
@@ -172,6 +178,7 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
     auto launch_all = [&](cudaStream_t s) -> sf_status {
         for (auto &j : jobs) SF_TRY(prepare_inputs(ctx, j.d_in, j.d_pow, j.k_in, j.d_ct, s));
         auto leaves = [&](const Job &j, int s0, int stride, int cnt, u64 *dst) -> sf_status {
+            const int jb = lb[&j - jobs.data()];
             SfLeafParams P = leaf_params(j.L);
             P.k_in = j.k_leaf();
             P.k_src = j.k_in;
@@ -181,15 +188,15 @@ static sf_status eval_jobs(sf_ctx *ctx, std::vector<Job> &jobs, cudaStream_t st)
             P.sig_out = j.so ? j.d_sig : nullptr;
             P.ct = j.d_ct;
             P.w1 = d_w1;
-            sf_leaf_tap_bind(R, P, ws + o_tap, LB);
+            sf_leaf_tap_bind(R, P, ws + o_tap, jb);
             P.n_slots_valid = j.L->E_out;
             P.leaf_stride = ct;
-            for (int t0 = 0; t0 < cnt; t0 += LB) {
+            for (int t0 = 0; t0 < cnt; t0 += jb) {
                 SfLeafParams p = P;
                 p.s0 = s0 + t0 * stride;
                 p.s_stride = stride;
                 p.leaves = dst + (size_t)t0 * ct;
-                SF_TRY(sf_leaves_launch(ctx, p, std::min(LB, cnt - t0), s));
+                SF_TRY(sf_leaves_launch(ctx, p, std::min(jb, cnt - t0), s));
             }
             return SF_OK;
         };
@@ -379,6 +386,30 @@ extern "C" sf_status sf_eval_layers(sf_ctx *ctx, int32_t n_layers, const sf_laye
     return SF_OK;
 }
 
+extern "C" sf_status sf_eval_layers_gamma(sf_ctx *ctx, int32_t n_layers, const sf_layer *const *layers,
+                                          const sf_rotkeys *const *rks, const uint64_t *const *d_ins,
+                                          const uint64_t *const *d_powers, const int32_t *k_ins,
+                                          const uint32_t *const *h_sigma_prevs, const uint32_t *const *h_sigma_outs,
+                                          uint64_t *const *d_outs, const int32_t *out_capacities, int32_t *n_outs,
+                                          void *stream)
+{
+    SF_CHECK_CTX(ctx);
+    if (n_layers < 1 || !layers || !rks || !d_ins || !k_ins || !d_outs || !out_capacities)
+        return sf_set_error(SF_EINVAL, "sf_eval_layers_gamma: bad arguments");
+    std::vector<Job> jobs(n_layers);
+    for (int x = 0; x < n_layers; ++x) {
+        SF_TRY(make_job(ctx, layers[x], rks[x], d_ins[x], k_ins[x], h_sigma_prevs ? h_sigma_prevs[x] : nullptr,
+                        h_sigma_outs ? h_sigma_outs[x] : nullptr, d_outs[x], out_capacities[x], &jobs[x]));
+        jobs[x].d_pow = d_powers ? d_powers[x] : nullptr;
+        if (jobs[x].d_pow && 2 * k_ins[x] * (ctx->ring.c / SF_NB) > 4096)
+            return sf_set_error(SF_EINVAL, "too many input ciphertexts for one round at gamma = 2");
+    }
+    SF_TRY(eval_jobs(ctx, jobs, (cudaStream_t)stream));
+    if (n_outs)
+        for (int x = 0; x < n_layers; ++x) n_outs[x] = jobs[x].G;
+    return SF_OK;
+}
+
 #define SF_AUTOTUNE_KS_SCRATCH ((size_t)16 << 30)
 
 extern "C" sf_status sf_autotune_layers(sf_ctx *ctx, int32_t n_layers, const sf_layer *const *layers,
@@ -464,6 +495,24 @@ extern "C" sf_status sf_autotune_layers(sf_ctx *ctx, int32_t n_layers, const sf_
             }
         }
         ctx->ks3_threads = best_nt;
+    }
+    // 4) NTT radix of the row passes (key-switch rows, inner product, ModDown
+    //    finish, leaf rows): radix-8 sweeps (three for 128- and 256-point rows)
+    //    or radix-4 sweeps only (four), which hold half the values per unit
+    if (status == SF_OK) {
+        const int saved = ctx->row_radix;
+        int best_rad = saved;
+        for (int rad : {0, 1}) {
+            if (rad == saved) continue;
+            ctx->row_radix = rad;
+            double t = 0;
+            if ((status = measure(&t)) != SF_OK) break;
+            if (t < best_t) {
+                best_t = t;
+                best_rad = rad;
+            }
+        }
+        ctx->row_radix = best_rad;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

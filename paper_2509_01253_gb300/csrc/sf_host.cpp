@@ -482,6 +482,7 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
     ctx->leaf_chunk = 1 << 30;
     ctx->leaf_sparse = 0;   // the transform measured faster than the closed form on GB300
     ctx->ks3_threads = 256;
+    ctx->row_radix = 0;
     ctx->mem_budget = (size_t)64 << 30;
     ctx->use_graph = 1;
     ctx->kernel_timing = 0;
@@ -677,6 +678,7 @@ extern "C" sf_status sf_ctx_get_option(const sf_ctx *ctx, const char *name, int6
     if (!ctx || !name || !value) return sf_set_error(SF_EINVAL, "sf_ctx_get_option: null argument");
     if (!strcmp(name, "ks_batch")) *value = ctx->ks_batch;
     else if (!strcmp(name, "ks3_threads")) *value = ctx->ks3_threads;
+    else if (!strcmp(name, "row_radix")) *value = ctx->row_radix;
     else if (!strcmp(name, "leaf_sparse")) *value = ctx->leaf_sparse;
     else if (!strcmp(name, "leaf_chunk")) *value = ctx->leaf_chunk;
     else if (!strcmp(name, "mem_budget")) *value = (int64_t)ctx->mem_budget;
@@ -700,6 +702,10 @@ extern "C" sf_status sf_ctx_set_option(sf_ctx *ctx, const char *name, int64_t va
     } else if (!strcmp(name, "ks3_threads")) {
         if (value != 256 && value != 512) return sf_set_error(SF_EINVAL, "ks3_threads must be 256 or 512");
         ctx->ks3_threads = (int)value;
+        sf_graph_cache_clear(ctx);
+    } else if (!strcmp(name, "row_radix")) {
+        if (value != 0 && value != 1) return sf_set_error(SF_EINVAL, "row_radix must be 0 or 1");
+        ctx->row_radix = (int)value;
         sf_graph_cache_clear(ctx);
     } else if (!strcmp(name, "leaf_chunk")) {
         if (value < 1 || (value & (value - 1))) return sf_set_error(SF_EINVAL, "leaf_chunk must be a power of two");

@@ -178,7 +178,7 @@ struct SfRowSet {
     int npoly, mod_base, mod_period;
 };
 
-template <bool INV, int LR, int LC>
+template <bool INV, int LR, int LC, int RAD = 0>
 __global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_rows(SfRing R, SfKsBatch B, SfRowSet S, int bpg)
 {
     constexpr int NT = SfRow<LC>::NT, NB = SfRow<LC>::NB;
@@ -210,8 +210,8 @@ __global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_rows(SfRing R, SfKsBatch B
             sf_cp_wait<0>();
         }
         __syncthreads();
-        if (INV) row_inverse_t<LC, NT>(cur, tw, M.q);
-        else row_forward_t<LC, NT>(cur, tw, M.q);
+        if (INV) row_inverse_t<LC, NT, RAD>(cur, tw, M.q);
+        else row_forward_t<LC, NT, RAD>(cur, tw, M.q);
         u64 *dst = B.scratch + per * b + off_d;
         #pragma unroll
         for (int e = threadIdx.x; e < SfRow<LC>::ELEMS; e += NT) dst[e] = cur[row_slot_t<LC>(e)];
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
 // NT: 256 (8 elements per thread, three blocks per SM) or, for 128-point
 // rows, 512 (4 elements per thread, half the accumulator registers, two
 // 16-warp blocks per SM); 256-point rows always run 512.
-template <int LR, int LC, int NT>
+template <int LR, int LC, int NT, int RAD = 0>
 __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) k_ks3(SfRing R, SfKsBatch B, int bpg)
 {
     constexpr int NB = SfRow<LC>::NB, EPT = SfRow<LC>::ELEMS / NT;
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) k_ks3(SfRing R, SfKsBat
         }
         __syncthreads();
         const bool own = (m >= j * R.K && m < min((j + 1) * R.K, R.L));
-        if (!own) tile_forward_t<LC, true, NT, NB>(cur, tw, M.q);
+        if (!own) tile_forward_t<LC, true, NT, NB, RAD>(cur, tw, M.q);
         const size_t comp = (size_t)R.dnum * 2 * R.nm << (LR + LC);   // companions follow the key values
         const u64 *ka = B.key + ((((size_t)j * 2 + 0) * R.nm + m) << (LR + LC)) + tile_off;
         const u64 *kb = B.key + ((((size_t)j * 2 + 1) * R.nm + m) << (LR + LC)) + tile_off;
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
 // out += ACC - conv, both already multiplied by P^-1.  smem: forward row twiddles and two conversion
 // tiles (double-buffered); ACC and out are read elementwise from global into
 // registers before the row pass.
-template <int LR, int LC>
+template <int LR, int LC, int RAD = 0>
 __global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_ks5(SfRing R, SfKsBatch B, int bpg)
 {
     constexpr int NT = SfRow<LC>::NT, NB = SfRow<LC>::NB, EPT = SfRow<LC>::ELEMS / NT;
@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_ks5(SfRing R, SfKsBatch B,
             vo[x] = out[threadIdx.x + x * NT];
         }
         __syncthreads();
-        row_forward_t<LC, NT>(cur, tw, M.q);
+        row_forward_t<LC, NT, RAD>(cur, tw, M.q);
         // acc and conv both carry P^-1 already: out += acc - conv, one reduction
 #pragma unroll
         for (int x = 0; x < EPT; ++x) {
@@ -601,8 +601,10 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
             {
                 const SfRowSet S{0, (size_t)R.L << R.log_n, R.L, 0, R.L};   // TA -> X1
                 const int ng = rtiles * S.npoly;
-                const int bpg = blocks_per_group(ctx, occupancy(k_rows<true, LR, LC>, NTR, sm_rows), ng, b.count);
-                k_rows<true, LR, LC><<<ng * bpg, NTR, sm_rows, st>>>(R, b, S, bpg);
+                SF_RAD_DISPATCH(ctx->row_radix, {
+                    const int bpg = blocks_per_group(ctx, occupancy(k_rows<true, LR, LC, RAD>, NTR, sm_rows), ng, b.count);
+                    k_rows<true, LR, LC, RAD><<<ng * bpg, NTR, sm_rows, st>>>(R, b, S, bpg);
+                });
             }
             sf_launch_end(ctx, SFK_KS1_INV_ROW, st, ev);
 
@@ -618,8 +620,10 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
             {
                 const int ng = rtiles * R.nm;
                 if (!ks3_launch_wide<LR, LC>(ctx, b, sm3, ng, st)) {
-                    const int bpg = blocks_per_group(ctx, occupancy(k_ks3<LR, LC, NTR>, NTR, sm3), ng, b.count);
-                    k_ks3<LR, LC, NTR><<<ng * bpg, NTR, sm3, st>>>(R, b, bpg);
+                    SF_RAD_DISPATCH(ctx->row_radix, {
+                        const int bpg = blocks_per_group(ctx, occupancy(k_ks3<LR, LC, NTR, RAD>, NTR, sm3), ng, b.count);
+                        k_ks3<LR, LC, NTR, RAD><<<ng * bpg, NTR, sm3, st>>>(R, b, bpg);
+                    });
                 }
             }
             sf_launch_end(ctx, SFK_KS3_INNER_ROW, st, ev);
@@ -628,8 +632,10 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
                 // inverse row pass of the special limbs' accumulators, in place in x1
                 const SfRowSet S{(size_t)R.L << R.log_n, (size_t)R.L << R.log_n, 2 * R.K, R.L, R.K};
                 const int ng2 = rtiles * S.npoly;
-                const int bpg2 = blocks_per_group(ctx, occupancy(k_rows<true, LR, LC>, NTR, sm_rows), ng2, b.count);
-                k_rows<true, LR, LC><<<ng2 * bpg2, NTR, sm_rows, st>>>(R, b, S, bpg2);
+                SF_RAD_DISPATCH(ctx->row_radix, {
+                    const int bpg2 = blocks_per_group(ctx, occupancy(k_rows<true, LR, LC, RAD>, NTR, sm_rows), ng2, b.count);
+                    k_rows<true, LR, LC, RAD><<<ng2 * bpg2, NTR, sm_rows, st>>>(R, b, S, bpg2);
+                });
             }
             sf_launch_end(ctx, SFK_KS3_INV_ROW_P, st, ev);
 
@@ -644,8 +650,10 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
             sf_launch_begin(ctx, SFK_KS5_FINISH_ROW, st, &ev);
             {
                 const int ng = rtiles * R.L;
-                const int bpg = blocks_per_group(ctx, occupancy(k_ks5<LR, LC>, NTR, sm5), ng, 2 * b.count);
-                k_ks5<LR, LC><<<ng * bpg, NTR, sm5, st>>>(R, b, bpg);
+                SF_RAD_DISPATCH(ctx->row_radix, {
+                    const int bpg = blocks_per_group(ctx, occupancy(k_ks5<LR, LC, RAD>, NTR, sm5), ng, 2 * b.count);
+                    k_ks5<LR, LC, RAD><<<ng * bpg, NTR, sm5, st>>>(R, b, bpg);
+                });
             }
             sf_launch_end(ctx, SFK_KS5_FINISH_ROW, st, ev);
         });
@@ -677,7 +685,8 @@ sf_status sf_ks_init_attributes()
 #define SF_KS_ATTR(K) SF_CUDA_TRY(cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
 #define SF_KS_ATTRS(LR, LC)                                                                                  \
     SF_KS_ATTR((k_rows<true, LR, LC>)) SF_KS_ATTR((k_ks2<LR, LC>)) SF_KS_ATTR((k_ks3<LR, LC, SfRow<LC>::NT>)) \
-    SF_KS_ATTR((k_ks4<LR, LC>)) SF_KS_ATTR((k_ks5<LR, LC>))
+    SF_KS_ATTR((k_ks4<LR, LC>)) SF_KS_ATTR((k_ks5<LR, LC>)) SF_KS_ATTR((k_rows<true, LR, LC, 1>))               \
+    SF_KS_ATTR((k_ks3<LR, LC, SfRow<LC>::NT, 1>)) SF_KS_ATTR((k_ks5<LR, LC, 1>))
     SF_KS_ATTRS(5, 5) SF_KS_ATTRS(5, 6) SF_KS_ATTRS(6, 6) SF_KS_ATTRS(6, 7) SF_KS_ATTRS(7, 7) SF_KS_ATTRS(7, 8)
     SF_KS_ATTRS(8, 8)
     SF_KS_ATTR((k_ks3<6, 7, 512>)) SF_KS_ATTR((k_ks3<7, 7, 512>))

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
 }
 
 // leaf_row: grid (R/16 row tiles, L, slots).  smem: forward row twiddles + 1 tile.
-template <int LR, int LC>
+template <int LR, int LC, int RAD = 0>
 __global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_leaf_row(SfRing R, SfLeafParams P)
 {
     constexpr int NT = SfRow<LC>::NT, NB = SfRow<LC>::NB, EPT = SfRow<LC>::ELEMS / NT;
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_leaf_row(SfRing R, SfLeafP
             sm[row_slot_t<LC>(e)] = src[e];
         }
         __syncthreads();
-        row_forward_t<LC, NT>(sm, tw, M.q);
+        row_forward_t<LC, NT, RAD>(sm, tw, M.q);
         const size_t comp = (size_t)P.k_in * 2 * R.L << (LR + LC);
         const u64 *ca = P.ct + (((size_t)j * 2 + 0) * R.L + i) * (size_t)(1 << (LR + LC)) + tile_off;
         const u64 *cb = P.ct + (((size_t)j * 2 + 1) * R.L + i) * (size_t)(1 << (LR + LC)) + tile_off;
@@ -296,7 +296,7 @@ sf_status sf_leaves_launch(sf_ctx *ctx, const SfLeafParams &P, int cnt, cudaStre
         sf_launch_end(ctx, SFK_LEAF_COL, st, ev);
         sf_launch_begin(ctx, SFK_LEAF_ROW, st, &ev);
         const dim3 gr(R.r / sf_row_nb(R.log_c), R.L, c);
-        SF_GEO_DISPATCH(R.log_n, k_leaf_row<LR, LC><<<gr, SfRow<LC>::NT, smem_r, st>>>(R, p););
+        SF_GEO_DISPATCH(R.log_n, SF_RAD_DISPATCH(ctx->row_radix, k_leaf_row<LR, LC, RAD><<<gr, SfRow<LC>::NT, smem_r, st>>>(R, p);););
         sf_launch_end(ctx, SFK_LEAF_ROW, st, ev);
     }
     SF_CUDA_TRY(cudaGetLastError());
@@ -601,7 +601,8 @@ sf_status sf_layer_init_attributes()
     SF_LEAF_ATTRS(7, 8) SF_LEAF_ATTRS(8, 8)
 #undef SF_LEAF_ATTRS
 #define SF_LEAF_ROW_ATTR(LR, LC) \
-    SF_CUDA_TRY(cudaFuncSetAttribute((k_leaf_row<LR, LC>), cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    SF_CUDA_TRY(cudaFuncSetAttribute((k_leaf_row<LR, LC>), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)); \
+    SF_CUDA_TRY(cudaFuncSetAttribute((k_leaf_row<LR, LC, 1>), cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     SF_LEAF_ROW_ATTR(5, 5) SF_LEAF_ROW_ATTR(5, 6) SF_LEAF_ROW_ATTR(6, 6) SF_LEAF_ROW_ATTR(6, 7) SF_LEAF_ROW_ATTR(7, 7)
     SF_LEAF_ROW_ATTR(7, 8) SF_LEAF_ROW_ATTR(8, 8)
 #undef SF_LEAF_ROW_ATTR

@@ -132,10 +132,18 @@ __device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
 // Forward stages of all NB sub-transforms of size 2^LOG_S; values in [0, 4q).
 // 128-point sub-transforms in 512-thread blocks (4 elements per thread) run
 // radix-4 sweeps so that every thread holds one unit.
-template <int LOG_S, bool ROWTW, int NT, int NB = SF_NB>
+template <int LOG_S, bool ROWTW, int NT, int NB = SF_NB, int RAD = 0>
 __device__ __forceinline__ void tile_forward_t(u64 *s, const sf_tw *tw, u64 q)
 {
-    if constexpr (LOG_S == 7 && NT == 512) {
+    if constexpr (RAD == 1) {
+        // radix-4 sweeps only (two stages per sweep, a radix-2 sweep last for an odd count)
+        tile_sweep<LOG_S, LOG_S - 1, 2, false, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<LOG_S, LOG_S - 3, 2, false, ROWTW, NT, NB>(s, tw, q);
+        if constexpr (LOG_S >= 6) tile_sweep<LOG_S, LOG_S - 5, 2, false, ROWTW, NT, NB>(s, tw, q);
+        else tile_sweep<LOG_S, 0, 1, false, ROWTW, NT, NB>(s, tw, q);
+        if constexpr (LOG_S == 7) tile_sweep<LOG_S, 0, 1, false, ROWTW, NT, NB>(s, tw, q);
+        if constexpr (LOG_S == 8) tile_sweep<LOG_S, 1, 2, false, ROWTW, NT, NB>(s, tw, q);
+    } else if constexpr (LOG_S == 7 && NT == 512) {
         tile_sweep<7, 6, 2, false, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<7, 4, 2, false, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<7, 2, 2, false, ROWTW, NT, NB>(s, tw, q);
@@ -158,10 +166,17 @@ __device__ __forceinline__ void tile_forward_t(u64 *s, const sf_tw *tw, u64 q)
 }
 
 // Inverse stages (no N^-1 factor); inputs and values in [0, 4q).
-template <int LOG_S, bool ROWTW, int NT, int NB = SF_NB>
+template <int LOG_S, bool ROWTW, int NT, int NB = SF_NB, int RAD = 0>
 __device__ __forceinline__ void tile_inverse_t(u64 *s, const sf_tw *tw, u64 q)
 {
-    if constexpr (LOG_S == 7 && NT == 512) {
+    if constexpr (RAD == 1) {
+        tile_sweep<LOG_S, 0, 2, true, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<LOG_S, 2, 2, true, ROWTW, NT, NB>(s, tw, q);
+        if constexpr (LOG_S == 5) tile_sweep<LOG_S, 4, 1, true, ROWTW, NT, NB>(s, tw, q);
+        else tile_sweep<LOG_S, 4, 2, true, ROWTW, NT, NB>(s, tw, q);
+        if constexpr (LOG_S == 7) tile_sweep<LOG_S, 6, 1, true, ROWTW, NT, NB>(s, tw, q);
+        if constexpr (LOG_S == 8) tile_sweep<LOG_S, 6, 2, true, ROWTW, NT, NB>(s, tw, q);
+    } else if constexpr (LOG_S == 7 && NT == 512) {
         tile_sweep<7, 0, 2, true, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<7, 2, 2, true, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<7, 4, 2, true, ROWTW, NT, NB>(s, tw, q);
@@ -342,15 +357,17 @@ __device__ __forceinline__ void load_row_tw_t(sf_tw *dst, const sf_tw *__restric
 }
 
 // forward / inverse row pass of a row tile (its width from the row length)
-template <int LC, int NT>
+// RAD: 0 radix-8 sweeps (the default schedule), 1 radix-4 sweeps only; the
+// autotuner times both (context option row_radix)
+template <int LC, int NT, int RAD = 0>
 __device__ __forceinline__ void row_forward_t(u64 *s, const sf_tw *tw, u64 q)
 {
-    tile_forward_t<LC, true, NT, SfRow<LC>::NB>(s, tw, q);
+    tile_forward_t<LC, true, NT, SfRow<LC>::NB, RAD>(s, tw, q);
 }
-template <int LC, int NT>
+template <int LC, int NT, int RAD = 0>
 __device__ __forceinline__ void row_inverse_t(u64 *s, const sf_tw *tw, u64 q)
 {
-    tile_inverse_t<LC, true, NT, SfRow<LC>::NB>(s, tw, q);
+    tile_inverse_t<LC, true, NT, SfRow<LC>::NB, RAD>(s, tw, q);
 }
 
 // column twiddles (R pairs) of modulus mod
@@ -360,6 +377,19 @@ __device__ __forceinline__ void load_col_tw_t(sf_tw *dst, const sf_tw *__restric
     const sf_tw *src = table + ((size_t)mod << LR);
     for (int k = threadIdx.x; k < (1 << LR); k += NT) dst[k] = src[k];
 }
+
+// runs the statements with the row-pass sweep schedule RAD (0: radix-8
+// sweeps, 1: radix-4 sweeps) as a compile-time constant
+#define SF_RAD_DISPATCH(rad, ...)           \
+    do {                                    \
+        if ((rad) == 1) {                   \
+            constexpr int RAD = 1;          \
+            __VA_ARGS__                     \
+        } else {                            \
+            constexpr int RAD = 0;          \
+            __VA_ARGS__                     \
+        }                                   \
+    } while (0)
 
 // runs the statements with constexpr LR, LC for the ring size log_n (10..16)
 #define SF_GEO_DISPATCH(log_n, ...)                       \

@@ -71,10 +71,15 @@ class EncodedNetwork:
     act_bits set: quantised mode (integer weights at scale 1, outputs at
     Delta, requantisation scale eta per round)."""
 
-    def __init__(self, params, ctx, ps: wl.ParamSet, rounds: list, integer: bool = False, act_bits: int = None):
+    def __init__(self, params, ctx, ps: wl.ParamSet, rounds: list, integer: bool = False, act_bits: int = None,
+                 gamma: int = 0):
         self.params, self.ctx, self.ps, self.rounds = params, ctx, ps, rounds
         self.n = 1 << ps.log_n
         self.act_bits = act_bits
+        # partial trace extraction level (Sec. 4.3, 4.4): at gamma = 2 the client
+        # also sends RLWE(m_j(X^3)) and the packed values carry the factor 2
+        assert gamma in (0, 2)
+        self.gamma = gamma
         self.quant = act_bits is not None
         wscale = 1.0 if self.quant else ps.delta
         self.out_scale = ps.delta * wscale
@@ -164,6 +169,10 @@ class ClientState:
     def encrypt_seed(self, r: int) -> int:
         return _mix(self.request_seed, r, 0xE)
 
+    def power_seed(self, r: int) -> int:
+        """Encryption seed of round r's powers (gamma = 2)."""
+        return _mix(self.request_seed, r, 0x3)
+
     def absorb(self, r: int, values: np.ndarray, sigma_out, stream_in=None, sigma_in=None):
         """Store round r's decoded outputs (slot order) as the activation it names."""
         spec = self.net.rounds[r]
@@ -196,7 +205,7 @@ def round_float_reference(net: EncodedNetwork, r: int, x_orig: np.ndarray) -> np
 def decode_outputs(net: EncodedNetwork, r: int, residues: np.ndarray) -> np.ndarray:
     info = net.infos[r]
     return sf.sf_decode(net.params, residues, info["n_groups"], net.n // info["group_size"],
-                        info["E_out"], net.out_scale)
+                        info["E_out"], net.out_scale * (2 if net.gamma == 2 else 1))
 
 
 def run_request(net: EncodedNetwork, sk, rk, client: ClientState, stream=None, device: str = "cuda:0",
@@ -218,6 +227,11 @@ def run_request(net: EncodedNetwork, sk, rk, client: ClientState, stream=None, d
         msg, sigma_prev, stream_in = client.encode(r)
         d_in = torch.empty((info["k_in"], 2, L, n), dtype=torch.int64, device=device)
         sf.sf_encrypt(net.ctx, sk, msg, client.encrypt_seed(r), d_in, info["k_in"], stream)
+        d_pow = None
+        if net.gamma == 2:
+            d_pow = torch.empty_like(d_in)
+            sf.sf_encrypt(net.ctx, sk, sf.sf_client_power(net.params, msg, info["k_in"], 3),
+                          client.power_seed(r), d_pow, info["k_in"], stream)
         st.synchronize()
         t_client = time.perf_counter() - t0
         so = client.sigma_out(r)
@@ -226,8 +240,8 @@ def run_request(net: EncodedNetwork, sk, rk, client: ClientState, stream=None, d
             d_out = torch.empty((info["n_groups"], 2, L, n), dtype=torch.int64, device=device)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            sf.sf_eval_linear_layer(net.ctx, net.layers[rr], rk, payload, info["k_in"], sigma_prev, so, d_out,
-                                    info["n_groups"], st)
+            sf.sf_eval_linear_layer_gamma(net.ctx, net.layers[rr], rk, net.gamma, payload, d_pow, info["k_in"],
+                                          sigma_prev, so, d_out, info["n_groups"], st)
             e1.record(st)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -244,7 +258,7 @@ def run_request(net: EncodedNetwork, sk, rk, client: ClientState, stream=None, d
         client.absorb(r, vals, so, stream_in if keep_trace else None, sigma_prev)
         t_client += time.perf_counter() - t0
         if log is not None:
-            up, down = protocol.round_bytes(info, L, n)
+            up, down = protocol.round_bytes(info, L, n, net.gamma)
             log.add(r, up, down, ms[-1] / 1e3, t_client)
     return ms
 

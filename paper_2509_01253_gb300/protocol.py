@@ -60,11 +60,12 @@ def round_shape(E_in: int, E_out: int, n: int) -> dict:
     return {"k_in": -(-E_in // n), "group_size": group, "n_groups": -(-E_out // group)}
 
 
-def round_bytes(info: dict, L: int, n: int) -> tuple:
-    """(upload, download) bytes of one round: k_in input ciphertexts up,
-    n_groups packed ciphertexts down."""
+def round_bytes(info: dict, L: int, n: int, gamma: int = 0) -> tuple:
+    """(upload, download) bytes of one round: k_in input ciphertexts up (and
+    as many powers RLWE(m_j(X^3)) at gamma = 2, Sec. 4.3), n_groups packed
+    ciphertexts down."""
     ct = ciphertext_bytes(L, n)
-    return info["k_in"] * ct, info["n_groups"] * ct
+    return info["k_in"] * ct * (2 if gamma == 2 else 1), info["n_groups"] * ct
 
 
 class ServerSession:

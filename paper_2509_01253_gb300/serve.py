@@ -56,6 +56,7 @@ class Request:
     down_bytes: int = 0
     # the pending round on the device
     d_in: object = None
+    d_pow: object = None     # the client's powers at gamma = 2
     d_out: object = None
     sigma_prev: object = None
     sigma_out: object = None
@@ -66,7 +67,7 @@ class Pool:
     """One parameter set: context, stream, resident weights and client keys."""
 
     def __init__(self, ps: wl.ParamSet, nets: list, n_clients: int, device: int = 0, key_seed: int = 7000,
-                 engine_budget: int = 16 << 30, ks_batch: int = None, priority: int = 0):
+                 engine_budget: int = 16 << 30, ks_batch: int = None, priority: int = 0, gamma: int = 0):
         import torch
         self.torch = torch
         self.ps = ps
@@ -79,7 +80,10 @@ class Pool:
         self.device = f"cuda:{device}"
         self.sks = [sf.sf_keygen(self.ctx, key_seed + 2 * c) for c in range(n_clients)]
         self.rks = [sf.sf_gen_rotation_keys(self.ctx, sk, None, key_seed + 2 * c + 1) for c, sk in enumerate(self.sks)]
-        self.nets = {name: nw.EncodedNetwork(self.params, self.ctx, ps, wl.resnet_rounds(name)) for name in nets}
+        # partial trace extraction level of every request of the pool (Sec. 4.3, 4.4)
+        self.gamma = gamma
+        self.nets = {name: nw.EncodedNetwork(self.params, self.ctx, ps, wl.resnet_rounds(name), gamma=gamma)
+                     for name in nets}
         # CUDA stream priority (lower = higher): the pool of short requests runs
         # above the pool of long ones, so its launches take SMs as they free up
         self.stream = torch.cuda.Stream(device=device, priority=priority)
@@ -90,7 +94,9 @@ class Pool:
         self.last_call = []
 
     def reserve_of(self, net: str) -> int:
-        return self.nets[net].max_cts() * self.ct_bytes
+        # input (and, at gamma = 2, the powers) plus output ciphertexts of the largest round
+        per = max(i["k_in"] * (2 if self.gamma == 2 else 1) + i["n_groups"] for i in self.nets[net].infos)
+        return per * self.ct_bytes
 
     def new_client(self, req: Request) -> nw.ClientState:
         req.session = protocol.ServerSession(req.session_seed, len(self.nets[req.net].rounds))
@@ -110,10 +116,15 @@ class Pool:
         # the upload of round r: checked against the session's next round
         if not req.session.begin(req.session_seed, r):
             raise protocol.ProtocolError("order", f"request {req.rid}: round {r} was evaluated already")
-        req.up_bytes += protocol.round_bytes(info, self.L, self.n)[0]
+        req.up_bytes += protocol.round_bytes(info, self.L, self.n, self.gamma)[0]
         req.d_in = torch.empty((info["k_in"], 2, self.L, self.n), dtype=torch.int64, device=self.device)
         sf.sf_encrypt(self.ctx, self.sks[req.key], msg, req.client.encrypt_seed(r), req.d_in, info["k_in"],
                       self.stream)
+        req.d_pow = None
+        if self.gamma == 2:
+            req.d_pow = torch.empty_like(req.d_in)
+            sf.sf_encrypt(self.ctx, self.sks[req.key], sf.sf_client_power(self.params, msg, info["k_in"], 3),
+                          req.client.power_seed(r), req.d_pow, info["k_in"], self.stream)
         req.d_out = torch.empty((info["n_groups"], 2, self.L, self.n), dtype=torch.int64, device=self.device)
         req.sigma_prev = sp
         req.sigma_out = req.client.sigma_out(r)
@@ -133,13 +144,13 @@ class Pool:
         req.client.absorb(r, vals, req.sigma_out)
         # the simulated client never loses a download here: nothing is kept to resend
         req.session.complete(r, None)
-        req.down_bytes += protocol.round_bytes(info, self.L, self.n)[1]
+        req.down_bytes += protocol.round_bytes(info, self.L, self.n, self.gamma)[1]
         req.rounds_run += 1
-        req.d_in = req.d_out = None
+        req.d_in = req.d_out = req.d_pow = None
 
     def evaluate(self, batch: list):
         """One engine call over the pending rounds of `batch`."""
-        layers, rks, d_ins, k_ins, sps, sos, d_outs, caps = [], [], [], [], [], [], [], []
+        layers, rks, d_ins, d_pows, k_ins, sps, sos, d_outs, caps = [], [], [], [], [], [], [], [], []
         for req in batch:
             net = self.nets[req.net]
             r = req.client.round
@@ -147,13 +158,17 @@ class Pool:
             layers.append(net.layers[r])
             rks.append(self.rks[req.key])
             d_ins.append(req.d_in)
+            d_pows.append(req.d_pow)
             k_ins.append(info["k_in"])
             sps.append(req.sigma_prev)
             sos.append(req.sigma_out)
             d_outs.append(req.d_out)
             caps.append(info["n_groups"])
         self.last_call = [(req.rid, req.net, req.key, req.client.round) for req in batch]
-        sf.sf_eval_layers(self.ctx, layers, rks, d_ins, k_ins, sps, sos, d_outs, caps, self.stream)
+        if self.gamma == 2:
+            sf.sf_eval_layers_gamma(self.ctx, layers, rks, d_ins, d_pows, k_ins, sps, sos, d_outs, caps, self.stream)
+        else:
+            sf.sf_eval_layers(self.ctx, layers, rks, d_ins, k_ins, sps, sos, d_outs, caps, self.stream)
         self.stream.synchronize()
 
     def destroy(self):

@@ -160,3 +160,56 @@ def test_quantised_request_matches_oracle_rounds_and_cleartext(oracle):
         if net is not None:
             net.destroy()
         s.close()
+
+
+@pytest.fixture(scope="module")
+def pool_g2():
+    """A gamma = 2 pool at N = 2^14 with the keys of the p14 pool (same key seed)."""
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    p = serve.Pool(wl.PARAMS["conv16"], ["tiny_b", "resnet20"], 2, 0, key_seed=21, engine_budget=1 << 30, gamma=2)
+    yield p
+    p.destroy()
+
+
+@pytest.mark.gpu
+def test_gamma2_request_matches_float64(pools, pool_g2):
+    """A whole request with partial trace extraction at gamma = 2 (the client
+    sends RLWE(m(X^3)) beside every input ciphertext, every round skips the
+    tau_3 level): each round within 1e-3 of float64 on its actual input, the
+    logits within 1e-3 of the float64 network and of the gamma = 0 request, and
+    the upload doubled."""
+    log2, log0 = protocol.CommLog(), protocol.CommLog()
+    c2 = _alone(pool_g2, "tiny_b", 1, 5, log=log2)
+    c0 = _alone(pools["p14"], "tiny_b", 1, 5, log=log0)
+    encnet = pool_g2.nets["tiny_b"]
+    for r, (x_in, y) in enumerate(c2.trace):
+        assert np.abs(y - nw.round_float_reference(encnet, r, x_in)).max() <= 1e-3, r
+    ref = nw.float_forward(encnet, wl.network_input("tiny_b", 5))
+    assert np.abs(c2.logits() - ref).max() <= 1e-3
+    assert np.abs(c2.logits() - c0.logits()).max() <= 1e-3
+    assert log2.up_bytes == 2 * log0.up_bytes and log2.down_bytes == log0.down_bytes
+
+
+@pytest.mark.gpu
+def test_served_gamma2_mix_equals_alone(pool_g2):
+    """ResNet-20 and tiny_b requests at gamma = 2 under two client keys, three
+    at a time in one engine call (sf_eval_layers_gamma): identical to each
+    request alone."""
+    route = {"resnet20": "g2", "tiny_b": "g2"}
+    specs = [("resnet20", 0, 61), ("tiny_b", 1, 62), ("resnet20", 1, 63)]
+    alone = {seed: _alone(pool_g2, net, key, seed).logits() for net, key, seed in specs}
+    srv = serve.Server({"g2": pool_g2}, route, mem_budget=1 << 36, max_queue=8, max_active=3, max_batch=3)
+    srv.start()
+    import time
+    for i, (net, key, seed) in enumerate(specs):
+        assert srv.submit(serve.make_request(i, net, key, seed))
+    t_end = time.perf_counter() + 600
+    while not srv.idle() and time.perf_counter() < t_end and not srv.errors:
+        time.sleep(0.02)
+    srv.shutdown()
+    assert not srv.errors and len(srv.completed) == 3
+    for req in srv.completed:
+        assert np.array_equal(req.logits, alone[req.request_seed]), req.request_seed
+    ref = nw.float_forward(pool_g2.nets["resnet20"], wl.network_input("resnet20", 61))
+    assert np.abs(alone[61] - ref).max() <= 1e-3

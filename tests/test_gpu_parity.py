@@ -474,16 +474,18 @@ def test_conv16_full_size(oracle):
 
 def test_conv16_launch_shapes_identical():
     """The benchmark round gives the same residues under every launch shape
-    the autotuner can pick: key-switch launch batches of 512 and 4096 merges
-    and both block shapes of the inner product (256 x 8 and 512 x 4)."""
+    the autotuner can pick: key-switch launch batches of 512 and 4096 merges,
+    both block shapes of the inner product (256 x 8 and 512 x 4) and both
+    row-pass sweep schedules (radix 8 and radix 4)."""
     ps = wl.PARAMS["conv16"]
     case = wl.conv16_case()
     s = Session.from_set(ps, sk_seed=203, rk_seed=205)
     try:
         outs = []
-        for batch, nt in ((512, 256), (4096, 256), (512, 512), (4096, 512)):
+        for batch, nt, rad in ((512, 256, 0), (4096, 256, 0), (512, 512, 0), (4096, 512, 0), (512, 256, 1)):
             sf.sf_ctx_set_option(s.ctx, "ks_batch", batch)
             sf.sf_ctx_set_option(s.ctx, "ks3_threads", nt)
+            sf.sf_ctx_set_option(s.ctx, "row_radix", rad)
             lay, info, msg, d_in, got = _run_layer(s, case, ps.delta, ps.delta ** 2, ps.delta)
             outs.append(got)
             sf.sf_layer_destroy(lay)
@@ -829,8 +831,12 @@ def test_largest_ring_rotate_and_leaves(oracle):
         d_ct = s.encrypt(msg, 73, 1)
         ct = from_dev(d_ct).reshape(2, s.L, s.n)
         out = dev_zeros(1, 2, s.L, s.n)
-        sf.sf_rotate(s.ctx, s.rk, 3, d_ct, out, 1)
-        assert (from_dev(out)[0] == oracle.rotate(prm, keys, 3, ct)).all()
+        want = oracle.rotate(prm, keys, 3, ct)
+        for rad in (0, 1):                               # both row-pass sweep schedules
+            sf.sf_ctx_set_option(s.ctx, "row_radix", rad)
+            sf.sf_rotate(s.ctx, s.rk, 3, d_ct, out, 1)
+            assert (from_dev(out)[0] == want).all(), rad
+        sf.sf_ctx_set_option(s.ctx, "row_radix", 0)
         # leaves: stride-2 3x3 conv 16 -> 8 on 96x96x16 plus a 1x1 stride-2 shortcut term: 5 input cts
         case = wl.small_conv_case(75, 96, 96, 16, 8, stride=2, shortcut=True)
         lay = gpu_layer(s, case, ps.delta, ps.delta ** 2)
@@ -848,6 +854,10 @@ def test_largest_ring_rotate_and_leaves(oracle):
         leaves = from_dev(d_leaf)
         for t, o in enumerate(sample):
             assert (leaves[t] == oracle.linear_output(prm, olay, cts, int(o), case.sigma_prev)).all(), o
+        sf.sf_ctx_set_option(s.ctx, "row_radix", 1)
+        d_leaf1 = dev_zeros(len(sample), 2, s.L, s.n)
+        sf.sf_linear_outputs(s.ctx, lay, d_in, info["k_in"], case.sigma_prev, sample, d_leaf1)
+        assert (from_dev(d_leaf1) == leaves).all()
         sf.sf_layer_destroy(lay)
     finally:
         s.close()
