@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--reference-sample-s", type=float, default=8.0,
                     help="--impl reference: CPU seconds bound of each step's oracle sample")
     ap.add_argument("--workload", default="r34", choices=["r34", "conv16", "resnet18", "resnet34", "serve"])
+    ap.add_argument("--gamma", type=int, default=0, choices=[0, 2],
+                    help="resnet34 / serve: partial trace extraction level of every round (Sec. 4.3, 4.4)")
     ap.add_argument("--no-extras", action="store_true",
                     help="r34: skip the conv16, serving and batched-vs-per-layer sub-records")
     ap.add_argument("--rates", default="5,20,200", help="serve: arrival rates (requests/s)")
@@ -247,7 +249,8 @@ class RingShape:
         self.L, self.K, self.dnum = p_info["n_data"], p_info["n_special"], p_info["dnum"]
         self.nm = self.L + self.K
         log_n = self.n.bit_length() - 1
-        self.lc = (log_n + 1) // 2
+        # the library's split N = R x C (2^16 = 128 x 512)
+        self.lc = 9 if log_n == 16 else (log_n + 1) // 2
         self.lr = log_n - self.lc
         self.digits = [min(self.K, self.L - j * self.K) for j in range(self.dnum)]
 
@@ -338,9 +341,6 @@ def load_peaks():
 # items), kept only while the kernel's code is unchanged since the capture;
 # scaled to a full launch by its items
 TRAFFIC_PER_ITEM = {
-    # k_ks2 at N = 2^16 (5 + 2 primes), one launch of 128 merges of the small
-    # r34 case (--small, ks_batch=128): 0.315303 GB read + 947.246336 MB written
-    ("ks2_modup_col", 16): (0.315303e9 + 947.246336e6) / 128,
 }
 
 
@@ -802,7 +802,7 @@ def run_request_e2e(args, local: int) -> int:
     ctx = sf.sf_ctx_create(params, local)
     sk = sf.sf_keygen(ctx, 401)
     rk = sf.sf_gen_rotation_keys(ctx, sk, None, 405)
-    net = nw.EncodedNetwork(params, ctx, ps, wl.resnet_rounds(kind))
+    net = nw.EncodedNetwork(params, ctx, ps, wl.resnet_rounds(kind), gamma=args.gamma)
     x = wl.network_input(kind, 402)
     client = nw.ClientState(net, x, session_seed=404, request_seed=403)
     clocks = ClockSampler(local)
@@ -818,7 +818,8 @@ def run_request_e2e(args, local: int) -> int:
     for r, (x_in, y) in enumerate(client.trace):
         errs.append(float(np.abs(y - nw.round_float_reference(net, r, x_in)).max()))
     R = len(net.rounds)
-    rec = {"metric": METRIC, "unit": UNIT, "workload": kind, "rounds": R, "n": 1 << ps.log_n, "L": ps.n_data,
+    rec = {"metric": METRIC, "unit": UNIT, "workload": kind, "gamma": args.gamma, "rounds": R, "n": 1 << ps.log_n,
+           "L": ps.n_data,
            "ks_total": net.total_ks(), "outputs_total": sum(i["E_out"] for i in net.infos),
            "data": "synthetic: image U(0,1), Kaiming-uniform weights, pool folded into the first block",
            "per_layer_ms": {net.rounds[r].name: ms[r] for r in range(R)},

@@ -444,7 +444,9 @@ sf_status sf_rotate_noalloc(sf_ctx *ctx, const sf_rotkeys *rk, int32_t d, const 
  * canonical, slot j holding the evaluation at psi^(2 brev(j) + 1) with psi a
  * primitive 2N-th root modulo q_i; inverse = 1: NTT-domain values (below
  * 4 q_i) -> canonical coefficients.  Two persistent launches on `stream`.
- * Errors: SF_EINVAL for null buffers, count < 1 or inverse not 0/1. */
+ * Errors: SF_EINVAL for null buffers, count < 1, inverse not 0/1, or a batch
+ * whose count x L x (tiles per limb) exceeds 2^31 - 1 (larger than any
+ * device memory). */
 sf_status sf_ntt_batch(sf_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int32_t count, int32_t inverse,
                        void *stream);
 

@@ -4,11 +4,11 @@
 // The batch is [count][L][N]: limb i of polynomial p is reduced modulo q_i.
 // A transform is the two tiled passes of sf_tile.cuh (forward: column pass,
 // then row pass; inverse: row pass, then column pass with the factor N^-1).
-// Each pass is one persistent launch: a block owns a group (a 16-column or
-// 16-row tile position and a limb), stages that group's twiddles once, and
-// walks the polynomials p = sub, sub + bpg, ... of the batch, prefetching the
-// next polynomial's tile with cp.async while it transforms the current one.
-// gridDim.x = n_groups * bpg, one resident wave.
+// Each pass is one persistent launch of one resident wave over the units
+// (group, polynomial), a group being a column or row tile position and a limb:
+// a block takes an equal range of units (sf_block_units), stages a group's
+// twiddles when its range enters the group, and prefetches the next unit's
+// tile with cp.async while it transforms the current one.
 #include <algorithm>
 
 #include "sf_async.cuh"
@@ -18,72 +18,95 @@
 
 template <bool INV, int LR, int LC>
 __global__ void __launch_bounds__(SfRow<LC>::NT, 3)
-    k_bntt_row(SfRing R, const u64 *src, u64 *dst, int count, int bpg)
+    k_bntt_row(SfRing R, const u64 *src, u64 *dst, int count, int ng)
 {
     constexpr int NT = SfRow<LC>::NT, NB = SfRow<LC>::NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr SfGeoT<LR, LC> g{};
-    const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
-    const int i = grp % R.L, r0 = (grp / R.L) * NB;
-    const SfMod M = R.m[i];
+    const SfUnits U = sf_block_units(ng * count);
     constexpr bool DB = sf_rows_double_buffered(LC);
     sf_tw *tw = (sf_tw *)smem_raw;
     u64 *buf0 = (u64 *)(tw + NB * g.c);
     u64 *buf1 = DB ? buf0 + SfRow<LC>::WORDS : buf0;
-    load_row_tw_t<LR, LC, NT>(tw, INV ? R.rowT_i : R.rowT_f, i, r0);
     const size_t per = (size_t)R.L << (LR + LC);
-    const size_t off = ((size_t)i << (LR + LC)) + (size_t)r0 * g.c;
-    if (DB && sub < count) issue_row_tile_t<LC, NT>(buf0, src + per * sub + off);
+    // unit u: group u / count = (row tile, limb i), item u % count = polynomial
+    auto unit_off = [&](int u) -> size_t {
+        const int gg = u / count;
+        return per * (u % count) + ((size_t)(gg % R.L) << (LR + LC)) + (size_t)(gg / R.L) * NB * g.c;
+    };
+    if (DB && U.u0 < U.u1) issue_row_tile_t<LC, NT>(buf0, src + unit_off(U.u0));
     sf_cp_commit();
-    for (int k = 0, p = sub; p < count; ++k, p += bpg) {
+    int staged = -1;
+    u64 q = 0, one_p = 0;
+    for (int k = 0, u = U.u0; u < U.u1; ++k, ++u) {
+        const int grp = u / count;
+        if (grp != staged) {
+            // the previous unit ended at a barrier: nothing reads tw now
+            const int i = grp % R.L;
+            load_row_tw_t<LR, LC, NT>(tw, INV ? R.rowT_i : R.rowT_f, i, (grp / R.L) * NB);
+            q = R.m[i].q;
+            one_p = R.m[i].one_p;
+            staged = grp;
+        }
         u64 *cur = (k & 1) ? buf1 : buf0, *nxt = (k & 1) ? buf0 : buf1;
         if (DB) {
-            if (p + bpg < count) issue_row_tile_t<LC, NT>(nxt, src + per * (p + bpg) + off);
+            if (u + 1 < U.u1) issue_row_tile_t<LC, NT>(nxt, src + unit_off(u + 1));
             sf_cp_commit();
             sf_cp_wait<1>();
         } else {
-            issue_row_tile_t<LC, NT>(cur, src + per * p + off);
+            issue_row_tile_t<LC, NT>(cur, src + unit_off(u));
             sf_cp_commit();
             sf_cp_wait<0>();
         }
         __syncthreads();
-        if (INV) row_inverse_t<LC, NT>(cur, tw, M.q);
-        else row_forward_t<LC, NT>(cur, tw, M.q);
+        if (INV) row_inverse_t<LC, NT>(cur, tw, q);
+        else row_forward_t<LC, NT>(cur, tw, q);
         // forward: the last pass, canonical output; inverse: lazy in [0, 4q), the column pass follows
-        store_row_tile_t<LC, NT>(dst + per * p + off, cur, [&](u64 v) { return INV ? v : sf_reduce(v, M.q, M.one_p); });
+        store_row_tile_t<LC, NT>(dst + unit_off(u), cur, [&](u64 v) { return INV ? v : sf_reduce(v, q, one_p); });
         __syncthreads();
     }
 }
 
 template <bool INV, int LR, int LC>
 __global__ void __launch_bounds__(SfThreads<LR>::value, LR >= 8 ? 2 : 3)
-    k_bntt_col(SfRing R, const u64 *src, u64 *dst, int count, int bpg)
+    k_bntt_col(SfRing R, const u64 *src, u64 *dst, int count, int ng)
 {
     constexpr int NT = SfThreads<LR>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr SfGeoT<LR, LC> g{};
-    const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
-    const int i = grp % R.L, c0 = (grp / R.L) * SF_NB;
-    const SfMod M = R.m[i];
+    const SfUnits U = sf_block_units(ng * count);
     sf_tw *tw = (sf_tw *)smem_raw;
     u64 *buf0 = (u64 *)(tw + g.r);
     u64 *buf1 = buf0 + tile_words(g.log_r);
-    load_col_tw_t<LR, NT>(tw, INV ? R.colT_i : R.colT_f, i);
     const size_t per = (size_t)R.L << (LR + LC);
-    const size_t off = (size_t)i << (LR + LC);
-    if (sub < count) issue_col_tile_t<LR, LC, NT>(buf0, src + per * sub + off, c0);
+    // unit u: group u / count = (column tile, limb i), item u % count = polynomial
+    auto unit_off = [&](int u) -> size_t { return per * (u % count) + ((size_t)((u / count) % R.L) << (LR + LC)); };
+    auto unit_c0 = [&](int u) -> int { return ((u / count) / R.L) * SF_NB; };
+    if (U.u0 < U.u1) issue_col_tile_t<LR, LC, NT>(buf0, src + unit_off(U.u0), unit_c0(U.u0));
     sf_cp_commit();
-    for (int k = 0, p = sub; p < count; ++k, p += bpg) {
+    int staged = -1;
+    u64 q = 0, ninv = 0, ninv_p = 0;
+    for (int k = 0, u = U.u0; u < U.u1; ++k, ++u) {
+        const int grp = u / count;
+        if (grp != staged) {
+            // the previous unit ended at a barrier: nothing reads tw now
+            const int i = grp % R.L;
+            load_col_tw_t<LR, NT>(tw, INV ? R.colT_i : R.colT_f, i);
+            q = R.m[i].q;
+            ninv = R.m[i].ninv;
+            ninv_p = R.m[i].ninv_p;
+            staged = grp;
+        }
         u64 *cur = (k & 1) ? buf1 : buf0, *nxt = (k & 1) ? buf0 : buf1;
-        if (p + bpg < count) issue_col_tile_t<LR, LC, NT>(nxt, src + per * (p + bpg) + off, c0);
+        if (u + 1 < U.u1) issue_col_tile_t<LR, LC, NT>(nxt, src + unit_off(u + 1), unit_c0(u + 1));
         sf_cp_commit();
         sf_cp_wait<1>();
         __syncthreads();
-        if (INV) tile_inverse_t<LR, false, NT>(cur, tw, M.q);
-        else tile_forward_t<LR, false, NT>(cur, tw, M.q);
+        if (INV) tile_inverse_t<LR, false, NT>(cur, tw, q);
+        else tile_forward_t<LR, false, NT>(cur, tw, q);
         // inverse: the last pass, times N^-1, canonical; forward: lazy, the row pass follows
-        store_col_tile_t<LR, LC, NT>(dst + per * p + off, cur, c0,
-                                     [&](u64 v) { return INV ? sf_mul_shoup(v, M.ninv, M.ninv_p, M.q) : v; });
+        store_col_tile_t<LR, LC, NT>(dst + unit_off(u), cur, unit_c0(u),
+                                     [&](u64 v) { return INV ? sf_mul_shoup(v, ninv, ninv_p, q) : v; });
         __syncthreads();
     }
 }
@@ -99,10 +122,10 @@ static int bntt_occupancy(K kernel, int threads, size_t smem)
     return std::max(1, b);
 }
 
-// one resident wave: blocks per group = SMs x occupancy / groups, at most one per polynomial
-static int bntt_bpg(const sf_ctx *ctx, int occ, int n_groups, int count)
+// one resident wave (SMs x occupancy blocks), at most one block per unit
+static int bntt_blocks(const sf_ctx *ctx, int occ, int n_units)
 {
-    return std::max(1, std::min(ctx->num_sms * occ / n_groups, count));
+    return std::max(1, std::min(ctx->num_sms * occ, n_units));
 }
 
 static size_t bntt_smem_row(const SfRing &R)
@@ -120,27 +143,29 @@ extern "C" sf_status sf_ntt_batch(sf_ctx *ctx, const uint64_t *d_in, uint64_t *d
     const SfRing &R = ctx->ring;
     cudaStream_t st = (cudaStream_t)stream;
     const int rg = (R.r / sf_row_nb(R.log_c)) * R.L, cg = (R.c / SF_NB) * R.L;
+    if ((long long)count * std::max(rg, cg) > INT32_MAX)
+        return sf_set_error(SF_EINVAL, "sf_ntt_batch: count too large");
     const size_t smr = bntt_smem_row(R), smc = bntt_smem_col(R);
     cudaEvent_t ev;
     SF_GEO_DISPATCH(R.log_n, {
         constexpr int NTR = SfRow<LC>::NT, NTC = SfThreads<LR>::value;
         if (!inverse) {
-            const int bc = bntt_bpg(ctx, bntt_occupancy(k_bntt_col<false, LR, LC>, NTC, smc), cg, count);
+            const int bc = bntt_blocks(ctx, bntt_occupancy(k_bntt_col<false, LR, LC>, NTC, smc), cg * count);
             sf_launch_begin(ctx, SFK_BNTT_COL, st, &ev);
-            k_bntt_col<false, LR, LC><<<cg * bc, NTC, smc, st>>>(R, d_in, d_out, count, bc);
+            k_bntt_col<false, LR, LC><<<bc, NTC, smc, st>>>(R, d_in, d_out, count, cg);
             sf_launch_end(ctx, SFK_BNTT_COL, st, ev);
-            const int br = bntt_bpg(ctx, bntt_occupancy(k_bntt_row<false, LR, LC>, NTR, smr), rg, count);
+            const int br = bntt_blocks(ctx, bntt_occupancy(k_bntt_row<false, LR, LC>, NTR, smr), rg * count);
             sf_launch_begin(ctx, SFK_BNTT_ROW, st, &ev);
-            k_bntt_row<false, LR, LC><<<rg * br, NTR, smr, st>>>(R, d_out, d_out, count, br);
+            k_bntt_row<false, LR, LC><<<br, NTR, smr, st>>>(R, d_out, d_out, count, rg);
             sf_launch_end(ctx, SFK_BNTT_ROW, st, ev);
         } else {
-            const int br = bntt_bpg(ctx, bntt_occupancy(k_bntt_row<true, LR, LC>, NTR, smr), rg, count);
+            const int br = bntt_blocks(ctx, bntt_occupancy(k_bntt_row<true, LR, LC>, NTR, smr), rg * count);
             sf_launch_begin(ctx, SFK_BNTT_ROW, st, &ev);
-            k_bntt_row<true, LR, LC><<<rg * br, NTR, smr, st>>>(R, d_in, d_out, count, br);
+            k_bntt_row<true, LR, LC><<<br, NTR, smr, st>>>(R, d_in, d_out, count, rg);
             sf_launch_end(ctx, SFK_BNTT_ROW, st, ev);
-            const int bc = bntt_bpg(ctx, bntt_occupancy(k_bntt_col<true, LR, LC>, NTC, smc), cg, count);
+            const int bc = bntt_blocks(ctx, bntt_occupancy(k_bntt_col<true, LR, LC>, NTC, smc), cg * count);
             sf_launch_begin(ctx, SFK_BNTT_COL, st, &ev);
-            k_bntt_col<true, LR, LC><<<cg * bc, NTC, smc, st>>>(R, d_out, d_out, count, bc);
+            k_bntt_col<true, LR, LC><<<bc, NTC, smc, st>>>(R, d_out, d_out, count, cg);
             sf_launch_end(ctx, SFK_BNTT_COL, st, ev);
         }
     });
@@ -156,7 +181,7 @@ sf_status sf_bntt_init_attributes()
     SF_BNTT_ATTR((k_bntt_row<false, LR, LC>)) SF_BNTT_ATTR((k_bntt_row<true, LR, LC>))                             \
     SF_BNTT_ATTR((k_bntt_col<false, LR, LC>)) SF_BNTT_ATTR((k_bntt_col<true, LR, LC>))
     SF_BNTT_ATTRS(5, 5) SF_BNTT_ATTRS(5, 6) SF_BNTT_ATTRS(6, 6) SF_BNTT_ATTRS(6, 7) SF_BNTT_ATTRS(7, 7)
-    SF_BNTT_ATTRS(7, 8) SF_BNTT_ATTRS(8, 8)
+    SF_BNTT_ATTRS(7, 8) SF_BNTT_ATTRS(7, 9)
 #undef SF_BNTT_ATTRS
 #undef SF_BNTT_ATTR
     return SF_OK;

@@ -493,7 +493,9 @@ extern "C" sf_status sf_ctx_create(const sf_params *p, int32_t device, sf_ctx **
     memset(&R, 0, sizeof(R));
     R.log_n = p->log_n;
     R.n = N;
-    R.log_c = (p->log_n + 1) / 2;
+    // N = R x C: C = 2^ceil(log2 N / 2), except 2^16 = 128 x 512, so that the
+    // column passes of the largest ring keep 128-point columns
+    R.log_c = p->log_n == 16 ? 9 : (p->log_n + 1) / 2;
     R.log_r = p->log_n - R.log_c;
     R.c = 1 << R.log_c;
     R.r = 1 << R.log_r;

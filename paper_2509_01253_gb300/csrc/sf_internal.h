@@ -11,9 +11,10 @@
 
 #define SF_MAX_DIGITS 8
 
-// Rows per row tile of the two-pass NTT: 16, or 8 for 256-point rows, so a
-// row tile holds at most 2048 residues (8 per thread of a 256-thread block).
-SF_HD int sf_row_nb(int log_c) { return log_c >= 8 ? 8 : 16; }
+// Rows per row tile of the two-pass NTT: 16, 8 for 256-point rows, 4 for
+// 512-point rows, so a row tile holds at most 2048 residues (8 per thread of
+// a 256-thread block).
+SF_HD int sf_row_nb(int log_c) { return log_c >= 9 ? 4 : (log_c >= 8 ? 8 : 16); }
 
 // Per-modulus constants, passed to kernels by value (kernel parameter space).
 struct SfMod {

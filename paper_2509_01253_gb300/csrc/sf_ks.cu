@@ -115,11 +115,12 @@ __device__ __forceinline__ u64 merge_v(const SfRing &R, const SfKsBatch &B, cons
 }
 
 // ---------------------------------------------------------------------------
-// Persistent transform kernels.  A block owns one group (a tile position and a
-// modulus or digit), stages that group's twiddles once, and loops over the
-// merges of the launch batch (items it = sub, sub + bpg, ...), prefetching the
-// next item's tiles with cp.async while it transforms the current one.
-// gridDim.x = n_groups * bpg.
+// Persistent transform kernels.  Work units are (group, item) pairs: a group is
+// a tile position and a modulus or digit, an item a merge of the launch batch.
+// One resident wave of blocks splits the units group-major into equal ranges
+// (sf_block_units); a block stages a group's twiddles when its range enters
+// the group and prefetches the next unit's tiles with cp.async while it
+// transforms the current one.
 // ---------------------------------------------------------------------------
 
 
@@ -179,40 +180,49 @@ struct SfRowSet {
 };
 
 template <bool INV, int LR, int LC, int RAD = 0>
-__global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_rows(SfRing R, SfKsBatch B, SfRowSet S, int bpg)
+__global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_rows(SfRing R, SfKsBatch B, SfRowSet S, int ng)
 {
     constexpr int NT = SfRow<LC>::NT, NB = SfRow<LC>::NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr SfGeoT<LR, LC> g{};
-    const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
-    const int t = grp % S.npoly, r0 = (grp / S.npoly) * NB;
-    const int mod = S.mod_base + t % S.mod_period;
-    const SfMod M = R.m[mod];
     const size_t per = sf_ks_scratch_words_dev(R);
-    const size_t off_s = S.src_off + ((size_t)t << (LR + LC)) + (size_t)r0 * g.c;
-    const size_t off_d = S.dst_off + ((size_t)t << (LR + LC)) + (size_t)r0 * g.c;
+    const SfUnits U = sf_block_units(ng * B.count);
     constexpr bool DB = sf_rows_double_buffered(LC);
     sf_tw *tw = (sf_tw *)smem_raw;
     u64 *buf0 = (u64 *)(tw + NB * g.c);
     u64 *buf1 = DB ? buf0 + SfRow<LC>::WORDS : buf0;
-    load_row_tw_t<LR, LC, NT>(tw, INV ? R.rowT_i : R.rowT_f, mod, r0);
-    if (DB && sub < B.count) issue_row_tile_t<LC, NT>(buf0, B.scratch + per * sub + off_s);
+    // unit u: group u / count = (row tile, poly t), item u % count = merge
+    auto unit_off = [&](int u, size_t base) -> size_t {
+        const int grp = u / B.count, t = grp % S.npoly, r0 = (grp / S.npoly) * NB;
+        return per * (u % B.count) + base + ((size_t)t << (LR + LC)) + (size_t)r0 * g.c;
+    };
+    if (DB && U.u0 < U.u1) issue_row_tile_t<LC, NT>(buf0, B.scratch + unit_off(U.u0, S.src_off));
     sf_cp_commit();
-    for (int k = 0, b = sub; b < B.count; ++k, b += bpg) {
+    int staged = -1;
+    u64 q = 0;
+    for (int k = 0, u = U.u0; u < U.u1; ++k, ++u) {
+        const int grp = u / B.count;
+        if (grp != staged) {
+            // the previous unit ended at a barrier: nothing reads tw now
+            const int mod = S.mod_base + (grp % S.npoly) % S.mod_period;
+            load_row_tw_t<LR, LC, NT>(tw, INV ? R.rowT_i : R.rowT_f, mod, (grp / S.npoly) * NB);
+            q = R.m[mod].q;
+            staged = grp;
+        }
         u64 *cur = (k & 1) ? buf1 : buf0, *nxt = (k & 1) ? buf0 : buf1;
         if (DB) {
-            if (b + bpg < B.count) issue_row_tile_t<LC, NT>(nxt, B.scratch + per * (b + bpg) + off_s);
+            if (u + 1 < U.u1) issue_row_tile_t<LC, NT>(nxt, B.scratch + unit_off(u + 1, S.src_off));
             sf_cp_commit();
             sf_cp_wait<1>();
         } else {
-            issue_row_tile_t<LC, NT>(cur, B.scratch + per * b + off_s);
+            issue_row_tile_t<LC, NT>(cur, B.scratch + unit_off(u, S.src_off));
             sf_cp_commit();
             sf_cp_wait<0>();
         }
         __syncthreads();
-        if (INV) row_inverse_t<LC, NT, RAD>(cur, tw, M.q);
-        else row_forward_t<LC, NT, RAD>(cur, tw, M.q);
-        u64 *dst = B.scratch + per * b + off_d;
+        if (INV) row_inverse_t<LC, NT, RAD>(cur, tw, q);
+        else row_forward_t<LC, NT, RAD>(cur, tw, q);
+        u64 *dst = B.scratch + unit_off(u, S.dst_off);
         #pragma unroll
         for (int e = threadIdx.x; e < SfRow<LC>::ELEMS; e += NT) dst[e] = cur[row_slot_t<LC>(e)];
         __syncthreads();
@@ -220,45 +230,64 @@ __global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_rows(SfRing R, SfKsBatch B
 }
 
 // ModUp.  Groups: (column tile, digit j); items: merges.  smem: inverse and
-// forward column tables of every modulus, two buffers of nd source tiles, one
-// work tile.
+// the inverse column tables of the digit's limbs and the forward tables of the
+// other moduli (nm tables in all), the nd source tiles (two buffers when db),
+// one work tile.
 template <int LR, int LC>
-__global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 512 ? 1 : 3) k_ks2(SfRing R, SfKsBatch B, int bpg)
+__global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 512 ? 1 : 3)
+    k_ks2(SfRing R, SfKsBatch B, int ng, int db)
 {
     constexpr int NT = SfThreads<LR>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr SfGeoT<LR, LC> g{};
-    const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
-    const int j = grp % R.dnum, c0 = (grp / R.dnum) * SF_NB;
-    const int lo = j * R.K, hi = min((j + 1) * R.K, R.L), nd = hi - lo;
+    const int maxd = min(R.K, R.L);
     const int tw_words = tile_words(g.log_r);
-    sf_tw *twi = (sf_tw *)smem_raw;                 // [nm][R] inverse
-    sf_tw *twf = twi + (size_t)R.nm * g.r;          // [nm][R] forward
-    u64 *bufs = (u64 *)(twf + (size_t)R.nm * g.r);  // 2 x nd tiles
-    u64 *work = bufs + (size_t)2 * nd * tw_words;
-    for (int m = 0; m < R.nm; ++m) {
-        load_col_tw_t<LR, NT>(twi + (size_t)m * g.r, R.colT_i, m);
-        load_col_tw_t<LR, NT>(twf + (size_t)m * g.r, R.colT_f, m);
-    }
-    if (sub < B.count) {
-        const KsLayout Lo = ks_layout(R, B, sub);
-        for (int t = 0; t < nd; ++t) issue_col_tile_t<LR, LC, NT>(bufs + (size_t)t * tw_words, Lo.x1 + ((size_t)(lo + t) << (LR + LC)), c0);
-    }
+    const SfUnits U = sf_block_units(ng * B.count);
+    sf_tw *twi = (sf_tw *)smem_raw;                 // [nd][R] inverse, the digit's limbs
+    sf_tw *twf = twi;                               // [nm - nd][R] forward, slot m (m < lo) or m - nd (m >= hi)
+    u64 *bufs = (u64 *)(twi + (size_t)R.nm * g.r);  // (db ? 2 : 1) x maxd tiles
+    u64 *work = bufs + (size_t)(db ? 2 : 1) * maxd * tw_words;
+    // unit u: group u / count = (column tile, digit j), item u % count = merge
+    auto issue = [&](u64 *dst, int u) {
+        const int grp = u / B.count, jj = grp % R.dnum, cc = (grp / R.dnum) * SF_NB;
+        const int l0 = jj * R.K, n0 = min((jj + 1) * R.K, R.L) - l0;
+        const KsLayout Ls = ks_layout(R, B, u % B.count);
+        for (int t = 0; t < n0; ++t) issue_col_tile_t<LR, LC, NT>(dst + (size_t)t * tw_words, Ls.x1 + ((size_t)(l0 + t) << (LR + LC)), cc);
+    };
+    if (db && U.u0 < U.u1) issue(bufs, U.u0);
     sf_cp_commit();
-    for (int k = 0, b = sub; b < B.count; ++k, b += bpg) {
-        u64 *cur = bufs + (size_t)(k & 1) * nd * tw_words, *nxt = bufs + (size_t)((k + 1) & 1) * nd * tw_words;
-        if (b + bpg < B.count) {
-            const KsLayout Ln = ks_layout(R, B, b + bpg);
-            for (int t = 0; t < nd; ++t) issue_col_tile_t<LR, LC, NT>(nxt + (size_t)t * tw_words, Ln.x1 + ((size_t)(lo + t) << (LR + LC)), c0);
+    int staged = -1, j = 0, c0 = 0, lo = 0, hi = 0, nd = 0;
+    for (int k = 0, u = U.u0; u < U.u1; ++k, ++u) {
+        const int grp = u / B.count, b = u % B.count;
+        if (grp != staged) {
+            // the previous unit ended at a barrier: nothing reads the tables now
+            j = grp % R.dnum;
+            c0 = (grp / R.dnum) * SF_NB;
+            lo = j * R.K;
+            hi = min((j + 1) * R.K, R.L);
+            nd = hi - lo;
+            twf = twi + (size_t)nd * g.r;
+            for (int t = 0; t < nd; ++t) load_col_tw_t<LR, NT>(twi + (size_t)t * g.r, R.colT_i, lo + t);
+            for (int m = 0; m < R.nm; ++m)
+                if (m < lo || m >= hi) load_col_tw_t<LR, NT>(twf + (size_t)(m < lo ? m : m - nd) * g.r, R.colT_f, m);
+            staged = grp;
         }
-        sf_cp_commit();
-        sf_cp_wait<1>();
+        u64 *cur = bufs + (size_t)(db ? (k & 1) : 0) * maxd * tw_words, *nxt = bufs + (size_t)((k + 1) & 1) * maxd * tw_words;
+        if (db) {
+            if (u + 1 < U.u1) issue(nxt, u + 1);
+            sf_cp_commit();
+            sf_cp_wait<1>();
+        } else {
+            issue(cur, u);
+            sf_cp_commit();
+            sf_cp_wait<0>();
+        }
         __syncthreads();
         // inverse column pass of the digit's limbs, then y_i = x_i N^-1 Qhat_i^-1 mod q_i
         for (int t = 0; t < nd; ++t) {
             const int i = lo + t;
             u64 *st = cur + (size_t)t * tw_words;
-            tile_inverse_t<LR, false, NT>(st, twi + (size_t)i * g.r, R.m[i].q);
+            tile_inverse_t<LR, false, NT>(st, twi + (size_t)t * g.r, R.m[i].q);
             const u64 w = R.mu_inv[j * R.K + t], wp = R.mu_inv_p[j * R.K + t];
             #pragma unroll
             for (int e = threadIdx.x; e < (SF_NB << LR); e += NT)
@@ -295,7 +324,7 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
                 }
             }
             __syncthreads();
-            tile_forward_t<LR, false, NT>(work, twf + (size_t)m * g.r, M.q);
+            tile_forward_t<LR, false, NT>(work, twf + (size_t)(m < lo ? m : m - nd) * g.r, M.q);
             u64 *dst = Lo.x2 + ((size_t)(j * R.nm + m) << (LR + LC));
             #pragma unroll
             for (int e = threadIdx.x; e < (SF_NB << LR); e += NT) dst[col_gidx_t<LC>(c0, e)] = work[col_slot(e)];
@@ -309,40 +338,52 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
 // Output: ACC (data moduli, NTT domain) or, for the special moduli, their NTT
 // values in the x1 region (the inverse row pass runs in k_rows<true>).
 // NT: 256 (8 elements per thread, three blocks per SM) or, for 128-point
-// rows, 512 (4 elements per thread, half the accumulator registers, two
-// 16-warp blocks per SM); 256-point rows always run 512.
+// rows when the context asks for it, 512 (4 elements per thread, half the
+// accumulator registers, two 16-warp blocks per SM).
 template <int LR, int LC, int NT, int RAD = 0>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) k_ks3(SfRing R, SfKsBatch B, int bpg)
+__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) k_ks3(SfRing R, SfKsBatch B, int ng)
 {
     constexpr int NB = SfRow<LC>::NB, EPT = SfRow<LC>::ELEMS / NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr SfGeoT<LR, LC> g{};
-    const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
-    const int m = grp % R.nm, r0 = (grp / R.nm) * NB;
-    const SfMod M = R.m[m];
-    const size_t tile_off = (size_t)r0 * g.c;
+    const SfUnits U = sf_block_units(ng * B.count);
     constexpr bool DB = true;
     sf_tw *tw = (sf_tw *)smem_raw;
     u64 *buf0 = (u64 *)(tw + NB * g.c);
     u64 *buf1 = DB ? buf0 + SfRow<LC>::WORDS : buf0;
-    load_row_tw_t<LR, LC, NT>(tw, R.rowT_f, m, r0);
-    const int n_mine = sub < B.count ? (B.count - sub + bpg - 1) / bpg : 0;
-    const int steps = n_mine * R.dnum;
-    // step k -> merge sub + (k / dnum) * bpg, digit k % dnum; its tile is TA's
-    // limb m when m is one of digit j's own limbs, else the digit's extension
+    const int steps = (U.u1 - U.u0) * R.dnum;
+    // step k -> unit U.u0 + k / dnum (group (row tile, modulus m), item a
+    // merge), digit k % dnum; its tile is TA's limb m when m is one of digit
+    // j's own limbs, else the digit's extension
     auto step_src = [&](int kk) -> const u64 * {
-        const int bb = sub + (kk / R.dnum) * bpg, jj = kk % R.dnum;
-        const KsLayout Ls = ks_layout(R, B, bb);
-        const bool own_s = (m >= jj * R.K && m < min((jj + 1) * R.K, R.L));
-        return (own_s ? Ls.ta + ((size_t)m << (LR + LC)) : Ls.x2 + ((size_t)(jj * R.nm + m) << (LR + LC))) + tile_off;
+        const int uu = U.u0 + kk / R.dnum, jj = kk % R.dnum;
+        const int gg = uu / B.count, ms = gg % R.nm;
+        const KsLayout Ls = ks_layout(R, B, uu % B.count);
+        const bool own_s = (ms >= jj * R.K && ms < min((jj + 1) * R.K, R.L));
+        return (own_s ? Ls.ta + ((size_t)ms << (LR + LC)) : Ls.x2 + ((size_t)(jj * R.nm + ms) << (LR + LC))) +
+               (size_t)(gg / R.nm) * NB * g.c;
     };
     if (DB && steps > 0) issue_row_tile_t<LC, NT>(buf0, step_src(0));
     sf_cp_commit();
     u64 acc_a[EPT], acc_b[EPT];
 #pragma unroll
     for (int x = 0; x < EPT; ++x) acc_a[x] = acc_b[x] = 0;
+    int staged = -1, m = 0;
+    size_t tile_off = 0;
+    u64 q = 0, one_p = 0;
     for (int k = 0; k < steps; ++k) {
-        const int b = sub + (k / R.dnum) * bpg, j = k % R.dnum;
+        const int u = U.u0 + k / R.dnum, j = k % R.dnum;
+        const int grp = u / B.count, b = u % B.count;
+        if (grp != staged) {
+            // a new group starts at digit 0, after the previous unit's last barrier
+            m = grp % R.nm;
+            const int r0 = (grp / R.nm) * NB;
+            tile_off = (size_t)r0 * g.c;
+            load_row_tw_t<LR, LC, NT>(tw, R.rowT_f, m, r0);
+            q = R.m[m].q;
+            one_p = R.m[m].one_p;
+            staged = grp;
+        }
         u64 *cur = (k & 1) ? buf1 : buf0, *nxt = (k & 1) ? buf0 : buf1;
         if (DB) {
             if (k + 1 < steps) issue_row_tile_t<LC, NT>(nxt, step_src(k + 1));
@@ -355,7 +396,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) k_ks3(SfRing R, SfKsBat
         }
         __syncthreads();
         const bool own = (m >= j * R.K && m < min((j + 1) * R.K, R.L));
-        if (!own) tile_forward_t<LC, true, NT, NB, RAD>(cur, tw, M.q);
+        if (!own) tile_forward_t<LC, true, NT, NB, RAD>(cur, tw, q);
         const size_t comp = (size_t)R.dnum * 2 * R.nm << (LR + LC);   // companions follow the key values
         const u64 *ka = B.key + ((((size_t)j * 2 + 0) * R.nm + m) << (LR + LC)) + tile_off;
         const u64 *kb = B.key + ((((size_t)j * 2 + 1) * R.nm + m) << (LR + LC)) + tile_off;
@@ -364,8 +405,8 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) k_ks3(SfRing R, SfKsBat
         for (int x = 0; x < EPT; ++x) {
             const int e = threadIdx.x + x * NT;
             const u64 c = cur[row_slot_t<LC>(e)];
-            acc_a[x] += sf_mul_shoup_lazy4(c, __ldg(ka + e), __ldg(ka + comp + e), M.q);
-            acc_b[x] += sf_mul_shoup_lazy4(c, __ldg(kb + e), __ldg(kb + comp + e), M.q);
+            acc_a[x] += sf_mul_shoup_lazy4(c, __ldg(ka + e), __ldg(ka + comp + e), q);
+            acc_b[x] += sf_mul_shoup_lazy4(c, __ldg(kb + e), __ldg(kb + comp + e), q);
         }
         if (j == R.dnum - 1) {
             const KsLayout Lo = ks_layout(R, B, b);
@@ -380,8 +421,8 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) k_ks3(SfRing R, SfKsBat
 #pragma unroll
             for (int x = 0; x < EPT; ++x) {
                 const int e = threadIdx.x + x * NT;
-                da[e] = sf_reduce(acc_a[x], M.q, M.one_p);
-                db[e] = sf_reduce(acc_b[x], M.q, M.one_p);
+                da[e] = sf_reduce(acc_a[x], q, one_p);
+                db[e] = sf_reduce(acc_b[x], q, one_p);
                 acc_a[x] = acc_b[x] = 0;
             }
         }
@@ -390,38 +431,46 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) k_ks3(SfRing R, SfKsBat
 }
 
 // ModDown conversion.  Groups: (column tile, part p); items: merges.  smem: K
-// inverse (special) + L forward (data) column tables, two buffers of K tiles,
-// one work tile.
+// inverse (special) + L forward (data) column tables, K source tiles (two
+// buffers when db), one work tile.
 template <int LR, int LC>
-__global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 512 ? 1 : 3) k_ks4(SfRing R, SfKsBatch B, int bpg)
+__global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 512 ? 1 : 3)
+    k_ks4(SfRing R, SfKsBatch B, int ng, int db)
 {
     constexpr int NT = SfThreads<LR>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr SfGeoT<LR, LC> g{};
-    const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
-    const int p = grp % 2, c0 = (grp / 2) * SF_NB;
+    const SfUnits U = sf_block_units(ng * B.count);
     const int tw_words = tile_words(g.log_r);
     sf_tw *twi = (sf_tw *)smem_raw;                 // [K][R] inverse, special moduli
     sf_tw *twf = twi + (size_t)R.K * g.r;           // [L][R] forward, data moduli
-    u64 *bufs = (u64 *)(twf + (size_t)R.L * g.r);   // 2 x K tiles
-    u64 *work = bufs + (size_t)2 * R.K * tw_words;
+    u64 *bufs = (u64 *)(twf + (size_t)R.L * g.r);   // (db ? 2 : 1) x K tiles
+    u64 *work = bufs + (size_t)(db ? 2 : 1) * R.K * tw_words;
     for (int k = 0; k < R.K; ++k) load_col_tw_t<LR, NT>(twi + (size_t)k * g.r, R.colT_i, R.L + k);
     for (int i = 0; i < R.L; ++i) load_col_tw_t<LR, NT>(twf + (size_t)i * g.r, R.colT_f, i);
-    if (sub < B.count) {
-        const KsLayout Lo = ks_layout(R, B, sub);
+    // unit u: group u / count = (column tile, part p), item u % count = merge;
+    // the staged tables are the same for every group
+    auto issue = [&](u64 *dst, int u) {
+        const int gg = u / B.count, pp = gg % 2, cc = (gg / 2) * SF_NB;
+        const KsLayout Ls = ks_layout(R, B, u % B.count);
         for (int k = 0; k < R.K; ++k)
-            issue_col_tile_t<LR, LC, NT>(bufs + (size_t)k * tw_words, Lo.x1 + ((size_t)(p * R.K + k) << (LR + LC)), c0);
-    }
+            issue_col_tile_t<LR, LC, NT>(dst + (size_t)k * tw_words, Ls.x1 + ((size_t)(pp * R.K + k) << (LR + LC)), cc);
+    };
+    if (db && U.u0 < U.u1) issue(bufs, U.u0);
     sf_cp_commit();
-    for (int kk = 0, b = sub; b < B.count; ++kk, b += bpg) {
-        u64 *cur = bufs + (size_t)(kk & 1) * R.K * tw_words, *nxt = bufs + (size_t)((kk + 1) & 1) * R.K * tw_words;
-        if (b + bpg < B.count) {
-            const KsLayout Ln = ks_layout(R, B, b + bpg);
-            for (int k = 0; k < R.K; ++k)
-                issue_col_tile_t<LR, LC, NT>(nxt + (size_t)k * tw_words, Ln.x1 + ((size_t)(p * R.K + k) << (LR + LC)), c0);
+    for (int kk = 0, u = U.u0; u < U.u1; ++kk, ++u) {
+        const int grp = u / B.count, b = u % B.count;
+        const int p = grp % 2, c0 = (grp / 2) * SF_NB;
+        u64 *cur = bufs + (size_t)(db ? (kk & 1) : 0) * R.K * tw_words, *nxt = bufs + (size_t)((kk + 1) & 1) * R.K * tw_words;
+        if (db) {
+            if (u + 1 < U.u1) issue(nxt, u + 1);
+            sf_cp_commit();
+            sf_cp_wait<1>();
+        } else {
+            issue(cur, u);
+            sf_cp_commit();
+            sf_cp_wait<0>();
         }
-        sf_cp_commit();
-        sf_cp_wait<1>();
         __syncthreads();
         for (int k = 0; k < R.K; ++k) {
             const int m = R.L + k;
@@ -467,38 +516,50 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
 // tiles (double-buffered); ACC and out are read elementwise from global into
 // registers before the row pass.
 template <int LR, int LC, int RAD = 0>
-__global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_ks5(SfRing R, SfKsBatch B, int bpg)
+__global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_ks5(SfRing R, SfKsBatch B, int ng)
 {
     constexpr int NT = SfRow<LC>::NT, NB = SfRow<LC>::NB, EPT = SfRow<LC>::ELEMS / NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr SfGeoT<LR, LC> g{};
-    const int grp = blockIdx.x / bpg, sub = blockIdx.x % bpg;
-    const int i = grp % R.L, r0 = (grp / R.L) * NB;
-    const SfMod M = R.m[i];
-    const size_t tile_off = (size_t)r0 * g.c;
+    const int n_items = 2 * B.count;
+    const SfUnits U = sf_block_units(ng * n_items);
     const int tw_words = SfRow<LC>::WORDS;
     constexpr bool DB = true;
     sf_tw *tw = (sf_tw *)smem_raw;
     u64 *bufs = (u64 *)(tw + NB * g.c);             // 2 conversion tiles
-    load_row_tw_t<LR, LC, NT>(tw, R.rowT_f, i, r0);
-    const int n_items = 2 * B.count;
-    auto item_src = [&](int it2) -> const u64 * {
+    // unit u: group u / n_items = (row tile, limb i), item u % n_items = (merge, part)
+    auto unit_src = [&](int uu) -> const u64 * {
+        const int gg = uu / n_items, it2 = uu % n_items;
         const KsLayout Ls = ks_layout(R, B, it2 >> 1);
-        return Ls.x2 + ((size_t)((it2 & 1) * R.L + i) << (LR + LC)) + tile_off;
+        return Ls.x2 + ((size_t)((it2 & 1) * R.L + gg % R.L) << (LR + LC)) + (size_t)(gg / R.L) * NB * g.c;
     };
-    if (DB && sub < n_items) issue_row_tile_t<LC, NT>(bufs, item_src(sub));
+    if (DB && U.u0 < U.u1) issue_row_tile_t<LC, NT>(bufs, unit_src(U.u0));
     sf_cp_commit();
-    // conv leaves the lazy forward transform below 72 q (inputs below 2 K q <= 8 q,
-    // at most 16 stages adding 4 q each); 128 q keeps the sum positive
-    const u64 conv_off = 128 * M.q;
-    for (int k = 0, it = sub; it < n_items; ++k, it += bpg) {
+    int staged = -1, i = 0;
+    size_t tile_off = 0;
+    u64 q = 0, one_p = 0, conv_off = 0;
+    for (int k = 0, u = U.u0; u < U.u1; ++k, ++u) {
+        const int grp = u / n_items, it = u % n_items;
+        if (grp != staged) {
+            // the previous unit ended at a barrier: nothing reads tw now
+            i = grp % R.L;
+            const int r0 = (grp / R.L) * NB;
+            tile_off = (size_t)r0 * g.c;
+            load_row_tw_t<LR, LC, NT>(tw, R.rowT_f, i, r0);
+            q = R.m[i].q;
+            one_p = R.m[i].one_p;
+            // conv leaves the lazy forward transform below 72 q (inputs below 2 K q <= 8 q,
+            // at most 16 stages adding 4 q each); 128 q keeps the sum positive
+            conv_off = 128 * q;
+            staged = grp;
+        }
         u64 *cur = bufs + (DB ? (size_t)(k & 1) * tw_words : 0), *nxt = bufs + (DB ? (size_t)((k + 1) & 1) * tw_words : 0);
         if (DB) {
-            if (it + bpg < n_items) issue_row_tile_t<LC, NT>(nxt, item_src(it + bpg));
+            if (u + 1 < U.u1) issue_row_tile_t<LC, NT>(nxt, unit_src(u + 1));
             sf_cp_commit();
             sf_cp_wait<1>();
         } else {
-            issue_row_tile_t<LC, NT>(cur, item_src(it));
+            issue_row_tile_t<LC, NT>(cur, unit_src(u));
             sf_cp_commit();
             sf_cp_wait<0>();
         }
@@ -515,12 +576,12 @@ __global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_ks5(SfRing R, SfKsBatch B,
             vo[x] = out[threadIdx.x + x * NT];
         }
         __syncthreads();
-        row_forward_t<LC, NT, RAD>(cur, tw, M.q);
+        row_forward_t<LC, NT, RAD>(cur, tw, q);
         // acc and conv both carry P^-1 already: out += acc - conv, one reduction
 #pragma unroll
         for (int x = 0; x < EPT; ++x) {
             const int e = threadIdx.x + x * NT;
-            out[e] = sf_reduce(vo[x] + va[x] + conv_off - cur[row_slot_t<LC>(e)], M.q, M.one_p);
+            out[e] = sf_reduce(vo[x] + va[x] + conv_off - cur[row_slot_t<LC>(e)], q, one_p);
         }
         __syncthreads();
     }
@@ -544,15 +605,13 @@ static int occupancy(K kernel, int threads, size_t smem)
     return std::max(1, b);
 }
 
-// blocks per group: as many as one resident wave holds (num_sms x occupancy
-// blocks in all), at most one block per item.  Rounding up instead would
-// leave a second wave of a few blocks that starts only when the first wave
-// ends, doubling the kernel's time.
-static int blocks_per_group(const sf_ctx *ctx, int occ, int n_groups, int n_items)
+// blocks of a persistent launch over n_units (group, item) units: one
+// resident wave (num_sms x occupancy blocks), at most one block per unit.
+// The kernels split the units evenly (sf_block_units), so no block slot idles
+// when the group count does not divide the wave.
+static int wave_blocks(const sf_ctx *ctx, int occ, int n_units)
 {
-    const int target = ctx->num_sms * occ;
-    const int bpg = target / n_groups;
-    return std::max(1, std::min(bpg, n_items));
+    return std::max(1, std::min(ctx->num_sms * occ, n_units));
 }
 
 // The 512-thread inner product (128-point rows only, when the context asks
@@ -563,8 +622,8 @@ static bool ks3_launch_wide(sf_ctx *ctx, const SfKsBatch &b, size_t sm3, int ng,
 {
     if constexpr (LC == 7) {
         if (ctx->ks3_threads != 512) return false;
-        const int bpg = blocks_per_group(ctx, occupancy(k_ks3<LR, LC, 512>, 512, sm3), ng, b.count);
-        k_ks3<LR, LC, 512><<<ng * bpg, 512, sm3, st>>>(ctx->ring, b, bpg);
+        const int nb = wave_blocks(ctx, occupancy(k_ks3<LR, LC, 512>, 512, sm3), ng * b.count);
+        k_ks3<LR, LC, 512><<<nb, 512, sm3, st>>>(ctx->ring, b, ng);
         return true;
     } else {
         return false;
@@ -579,9 +638,13 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
     const int rtiles = R.r / sf_row_nb(R.log_c), ctiles = R.c / SF_NB;
     const int row_bufs = sf_rows_double_buffered(R.log_c) ? 2 : 1;
     const size_t sm_rows = smem_rows(R, row_bufs);
-    const size_t sm2 = sizeof(sf_tw) * 2 * R.nm * R.r + sizeof(u64) * tile_words(R.log_r) * (2 * maxd + 1);
+    // ks2 / ks4 shared memory with two buffers of source tiles (db) or one
+    const size_t tw_bytes = sizeof(u64) * tile_words(R.log_r);
+    const size_t sm2[2] = {sizeof(sf_tw) * R.nm * R.r + tw_bytes * (maxd + 1),
+                           sizeof(sf_tw) * R.nm * R.r + tw_bytes * (2 * maxd + 1)};
     const size_t sm3 = smem_rows(R, 2);
-    const size_t sm4 = sizeof(sf_tw) * (R.K + R.L) * R.r + sizeof(u64) * tile_words(R.log_r) * (2 * R.K + 1);
+    const size_t sm4[2] = {sizeof(sf_tw) * (R.K + R.L) * R.r + tw_bytes * (R.K + 1),
+                           sizeof(sf_tw) * (R.K + R.L) * R.r + tw_bytes * (2 * R.K + 1)};
     const size_t sm5 = smem_rows(R, 2);
     cudaEvent_t ev;
     for (int off = 0; off < B0.count; off += 32768) {
@@ -602,8 +665,8 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
                 const SfRowSet S{0, (size_t)R.L << R.log_n, R.L, 0, R.L};   // TA -> X1
                 const int ng = rtiles * S.npoly;
                 SF_RAD_DISPATCH(ctx->row_radix, {
-                    const int bpg = blocks_per_group(ctx, occupancy(k_rows<true, LR, LC, RAD>, NTR, sm_rows), ng, b.count);
-                    k_rows<true, LR, LC, RAD><<<ng * bpg, NTR, sm_rows, st>>>(R, b, S, bpg);
+                    const int nb = wave_blocks(ctx, occupancy(k_rows<true, LR, LC, RAD>, NTR, sm_rows), ng * b.count);
+                    k_rows<true, LR, LC, RAD><<<nb, NTR, sm_rows, st>>>(R, b, S, ng);
                 });
             }
             sf_launch_end(ctx, SFK_KS1_INV_ROW, st, ev);
@@ -611,8 +674,10 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
             sf_launch_begin(ctx, SFK_KS2_MODUP_COL, st, &ev);
             {
                 const int ng = ctiles * R.dnum;
-                const int bpg = blocks_per_group(ctx, occupancy(k_ks2<LR, LC>, NTC, sm2), ng, b.count);
-                k_ks2<LR, LC><<<ng * bpg, NTC, sm2, st>>>(R, b, bpg);
+                const int o1 = occupancy(k_ks2<LR, LC>, NTC, sm2[0]), o2 = occupancy(k_ks2<LR, LC>, NTC, sm2[1]);
+                const int db = o2 >= o1;   // double-buffer unless one buffer fits more blocks
+                const int nb = wave_blocks(ctx, db ? o2 : o1, ng * b.count);
+                k_ks2<LR, LC><<<nb, NTC, sm2[db], st>>>(R, b, ng, db);
             }
             sf_launch_end(ctx, SFK_KS2_MODUP_COL, st, ev);
 
@@ -621,8 +686,8 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
                 const int ng = rtiles * R.nm;
                 if (!ks3_launch_wide<LR, LC>(ctx, b, sm3, ng, st)) {
                     SF_RAD_DISPATCH(ctx->row_radix, {
-                        const int bpg = blocks_per_group(ctx, occupancy(k_ks3<LR, LC, NTR, RAD>, NTR, sm3), ng, b.count);
-                        k_ks3<LR, LC, NTR, RAD><<<ng * bpg, NTR, sm3, st>>>(R, b, bpg);
+                        const int nb = wave_blocks(ctx, occupancy(k_ks3<LR, LC, NTR, RAD>, NTR, sm3), ng * b.count);
+                        k_ks3<LR, LC, NTR, RAD><<<nb, NTR, sm3, st>>>(R, b, ng);
                     });
                 }
             }
@@ -633,8 +698,8 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
                 const SfRowSet S{(size_t)R.L << R.log_n, (size_t)R.L << R.log_n, 2 * R.K, R.L, R.K};
                 const int ng2 = rtiles * S.npoly;
                 SF_RAD_DISPATCH(ctx->row_radix, {
-                    const int bpg2 = blocks_per_group(ctx, occupancy(k_rows<true, LR, LC, RAD>, NTR, sm_rows), ng2, b.count);
-                    k_rows<true, LR, LC, RAD><<<ng2 * bpg2, NTR, sm_rows, st>>>(R, b, S, bpg2);
+                    const int nb2 = wave_blocks(ctx, occupancy(k_rows<true, LR, LC, RAD>, NTR, sm_rows), ng2 * b.count);
+                    k_rows<true, LR, LC, RAD><<<nb2, NTR, sm_rows, st>>>(R, b, S, ng2);
                 });
             }
             sf_launch_end(ctx, SFK_KS3_INV_ROW_P, st, ev);
@@ -642,8 +707,10 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
             sf_launch_begin(ctx, SFK_KS4_MODDOWN_COL, st, &ev);
             {
                 const int ng = ctiles * 2;
-                const int bpg = blocks_per_group(ctx, occupancy(k_ks4<LR, LC>, NTC, sm4), ng, b.count);
-                k_ks4<LR, LC><<<ng * bpg, NTC, sm4, st>>>(R, b, bpg);
+                const int o1 = occupancy(k_ks4<LR, LC>, NTC, sm4[0]), o2 = occupancy(k_ks4<LR, LC>, NTC, sm4[1]);
+                const int db = o2 >= o1;
+                const int nb = wave_blocks(ctx, db ? o2 : o1, ng * b.count);
+                k_ks4<LR, LC><<<nb, NTC, sm4[db], st>>>(R, b, ng, db);
             }
             sf_launch_end(ctx, SFK_KS4_MODDOWN_COL, st, ev);
 
@@ -651,8 +718,8 @@ sf_status sf_ks_launch(sf_ctx *ctx, const SfKsBatch &B0, cudaStream_t st)
             {
                 const int ng = rtiles * R.L;
                 SF_RAD_DISPATCH(ctx->row_radix, {
-                    const int bpg = blocks_per_group(ctx, occupancy(k_ks5<LR, LC, RAD>, NTR, sm5), ng, 2 * b.count);
-                    k_ks5<LR, LC, RAD><<<ng * bpg, NTR, sm5, st>>>(R, b, bpg);
+                    const int nb = wave_blocks(ctx, occupancy(k_ks5<LR, LC, RAD>, NTR, sm5), ng * 2 * b.count);
+                    k_ks5<LR, LC, RAD><<<nb, NTR, sm5, st>>>(R, b, ng);
                 });
             }
             sf_launch_end(ctx, SFK_KS5_FINISH_ROW, st, ev);
@@ -688,7 +755,7 @@ sf_status sf_ks_init_attributes()
     SF_KS_ATTR((k_ks4<LR, LC>)) SF_KS_ATTR((k_ks5<LR, LC>)) SF_KS_ATTR((k_rows<true, LR, LC, 1>))               \
     SF_KS_ATTR((k_ks3<LR, LC, SfRow<LC>::NT, 1>)) SF_KS_ATTR((k_ks5<LR, LC, 1>))
     SF_KS_ATTRS(5, 5) SF_KS_ATTRS(5, 6) SF_KS_ATTRS(6, 6) SF_KS_ATTRS(6, 7) SF_KS_ATTRS(7, 7) SF_KS_ATTRS(7, 8)
-    SF_KS_ATTRS(8, 8)
+    SF_KS_ATTRS(7, 9)
     SF_KS_ATTR((k_ks3<6, 7, 512>)) SF_KS_ATTR((k_ks3<7, 7, 512>))
 #undef SF_KS_ATTRS
 #undef SF_KS_ATTR

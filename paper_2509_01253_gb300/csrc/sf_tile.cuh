@@ -66,14 +66,15 @@ typedef ulonglong2 sf_tw;   // (w, w')
 
 // Shared-memory word of element k of sub-transform b in a tile of NB
 // sub-transforms.  NB = 16: a padded row of 17 words per k (conflict-free for
-// the sweeps and the coalesced copies).  NB = 8: rows of 8 words with the
-// sub-transform index XOR-swizzled by bits 1..3 of k, so that 16 consecutive
-// k of one b (a coalesced copy) hit 16 distinct bank pairs, and so do the two
-// units of a half-warp in every sweep whose units start an odd distance apart.
+// the sweeps and the coalesced copies).  NB = 8 (4): rows of 8 (4) words with
+// the sub-transform index XOR-swizzled by bits 1..3 (2..3) of k, so that 16
+// consecutive k of one b (a coalesced copy) hit 16 distinct bank pairs, and so
+// do the units of a half-warp in every sweep whose units start consecutively.
 template <int NB>
 __device__ __forceinline__ int tile_slot(int k, int b)
 {
     if constexpr (NB == 8) return (k << 3) + (b ^ ((k >> 1) & 7));
+    else if constexpr (NB == 4) return (k << 2) + (b ^ ((k >> 2) & 3));
     else return k * (NB + 1) + b;
 }
 
@@ -82,7 +83,7 @@ __host__ __device__ __forceinline__ int tile_words(int log_s) { return (1 << log
 // words of a row tile buffer (2^log_c rows of sf_row_nb(log_c) + 1 words)
 __host__ __device__ __forceinline__ int row_tile_words(int log_c)
 {
-    return (1 << log_c) * (sf_row_nb(log_c) == 8 ? 8 : sf_row_nb(log_c) + 1);
+    return (1 << log_c) * (sf_row_nb(log_c) < 16 ? sf_row_nb(log_c) : sf_row_nb(log_c) + 1);
 }
 
 // One sweep of R_ST consecutive stages over every unit of the tile.
@@ -93,7 +94,7 @@ __device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
     constexpr int S = 1 << LOG_S;
     constexpr int U = 1 << R_ST;
     constexpr int UNITS = NB * S / U;
-    constexpr int LOG_NB = NB == 8 ? 3 : 4;
+    constexpr int LOG_NB = NB == 4 ? 2 : (NB == 8 ? 3 : 4);
     constexpr int ITER = (UNITS + NT - 1) / NT;
     constexpr int LOG_STEP = INV ? LOG_H0 : (LOG_H0 - (R_ST - 1));
     constexpr int LOG_BLK = INV ? (LOG_H0 + R_ST) : (LOG_H0 + 1);
@@ -142,7 +143,8 @@ __device__ __forceinline__ void tile_forward_t(u64 *s, const sf_tw *tw, u64 q)
         if constexpr (LOG_S >= 6) tile_sweep<LOG_S, LOG_S - 5, 2, false, ROWTW, NT, NB>(s, tw, q);
         else tile_sweep<LOG_S, 0, 1, false, ROWTW, NT, NB>(s, tw, q);
         if constexpr (LOG_S == 7) tile_sweep<LOG_S, 0, 1, false, ROWTW, NT, NB>(s, tw, q);
-        if constexpr (LOG_S == 8) tile_sweep<LOG_S, 1, 2, false, ROWTW, NT, NB>(s, tw, q);
+        if constexpr (LOG_S >= 8) tile_sweep<LOG_S, LOG_S - 7, 2, false, ROWTW, NT, NB>(s, tw, q);
+        if constexpr (LOG_S == 9) tile_sweep<LOG_S, 0, 1, false, ROWTW, NT, NB>(s, tw, q);
     } else if constexpr (LOG_S == 7 && NT == 512) {
         tile_sweep<7, 6, 2, false, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<7, 4, 2, false, ROWTW, NT, NB>(s, tw, q);
@@ -158,10 +160,14 @@ __device__ __forceinline__ void tile_forward_t(u64 *s, const sf_tw *tw, u64 q)
         tile_sweep<7, 6, 3, false, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<7, 3, 2, false, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<7, 1, 2, false, ROWTW, NT, NB>(s, tw, q);
-    } else {
+    } else if constexpr (LOG_S == 8) {
         tile_sweep<8, 7, 3, false, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<8, 4, 3, false, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<8, 1, 2, false, ROWTW, NT, NB>(s, tw, q);
+    } else {
+        tile_sweep<9, 8, 3, false, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<9, 5, 3, false, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<9, 2, 3, false, ROWTW, NT, NB>(s, tw, q);
     }
 }
 
@@ -175,7 +181,8 @@ __device__ __forceinline__ void tile_inverse_t(u64 *s, const sf_tw *tw, u64 q)
         if constexpr (LOG_S == 5) tile_sweep<LOG_S, 4, 1, true, ROWTW, NT, NB>(s, tw, q);
         else tile_sweep<LOG_S, 4, 2, true, ROWTW, NT, NB>(s, tw, q);
         if constexpr (LOG_S == 7) tile_sweep<LOG_S, 6, 1, true, ROWTW, NT, NB>(s, tw, q);
-        if constexpr (LOG_S == 8) tile_sweep<LOG_S, 6, 2, true, ROWTW, NT, NB>(s, tw, q);
+        if constexpr (LOG_S >= 8) tile_sweep<LOG_S, 6, 2, true, ROWTW, NT, NB>(s, tw, q);
+        if constexpr (LOG_S == 9) tile_sweep<LOG_S, 8, 1, true, ROWTW, NT, NB>(s, tw, q);
     } else if constexpr (LOG_S == 7 && NT == 512) {
         tile_sweep<7, 0, 2, true, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<7, 2, 2, true, ROWTW, NT, NB>(s, tw, q);
@@ -191,10 +198,14 @@ __device__ __forceinline__ void tile_inverse_t(u64 *s, const sf_tw *tw, u64 q)
         tile_sweep<7, 0, 2, true, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<7, 2, 2, true, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<7, 4, 3, true, ROWTW, NT, NB>(s, tw, q);
-    } else {
+    } else if constexpr (LOG_S == 8) {
         tile_sweep<8, 0, 2, true, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<8, 2, 3, true, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<8, 5, 3, true, ROWTW, NT, NB>(s, tw, q);
+    } else {
+        tile_sweep<9, 0, 3, true, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<9, 3, 3, true, ROWTW, NT, NB>(s, tw, q);
+        tile_sweep<9, 6, 3, true, ROWTW, NT, NB>(s, tw, q);
     }
 }
 
@@ -226,7 +237,8 @@ __device__ __forceinline__ void row_forward(u64 *s, const sf_tw *tw, int log_c, 
     case 5: tile_forward_t<5, true, NT>(s, tw, q); break;
     case 6: tile_forward_t<6, true, NT>(s, tw, q); break;
     case 7: tile_forward_t<7, true, NT>(s, tw, q); break;
-    default: tile_forward_t<8, true, NT, 8>(s, tw, q); break;
+    case 8: tile_forward_t<8, true, NT, 8>(s, tw, q); break;
+    default: tile_forward_t<9, true, NT, 4>(s, tw, q); break;
     }
 }
 template <int NT = SF_THREADS>
@@ -236,7 +248,8 @@ __device__ __forceinline__ void row_inverse(u64 *s, const sf_tw *tw, int log_c, 
     case 5: tile_inverse_t<5, true, NT>(s, tw, q); break;
     case 6: tile_inverse_t<6, true, NT>(s, tw, q); break;
     case 7: tile_inverse_t<7, true, NT>(s, tw, q); break;
-    default: tile_inverse_t<8, true, NT, 8>(s, tw, q); break;
+    case 8: tile_inverse_t<8, true, NT, 8>(s, tw, q); break;
+    default: tile_inverse_t<9, true, NT, 4>(s, tw, q); break;
     }
 }
 
@@ -252,8 +265,9 @@ __device__ __forceinline__ int col_slot(int e) { return (e >> 4) * SF_PAD + (e &
 __device__ __forceinline__ int row_elems(const SfGeo &g) { return sf_row_nb(g.log_c) * g.c; }
 __device__ __forceinline__ int row_slot(const SfGeo &g, int e)
 {
-    return sf_row_nb(g.log_c) == 8 ? tile_slot<8>(e & (g.c - 1), e >> g.log_c)
-                                   : tile_slot<16>(e & (g.c - 1), e >> g.log_c);
+    const int nb = sf_row_nb(g.log_c);
+    return nb == 4 ? tile_slot<4>(e & (g.c - 1), e >> g.log_c)
+                   : (nb == 8 ? tile_slot<8>(e & (g.c - 1), e >> g.log_c) : tile_slot<16>(e & (g.c - 1), e >> g.log_c));
 }
 
 // Stage twiddles: column table (R pairs) or the row table of tile r0/NB
@@ -267,6 +281,22 @@ __device__ __forceinline__ void load_row_tw(sf_tw *dst, const sf_tw *__restrict_
 {
     const sf_tw *src = table + ((size_t)mod << g.log_n) + (size_t)r0 * g.c;
     for (int k = threadIdx.x; k < sf_row_nb(g.log_c) * g.c; k += blockDim.x) dst[k] = src[k];
+}
+
+// ---- balanced persistent partition ----------------------------------------
+// A persistent launch of gridDim.x blocks over n_units work units numbered
+// group-major (u = group * n_items + item, where a group is a tile position
+// and modulus whose twiddles a block stages, and an item a merge or a
+// polynomial) gives block x the units [x n / grid, (x + 1) n / grid): every
+// block the floor or the ceiling of the mean, whatever the group count, and
+// a block restages twiddles only where its range crosses into a new group.
+struct SfUnits {
+    int u0, u1;
+};
+__device__ __forceinline__ SfUnits sf_block_units(int n_units)
+{
+    return {(int)((long long)blockIdx.x * n_units / gridDim.x),
+            (int)(((long long)blockIdx.x + 1) * n_units / gridDim.x)};
 }
 
 // ---- compile-time geometry -------------------------------------------------
@@ -285,14 +315,14 @@ struct SfThreads {
     static constexpr int value = LOG_S >= 8 ? 512 : SF_THREADS;
 };
 
-// Row tiles: NB rows of 2^LC points (NB = 16, or 8 for 256-point rows),
+// Row tiles: NB rows of 2^LC points (NB = 16, 8 for 256-point, 4 for 512-point rows),
 // always processed by 256-thread blocks (NB 2^LC / 256 residues per thread).
 template <int LC>
 struct SfRow {
-    static constexpr int NB = LC >= 8 ? 8 : 16;
+    static constexpr int NB = LC >= 9 ? 4 : (LC >= 8 ? 8 : 16);
     static constexpr int NT = SF_THREADS;
     static constexpr int ELEMS = NB << LC;
-    static constexpr int WORDS = (1 << LC) * (NB == 8 ? 8 : NB + 1);   // words of one tile buffer (see tile_slot)
+    static constexpr int WORDS = (1 << LC) * (NB < 16 ? NB : NB + 1);   // words of one tile buffer (see tile_slot)
 };
 
 template <int LC>
@@ -401,6 +431,6 @@ __device__ __forceinline__ void load_col_tw_t(sf_tw *dst, const sf_tw *__restric
         case 13: { constexpr int LR = 6, LC = 7; __VA_ARGS__ } break; \
         case 14: { constexpr int LR = 7, LC = 7; __VA_ARGS__ } break; \
         case 15: { constexpr int LR = 7, LC = 8; __VA_ARGS__ } break; \
-        default: { constexpr int LR = 8, LC = 8; __VA_ARGS__ } break; \
+        default: { constexpr int LR = 7, LC = 9; __VA_ARGS__ } break; \
         }                                                 \
     } while (0)

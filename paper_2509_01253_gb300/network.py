@@ -103,7 +103,12 @@ class EncodedNetwork:
         return max(i["k_in"] + i["n_groups"] for i in self.infos)
 
     def total_ks(self) -> int:
-        return sum(i["ks_count"] for i in self.infos)
+        """Key switches of all rounds; at gamma = 2 each group of n values
+        saves the n/2 merges of the tau_3 level (one trace step when n = 1)."""
+        if self.gamma != 2:
+            return sum(i["ks_count"] for i in self.infos)
+        return sum(i["ks_count"] - i["n_groups"] * (i["group_size"] // 2 if i["group_size"] >= 2 else 1)
+                   for i in self.infos)
 
 
 class ClientState:

@@ -376,12 +376,14 @@ def bench(args, device: int) -> int:
     request alone with one engine call per round (the plain form)."""
     import torch
     torch.cuda.set_device(device)
-    pools = {"c2": Pool(wl.PARAMS["conv16"], ["resnet20"], 4, device, key_seed=7000, priority=-1),
-             "c3": Pool(wl.PARAMS["r18"], ["resnet18"], 4, device, key_seed=8000, priority=0)}
+    gamma = getattr(args, "gamma", 0)
+    pools = {"c2": Pool(wl.PARAMS["conv16"], ["resnet20"], 4, device, key_seed=7000, priority=-1, gamma=gamma),
+             "c3": Pool(wl.PARAMS["r18"], ["resnet18"], 4, device, key_seed=8000, priority=0, gamma=gamma)}
     route = {"resnet20": "c2", "resnet18": "c3"}
     budget = 48 << 30
     max_active = {"c2": 16, "c3": 2}
     out = {"metric": "served encrypted layers/s; p50/p99 latency", "unit": "layers/s", "workload": "serve",
+           "gamma": gamma,
            "mix": SERVE_MIX, "client_keys": 4, "mem_budget_bytes": budget, "max_active": max_active,
            "stream_priority": {"c2": -1, "c3": 0},
            "duration_s": args.duration, "drain_s": args.drain, "rates": {}}
