@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--workload", default="r34", choices=["r34", "conv16", "resnet18", "resnet34", "serve"])
     ap.add_argument("--gamma", type=int, default=0, choices=[0, 2],
                     help="resnet34 / serve: partial trace extraction level of every round (Sec. 4.3, 4.4)")
+    ap.add_argument("--gamma-plan", action="store_true",
+                    help="resnet34: a gamma = 0 calibration request with the kernel split, then the "
+                         "timed request with the per-round levels the planner picks")
     ap.add_argument("--no-extras", action="store_true",
                     help="r34: skip the conv16, serving and batched-vs-per-layer sub-records")
     ap.add_argument("--rates", default="5,20,200", help="serve: arrival rates (requests/s)")
@@ -803,6 +806,19 @@ def run_request_e2e(args, local: int) -> int:
     sk = sf.sf_keygen(ctx, 401)
     rk = sf.sf_gen_rotation_keys(ctx, sk, None, 405)
     net = nw.EncodedNetwork(params, ctx, ps, wl.resnet_rounds(kind), gamma=args.gamma)
+    calib = None
+    if args.gamma_plan:
+        # a gamma = 0 request of another image with the per-round kernel split
+        split = []
+        c_cal = nw.ClientState(net, wl.network_input(kind, 412), session_seed=414, request_seed=413)
+        net.gammas = [0] * len(net.rounds)
+        ms_cal = nw.run_request(net, sk, rk, c_cal, split=split)
+        net.gammas = nw.plan_gammas(net, split)
+        calib = {"what": "gamma = 0 request of another image, kernel timing on (no graph replay)",
+                 "per_layer_ms": {net.rounds[r].name: ms_cal[r] for r in range(len(ms_cal))},
+                 "leaf_ms": {net.rounds[r].name: split[r][0] for r in range(len(split))},
+                 "kernel_ms": {net.rounds[r].name: split[r][1] for r in range(len(split))},
+                 "device_total_s": sum(ms_cal) / 1e3}
     x = wl.network_input(kind, 402)
     client = nw.ClientState(net, x, session_seed=404, request_seed=403)
     clocks = ClockSampler(local)
@@ -818,7 +834,8 @@ def run_request_e2e(args, local: int) -> int:
     for r, (x_in, y) in enumerate(client.trace):
         errs.append(float(np.abs(y - nw.round_float_reference(net, r, x_in)).max()))
     R = len(net.rounds)
-    rec = {"metric": METRIC, "unit": UNIT, "workload": kind, "gamma": args.gamma, "rounds": R, "n": 1 << ps.log_n,
+    rec = {"metric": METRIC, "unit": UNIT, "workload": kind,
+           "gamma": "per-round plan" if args.gamma_plan else args.gamma, "rounds": R, "n": 1 << ps.log_n,
            "L": ps.n_data,
            "ks_total": net.total_ks(), "outputs_total": sum(i["E_out"] for i in net.infos),
            "data": "synthetic: image U(0,1), Kaiming-uniform weights, pool folded into the first block",
@@ -828,6 +845,9 @@ def run_request_e2e(args, local: int) -> int:
            "max_abs_err_per_round": errs, "max_abs_err": max(errs), "clocks": clk,
            "protocol": log.summary(),
            "note": "each round's first call includes its graph capture"}
+    if calib is not None:
+        rec["gamma_per_round"] = {net.rounds[r].name: net.gammas[r] for r in range(R)}
+        rec["calibration"] = calib
     print(json.dumps(rec), flush=True)
     return 0
 

@@ -118,6 +118,13 @@ void sf_ctx_destroy(sf_ctx *ctx);
  *                   the NTT's rows have 128 points (N = 2^13, 2^14): 256
  *                   (8 residues per thread, the default) or 512 (4 per
  *                   thread, radix-4 row sweeps)
+ *   "row_radix"     sweep schedule of the row passes of the key-switch and
+ *                   leaf kernels: 0 radix-8 sweeps (the default), 1 radix-4
+ *                   sweeps, 2 radix-8 sweeps with the two sweeps nearest
+ *                   the rows' short butterflies of 256- and 512-point rows
+ *                   run back to back in registers, the lanes of a warp
+ *                   trading values by shuffles in between (other row
+ *                   lengths as 0); every schedule gives identical residues
  *   "leaf_chunk"    cap on the leaves per packing unit (power of two): a group
  *                   of n leaves is packed as n/CH residue classes of CH leaves
  *                   reduced to roots, then the roots finish the tree
@@ -132,8 +139,8 @@ void sf_ctx_destroy(sf_ctx *ctx);
 sf_status sf_ctx_set_option(sf_ctx *ctx, const char *name, int64_t value);
 
 /* Reads the current value of one of the options above that holds a value
- * ("ks_batch", "ks3_threads", "leaf_sparse", "leaf_chunk", "mem_budget",
- * "use_graph", "kernel_timing"), e.g. after sf_autotune_layers.  Errors:
+ * ("ks_batch", "ks3_threads", "leaf_sparse", "row_radix", "leaf_chunk",
+ * "mem_budget", "use_graph", "kernel_timing"), e.g. after sf_autotune_layers.  Errors:
  * SF_EINVAL for a null argument or an unknown name. */
 sf_status sf_ctx_get_option(const sf_ctx *ctx, const char *name, int64_t *value);
 
@@ -343,8 +350,9 @@ sf_status sf_eval_layers_gamma(sf_ctx *ctx, int32_t n_layers, const sf_layer *co
  * best batch, the leaf column pass of sparse tiles in closed form or as a
  * transform ("leaf_sparse" -1 or 0), then, for rings with 128-point rows,
  * the block shape of the key-switch inner product ("ks3_threads" 256 or
- * 512).  Keeps the fastest choices in the context and reports the batch
- * with the best time in milliseconds.
+ * 512), then the row-pass schedule ("row_radix" 0, 1, 2).  Keeps the
+ * fastest choices in the context and reports the batch with the best time
+ * in milliseconds.
  * Synchronises `stream`. */
 sf_status sf_autotune_layers(sf_ctx *ctx, int32_t n_layers, const sf_layer *const *layers, const sf_rotkeys *const *rks,
                              const uint64_t *const *d_ins, const int32_t *k_ins, const uint32_t *const *h_sigma_prevs,
@@ -443,7 +451,8 @@ sf_status sf_rotate_noalloc(sf_ctx *ctx, const sf_rotkeys *rk, int32_t d, const 
  * inverse = 0: coefficients (each residue below 4 q_i) -> NTT domain,
  * canonical, slot j holding the evaluation at psi^(2 brev(j) + 1) with psi a
  * primitive 2N-th root modulo q_i; inverse = 1: NTT-domain values (below
- * 4 q_i) -> canonical coefficients.  Two persistent launches on `stream`.
+ * 4 q_i) -> canonical coefficients.  Two persistent launches on `stream`;
+ * the row pass follows the context's "row_radix" schedule (same output).
  * Errors: SF_EINVAL for null buffers, count < 1, inverse not 0/1, or a batch
  * whose count x L x (tiles per limb) exceeds 2^31 - 1 (larger than any
  * device memory). */

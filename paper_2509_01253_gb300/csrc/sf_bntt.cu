@@ -16,7 +16,7 @@
 #include "sf_kernels.cuh"
 #include "sf_round.h"
 
-template <bool INV, int LR, int LC>
+template <bool INV, int LR, int LC, int RAD = 0>
 __global__ void __launch_bounds__(SfRow<LC>::NT, 3)
     k_bntt_row(SfRing R, const u64 *src, u64 *dst, int count, int ng)
 {
@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(SfRow<LC>::NT, 3)
             sf_cp_wait<0>();
         }
         __syncthreads();
-        if (INV) row_inverse_t<LC, NT>(cur, tw, q);
-        else row_forward_t<LC, NT>(cur, tw, q);
+        if (INV) row_inverse_t<LC, NT, RAD>(cur, tw, q);
+        else row_forward_t<LC, NT, RAD>(cur, tw, q);
         // forward: the last pass, canonical output; inverse: lazy in [0, 4q), the column pass follows
         store_row_tile_t<LC, NT>(dst + unit_off(u), cur, [&](u64 v) { return INV ? v : sf_reduce(v, q, one_p); });
         __syncthreads();
@@ -154,14 +154,18 @@ extern "C" sf_status sf_ntt_batch(sf_ctx *ctx, const uint64_t *d_in, uint64_t *d
             sf_launch_begin(ctx, SFK_BNTT_COL, st, &ev);
             k_bntt_col<false, LR, LC><<<bc, NTC, smc, st>>>(R, d_in, d_out, count, cg);
             sf_launch_end(ctx, SFK_BNTT_COL, st, ev);
-            const int br = bntt_blocks(ctx, bntt_occupancy(k_bntt_row<false, LR, LC>, NTR, smr), rg * count);
             sf_launch_begin(ctx, SFK_BNTT_ROW, st, &ev);
-            k_bntt_row<false, LR, LC><<<br, NTR, smr, st>>>(R, d_out, d_out, count, rg);
+            SF_RAD_DISPATCH(ctx->row_radix, {
+                const int br = bntt_blocks(ctx, bntt_occupancy(k_bntt_row<false, LR, LC, RAD>, NTR, smr), rg * count);
+                k_bntt_row<false, LR, LC, RAD><<<br, NTR, smr, st>>>(R, d_out, d_out, count, rg);
+            });
             sf_launch_end(ctx, SFK_BNTT_ROW, st, ev);
         } else {
-            const int br = bntt_blocks(ctx, bntt_occupancy(k_bntt_row<true, LR, LC>, NTR, smr), rg * count);
             sf_launch_begin(ctx, SFK_BNTT_ROW, st, &ev);
-            k_bntt_row<true, LR, LC><<<br, NTR, smr, st>>>(R, d_in, d_out, count, rg);
+            SF_RAD_DISPATCH(ctx->row_radix, {
+                const int br = bntt_blocks(ctx, bntt_occupancy(k_bntt_row<true, LR, LC, RAD>, NTR, smr), rg * count);
+                k_bntt_row<true, LR, LC, RAD><<<br, NTR, smr, st>>>(R, d_in, d_out, count, rg);
+            });
             sf_launch_end(ctx, SFK_BNTT_ROW, st, ev);
             const int bc = bntt_blocks(ctx, bntt_occupancy(k_bntt_col<true, LR, LC>, NTC, smc), cg * count);
             sf_launch_begin(ctx, SFK_BNTT_COL, st, &ev);
@@ -179,6 +183,8 @@ sf_status sf_bntt_init_attributes()
 #define SF_BNTT_ATTR(K) SF_CUDA_TRY(cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
 #define SF_BNTT_ATTRS(LR, LC)                                                                                     \
     SF_BNTT_ATTR((k_bntt_row<false, LR, LC>)) SF_BNTT_ATTR((k_bntt_row<true, LR, LC>))                             \
+    SF_BNTT_ATTR((k_bntt_row<false, LR, LC, 1>)) SF_BNTT_ATTR((k_bntt_row<true, LR, LC, 1>))                       \
+    SF_BNTT_ATTR((k_bntt_row<false, LR, LC, 2>)) SF_BNTT_ATTR((k_bntt_row<true, LR, LC, 2>))                       \
     SF_BNTT_ATTR((k_bntt_col<false, LR, LC>)) SF_BNTT_ATTR((k_bntt_col<true, LR, LC>))
     SF_BNTT_ATTRS(5, 5) SF_BNTT_ATTRS(5, 6) SF_BNTT_ATTRS(6, 6) SF_BNTT_ATTRS(6, 7) SF_BNTT_ATTRS(7, 7)
     SF_BNTT_ATTRS(7, 8) SF_BNTT_ATTRS(7, 9)

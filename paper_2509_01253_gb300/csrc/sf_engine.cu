@@ -497,12 +497,13 @@ extern "C" sf_status sf_autotune_layers(sf_ctx *ctx, int32_t n_layers, const sf_
         ctx->ks3_threads = best_nt;
     }
     // 4) NTT radix of the row passes (key-switch rows, inner product, ModDown
-    //    finish, leaf rows): radix-8 sweeps (three for 128- and 256-point rows)
-    //    or radix-4 sweeps only (four), which hold half the values per unit
+    //    finish, leaf rows): radix-8 sweeps (three per row pass), radix-4
+    //    sweeps only, which hold half the values per unit, or radix 8 with two
+    //    sweeps of 256- and 512-point rows fused by warp-shuffle exchanges
     if (status == SF_OK) {
         const int saved = ctx->row_radix;
         int best_rad = saved;
-        for (int rad : {0, 1}) {
+        for (int rad : {0, 1, 2}) {
             if (rad == saved) continue;
             ctx->row_radix = rad;
             double t = 0;

@@ -706,7 +706,7 @@ extern "C" sf_status sf_ctx_set_option(sf_ctx *ctx, const char *name, int64_t va
         ctx->ks3_threads = (int)value;
         sf_graph_cache_clear(ctx);
     } else if (!strcmp(name, "row_radix")) {
-        if (value != 0 && value != 1) return sf_set_error(SF_EINVAL, "row_radix must be 0 or 1");
+        if (value < 0 || value > 2) return sf_set_error(SF_EINVAL, "row_radix must be 0, 1 or 2");
         ctx->row_radix = (int)value;
         sf_graph_cache_clear(ctx);
     } else if (!strcmp(name, "leaf_chunk")) {

@@ -99,7 +99,7 @@ struct sf_ctx {
     int leaf_chunk;
     int leaf_sparse;          // taps per column tile up to which the leaf column pass uses the closed form (-1: default rule)
     int ks3_threads;          // block size of the key-switch inner product for 128-point rows (256 or 512)
-    int row_radix;            // row-pass sweep schedule of the key-switch and leaf row kernels: 0 radix-8, 1 radix-4
+    int row_radix;            // row-pass sweep schedule of the key-switch and leaf row kernels: 0 radix-8, 1 radix-4, 2 radix-8 with warp-shuffle exchanges
     size_t mem_budget;        // bytes of leaf + tree buffers a round may use
     int use_graph;
     int kernel_timing;

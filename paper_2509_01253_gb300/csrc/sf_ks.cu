@@ -753,7 +753,8 @@ sf_status sf_ks_init_attributes()
 #define SF_KS_ATTRS(LR, LC)                                                                                  \
     SF_KS_ATTR((k_rows<true, LR, LC>)) SF_KS_ATTR((k_ks2<LR, LC>)) SF_KS_ATTR((k_ks3<LR, LC, SfRow<LC>::NT>)) \
     SF_KS_ATTR((k_ks4<LR, LC>)) SF_KS_ATTR((k_ks5<LR, LC>)) SF_KS_ATTR((k_rows<true, LR, LC, 1>))               \
-    SF_KS_ATTR((k_ks3<LR, LC, SfRow<LC>::NT, 1>)) SF_KS_ATTR((k_ks5<LR, LC, 1>))
+    SF_KS_ATTR((k_ks3<LR, LC, SfRow<LC>::NT, 1>)) SF_KS_ATTR((k_ks5<LR, LC, 1>)) SF_KS_ATTR((k_rows<true, LR, LC, 2>))  \
+    SF_KS_ATTR((k_ks3<LR, LC, SfRow<LC>::NT, 2>)) SF_KS_ATTR((k_ks5<LR, LC, 2>))
     SF_KS_ATTRS(5, 5) SF_KS_ATTRS(5, 6) SF_KS_ATTRS(6, 6) SF_KS_ATTRS(6, 7) SF_KS_ATTRS(7, 7) SF_KS_ATTRS(7, 8)
     SF_KS_ATTRS(7, 9)
     SF_KS_ATTR((k_ks3<6, 7, 512>)) SF_KS_ATTR((k_ks3<7, 7, 512>))

@@ -602,7 +602,8 @@ sf_status sf_layer_init_attributes()
 #undef SF_LEAF_ATTRS
 #define SF_LEAF_ROW_ATTR(LR, LC) \
     SF_CUDA_TRY(cudaFuncSetAttribute((k_leaf_row<LR, LC>), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)); \
-    SF_CUDA_TRY(cudaFuncSetAttribute((k_leaf_row<LR, LC, 1>), cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+    SF_CUDA_TRY(cudaFuncSetAttribute((k_leaf_row<LR, LC, 1>), cudaFuncAttributeMaxDynamicSharedMemorySize, mx)); \
+    SF_CUDA_TRY(cudaFuncSetAttribute((k_leaf_row<LR, LC, 2>), cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
     SF_LEAF_ROW_ATTR(5, 5) SF_LEAF_ROW_ATTR(5, 6) SF_LEAF_ROW_ATTR(6, 6) SF_LEAF_ROW_ATTR(6, 7) SF_LEAF_ROW_ATTR(7, 7)
     SF_LEAF_ROW_ATTR(7, 8) SF_LEAF_ROW_ATTR(7, 9)
 #undef SF_LEAF_ROW_ATTR

@@ -27,7 +27,9 @@
 //    + k - m(k)] (m(k) the largest power of two <= k); the tile's NB*C pairs
 //    are one contiguous chunk copied straight into shared memory.
 // Each sweep runs 2 or 3 stages (radix 4 / radix 8) on register-resident
-// units with lazy Harvey butterflies.
+// units with lazy Harvey butterflies; in 256- and 512-point rows two sweeps can
+// run back to back in registers, the lanes of a warp trading values by
+// shuffles in between (schedule RAD = 2).
 #pragma once
 #include "sf_arith.cuh"
 #include "sf_async.cuh"
@@ -70,6 +72,10 @@ typedef ulonglong2 sf_tw;   // (w, w')
 // the sub-transform index XOR-swizzled by bits 1..3 (2..3) of k, so that 16
 // consecutive k of one b (a coalesced copy) hit 16 distinct bank pairs, and so
 // do the units of a half-warp in every sweep whose units start consecutively.
+// The sweep of the shortest butterflies (units 4 or 8 elements apart) keeps a
+// 2-way (4-way at NB = 4) conflict: a layout that also permutes k inside
+// 16-word segments removes it, but its extra index arithmetic cost the
+// integer-bound inner product more than the conflicts did.
 template <int NB>
 __device__ __forceinline__ int tile_slot(int k, int b)
 {
@@ -86,8 +92,30 @@ __host__ __device__ __forceinline__ int row_tile_words(int log_c)
     return (1 << log_c) * (sf_row_nb(log_c) < 16 ? sf_row_nb(log_c) : sf_row_nb(log_c) + 1);
 }
 
-// One sweep of R_ST consecutive stages over every unit of the tile.
+// The R_ST stages of one sweep on one register-resident unit x[0 .. 2^R_ST)
+// of sub-transform b; blk is the unit's block (its group index base).
 // Forward: halves H0, H0/2, ..., H0 >> (R_ST-1).  Inverse: halves H0, ..., H0 << (R_ST-1).
+template <int LOG_S, int LOG_H0, int R_ST, bool INV, bool ROWTW, int NB>
+__device__ __forceinline__ void unit_stages(u64 *x, int blk, int b, const sf_tw *tw, u64 q, u64 two_q)
+{
+    constexpr int S = 1 << LOG_S;
+    constexpr int U = 1 << R_ST;
+#pragma unroll
+    for (int sg = 0; sg < R_ST; ++sg) {
+        const int d = INV ? (1 << sg) : (1 << (R_ST - 1 - sg));
+        const int m = INV ? (S >> (LOG_H0 + 1 + sg)) : ((S >> (LOG_H0 + 1)) << sg);
+#pragma unroll
+        for (int t = 0; t < U; ++t) {
+            if (t & d) continue;
+            const int g = INV ? ((blk << (R_ST - sg - 1)) + (t >> (sg + 1))) : ((blk << sg) + (t >> (R_ST - sg)));
+            const sf_tw w = ROWTW ? tw[(m + g) * NB + b] : tw[m + g];
+            if (INV) sf_bfly_gs(x[t], x[t + d], w.x, w.y, q, two_q);
+            else sf_bfly_ct(x[t], x[t + d], w.x, w.y, q, two_q);
+        }
+    }
+}
+
+// One sweep of R_ST consecutive stages over every unit of the tile.
 template <int LOG_S, int LOG_H0, int R_ST, bool INV, bool ROWTW, int NT, int NB = SF_NB>
 __device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
 {
@@ -111,22 +139,134 @@ __device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
         u64 x[U];
 #pragma unroll
         for (int t = 0; t < U; ++t) x[t] = s[tile_slot<NB>(first + (t << LOG_STEP), b)];
-#pragma unroll
-        for (int sg = 0; sg < R_ST; ++sg) {
-            const int d = INV ? (1 << sg) : (1 << (R_ST - 1 - sg));
-            const int m = INV ? (S >> (LOG_H0 + 1 + sg)) : ((S >> (LOG_H0 + 1)) << sg);
-#pragma unroll
-            for (int t = 0; t < U; ++t) {
-                if (t & d) continue;
-                const int g = INV ? ((blk << (R_ST - sg - 1)) + (t >> (sg + 1))) : ((blk << sg) + (t >> (R_ST - sg)));
-                const sf_tw w = ROWTW ? tw[(m + g) * NB + b] : tw[m + g];
-                if (INV) sf_bfly_gs(x[t], x[t + d], w.x, w.y, q, two_q);
-                else sf_bfly_ct(x[t], x[t + d], w.x, w.y, q, two_q);
-            }
-        }
+        unit_stages<LOG_S, LOG_H0, R_ST, INV, ROWTW, NB>(x, blk, b, tw, q, two_q);
 #pragma unroll
         for (int t = 0; t < U; ++t) s[tile_slot<NB>(first + (t << LOG_STEP), b)] = x[t];
     }
+    __syncthreads();
+}
+
+// ---- warp-shuffle exchanges ----------------------------------------------
+// Two consecutive sweeps of a row pass fused through registers: the units of
+// the first sweep that touch one block of 32 or 64 consecutive elements per row
+// are held by the lanes of one warp, which exchange values with __shfl_xor_sync so that every lane then
+// holds its unit of the second sweep.  This drops one shared-memory round trip
+// and one block barrier per transform.  A lane exchange swaps one bit of the
+// lane index (mask LM) with one bit of the register index (mask RM): values
+// whose two bits differ move to the partner lane, the others stay.
+template <int RM>
+__device__ __forceinline__ void lane_exchange(u64 *x, int lm)
+{
+    const bool hi = (threadIdx.x & lm) != 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        if (t & RM) continue;
+        const u64 send = hi ? x[t] : x[t | RM];
+        const u64 recv = __shfl_xor_sync(0xffffffffu, send, lm);
+        if (hi) x[t] = recv;
+        else x[t | RM] = recv;
+    }
+}
+
+// Forward, the last two sweeps of a 512-point row pass (4-row tiles): the
+// radix-8 sweep over halves 32, 16, 8 and the one over halves 4, 2, 1.  Lane
+// bits 2..4 (o) and the register index (t) swap: lane o of a 64-element block
+// first holds elements 8t + o, then 8o + t.
+template <bool ROWTW, int NT>
+__device__ __forceinline__ void row_pair_fwd9(u64 *s, const sf_tw *tw, u64 q)
+{
+    static_assert(4 * 512 / 8 == NT, "one unit per thread");
+    const u64 two_q = 2 * q;
+    const int idx = threadIdx.x, b = idx & 3, o = (idx >> 2) & 7, blk = idx >> 5;
+    u64 x[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) x[t] = s[tile_slot<4>((blk << 6) + o + (t << 3), b)];
+    unit_stages<9, 5, 3, false, ROWTW, 4>(x, blk, b, tw, q, two_q);
+    lane_exchange<1>(x, 4);
+    lane_exchange<2>(x, 8);
+    lane_exchange<4>(x, 16);
+    const int blk3 = (blk << 3) + o;
+    unit_stages<9, 2, 3, false, ROWTW, 4>(x, blk3, b, tw, q, two_q);
+    __syncwarp();   // every lane's loads of this block are done before any store
+#pragma unroll
+    for (int t = 0; t < 8; ++t) s[tile_slot<4>((blk3 << 3) + t, b)] = x[t];
+    __syncthreads();
+}
+
+// Inverse, the first two sweeps of a 512-point row pass: halves 1, 2, 4, then
+// 8, 16, 32 (the same lane / register swap, in the other direction).
+template <bool ROWTW, int NT>
+__device__ __forceinline__ void row_pair_inv9(u64 *s, const sf_tw *tw, u64 q)
+{
+    static_assert(4 * 512 / 8 == NT, "one unit per thread");
+    const u64 two_q = 2 * q;
+    const int idx = threadIdx.x, b = idx & 3, o = (idx >> 2) & 7, k = idx >> 5;
+    u64 x[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) x[t] = s[tile_slot<4>((k << 6) + (o << 3) + t, b)];
+    unit_stages<9, 0, 3, true, ROWTW, 4>(x, (k << 3) + o, b, tw, q, two_q);
+    lane_exchange<1>(x, 4);
+    lane_exchange<2>(x, 8);
+    lane_exchange<4>(x, 16);
+    unit_stages<9, 3, 3, true, ROWTW, 4>(x, k, b, tw, q, two_q);
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 8; ++t) s[tile_slot<4>((k << 6) + o + (t << 3), b)] = x[t];
+    __syncthreads();
+}
+
+// Forward, the last two sweeps of a 256-point row pass (8-row tiles): radix 8
+// over halves 16, 8, 4, then two radix-4 units over halves 2, 1.  Lane bits
+// 3..4 (o) of a 32-element block: lane o first holds elements 4t + o, then
+// 8o + t (two exchanges and a fixed renaming of the registers).
+template <bool ROWTW, int NT>
+__device__ __forceinline__ void row_pair_fwd8(u64 *s, const sf_tw *tw, u64 q)
+{
+    static_assert(8 * 256 / 8 == NT, "one unit per thread");
+    const u64 two_q = 2 * q;
+    const int idx = threadIdx.x, b = idx & 7, o = (idx >> 3) & 3, blk = idx >> 5;
+    u64 x[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) x[t] = s[tile_slot<8>((blk << 5) + o + (t << 2), b)];
+    unit_stages<8, 4, 3, false, ROWTW, 8>(x, blk, b, tw, q, two_q);
+    lane_exchange<2>(x, 8);
+    lane_exchange<4>(x, 16);
+    // register r now holds element bits (E2, E0, E1); y[t] the element 8o + t
+    u64 y[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) y[t] = x[((t >> 2) & 1) | ((t & 1) << 1) | (((t >> 1) & 1) << 2)];
+    const int blk3 = (blk << 3) + (o << 1);
+    unit_stages<8, 1, 2, false, ROWTW, 8>(y, blk3, b, tw, q, two_q);
+    unit_stages<8, 1, 2, false, ROWTW, 8>(y + 4, blk3 + 1, b, tw, q, two_q);
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 8; ++t) s[tile_slot<8>((blk << 5) + (o << 3) + t, b)] = y[t];
+    __syncthreads();
+}
+
+// Inverse, the first two sweeps of a 256-point row pass: two radix-4 units
+// over halves 1, 2, then radix 8 over halves 4, 8, 16.
+template <bool ROWTW, int NT>
+__device__ __forceinline__ void row_pair_inv8(u64 *s, const sf_tw *tw, u64 q)
+{
+    static_assert(8 * 256 / 8 == NT, "one unit per thread");
+    const u64 two_q = 2 * q;
+    const int idx = threadIdx.x, b = idx & 7, o = (idx >> 3) & 3, k = idx >> 5;
+    u64 x[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) x[t] = s[tile_slot<8>((k << 5) + (o << 3) + t, b)];
+    unit_stages<8, 0, 2, true, ROWTW, 8>(x, (k << 3) + (o << 1), b, tw, q, two_q);
+    unit_stages<8, 0, 2, true, ROWTW, 8>(x + 4, (k << 3) + (o << 1) + 1, b, tw, q, two_q);
+    // undo the renaming of the forward pair, then its exchanges in reverse order
+    u64 z[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) z[r] = x[((r >> 1) & 1) | (((r >> 2) & 1) << 1) | ((r & 1) << 2)];
+    lane_exchange<4>(z, 16);
+    lane_exchange<2>(z, 8);
+    unit_stages<8, 2, 3, true, ROWTW, 8>(z, k, b, tw, q, two_q);
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 8; ++t) s[tile_slot<8>((k << 5) + o + (t << 2), b)] = z[t];
     __syncthreads();
 }
 
@@ -136,7 +276,14 @@ __device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
 template <int LOG_S, bool ROWTW, int NT, int NB = SF_NB, int RAD = 0>
 __device__ __forceinline__ void tile_forward_t(u64 *s, const sf_tw *tw, u64 q)
 {
-    if constexpr (RAD == 1) {
+    if constexpr (RAD == 2 && LOG_S == 9 && NB == 4 && NT == 256) {
+        // radix 8, the last two sweeps fused by warp-shuffle exchanges
+        tile_sweep<9, 8, 3, false, ROWTW, NT, NB>(s, tw, q);
+        row_pair_fwd9<ROWTW, NT>(s, tw, q);
+    } else if constexpr (RAD == 2 && LOG_S == 8 && NB == 8 && NT == 256) {
+        tile_sweep<8, 7, 3, false, ROWTW, NT, NB>(s, tw, q);
+        row_pair_fwd8<ROWTW, NT>(s, tw, q);
+    } else if constexpr (RAD == 1) {
         // radix-4 sweeps only (two stages per sweep, a radix-2 sweep last for an odd count)
         tile_sweep<LOG_S, LOG_S - 1, 2, false, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<LOG_S, LOG_S - 3, 2, false, ROWTW, NT, NB>(s, tw, q);
@@ -175,7 +322,14 @@ __device__ __forceinline__ void tile_forward_t(u64 *s, const sf_tw *tw, u64 q)
 template <int LOG_S, bool ROWTW, int NT, int NB = SF_NB, int RAD = 0>
 __device__ __forceinline__ void tile_inverse_t(u64 *s, const sf_tw *tw, u64 q)
 {
-    if constexpr (RAD == 1) {
+    if constexpr (RAD == 2 && LOG_S == 9 && NB == 4 && NT == 256) {
+        // radix 8, the first two sweeps fused by warp-shuffle exchanges
+        row_pair_inv9<ROWTW, NT>(s, tw, q);
+        tile_sweep<9, 6, 3, true, ROWTW, NT, NB>(s, tw, q);
+    } else if constexpr (RAD == 2 && LOG_S == 8 && NB == 8 && NT == 256) {
+        row_pair_inv8<ROWTW, NT>(s, tw, q);
+        tile_sweep<8, 5, 3, true, ROWTW, NT, NB>(s, tw, q);
+    } else if constexpr (RAD == 1) {
         tile_sweep<LOG_S, 0, 2, true, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<LOG_S, 2, 2, true, ROWTW, NT, NB>(s, tw, q);
         if constexpr (LOG_S == 5) tile_sweep<LOG_S, 4, 1, true, ROWTW, NT, NB>(s, tw, q);
@@ -409,10 +563,14 @@ __device__ __forceinline__ void load_col_tw_t(sf_tw *dst, const sf_tw *__restric
 }
 
 // runs the statements with the row-pass sweep schedule RAD (0: radix-8
-// sweeps, 1: radix-4 sweeps) as a compile-time constant
+// sweeps, 1: radix-4 sweeps, 2: radix-8 with two sweeps of 256- and
+// 512-point rows fused by warp-shuffle exchanges) as a compile-time constant
 #define SF_RAD_DISPATCH(rad, ...)           \
     do {                                    \
-        if ((rad) == 1) {                   \
+        if ((rad) == 2) {                   \
+            constexpr int RAD = 2;          \
+            __VA_ARGS__                     \
+        } else if ((rad) == 1) {            \
             constexpr int RAD = 1;          \
             __VA_ARGS__                     \
         } else {                            \

@@ -72,14 +72,15 @@ class EncodedNetwork:
     Delta, requantisation scale eta per round)."""
 
     def __init__(self, params, ctx, ps: wl.ParamSet, rounds: list, integer: bool = False, act_bits: int = None,
-                 gamma: int = 0):
+                 gamma=0):
         self.params, self.ctx, self.ps, self.rounds = params, ctx, ps, rounds
         self.n = 1 << ps.log_n
         self.act_bits = act_bits
-        # partial trace extraction level (Sec. 4.3, 4.4): at gamma = 2 the client
-        # also sends RLWE(m_j(X^3)) and the packed values carry the factor 2
-        assert gamma in (0, 2)
-        self.gamma = gamma
+        # partial trace extraction level (Sec. 4.3, 4.4), one for all rounds or
+        # one per round: at gamma = 2 the client also sends RLWE(m_j(X^3)) for
+        # that round and its packed values carry the factor 2
+        self.gammas = list(gamma) if isinstance(gamma, (list, tuple)) else [gamma] * len(rounds)
+        assert len(self.gammas) == len(rounds) and all(g in (0, 2) for g in self.gammas)
         self.quant = act_bits is not None
         wscale = 1.0 if self.quant else ps.delta
         self.out_scale = ps.delta * wscale
@@ -102,13 +103,19 @@ class EncodedNetwork:
         """Largest input + output ciphertext count over the rounds."""
         return max(i["k_in"] + i["n_groups"] for i in self.infos)
 
+    def ks_count(self, r: int, gamma: int = None) -> int:
+        """Key switches of round r at extraction level gamma (the round's own
+        by default); at gamma = 2 each group of n values saves the n/2 merges
+        of the tau_3 level (one trace step when n = 1)."""
+        i = self.infos[r]
+        g = self.gammas[r] if gamma is None else gamma
+        if g != 2:
+            return i["ks_count"]
+        return i["ks_count"] - i["n_groups"] * (i["group_size"] // 2 if i["group_size"] >= 2 else 1)
+
     def total_ks(self) -> int:
-        """Key switches of all rounds; at gamma = 2 each group of n values
-        saves the n/2 merges of the tau_3 level (one trace step when n = 1)."""
-        if self.gamma != 2:
-            return sum(i["ks_count"] for i in self.infos)
-        return sum(i["ks_count"] - i["n_groups"] * (i["group_size"] // 2 if i["group_size"] >= 2 else 1)
-                   for i in self.infos)
+        """Key switches of all rounds at their extraction levels."""
+        return sum(self.ks_count(r) for r in range(len(self.rounds)))
 
 
 class ClientState:
@@ -210,22 +217,37 @@ def round_float_reference(net: EncodedNetwork, r: int, x_orig: np.ndarray) -> np
 def decode_outputs(net: EncodedNetwork, r: int, residues: np.ndarray) -> np.ndarray:
     info = net.infos[r]
     return sf.sf_decode(net.params, residues, info["n_groups"], net.n // info["group_size"],
-                        info["E_out"], net.out_scale * (2 if net.gamma == 2 else 1))
+                        info["E_out"], net.out_scale * (2 if net.gammas[r] == 2 else 1))
 
 
 def run_request(net: EncodedNetwork, sk, rk, client: ClientState, stream=None, device: str = "cuda:0",
                 keep_trace: bool = False, log: protocol.CommLog = None, session: protocol.ServerSession = None,
-                io: list = None):
+                io: list = None, split: list = None):
     """All rounds of one request, one sf_eval_linear_layer call per round.
     Each upload goes through the server's session checks (its session id is
     the client's session seed); `log`, when given, receives every round's
     bytes, server (device) time and client time (encode, encrypt, decrypt,
-    decode, activation).  Returns per-round device milliseconds."""
+    decode, activation).  `split`, when given, receives per round the
+    (leaf milliseconds, all kernels' milliseconds) of the library's kernel
+    timing, which is on for the request (launches bracketed by events, no
+    graph replay).  Returns per-round device milliseconds."""
     import torch
     L, n = net.ps.n_data, net.n
     st = stream if stream is not None else torch.cuda.current_stream()
     session = session or protocol.ServerSession(client.session_seed, len(net.rounds))
     ms = []
+    timing = sf.sf_ctx_get_option(net.ctx, "kernel_timing")
+    if split is not None:
+        sf.sf_ctx_set_option(net.ctx, "kernel_timing", 1)
+    try:
+        _run_rounds(net, sk, rk, client, stream, st, device, keep_trace, log, session, io, split, ms, L, n)
+    finally:
+        sf.sf_ctx_set_option(net.ctx, "kernel_timing", timing)
+    return ms
+
+
+def _run_rounds(net, sk, rk, client, stream, st, device, keep_trace, log, session, io, split, ms, L, n):
+    import torch
     for r in range(len(net.rounds)):
         info = net.infos[r]
         t0 = time.perf_counter()
@@ -233,7 +255,7 @@ def run_request(net: EncodedNetwork, sk, rk, client: ClientState, stream=None, d
         d_in = torch.empty((info["k_in"], 2, L, n), dtype=torch.int64, device=device)
         sf.sf_encrypt(net.ctx, sk, msg, client.encrypt_seed(r), d_in, info["k_in"], stream)
         d_pow = None
-        if net.gamma == 2:
+        if net.gammas[r] == 2:
             d_pow = torch.empty_like(d_in)
             sf.sf_encrypt(net.ctx, sk, sf.sf_client_power(net.params, msg, info["k_in"], 3),
                           client.power_seed(r), d_pow, info["k_in"], stream)
@@ -244,12 +266,17 @@ def run_request(net: EncodedNetwork, sk, rk, client: ClientState, stream=None, d
         def evaluate(rr, payload):
             d_out = torch.empty((info["n_groups"], 2, L, n), dtype=torch.int64, device=device)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if split is not None:
+                sf.sf_kernel_stats_reset(net.ctx)
             e0.record(st)
-            sf.sf_eval_linear_layer_gamma(net.ctx, net.layers[rr], rk, net.gamma, payload, d_pow, info["k_in"],
+            sf.sf_eval_linear_layer_gamma(net.ctx, net.layers[rr], rk, net.gammas[rr], payload, d_pow, info["k_in"],
                                           sigma_prev, so, d_out, info["n_groups"], st)
             e1.record(st)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
+            if split is not None:
+                stats = sf.sf_kernel_stats(net.ctx)
+                split.append((sum(t for name, _, t in stats if name.startswith("leaf")), sum(t for _, _, t in stats)))
             return d_out
 
         d_out = session.submit(client.session_seed, r, d_in, evaluate)
@@ -263,9 +290,34 @@ def run_request(net: EncodedNetwork, sk, rk, client: ClientState, stream=None, d
         client.absorb(r, vals, so, stream_in if keep_trace else None, sigma_prev)
         t_client += time.perf_counter() - t0
         if log is not None:
-            up, down = protocol.round_bytes(info, L, n, net.gamma)
+            up, down = protocol.round_bytes(info, L, n, net.gammas[r])
             log.add(r, up, down, ms[-1] / 1e3, t_client)
     return ms
+
+
+def plan_gammas(net: EncodedNetwork, split: list, margin: float = 0.02, leaf_factor: float = 2.2) -> list:
+    """Per-round extraction level from the kernel split of one gamma = 0
+    request (run_request's `split`).  Partial extraction (Sec. 4.3, 4.4)
+    trades work: at gamma = 2 the server multiplies each round's weights into
+    the ciphertexts and into the client's powers, so the leaf kernels' time
+    grows by leaf_factor, while the rest of the round, the key switches of
+    the packing tree and the trace, shrinks with their count.  The predicted
+    gamma = 2 time of round r is leaf_factor leaf_r + (total_r - leaf_r)
+    ks_2 / ks_0, and the round takes gamma = 2 when that is below
+    (1 - margin) total_r.  The leaves alone would double; the default 2.2
+    also carries the powers' input transforms and the plain bottom-level
+    merges that the gamma = 2 rounds add (fitted on GB300 over the ResNet-34
+    rounds: 2.11 to 2.24).  Early, wide layers keep gamma = 0; the late
+    rounds, where key switches dominate, take gamma = 2.  The choice is the
+    server's alone: the client sends the powers for exactly the rounds that
+    take gamma = 2."""
+    assert len(split) == len(net.rounds)
+    plan = []
+    for r, (leaf, total) in enumerate(split):
+        ks0, ks2 = net.ks_count(r, 0), net.ks_count(r, 2)
+        pred2 = leaf_factor * leaf + (total - leaf) * (ks2 / ks0 if ks0 else 1.0)
+        plan.append(2 if pred2 < (1 - margin) * total else 0)
+    return plan
 
 
 def quant_forward(net: EncodedNetwork, x: np.ndarray, trace: list = None) -> np.ndarray:

@@ -67,7 +67,7 @@ class Pool:
     """One parameter set: context, stream, resident weights and client keys."""
 
     def __init__(self, ps: wl.ParamSet, nets: list, n_clients: int, device: int = 0, key_seed: int = 7000,
-                 engine_budget: int = 16 << 30, ks_batch: int = None, priority: int = 0, gamma: int = 0):
+                 engine_budget: int = 16 << 30, ks_batch: int = None, priority: int = 0, gamma=0):
         import torch
         self.torch = torch
         self.ps = ps
@@ -80,9 +80,10 @@ class Pool:
         self.device = f"cuda:{device}"
         self.sks = [sf.sf_keygen(self.ctx, key_seed + 2 * c) for c in range(n_clients)]
         self.rks = [sf.sf_gen_rotation_keys(self.ctx, sk, None, key_seed + 2 * c + 1) for c, sk in enumerate(self.sks)]
-        # partial trace extraction level of every request of the pool (Sec. 4.3, 4.4)
-        self.gamma = gamma
-        self.nets = {name: nw.EncodedNetwork(self.params, self.ctx, ps, wl.resnet_rounds(name), gamma=gamma)
+        # partial trace extraction level (Sec. 4.3, 4.4): one for every round of
+        # every network, or per network a per-round list (a plan_gammas result)
+        self.nets = {name: nw.EncodedNetwork(self.params, self.ctx, ps, wl.resnet_rounds(name),
+                                             gamma=gamma[name] if isinstance(gamma, dict) else gamma)
                      for name in nets}
         # CUDA stream priority (lower = higher): the pool of short requests runs
         # above the pool of long ones, so its launches take SMs as they free up
@@ -95,7 +96,8 @@ class Pool:
 
     def reserve_of(self, net: str) -> int:
         # input (and, at gamma = 2, the powers) plus output ciphertexts of the largest round
-        per = max(i["k_in"] * (2 if self.gamma == 2 else 1) + i["n_groups"] for i in self.nets[net].infos)
+        e = self.nets[net]
+        per = max(i["k_in"] * (2 if g == 2 else 1) + i["n_groups"] for i, g in zip(e.infos, e.gammas))
         return per * self.ct_bytes
 
     def new_client(self, req: Request) -> nw.ClientState:
@@ -116,12 +118,12 @@ class Pool:
         # the upload of round r: checked against the session's next round
         if not req.session.begin(req.session_seed, r):
             raise protocol.ProtocolError("order", f"request {req.rid}: round {r} was evaluated already")
-        req.up_bytes += protocol.round_bytes(info, self.L, self.n, self.gamma)[0]
+        req.up_bytes += protocol.round_bytes(info, self.L, self.n, net.gammas[r])[0]
         req.d_in = torch.empty((info["k_in"], 2, self.L, self.n), dtype=torch.int64, device=self.device)
         sf.sf_encrypt(self.ctx, self.sks[req.key], msg, req.client.encrypt_seed(r), req.d_in, info["k_in"],
                       self.stream)
         req.d_pow = None
-        if self.gamma == 2:
+        if net.gammas[r] == 2:
             req.d_pow = torch.empty_like(req.d_in)
             sf.sf_encrypt(self.ctx, self.sks[req.key], sf.sf_client_power(self.params, msg, info["k_in"], 3),
                           req.client.power_seed(r), req.d_pow, info["k_in"], self.stream)
@@ -144,7 +146,7 @@ class Pool:
         req.client.absorb(r, vals, req.sigma_out)
         # the simulated client never loses a download here: nothing is kept to resend
         req.session.complete(r, None)
-        req.down_bytes += protocol.round_bytes(info, self.L, self.n, self.gamma)[1]
+        req.down_bytes += protocol.round_bytes(info, self.L, self.n, net.gammas[r])[1]
         req.rounds_run += 1
         req.d_in = req.d_out = req.d_pow = None
 
@@ -165,7 +167,7 @@ class Pool:
             d_outs.append(req.d_out)
             caps.append(info["n_groups"])
         self.last_call = [(req.rid, req.net, req.key, req.client.round) for req in batch]
-        if self.gamma == 2:
+        if any(d is not None for d in d_pows):
             sf.sf_eval_layers_gamma(self.ctx, layers, rks, d_ins, d_pows, k_ins, sps, sos, d_outs, caps, self.stream)
         else:
             sf.sf_eval_layers(self.ctx, layers, rks, d_ins, k_ins, sps, sos, d_outs, caps, self.stream)

@@ -9,6 +9,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
+import paper_2509_01253_gb300 as sf  # noqa: E402
 from paper_2509_01253_gb300 import network as nw  # noqa: E402
 from paper_2509_01253_gb300 import protocol  # noqa: E402
 from paper_2509_01253_gb300 import serve  # noqa: E402
@@ -213,3 +214,56 @@ def test_served_gamma2_mix_equals_alone(pool_g2):
         assert np.array_equal(req.logits, alone[req.request_seed]), req.request_seed
     ref = nw.float_forward(pool_g2.nets["resnet20"], wl.network_input("resnet20", 61))
     assert np.abs(alone[61] - ref).max() <= 1e-3
+
+
+@pytest.mark.gpu
+def test_per_round_gamma_plan_request_and_served(pools, pool_g2):
+    """Extraction level per round: the planner turns the kernel split of a
+    gamma = 0 request into one level per round; a request whose rounds
+    alternate gamma = 0 and 2 (the client sends powers only for the latter)
+    is within 1e-3 of float64 and of the gamma = 0 request, uploads the
+    powers of exactly those rounds, and gives identical logits when served
+    two at a time (sf_eval_layers_gamma with and without powers in one call)."""
+    p0 = pools["p14"]
+    net0 = p0.nets["tiny_b"]
+    split = []
+    req = serve.make_request(0, "tiny_b", 0, 71)
+    client = nw.ClientState(net0, req.x, req.session_seed, req.request_seed)
+    nw.run_request(net0, p0.sks[0], p0.rks[0], client, split=split)
+    assert sf.sf_ctx_get_option(p0.ctx, "kernel_timing") == 0
+    assert len(split) == len(net0.rounds) and all(0 < leaf <= tot for leaf, tot in split)
+    plan = nw.plan_gammas(net0, split)
+    assert len(plan) == len(net0.rounds) and set(plan) <= {0, 2}
+    # a round whose time is all key switches takes gamma = 2, one all leaves keeps 0
+    assert nw.plan_gammas(net0, [(0.0, 1.0)] * len(net0.rounds)) == [2] * len(net0.rounds)
+    assert nw.plan_gammas(net0, [(1.0, 1.0)] * len(net0.rounds)) == [0] * len(net0.rounds)
+    net = pool_g2.nets["tiny_b"]
+    saved = list(net.gammas)
+    try:
+        net.gammas = [2 if r % 2 else 0 for r in range(len(net.rounds))]
+        log_m, log_0 = protocol.CommLog(), protocol.CommLog()
+        cm = _alone(pool_g2, "tiny_b", 1, 72, log=log_m)
+        c0 = _alone(pools["p14"], "tiny_b", 1, 72, log=log_0)
+        for r, (x_in, y) in enumerate(cm.trace):
+            assert np.abs(y - nw.round_float_reference(net, r, x_in)).max() <= 1e-3, r
+        assert np.abs(cm.logits() - c0.logits()).max() <= 1e-3
+        ct = protocol.ciphertext_bytes(pool_g2.L, pool_g2.n)
+        extra = sum(i["k_in"] for i, g in zip(net.infos, net.gammas) if g == 2) * ct
+        assert log_m.up_bytes == log_0.up_bytes + extra and log_m.down_bytes == log_0.down_bytes
+        assert net.total_ks() == sum(net.ks_count(r, g) for r, g in enumerate(net.gammas))
+        srv = serve.Server({"g2": pool_g2}, {"tiny_b": "g2"}, mem_budget=1 << 36, max_queue=4, max_active=2,
+                           max_batch=2)
+        srv.start()
+        import time
+        for i, seed in enumerate((72, 73)):
+            assert srv.submit(serve.make_request(i, "tiny_b", 1, seed))
+        t_end = time.perf_counter() + 300
+        while not srv.idle() and time.perf_counter() < t_end and not srv.errors:
+            time.sleep(0.02)
+        srv.shutdown()
+        assert not srv.errors and len(srv.completed) == 2
+        alone73 = _alone(pool_g2, "tiny_b", 1, 73).logits()
+        for r in srv.completed:
+            assert np.array_equal(r.logits, cm.logits() if r.request_seed == 72 else alone73), r.request_seed
+    finally:
+        net.gammas = saved

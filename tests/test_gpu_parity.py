@@ -95,6 +95,15 @@ def test_ntt_batch_transform_pair(oracle, log_n, L, bits, K, count):
         assert (from_dev(back) == a).all()
         sf.sf_ntt_batch(s.ctx, B, B, count, True)
         assert (from_dev(B) == b).all()
+        # the other row-pass schedules give the same values
+        for rad in (1, 2):
+            sf.sf_ctx_set_option(s.ctx, "row_radix", rad)
+            A2 = dev_zeros(count, L, s.n)
+            sf.sf_ntt_batch(s.ctx, to_dev(a), A2, count, False)
+            assert (from_dev(A2) == ha).all(), rad
+            sf.sf_ntt_batch(s.ctx, A2, A2, count, True)
+            assert (from_dev(A2) == a).all(), rad
+        sf.sf_ctx_set_option(s.ctx, "row_radix", 0)
         # pointwise product on the host, inverse on the device, schoolbook on the oracle
         prod = np.zeros_like(ha)
         for t in range(count):
@@ -797,7 +806,9 @@ def test_eval_layers_batch_matches_single_rounds():
 def test_large_ring_layer_bit_exact(oracle):
     """A small FC round on the ResNet-18 ring (N = 2^15, 4 x 50-bit + 2
     special, two-limb digits) end to end: 4 outputs packed into one ciphertext
-    (3 tree merges + 13 trace steps), every residue against the oracle."""
+    (3 tree merges + 13 trace steps), every residue against the oracle, under
+    each row-pass schedule of its 256-point rows (radix 8, radix 4, radix 8
+    with warp-shuffle exchanges)."""
     ps = wl.PARAMS["r18"]
     case = wl.fc_case(61, 24, 4, bias=True)
     delta = wsc = 2.0 ** 20           # bias at scale 2^40 fits int64
@@ -809,6 +820,12 @@ def test_large_ring_layer_bit_exact(oracle):
         want, _, ks = _oracle_layer_run(oracle, prm, case, msg, wsc, delta * wsc, 63, 65, info["k_in"])
         assert ks == 16
         assert (got == want).all()
+        for rad in (1, 2):
+            sf.sf_layer_destroy(lay)
+            sf.sf_ctx_set_option(s.ctx, "row_radix", rad)
+            lay, _, _, _, got_r = _run_layer(s, case, delta, delta * wsc, wsc)
+            assert (got_r == want).all(), rad
+        sf.sf_ctx_set_option(s.ctx, "row_radix", 0)
         vals = sf.sf_decode(s.params, s.decrypt(to_dev(got), 1), 1, s.n // 4, 4, delta * wsc)
         assert np.abs(vals - wl.float_reference(case)[case.sigma_out.astype(np.int64)]).max() <= 1e-3
         sf.sf_layer_destroy(lay)
@@ -832,7 +849,7 @@ def test_largest_ring_rotate_and_leaves(oracle):
         ct = from_dev(d_ct).reshape(2, s.L, s.n)
         out = dev_zeros(1, 2, s.L, s.n)
         want = oracle.rotate(prm, keys, 3, ct)
-        for rad in (0, 1):                               # both row-pass sweep schedules
+        for rad in (0, 1, 2):                            # every row-pass sweep schedule
             sf.sf_ctx_set_option(s.ctx, "row_radix", rad)
             sf.sf_rotate(s.ctx, s.rk, 3, d_ct, out, 1)
             assert (from_dev(out)[0] == want).all(), rad
@@ -854,10 +871,11 @@ def test_largest_ring_rotate_and_leaves(oracle):
         leaves = from_dev(d_leaf)
         for t, o in enumerate(sample):
             assert (leaves[t] == oracle.linear_output(prm, olay, cts, int(o), case.sigma_prev)).all(), o
-        sf.sf_ctx_set_option(s.ctx, "row_radix", 1)
-        d_leaf1 = dev_zeros(len(sample), 2, s.L, s.n)
-        sf.sf_linear_outputs(s.ctx, lay, d_in, info["k_in"], case.sigma_prev, sample, d_leaf1)
-        assert (from_dev(d_leaf1) == leaves).all()
+        for rad in (1, 2):
+            sf.sf_ctx_set_option(s.ctx, "row_radix", rad)
+            d_leaf1 = dev_zeros(len(sample), 2, s.L, s.n)
+            sf.sf_linear_outputs(s.ctx, lay, d_in, info["k_in"], case.sigma_prev, sample, d_leaf1)
+            assert (from_dev(d_leaf1) == leaves).all(), rad
         sf.sf_layer_destroy(lay)
     finally:
         s.close()
