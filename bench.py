@@ -344,6 +344,10 @@ def load_peaks():
 # items), kept only while the kernel's code is unchanged since the capture;
 # scaled to a full launch by its items
 TRAFFIC_PER_ITEM = {
+    # k_ks3 at N = 2^16 (5 + 2 primes), 128 x 512 split: one launch of 128
+    # merges of the small r34 case (--small, ks_batch=128), 1.636432 GB read +
+    # 0.849524 GB written
+    ("ks3_inner_row", 16): (1.636432e9 + 0.849524e9) / 128,
 }
 
 

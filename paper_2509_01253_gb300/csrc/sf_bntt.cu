@@ -102,11 +102,12 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, LR >= 8 ? 2 : 3)
         sf_cp_commit();
         sf_cp_wait<1>();
         __syncthreads();
-        if (INV) tile_inverse_t<LR, false, NT>(cur, tw, q);
-        else tile_forward_t<LR, false, NT>(cur, tw, q);
-        // inverse: the last pass, times N^-1, canonical; forward: lazy, the row pass follows
-        store_col_tile_t<LR, LC, NT>(dst + unit_off(u), cur, unit_c0(u),
-                                     [&](u64 v) { return INV ? sf_mul_shoup(v, ninv, ninv_p, q) : v; });
+        // inverse: the last pass, times N^-1, canonical; forward: lazy, the row
+        // pass follows.  The last sweep writes the tile to global memory itself.
+        u64 *gd = dst + unit_off(u) + unit_c0(u);
+        auto out = [&](int k, int b, u64 v) { gd[((size_t)k << LC) + b] = INV ? sf_mul_shoup(v, ninv, ninv_p, q) : v; };
+        if (INV) col_inverse_st<LR, NT>(cur, tw, q, out);
+        else col_forward_io<LR, NT>(cur, tw, q, [&](int k, int b) { return cur[tile_slot<SF_NB>(k, b)]; }, out);
         __syncthreads();
     }
 }

@@ -284,25 +284,28 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
         }
         __syncthreads();
         // inverse column pass of the digit's limbs, then y_i = x_i N^-1 Qhat_i^-1 mod q_i
+        // (the scaling rides on the last inverse sweep)
         for (int t = 0; t < nd; ++t) {
             const int i = lo + t;
-            u64 *st = cur + (size_t)t * tw_words;
-            tile_inverse_t<LR, false, NT>(st, twi + (size_t)t * g.r, R.m[i].q);
-            const u64 w = R.mu_inv[j * R.K + t], wp = R.mu_inv_p[j * R.K + t];
-            #pragma unroll
-            for (int e = threadIdx.x; e < (SF_NB << LR); e += NT)
-                st[col_slot(e)] = sf_mul_shoup(st[col_slot(e)], w, wp, R.m[i].q);
+            u64 *sti = cur + (size_t)t * tw_words;
+            const u64 w = R.mu_inv[j * R.K + t], wp = R.mu_inv_p[j * R.K + t], qi = R.m[i].q;
+            col_inverse_st<LR, NT>(sti, twi + (size_t)t * g.r, qi, [&](int k, int bb, u64 v) {
+                sti[tile_slot<SF_NB>(k, bb)] = sf_mul_shoup(v, w, wp, qi);
+            });
         }
         __syncthreads();
         const KsLayout Lo = ks_layout(R, B, b);
         for (int m = 0; m < R.nm; ++m) {
             if (m >= lo && m < hi) continue;
             const SfMod &M = R.m[m];
+            const sf_tw *twm = twf + (size_t)(m < lo ? m : m - nd) * g.r;
+            u64 *dst = Lo.x2 + ((size_t)(j * R.nm + m) << (LR + LC)) + c0;
+            // the forward column pass reads the conversion and writes x2 directly
+            auto out = [&](int k, int bb, u64 v) { dst[((size_t)k << LC) + bb] = v; };
             if (nd == 1 && R.modup_copy) {
                 // one-limb digit: Qhat = 1, so the conversion is the canonical
                 // residue itself, below 4 q_m and taken as it is by the transform
-#pragma unroll
-                for (int e = threadIdx.x; e < (SF_NB << LR); e += NT) work[col_slot(e)] = cur[col_slot(e)];
+                col_forward_io<LR, NT>(work, twm, M.q, [&](int k, int bb) { return cur[tile_slot<SF_NB>(k, bb)]; }, out);
             } else {
                 // base conversion, lazy: each term in [0, 2q), the sum below 2q * nd
                 // (digits hold at most 4 limbs: K <= 4)
@@ -313,21 +316,15 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
                     qh[t] = t < nd ? R.mu_qhat[ci] : 0;
                     qhp[t] = t < nd ? R.mu_qhat_p[ci] : 0;
                 }
-#pragma unroll
-                for (int e = threadIdx.x; e < (SF_NB << LR); e += NT) {
-                    const int sl = col_slot(e);
+                col_forward_io<LR, NT>(work, twm, M.q, [&](int k, int bb) {
+                    const int sl = tile_slot<SF_NB>(k, bb);
                     u64 acc = 0;
 #pragma unroll
                     for (int t = 0; t < 4; ++t)
                         if (t < nd) acc += sf_mul_shoup_lazy(cur[(size_t)t * tw_words + sl], qh[t], qhp[t], M.q);
-                    work[sl] = acc;
-                }
+                    return acc;
+                }, out);
             }
-            __syncthreads();
-            tile_forward_t<LR, false, NT>(work, twf + (size_t)(m < lo ? m : m - nd) * g.r, M.q);
-            u64 *dst = Lo.x2 + ((size_t)(j * R.nm + m) << (LR + LC));
-            #pragma unroll
-            for (int e = threadIdx.x; e < (SF_NB << LR); e += NT) dst[col_gidx_t<LC>(c0, e)] = work[col_slot(e)];
             __syncthreads();
         }
     }
@@ -472,40 +469,37 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
             sf_cp_wait<0>();
         }
         __syncthreads();
+        // inverse column pass of the special limbs, scaled by the ModDown
+        // constants on the last inverse sweep
         for (int k = 0; k < R.K; ++k) {
             const int m = R.L + k;
-            u64 *st = cur + (size_t)k * tw_words;
-            tile_inverse_t<LR, false, NT>(st, twi + (size_t)k * g.r, R.m[m].q);
-            const u64 w = R.md_inv[k], wp = R.md_inv_p[k];
-            #pragma unroll
-            for (int e = threadIdx.x; e < (SF_NB << LR); e += NT)
-                st[col_slot(e)] = sf_mul_shoup(st[col_slot(e)], w, wp, R.m[m].q);
+            u64 *stk = cur + (size_t)k * tw_words;
+            const u64 w = R.md_inv[k], wp = R.md_inv_p[k], qm = R.m[m].q;
+            col_inverse_st<LR, NT>(stk, twi + (size_t)k * g.r, qm, [&](int kk2, int bb, u64 v) {
+                stk[tile_slot<SF_NB>(kk2, bb)] = sf_mul_shoup(v, w, wp, qm);
+            });
         }
         __syncthreads();
         const KsLayout Lo = ks_layout(R, B, b);
         for (int i = 0; i < R.L; ++i) {
             const SfMod &M = R.m[i];
-            // base conversion, lazy: each term in [0, 2q), the sum below 2q * K
+            // base conversion, lazy: each term in [0, 2q), the sum below 2q * K,
+            // read by the forward column pass, which writes x2 directly
             u64 ph[4], php[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 ph[k] = k < R.K ? R.md_phat[(size_t)k * R.L + i] : 0;
                 php[k] = k < R.K ? R.md_phat_p[(size_t)k * R.L + i] : 0;
             }
-#pragma unroll
-            for (int e = threadIdx.x; e < (SF_NB << LR); e += NT) {
-                const int sl = col_slot(e);
+            u64 *dst = Lo.x2 + ((size_t)(p * R.L + i) << (LR + LC)) + c0;
+            col_forward_io<LR, NT>(work, twf + (size_t)i * g.r, M.q, [&](int kk2, int bb) {
+                const int sl = tile_slot<SF_NB>(kk2, bb);
                 u64 acc = 0;
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
                     if (k < R.K) acc += sf_mul_shoup_lazy(cur[(size_t)k * tw_words + sl], ph[k], php[k], M.q);
-                work[sl] = acc;
-            }
-            __syncthreads();
-            tile_forward_t<LR, false, NT>(work, twf + (size_t)i * g.r, M.q);
-            u64 *dst = Lo.x2 + ((size_t)(p * R.L + i) << (LR + LC));
-            #pragma unroll
-            for (int e = threadIdx.x; e < (SF_NB << LR); e += NT) dst[col_gidx_t<LC>(c0, e)] = work[col_slot(e)];
+                return acc;
+            }, [&](int kk2, int bb, u64 v) { dst[((size_t)kk2 << LC) + bb] = v; });
             __syncthreads();
         }
     }

@@ -207,8 +207,10 @@ __global__ void __launch_bounds__(SfThreads<LR>::value, SfThreads<LR>::value >= 
         }
     }
     __syncthreads();
-    tile_forward_t<LR, false, NT>(sm, tw, M.q);
-    for (int e = threadIdx.x; e < ne; e += NT) dst[col_gidx_t<LC>(c0, e)] = sm[col_slot(e)];
+    // forward column pass; its last sweep writes the tile to global memory
+    u64 *gd = dst + c0;
+    col_forward_io<LR, NT>(sm, tw, M.q, [&](int k, int b) { return sm[tile_slot<SF_NB>(k, b)]; },
+                           [&](int k, int b, u64 v) { gd[((size_t)k << LC) + b] = v; });
 }
 
 // leaf_row: grid (R/16 row tiles, L, slots).  smem: forward row twiddles + 1 tile.

@@ -115,9 +115,10 @@ __device__ __forceinline__ void unit_stages(u64 *x, int blk, int b, const sf_tw 
     }
 }
 
-// One sweep of R_ST consecutive stages over every unit of the tile.
-template <int LOG_S, int LOG_H0, int R_ST, bool INV, bool ROWTW, int NT, int NB = SF_NB>
-__device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
+// One sweep of R_ST consecutive stages over every unit of the tile, element
+// (k, b) read through ld(k, b) and written through st(k, b, v); no barrier.
+template <int LOG_S, int LOG_H0, int R_ST, bool INV, bool ROWTW, int NT, int NB, class LD, class ST>
+__device__ __forceinline__ void tile_sweep_io(const sf_tw *tw, u64 q, LD ld, ST st)
 {
     constexpr int S = 1 << LOG_S;
     constexpr int U = 1 << R_ST;
@@ -138,11 +139,21 @@ __device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
         const int first = (blk << LOG_BLK) + o;
         u64 x[U];
 #pragma unroll
-        for (int t = 0; t < U; ++t) x[t] = s[tile_slot<NB>(first + (t << LOG_STEP), b)];
+        for (int t = 0; t < U; ++t) x[t] = ld(first + (t << LOG_STEP), b);
         unit_stages<LOG_S, LOG_H0, R_ST, INV, ROWTW, NB>(x, blk, b, tw, q, two_q);
 #pragma unroll
-        for (int t = 0; t < U; ++t) s[tile_slot<NB>(first + (t << LOG_STEP), b)] = x[t];
+        for (int t = 0; t < U; ++t) st(first + (t << LOG_STEP), b, x[t]);
     }
+}
+
+// One sweep of R_ST consecutive stages over every unit of the tile, in place
+// in shared memory, then a block barrier.
+template <int LOG_S, int LOG_H0, int R_ST, bool INV, bool ROWTW, int NT, int NB = SF_NB>
+__device__ __forceinline__ void tile_sweep(u64 *s, const sf_tw *tw, u64 q)
+{
+    tile_sweep_io<LOG_S, LOG_H0, R_ST, INV, ROWTW, NT, NB>(
+        tw, q, [&](int k, int b) { return s[tile_slot<NB>(k, b)]; },
+        [&](int k, int b, u64 v) { s[tile_slot<NB>(k, b)] = v; });
     __syncthreads();
 }
 
@@ -360,6 +371,51 @@ __device__ __forceinline__ void tile_inverse_t(u64 *s, const sf_tw *tw, u64 q)
         tile_sweep<9, 0, 3, true, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<9, 3, 3, true, ROWTW, NT, NB>(s, tw, q);
         tile_sweep<9, 6, 3, true, ROWTW, NT, NB>(s, tw, q);
+    }
+}
+
+// Forward column transform of a 16-column tile whose input is produced by
+// ld(k, b) (element k of column b) and whose output is consumed by
+// st(k, b, v), staged in s in between.  For 128-point columns the first sweep
+// reads through ld and the last writes through st, so the producer (a base
+// conversion) and the consumer (the store to global memory: 16 consecutive
+// columns of one row per half-warp, 128 contiguous bytes) need no shared-
+// memory round trip and no barrier of their own.  No barrier at the end: the
+// caller syncs before it reuses s.
+template <int LOG_S, int NT, class LD, class ST>
+__device__ __forceinline__ void col_forward_io(u64 *s, const sf_tw *tw, u64 q, LD ld, ST st)
+{
+    auto s_ld = [&](int k, int b) { return s[tile_slot<SF_NB>(k, b)]; };
+    auto s_st = [&](int k, int b, u64 v) { s[tile_slot<SF_NB>(k, b)] = v; };
+    if constexpr (LOG_S == 7 && NT == 256) {
+        // the schedule of tile_forward_t<7>: radix 8, radix 4, radix 4
+        tile_sweep_io<7, 6, 3, false, false, NT, SF_NB>(tw, q, ld, s_st);
+        __syncthreads();
+        tile_sweep<7, 3, 2, false, false, NT, SF_NB>(s, tw, q);
+        tile_sweep_io<7, 1, 2, false, false, NT, SF_NB>(tw, q, s_ld, st);
+    } else {
+        for (int e = threadIdx.x; e < (SF_NB << LOG_S); e += NT) s_st(e >> 4, e & 15, ld(e >> 4, e & 15));
+        __syncthreads();
+        tile_forward_t<LOG_S, false, NT>(s, tw, q);
+        for (int e = threadIdx.x; e < (SF_NB << LOG_S); e += NT) st(e >> 4, e & 15, s_ld(e >> 4, e & 15));
+    }
+}
+
+// Inverse column transform of the tile in s whose output goes through
+// st(k, b, v) (a scaling written back in place): for 128-point columns the
+// last sweep writes through st directly.  No barrier at the end.
+template <int LOG_S, int NT, class ST>
+__device__ __forceinline__ void col_inverse_st(u64 *s, const sf_tw *tw, u64 q, ST st)
+{
+    auto s_ld = [&](int k, int b) { return s[tile_slot<SF_NB>(k, b)]; };
+    if constexpr (LOG_S == 7 && NT == 256) {
+        // the schedule of tile_inverse_t<7>: radix 4, radix 4, radix 8
+        tile_sweep<7, 0, 2, true, false, NT, SF_NB>(s, tw, q);
+        tile_sweep<7, 2, 2, true, false, NT, SF_NB>(s, tw, q);
+        tile_sweep_io<7, 4, 3, true, false, NT, SF_NB>(tw, q, s_ld, st);
+    } else {
+        tile_inverse_t<LOG_S, false, NT>(s, tw, q);
+        for (int e = threadIdx.x; e < (SF_NB << LOG_S); e += NT) st(e >> 4, e & 15, s_ld(e >> 4, e & 15));
     }
 }
 
