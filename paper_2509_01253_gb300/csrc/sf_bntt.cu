@@ -59,10 +59,14 @@ __global__ void __launch_bounds__(SfRow<LC>::NT, 3)
             sf_cp_wait<0>();
         }
         __syncthreads();
-        if (INV) row_inverse_t<LC, NT, RAD>(cur, tw, q);
-        else row_forward_t<LC, NT, RAD>(cur, tw, q);
         // forward: the last pass, canonical output; inverse: lazy in [0, 4q), the column pass follows
-        store_row_tile_t<LC, NT>(dst + unit_off(u), cur, [&](u64 v) { return INV ? v : sf_reduce(v, q, one_p); });
+        if (INV) {
+            u64 *gd = dst + unit_off(u);
+            row_inverse_out<LC, NT, RAD>(cur, tw, q, [&](int k, int b, u64 v) { gd[(b << LC) + k] = v; });
+        } else {
+            row_forward_t<LC, NT, RAD>(cur, tw, q);
+            store_row_tile_t<LC, NT>(dst + unit_off(u), cur, [&](u64 v) { return sf_reduce(v, q, one_p); });
+        }
         __syncthreads();
     }
 }

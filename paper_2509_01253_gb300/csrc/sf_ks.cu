@@ -220,11 +220,14 @@ __global__ void __launch_bounds__(SfRow<LC>::NT, 3) k_rows(SfRing R, SfKsBatch B
             sf_cp_wait<0>();
         }
         __syncthreads();
-        if (INV) row_inverse_t<LC, NT, RAD>(cur, tw, q);
-        else row_forward_t<LC, NT, RAD>(cur, tw, q);
         u64 *dst = B.scratch + unit_off(u, S.dst_off);
-        #pragma unroll
-        for (int e = threadIdx.x; e < SfRow<LC>::ELEMS; e += NT) dst[e] = cur[row_slot_t<LC>(e)];
+        if (INV) {
+            row_inverse_out<LC, NT, RAD>(cur, tw, q, [&](int kk, int bb, u64 v) { dst[(bb << LC) + kk] = v; });
+        } else {
+            row_forward_t<LC, NT, RAD>(cur, tw, q);
+            #pragma unroll
+            for (int e = threadIdx.x; e < SfRow<LC>::ELEMS; e += NT) dst[e] = cur[row_slot_t<LC>(e)];
+        }
         __syncthreads();
     }
 }

@@ -11,12 +11,10 @@
 // then row pass; inverse = row pass then column pass.
 //
 // A tile holds NB sub-transforms (16 columns of R elements, or NB rows of C
-// elements: NB = 16, or 8 for 256-point rows) in shared memory as [k][b]:
-// element k of sub-transform b sits at k*(NB + 1) + b.  With that stride the
-// coalesced global loads of both tile kinds are free of bank conflicts, and so
-// is every butterfly sweep of a 16-wide tile (consecutive threads on
-// consecutive b); an 8-wide tile puts two units in a half-warp, which share
-// one bank pair once.
+// elements: NB = 16, 8 for 256-point rows, 4 for 512-point rows) in shared
+// memory as [k][b] (tile_slot): a 17-word pitch for 16-wide tiles, XOR-swizzled
+// rows of NB words otherwise, so that the coalesced copies and nearly every
+// butterfly sweep are free of bank conflicts.
 //
 // Twiddles are staged in shared memory as (w, w') pairs, w' = floor(w 2^64/q)
 // (Shoup).  Local stage with m groups, group g, uses local index k = m + g:
@@ -575,17 +573,6 @@ __device__ __forceinline__ void store_row_tile_t(u64 *dst, const u64 *src, F f)
     }
 }
 
-// shared column tile -> global (R rows of 16 columns from c0)
-template <int LR, int LC, int NT, class F>
-__device__ __forceinline__ void store_col_tile_t(u64 *dst, const u64 *src, int c0, F f)
-{
-    constexpr int E = (SF_NB << LR) / NT;
-    u64 *g0 = dst + c0 + (threadIdx.x & 15) + (size_t)(threadIdx.x >> 4) * (1 << LC);
-    const u64 *s0 = src + (threadIdx.x >> 4) * SF_PAD + (threadIdx.x & 15);
-#pragma unroll
-    for (int x = 0; x < E; ++x) g0[(size_t)x * (NT / 16) * (1 << LC)] = f(s0[x * (NT / 16) * SF_PAD]);
-}
-
 // twiddles of the row tile starting at row r0 for modulus mod ([nm][R/NB][C][NB] table)
 template <int LR, int LC, int NT>
 __device__ __forceinline__ void load_row_tw_t(sf_tw *dst, const sf_tw *__restrict__ table, int mod, int r0)
@@ -608,6 +595,32 @@ template <int LC, int NT, int RAD = 0>
 __device__ __forceinline__ void row_inverse_t(u64 *s, const sf_tw *tw, u64 q)
 {
     tile_inverse_t<LC, true, NT, SfRow<LC>::NB, RAD>(s, tw, q);
+}
+
+// Inverse row pass whose output goes to st(k, b, v) (element k of row b).  In
+// 256- and 512-point rows under the radix-8 schedule the last sweep writes
+// through st itself: its units hold elements 32 or 64 apart, so a warp stores
+// 4 or 8 consecutive elements of each of its rows (whole 32-byte sectors).
+// Otherwise the pass runs in shared memory and a copy loop calls st in row
+// order.  No barrier at the end.
+template <int LC, int NT, int RAD, class ST>
+__device__ __forceinline__ void row_inverse_out(u64 *s, const sf_tw *tw, u64 q, ST st)
+{
+    constexpr int NB = SfRow<LC>::NB;
+    auto s_ld = [&](int k, int b) { return s[tile_slot<NB>(k, b)]; };
+    if constexpr (RAD == 0 && NT == 256 && LC == 9 && NB == 4) {
+        tile_sweep<9, 0, 3, true, true, NT, NB>(s, tw, q);
+        tile_sweep<9, 3, 3, true, true, NT, NB>(s, tw, q);
+        tile_sweep_io<9, 6, 3, true, true, NT, NB>(tw, q, s_ld, st);
+    } else if constexpr (RAD == 0 && NT == 256 && LC == 8 && NB == 8) {
+        tile_sweep<8, 0, 2, true, true, NT, NB>(s, tw, q);
+        tile_sweep<8, 2, 3, true, true, NT, NB>(s, tw, q);
+        tile_sweep_io<8, 5, 3, true, true, NT, NB>(tw, q, s_ld, st);
+    } else {
+        row_inverse_t<LC, NT, RAD>(s, tw, q);
+#pragma unroll
+        for (int e = threadIdx.x; e < SfRow<LC>::ELEMS; e += NT) st(e & ((1 << LC) - 1), e >> LC, s_ld(e & ((1 << LC) - 1), e >> LC));
+    }
 }
 
 // column twiddles (R pairs) of modulus mod
