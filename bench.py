@@ -448,6 +448,43 @@ def ntt_record(sf, torch, wl_, p_info: dict, probe: dict, flush) -> dict:
             "frac_hbm": gbs / hbm_peak, "gmodmul_s": gmm, "frac_of_probe": gmm / probe["fwd_bfly"]}
 
 
+def pp_ntt_record(local: int, flush, t: int = 3, alpha: int = 7, L: int = 5, count: int = 4096) -> dict:
+    """Batched length-M transform of the paper's prime-power ring M = 3^7
+    (Table 2; sf_pp_ntt, one block per limb, radix-3 stages in shared memory)
+    over count x L limbs: algorithmic GB/s (each limb read and written once)
+    and radix-3 butterflies/s (M/3 per stage, alpha stages, each 6 modular
+    products counted as 6)."""
+    import torch
+    import paper_2509_01253_gb300 as sf
+    r = sf.sf_pp_ring_create(t, alpha, L, 50, local)
+    try:
+        info = sf.sf_pp_ring_info(r, L)
+        M = info["M"]
+        x = torch.randint(0, min(info["moduli"]), (count, L, M), dtype=torch.int64, device=f"cuda:{local}")
+        y = torch.empty_like(x)
+        stream = torch.cuda.current_stream()
+        for _ in range(3):
+            sf.sf_pp_ntt(r, x, y, count, False, stream)
+        reps = 5
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for i in range(reps):
+            flush_l2(flush)
+            ev[i][0].record(stream)
+            sf.sf_pp_ntt(r, x, y, count, False, stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / reps
+        nbytes = 2 * count * L * M * 8
+        mods = count * L * (M // t) * alpha * (t - 1) * t
+        hbm_peak, kind = load_peaks()
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        return {"what": f"forward length-{M} transform (M = {t}^{alpha}, N = {info['N']}) of {count} x {L} limbs "
+                        f"(sf_pp_ntt)", "ms_per_call": ms, "algorithmic_bytes": nbytes, "gbs": gbs,
+                "frac_hbm": gbs / hbm_peak, "peak_source": kind, "gmodmul_s": mods / (ms * 1e-3) / 1e9}
+    finally:
+        sf.sf_pp_ring_destroy(r)
+
+
 # ------------------------------------------------------- CPU baseline ----
 
 def host_cores() -> int:
@@ -1141,7 +1178,8 @@ def main():
                          ("serving", lambda: serving_record(local)),
                          ("batched_vs_per_layer", lambda: batched_record(local, "resnet18", BATCH_ROUNDS)),
                          ("batched_small_rounds", lambda: batched_record(local, "resnet20", R20_LATE)),
-                         ("batched_requests", lambda: batched_record(local, "resnet20", ["s2b1c1"], copies=7))):
+                         ("batched_requests", lambda: batched_record(local, "resnet20", ["s2b1c1"], copies=7)),
+                         ("pp_ntt", lambda: pp_ntt_record(local, flush))):
             t0 = time.perf_counter()
             try:
                 extras[name] = fn()

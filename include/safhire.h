@@ -477,6 +477,53 @@ sf_status sf_modmul_probe(sf_ctx *ctx, int32_t kind, double *gmodmul_per_s);
 sf_status sf_poly_mul(sf_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b, uint64_t *d_out, int32_t n_polys,
                       void *stream);
 
+/* ---- prime-power cyclotomic rings (Sec. 2.1-2.3; Table 2's M = 3^7, 7^4, 5^5)
+ *
+ * K = Q[X]/Phi_M(X) with M = t^alpha, t an odd prime, N = phi(M) = (t-1) t^(alpha-1),
+ * Phi_M(X) = sum_{k<t} X^(k M/t), reduced modulo L RNS primes q_i = 1 (mod M).
+ * Polynomials are uint64[count][L][N] coefficient arrays, canonical residues,
+ * device memory owned by the caller; count <= 65535 per call.  Every call is
+ * asynchronous on `stream`. */
+typedef struct sf_pp_ring sf_pp_ring;
+
+/* The ring for (t, alpha) with the L largest primes q = 1 (mod M) below 2^bits
+ * and, per prime, a primitive M-th root of unity omega and its power tables
+ * (uploaded to `device`).  Errors: SF_EINVAL (t not an odd prime <= 7, M = t^alpha
+ * outside [t^2, 4096], 1 <= L <= SF_MAX_MODULI and 20 <= bits <= 61 violated, or too few
+ * primes), SF_ECUDA. */
+sf_status sf_pp_ring_create(int32_t t, int32_t alpha, int32_t L, int32_t bits, int32_t device, sf_pp_ring **out);
+void sf_pp_ring_destroy(sf_pp_ring *ring);
+/* N, M and the L moduli (each output may be NULL). */
+sf_status sf_pp_ring_info(const sf_pp_ring *ring, int32_t *N, int32_t *M, uint64_t *moduli);
+
+/* Length-M cyclic transform over Z_{q_i} of uint64[count][L][M] (d_out may
+ * equal d_in).  inverse = 0: natural order in, out[j] = sum_k in[k] omega^(k rev(j)),
+ * rev(j) reversing the alpha base-t digits of j; inverse = 1: the exact
+ * inverse (digit-reversed in, natural out, times M^-1).  The transform that
+ * stands in for the paper's length-M FFT (Sec. 6.1).  Errors: SF_EINVAL, SF_ECUDA. */
+sf_status sf_pp_ntt(sf_pp_ring *ring, const uint64_t *d_in, uint64_t *d_out, int32_t count, int32_t inverse,
+                    void *stream);
+
+/* d_out[x] = d_a[x] * d_b[x] in Z_{q_i}[X]/Phi_M (length-M cyclic product by
+ * the transform, then the reduction modulo Phi_M).  Errors: SF_EINVAL, SF_ECUDA. */
+sf_status sf_pp_mul(sf_pp_ring *ring, const uint64_t *d_a, const uint64_t *d_b, uint64_t *d_out, int32_t count,
+                    void *stream);
+
+/* d_out[x] = tau_d(d_in[x]) = d_in[x](X^d) mod Phi_M for gcd(d, M) = 1 (Sec. 2.2);
+ * d_out must not alias d_in.  Errors: SF_EINVAL (d a multiple of t), SF_ECUDA. */
+sf_status sf_pp_automorphism(sf_pp_ring *ring, const uint64_t *d_in, uint64_t *d_out, int32_t count, int32_t d,
+                             void *stream);
+
+/* The trace along the tower of Sec. 2.3: gamma = 0 the full trace Tr_{K/Q}
+ * (Tr_{K_(i+1)/K_i} for i = alpha-1 .. 1 by powers of tau_(1+t^i), then
+ * Tr_{K_1/K_0} one prime factor of t - 1 at a time), gamma >= 1 the partial
+ * trace Tr_{K/K_gamma} only.  *n_automorphisms (may be NULL) receives the
+ * automorphisms applied: (alpha - max(gamma,1))(t-1), plus sum (l - 1) over the
+ * prime factors l of t - 1 at gamma = 0.  Uses a grow-only scratch of the ring
+ * (2 x count x L x N words).  Errors: SF_EINVAL (gamma outside [0, alpha]), SF_ECUDA. */
+sf_status sf_pp_trace(sf_pp_ring *ring, const uint64_t *d_in, uint64_t *d_out, int32_t count, int32_t gamma,
+                      int32_t *n_automorphisms, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -98,6 +98,13 @@ _SIGS = {
     "sf_poly_mul": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
     "sf_ntt_batch": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp]),
     "sf_modmul_probe": (_i32, [_vp, _i32, ctypes.POINTER(_dbl)]),
+    "sf_pp_ring_create": (_i32, [_i32, _i32, _i32, _i32, _i32, _pp]),
+    "sf_pp_ring_destroy": (None, [_vp]),
+    "sf_pp_ring_info": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _vp]),
+    "sf_pp_ntt": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp]),
+    "sf_pp_mul": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
+    "sf_pp_automorphism": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp]),
+    "sf_pp_trace": (_i32, [_vp, _vp, _vp, _i32, _i32, ctypes.POINTER(_i32), _vp]),
 }
 
 _lib = None
@@ -461,3 +468,39 @@ def sf_modmul_probe(ctx, kind: int) -> float:
 
 
 EXPORTED = sorted(_SIGS)
+
+
+# ---------------------------------------------------- prime-power rings --
+
+def sf_pp_ring_create(t: int, alpha: int, L: int, bits: int, device: int = 0):
+    return _out_handle(lib().sf_pp_ring_create, t, alpha, L, bits, device)
+
+
+def sf_pp_ring_destroy(r):
+    lib().sf_pp_ring_destroy(r)
+
+
+def sf_pp_ring_info(r, L: int) -> dict:
+    n, m = _i32(), _i32()
+    mods = np.zeros(L, dtype=np.uint64)
+    _check(lib().sf_pp_ring_info(r, ctypes.byref(n), ctypes.byref(m), mods.ctypes.data))
+    return {"N": n.value, "M": m.value, "moduli": [int(q) for q in mods]}
+
+
+def sf_pp_ntt(r, d_in, d_out, count: int, inverse: bool, stream=None):
+    _check(lib().sf_pp_ntt(r, _ptr(d_in), _ptr(d_out), count, 1 if inverse else 0, _stream(stream)))
+
+
+def sf_pp_mul(r, d_a, d_b, d_out, count: int, stream=None):
+    _check(lib().sf_pp_mul(r, _ptr(d_a), _ptr(d_b), _ptr(d_out), count, _stream(stream)))
+
+
+def sf_pp_automorphism(r, d_in, d_out, count: int, d: int, stream=None):
+    _check(lib().sf_pp_automorphism(r, _ptr(d_in), _ptr(d_out), count, d, _stream(stream)))
+
+
+def sf_pp_trace(r, d_in, d_out, count: int, gamma: int, stream=None) -> int:
+    """Returns the number of automorphisms applied."""
+    n = _i32()
+    _check(lib().sf_pp_trace(r, _ptr(d_in), _ptr(d_out), count, gamma, ctypes.byref(n), _stream(stream)))
+    return n.value

@@ -1,0 +1,439 @@
+// sf_pp.cu -- arithmetic in the paper's prime-power cyclotomic rings
+// K = Q[X] / Phi_M(X), M = t^alpha with t an odd prime (Sec. 2.1-2.3; Table 2
+// lists M = 3^7, 7^4, 5^5), modulo RNS primes q_i = 1 (mod M).
+//
+// Phi_M(X) = sum_{k < t} X^(k m), m = M / t, N = phi(M) = (t - 1) m.  Products
+// in Z_q[X] / Phi_M are taken as cyclic products of length M (Phi_M divides
+// X^M - 1) followed by the reduction X^(N + e) = -sum_{k < t-1} X^(e + k m),
+// e < m.  The cyclic product uses a length-M radix-t number-theoretic
+// transform over Z_q with omega a primitive M-th root of unity: decimation in
+// frequency (Gentleman-Sande) forward, natural input and base-t digit-reversed
+// output, and the mirror decimation in time inverse with the factor M^-1.
+// Automorphisms tau_d: X -> X^d permute the length-M coefficients (i -> i d
+// mod M) before the same reduction; traces are sums of automorphisms taken
+// along the tower of Sec. 2.3.
+//
+// One block per (polynomial, limb) holds its length-M vector in shared memory
+// (at most 3125 words for Table 2's rings).  Each radix-t butterfly runs the
+// t-point DFT with t products per output, summed lazily below 2 t q, then one
+// reduction; twiddles and t-th roots come from a per-limb table of omega^e.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "sf_arith.cuh"
+#include "sf_internal.h"
+
+#define SF_PP_THREADS 256
+#define SF_PP_MAX_T 7
+#define SF_PP_MAX_M 4096
+
+struct SfPpMod {
+    u64 q, one_p;            // modulus, floor(2^64 / q)
+    u64 qinv_neg, r2;        // -q^-1 mod 2^64, 2^128 mod q (Montgomery products of two residues)
+    u64 minv, minv_p;        // M^-1 mod q (Shoup)
+};
+
+struct SfPpRing {
+    int t, alpha, M, N, m, L;
+    const u64 *w;            // [L][M] omega_i^e
+    const u64 *w_p;          // [L][M] Shoup companions
+    const u64 *iw;           // [L][M] omega_i^-e
+    const u64 *iw_p;
+    SfPpMod mod[SF_MAX_MODULI];
+};
+
+struct sf_pp_ring {
+    int device;
+    SfPpRing R;
+    std::vector<u64> q;
+    u64 *d_tables = nullptr;     // w, w_p, iw, iw_p
+    u64 *d_scratch = nullptr;    // trace work buffers
+    size_t scratch_words = 0;
+};
+
+// a * b mod q for two residues below q (two Montgomery reductions: a b 2^-64,
+// then times 2^128 2^-64)
+__device__ __forceinline__ u64 pp_mulmod(u64 a, u64 b, const SfPpMod &P)
+{
+    return sf_mul_mont(sf_mul_mont(a, b, P.q, P.qinv_neg), P.r2, P.q, P.qinv_neg);
+}
+
+// one forward (DIF) stage of span len over the block's vector s
+__device__ __forceinline__ void pp_stage_fwd(u64 *s, const SfPpRing &R, int i, int len)
+{
+    const int t = R.t, third = len / t, stride = R.M / len;
+    const u64 q = R.mod[i].q, one_p = R.mod[i].one_p;
+    const u64 *w = R.w + (size_t)i * R.M, *wp = R.w_p + (size_t)i * R.M;
+    const int root_t = R.M / t;   // omega^(M/t): a primitive t-th root
+    for (int idx = threadIdx.x; idx < R.M / t; idx += blockDim.x) {
+        const int blk = idx / third, j = idx - blk * third;
+        const int base = blk * len + j;
+        u64 x[SF_PP_MAX_T];
+        for (int r = 0; r < t; ++r) x[r] = s[base + r * third];
+        for (int k = 0; k < t; ++k) {
+            // y_k = sum_r x_r zeta^(r k), zeta = omega^(M/t); lazily below 2 t q
+            u64 acc = x[0];
+            for (int r = 1; r < t; ++r) {
+                const int e = (root_t * ((r * k) % t)) % R.M;
+                acc += sf_mul_shoup_lazy(x[r], w[e], wp[e], q);
+            }
+            u64 y = sf_reduce(acc, q, one_p);
+            // twiddle omega_len^(j k) = omega^(stride j k)
+            const int e = (int)(((long long)stride * j * k) % R.M);
+            if (e) y = sf_mul_shoup(y, w[e], wp[e], q);
+            s[base + k * third] = y;
+        }
+    }
+}
+
+// one inverse (DIT) stage of span len: untwiddle, then the inverse t-point DFT
+__device__ __forceinline__ void pp_stage_inv(u64 *s, const SfPpRing &R, int i, int len)
+{
+    const int t = R.t, third = len / t, stride = R.M / len;
+    const u64 q = R.mod[i].q, one_p = R.mod[i].one_p;
+    const u64 *iw = R.iw + (size_t)i * R.M, *iwp = R.iw_p + (size_t)i * R.M;
+    const int root_t = R.M / t;
+    for (int idx = threadIdx.x; idx < R.M / t; idx += blockDim.x) {
+        const int blk = idx / third, j = idx - blk * third;
+        const int base = blk * len + j;
+        u64 x[SF_PP_MAX_T];
+        for (int k = 0; k < t; ++k) {
+            u64 v = s[base + k * third];
+            const int e = (int)(((long long)stride * j * k) % R.M);
+            x[k] = e ? sf_mul_shoup(v, iw[e], iwp[e], q) : v;
+        }
+        for (int r = 0; r < t; ++r) {
+            u64 acc = x[0];
+            for (int k = 1; k < t; ++k) {
+                const int e = (root_t * ((r * k) % t)) % R.M;
+                acc += sf_mul_shoup_lazy(x[k], iw[e], iwp[e], q);
+            }
+            s[base + r * third] = sf_reduce(acc, q, one_p);
+        }
+    }
+}
+
+__device__ __forceinline__ void pp_forward(u64 *s, const SfPpRing &R, int i)
+{
+    for (int len = R.M; len >= R.t; len /= R.t) {
+        pp_stage_fwd(s, R, i, len);
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void pp_inverse(u64 *s, const SfPpRing &R, int i)
+{
+    for (int len = R.t; len <= R.M; len *= R.t) {
+        pp_stage_inv(s, R, i, len);
+        __syncthreads();
+    }
+    const SfPpMod &P = R.mod[i];
+    for (int e = threadIdx.x; e < R.M; e += blockDim.x) s[e] = sf_mul_shoup(s[e], P.minv, P.minv_p, P.q);
+    __syncthreads();
+}
+
+// X^(N + e) = -sum_{k < t-1} X^(e + k m): fold positions N .. M-1 into 0 .. N-1
+__device__ __forceinline__ void pp_reduce_phi(u64 *s, const SfPpRing &R, int i)
+{
+    const u64 q = R.mod[i].q;
+    for (int e = threadIdx.x; e < R.m; e += blockDim.x) {
+        const u64 v = s[R.N + e];
+        for (int k = 0; k < R.t - 1; ++k) s[e + k * R.m] = sf_sub(s[e + k * R.m], v, q);
+    }
+    __syncthreads();
+}
+
+// Batched length-M transform: grid (L, count); [count][L][M] in and out.
+__global__ void __launch_bounds__(SF_PP_THREADS) k_pp_ntt(SfPpRing R, const u64 *in, u64 *out, int inverse)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    u64 *s = (u64 *)smem_raw;
+    const int i = blockIdx.x;
+    const size_t off = ((size_t)blockIdx.y * R.L + i) * R.M;
+    for (int e = threadIdx.x; e < R.M; e += blockDim.x) s[e] = in[off + e];
+    __syncthreads();
+    if (inverse) pp_inverse(s, R, i);
+    else pp_forward(s, R, i);
+    for (int e = threadIdx.x; e < R.M; e += blockDim.x) out[off + e] = s[e];
+}
+
+// Products in Z_q[X] / Phi_M: grid (L, count); a, b, out [count][L][N], canonical.
+__global__ void __launch_bounds__(SF_PP_THREADS) k_pp_mul(SfPpRing R, const u64 *a, const u64 *b, u64 *out)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    u64 *sa = (u64 *)smem_raw, *sb = sa + R.M;
+    const int i = blockIdx.x;
+    const size_t off = ((size_t)blockIdx.y * R.L + i) * R.N;
+    for (int e = threadIdx.x; e < R.M; e += blockDim.x) {
+        sa[e] = e < R.N ? a[off + e] : 0;
+        sb[e] = e < R.N ? b[off + e] : 0;
+    }
+    __syncthreads();
+    pp_forward(sa, R, i);
+    pp_forward(sb, R, i);
+    for (int e = threadIdx.x; e < R.M; e += blockDim.x) sa[e] = pp_mulmod(sa[e], sb[e], R.mod[i]);
+    __syncthreads();
+    pp_inverse(sa, R, i);
+    pp_reduce_phi(sa, R, i);
+    for (int e = threadIdx.x; e < R.N; e += blockDim.x) out[off + e] = sa[e];
+}
+
+// tau_d: X -> X^d, gcd(d, M) = 1: coefficient i moves to i d mod M (distinct
+// targets), then the Phi_M reduction.  grid (L, count); [count][L][N].
+__global__ void __launch_bounds__(SF_PP_THREADS) k_pp_auto(SfPpRing R, const u64 *in, u64 *out, int d)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    u64 *s = (u64 *)smem_raw;
+    const int i = blockIdx.x;
+    const size_t off = ((size_t)blockIdx.y * R.L + i) * R.N;
+    for (int e = threadIdx.x; e < R.M; e += blockDim.x) s[e] = 0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < R.N; e += blockDim.x) s[(int)(((long long)e * d) % R.M)] = in[off + e];
+    __syncthreads();
+    pp_reduce_phi(s, R, i);
+    for (int e = threadIdx.x; e < R.N; e += blockDim.x) out[off + e] = s[e];
+}
+
+// acc += x, limb-wise modulo q_i; [count][L][N]
+__global__ void k_pp_add(SfPpRing R, u64 *acc, const u64 *x, size_t total)
+{
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)((k / R.N) % R.L);
+        acc[k] = sf_add(acc[k], x[k], R.mod[i].q);
+    }
+}
+
+// ------------------------------------------------------------------ host ----
+
+static u64 pp_powmod(u64 a, u64 e, u64 q) { return sf_host_powmod(a, e, q); }
+
+// element of exact multiplicative order M = t^alpha modulo q (q = 1 mod M)
+static u64 pp_root(u64 q, int M, int t)
+{
+    for (u64 g = 2; g < q; ++g) {
+        const u64 x = pp_powmod(g, (q - 1) / (u64)M, q);
+        if (pp_powmod(x, (u64)(M / t), q) != 1) return x;
+    }
+    return 0;
+}
+
+static bool pp_is_odd_prime(int t)
+{
+    if (t < 3 || !(t & 1)) return false;
+    for (int d = 3; d * d <= t; d += 2)
+        if (t % d == 0) return false;
+    return true;
+}
+
+extern "C" sf_status sf_pp_ring_create(int32_t t, int32_t alpha, int32_t L, int32_t bits, int32_t device,
+                                       sf_pp_ring **out)
+{
+    if (!out) return sf_set_error(SF_EINVAL, "sf_pp_ring_create: null output");
+    *out = nullptr;
+    if (!pp_is_odd_prime(t) || t > SF_PP_MAX_T || alpha < 1 || L < 1 || L > SF_MAX_MODULI || bits < 20 || bits > 61)
+        return sf_set_error(SF_EINVAL, "sf_pp_ring_create: t must be an odd prime <= 7, 1 <= L <= %d, 20 <= bits <= 61",
+                            SF_MAX_MODULI);
+    long long M = 1;
+    for (int k = 0; k < alpha; ++k) M *= t;
+    if (M < t * t || M > SF_PP_MAX_M) return sf_set_error(SF_EINVAL, "sf_pp_ring_create: M = t^alpha must lie in [t^2, %d]", SF_PP_MAX_M);
+    sf_pp_ring *r = new sf_pp_ring();
+    r->device = device;
+    SfPpRing &R = r->R;
+    R.t = t;
+    R.alpha = alpha;
+    R.M = (int)M;
+    R.m = (int)(M / t);
+    R.N = (t - 1) * R.m;
+    R.L = L;
+    r->q.resize(L);
+    if (sf_find_primes((u64)M, bits, L, r->q.data()) != L) {
+        delete r;
+        return sf_set_error(SF_EINVAL, "sf_pp_ring_create: not enough primes = 1 mod %lld below 2^%d", M, bits);
+    }
+    std::vector<u64> tab((size_t)4 * L * R.M);
+    for (int i = 0; i < L; ++i) {
+        const u64 q = r->q[i];
+        const u64 w = pp_root(q, R.M, t), iw = sf_host_invmod(w, q);
+        u64 a = 1, b = 1;
+        for (int e = 0; e < R.M; ++e) {
+            tab[(size_t)0 * L * R.M + (size_t)i * R.M + e] = a;
+            tab[(size_t)1 * L * R.M + (size_t)i * R.M + e] = sf_shoup_companion(a, q);
+            tab[(size_t)2 * L * R.M + (size_t)i * R.M + e] = b;
+            tab[(size_t)3 * L * R.M + (size_t)i * R.M + e] = sf_shoup_companion(b, q);
+            a = sf_host_mulmod(a, w, q);
+            b = sf_host_mulmod(b, iw, q);
+        }
+        SfPpMod &P = R.mod[i];
+        P.q = q;
+        P.one_p = sf_shoup_companion(1, q);
+        u64 inv = 1;   // q^-1 mod 2^64 by Newton iteration
+        for (int k = 0; k < 6; ++k) inv *= 2 - q * inv;
+        P.qinv_neg = (u64)0 - inv;
+        const u64 r1 = (u64)(((unsigned __int128)1 << 64) % q);
+        P.r2 = sf_host_mulmod(r1, r1, q);
+        P.minv = sf_host_invmod((u64)R.M % q, q);
+        P.minv_p = sf_shoup_companion(P.minv, q);
+    }
+    // the product kernel holds two length-M vectors (up to 64 KB of shared memory)
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaFuncSetAttribute(k_pp_mul, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * sizeof(u64) * SF_PP_MAX_M)) != cudaSuccess ||
+        cudaMalloc((void **)&r->d_tables, sizeof(u64) * tab.size()) != cudaSuccess ||
+        cudaMemcpy(r->d_tables, tab.data(), sizeof(u64) * tab.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        if (r->d_tables) cudaFree(r->d_tables);
+        delete r;
+        return sf_set_error(SF_ECUDA, "sf_pp_ring_create: table upload failed");
+    }
+    R.w = r->d_tables;
+    R.w_p = R.w + (size_t)L * R.M;
+    R.iw = R.w_p + (size_t)L * R.M;
+    R.iw_p = R.iw + (size_t)L * R.M;
+    *out = r;
+    return SF_OK;
+}
+
+extern "C" void sf_pp_ring_destroy(sf_pp_ring *r)
+{
+    if (!r) return;
+    cudaSetDevice(r->device);
+    if (r->d_tables) cudaFree(r->d_tables);
+    if (r->d_scratch) cudaFree(r->d_scratch);
+    delete r;
+}
+
+extern "C" sf_status sf_pp_ring_info(const sf_pp_ring *r, int32_t *N, int32_t *M, uint64_t *moduli)
+{
+    if (!r) return sf_set_error(SF_EINVAL, "sf_pp_ring_info: null ring");
+    if (N) *N = r->R.N;
+    if (M) *M = r->R.M;
+    if (moduli)
+        for (int i = 0; i < r->R.L; ++i) moduli[i] = r->q[i];
+    return SF_OK;
+}
+
+static sf_status pp_check(const sf_pp_ring *r, const void *a, const void *b, int count)
+{
+    if (!r || !a || !b || count < 1) return sf_set_error(SF_EINVAL, "prime-power ring: bad arguments");
+    if (count > 65535) return sf_set_error(SF_EINVAL, "prime-power ring: at most 65535 polynomials per call");
+    if (cudaSetDevice(r->device) != cudaSuccess) return sf_set_error(SF_ECUDA, "cudaSetDevice failed");
+    return SF_OK;
+}
+
+extern "C" sf_status sf_pp_ntt(sf_pp_ring *r, const uint64_t *d_in, uint64_t *d_out, int32_t count, int32_t inverse,
+                               void *stream)
+{
+    SF_TRY(pp_check(r, d_in, d_out, count));
+    if (inverse != 0 && inverse != 1) return sf_set_error(SF_EINVAL, "sf_pp_ntt: inverse must be 0 or 1");
+    const SfPpRing &R = r->R;
+    k_pp_ntt<<<dim3(R.L, count), SF_PP_THREADS, sizeof(u64) * R.M, (cudaStream_t)stream>>>(R, d_in, d_out, inverse);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+extern "C" sf_status sf_pp_mul(sf_pp_ring *r, const uint64_t *d_a, const uint64_t *d_b, uint64_t *d_out,
+                               int32_t count, void *stream)
+{
+    SF_TRY(pp_check(r, d_a, d_b, count));
+    if (!d_out) return sf_set_error(SF_EINVAL, "sf_pp_mul: null output");
+    const SfPpRing &R = r->R;
+    k_pp_mul<<<dim3(R.L, count), SF_PP_THREADS, 2 * sizeof(u64) * R.M, (cudaStream_t)stream>>>(R, d_a, d_b, d_out);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+static sf_status pp_auto(sf_pp_ring *r, const u64 *in, u64 *out, int count, int d, cudaStream_t st)
+{
+    const SfPpRing &R = r->R;
+    const int dd = ((d % R.M) + R.M) % R.M;
+    if (dd % R.t == 0) return sf_set_error(SF_EINVAL, "automorphism index %d not coprime to M = %d", d, R.M);
+    k_pp_auto<<<dim3(R.L, count), SF_PP_THREADS, sizeof(u64) * R.M, st>>>(R, in, out, dd);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+extern "C" sf_status sf_pp_automorphism(sf_pp_ring *r, const uint64_t *d_in, uint64_t *d_out, int32_t count,
+                                        int32_t d, void *stream)
+{
+    SF_TRY(pp_check(r, d_in, d_out, count));
+    if (d_in == d_out) return sf_set_error(SF_EINVAL, "sf_pp_automorphism: in place is not supported");
+    return pp_auto(r, d_in, d_out, count, d, (cudaStream_t)stream);
+}
+
+static void pp_prime_factors(int x, std::vector<int> &out)
+{
+    for (int d = 2; d * d <= x; ++d)
+        while (x % d == 0) {
+            out.push_back(d);
+            x /= d;
+        }
+    if (x > 1) out.push_back(x);
+}
+
+// the automorphisms of the tower of Sec. 2.3: per step (h, length), the step
+// maps x to sum_{k < length} tau_h^k(x)
+static void pp_tower_steps(const SfPpRing &R, int gamma, std::vector<std::pair<int, int>> &steps)
+{
+    long long tp = 1;
+    for (int k = 0; k < R.alpha - 1; ++k) tp *= R.t;     // t^(alpha-1)
+    // Tr_{K_(i+1) / K_i} for i = alpha - 1 .. max(gamma, 1): generator 1 + t^i, order t
+    for (int i = R.alpha - 1; i >= std::max(gamma, 1); --i, tp /= R.t) steps.push_back({(int)((1 + tp) % R.M), R.t});
+    if (gamma >= 1) return;
+    // Tr_{K_1 / K_0}: the cyclic group (Z/MZ)^* / (1 + tZ) of order t - 1, one
+    // prime factor l at a time, with a primitive root g mod M
+    std::vector<int> fac;
+    pp_prime_factors(R.N, fac);
+    std::sort(fac.begin(), fac.end());
+    fac.erase(std::unique(fac.begin(), fac.end()), fac.end());
+    int g = 2;
+    for (; g < R.M; ++g) {
+        if (g % R.t == 0) continue;
+        bool ok = true;
+        for (int f : fac) ok = ok && sf_host_powmod((u64)g, (u64)(R.N / f), (u64)R.M) != 1;
+        if (ok) break;
+    }
+    std::vector<int> lf;
+    pp_prime_factors(R.t - 1, lf);
+    int rest = R.t - 1;
+    for (int l : lf) {
+        rest /= l;
+        steps.push_back({(int)sf_host_powmod((u64)g, (u64)rest, (u64)R.M), l});
+    }
+}
+
+extern "C" sf_status sf_pp_trace(sf_pp_ring *r, const uint64_t *d_in, uint64_t *d_out, int32_t count, int32_t gamma,
+                                 int32_t *n_automorphisms, void *stream)
+{
+    SF_TRY(pp_check(r, d_in, d_out, count));
+    const SfPpRing &R = r->R;
+    if (gamma < 0 || gamma > R.alpha) return sf_set_error(SF_EINVAL, "sf_pp_trace: gamma must lie in [0, alpha]");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t words = (size_t)count * R.L * R.N;
+    if (r->scratch_words < 2 * words) {
+        if (r->d_scratch) cudaFree(r->d_scratch);
+        r->d_scratch = nullptr;
+        r->scratch_words = 0;
+        SF_CUDA_TRY(cudaMalloc((void **)&r->d_scratch, sizeof(u64) * 2 * words));
+        r->scratch_words = 2 * words;
+    }
+    u64 *cur = r->d_scratch, *nxt = cur + words;
+    std::vector<std::pair<int, int>> steps;
+    pp_tower_steps(R, gamma, steps);
+    // acc (in d_out) starts as the input; each step: acc <- sum_k tau_h^k(acc)
+    SF_CUDA_TRY(cudaMemcpyAsync(d_out, d_in, sizeof(u64) * words, cudaMemcpyDeviceToDevice, st));
+    int autos = 0;
+    const int grid = (int)std::min<size_t>((words + 255) / 256, 4096);
+    for (const auto &s : steps) {
+        SF_CUDA_TRY(cudaMemcpyAsync(cur, d_out, sizeof(u64) * words, cudaMemcpyDeviceToDevice, st));
+        for (int k = 1; k < s.second; ++k) {
+            SF_TRY(pp_auto(r, cur, nxt, count, s.first, st));
+            std::swap(cur, nxt);
+            k_pp_add<<<grid, 256, 0, st>>>(R, d_out, cur, words);
+            SF_CUDA_TRY(cudaGetLastError());
+            ++autos;
+        }
+    }
+    if (n_automorphisms) *n_automorphisms = autos;
+    return SF_OK;
+}

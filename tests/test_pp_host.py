@@ -1,0 +1,24 @@
+"""Host side of the prime-power ring entry points (no GPU): parameter checks
+return SF_EINVAL before any device work, and without a CUDA device a valid
+ring fails with SF_ECUDA (no CPU fallback)."""
+import pytest
+
+import paper_2509_01253_gb300 as sf
+
+
+@pytest.mark.parametrize("t,alpha,L,bits", [(2, 5, 1, 50), (9, 2, 1, 50), (11, 2, 1, 50), (3, 1, 1, 50),
+                                            (3, 8, 1, 50), (3, 3, 0, 50), (3, 3, 13, 50), (3, 3, 1, 62),
+                                            (3, 3, 1, 19)])
+def test_pp_ring_parameter_checks(t, alpha, L, bits):
+    with pytest.raises(sf.SafhireError) as e:
+        sf.sf_pp_ring_create(t, alpha, L, bits, 0)
+    assert e.value.status == sf.SF_EINVAL
+
+
+def test_pp_ring_needs_a_device():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(sf.SafhireError) as e:
+        sf.sf_pp_ring_create(3, 7, 2, 50, 0)
+    assert e.value.status == sf.SF_ECUDA
