@@ -144,6 +144,129 @@ __device__ __forceinline__ void pp_reduce_phi(u64 *s, const SfPpRing &R, int i)
     __syncthreads();
 }
 
+// ---- compile-time rings (Table 2: 3^7, 7^4, 5^5, and the smaller test rings)
+// The same stages with t and alpha as template parameters: every span, stride
+// and root index is a constant, the t values of a butterfly stay in
+// registers, and one thread runs one butterfly per stage (M / t threads,
+// rounded up to whole warps).  Twiddle exponents need no reduction: for span
+// len, j < len / t and k < t give (M / len) j k < M.
+template <int T, int ALPHA>
+struct SfPpT {
+    static constexpr int M = T == 3 ? (ALPHA == 2 ? 9 : ALPHA == 3 ? 27 : ALPHA == 4 ? 81 : ALPHA == 5 ? 243 : ALPHA == 6 ? 729 : 2187)
+                           : T == 5 ? (ALPHA == 2 ? 25 : ALPHA == 3 ? 125 : ALPHA == 4 ? 625 : 3125)
+                                    : (ALPHA == 2 ? 49 : ALPHA == 3 ? 343 : 2401);
+    static constexpr int BFLY = M / T;
+    static constexpr int THREADS = (BFLY + 31) / 32 * 32;
+};
+
+template <int T, int M, int LEN>
+__device__ __forceinline__ void ppt_stage_fwd(u64 *s, const u64 *w, const u64 *wp, u64 q, u64 one_p)
+{
+    constexpr int THIRD = LEN / T, STRIDE = M / LEN, ROOT = M / T;
+    const int idx = threadIdx.x;
+    if (idx < M / T) {
+        const int blk = idx / THIRD, j = idx - blk * THIRD;
+        const int base = blk * LEN + j;
+        u64 x[T];
+#pragma unroll
+        for (int r = 0; r < T; ++r) x[r] = s[base + r * THIRD];
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+            u64 acc = x[0];
+#pragma unroll
+            for (int r = 1; r < T; ++r) {
+                const int e = ROOT * ((r * k) % T);
+                acc += sf_mul_shoup_lazy(x[r], __ldg(w + e), __ldg(wp + e), q);
+            }
+            u64 y = sf_reduce(acc, q, one_p);
+            if (k) {
+                const int e = STRIDE * j * k;
+                if (e) y = sf_mul_shoup(y, __ldg(w + e), __ldg(wp + e), q);
+            }
+            s[base + k * THIRD] = y;
+        }
+    }
+}
+
+template <int T, int M, int LEN>
+__device__ __forceinline__ void ppt_stage_inv(u64 *s, const u64 *iw, const u64 *iwp, u64 q, u64 one_p)
+{
+    constexpr int THIRD = LEN / T, STRIDE = M / LEN, ROOT = M / T;
+    const int idx = threadIdx.x;
+    if (idx < M / T) {
+        const int blk = idx / THIRD, j = idx - blk * THIRD;
+        const int base = blk * LEN + j;
+        u64 x[T];
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+            const u64 v = s[base + k * THIRD];
+            const int e = STRIDE * j * k;
+            x[k] = e ? sf_mul_shoup(v, __ldg(iw + e), __ldg(iwp + e), q) : v;
+        }
+#pragma unroll
+        for (int r = 0; r < T; ++r) {
+            u64 acc = x[0];
+#pragma unroll
+            for (int k = 1; k < T; ++k) {
+                const int e = ROOT * ((r * k) % T);
+                acc += sf_mul_shoup_lazy(x[k], __ldg(iw + e), __ldg(iwp + e), q);
+            }
+            s[base + r * THIRD] = sf_reduce(acc, q, one_p);
+        }
+    }
+}
+
+template <int T, int M, int LEN>
+__device__ __forceinline__ void ppt_forward(u64 *s, const u64 *w, const u64 *wp, u64 q, u64 one_p)
+{
+    ppt_stage_fwd<T, M, LEN>(s, w, wp, q, one_p);
+    __syncthreads();
+    if constexpr (LEN / T >= T) ppt_forward<T, M, LEN / T>(s, w, wp, q, one_p);
+}
+
+template <int T, int M, int LEN>
+__device__ __forceinline__ void ppt_inverse(u64 *s, const u64 *iw, const u64 *iwp, u64 q, u64 one_p)
+{
+    ppt_stage_inv<T, M, LEN>(s, iw, iwp, q, one_p);
+    __syncthreads();
+    if constexpr (LEN * T <= M) ppt_inverse<T, M, LEN * T>(s, iw, iwp, q, one_p);
+}
+
+template <int T, int ALPHA>
+__global__ void __launch_bounds__(SfPpT<T, ALPHA>::THREADS) k_ppt_ntt(SfPpRing R, const u64 *in, u64 *out, int inverse)
+{
+    constexpr int M = SfPpT<T, ALPHA>::M, NT = SfPpT<T, ALPHA>::THREADS;
+    __shared__ u64 s[M];
+    const int i = blockIdx.x;
+    const SfPpMod &P = R.mod[i];
+    const size_t off = ((size_t)blockIdx.y * R.L + i) * M;
+    for (int e = threadIdx.x; e < M; e += NT) s[e] = in[off + e];
+    __syncthreads();
+    if (inverse) {
+        ppt_inverse<T, M, T>(s, R.iw + (size_t)i * M, R.iw_p + (size_t)i * M, P.q, P.one_p);
+        for (int e = threadIdx.x; e < M; e += NT) out[off + e] = sf_mul_shoup(s[e], P.minv, P.minv_p, P.q);
+    } else {
+        ppt_forward<T, M, M>(s, R.w + (size_t)i * M, R.w_p + (size_t)i * M, P.q, P.one_p);
+        for (int e = threadIdx.x; e < M; e += NT) out[off + e] = s[e];
+    }
+}
+
+// runs the statements with constexpr T, ALPHA when (t, alpha) is one of the
+// compiled rings; `done` tells whether it did
+#define SF_PPT_DISPATCH(t, alpha, done, ...)                                                 \
+    do {                                                                                       \
+        done = true;                                                                           \
+        if ((t) == 3 && (alpha) == 7) { constexpr int T = 3, ALPHA = 7; __VA_ARGS__ }          \
+        else if ((t) == 3 && (alpha) == 4) { constexpr int T = 3, ALPHA = 4; __VA_ARGS__ }     \
+        else if ((t) == 3 && (alpha) == 3) { constexpr int T = 3, ALPHA = 3; __VA_ARGS__ }     \
+        else if ((t) == 5 && (alpha) == 5) { constexpr int T = 5, ALPHA = 5; __VA_ARGS__ }     \
+        else if ((t) == 5 && (alpha) == 3) { constexpr int T = 5, ALPHA = 3; __VA_ARGS__ }     \
+        else if ((t) == 5 && (alpha) == 2) { constexpr int T = 5, ALPHA = 2; __VA_ARGS__ }     \
+        else if ((t) == 7 && (alpha) == 4) { constexpr int T = 7, ALPHA = 4; __VA_ARGS__ }     \
+        else if ((t) == 7 && (alpha) == 2) { constexpr int T = 7, ALPHA = 2; __VA_ARGS__ }     \
+        else done = false;                                                                     \
+    } while (0)
+
 // Batched length-M transform: grid (L, count); [count][L][M] in and out.
 __global__ void __launch_bounds__(SF_PP_THREADS) k_pp_ntt(SfPpRing R, const u64 *in, u64 *out, int inverse)
 {
@@ -327,7 +450,13 @@ extern "C" sf_status sf_pp_ntt(sf_pp_ring *r, const uint64_t *d_in, uint64_t *d_
     SF_TRY(pp_check(r, d_in, d_out, count));
     if (inverse != 0 && inverse != 1) return sf_set_error(SF_EINVAL, "sf_pp_ntt: inverse must be 0 or 1");
     const SfPpRing &R = r->R;
-    k_pp_ntt<<<dim3(R.L, count), SF_PP_THREADS, sizeof(u64) * R.M, (cudaStream_t)stream>>>(R, d_in, d_out, inverse);
+    bool done = false;
+    SF_PPT_DISPATCH(R.t, R.alpha, done, {
+        k_ppt_ntt<T, ALPHA><<<dim3(R.L, count), SfPpT<T, ALPHA>::THREADS, 0, (cudaStream_t)stream>>>(R, d_in, d_out,
+                                                                                                    inverse);
+    });
+    if (!done)
+        k_pp_ntt<<<dim3(R.L, count), SF_PP_THREADS, sizeof(u64) * R.M, (cudaStream_t)stream>>>(R, d_in, d_out, inverse);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
 }

@@ -12,7 +12,8 @@ from oracle import primepower as pp
 
 pytestmark = pytest.mark.gpu
 
-CASES = [(3, 3, 2), (3, 4, 3), (5, 2, 2), (7, 2, 2), (5, 3, 1), (3, 7, 2), (7, 4, 1), (5, 5, 1)]
+# rings with a compile-time transform and, (3, 5) and (7, 3), rings on the generic one
+CASES = [(3, 3, 2), (3, 4, 3), (5, 2, 2), (7, 2, 2), (5, 3, 1), (3, 7, 2), (7, 4, 1), (5, 5, 1), (3, 5, 2), (7, 3, 1)]
 
 
 def _ring(t, alpha, L):
