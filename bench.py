@@ -452,8 +452,9 @@ def pp_ntt_record(local: int, flush, t: int = 3, alpha: int = 7, L: int = 5, cou
     """Batched length-M transform of the paper's prime-power ring M = 3^7
     (Table 2; sf_pp_ntt, one block per limb, radix-3 stages in shared memory)
     over count x L limbs: algorithmic GB/s (each limb read and written once)
-    and radix-3 butterflies/s (M/3 per stage, alpha stages, each 6 modular
-    products counted as 6)."""
+    and modular products/s: M/t butterflies per stage, alpha stages, each
+    with its t - 1 twiddle products and the t-point DFT's products (2 for
+    t = 3, t (t - 1) otherwise)."""
     import torch
     import paper_2509_01253_gb300 as sf
     r = sf.sf_pp_ring_create(t, alpha, L, 50, local)
@@ -475,7 +476,7 @@ def pp_ntt_record(local: int, flush, t: int = 3, alpha: int = 7, L: int = 5, cou
         torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev) / reps
         nbytes = 2 * count * L * M * 8
-        mods = count * L * (M // t) * alpha * (t - 1) * t
+        mods = count * L * (M // t) * alpha * ((2 if t == 3 else t * (t - 1)) + t - 1)
         hbm_peak, kind = load_peaks()
         gbs = nbytes / (ms * 1e-3) / 1e9
         return {"what": f"forward length-{M} transform (M = {t}^{alpha}, N = {info['N']}) of {count} x {L} limbs "

@@ -32,6 +32,8 @@ struct SfPpMod {
     u64 q, one_p;            // modulus, floor(2^64 / q)
     u64 qinv_neg, r2;        // -q^-1 mod 2^64, 2^128 mod q (Montgomery products of two residues)
     u64 minv, minv_p;        // M^-1 mod q (Shoup)
+    u64 h2, h2_p;            // 2^-1 mod q (Shoup)
+    u64 c3, c3_p;            // t = 3: (zeta - zeta^2) / 2, zeta = omega^(M/3) (Shoup)
 };
 
 struct SfPpRing {
@@ -159,8 +161,23 @@ struct SfPpT {
     static constexpr int THREADS = (BFLY + 31) / 32 * 32;
 };
 
+// the 3-point DFT with two products: with zeta + zeta^2 = -1,
+// y1, y2 = x0 - (x1 + x2) / 2 +- c (x1 - x2), c = (zeta - zeta^2) / 2
+// (the inverse transform's root zeta^-1 flips the sign of c)
+template <bool INV>
+__device__ __forceinline__ void ppt_dft3(u64 &x0, u64 &x1, u64 &x2, const SfPpMod &P)
+{
+    const u64 q = P.q;
+    const u64 sm = sf_add(x1, x2, q), df = sf_sub(x1, x2, q);
+    const u64 u = sf_sub(x0, sf_mul_shoup(sm, P.h2, P.h2_p, q), q);
+    const u64 v = sf_mul_shoup(df, P.c3, P.c3_p, q);
+    x0 = sf_add(x0, sm, q);
+    x1 = INV ? sf_sub(u, v, q) : sf_add(u, v, q);
+    x2 = INV ? sf_add(u, v, q) : sf_sub(u, v, q);
+}
+
 template <int T, int M, int LEN>
-__device__ __forceinline__ void ppt_stage_fwd(u64 *s, const u64 *w, const u64 *wp, u64 q, u64 one_p)
+__device__ __forceinline__ void ppt_stage_fwd(u64 *s, const u64 *w, const u64 *wp, u64 q, u64 one_p, const SfPpMod &P)
 {
     constexpr int THIRD = LEN / T, STRIDE = M / LEN, ROOT = M / T;
     const int idx = threadIdx.x;
@@ -170,6 +187,15 @@ __device__ __forceinline__ void ppt_stage_fwd(u64 *s, const u64 *w, const u64 *w
         u64 x[T];
 #pragma unroll
         for (int r = 0; r < T; ++r) x[r] = s[base + r * THIRD];
+        if constexpr (T == 3) {
+            ppt_dft3<false>(x[0], x[1], x[2], P);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int e = STRIDE * j * k;
+                s[base + k * THIRD] = e ? sf_mul_shoup(x[k], __ldg(w + e), __ldg(wp + e), q) : x[k];
+            }
+            return;
+        }
 #pragma unroll
         for (int k = 0; k < T; ++k) {
             u64 acc = x[0];
@@ -189,7 +215,7 @@ __device__ __forceinline__ void ppt_stage_fwd(u64 *s, const u64 *w, const u64 *w
 }
 
 template <int T, int M, int LEN>
-__device__ __forceinline__ void ppt_stage_inv(u64 *s, const u64 *iw, const u64 *iwp, u64 q, u64 one_p)
+__device__ __forceinline__ void ppt_stage_inv(u64 *s, const u64 *iw, const u64 *iwp, u64 q, u64 one_p, const SfPpMod &P)
 {
     constexpr int THIRD = LEN / T, STRIDE = M / LEN, ROOT = M / T;
     const int idx = threadIdx.x;
@@ -202,6 +228,12 @@ __device__ __forceinline__ void ppt_stage_inv(u64 *s, const u64 *iw, const u64 *
             const u64 v = s[base + k * THIRD];
             const int e = STRIDE * j * k;
             x[k] = e ? sf_mul_shoup(v, __ldg(iw + e), __ldg(iwp + e), q) : v;
+        }
+        if constexpr (T == 3) {
+            ppt_dft3<true>(x[0], x[1], x[2], P);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) s[base + r * THIRD] = x[r];
+            return;
         }
 #pragma unroll
         for (int r = 0; r < T; ++r) {
@@ -217,19 +249,19 @@ __device__ __forceinline__ void ppt_stage_inv(u64 *s, const u64 *iw, const u64 *
 }
 
 template <int T, int M, int LEN>
-__device__ __forceinline__ void ppt_forward(u64 *s, const u64 *w, const u64 *wp, u64 q, u64 one_p)
+__device__ __forceinline__ void ppt_forward(u64 *s, const u64 *w, const u64 *wp, u64 q, u64 one_p, const SfPpMod &P)
 {
-    ppt_stage_fwd<T, M, LEN>(s, w, wp, q, one_p);
+    ppt_stage_fwd<T, M, LEN>(s, w, wp, q, one_p, P);
     __syncthreads();
-    if constexpr (LEN / T >= T) ppt_forward<T, M, LEN / T>(s, w, wp, q, one_p);
+    if constexpr (LEN / T >= T) ppt_forward<T, M, LEN / T>(s, w, wp, q, one_p, P);
 }
 
 template <int T, int M, int LEN>
-__device__ __forceinline__ void ppt_inverse(u64 *s, const u64 *iw, const u64 *iwp, u64 q, u64 one_p)
+__device__ __forceinline__ void ppt_inverse(u64 *s, const u64 *iw, const u64 *iwp, u64 q, u64 one_p, const SfPpMod &P)
 {
-    ppt_stage_inv<T, M, LEN>(s, iw, iwp, q, one_p);
+    ppt_stage_inv<T, M, LEN>(s, iw, iwp, q, one_p, P);
     __syncthreads();
-    if constexpr (LEN * T <= M) ppt_inverse<T, M, LEN * T>(s, iw, iwp, q, one_p);
+    if constexpr (LEN * T <= M) ppt_inverse<T, M, LEN * T>(s, iw, iwp, q, one_p, P);
 }
 
 template <int T, int ALPHA>
@@ -243,10 +275,10 @@ __global__ void __launch_bounds__(SfPpT<T, ALPHA>::THREADS) k_ppt_ntt(SfPpRing R
     for (int e = threadIdx.x; e < M; e += NT) s[e] = in[off + e];
     __syncthreads();
     if (inverse) {
-        ppt_inverse<T, M, T>(s, R.iw + (size_t)i * M, R.iw_p + (size_t)i * M, P.q, P.one_p);
+        ppt_inverse<T, M, T>(s, R.iw + (size_t)i * M, R.iw_p + (size_t)i * M, P.q, P.one_p, P);
         for (int e = threadIdx.x; e < M; e += NT) out[off + e] = sf_mul_shoup(s[e], P.minv, P.minv_p, P.q);
     } else {
-        ppt_forward<T, M, M>(s, R.w + (size_t)i * M, R.w_p + (size_t)i * M, P.q, P.one_p);
+        ppt_forward<T, M, M>(s, R.w + (size_t)i * M, R.w_p + (size_t)i * M, P.q, P.one_p, P);
         for (int e = threadIdx.x; e < M; e += NT) out[off + e] = s[e];
     }
 }
@@ -397,6 +429,12 @@ extern "C" sf_status sf_pp_ring_create(int32_t t, int32_t alpha, int32_t L, int3
         P.r2 = sf_host_mulmod(r1, r1, q);
         P.minv = sf_host_invmod((u64)R.M % q, q);
         P.minv_p = sf_shoup_companion(P.minv, q);
+        P.h2 = sf_host_invmod(2, q);
+        P.h2_p = sf_shoup_companion(P.h2, q);
+        // zeta = omega^(M/3): c = (zeta - zeta^2) / 2 (used at t = 3 only)
+        const u64 z = sf_host_powmod(w, (u64)(R.M / t), q), z2 = sf_host_mulmod(z, z, q);
+        P.c3 = sf_host_mulmod((z + q - z2) % q, P.h2, q);
+        P.c3_p = sf_shoup_companion(P.c3, q);
     }
     // the product kernel holds two length-M vectors (up to 64 KB of shared memory)
     if (cudaSetDevice(device) != cudaSuccess ||
