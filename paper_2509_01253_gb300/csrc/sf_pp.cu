@@ -15,10 +15,12 @@
 //
 // One block per (polynomial, limb) holds its length-M vector in shared memory
 // (at most 3125 words for Table 2's rings).  Each radix-t butterfly runs the
-// t-point DFT with t products per output, summed lazily below 2 t q, then one
-// reduction; twiddles and t-th roots come from a per-limb table of omega^e.
+// t-point DFT with t - 1 products per output, summed lazily below 2 t q, then
+// one reduction (at t = 3 the DFT takes two products in all, ppt_dft3);
+// twiddles and t-th roots come from a per-limb table of omega^e.  Table 2's
+// rings and the small test rings are compiled with t and alpha as constants
+// (k_ppt_ntt); other rings run the generic kernel (k_pp_ntt).
 #include <algorithm>
-#include <cstring>
 #include <vector>
 
 #include "sf_arith.cuh"
