@@ -20,6 +20,10 @@ definitions literally:
 * The dual basis Omega_i^* of the power basis X^i for the pairing
   <P, Q> = Tr(P Q-bar), Q-bar(X) = Q(X^(M-1)), so that coefficient i of m is
   Tr(m Omega_i^*-bar) (Sec. 4.4), and Lemma 1's partial-trace rows.
+* RnsRlwe: RLWE over the same ring modulo Q = prod q_i (q_i = 1 mod M), with
+  encryption, decryption, key switching after an automorphism by the RNS
+  limbs of tau_h(a), and the homomorphic tower trace (Sec. 2.1-2.3 on
+  ciphertexts).
 """
 from __future__ import annotations
 
@@ -134,42 +138,41 @@ class Ring:
                 return g
         raise ValueError("no primitive root")
 
+    def tower_steps(self, gamma: int = 0) -> list:
+        """The steps (h, length) of the tower of Sec. 2.3 (t odd): each maps x
+        to sum_{k < length} tau_h^k(x).  Tr_{K_(i+1) / K_i} for i = alpha - 1
+        .. max(gamma, 1): the subgroup {d = 1 mod t^i} / {d = 1 mod t^(i+1)}
+        is cyclic of order t, generated by 1 + t^i.  At gamma = 0 then
+        Tr_{K_1 / K_0}: (Z / tZ)^* is cyclic of order t - 1, generated by a
+        primitive root g mod M, taken one prime factor l of t - 1 at a time
+        (the sum over a cyclic group of order n factors as
+        prod_i sum_{j < l_i} g^(j n / (l_1 ... l_i))): h = g^rest acts on K_1
+        with order l."""
+        t, M = self.t, self.M
+        steps = [((1 + t ** i) % M, t) for i in range(self.alpha - 1, max(gamma, 1) - 1, -1)]
+        if gamma >= 1:
+            return steps
+        g = self.primitive_root()
+        rest = t - 1
+        for l in prime_factors(t - 1):
+            rest //= l
+            steps.append((pow(g, rest, M), l))
+        return steps
+
     def tower_trace(self, a, gamma: int = 0, counter: list | None = None) -> list:
         """The full trace by the tower of Sec. 2.3 (t odd), or, with gamma >= 1,
         only Tr_{K / K_gamma} (the levels the server still computes when the
         client supplied Tr_{K_gamma / K_0}).  counter[0] is incremented once
         per automorphism (one key switch each on ciphertexts)."""
-        t, M = self.t, self.M
-
-        def step(x, h, length):
-            # sum_{k < length} tau_h^k(x), with length - 1 automorphisms
+        x = list(a)
+        for h, length in self.tower_steps(gamma):
             acc, cur = list(x), list(x)
             for _ in range(length - 1):
                 cur = self.automorphism(cur, h)
                 if counter is not None:
                     counter[0] += 1
                 acc = self.add(acc, cur)
-            return acc
-
-        x = list(a)
-        # Tr_{K_{i+1} / K_i} for i = alpha - 1 .. max(gamma, 1): the subgroup
-        # {d = 1 mod t^i} / {d = 1 mod t^(i+1)} is cyclic of order t,
-        # generated by 1 + t^i
-        for i in range(self.alpha - 1, max(gamma, 1) - 1, -1):
-            x = step(x, (1 + t ** i) % M, t)
-        if gamma >= 1:
-            return x
-        # Tr_{K_1 / K_0}: (Z / tZ)^* is cyclic of order t - 1, generated by a
-        # primitive root g mod M; it is taken one prime factor l of t - 1 at a
-        # time
-        g = self.primitive_root()
-        rest = t - 1
-        for l in prime_factors(t - 1):
-            # (the sum over a cyclic group of order n factors as
-            # prod_i sum_{j < l_i} g^(j n / (l_1 ... l_i))): h = g^rest acts
-            # on K_1 with order l
-            rest //= l
-            x = step(x, pow(g, rest, M), l)
+            x = acc
         return x
 
     def tower_ks_count(self, gamma: int = 0) -> int:
@@ -217,3 +220,107 @@ def _invert(A):
                 f = M[r][col]
                 M[r] = [a - f * b for a, b in zip(M[r], M[col])]
     return [row[n:] for row in M]
+
+
+class RnsRlwe:
+    """RLWE over K = Q[X]/Phi_M modulo Q = prod q_i (Sec. 2.1 at general t),
+    residues per limb: a ciphertext is ([a mod q_i]_i, [b mod q_i]_i) with
+    b = a s + m + e, the sign convention of the t = 2 scheme.  Key switching
+    after an automorphism (Sec. 2.2) decomposes tau_h(a) by its RNS limbs,
+    d_i = [tau_h(a)_i (Q/q_i)^-1]_{q_i}, so that tau_h(a) = sum_i d_i Q/q_i
+    (mod Q), and uses one key pair per digit:
+        kb_i = ka_i s + e_i + (Q/q_i) tau_h(s)  (mod Q).
+    Then (a', b') = (-sum_i d_i ka_i, tau_h(b) - sum_i d_i kb_i) decrypts under
+    s to tau_h(m) + tau_h(e) - sum_i d_i e_i.  Every product is the ring's
+    exact product in Z[X]/Phi_M reduced mod q_j.  The uniform a, ka and the
+    noise e are inputs (drawn by the caller)."""
+
+    def __init__(self, ring: Ring, moduli):
+        self.R = ring
+        self.q = [int(x) for x in moduli]
+        self.Q = 1
+        for x in self.q:
+            self.Q *= x
+
+    def _mulq(self, a, b, q):
+        return self.R.mod(self.R.mul(a, b), q)
+
+    def residues(self, poly) -> list:
+        """An integer polynomial (length N) as its L limbs."""
+        return [[int(c) % q for c in poly] for q in self.q]
+
+    def encrypt(self, s, a_res, m, e) -> tuple:
+        """(a, b = a s + m + e) limb by limb; s, m, e integer polynomials."""
+        b = []
+        for j, q in enumerate(self.q):
+            as_ = self._mulq(a_res[j], s, q)
+            b.append([(x + int(mi) + int(ei)) % q for x, mi, ei in zip(as_, m, e)])
+        return ([list(map(int, r)) for r in a_res], b)
+
+    def decrypt(self, s, ct) -> list:
+        """Residues of b - a s per limb (m + noise)."""
+        a, b = ct
+        return [[(y - x) % q for x, y in zip(self._mulq(a[j], s, q), b[j])] for j, q in enumerate(self.q)]
+
+    def centered(self, res) -> list:
+        """CRT of limb residues to the centered integer in (-Q/2, Q/2]."""
+        out = []
+        for k in range(len(res[0])):
+            v = 0
+            for j, q in enumerate(self.q):
+                qh = self.Q // q
+                v += res[j][k] * qh * pow(qh, -1, q)
+            v %= self.Q
+            out.append(v - self.Q if v > self.Q // 2 else v)
+        return out
+
+    def ksk(self, s, h: int, ka, e) -> list:
+        """Key for tau_h: kb[i][j] = ka[i][j] s + e_i + (Q/q_i) tau_h(s) mod q_j;
+        ka[i][j] uniform residues, e[i] integer noise polynomials."""
+        ts = self.R.automorphism(list(s), h)
+        kb = []
+        for i, qi in enumerate(self.q):
+            qh = self.Q // qi
+            row = []
+            for j, q in enumerate(self.q):
+                prod = self._mulq(ka[i][j], s, q)
+                row.append([(p + int(ei) + (qh % q) * x) % q for p, ei, x in zip(prod, e[i], ts)])
+            kb.append(row)
+        return kb
+
+    def keyswitch(self, ct, h: int, ka, kb) -> tuple:
+        """The automorphism tau_h of ct followed by the key switch back to s."""
+        a, b = ct
+        ta = [self.R.mod(self.R.automorphism(a[j], h), q) for j, q in enumerate(self.q)]
+        tb = [self.R.mod(self.R.automorphism(b[j], h), q) for j, q in enumerate(self.q)]
+        n = self.R.N
+        a2 = [[0] * n for _ in self.q]
+        b2 = [list(r) for r in tb]
+        for i, qi in enumerate(self.q):
+            w = pow(self.Q // qi, -1, qi)
+            d = [(x * w) % qi for x in ta[i]]          # digit i, an integer polynomial in [0, q_i)
+            for j, q in enumerate(self.q):
+                pa = self._mulq(d, ka[i][j], q)
+                pb = self._mulq(d, kb[i][j], q)
+                a2[j] = [(x - y) % q for x, y in zip(a2[j], pa)]
+                b2[j] = [(x - y) % q for x, y in zip(b2[j], pb)]
+        return (a2, b2)
+
+    def add(self, c1, c2) -> tuple:
+        return tuple([[(x + y) % q for x, y in zip(u[j], v[j])] for j, q in enumerate(self.q)]
+                     for u, v in zip(c1, c2))
+
+    def hom_trace(self, ct, gamma: int, keys: dict, counter: list | None = None) -> tuple:
+        """Tr_{K / K_gamma} (gamma >= 1) or the full trace (gamma = 0) on a
+        ciphertext, along the tower's steps: x <- sum_{k < length} tau_h^k(x),
+        every tau_h followed by its key switch; keys[h] = (ka, kb)."""
+        x = ct
+        for h, length in self.R.tower_steps(gamma):
+            acc, cur = x, x
+            for _ in range(length - 1):
+                cur = self.keyswitch(cur, h, *keys[h])
+                if counter is not None:
+                    counter[0] += 1
+                acc = self.add(acc, cur)
+            x = acc
+        return x

@@ -126,3 +126,103 @@ def test_lemma1_partial_trace_rows(t, alpha, gamma):
             row = R.add(row, R.mul(R.automorphism(P, d), R.automorphism(obar, d)))
         out = R.tower_trace(row, gamma)
         assert out[0] == P[i] and all(v == 0 for v in out[1:]), i
+
+
+# ---------------------------------------------------------------- RLWE ----
+
+def _is_prime(n: int) -> bool:
+    if n < 2:
+        return False
+    for p in (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37):
+        if n % p == 0:
+            return n == p
+    d, r = n - 1, 0
+    while d % 2 == 0:
+        d //= 2
+        r += 1
+    for a in (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37):
+        x = pow(a, d, n)
+        if x in (1, n - 1):
+            continue
+        for _ in range(r - 1):
+            x = x * x % n
+            if x == n - 1:
+                break
+        else:
+            return False
+    return True
+
+
+def _primes_1_mod(M: int, bits: int, count: int) -> list:
+    out, k = [], ((1 << bits) - 2) // M
+    while len(out) < count:
+        if _is_prime(k * M + 1):
+            out.append(k * M + 1)
+        k -= 1
+    return out
+
+
+def _rlwe_setup(t, alpha, L, seed):
+    R = pp.Ring(t, alpha)
+    E = pp.RnsRlwe(R, _primes_1_mod(R.M, 30, L))
+    rng = random.Random(seed)
+    s = [rng.choice((-1, 0, 1)) for _ in range(R.N)]
+    return R, E, rng, s
+
+
+@pytest.mark.parametrize("t,alpha", [(3, 2), (3, 3), (5, 2), (7, 2)])
+def test_rlwe_encrypt_decrypt_round_trip(t, alpha):
+    """b - a s = m + e exactly (CRT of the limbs, centered)."""
+    R, E, rng, s = _rlwe_setup(t, alpha, 3, 5 + t)
+    m = [rng.randrange(-2 ** 40, 2 ** 40) for _ in range(R.N)]
+    e = [rng.randrange(-8, 9) for _ in range(R.N)]
+    a = [[rng.randrange(q) for _ in range(R.N)] for q in E.q]
+    ct = E.encrypt(s, a, m, e)
+    assert E.centered(E.decrypt(s, ct)) == [x + y for x, y in zip(m, e)]
+
+
+@pytest.mark.parametrize("t,alpha,h", [(3, 2, 4), (3, 3, 10), (5, 2, 6), (7, 2, 3)])
+def test_rlwe_keyswitch_is_the_automorphism(t, alpha, h):
+    """With noiseless keys the key-switched tau_h(ct) decrypts to exactly
+    tau_h(m + e); with noisy keys the extra term is -sum_i d_i e_i, bounded
+    by sum_i q_i ||e_i||_1 times the ring's expansion."""
+    R, E, rng, s = _rlwe_setup(t, alpha, 2, 17 + h)
+    m = [rng.randrange(-2 ** 30, 2 ** 30) for _ in range(R.N)]
+    e = [rng.randrange(-8, 9) for _ in range(R.N)]
+    a = [[rng.randrange(q) for _ in range(R.N)] for q in E.q]
+    ct = E.encrypt(s, a, m, e)
+    ka = [[[rng.randrange(q) for _ in range(R.N)] for q in E.q] for _ in E.q]
+    zero = [[0] * R.N for _ in E.q]
+    kb = E.ksk(s, h, ka, zero)
+    out = E.keyswitch(ct, h, ka, kb)
+    want = R.automorphism([x + y for x, y in zip(m, e)], h)
+    assert E.centered(E.decrypt(s, out)) == want
+    ek = [[rng.randrange(-4, 5) for _ in range(R.N)] for _ in E.q]
+    out = E.keyswitch(ct, h, ka, E.ksk(s, h, ka, ek))
+    diff = [x - y for x, y in zip(E.centered(E.decrypt(s, out)), want)]
+    bound = sum(q * sum(abs(v) for v in ek[i]) for i, q in enumerate(E.q)) * (R.t - 1)
+    assert any(diff) and max(abs(v) for v in diff) <= bound
+
+
+@pytest.mark.parametrize("t,alpha", [(3, 2), (3, 3), (5, 2), (7, 2)])
+def test_rlwe_hom_trace_is_the_trace(t, alpha):
+    """With noiseless keys the homomorphic tower trace decrypts to exactly
+    Tr_{K/K_gamma}(m + e) by definition (the sum over Gal(K/K_gamma)), using
+    (alpha - max(gamma,1))(t-1) (+ the K_1/K_0 steps) key switches."""
+    R, E, rng, s = _rlwe_setup(t, alpha, 2, 31 + t)
+    m = [rng.randrange(-2 ** 20, 2 ** 20) for _ in range(R.N)]
+    e = [rng.randrange(-8, 9) for _ in range(R.N)]
+    a = [[rng.randrange(q) for _ in range(R.N)] for q in E.q]
+    ct = E.encrypt(s, a, m, e)
+    keys = {}
+    for gamma in range(0, alpha + 1):
+        for h, _ in R.tower_steps(gamma):
+            if h not in keys:
+                ka = [[[rng.randrange(q) for _ in range(R.N)] for q in E.q] for _ in E.q]
+                keys[h] = (ka, E.ksk(s, h, ka, [[0] * R.N for _ in E.q]))
+        c = [0]
+        out = E.hom_trace(ct, gamma, keys, c)
+        assert c[0] == R.tower_ks_count(gamma)
+        me = [x + y for x, y in zip(m, e)]
+        want = R.partial_trace(me, gamma) if gamma >= 1 else R.trace(me)
+        assert E.centered(E.decrypt(s, out)) == want, gamma
