@@ -524,6 +524,39 @@ sf_status sf_pp_automorphism(sf_pp_ring *ring, const uint64_t *d_in, uint64_t *d
 sf_status sf_pp_trace(sf_pp_ring *ring, const uint64_t *d_in, uint64_t *d_out, int32_t count, int32_t gamma,
                       int32_t *n_automorphisms, void *stream);
 
+/* RLWE over the same ring modulo Q = prod q_i (Sec. 2.1 at general t).  A
+ * ciphertext is uint64[2][L][N] residues (a, b = a s + m + e), arrays of them
+ * uint64[count][2][L][N].  The secret s, messages m and noise e are int64
+ * coefficient arrays (s: [N], m and e: [count][N]); the uniform masks are
+ * inputs too (drawn by the caller).  These calls use a grow-only work buffer
+ * of the ring.  Errors: SF_EINVAL for null or aliasing buffers, SF_ECUDA. */
+sf_status sf_pp_encrypt(sf_pp_ring *ring, const int64_t *d_s, const uint64_t *d_a, const int64_t *d_m,
+                        const int64_t *d_e, uint64_t *d_ct, int32_t count, void *stream);
+/* d_out = residues of b - a s, uint64[count][L][N]. */
+sf_status sf_pp_decrypt(sf_pp_ring *ring, const int64_t *d_s, const uint64_t *d_ct, uint64_t *d_out, int32_t count,
+                        void *stream);
+
+/* Key switching after tau_h (Sec. 2.2) by the RNS limbs of tau_h(a): digit i
+ * is d_i = [tau_h(a)_i (Q/q_i)^-1]_{q_i}, so tau_h(a) = sum_i d_i Q/q_i (mod Q).
+ * sf_pp_ksk: from the uniform d_ka uint64[L digits][L limbs][N] and the noise
+ * d_e int64[L][N], d_kb[i] = ka_i s + e_i + (Q/q_i) tau_h(s) (mod Q).
+ * sf_pp_keyswitch: d_out[c] = (-sum_i d_i ka_i, tau_h(b) - sum_i d_i kb_i),
+ * which decrypts under s to tau_h(m + e) - sum_i d_i e_i; d_out must not
+ * alias d_ct. */
+sf_status sf_pp_ksk(sf_pp_ring *ring, const int64_t *d_s, int32_t h, const uint64_t *d_ka, const int64_t *d_e,
+                    uint64_t *d_kb, void *stream);
+sf_status sf_pp_keyswitch(sf_pp_ring *ring, const uint64_t *d_ct, uint64_t *d_out, int32_t count, int32_t h,
+                          const uint64_t *d_ka, const uint64_t *d_kb, void *stream);
+
+/* The trace of sf_pp_trace on ciphertexts: the same tower steps, every
+ * automorphism followed by its key switch, with keys (hs[x], d_kas[x],
+ * d_kbs[x]) for x < n_keys (host arrays of device pointers).  *n_keyswitches
+ * (may be NULL) receives the key switches run.  Errors: SF_EINVAL (gamma
+ * outside [0, alpha], or no key for an automorphism of the tower), SF_ECUDA. */
+sf_status sf_pp_hom_trace(sf_pp_ring *ring, const uint64_t *d_ct, uint64_t *d_out, int32_t count, int32_t gamma,
+                          int32_t n_keys, const int32_t *hs, const uint64_t *const *d_kas,
+                          const uint64_t *const *d_kbs, int32_t *n_keyswitches, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -105,6 +105,11 @@ _SIGS = {
     "sf_pp_mul": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
     "sf_pp_automorphism": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp]),
     "sf_pp_trace": (_i32, [_vp, _vp, _vp, _i32, _i32, ctypes.POINTER(_i32), _vp]),
+    "sf_pp_encrypt": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp]),
+    "sf_pp_decrypt": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
+    "sf_pp_ksk": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp]),
+    "sf_pp_keyswitch": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp, _vp]),
+    "sf_pp_hom_trace": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32), _vp]),
 }
 
 _lib = None
@@ -503,4 +508,32 @@ def sf_pp_trace(r, d_in, d_out, count: int, gamma: int, stream=None) -> int:
     """Returns the number of automorphisms applied."""
     n = _i32()
     _check(lib().sf_pp_trace(r, _ptr(d_in), _ptr(d_out), count, gamma, ctypes.byref(n), _stream(stream)))
+    return n.value
+
+
+def sf_pp_encrypt(r, d_s, d_a, d_m, d_e, d_ct, count: int, stream=None):
+    _check(lib().sf_pp_encrypt(r, _ptr(d_s), _ptr(d_a), _ptr(d_m), _ptr(d_e), _ptr(d_ct), count, _stream(stream)))
+
+
+def sf_pp_decrypt(r, d_s, d_ct, d_out, count: int, stream=None):
+    _check(lib().sf_pp_decrypt(r, _ptr(d_s), _ptr(d_ct), _ptr(d_out), count, _stream(stream)))
+
+
+def sf_pp_ksk(r, d_s, h: int, d_ka, d_e, d_kb, stream=None):
+    _check(lib().sf_pp_ksk(r, _ptr(d_s), h, _ptr(d_ka), _ptr(d_e), _ptr(d_kb), _stream(stream)))
+
+
+def sf_pp_keyswitch(r, d_ct, d_out, count: int, h: int, d_ka, d_kb, stream=None):
+    _check(lib().sf_pp_keyswitch(r, _ptr(d_ct), _ptr(d_out), count, h, _ptr(d_ka), _ptr(d_kb), _stream(stream)))
+
+
+def sf_pp_hom_trace(r, d_ct, d_out, count: int, gamma: int, keys: dict, stream=None) -> int:
+    """keys: {h: (d_ka, d_kb)}.  Returns the number of key switches run."""
+    hs = sorted(keys)
+    H = (_i32 * max(1, len(hs)))(*hs)
+    KA = (_vp * max(1, len(hs)))(*[_ptr(keys[h][0]) for h in hs])
+    KB = (_vp * max(1, len(hs)))(*[_ptr(keys[h][1]) for h in hs])
+    n = _i32()
+    _check(lib().sf_pp_hom_trace(r, _ptr(d_ct), _ptr(d_out), count, gamma, len(hs), ctypes.cast(H, _vp),
+                                 ctypes.cast(KA, _vp), ctypes.cast(KB, _vp), ctypes.byref(n), _stream(stream)))
     return n.value

@@ -36,6 +36,7 @@ struct SfPpMod {
     u64 minv, minv_p;        // M^-1 mod q (Shoup)
     u64 h2, h2_p;            // 2^-1 mod q (Shoup)
     u64 c3, c3_p;            // t = 3: (zeta - zeta^2) / 2, zeta = omega^(M/3) (Shoup)
+    u64 qh_inv, qh_inv_p;    // (Q / q_i)^-1 mod q_i (Shoup): the RNS digits of key switching
 };
 
 struct SfPpRing {
@@ -44,6 +45,7 @@ struct SfPpRing {
     const u64 *w_p;          // [L][M] Shoup companions
     const u64 *iw;           // [L][M] omega_i^-e
     const u64 *iw_p;
+    const u64 *qhat;         // [L][L][2]: (Q / q_i) mod q_j and its Shoup companion
     SfPpMod mod[SF_MAX_MODULI];
 };
 
@@ -54,6 +56,8 @@ struct sf_pp_ring {
     u64 *d_tables = nullptr;     // w, w_p, iw, iw_p
     u64 *d_scratch = nullptr;    // trace work buffers
     size_t scratch_words = 0;
+    u64 *d_ks = nullptr;         // key-switch and ciphertext work buffers
+    size_t ks_words = 0;
 };
 
 // a * b mod q for two residues below q (two Montgomery reductions: a b 2^-64,
@@ -316,15 +320,17 @@ __global__ void __launch_bounds__(SF_PP_THREADS) k_pp_ntt(SfPpRing R, const u64 
 }
 
 // Products in Z_q[X] / Phi_M: grid (L, count); a, b, out [count][L][N], canonical.
-__global__ void __launch_bounds__(SF_PP_THREADS) k_pp_mul(SfPpRing R, const u64 *a, const u64 *b, u64 *out)
+// b_polys: b holds that many polynomials, polynomial y of a pairs with y mod b_polys
+__global__ void __launch_bounds__(SF_PP_THREADS) k_pp_mul(SfPpRing R, const u64 *a, const u64 *b, u64 *out, int b_polys)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sa = (u64 *)smem_raw, *sb = sa + R.M;
     const int i = blockIdx.x;
     const size_t off = ((size_t)blockIdx.y * R.L + i) * R.N;
+    const size_t offb = ((size_t)(blockIdx.y % b_polys) * R.L + i) * R.N;
     for (int e = threadIdx.x; e < R.M; e += blockDim.x) {
         sa[e] = e < R.N ? a[off + e] : 0;
-        sb[e] = e < R.N ? b[off + e] : 0;
+        sb[e] = e < R.N ? b[offb + e] : 0;
     }
     __syncthreads();
     pp_forward(sa, R, i);
@@ -408,7 +414,7 @@ extern "C" sf_status sf_pp_ring_create(int32_t t, int32_t alpha, int32_t L, int3
         delete r;
         return sf_set_error(SF_EINVAL, "sf_pp_ring_create: not enough primes = 1 mod %lld below 2^%d", M, bits);
     }
-    std::vector<u64> tab((size_t)4 * L * R.M);
+    std::vector<u64> tab((size_t)4 * L * R.M + (size_t)2 * L * L);
     for (int i = 0; i < L; ++i) {
         const u64 q = r->q[i];
         const u64 w = pp_root(q, R.M, t), iw = sf_host_invmod(w, q);
@@ -438,6 +444,20 @@ extern "C" sf_status sf_pp_ring_create(int32_t t, int32_t alpha, int32_t L, int3
         P.c3 = sf_host_mulmod((z + q - z2) % q, P.h2, q);
         P.c3_p = sf_shoup_companion(P.c3, q);
     }
+    // RNS digits: (Q / q_i) mod q_j and (Q / q_i)^-1 mod q_i
+    for (int i = 0; i < L; ++i) {
+        for (int j = 0; j < L; ++j) {
+            u64 v = 1;
+            for (int k = 0; k < L; ++k)
+                if (k != i) v = sf_host_mulmod(v, r->q[k] % r->q[j], r->q[j]);
+            tab[(size_t)4 * L * R.M + 2 * ((size_t)i * L + j)] = v;
+            tab[(size_t)4 * L * R.M + 2 * ((size_t)i * L + j) + 1] = sf_shoup_companion(v, r->q[j]);
+            if (j == i) {
+                R.mod[i].qh_inv = sf_host_invmod(v, r->q[i]);
+                R.mod[i].qh_inv_p = sf_shoup_companion(R.mod[i].qh_inv, r->q[i]);
+            }
+        }
+    }
     // the product kernel holds two length-M vectors (up to 64 KB of shared memory)
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaFuncSetAttribute(k_pp_mul, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -453,6 +473,7 @@ extern "C" sf_status sf_pp_ring_create(int32_t t, int32_t alpha, int32_t L, int3
     R.w_p = R.w + (size_t)L * R.M;
     R.iw = R.w_p + (size_t)L * R.M;
     R.iw_p = R.iw + (size_t)L * R.M;
+    R.qhat = R.iw_p + (size_t)L * R.M;
     *out = r;
     return SF_OK;
 }
@@ -463,6 +484,7 @@ extern "C" void sf_pp_ring_destroy(sf_pp_ring *r)
     cudaSetDevice(r->device);
     if (r->d_tables) cudaFree(r->d_tables);
     if (r->d_scratch) cudaFree(r->d_scratch);
+    if (r->d_ks) cudaFree(r->d_ks);
     delete r;
 }
 
@@ -507,7 +529,8 @@ extern "C" sf_status sf_pp_mul(sf_pp_ring *r, const uint64_t *d_a, const uint64_
     SF_TRY(pp_check(r, d_a, d_b, count));
     if (!d_out) return sf_set_error(SF_EINVAL, "sf_pp_mul: null output");
     const SfPpRing &R = r->R;
-    k_pp_mul<<<dim3(R.L, count), SF_PP_THREADS, 2 * sizeof(u64) * R.M, (cudaStream_t)stream>>>(R, d_a, d_b, d_out);
+    k_pp_mul<<<dim3(R.L, count), SF_PP_THREADS, 2 * sizeof(u64) * R.M, (cudaStream_t)stream>>>(R, d_a, d_b, d_out,
+                                                                                                count);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
 }
@@ -604,5 +627,243 @@ extern "C" sf_status sf_pp_trace(sf_pp_ring *r, const uint64_t *d_in, uint64_t *
         }
     }
     if (n_automorphisms) *n_automorphisms = autos;
+    return SF_OK;
+}
+
+// ------------------------------------------------------ RLWE over Phi_M ----
+// Ciphertexts uint64[count][2][L][N]: part 0 = a, part 1 = b = a s + m + e.
+
+// signed integer polynomials [polys][N] -> residues [polys][L][N]
+__global__ void k_pp_signed(SfPpRing R, const int64_t *v, u64 *out, int polys)
+{
+    const size_t total = (size_t)polys * R.L * R.N;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(k % R.N), j = (int)((k / R.N) % R.L);
+        const size_t p = k / ((size_t)R.N * R.L);
+        const long long x = v[p * R.N + e];
+        const u64 q = R.mod[j].q;
+        const long long r = x % (long long)q;
+        out[k] = r < 0 ? (u64)(r + (long long)q) : (u64)r;
+    }
+}
+
+// ct[c] = (a[c], prod[c] + m[c] + e[c]); m, e already residues [count][L][N]
+__global__ void k_pp_enc_finish(SfPpRing R, const u64 *a, const u64 *prod, const u64 *m, const u64 *e, u64 *ct,
+                                int count)
+{
+    const size_t per = (size_t)R.L * R.N, total = (size_t)count * per;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+        const size_t c = k / per, r = k - c * per;
+        const u64 q = R.mod[(int)(r / R.N)].q;
+        ct[c * 2 * per + r] = a[k];
+        ct[c * 2 * per + per + r] = sf_add(sf_add(prod[k], m[k], q), e[k], q);
+    }
+}
+
+// out = x - y limb-wise; [count][L][N] with x, y at strides sx, sy (words per polynomial)
+__global__ void k_pp_sub(SfPpRing R, const u64 *x, size_t sx, const u64 *y, size_t sy, u64 *out, int count)
+{
+    const size_t per = (size_t)R.L * R.N, total = (size_t)count * per;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+        const size_t c = k / per, r = k - c * per;
+        out[k] = sf_sub(x[c * sx + r], y[c * sy + r], R.mod[(int)(r / R.N)].q);
+    }
+}
+
+// key for tau_h: kb[i][j] = prod[i][j] + e_i + (Q / q_i mod q_j) ts[j] (mod q_j)
+__global__ void k_pp_ksk_finish(SfPpRing R, const u64 *prod, const u64 *e_res, const u64 *ts, u64 *kb)
+{
+    const size_t per = (size_t)R.L * R.N, total = (size_t)R.L * per;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k / per);
+        const size_t r = k - (size_t)i * per;
+        const int j = (int)(r / R.N);
+        const u64 q = R.mod[j].q;
+        const u64 *qh = R.qhat + 2 * ((size_t)i * R.L + j);
+        kb[k] = sf_add(sf_add(prod[k], e_res[k], q), sf_mul_shoup(ts[r], qh[0], qh[1], q), q);
+    }
+}
+
+// RNS digits of ta = tau_h(a): d_i = [ta_i (Q/q_i)^-1]_{q_i} (an integer below
+// q_i), written as residues modulo every q_j: D[i][j][e]
+__global__ void k_pp_digits(SfPpRing R, const u64 *ta, u64 *D)
+{
+    const size_t per = (size_t)R.L * R.N, total = (size_t)R.L * per;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k / per);
+        const size_t r = k - (size_t)i * per;
+        const int j = (int)(r / R.N), e = (int)(r % R.N);
+        const SfPpMod &Pi = R.mod[i];
+        const u64 d = sf_mul_shoup(ta[(size_t)i * R.N + e], Pi.qh_inv, Pi.qh_inv_p, Pi.q);
+        D[k] = j == i ? d : sf_reduce(d, R.mod[j].q, R.mod[j].one_p);
+    }
+}
+
+// out = (-sum_i PA[i], tb - sum_i PB[i]) for one ciphertext
+__global__ void k_pp_ks_combine(SfPpRing R, const u64 *PA, const u64 *PB, const u64 *tb, u64 *out)
+{
+    const size_t per = (size_t)R.L * R.N;
+    for (size_t r = (size_t)blockIdx.x * blockDim.x + threadIdx.x; r < per; r += (size_t)gridDim.x * blockDim.x) {
+        const u64 q = R.mod[(int)(r / R.N)].q;
+        u64 a = 0, b = tb[r];
+        for (int i = 0; i < R.L; ++i) {
+            a = sf_sub(a, PA[(size_t)i * per + r], q);
+            b = sf_sub(b, PB[(size_t)i * per + r], q);
+        }
+        out[r] = a;
+        out[per + r] = b;
+    }
+}
+
+static int pp_grid(size_t total) { return (int)std::min<size_t>((total + 255) / 256, 8192); }
+
+static sf_status pp_ks_buffer(sf_pp_ring *r, size_t words, u64 **out)
+{
+    if (r->ks_words < words) {
+        if (r->d_ks) cudaFree(r->d_ks);
+        r->d_ks = nullptr;
+        r->ks_words = 0;
+        SF_CUDA_TRY(cudaMalloc((void **)&r->d_ks, sizeof(u64) * words));
+        r->ks_words = words;
+    }
+    *out = r->d_ks;
+    return SF_OK;
+}
+
+extern "C" sf_status sf_pp_encrypt(sf_pp_ring *r, const int64_t *d_s, const uint64_t *d_a, const int64_t *d_m,
+                                   const int64_t *d_e, uint64_t *d_ct, int32_t count, void *stream)
+{
+    SF_TRY(pp_check(r, d_s, d_a, count));
+    if (!d_m || !d_e || !d_ct) return sf_set_error(SF_EINVAL, "sf_pp_encrypt: null buffer");
+    const SfPpRing &R = r->R;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t per = (size_t)R.L * R.N;
+    u64 *buf;
+    SF_TRY(pp_ks_buffer(r, per * (1 + 3 * (size_t)count), &buf));
+    u64 *S = buf, *prod = S + per, *mr = prod + per * count, *er = mr + per * count;
+    k_pp_signed<<<pp_grid(per), 256, 0, st>>>(R, d_s, S, 1);
+    k_pp_signed<<<pp_grid(per * count), 256, 0, st>>>(R, d_m, mr, count);
+    k_pp_signed<<<pp_grid(per * count), 256, 0, st>>>(R, d_e, er, count);
+    k_pp_mul<<<dim3(R.L, count), SF_PP_THREADS, 2 * sizeof(u64) * R.M, st>>>(R, d_a, S, prod, 1);
+    k_pp_enc_finish<<<pp_grid(per * count), 256, 0, st>>>(R, d_a, prod, mr, er, d_ct, count);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+extern "C" sf_status sf_pp_decrypt(sf_pp_ring *r, const int64_t *d_s, const uint64_t *d_ct, uint64_t *d_out,
+                                   int32_t count, void *stream)
+{
+    SF_TRY(pp_check(r, d_s, d_ct, count));
+    if (!d_out) return sf_set_error(SF_EINVAL, "sf_pp_decrypt: null output");
+    const SfPpRing &R = r->R;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t per = (size_t)R.L * R.N;
+    u64 *buf;
+    SF_TRY(pp_ks_buffer(r, per * (1 + 2 * (size_t)count), &buf));
+    u64 *S = buf, *a = S + per, *prod = a + per * count;
+    k_pp_signed<<<pp_grid(per), 256, 0, st>>>(R, d_s, S, 1);
+    // gather the a parts, multiply by s, subtract from the b parts
+    for (int c = 0; c < count; ++c)
+        SF_CUDA_TRY(cudaMemcpyAsync(a + per * c, d_ct + 2 * per * c, sizeof(u64) * per, cudaMemcpyDeviceToDevice, st));
+    k_pp_mul<<<dim3(R.L, count), SF_PP_THREADS, 2 * sizeof(u64) * R.M, st>>>(R, a, S, prod, 1);
+    k_pp_sub<<<pp_grid(per * count), 256, 0, st>>>(R, d_ct + per, 2 * per, prod, per, d_out, count);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+extern "C" sf_status sf_pp_ksk(sf_pp_ring *r, const int64_t *d_s, int32_t h, const uint64_t *d_ka, const int64_t *d_e,
+                               uint64_t *d_kb, void *stream)
+{
+    SF_TRY(pp_check(r, d_s, d_ka, 1));
+    if (!d_e || !d_kb) return sf_set_error(SF_EINVAL, "sf_pp_ksk: null buffer");
+    const SfPpRing &R = r->R;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t per = (size_t)R.L * R.N;
+    u64 *buf;
+    SF_TRY(pp_ks_buffer(r, per * (2 + 2 * (size_t)R.L), &buf));
+    u64 *S = buf, *TS = S + per, *er = TS + per, *prod = er + per * R.L;
+    k_pp_signed<<<pp_grid(per), 256, 0, st>>>(R, d_s, S, 1);
+    SF_TRY(pp_auto(r, S, TS, 1, h, st));
+    k_pp_signed<<<pp_grid(per * R.L), 256, 0, st>>>(R, d_e, er, R.L);
+    k_pp_mul<<<dim3(R.L, R.L), SF_PP_THREADS, 2 * sizeof(u64) * R.M, st>>>(R, d_ka, S, prod, 1);
+    k_pp_ksk_finish<<<pp_grid(per * R.L), 256, 0, st>>>(R, prod, er, TS, d_kb);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+// tau_h then the key switch back to s, one ciphertext at a time; `in` and
+// `out` may not alias; work: 2 + 3 L polynomials of L limbs
+static sf_status pp_keyswitch(sf_pp_ring *r, const u64 *in, u64 *out, int count, int h, const u64 *ka, const u64 *kb,
+                              u64 *work, cudaStream_t st)
+{
+    const SfPpRing &R = r->R;
+    const size_t per = (size_t)R.L * R.N;
+    u64 *T = work, *D = T + 2 * per, *PA = D + per * R.L, *PB = PA + per * R.L;
+    for (int c = 0; c < count; ++c) {
+        SF_TRY(pp_auto(r, in + 2 * per * c, T, 2, h, st));
+        k_pp_digits<<<pp_grid(per * R.L), 256, 0, st>>>(R, T, D);
+        k_pp_mul<<<dim3(R.L, R.L), SF_PP_THREADS, 2 * sizeof(u64) * R.M, st>>>(R, D, ka, PA, R.L);
+        k_pp_mul<<<dim3(R.L, R.L), SF_PP_THREADS, 2 * sizeof(u64) * R.M, st>>>(R, D, kb, PB, R.L);
+        k_pp_ks_combine<<<pp_grid(per), 256, 0, st>>>(R, PA, PB, T + per, out + 2 * per * c);
+    }
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+extern "C" sf_status sf_pp_keyswitch(sf_pp_ring *r, const uint64_t *d_ct, uint64_t *d_out, int32_t count, int32_t h,
+                                     const uint64_t *d_ka, const uint64_t *d_kb, void *stream)
+{
+    SF_TRY(pp_check(r, d_ct, d_out, count));
+    if (!d_ka || !d_kb || d_ct == d_out) return sf_set_error(SF_EINVAL, "sf_pp_keyswitch: bad key or aliasing");
+    const SfPpRing &R = r->R;
+    u64 *work;
+    SF_TRY(pp_ks_buffer(r, (size_t)R.L * R.N * (2 + 3 * (size_t)R.L), &work));
+    return pp_keyswitch(r, d_ct, d_out, count, h, d_ka, d_kb, work, (cudaStream_t)stream);
+}
+
+extern "C" sf_status sf_pp_hom_trace(sf_pp_ring *r, const uint64_t *d_ct, uint64_t *d_out, int32_t count,
+                                     int32_t gamma, int32_t n_keys, const int32_t *hs, const uint64_t *const *d_kas,
+                                     const uint64_t *const *d_kbs, int32_t *n_keyswitches, void *stream)
+{
+    SF_TRY(pp_check(r, d_ct, d_out, count));
+    const SfPpRing &R = r->R;
+    if (gamma < 0 || gamma > R.alpha) return sf_set_error(SF_EINVAL, "sf_pp_hom_trace: gamma must lie in [0, alpha]");
+    if (n_keys < 0 || (n_keys > 0 && (!hs || !d_kas || !d_kbs)))
+        return sf_set_error(SF_EINVAL, "sf_pp_hom_trace: bad key list");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<std::pair<int, int>> steps;
+    pp_tower_steps(R, gamma, steps);
+    std::vector<int> key_of(steps.size());
+    for (size_t k = 0; k < steps.size(); ++k) {
+        key_of[k] = -1;
+        for (int x = 0; x < n_keys; ++x)
+            if (((hs[x] % R.M) + R.M) % R.M == steps[k].first) key_of[k] = x;
+        if (key_of[k] < 0) return sf_set_error(SF_EINVAL, "sf_pp_hom_trace: no key for tau_%d", steps[k].first);
+    }
+    const size_t words = (size_t)count * 2 * R.L * R.N;
+    if (r->scratch_words < 2 * words) {
+        if (r->d_scratch) cudaFree(r->d_scratch);
+        r->d_scratch = nullptr;
+        r->scratch_words = 0;
+        SF_CUDA_TRY(cudaMalloc((void **)&r->d_scratch, sizeof(u64) * 2 * words));
+        r->scratch_words = 2 * words;
+    }
+    u64 *work;
+    SF_TRY(pp_ks_buffer(r, (size_t)R.L * R.N * (2 + 3 * (size_t)R.L), &work));
+    u64 *cur = r->d_scratch, *nxt = cur + words;
+    SF_CUDA_TRY(cudaMemcpyAsync(d_out, d_ct, sizeof(u64) * words, cudaMemcpyDeviceToDevice, st));
+    int ks = 0;
+    const int grid = pp_grid(words);
+    for (size_t k = 0; k < steps.size(); ++k) {
+        SF_CUDA_TRY(cudaMemcpyAsync(cur, d_out, sizeof(u64) * words, cudaMemcpyDeviceToDevice, st));
+        for (int x = 1; x < steps[k].second; ++x) {
+            SF_TRY(pp_keyswitch(r, cur, nxt, count, steps[k].first, d_kas[key_of[k]], d_kbs[key_of[k]], work, st));
+            std::swap(cur, nxt);
+            k_pp_add<<<grid, 256, 0, st>>>(R, d_out, cur, words);
+            SF_CUDA_TRY(cudaGetLastError());
+            ++ks;
+        }
+    }
+    if (n_keyswitches) *n_keyswitches = ks;
     return SF_OK;
 }
