@@ -454,7 +454,7 @@ def pp_ntt_record(local: int, flush, t: int = 3, alpha: int = 7, L: int = 5, cou
     over count x L limbs: algorithmic GB/s (each limb read and written once)
     and modular products/s: M/t butterflies per stage, alpha stages, each
     with its t - 1 twiddle products and the t-point DFT's products (2 for
-    t = 3, t (t - 1) otherwise)."""
+    t = 3, (t - 1)^2 / 2 by conjugate pairs otherwise)."""
     import torch
     import paper_2509_01253_gb300 as sf
     r = sf.sf_pp_ring_create(t, alpha, L, 50, local)
@@ -476,7 +476,7 @@ def pp_ntt_record(local: int, flush, t: int = 3, alpha: int = 7, L: int = 5, cou
         torch.cuda.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev) / reps
         nbytes = 2 * count * L * M * 8
-        mods = count * L * (M // t) * alpha * ((2 if t == 3 else t * (t - 1)) + t - 1)
+        mods = count * L * (M // t) * alpha * ((2 if t == 3 else (t - 1) ** 2 // 2) + t - 1)
         hbm_peak, kind = load_peaks()
         gbs = nbytes / (ms * 1e-3) / 1e9
         return {"what": f"forward length-{M} transform (M = {t}^{alpha}, N = {info['N']}) of {count} x {L} limbs "

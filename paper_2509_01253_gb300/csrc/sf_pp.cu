@@ -16,7 +16,8 @@
 // One block per (polynomial, limb) holds its length-M vector in shared memory
 // (at most 3125 words for Table 2's rings).  Each radix-t butterfly runs the
 // t-point DFT with t - 1 products per output, summed lazily below 2 t q, then
-// one reduction (at t = 3 the DFT takes two products in all, ppt_dft3);
+// one reduction; the compiled rings pair conjugate terms instead ((t-1)^2 / 2
+// products, ppt_dft_pairs; two at t = 3, ppt_dft3);
 // twiddles and t-th roots come from a per-limb table of omega^e.  Table 2's
 // rings and the small test rings are compiled with t and alpha as constants
 // (k_ppt_ntt); other rings run the generic kernel (k_pp_ntt).
@@ -46,6 +47,7 @@ struct SfPpRing {
     const u64 *iw;           // [L][M] omega_i^-e
     const u64 *iw_p;
     const u64 *qhat;         // [L][L][2]: (Q / q_i) mod q_j and its Shoup companion
+    const u64 *dftc;         // [L][H][H][4], H = (t-1)/2: C_rk, C_rk', S_rk, S_rk' of the paired t-point DFT
     SfPpMod mod[SF_MAX_MODULI];
 };
 
@@ -182,8 +184,46 @@ __device__ __forceinline__ void ppt_dft3(u64 &x0, u64 &x1, u64 &x2, const SfPpMo
     x2 = INV ? sf_add(u, v, q) : sf_sub(u, v, q);
 }
 
+// The t-point DFT for odd t >= 5 by conjugate pairs: with A_r = x_r + x_(t-r),
+// B_r = x_r - x_(t-r) (r = 1 .. H, H = (t-1)/2),
+//   y_k, y_(t-k) = x_0 + sum_r A_r C_rk +- sum_r B_r S_rk,
+// C_rk = (zeta^(rk) + zeta^(-rk)) / 2, S_rk = (zeta^(rk) - zeta^(-rk)) / 2, so
+// (t-1)^2 / 2 products instead of t (t-1); the inverse (root zeta^-1) flips S.
+template <int T, bool INV>
+__device__ __forceinline__ void ppt_dft_pairs(u64 *x, const u64 *dc, u64 q, u64 one_p)
+{
+    constexpr int H = (T - 1) / 2;
+    u64 A[H], B[H];
+    u64 y0 = x[0];
+#pragma unroll
+    for (int r = 1; r <= H; ++r) {
+        A[r - 1] = sf_add(x[r], x[T - r], q);
+        B[r - 1] = sf_sub(x[r], x[T - r], q);
+        y0 = sf_add(y0, A[r - 1], q);
+    }
+    u64 y[T];
+    y[0] = y0;
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        u64 U = 0, V = 0;   // lazy: H terms below 2q each
+#pragma unroll
+        for (int r = 1; r <= H; ++r) {
+            const u64 *c = dc + 4 * ((r - 1) * H + (k - 1));
+            U += sf_mul_shoup_lazy(A[r - 1], __ldg(c), __ldg(c + 1), q);
+            V += sf_mul_shoup_lazy(B[r - 1], __ldg(c + 2), __ldg(c + 3), q);
+        }
+        const u64 base = sf_add(x[0], sf_reduce(U, q, one_p), q);
+        V = sf_reduce(V, q, one_p);
+        y[k] = INV ? sf_sub(base, V, q) : sf_add(base, V, q);
+        y[T - k] = INV ? sf_add(base, V, q) : sf_sub(base, V, q);
+    }
+#pragma unroll
+    for (int k = 0; k < T; ++k) x[k] = y[k];
+}
+
 template <int T, int M, int LEN>
-__device__ __forceinline__ void ppt_stage_fwd(u64 *s, const u64 *w, const u64 *wp, u64 q, u64 one_p, const SfPpMod &P)
+__device__ __forceinline__ void ppt_stage_fwd(u64 *s, const u64 *w, const u64 *wp, const u64 *dc, u64 q, u64 one_p,
+                                              const SfPpMod &P)
 {
     constexpr int THIRD = LEN / T, STRIDE = M / LEN, ROOT = M / T;
     const int idx = threadIdx.x;
@@ -197,6 +237,14 @@ __device__ __forceinline__ void ppt_stage_fwd(u64 *s, const u64 *w, const u64 *w
             ppt_dft3<false>(x[0], x[1], x[2], P);
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
+                const int e = STRIDE * j * k;
+                s[base + k * THIRD] = e ? sf_mul_shoup(x[k], __ldg(w + e), __ldg(wp + e), q) : x[k];
+            }
+            return;
+        } else if constexpr (T >= 5) {
+            ppt_dft_pairs<T, false>(x, dc, q, one_p);
+#pragma unroll
+            for (int k = 0; k < T; ++k) {
                 const int e = STRIDE * j * k;
                 s[base + k * THIRD] = e ? sf_mul_shoup(x[k], __ldg(w + e), __ldg(wp + e), q) : x[k];
             }
@@ -221,7 +269,8 @@ __device__ __forceinline__ void ppt_stage_fwd(u64 *s, const u64 *w, const u64 *w
 }
 
 template <int T, int M, int LEN>
-__device__ __forceinline__ void ppt_stage_inv(u64 *s, const u64 *iw, const u64 *iwp, u64 q, u64 one_p, const SfPpMod &P)
+__device__ __forceinline__ void ppt_stage_inv(u64 *s, const u64 *iw, const u64 *iwp, const u64 *dc, u64 q, u64 one_p,
+                                              const SfPpMod &P)
 {
     constexpr int THIRD = LEN / T, STRIDE = M / LEN, ROOT = M / T;
     const int idx = threadIdx.x;
@@ -240,6 +289,11 @@ __device__ __forceinline__ void ppt_stage_inv(u64 *s, const u64 *iw, const u64 *
 #pragma unroll
             for (int r = 0; r < 3; ++r) s[base + r * THIRD] = x[r];
             return;
+        } else if constexpr (T >= 5) {
+            ppt_dft_pairs<T, true>(x, dc, q, one_p);
+#pragma unroll
+            for (int r = 0; r < T; ++r) s[base + r * THIRD] = x[r];
+            return;
         }
 #pragma unroll
         for (int r = 0; r < T; ++r) {
@@ -255,19 +309,21 @@ __device__ __forceinline__ void ppt_stage_inv(u64 *s, const u64 *iw, const u64 *
 }
 
 template <int T, int M, int LEN>
-__device__ __forceinline__ void ppt_forward(u64 *s, const u64 *w, const u64 *wp, u64 q, u64 one_p, const SfPpMod &P)
+__device__ __forceinline__ void ppt_forward(u64 *s, const u64 *w, const u64 *wp, const u64 *dc, u64 q, u64 one_p,
+                                            const SfPpMod &P)
 {
-    ppt_stage_fwd<T, M, LEN>(s, w, wp, q, one_p, P);
+    ppt_stage_fwd<T, M, LEN>(s, w, wp, dc, q, one_p, P);
     __syncthreads();
-    if constexpr (LEN / T >= T) ppt_forward<T, M, LEN / T>(s, w, wp, q, one_p, P);
+    if constexpr (LEN / T >= T) ppt_forward<T, M, LEN / T>(s, w, wp, dc, q, one_p, P);
 }
 
 template <int T, int M, int LEN>
-__device__ __forceinline__ void ppt_inverse(u64 *s, const u64 *iw, const u64 *iwp, u64 q, u64 one_p, const SfPpMod &P)
+__device__ __forceinline__ void ppt_inverse(u64 *s, const u64 *iw, const u64 *iwp, const u64 *dc, u64 q, u64 one_p,
+                                            const SfPpMod &P)
 {
-    ppt_stage_inv<T, M, LEN>(s, iw, iwp, q, one_p, P);
+    ppt_stage_inv<T, M, LEN>(s, iw, iwp, dc, q, one_p, P);
     __syncthreads();
-    if constexpr (LEN * T <= M) ppt_inverse<T, M, LEN * T>(s, iw, iwp, q, one_p, P);
+    if constexpr (LEN * T <= M) ppt_inverse<T, M, LEN * T>(s, iw, iwp, dc, q, one_p, P);
 }
 
 template <int T, int ALPHA>
@@ -281,10 +337,14 @@ __global__ void __launch_bounds__(SfPpT<T, ALPHA>::THREADS) k_ppt_ntt(SfPpRing R
     for (int e = threadIdx.x; e < M; e += NT) s[e] = in[off + e];
     __syncthreads();
     if (inverse) {
-        ppt_inverse<T, M, T>(s, R.iw + (size_t)i * M, R.iw_p + (size_t)i * M, P.q, P.one_p, P);
+        constexpr int H = (T - 1) / 2;
+        ppt_inverse<T, M, T>(s, R.iw + (size_t)i * M, R.iw_p + (size_t)i * M, R.dftc + (size_t)i * H * H * 4, P.q,
+                             P.one_p, P);
         for (int e = threadIdx.x; e < M; e += NT) out[off + e] = sf_mul_shoup(s[e], P.minv, P.minv_p, P.q);
     } else {
-        ppt_forward<T, M, M>(s, R.w + (size_t)i * M, R.w_p + (size_t)i * M, P.q, P.one_p, P);
+        constexpr int H = (T - 1) / 2;
+        ppt_forward<T, M, M>(s, R.w + (size_t)i * M, R.w_p + (size_t)i * M, R.dftc + (size_t)i * H * H * 4, P.q,
+                             P.one_p, P);
         for (int e = threadIdx.x; e < M; e += NT) out[off + e] = s[e];
     }
 }
@@ -414,7 +474,9 @@ extern "C" sf_status sf_pp_ring_create(int32_t t, int32_t alpha, int32_t L, int3
         delete r;
         return sf_set_error(SF_EINVAL, "sf_pp_ring_create: not enough primes = 1 mod %lld below 2^%d", M, bits);
     }
-    std::vector<u64> tab((size_t)4 * L * R.M + (size_t)2 * L * L);
+    const int H = (t - 1) / 2;
+    const size_t o_qhat = (size_t)4 * L * R.M, o_dftc = o_qhat + (size_t)2 * L * L;
+    std::vector<u64> tab(o_dftc + (size_t)4 * L * H * H);
     for (int i = 0; i < L; ++i) {
         const u64 q = r->q[i];
         const u64 w = pp_root(q, R.M, t), iw = sf_host_invmod(w, q);
@@ -443,6 +505,18 @@ extern "C" sf_status sf_pp_ring_create(int32_t t, int32_t alpha, int32_t L, int3
         const u64 z = sf_host_powmod(w, (u64)(R.M / t), q), z2 = sf_host_mulmod(z, z, q);
         P.c3 = sf_host_mulmod((z + q - z2) % q, P.h2, q);
         P.c3_p = sf_shoup_companion(P.c3, q);
+        // paired t-point DFT: C_rk = (z^(rk) + z^(-rk)) / 2, S_rk = (z^(rk) - z^(-rk)) / 2
+        for (int rr = 1; rr <= H; ++rr)
+            for (int kk = 1; kk <= H; ++kk) {
+                const int e = (rr * kk) % t;
+                const u64 zp = sf_host_powmod(z, (u64)e, q), zm = sf_host_powmod(z, (u64)(t - e), q);
+                const u64 C = sf_host_mulmod((zp + zm) % q, P.h2, q), S = sf_host_mulmod((zp + q - zm) % q, P.h2, q);
+                u64 *d = &tab[o_dftc + 4 * (((size_t)i * H + (rr - 1)) * H + (kk - 1))];
+                d[0] = C;
+                d[1] = sf_shoup_companion(C, q);
+                d[2] = S;
+                d[3] = sf_shoup_companion(S, q);
+            }
     }
     // RNS digits: (Q / q_i) mod q_j and (Q / q_i)^-1 mod q_i
     for (int i = 0; i < L; ++i) {
@@ -450,8 +524,8 @@ extern "C" sf_status sf_pp_ring_create(int32_t t, int32_t alpha, int32_t L, int3
             u64 v = 1;
             for (int k = 0; k < L; ++k)
                 if (k != i) v = sf_host_mulmod(v, r->q[k] % r->q[j], r->q[j]);
-            tab[(size_t)4 * L * R.M + 2 * ((size_t)i * L + j)] = v;
-            tab[(size_t)4 * L * R.M + 2 * ((size_t)i * L + j) + 1] = sf_shoup_companion(v, r->q[j]);
+            tab[o_qhat + 2 * ((size_t)i * L + j)] = v;
+            tab[o_qhat + 2 * ((size_t)i * L + j) + 1] = sf_shoup_companion(v, r->q[j]);
             if (j == i) {
                 R.mod[i].qh_inv = sf_host_invmod(v, r->q[i]);
                 R.mod[i].qh_inv_p = sf_shoup_companion(R.mod[i].qh_inv, r->q[i]);
@@ -474,6 +548,7 @@ extern "C" sf_status sf_pp_ring_create(int32_t t, int32_t alpha, int32_t L, int3
     R.iw = R.w_p + (size_t)L * R.M;
     R.iw_p = R.iw + (size_t)L * R.M;
     R.qhat = R.iw_p + (size_t)L * R.M;
+    R.dftc = R.qhat + (size_t)2 * L * L;
     *out = r;
     return SF_OK;
 }
