@@ -29,7 +29,8 @@
  * (M = 2N, N = phi(M) a power of two, Sec. 2.1), RNS modulus Q = prod q_i of
  * L data primes plus P = prod p_k of K special primes for hybrid key
  * switching; all primes are 1 mod 2N.  Key-switch digits are consecutive
- * groups of K data limbs, dnum = ceil(L / K).
+ * groups of K data limbs, dnum = ceil(L / K).  The sf_pp_* calls at the end
+ * work over the prime-power rings M = t^alpha with t an odd prime.
  */
 #ifndef SAFHIRE_H
 #define SAFHIRE_H
@@ -53,7 +54,7 @@ typedef int32_t sf_status;
 #define SF_ECUDA 3    /* a CUDA runtime call failed, or no usable device */
 #define SF_ERANGE 6   /* a value does not fit the requested representation, or (latched on the
                          device, see sf_sync) an input residue is not below its modulus */
-#define SF_ENOTSUP 8  /* valid request that this build does not implement */
+#define SF_ENOTSUP 8  /* valid request that this library does not implement */
 /* (codes 4, 5 and 7 are not used) */
 
 /* Copies the calling thread's last error message into buf (always
