@@ -24,6 +24,9 @@ definitions literally:
   encryption, decryption, key switching after an automorphism by the RNS
   limbs of tau_h(a), and the homomorphic tower trace (Sec. 2.1-2.3 on
   ciphertexts).
+* TorusRlwe: the paper's own scheme, RLWE over the torus T_q, q = 2^53
+  (Sec. 2.1), with the (D, l) gadget key switching of Sec. 2.2 / Sec. 4.2
+  and Table 2, and the same homomorphic tower trace.
 """
 from __future__ import annotations
 
@@ -314,6 +317,151 @@ class RnsRlwe:
         """Tr_{K / K_gamma} (gamma >= 1) or the full trace (gamma = 0) on a
         ciphertext, along the tower's steps: x <- sum_{k < length} tau_h^k(x),
         every tau_h followed by its key switch; keys[h] = (ka, kb)."""
+        x = ct
+        for h, length in self.R.tower_steps(gamma):
+            acc, cur = x, x
+            for _ in range(length - 1):
+                cur = self.keyswitch(cur, h, *keys[h])
+                if counter is not None:
+                    counter[0] += 1
+                acc = self.add(acc, cur)
+            x = acc
+        return x
+
+
+class TorusRlwe:
+    """RLWE over the discrete torus T_q = (1/q) Z_q with q = 2^53 (Sec. 2.1) in
+    the ring T_q[X]/Phi_M, with the gadget key switching of Sec. 2.2 and Sec.
+    4.2: the key for tau_h is the l encryptions RLWE_s(tau_h(s) / D^i),
+    i = 1 .. l, with the base D and depth l of Table 2.
+
+    A torus value x / q is stored as the integer x in [0, q).  A ciphertext is
+    (a, b) with b = a s + m + e (mod q), the convention of RnsRlwe.  The uniform
+    a, ka and the noise e are inputs (drawn by the caller).
+
+    * Products are taken of a torus polynomial and an integer polynomial
+      (a digit polynomial or the secret): schoolbook in numpy uint64, i.e.
+      modulo 2^64, which is exact modulo q because q divides 2^64, then the
+      reduction mod Phi_M of Ring.reduce, then mod q.
+    * Gadget decomposition of x in [0, q): xr = round(x D^l / q) mod D^l
+      (halves rounded up), then the signed base-D digits d_1 .. d_l of xr,
+      d_1 the most significant, each in [-floor(D/2), D - floor(D/2)), with
+      sum_i d_i D^(l-i) = xr (mod D^l); so sum_i d_i / D^i equals x / q up to
+      1 / (2 D^l) on the torus.  Digits are taken from the least significant
+      end, a digit in the upper part of [0, D) becoming negative with a carry
+      into the next one; the carry out of d_1 is dropped (a multiple of D^l,
+      an integer on the torus).
+    * The key message tau_h(s) / D^i is taken coefficient by coefficient as
+      round(c q / D^i) mod q (halves rounded up).
+    * Key switch after tau_h: with d_i the digit polynomials of tau_h(a),
+      (a', b') = (-sum_i d_i ka_i, tau_h(b) - sum_i d_i kb_i) mod q, which
+      decrypts to tau_h(m + e) - sum_i d_i e_i minus the gadget's rounding.
+    """
+
+    LOGQ = 53
+
+    def __init__(self, ring: Ring, D: int, l: int):
+        assert D >= 2 and l >= 1 and D ** l <= 2 ** self.LOGQ
+        self.R, self.D, self.l = ring, int(D), int(l)
+        self.q = 2 ** self.LOGQ
+
+    # ------------------------------------------------------------ products
+    def mul(self, a, b) -> list:
+        """a b in Z_q[X]/Phi_M for integer polynomials a, b of length N (any
+        signs): schoolbook modulo 2^64, reduction mod Phi_M, then mod q."""
+        import numpy as np
+
+        R = self.R
+        A = np.array([int(x) % 2 ** 64 for x in a], dtype=np.uint64)
+        B = np.array([int(x) % 2 ** 64 for x in b], dtype=np.uint64)
+        prod = np.zeros(2 * R.N - 1, dtype=np.uint64)
+        for i in np.nonzero(A)[0]:
+            prod[i:i + R.N] += A[i] * B
+        c = [0] * R.M
+        for e, v in enumerate(prod.tolist()):
+            c[e % R.M] += v
+        return [v % self.q for v in R.reduce(c)]
+
+    def add(self, c1, c2) -> tuple:
+        return tuple([(x + y) % self.q for x, y in zip(u, v)] for u, v in zip(c1, c2))
+
+    def centered(self, x) -> list:
+        """Torus integers in [0, q) as representatives in [-q/2, q/2)."""
+        h = self.q // 2
+        return [(v + h) % self.q - h for v in x]
+
+    # ------------------------------------------------------ enc, dec, codec
+    def encode(self, mu, log_p: int) -> list:
+        """mu in T_p, p = 2^log_p (integers mod p) -> the torus integers mu q / p."""
+        return [(int(v) % 2 ** log_p) << (self.LOGQ - log_p) for v in mu]
+
+    def decode(self, phase, log_p: int) -> list:
+        """pi_p of Sec. 2.1: round(p x / q) mod p (halves rounded up)."""
+        sh = self.LOGQ - log_p
+        return [((v + (1 << (sh - 1))) >> sh) % 2 ** log_p for v in phase]
+
+    def encrypt(self, s, a, m, e) -> tuple:
+        """(a, b = a s + m + e mod q); a and m torus integers, s and e integer
+        polynomials."""
+        a = [int(x) % self.q for x in a]
+        as_ = self.mul(a, s)
+        return (a, [(x + int(mi) + int(ei)) % self.q for x, mi, ei in zip(as_, m, e)])
+
+    def decrypt(self, s, ct) -> list:
+        """The phase b - a s mod q (m + noise)."""
+        a, b = ct
+        return [(y - x) % self.q for x, y in zip(self.mul(a, s), b)]
+
+    # --------------------------------------------------------------- gadget
+    def decompose(self, x) -> list:
+        """The l digit polynomials [d_1, .., d_l] of a torus polynomial x."""
+        D, l, q = self.D, self.l, self.q
+        Dl, half = D ** l, D // 2
+        out = [[0] * len(x) for _ in range(l)]
+        for k, v in enumerate(x):
+            xr = ((int(v) % q) * Dl + q // 2) // q % Dl
+            for i in range(l, 0, -1):
+                r = xr % D
+                xr //= D
+                if r >= D - half:
+                    r -= D
+                    xr += 1
+                out[i - 1][k] = r
+        return out
+
+    def gadget_message(self, c, i: int) -> list:
+        """The torus polynomial c / D^i for an integer polynomial c:
+        round(c_k q / D^i) mod q per coefficient."""
+        Di = self.D ** i
+        return [((2 * int(v) * self.q + Di) // (2 * Di)) % self.q for v in c]
+
+    def ksk(self, s, h: int, ka, e) -> list:
+        """kb_i = ka_i s + e_i + tau_h(s) / D^i (mod q), i = 1 .. l; ka[i - 1]
+        uniform torus integers, e[i - 1] integer noise polynomials."""
+        ts = self.R.automorphism(list(s), h)
+        kb = []
+        for i in range(1, self.l + 1):
+            prod = self.mul(ka[i - 1], s)
+            g = self.gadget_message(ts, i)
+            kb.append([(p + int(ei) + gi) % self.q for p, ei, gi in zip(prod, e[i - 1], g)])
+        return kb
+
+    def keyswitch(self, ct, h: int, ka, kb) -> tuple:
+        """tau_h of ct, then the gadget key switch back to s."""
+        a, b = ct
+        ta = [v % self.q for v in self.R.automorphism(list(a), h)]
+        tb = [v % self.q for v in self.R.automorphism(list(b), h)]
+        a2, b2 = [0] * self.R.N, tb
+        for i, d in enumerate(self.decompose(ta)):
+            pa, pb = self.mul(d, ka[i]), self.mul(d, kb[i])
+            a2 = [(x - y) % self.q for x, y in zip(a2, pa)]
+            b2 = [(x - y) % self.q for x, y in zip(b2, pb)]
+        return (a2, b2)
+
+    def hom_trace(self, ct, gamma: int, keys: dict, counter: list | None = None) -> tuple:
+        """Tr_{K / K_gamma} (gamma >= 1) or the full trace (gamma = 0) on a
+        torus ciphertext along the tower's steps: x <- sum_{k < length}
+        tau_h^k(x), each tau_h followed by its key switch; keys[h] = (ka, kb)."""
         x = ct
         for h, length in self.R.tower_steps(gamma):
             acc, cur = x, x
