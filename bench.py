@@ -486,6 +486,98 @@ def pp_ntt_record(local: int, flush, t: int = 3, alpha: int = 7, L: int = 5, cou
         sf.sf_pp_ring_destroy(r)
 
 
+def tq_record(local: int, flush, count: int = 4096) -> dict:
+    """The paper's torus scheme (q = 2^53) with Table 2's rings and gadgets:
+    one sf_tq_keyswitch launch over `count` ciphertexts per gadget (one fused
+    kernel: tau_h, gadget digits, 2 (l + 2) length-M transforms over two CRT
+    primes, the key products and the CRT), and the full homomorphic trace of
+    `count` ciphertexts at M = 5^5, (310, 5).  Modular products per key switch,
+    counted nominally: per transform alpha stages of M / t butterflies with the
+    DFT's products (2 at t = 3, (t - 1)^2 / 2 otherwise) and t - 1 twiddles;
+    per prime 2 l M key products and 2 M inverse scalings; 2 N CRT steps of two
+    products each.  Inputs are larger than L2 (4096 x 2 x N words) and L2 is
+    flushed before every timed call."""
+    import torch
+    import paper_2509_01253_gb300 as sf
+    dev = f"cuda:{local}"
+    stream = torch.cuda.current_stream()
+    alu_pk = alu_peak(torch.cuda.get_device_properties(local).multi_processor_count, 2070.0) / 1e9
+    rows = []
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for i in range(reps):
+            flush_l2(flush)
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / reps
+
+    def setup(t, alpha, D, l, h_of=None):
+        r = sf.sf_tq_ring_create(t, alpha, D, l, local)
+        info = sf.sf_tq_ring_info(r)
+        N = info["N"]
+        g = torch.Generator(device=dev).manual_seed(11)
+        s = torch.randint(-1, 2, (N,), dtype=torch.int64, device=dev, generator=g)
+        a = torch.randint(0, 2 ** 53, (count, N), dtype=torch.int64, device=dev, generator=g)
+        m = torch.randint(0, 2 ** 53, (count, N), dtype=torch.int64, device=dev, generator=g)
+        e = torch.randint(-2 ** 17, 2 ** 17, (count, N), dtype=torch.int64, device=dev, generator=g)
+        ct = torch.empty((count, 2, N), dtype=torch.int64, device=dev)
+        sf.sf_tq_encrypt(r, s, a, m, e, ct, count, stream)
+        return r, info, s, ct, g
+
+    def key(r, info, s, h, l, g):
+        N = info["N"]
+        ka = torch.randint(0, 2 ** 53, (l, N), dtype=torch.int64, device=dev, generator=g)
+        ek = torch.randint(-2 ** 17, 2 ** 17, (l, N), dtype=torch.int64, device=dev, generator=g)
+        kb = torch.empty_like(ka)
+        sf.sf_tq_ksk(r, s, h, ka, ek, kb, stream)
+        k = torch.empty(info["key_words"], dtype=torch.int64, device=dev)
+        sf.sf_tq_key_prepare(r, ka, kb, k, stream)
+        return k
+
+    def products(t, alpha, M, N, l):
+        per_tr = alpha * (M // t) * ((2 if t == 3 else (t - 1) ** 2 // 2) + t - 1)
+        return 2 * (l + 2) * per_tr + 2 * (2 * l * M + 2 * M) + 2 * 2 * N
+
+    for t, alpha, D, l in ((3, 7, 512, 3), (7, 4, 2 ** 12, 3), (7, 4, 2 ** 16, 2), (5, 5, 310, 5), (5, 5, 310, 4)):
+        r, info, s, ct, g = setup(t, alpha, D, l)
+        try:
+            M, N = info["M"], info["N"]
+            h = 1 + t ** (alpha - 1)
+            k = key(r, info, s, h, l, g)
+            out = torch.empty_like(ct)
+            ms = timed(lambda: sf.sf_tq_keyswitch(r, ct, out, count, h, k, stream))
+            prods = products(t, alpha, M, N, l) * count
+            gm = prods / (ms * 1e-3) / 1e9
+            rows.append({"M": f"{t}^{alpha}", "N": N, "D": D, "l": l, "ciphertexts": count, "ms_per_call": ms,
+                         "us_per_keyswitch": ms * 1e3 / count, "keyswitches_per_s": count / (ms * 1e-3),
+                         "gmodmul_s": gm, "frac_alu_peak": gm / alu_pk,
+                         "hbm_bytes": 2 * count * 2 * N * 8,
+                         "gbs": 2 * count * 2 * N * 8 / (ms * 1e-3) / 1e9})
+        finally:
+            sf.sf_tq_ring_destroy(r)
+        torch.cuda.empty_cache()
+    # Tr_(K / K_1) at M = 5^5 with Table 2's gamma >= 1 gadget (310, 4): the
+    # tower steps tau_(1 + 5^i), i = 4 .. 1, four key switches each
+    r, info, s, ct, g = setup(5, 5, 310, 4)
+    try:
+        keys = {1 + 5 ** i: key(r, info, s, 1 + 5 ** i, 4, g) for i in range(1, 5)}
+        out = torch.empty_like(ct)
+        n_ks = sf.sf_tq_hom_trace(r, ct, out, count, 1, keys, stream)
+        ms = timed(lambda: sf.sf_tq_hom_trace(r, ct, out, count, 1, keys, stream), reps=3)
+        trace = {"what": f"Tr_(K/K_1) (gamma = 1) of {count} ciphertexts, M = 5^5, (D, l) = (310, 4)",
+                 "keyswitches_per_ciphertext": n_ks, "ms_per_call": ms, "us_per_ciphertext": ms * 1e3 / count}
+    finally:
+        sf.sf_tq_ring_destroy(r)
+    return {"what": "torus RLWE (q = 2^53) gadget key switch, Table 2's rings and gadgets (sf_tq_keyswitch)",
+            "alu_peak_gmodmul_s": alu_pk, "peak_source": "derived: SMs x 64 int32 multiply-adds/clk x 2070 MHz / 10",
+            "rows": rows, "trace": trace}
+
+
 # ------------------------------------------------------- CPU baseline ----
 
 def host_cores() -> int:
@@ -1180,7 +1272,8 @@ def main():
                          ("batched_vs_per_layer", lambda: batched_record(local, "resnet18", BATCH_ROUNDS)),
                          ("batched_small_rounds", lambda: batched_record(local, "resnet20", R20_LATE)),
                          ("batched_requests", lambda: batched_record(local, "resnet20", ["s2b1c1"], copies=7)),
-                         ("pp_ntt", lambda: pp_ntt_record(local, flush))):
+                         ("pp_ntt", lambda: pp_ntt_record(local, flush)),
+                         ("torus_ks", lambda: tq_record(local, flush))):
             t0 = time.perf_counter()
             try:
                 extras[name] = fn()

@@ -558,6 +558,74 @@ sf_status sf_pp_hom_trace(sf_pp_ring *ring, const uint64_t *d_ct, uint64_t *d_ou
                           int32_t n_keys, const int32_t *hs, const uint64_t *const *d_kas,
                           const uint64_t *const *d_kbs, int32_t *n_keyswitches, void *stream);
 
+/* ---- the paper's torus scheme: RLWE over T_q = (1/q) Z_q, q = 2^53 (Sec. 2.1),
+ * in the prime-power rings above, with the gadget key switching of Sec. 2.2 and
+ * Sec. 4.2 (base D, depth l; Table 2: M = 3^7 with (512, 3), 7^4 with (2^12, 3)
+ * or (2^16, 2), 5^5 with (310, 5) or (310, 4)).
+ *
+ * A torus value x / q is the integer x in [0, 2^53) in one uint64 word; input
+ * words are read modulo 2^53.  Polynomials are uint64[count][N], ciphertexts
+ * uint64[count][2][N] (a, then b = a s + m + e mod 2^53).  The secret s
+ * (int64[N], |s_e| <= 65536) and the noise (int64) are inputs, as are the
+ * uniform masks a and ka.  Products are exact: computed over Z through two NTT
+ * primes p_0, p_1 = 1 (mod M) of 50 bits and the CRT, then taken mod 2^53.  All
+ * buffers are device memory owned by the caller; every call is asynchronous on
+ * `stream` and uses a grow-only work buffer of the ring. */
+typedef struct sf_tq_ring sf_tq_ring;
+
+/* The ring for (t, alpha) with the gadget (D, l).  Errors: SF_EINVAL (the
+ * limits of sf_pp_ring_create on t and alpha, 2 <= D <= 65536, 1 <= l <= 8,
+ * D^l <= 2^53, or products that could leave the CRT range), SF_ECUDA. */
+sf_status sf_tq_ring_create(int32_t t, int32_t alpha, int32_t D, int32_t l, int32_t device, sf_tq_ring **out);
+void sf_tq_ring_destroy(sf_tq_ring *ring);
+/* N, M, the two CRT primes (uint64[2]) and the words of a prepared key,
+ * 8 l M (each output may be NULL). */
+sf_status sf_tq_ring_info(const sf_tq_ring *ring, int32_t *N, int32_t *M, uint64_t *primes, int64_t *key_words);
+
+/* Gadget decomposition of uint64[count][N] torus polynomials into
+ * int32[count][l][N] signed digits: with xr = round(x D^l / q) mod D^l (halves
+ * up), d_1 .. d_l (d_1 most significant) in [-floor(D/2), D - floor(D/2)) and
+ * sum_i d_i D^(l-i) = xr (mod D^l), so sum_i d_i / D^i = x / q up to 1 / (2 D^l).
+ * Errors: SF_EINVAL, SF_ECUDA. */
+sf_status sf_tq_decompose(sf_tq_ring *ring, const uint64_t *d_in, int32_t *d_digits, int32_t count, void *stream);
+
+/* d_ct[c] = (a[c], a[c] s + m[c] + e[c]): d_a and d_m uint64[count][N] torus
+ * words (the message already scaled, mu q / p), d_e int64[count][N]. */
+sf_status sf_tq_encrypt(sf_tq_ring *ring, const int64_t *d_s, const uint64_t *d_a, const uint64_t *d_m,
+                        const int64_t *d_e, uint64_t *d_ct, int32_t count, void *stream);
+/* d_phase[c] = b - a s mod 2^53 (m + noise), uint64[count][N]; decoding is
+ * round(p x / q) mod p (Sec. 2.1). */
+sf_status sf_tq_decrypt(sf_tq_ring *ring, const int64_t *d_s, const uint64_t *d_ct, uint64_t *d_phase, int32_t count,
+                        void *stream);
+
+/* The key for tau_h (Sec. 4.2): l encryptions of tau_h(s) / D^i, i = 1 .. l:
+ * d_kb[i-1] = ka_i s + e_i + round(q tau_h(s) / D^i) mod 2^53 (halves up),
+ * from the uniform d_ka uint64[l][N] and the noise d_e int64[l][N].  Errors:
+ * SF_EINVAL (h a multiple of t, null buffers), SF_ECUDA. */
+sf_status sf_tq_ksk(sf_tq_ring *ring, const int64_t *d_s, int32_t h, const uint64_t *d_ka, const int64_t *d_e,
+                    uint64_t *d_kb, void *stream);
+/* The key in the form the key switch reads: the 2 l polynomials ka_i, kb_i
+ * transformed modulo each CRT prime, with Shoup companions; d_key holds
+ * key_words (sf_tq_ring_info) words. */
+sf_status sf_tq_key_prepare(sf_tq_ring *ring, const uint64_t *d_ka, const uint64_t *d_kb, uint64_t *d_key,
+                            void *stream);
+
+/* Key switch after tau_h (Sec. 2.2): with d_i the gadget digits of tau_h(a),
+ * d_out[c] = (-sum_i d_i ka_i, tau_h(b) - sum_i d_i kb_i) mod 2^53, which
+ * decrypts to tau_h(m + e) - sum_i d_i e_i up to the gadget's rounding.  One
+ * fused kernel per call.  d_key: the prepared key of tau_h.  Errors: SF_EINVAL
+ * (h a multiple of t, null key, d_out == d_ct), SF_ECUDA. */
+sf_status sf_tq_keyswitch(sf_tq_ring *ring, const uint64_t *d_ct, uint64_t *d_out, int32_t count, int32_t h,
+                          const uint64_t *d_key, void *stream);
+
+/* The homomorphic tower trace of sf_pp_hom_trace over the torus: every
+ * automorphism followed by its gadget key switch, keys (hs[x], d_keys[x])
+ * prepared by sf_tq_key_prepare.  Errors: SF_EINVAL (gamma outside [0, alpha],
+ * no key for an automorphism of the tower, d_out == d_ct), SF_ECUDA. */
+sf_status sf_tq_hom_trace(sf_tq_ring *ring, const uint64_t *d_ct, uint64_t *d_out, int32_t count, int32_t gamma,
+                          int32_t n_keys, const int32_t *hs, const uint64_t *const *d_keys, int32_t *n_keyswitches,
+                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -110,6 +110,16 @@ _SIGS = {
     "sf_pp_ksk": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp]),
     "sf_pp_keyswitch": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp, _vp]),
     "sf_pp_hom_trace": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32), _vp]),
+    "sf_tq_ring_create": (_i32, [_i32, _i32, _i32, _i32, _i32, _pp]),
+    "sf_tq_ring_destroy": (None, [_vp]),
+    "sf_tq_ring_info": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _vp, ctypes.POINTER(_i64)]),
+    "sf_tq_decompose": (_i32, [_vp, _vp, _vp, _i32, _vp]),
+    "sf_tq_encrypt": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp]),
+    "sf_tq_decrypt": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp]),
+    "sf_tq_ksk": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp]),
+    "sf_tq_key_prepare": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "sf_tq_keyswitch": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp]),
+    "sf_tq_hom_trace": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, ctypes.POINTER(_i32), _vp]),
 }
 
 _lib = None
@@ -536,4 +546,56 @@ def sf_pp_hom_trace(r, d_ct, d_out, count: int, gamma: int, keys: dict, stream=N
     n = _i32()
     _check(lib().sf_pp_hom_trace(r, _ptr(d_ct), _ptr(d_out), count, gamma, len(hs), ctypes.cast(H, _vp),
                                  ctypes.cast(KA, _vp), ctypes.cast(KB, _vp), ctypes.byref(n), _stream(stream)))
+    return n.value
+
+
+# ------------------------------------- torus scheme (q = 2^53, gadget D, l) --
+
+def sf_tq_ring_create(t: int, alpha: int, D: int, l: int, device: int = 0):
+    return _out_handle(lib().sf_tq_ring_create, t, alpha, D, l, device)
+
+
+def sf_tq_ring_destroy(r):
+    lib().sf_tq_ring_destroy(r)
+
+
+def sf_tq_ring_info(r) -> dict:
+    n, m, kw = _i32(), _i32(), _i64()
+    primes = np.zeros(2, dtype=np.uint64)
+    _check(lib().sf_tq_ring_info(r, ctypes.byref(n), ctypes.byref(m), primes.ctypes.data, ctypes.byref(kw)))
+    return {"N": n.value, "M": m.value, "primes": [int(p) for p in primes], "key_words": kw.value}
+
+
+def sf_tq_decompose(r, d_in, d_digits, count: int, stream=None):
+    _check(lib().sf_tq_decompose(r, _ptr(d_in), _ptr(d_digits), count, _stream(stream)))
+
+
+def sf_tq_encrypt(r, d_s, d_a, d_m, d_e, d_ct, count: int, stream=None):
+    _check(lib().sf_tq_encrypt(r, _ptr(d_s), _ptr(d_a), _ptr(d_m), _ptr(d_e), _ptr(d_ct), count, _stream(stream)))
+
+
+def sf_tq_decrypt(r, d_s, d_ct, d_phase, count: int, stream=None):
+    _check(lib().sf_tq_decrypt(r, _ptr(d_s), _ptr(d_ct), _ptr(d_phase), count, _stream(stream)))
+
+
+def sf_tq_ksk(r, d_s, h: int, d_ka, d_e, d_kb, stream=None):
+    _check(lib().sf_tq_ksk(r, _ptr(d_s), h, _ptr(d_ka), _ptr(d_e), _ptr(d_kb), _stream(stream)))
+
+
+def sf_tq_key_prepare(r, d_ka, d_kb, d_key, stream=None):
+    _check(lib().sf_tq_key_prepare(r, _ptr(d_ka), _ptr(d_kb), _ptr(d_key), _stream(stream)))
+
+
+def sf_tq_keyswitch(r, d_ct, d_out, count: int, h: int, d_key, stream=None):
+    _check(lib().sf_tq_keyswitch(r, _ptr(d_ct), _ptr(d_out), count, h, _ptr(d_key), _stream(stream)))
+
+
+def sf_tq_hom_trace(r, d_ct, d_out, count: int, gamma: int, keys: dict, stream=None) -> int:
+    """keys: {h: d_key (prepared)}.  Returns the number of key switches run."""
+    hs = sorted(keys)
+    H = (_i32 * max(1, len(hs)))(*hs)
+    K = (_vp * max(1, len(hs)))(*[_ptr(keys[h]) for h in hs])
+    n = _i32()
+    _check(lib().sf_tq_hom_trace(r, _ptr(d_ct), _ptr(d_out), count, gamma, len(hs), ctypes.cast(H, _vp),
+                                 ctypes.cast(K, _vp), ctypes.byref(n), _stream(stream)))
     return n.value

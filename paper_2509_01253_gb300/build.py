@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_safhire.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["sf_host.cpp", "sf_ntt.cu", "sf_ks.cu", "sf_layer.cu", "sf_api.cu", "sf_engine.cu", "sf_noalloc.cu", "sf_pp.cu",
-           "sf_bntt.cu"]
+           "sf_bntt.cu", "sf_tq.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -22,3 +22,22 @@ def test_pp_ring_needs_a_device():
     with pytest.raises(sf.SafhireError) as e:
         sf.sf_pp_ring_create(3, 7, 2, 50, 0)
     assert e.value.status == sf.SF_ECUDA
+
+
+@pytest.mark.parametrize("t,alpha,D,l", [(3, 3, 1, 3), (3, 3, 65537, 1), (3, 3, 512, 0), (3, 3, 512, 9),
+                                         (3, 3, 2 ** 16, 4), (3, 3, 3, 34), (2, 5, 512, 3), (3, 8, 512, 3)])
+def test_tq_ring_parameter_checks(t, alpha, D, l):
+    """Torus rings: the gadget limits (2 <= D <= 65536, 1 <= l <= 8, D^l <= 2^53)
+    and the ring limits are checked before any device work."""
+    with pytest.raises(sf.SafhireError) as e:
+        sf.sf_tq_ring_create(t, alpha, D, l, 0)
+    assert e.value.status == sf.SF_EINVAL
+
+
+def test_tq_ring_needs_a_device():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(sf.SafhireError) as e:
+        sf.sf_tq_ring_create(5, 5, 310, 5, 0)
+    assert e.value.status == sf.SF_ECUDA
