@@ -58,14 +58,18 @@ struct sf_tq_ring {
     size_t work_words = 0;
 };
 
-// compile-time shape: T = 0 is the generic ring (runtime t, alpha)
+// compile-time shape: T = 0 is the generic ring (runtime t, alpha).  The key
+// switch of a compiled ring is bounded to two blocks per SM: at M = 3^7 and
+// 5^5 that caps its registers at 40 and 48 (with a few spilled words) and was
+// measured 12 and 10 % faster than one block of 72 and 94 registers; three
+// blocks spill more and lose again.
 template <int T, int ALPHA>
 struct SfTqShape {
-    static constexpr int NT = SfPpT<T, ALPHA>::THREADS, MMAX = SfPpT<T, ALPHA>::M;
+    static constexpr int NT = SfPpT<T, ALPHA>::THREADS, MMAX = SfPpT<T, ALPHA>::M, MINB = 2;
 };
 template <int ALPHA>
 struct SfTqShape<0, ALPHA> {
-    static constexpr int NT = SF_PP_THREADS, MMAX = SF_PP_MAX_M;
+    static constexpr int NT = SF_PP_THREADS, MMAX = SF_PP_MAX_M, MINB = 1;
 };
 
 // forward transform of the block's length-M vector modulo prime j
@@ -187,7 +191,7 @@ static size_t tq_ks_smem(const SfPpRing &R, int l)
 // transformed key values (digit i, part a / b, prime j), then their Shoup
 // companions in the same order.
 template <int T, int ALPHA>
-__global__ void __launch_bounds__(SfTqShape<T, ALPHA>::NT)
+__global__ void __launch_bounds__(SfTqShape<T, ALPHA>::NT, SfTqShape<T, ALPHA>::MINB)
     k_tq_ks(SfPpRing R, SfTqGadget G, const u64 *ct, u64 *out, int h, int hinv, const u64 *key)
 {
     constexpr int NT = SfTqShape<T, ALPHA>::NT, EPT = (SfTqShape<T, ALPHA>::MMAX + NT - 1) / NT;
