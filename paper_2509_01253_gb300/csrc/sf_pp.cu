@@ -34,17 +34,19 @@ __global__ void __launch_bounds__(SfPpT<T, ALPHA>::THREADS) k_ppt_ntt(SfPpRing R
     const int i = blockIdx.x;
     const SfPpMod &P = R.mod[i];
     const size_t off = ((size_t)blockIdx.y * R.L + i) * M;
-    for (int e = threadIdx.x; e < M; e += NT) s[e] = in[off + e];
-    __syncthreads();
     if (inverse) {
+        for (int e = threadIdx.x; e < M; e += NT) s[e] = in[off + e];
+        __syncthreads();
         constexpr int H = (T - 1) / 2;
         ppt_inverse<T, M, T>(s, R.iw + (size_t)i * M, R.iw_p + (size_t)i * M, R.dftc + (size_t)i * H * H * 4, P.q,
                              P.one_p, P);
         for (int e = threadIdx.x; e < M; e += NT) out[off + e] = sf_mul_shoup(s[e], P.minv, P.minv_p, P.q);
     } else {
         constexpr int H = (T - 1) / 2;
-        ppt_forward<T, M, M>(s, R.w + (size_t)i * M, R.w_p + (size_t)i * M, R.dftc + (size_t)i * H * H * 4, P.q,
-                             P.one_p, P);
+        // the first stage reads the input straight from global memory
+        const u64 *src = in + off;
+        ppt_forward_ld<T, M>(s, [src](int e) { return src[e]; }, R.w + (size_t)i * M, R.w_p + (size_t)i * M,
+                             R.dftc + (size_t)i * H * H * 4, P.q, P.one_p, P);
         for (int e = threadIdx.x; e < M; e += NT) out[off + e] = s[e];
     }
 }

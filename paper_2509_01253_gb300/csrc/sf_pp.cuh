@@ -205,9 +205,11 @@ __device__ __forceinline__ void ppt_dft_pairs(u64 *x, const u64 *dc, u64 q, u64 
     for (int k = 0; k < T; ++k) x[k] = y[k];
 }
 
-template <int T, int M, int LEN>
-__device__ __forceinline__ void ppt_stage_fwd(u64 *s, const u64 *w, const u64 *wp, const u64 *dc, u64 q, u64 one_p,
-                                              const SfPpMod &P)
+// one forward stage reading its inputs through ld(index) (the block's vector
+// itself, or a producer for the first stage) and writing them to s
+template <int T, int M, int LEN, class LD>
+__device__ __forceinline__ void ppt_stage_fwd_ld(u64 *s, LD ld, const u64 *w, const u64 *wp, const u64 *dc, u64 q,
+                                                 u64 one_p, const SfPpMod &P)
 {
     static_assert(T >= 3 && (T & 1), "compiled rings have an odd prime t");
     constexpr int THIRD = LEN / T, STRIDE = M / LEN;
@@ -217,7 +219,7 @@ __device__ __forceinline__ void ppt_stage_fwd(u64 *s, const u64 *w, const u64 *w
         const int base = blk * LEN + j;
         u64 x[T];
 #pragma unroll
-        for (int r = 0; r < T; ++r) x[r] = s[base + r * THIRD];
+        for (int r = 0; r < T; ++r) x[r] = ld(base + r * THIRD);
         if constexpr (T == 3) {
             ppt_dft3<false>(x[0], x[1], x[2], P);
 #pragma unroll
@@ -234,6 +236,13 @@ __device__ __forceinline__ void ppt_stage_fwd(u64 *s, const u64 *w, const u64 *w
             }
         }
     }
+}
+
+template <int T, int M, int LEN>
+__device__ __forceinline__ void ppt_stage_fwd(u64 *s, const u64 *w, const u64 *wp, const u64 *dc, u64 q, u64 one_p,
+                                              const SfPpMod &P)
+{
+    ppt_stage_fwd_ld<T, M, LEN>(s, [s](int i) { return s[i]; }, w, wp, dc, q, one_p, P);
 }
 
 template <int T, int M, int LEN>
@@ -272,6 +281,17 @@ __device__ __forceinline__ void ppt_forward(u64 *s, const u64 *w, const u64 *wp,
     ppt_stage_fwd<T, M, LEN>(s, w, wp, dc, q, one_p, P);
     __syncthreads();
     if constexpr (LEN / T >= T) ppt_forward<T, M, LEN / T>(s, w, wp, dc, q, one_p, P);
+}
+
+// the whole forward transform with the first stage's inputs read through
+// ld(index), index < M (each read once), e.g. straight from global memory
+template <int T, int M, class LD>
+__device__ __forceinline__ void ppt_forward_ld(u64 *s, LD ld, const u64 *w, const u64 *wp, const u64 *dc, u64 q,
+                                               u64 one_p, const SfPpMod &P)
+{
+    ppt_stage_fwd_ld<T, M, M>(s, ld, w, wp, dc, q, one_p, P);
+    __syncthreads();
+    if constexpr (M / T >= T) ppt_forward<T, M, M / T>(s, w, wp, dc, q, one_p, P);
 }
 
 template <int T, int M, int LEN>

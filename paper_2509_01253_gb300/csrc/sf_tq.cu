@@ -86,6 +86,22 @@ __device__ __forceinline__ void tq_forward(u64 *s, const SfPpRing &R, int j)
     }
 }
 
+// the same with the first stage reading its inputs through ld(index), index < M
+template <int T, int ALPHA, class LD>
+__device__ __forceinline__ void tq_forward_ld(u64 *s, LD ld, const SfPpRing &R, int j)
+{
+    if constexpr (T == 0) {
+        for (int e = threadIdx.x; e < R.M; e += blockDim.x) s[e] = ld(e);
+        __syncthreads();
+        pp_forward(s, R, j);
+    } else {
+        constexpr int M = SfPpT<T, ALPHA>::M, H = (T - 1) / 2;
+        const SfPpMod &P = R.mod[j];
+        ppt_forward_ld<T, M>(s, ld, R.w + (size_t)j * M, R.w_p + (size_t)j * M, R.dftc + (size_t)j * H * H * 4, P.q,
+                             P.one_p, P);
+    }
+}
+
 // inverse transform, scaled by M^-1
 template <int T, int ALPHA>
 __device__ __forceinline__ void tq_inverse(u64 *s, const SfPpRing &R, int j)
@@ -224,12 +240,16 @@ __global__ void __launch_bounds__(SfTqShape<T, ALPHA>::NT, SfTqShape<T, ALPHA>::
 #pragma unroll
         for (int x = 0; x < EPT; ++x) acc_a[x] = acc_b[x] = 0;
         for (int i = 0; i < G.l; ++i) {
-            for (int e = threadIdx.x; e < M; e += NT) {
-                const int d = e < N ? dig[(size_t)i * N + e] : 0;
-                vec[e] = d >= 0 ? (u64)d : P.q - (u64)(-d);
-            }
-            __syncthreads();
-            tq_forward<T, ALPHA>(vec, R, j);
+            // digit i lifted mod p_j as the first stage reads it
+            const int16_t *di = dig + (size_t)i * N;
+            const u64 pq = P.q;
+            tq_forward_ld<T, ALPHA>(
+                vec,
+                [di, N, pq](int e) -> u64 {
+                    const int d = e < N ? di[e] : 0;
+                    return d >= 0 ? (u64)d : pq - (u64)(-d);
+                },
+                R, j);
             const u64 *ka = key + ((size_t)(i * 2 + 0) * 2 + j) * M;
             const u64 *kb = key + ((size_t)(i * 2 + 1) * 2 + j) * M;
 #pragma unroll
@@ -283,13 +303,9 @@ __global__ void __launch_bounds__(SfTqShape<T, ALPHA>::NT)
     const u64 *x = a + blockIdx.x * sa;
     for (int j = 0; j < 2; ++j) {
         const SfPpMod &P = R.mod[j];
-        for (int e = threadIdx.x; e < M; e += NT) {
-            va[e] = e < N ? sf_reduce(x[e] & SF_TQ_MASK, P.q, P.one_p) : 0;
-            vs[e] = e < N ? tq_lift_signed(s[e], P) : 0;
-        }
-        __syncthreads();
-        tq_forward<T, ALPHA>(va, R, j);
-        tq_forward<T, ALPHA>(vs, R, j);
+        tq_forward_ld<T, ALPHA>(
+            va, [x, N, &P](int e) -> u64 { return e < N ? sf_reduce(x[e] & SF_TQ_MASK, P.q, P.one_p) : 0; }, R, j);
+        tq_forward_ld<T, ALPHA>(vs, [s, N, &P](int e) -> u64 { return e < N ? tq_lift_signed(s[e], P) : 0; }, R, j);
         for (int e = threadIdx.x; e < M; e += NT) va[e] = pp_mulmod(va[e], vs[e], P);
         __syncthreads();
         tq_inverse<T, ALPHA>(va, R, j);
@@ -318,9 +334,9 @@ __global__ void __launch_bounds__(SfTqShape<T, ALPHA>::NT)
     const int j = blockIdx.x, p = blockIdx.y, i = p / 2, part = p % 2;
     const SfPpMod &P = R.mod[j];
     const u64 *x = (part ? kb : ka) + (size_t)i * R.N;
-    for (int e = threadIdx.x; e < R.M; e += NT) vec[e] = e < R.N ? sf_reduce(x[e] & SF_TQ_MASK, P.q, P.one_p) : 0;
-    __syncthreads();
-    tq_forward<T, ALPHA>(vec, R, j);
+    const int N = R.N;
+    tq_forward_ld<T, ALPHA>(
+        vec, [x, N, &P](int e) -> u64 { return e < N ? sf_reduce(x[e] & SF_TQ_MASK, P.q, P.one_p) : 0; }, R, j);
     u64 *dst = key + ((size_t)(i * 2 + part) * 2 + j) * R.M;
     const size_t kw = (size_t)4 * l * R.M;
     for (int e = threadIdx.x; e < R.M; e += NT) {
