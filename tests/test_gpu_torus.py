@@ -237,3 +237,32 @@ def test_tq_table2_trace_decodes_to_the_trace():
         assert S.T.decode(_L(_host(ph)[0]), b) == [v % 2 ** b for v in S.R.tower_trace(mu.tolist(), 0)]
     finally:
         sf.sf_tq_ring_destroy(S.r)
+
+
+def test_tq_edge_cases():
+    """Input words are read modulo 2^53 (high bits set change nothing), a single
+    ciphertext, gamma = alpha (no automorphism: the trace is the input, zero
+    key switches), a key prepared twice gives the same words, and a negative
+    automorphism index is taken modulo M."""
+    S = _Setup(3, 3, 512, 3, 601)
+    try:
+        _, _, _, ct = S.encrypt(1)
+        hct = _host(ct)
+        h = 10
+        d_kb, d_key, ka_l, kb_want = S.key(h)
+        ref = S.T.keyswitch(S.ct_lists(hct[0]), h, ka_l, kb_want)
+        dirty = hct.copy()
+        dirty |= np.uint64(0x7FF) << np.uint64(53)               # bits 53..63 set
+        out = torch.zeros_like(ct)
+        sf.sf_tq_keyswitch(S.r, _dev(dirty), out, 1, h, d_key)
+        assert S.ct_lists(_host(out)[0]) == ref
+        sf.sf_tq_keyswitch(S.r, ct, out, 1, h - S.R.M, d_key)     # h - M = h (mod M)
+        assert S.ct_lists(_host(out)[0]) == ref
+        again = torch.zeros_like(d_key)
+        sf.sf_tq_key_prepare(S.r, _dev(np.array(ka_l, dtype=np.uint64)), d_kb, again)
+        assert torch.equal(again, d_key)
+        tr = torch.zeros_like(ct)
+        assert sf.sf_tq_hom_trace(S.r, ct, tr, 1, S.R.alpha, {}) == 0
+        assert torch.equal(tr, ct)
+    finally:
+        sf.sf_tq_ring_destroy(S.r)
