@@ -41,3 +41,19 @@ def test_tq_ring_needs_a_device():
     with pytest.raises(sf.SafhireError) as e:
         sf.sf_tq_ring_create(5, 5, 310, 5, 0)
     assert e.value.status == sf.SF_ECUDA
+
+
+def test_tq_calls_reject_a_null_ring():
+    """Every torus call checks its ring and buffers before any device work."""
+    for call in (lambda: sf.sf_tq_ring_info(None),
+                 lambda: sf.sf_tq_decompose(None, 8, 8, 1),
+                 lambda: sf.sf_tq_encrypt(None, 8, 8, 8, 8, 8, 1),
+                 lambda: sf.sf_tq_decrypt(None, 8, 8, 8, 1),
+                 lambda: sf.sf_tq_ksk(None, 8, 2, 8, 8, 8),
+                 lambda: sf.sf_tq_key_prepare(None, 8, 8, 8),
+                 lambda: sf.sf_tq_keyswitch(None, 8, 16, 1, 2, 8),
+                 lambda: sf.sf_tq_hom_trace(None, 8, 16, 1, 0, {})):
+        with pytest.raises(sf.SafhireError) as e:
+            call()
+        assert e.value.status == sf.SF_EINVAL
+    sf.sf_tq_ring_destroy(None)   # a null ring is ignored
