@@ -570,7 +570,8 @@ sf_status sf_pp_hom_trace(sf_pp_ring *ring, const uint64_t *d_ct, uint64_t *d_ou
  * uniform masks a and ka.  Products are exact: computed over Z through two NTT
  * primes p_0, p_1 = 1 (mod M) of 50 bits and the CRT, then taken mod 2^53.  All
  * buffers are device memory owned by the caller; every call is asynchronous on
- * `stream` and uses a grow-only work buffer of the ring. */
+ * `stream` and uses a grow-only work buffer of the ring, so calls on one ring
+ * must not overlap in time (growing the buffer synchronizes the device). */
 typedef struct sf_tq_ring sf_tq_ring;
 
 /* The ring for (t, alpha) with the gadget (D, l).  Errors: SF_EINVAL (the
