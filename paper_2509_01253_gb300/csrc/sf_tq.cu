@@ -72,21 +72,8 @@ struct SfTqShape<0, ALPHA> {
     static constexpr int NT = SF_PP_THREADS, MMAX = SF_PP_MAX_M, MINB = 1;
 };
 
-// forward transform of the block's length-M vector modulo prime j
-template <int T, int ALPHA>
-__device__ __forceinline__ void tq_forward(u64 *s, const SfPpRing &R, int j)
-{
-    if constexpr (T == 0) {
-        pp_forward(s, R, j);
-    } else {
-        constexpr int M = SfPpT<T, ALPHA>::M, H = (T - 1) / 2;
-        const SfPpMod &P = R.mod[j];
-        ppt_forward<T, M, M>(s, R.w + (size_t)j * M, R.w_p + (size_t)j * M, R.dftc + (size_t)j * H * H * 4, P.q,
-                             P.one_p, P);
-    }
-}
-
-// the same with the first stage reading its inputs through ld(index), index < M
+// forward transform of the block's length-M vector modulo prime j, the first
+// stage reading its inputs through ld(index), index < M (each read once)
 template <int T, int ALPHA, class LD>
 __device__ __forceinline__ void tq_forward_ld(u64 *s, LD ld, const SfPpRing &R, int j)
 {
